@@ -1,0 +1,149 @@
+/*
+ * dpa1.h - C ABI of the GB300 DPA-1 (se_atten) energy / force / virial engine.
+ *
+ * The calls follow the contract of the paper's DeepmdModel wrapper around
+ * deepmd::compute() (Sec. IV-A): a model is loaded once with its type map,
+ * cutoff and neighbour cap, and each call maps coordinates, box and atom
+ * types to the total energy, per-atom forces and the virial.  The energy is
+ * a sum of atomic energies e_i = Phi(D_i) of the descriptor D_i built from
+ * the full neighbour list of atom i (Sec. II-B, Eq. eq_totE_singleAtomE),
+ * and the forces are its exact negative gradient (Eq. eq_forceGradE,
+ * Eq. eq_forceAtomicEnergy).
+ *
+ * Conventions shared by every call:
+ *   - Units: Angstrom for lengths, eV for energies, eV/A for forces, eV for
+ *     the virial.  Unit conversion for an MD engine is the caller's job.
+ *   - The box is 9 doubles, row-major cell vectors; it must be orthorhombic
+ *     (off-diagonal entries exactly 0) with every edge > 2 * rcut, else
+ *     DP_ERR_BOX.
+ *   - coord is [natoms][3] double, atype is [natoms] int in [0, ntypes).
+ *   - Outputs: energy [1], force [natoms][3], virial [9] (row-major,
+ *     W_ab = -sum_ij r_ij,a dE/dr_ij,b), atom_energy [natoms] (nullable).
+ *   - The caller owns every array it passes.  The library owns the model and
+ *     its device workspace.  No call keeps a pointer after it returns.
+ *   - Every call returns a dp_status; no C++ exception crosses the ABI.  The
+ *     text of the last error of the calling thread is dp_last_error().
+ *   - One model is used by one host thread / stream at a time.
+ */
+#ifndef DPA1_H
+#define DPA1_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define DP_API __attribute__((visibility("default")))
+#else
+#define DP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dp_model dp_model; /* opaque, library-owned */
+
+enum dp_status {
+  DP_OK = 0,
+  DP_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, type out of range) */
+  DP_ERR_IO = -2,       /* weight file missing, truncated or of another format */
+  DP_ERR_BOX = -3,      /* box not orthorhombic or an edge <= 2 * rcut */
+  DP_ERR_CAPACITY = -4, /* natoms above the reserved size, or a device-side buffer overflowed */
+  DP_ERR_CUDA = -5,     /* a CUDA runtime call failed */
+  DP_ERR_TIMEOUT = -6,  /* a bounded device-side wait gave up */
+  DP_ERR_NAN = -7,      /* non-finite coordinates */
+  DP_ERR_UNSUPPORTED = -8 /* model shape this build has no kernel for */
+};
+
+enum dp_precision {
+  DP_PREC_FP32 = 0, /* every matrix product in FP32 SIMT arithmetic */
+  DP_PREC_BF16 = 1  /* network matrix products on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+};
+
+/* Load a model.
+ *   weights_path : binary weight file (layout documented in synth/model.py).
+ *   type_map     : ntypes element names; must equal the file's map, in order
+ *                  (type id t of atype is type_map[t]).  May be NULL to accept
+ *                  the file's map.
+ *   rcut, rcut_smth, sel : must equal the file's values (Sec. II-C: the
+ *                  cutoff of the full neighbour list and its cap), else
+ *                  DP_ERR_ARG.  Pass a negative value to accept the file's.
+ *   precision    : DP_PREC_FP32 or DP_PREC_BF16.
+ *   device       : CUDA device ordinal; the model's memory lives there.
+ * On success *out is a new model; release it with dp_free. */
+DP_API int dp_init(dp_model** out, const char* weights_path, const char* const* type_map, int ntypes,
+            double rcut, double rcut_smth, int sel, int precision, int device);
+
+/* Energy, forces and virial of one frame from HOST arrays (Sec. IV-A,
+ * deepmd::compute()).  Copies inputs to the device, runs the whole path on
+ * the model's stream, copies results back and synchronises.  Grows the
+ * workspace when natoms exceeds the reserved size.  natoms == 0 gives
+ * zero energy and virial. */
+DP_API int dp_compute(dp_model* m, int natoms, const double* coord, const double* box, const int* atype,
+               double* energy, double* force, double* virial, double* atom_energy);
+
+/* Same as dp_compute with DEVICE arrays on the caller's CUDA stream
+ * (cudaStream_t passed as void*; NULL = the legacy default stream).  Never
+ * synchronises the host and never allocates, so it can be captured in a
+ * CUDA graph.  natoms must not exceed the size reserved with dp_reserve
+ * (DP_ERR_CAPACITY otherwise, nothing launched).  Device-side failures (box
+ * check, buffer overflow) are recorded in a device flag read by
+ * dp_get_status; the outputs are then unspecified. */
+DP_API int dp_compute_device(dp_model* m, int natoms, const double* d_coord, const double* d_box,
+                      const int* d_atype, double* d_energy, double* d_force, double* d_virial,
+                      double* d_atom_energy, void* cuda_stream);
+
+/* Several independent frames of uneven size from HOST arrays.  Frame f owns
+ * atoms [atom_offsets[f], atom_offsets[f+1]) of coord / atype / force and
+ * box[9f .. 9f+8], energy[f], virial[9f .. 9f+8].  Frames never interact. */
+DP_API int dp_compute_batch(dp_model* m, int nframes, const int* atom_offsets, const double* coord,
+                     const double* box, const int* atype, double* energy, double* force,
+                     double* virial);
+
+/* Pre-size the device workspace for up to max_atoms atoms (needed before
+ * dp_compute_device and before capturing it in a CUDA graph). */
+DP_API int dp_reserve(dp_model* m, int max_atoms);
+
+/* Switch the arithmetic of the network products (enum dp_precision). */
+DP_API int dp_set_precision(dp_model* m, int precision);
+
+/* Synchronise the model's last stream and return (then clear) the status
+ * recorded by device-side checks of asynchronous calls. */
+DP_API int dp_get_status(dp_model* m);
+
+/* Full neighbour list of every atom (Sec. II-C): atoms j != i with
+ * |mic(r_j - r_i)| < rcut, the sel nearest kept, sorted by (|r_ij|^2, j),
+ * each row padded with -1 to 128 entries.  DEVICE arrays: d_nlist
+ * [natoms][128] int, d_nnei [natoms] int (kept count).  Distances are
+ * evaluated in FP64 without fused multiply-adds, so the list is exactly
+ * reproducible on the host.  Same capacity and status rules as
+ * dp_compute_device. */
+DP_API int dp_nlist_device(dp_model* m, int natoms, const double* d_coord, const double* d_box,
+                    int* d_nlist, int* d_nnei, void* cuda_stream);
+
+/* Largest neighbour count and number of atoms whose candidate set exceeded
+ * sel in the last call (the sel cap is a property of the method, not an
+ * error). */
+DP_API int dp_stats(const dp_model* m, int* max_nnei, long long* n_truncated);
+
+/* Parse the header of a weight file on the host only (no GPU needed).
+ * ints16 receives the 16 header integers and dbls8 the 8 header doubles
+ * described in synth/model.py; either may be NULL. */
+DP_API int dp_inspect_weights(const char* weights_path, int* ints16, double* dbls8);
+
+/* Diagnostics: copy the named internal device buffer of the last call to
+ * host memory (at most bytes bytes).  Names: "nlist", "env", "G0", "G1",
+ * "G2", "D", "e", "g".  Returns the number of bytes copied, or a negative
+ * dp_status. */
+DP_API long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t bytes);
+
+/* Text of the calling thread's last error ("" if none). */
+DP_API const char* dp_last_error(void);
+
+/* Release the model and its device memory.  NULL is allowed. */
+DP_API void dp_free(dp_model* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPA1_H */

@@ -1,0 +1,200 @@
+"""ctypes binding of ``libdpa1.so`` (the C ABI of ``include/dpa1.h``).
+
+Argument marshalling only: every stage of the energy / force / virial path
+runs in the library's CUDA kernels.  Importing this module loads the library
+and raises ``ImportError`` if it has not been built (there is no fallback).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libdpa1.so")
+
+DP_OK = 0
+STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_IO", -3: "DP_ERR_BOX", -4: "DP_ERR_CAPACITY",
+          -5: "DP_ERR_CUDA", -6: "DP_ERR_TIMEOUT", -7: "DP_ERR_NAN", -8: "DP_ERR_UNSUPPORTED"}
+PRECISION = {"fp32": 0, "bf16": 1}
+
+EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_batch", "dp_reserve", "dp_set_precision",
+           "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
+           "dp_last_error", "dp_free")
+
+
+class DPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdpa1.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.POINTER(ctypes.c_int)
+    lib.dp_init.argtypes = [ctypes.POINTER(P), ctypes.c_char_p, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
+                            ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.dp_compute.argtypes = [P, ctypes.c_int, D, D, I, D, D, D, D]
+    lib.dp_compute_device.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.dp_compute_batch.argtypes = [P, ctypes.c_int, I, D, D, I, D, D, D]
+    lib.dp_reserve.argtypes = [P, ctypes.c_int]
+    lib.dp_set_precision.argtypes = [P, ctypes.c_int]
+    lib.dp_get_status.argtypes = [P]
+    lib.dp_nlist_device.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+    lib.dp_stats.argtypes = [P, I, ctypes.POINTER(ctypes.c_longlong)]
+    lib.dp_inspect_weights.argtypes = [ctypes.c_char_p, I, D]
+    lib.dp_debug_copy.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t]
+    lib.dp_debug_copy.restype = ctypes.c_longlong
+    lib.dp_last_error.argtypes = []
+    lib.dp_last_error.restype = ctypes.c_char_p
+    lib.dp_free.argtypes = [P]
+    lib.dp_free.restype = None
+    for name in EXPORTS:
+        if name not in ("dp_debug_copy", "dp_last_error", "dp_free"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int) -> None:
+    if code != DP_OK:
+        raise DPError(code, load_library().dp_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def box9(box) -> np.ndarray:
+    b = np.asarray(box, dtype=np.float64)
+    if b.shape == (3,):
+        b = np.diag(b)
+    return np.ascontiguousarray(b.reshape(9))
+
+
+def inspect_weights(path: str) -> Tuple[np.ndarray, np.ndarray]:
+    ints = np.zeros(16, dtype=np.int32)
+    dbls = np.zeros(8, dtype=np.float64)
+    _check(load_library().dp_inspect_weights(path.encode(), _iptr(ints), _dptr(dbls)))
+    return ints, dbls
+
+
+class DPA1:
+    """One loaded DPA-1 model on one GPU (``dp_init`` .. ``dp_free``)."""
+
+    def __init__(self, weights_path: str, precision: str = "fp32", device: int = 0,
+                 type_map: Optional[Sequence[str]] = None, rcut: float = -1.0, rcut_smth: float = -1.0,
+                 sel: int = -1):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        tm = None
+        nt = 0
+        if type_map is not None:
+            nt = len(type_map)
+            tm = (ctypes.c_char_p * nt)(*[t.encode() for t in type_map])
+        _check(self.lib.dp_init(ctypes.byref(h), weights_path.encode(), tm, nt, rcut, rcut_smth, sel,
+                                PRECISION[precision], device))
+        self.h = h
+        self.precision = precision
+        self.device = device
+
+    # -- host arrays ---------------------------------------------------------
+    def compute(self, coord, box, atype, atom_energy: bool = False):
+        """(E, F [N,3], W [3,3], e [N] or None) from host arrays (``dp_compute``)."""
+        c = np.ascontiguousarray(coord, dtype=np.float64).reshape(-1, 3)
+        t = np.ascontiguousarray(atype, dtype=np.int32)
+        b = box9(box)
+        n = c.shape[0]
+        e = np.zeros(1)
+        f = np.zeros((n, 3))
+        w = np.zeros(9)
+        ae = np.zeros(n) if atom_energy else None
+        _check(self.lib.dp_compute(self.h, n, _dptr(c), _dptr(b), _iptr(t), _dptr(e), _dptr(f), _dptr(w),
+                                   _dptr(ae) if ae is not None else None))
+        return float(e[0]), f, w.reshape(3, 3), ae
+
+    def compute_batch(self, frames):
+        """frames: list of (coord, atype, box); returns lists of E, F, W."""
+        offs = np.zeros(len(frames) + 1, dtype=np.int32)
+        for i, (c, t, b) in enumerate(frames):
+            offs[i + 1] = offs[i] + len(t)
+        coord = np.ascontiguousarray(np.concatenate([np.asarray(c).reshape(-1, 3) for c, _, _ in frames]), np.float64)
+        atype = np.ascontiguousarray(np.concatenate([np.asarray(t) for _, t, _ in frames]), np.int32)
+        box = np.ascontiguousarray(np.concatenate([box9(b) for _, _, b in frames]))
+        e = np.zeros(len(frames))
+        f = np.zeros((int(offs[-1]), 3))
+        w = np.zeros(9 * len(frames))
+        _check(self.lib.dp_compute_batch(self.h, len(frames), _iptr(offs), _dptr(coord), _dptr(box), _iptr(atype),
+                                         _dptr(e), _dptr(f), _dptr(w)))
+        return e, [f[offs[i]:offs[i + 1]] for i in range(len(frames))], w.reshape(-1, 3, 3)
+
+    # -- device arrays (torch tensors) ----------------------------------------
+    def compute_device(self, coord, box, atype, energy, force, virial, atom_energy=None, stream=None):
+        """``dp_compute_device`` on CUDA tensors; no host synchronisation."""
+        import torch
+
+        st = stream if stream is not None else torch.cuda.current_stream(coord.device).cuda_stream
+        _check(self.lib.dp_compute_device(self.h, int(coord.shape[0]), coord.data_ptr(), box.data_ptr(),
+                                          atype.data_ptr(), energy.data_ptr(), force.data_ptr(), virial.data_ptr(),
+                                          atom_energy.data_ptr() if atom_energy is not None else None, st))
+
+    def nlist_device(self, coord, box, stream=None):
+        import torch
+
+        n = int(coord.shape[0])
+        nl = torch.empty((n, 128), dtype=torch.int32, device=coord.device)
+        nn = torch.empty((n,), dtype=torch.int32, device=coord.device)
+        st = stream if stream is not None else torch.cuda.current_stream(coord.device).cuda_stream
+        _check(self.lib.dp_nlist_device(self.h, n, coord.data_ptr(), box.data_ptr(), nl.data_ptr(), nn.data_ptr(), st))
+        return nl, nn
+
+    def reserve(self, max_atoms: int) -> None:
+        _check(self.lib.dp_reserve(self.h, int(max_atoms)))
+
+    def set_precision(self, precision: str) -> None:
+        _check(self.lib.dp_set_precision(self.h, PRECISION[precision]))
+        self.precision = precision
+
+    def status(self) -> None:
+        _check(self.lib.dp_get_status(self.h))
+
+    def stats(self) -> Tuple[int, int]:
+        mx = ctypes.c_int()
+        tr = ctypes.c_longlong()
+        _check(self.lib.dp_stats(self.h, ctypes.byref(mx), ctypes.byref(tr)))
+        return mx.value, tr.value
+
+    def debug(self, name: str, shape, dtype=np.float32) -> np.ndarray:
+        out = np.zeros(shape, dtype=dtype)
+        r = self.lib.dp_debug_copy(self.h, name.encode(), out.ctypes.data, out.nbytes)
+        if r < 0:
+            _check(int(r))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dp_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,744 @@
+// C ABI of the DPA-1 engine: model loading, device workspace and the
+// orchestration of stages a1-a15 on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dpa1.h"
+#include "kernels.h"
+#include "model.h"
+
+using namespace dpa1;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) return fail(DP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct HostWeights {
+  int ints[16];
+  double dbls[8];
+  std::vector<std::string> type_map;
+  std::vector<std::pair<std::string, std::vector<double>>> arrays;
+  const std::vector<double>* get(const std::string& name) const {
+    for (auto& kv : arrays)
+      if (kv.first == name) return &kv.second;
+    return nullptr;
+  }
+};
+
+struct Shape {
+  std::string name;
+  size_t count;
+};
+
+std::vector<Shape> tensor_order(const int* I) {
+  const int nt = I[1], td = I[2], nemb = I[5], nattn = I[9], A = I[10], nfit = I[11];
+  const int* emb = I + 6;
+  const int* fit = I + 12;
+  const int m1 = emb[nemb - 1], axis = I[4];
+  std::vector<Shape> out;
+  out.push_back({"te_W", (size_t)nt * td});
+  out.push_back({"te_b", (size_t)td});
+  int fan = 2 * td;
+  for (int l = 0; l < nemb; ++l) {
+    out.push_back({"tt_W" + std::to_string(l), (size_t)fan * emb[l]});
+    out.push_back({"tt_b" + std::to_string(l), (size_t)emb[l]});
+    fan = emb[l];
+  }
+  fan = 1;
+  for (int l = 0; l < nemb; ++l) {
+    out.push_back({"em_W" + std::to_string(l), (size_t)fan * emb[l]});
+    out.push_back({"em_b" + std::to_string(l), (size_t)emb[l]});
+    fan = emb[l];
+  }
+  out.push_back({"davg", (size_t)nt * 4});
+  out.push_back({"dstd", (size_t)nt * 4});
+  for (int l = 0; l < nattn; ++l) {
+    std::string p = "at" + std::to_string(l) + "_";
+    out.push_back({p + "Wq", (size_t)m1 * A}); out.push_back({p + "bq", (size_t)A});
+    out.push_back({p + "Wk", (size_t)m1 * A}); out.push_back({p + "bk", (size_t)A});
+    out.push_back({p + "Wv", (size_t)m1 * A}); out.push_back({p + "bv", (size_t)A});
+    out.push_back({p + "Wo", (size_t)A * m1}); out.push_back({p + "bo", (size_t)m1});
+    out.push_back({p + "ln_g", (size_t)m1}); out.push_back({p + "ln_b", (size_t)m1});
+  }
+  fan = m1 * axis + td;
+  for (int l = 0; l < nfit; ++l) {
+    out.push_back({"fit_W" + std::to_string(l), (size_t)fan * fit[l]});
+    out.push_back({"fit_b" + std::to_string(l), (size_t)fit[l]});
+    fan = fit[l];
+  }
+  out.push_back({"fit_W" + std::to_string(nfit), (size_t)fan});
+  out.push_back({"fit_b" + std::to_string(nfit), (size_t)1});
+  out.push_back({"ebias", (size_t)nt});
+  return out;
+}
+
+int read_weights(const char* path, HostWeights& w, bool header_only) {
+  if (!path) return fail(DP_ERR_ARG, "weights_path is null");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(DP_ERR_IO, std::string("cannot open ") + path);
+  char magic[8];
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "DPA1WTS1", 8) == 0;
+  ok = ok && fread(w.ints, sizeof(int), 16, f) == 16 && fread(w.dbls, sizeof(double), 8, f) == 8;
+  if (!ok) { fclose(f); return fail(DP_ERR_IO, "bad weight file header"); }
+  const int* I = w.ints;
+  if (I[0] != 1 || I[1] < 1 || I[1] > 64 || I[2] < 1 || I[2] > 16 || I[3] < 1 || I[5] != 3 || I[9] < 0 ||
+      I[9] > 8 || I[11] < 1 || I[11] > 3 || I[4] < 1 || I[4] > I[8]) {
+    fclose(f);
+    return fail(DP_ERR_IO, "weight file header out of range");
+  }
+  for (int t = 0; t < I[1]; ++t) {
+    char name[8];
+    if (fread(name, 1, 8, f) != 8) { fclose(f); return fail(DP_ERR_IO, "truncated type map"); }
+    name[7] = 0;
+    w.type_map.emplace_back(name);
+  }
+  if (header_only) { fclose(f); return DP_OK; }
+  for (auto& s : tensor_order(I)) {
+    std::vector<double> v(s.count);
+    if (fread(v.data(), sizeof(double), s.count, f) != s.count) {
+      fclose(f);
+      return fail(DP_ERR_IO, "truncated weight array " + s.name);
+    }
+    for (double x : v)
+      if (!std::isfinite(x)) { fclose(f); return fail(DP_ERR_IO, "non-finite weight in " + s.name); }
+    w.arrays.emplace_back(s.name, std::move(v));
+  }
+  fclose(f);
+  return DP_OK;
+}
+
+// Init-time type tables on the device (a4): Z[t] = tanh(onehot(t) W + b) and
+// Gt[a][b] = net_t([Z[b], Z[a]]), evaluated in FP64 and stored in FP32.
+__global__ void k_type_tables(const double* __restrict__ teW, const double* __restrict__ teb,
+                              const double* __restrict__ tt, int nt, int td, int e0, int e1, int e2,
+                              float* __restrict__ tebd, float* __restrict__ Gt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nt * nt) return;
+  const int a = p / nt, b = p % nt;
+  double x[256], y[256];
+  for (int c = 0; c < td; ++c) {
+    x[c] = tanh(teW[b * td + c] + teb[c]);       // neighbour type first
+    x[td + c] = tanh(teW[a * td + c] + teb[c]);  // centre type second
+  }
+  if (b == 0)
+    for (int c = 0; c < td; ++c) tebd[a * td + c] = (float)x[td + c];
+  const int widths[3] = {e0, e1, e2};
+  int in = 2 * td;
+  const double* wp = tt;
+  for (int l = 0; l < 3; ++l) {
+    const int out = widths[l];
+    const double* W = wp;
+    const double* bb = wp + (size_t)in * out;
+    for (int o = 0; o < out; ++o) {
+      double z = bb[o];
+      for (int i = 0; i < in; ++i) z += x[i] * W[(size_t)i * out + o];
+      const double t = tanh(z);
+      y[o] = (out == in) ? x[o] + t : (out == 2 * in) ? x[o % in] + t : t;
+    }
+    for (int o = 0; o < out; ++o) x[o] = y[o];
+    wp = bb + out;
+    in = out;
+  }
+  for (int o = 0; o < e2; ++o) Gt[(size_t)p * e2 + o] = (float)x[o];
+}
+
+}  // namespace
+
+namespace {
+
+template <class T>
+int dev_upload(dp_model* m, T** out, const std::vector<T>& host) {
+  void* p = nullptr;
+  CUDA_TRY(cudaMalloc(&p, std::max<size_t>(host.size(), 1) * sizeof(T)));
+  m->allocations.push_back(p);
+  if (!host.empty()) CUDA_TRY(cudaMemcpy(p, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = reinterpret_cast<T*>(p);
+  return DP_OK;
+}
+
+std::vector<float> to_f(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+std::vector<float> transpose_f(const std::vector<double>& v, int rows, int cols) {
+  std::vector<float> t((size_t)rows * cols);
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) t[(size_t)c * rows + r] = (float)v[(size_t)r * cols + c];
+  return t;
+}
+
+void free_workspace(Workspace& ws) {
+  if (ws.mem) cudaFree(ws.mem);
+  ws.mem = nullptr;
+  ws.cap = 0;
+}
+
+int alloc_workspace(dp_model* m, int cap) {
+  Workspace& ws = m->ws;
+  free_workspace(ws);
+  if (cap < 1) cap = 1;
+  const size_t rows = (size_t)cap * NP;
+  const int L = m->nattn, A = m->A, m1 = m->m1;
+  int fmax = m->fit_in;
+  for (int l = 0; l < m->nfit; ++l) fmax = std::max(fmax, m->fit[l]);
+  // cells: edge >= rcut and at most ~2 atoms per cell on average
+  int cap_dim = (int)std::cbrt((double)cap * 2.0);
+  cap_dim = std::max(3, std::min(cap_dim, 1024));
+  ws.cap_dim = cap_dim;
+  ws.cell_cap = cap_dim * cap_dim * cap_dim;
+  int dev_sm = 0;
+  cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, m->device);
+  ws.attn_scratch_blocks = std::max(1, dev_sm);
+  auto plan = [&](Arena& a) {
+    ws.grid = a.take<CellGrid>(1);
+    ws.cell_of = a.take<int>(cap);
+    ws.cell_count = a.take<int>(ws.cell_cap);
+    ws.cell_start = a.take<int>(ws.cell_cap + 1);
+    ws.cell_cursor = a.take<int>(ws.cell_cap);
+    ws.cell_atoms = a.take<int>(cap);
+    ws.nlist = a.take<int>(rows);
+    ws.nnei = a.take<int>(cap);
+    ws.ncand = a.take<int>(cap);
+    ws.rev_cnt = a.take<int>(cap);
+    ws.rev_rows = a.take<int>((size_t)cap * REV_CAP);
+    ws.R = a.take<float>(rows * 4);
+    ws.rw = a.take<float>(rows * 4);
+    ws.rv = a.take<float>(rows * 4);
+    ws.dR = a.take<float>(rows * 4);
+    ws.dgeo = a.take<float>(rows * 4);
+    ws.g = a.take<float>(rows * 4);
+    ws.G.assign(L + 1, nullptr);
+    for (int l = 0; l <= L; ++l) ws.G[l] = a.take<float>(rows * m1);
+    ws.QKV.assign(L, nullptr); ws.O.assign(L, nullptr); ws.Y.assign(L, nullptr); ws.stats.assign(L, nullptr);
+    if (m->precision == DP_PREC_FP32) {
+      for (int l = 0; l < L; ++l) {
+        ws.QKV[l] = a.take<float>(rows * 3 * A);
+        ws.O[l] = a.take<float>(rows * A);
+        ws.Y[l] = a.take<float>(rows * m1);
+        ws.stats[l] = a.take<float>(rows * 2);
+      }
+      ws.dY = a.take<float>(rows * m1);
+      ws.dO = a.take<float>(rows * (L > 0 ? A : 1));
+      ws.dQKV = a.take<float>(rows * (L > 0 ? 3 * A : 1));
+      ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 2 * NP * NP);
+    }
+    ws.dG = a.take<float>(rows * m1);
+    ws.T = a.take<float>((size_t)cap * 4 * m1);
+    ws.X = a.take<float>((size_t)cap * m->fit_in);
+    ws.dX = a.take<float>((size_t)cap * m->fit_in);
+    ws.e = a.take<float>(cap);
+    ws.H.assign(m->nfit, nullptr);
+    for (int l = 0; l < m->nfit; ++l) ws.H[l] = a.take<float>((size_t)cap * m->fit[l]);
+    ws.dHa = a.take<float>((size_t)cap * fmax);
+    ws.dHb = a.take<float>((size_t)cap * fmax);
+    ws.dZ = a.take<float>((size_t)cap * fmax);
+    ws.partials = a.take<double>((size_t)((cap + 3) / 4 + 1) * 10);
+    ws.coord = a.take<double>((size_t)cap * 3);
+    ws.box = a.take<double>(9);
+    ws.force = a.take<double>((size_t)cap * 3);
+    ws.virial = a.take<double>(9);
+    ws.energy = a.take<double>(1);
+    ws.atom_energy = a.take<double>(cap);
+    ws.atype = a.take<int>(cap);
+    if (m->precision == DP_PREC_BF16) tc_plan_buffers(m, a, cap);
+  };
+  Arena probe;
+  plan(probe);
+  const size_t bytes = probe.off;
+  void* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DP_ERR_CUDA, "workspace allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                 cudaGetErrorString(e));
+  }
+  Arena real;
+  real.base = reinterpret_cast<char*>(mem);
+  real.cap = bytes;
+  plan(real);
+  ws.mem = mem;
+  ws.bytes = bytes;
+  ws.cap = cap;
+  return DP_OK;
+}
+
+int check_model(const dp_model* m) {
+  if (!m) return fail(DP_ERR_ARG, "model is null");
+  return DP_OK;
+}
+
+int translate_err(int bits) {
+  if (bits & ERR_BOX) return fail(DP_ERR_BOX, "box must be orthorhombic with every edge > 2*rcut");
+  if (bits & ERR_NAN) return fail(DP_ERR_NAN, "non-finite coordinate");
+  if (bits & ERR_TYPE) return fail(DP_ERR_ARG, "atom type out of range");
+  if (bits & ERR_TIMEOUT) return fail(DP_ERR_TIMEOUT, "a device-side wait gave up");
+  if (bits & ERR_CAPACITY) return fail(DP_ERR_CAPACITY, "a device-side buffer overflowed (neighbour candidates or reverse list)");
+  return DP_OK;
+}
+
+// Stages a1-a2 on the stream.
+void run_neighbors(dp_model* m, int n, const double* coord, const double* box, const int* atype, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  NbrArgs a;
+  a.coord = coord; a.box = box; a.atype = atype;
+  a.n = n; a.ntypes = m->nt; a.sel = m->sel; a.rcut = m->rcut;
+  a.cap_dim = ws.cap_dim; a.cell_cap = ws.cell_cap; a.grid = ws.grid;
+  a.cell_of = ws.cell_of; a.cell_count = ws.cell_count; a.cell_start = ws.cell_start;
+  a.cell_cursor = ws.cell_cursor; a.cell_atoms = ws.cell_atoms;
+  a.nlist = ws.nlist; a.nnei = ws.nnei; a.ncand = ws.ncand; a.err = m->d_err;
+  launch_neighbors(a, st);
+}
+
+// The FP32 network path (stages a5-a13) between the environment matrix and
+// the per-pair gradient.
+void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
+  // a5: embedding
+  EmbedArgs ea{};
+  ea.R = ws.R; ea.nlist = ws.nlist; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
+  launch_embed_fwd(ea, m->emb, st);
+  // a6: attention layers
+  for (int l = 0; l < L; ++l) {
+    const AttnLayerW& w = m->attn[l];
+    gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, 3 * A, m1, EPI_BIAS, st);
+    AttnArgs aa{};
+    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
+    aa.O = ws.O[l];
+    launch_attn_fwd_f32(aa, st);
+    gemm_f32(ws.O[l], A, w.Wo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, A, EPI_BIAS, st);
+    launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
+                      m1, st);
+  }
+  // a7: descriptor
+  DescArgs da{};
+  da.R = ws.R; da.G = ws.G[L]; da.nnei = ws.nnei; da.atype = atype; da.tebd = m->tebd;
+  da.n = n; da.m1 = m1; da.axis = m->axis; da.tebd_dim = m->td; da.sel = m->sel; da.fit_in = m->fit_in;
+  da.T = ws.T; da.X = ws.X; da.dX = ws.dX; da.dG = ws.dG; da.dR = ws.dR;
+  launch_desc_fwd(da, st);
+  // a8: fitting forward
+  int fan = m->fit_in;
+  const float* hin = ws.X;
+  for (int l = 0; l < m->nfit; ++l) {
+    const int out = m->fit[l];
+    const bool res = (l > 0 && out == fan);
+    gemm_f32(hin, fan, m->fitW[l], out, m->fitb[l], res ? hin : nullptr, fan, ws.H[l], out, n, out, fan,
+             res ? EPI_RES_TANH : EPI_TANH, st);
+    hin = ws.H[l];
+    fan = out;
+  }
+  // w_out and b_out are stored multiplied by out_scale
+  launch_energy_head(ws.H[m->nfit - 1], n, fan, m->w_out, m->b_out, 1.0f, m->ebias, atype, ws.e, st);
+  // a10: fitting backward, seeded with dE/dH_last = out_scale * w_out
+  launch_fill_rows(ws.dHa, m->w_out, n, fan, st);
+  float* dH = ws.dHa;
+  float* dHn = ws.dHb;
+  for (int l = m->nfit - 1; l >= 0; --l) {
+    const int out = m->fit[l];
+    const int in = l > 0 ? m->fit[l - 1] : m->fit_in;
+    const bool res = (l > 0 && out == in);
+    launch_tanh_bwd(dH, ws.H[l], res ? ws.H[l - 1] : nullptr, ws.dZ, (long long)n * out, st);
+    float* dst = l > 0 ? dHn : ws.dX;
+    gemm_f32(ws.dZ, out, m->fitWT[l], in, nullptr, res ? dH : nullptr, out, dst, in, n, in, out,
+             res ? EPI_RES : EPI_BIAS, st);
+    std::swap(dH, dHn);
+  }
+  // a11: descriptor backward -> dG (w.r.t. G_L) and dR
+  launch_desc_bwd(da, st);
+  // a12: attention backward
+  cudaMemsetAsync(ws.dgeo, 0, sizeof(float) * (size_t)rows * 4, st);
+  for (int l = L - 1; l >= 0; --l) {
+    const AttnLayerW& w = m->attn[l];
+    launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
+    gemm_f32(ws.dY, m1, w.WoT, A, nullptr, nullptr, 0, ws.dO, A, rows, A, m1, EPI_BIAS, st);
+    AttnArgs aa{};
+    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
+    aa.dO = ws.dO; aa.dQKV = ws.dQKV; aa.dgeo = ws.dgeo; aa.scratch = ws.attn_scratch;
+    aa.scratch_blocks = ws.attn_scratch_blocks;
+    launch_attn_bwd_f32(aa, st);
+    gemm_f32(ws.dQKV, 3 * A, w.WqkvT, m1, nullptr, nullptr, 0, ws.dG, m1, rows, m1, 3 * A, EPI_ACCUM, st);
+  }
+  // a13: embedding backward -> dR[:,0]
+  ea.dG0 = ws.dG; ea.dR = ws.dR;
+  launch_embed_bwd(ea, m->emb, st);
+}
+
+int run_device(dp_model* m, int n, const double* coord, const double* box, const int* atype, double* energy,
+               double* force, double* virial, double* atom_energy, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  if (n > ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
+  m->last_stream = st;
+  m->last_natoms = n;
+  run_neighbors(m, n, coord, box, atype, st);
+  // a3: environment matrix
+  EnvArgs ea{};
+  ea.coord = coord; ea.atype = atype; ea.grid = ws.grid; ea.nlist = ws.nlist; ea.n = n;
+  ea.davg = m->davg; ea.dstd = m->dstd; ea.rcs = (float)m->rcs; ea.rc = (float)m->rcut;
+  ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv;
+  launch_env(ea, st);
+  if (m->precision == DP_PREC_BF16)
+    tc_run_network(m, n, atype, st);
+  else
+    run_network_f32(m, n, atype, st);
+  // a14: per-pair gradient
+  EnvBwdArgs eb{};
+  eb.rv = ws.rv; eb.nlist = ws.nlist; eb.atype = atype; eb.n = n; eb.dstd = m->dstd;
+  eb.rcs = (float)m->rcs; eb.rc = (float)m->rcut; eb.dR = ws.dR; eb.dgeo = ws.dgeo; eb.g = ws.g;
+  launch_env_bwd(eb, st);
+  // a15: forces, virial, energy
+  launch_reverse(ws.nlist, n, ws.rev_cnt, ws.rev_rows, m->d_err, st);
+  ForceArgs fa{};
+  fa.g = ws.g; fa.rv = ws.rv; fa.nnei = ws.nnei; fa.rev_cnt = ws.rev_cnt; fa.rev_rows = ws.rev_rows; fa.e = ws.e;
+  fa.n = n; fa.force = force; fa.atom_energy = atom_energy; fa.partials = ws.partials; fa.energy = energy;
+  fa.virial = virial; fa.err = m->d_err;
+  launch_force_virial(fa, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+  return DP_OK;
+}
+
+int read_status(dp_model* m) {
+  int bits = 0;
+  CUDA_TRY(cudaMemcpy(&bits, m->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(m->d_err, 0, sizeof(int)));
+  return translate_err(bits);
+}
+
+int check_box_host(const double* box, double rcut) {
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b)
+      if (a != b && box[3 * a + b] != 0.0) return fail(DP_ERR_BOX, "box must be orthorhombic");
+    if (!(box[4 * a] > 2.0 * rcut)) return fail(DP_ERR_BOX, "every box edge must exceed 2*rcut");
+  }
+  return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dp_last_error(void) { return g_last_error.c_str(); }
+
+int dp_inspect_weights(const char* path, int* ints16, double* dbls8) {
+  HostWeights w;
+  int rc = read_weights(path, w, true);
+  if (rc != DP_OK) return rc;
+  if (ints16) memcpy(ints16, w.ints, sizeof(w.ints));
+  if (dbls8) memcpy(dbls8, w.dbls, sizeof(w.dbls));
+  return DP_OK;
+}
+
+int dp_init(dp_model** out, const char* weights_path, const char* const* type_map, int ntypes, double rcut,
+            double rcut_smth, int sel, int precision, int device) {
+  g_last_error.clear();
+  if (!out) return fail(DP_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (precision != DP_PREC_FP32 && precision != DP_PREC_BF16) return fail(DP_ERR_ARG, "unknown precision");
+  HostWeights w;
+  int rc = read_weights(weights_path, w, false);
+  if (rc != DP_OK) return rc;
+  const int* I = w.ints;
+  if (type_map) {
+    if (ntypes != I[1]) return fail(DP_ERR_ARG, "ntypes differs from the weight file");
+    for (int t = 0; t < ntypes; ++t)
+      if (!type_map[t] || w.type_map[t] != type_map[t])
+        return fail(DP_ERR_ARG, "type map differs from the weight file at type " + std::to_string(t));
+  }
+  if (rcut >= 0 && rcut != w.dbls[0]) return fail(DP_ERR_ARG, "rcut differs from the weight file");
+  if (rcut_smth >= 0 && rcut_smth != w.dbls[1]) return fail(DP_ERR_ARG, "rcut_smth differs from the weight file");
+  if (sel >= 0 && sel != I[3]) return fail(DP_ERR_ARG, "sel differs from the weight file");
+  if (I[3] > NP) return fail(DP_ERR_UNSUPPORTED, "sel above 128 is not supported");
+  if (I[8] > 128) return fail(DP_ERR_UNSUPPORTED, "embedding width above 128 is not supported");
+  if (I[9] > 0 && I[10] != 128) return fail(DP_ERR_UNSUPPORTED, "attention width other than 128 is not supported");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(DP_ERR_CUDA, "CUDA device " + std::to_string(device) + " is not available");
+  }
+  CUDA_TRY(cudaSetDevice(device));
+  dp_model* m = new dp_model();
+  m->device = device;
+  m->precision = precision;
+  memcpy(m->ints, I, sizeof(m->ints));
+  memcpy(m->dbls, w.dbls, sizeof(m->dbls));
+  m->type_map = w.type_map;
+  m->nt = I[1]; m->td = I[2]; m->sel = I[3]; m->axis = I[4];
+  m->emb[0] = I[6]; m->emb[1] = I[7]; m->emb[2] = I[8];
+  m->nattn = I[9]; m->A = I[10]; m->nfit = I[11];
+  for (int l = 0; l < 3; ++l) m->fit[l] = I[12 + l];
+  m->m1 = m->emb[2];
+  m->fit_in = m->m1 * m->axis + m->td;
+  m->rcut = w.dbls[0]; m->rcs = w.dbls[1]; m->shift = w.dbls[2]; m->ln_eps = w.dbls[3]; m->out_scale = w.dbls[4];
+  auto fail_free = [&](int code) { dp_free(m); return code; };
+  const int probe_widths[3] = {m->emb[0], m->emb[1], m->emb[2]};
+  if (!((probe_widths[0] == 25 && probe_widths[1] == 50 && probe_widths[2] == 100) ||
+        (probe_widths[0] == 16 && probe_widths[1] == 32 && probe_widths[2] == 64) ||
+        (probe_widths[0] == 32 && probe_widths[1] == 64 && probe_widths[2] == 128)))
+    return fail_free(fail(DP_ERR_UNSUPPORTED, "embedding widths without a kernel instance"));
+  // embedding net packed as W0 b0 W1 b1 W2 b2
+  std::vector<float> packed;
+  for (int l = 0; l < 3; ++l) {
+    auto* W = w.get("em_W" + std::to_string(l));
+    auto* b = w.get("em_b" + std::to_string(l));
+    packed.insert(packed.end(), W->begin(), W->end());
+    packed.insert(packed.end(), b->begin(), b->end());
+  }
+  if ((rc = dev_upload(m, &m->emb_packed, packed)) != DP_OK) return fail_free(rc);
+  if ((rc = dev_upload(m, &m->davg, to_f(*w.get("davg")))) != DP_OK) return fail_free(rc);
+  if ((rc = dev_upload(m, &m->dstd, to_f(*w.get("dstd")))) != DP_OK) return fail_free(rc);
+  if ((rc = dev_upload(m, &m->ebias, to_f(*w.get("ebias")))) != DP_OK) return fail_free(rc);
+  // type tables (a4) on the device
+  {
+    std::vector<double> tt;
+    for (int l = 0; l < 3; ++l) {
+      auto* W = w.get("tt_W" + std::to_string(l));
+      auto* b = w.get("tt_b" + std::to_string(l));
+      tt.insert(tt.end(), W->begin(), W->end());
+      tt.insert(tt.end(), b->begin(), b->end());
+    }
+    double *dteW, *dteb, *dtt;
+    if ((rc = dev_upload(m, &dteW, *w.get("te_W"))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &dteb, *w.get("te_b"))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &dtt, tt)) != DP_OK) return fail_free(rc);
+    std::vector<float> z((size_t)m->nt * m->td), gt((size_t)m->nt * m->nt * m->m1);
+    if ((rc = dev_upload(m, &m->tebd, z)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->Gt, gt)) != DP_OK) return fail_free(rc);
+    const int pairs = m->nt * m->nt;
+    k_type_tables<<<(pairs + 63) / 64, 64>>>(dteW, dteb, dtt, m->nt, m->td, m->emb[0], m->emb[1], m->emb[2], m->tebd,
+                                             m->Gt);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(fail(DP_ERR_CUDA, "type table kernel failed"));
+  }
+  const int A = m->A, m1 = m->m1;
+  m->attn.resize(m->nattn);
+  for (int l = 0; l < m->nattn; ++l) {
+    std::string p = "at" + std::to_string(l) + "_";
+    auto* Wq = w.get(p + "Wq"); auto* Wk = w.get(p + "Wk"); auto* Wv = w.get(p + "Wv");
+    std::vector<double> Wqkv((size_t)m1 * 3 * A);
+    for (int r = 0; r < m1; ++r)
+      for (int c = 0; c < A; ++c) {
+        Wqkv[(size_t)r * 3 * A + c] = (*Wq)[(size_t)r * A + c];
+        Wqkv[(size_t)r * 3 * A + A + c] = (*Wk)[(size_t)r * A + c];
+        Wqkv[(size_t)r * 3 * A + 2 * A + c] = (*Wv)[(size_t)r * A + c];
+      }
+    std::vector<double> bqkv;
+    for (auto nm : {"bq", "bk", "bv"}) bqkv.insert(bqkv.end(), w.get(p + nm)->begin(), w.get(p + nm)->end());
+    AttnLayerW& L = m->attn[l];
+    if ((rc = dev_upload(m, &L.Wqkv, to_f(Wqkv))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.WqkvT, transpose_f(Wqkv, m1, 3 * A))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.bqkv, to_f(bqkv))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.Wo, to_f(*w.get(p + "Wo")))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.WoT, transpose_f(*w.get(p + "Wo"), A, m1))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.bo, to_f(*w.get(p + "bo")))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.ln_g, to_f(*w.get(p + "ln_g")))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.ln_b, to_f(*w.get(p + "ln_b")))) != DP_OK) return fail_free(rc);
+  }
+  int fan = m->fit_in;
+  m->fitW.resize(m->nfit); m->fitWT.resize(m->nfit); m->fitb.resize(m->nfit);
+  for (int l = 0; l < m->nfit; ++l) {
+    auto* W = w.get("fit_W" + std::to_string(l));
+    if ((rc = dev_upload(m, &m->fitW[l], to_f(*W))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->fitWT[l], transpose_f(*W, fan, m->fit[l]))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->fitb[l], to_f(*w.get("fit_b" + std::to_string(l))))) != DP_OK) return fail_free(rc);
+    fan = m->fit[l];
+  }
+  {
+    // output layer, stored multiplied by out_scale: the forward head and the
+    // backward seed dE/dH_last use the same FP32 vector
+    auto* W = w.get("fit_W" + std::to_string(m->nfit));
+    std::vector<float> ws((size_t)fan);
+    for (int c = 0; c < fan; ++c) ws[c] = (float)((*W)[c] * m->out_scale);
+    if ((rc = dev_upload(m, &m->w_out, ws)) != DP_OK) return fail_free(rc);
+    m->b_out = (float)((*w.get("fit_b" + std::to_string(m->nfit)))[0] * m->out_scale);
+  }
+  if (precision == DP_PREC_BF16) {
+    std::string msg;
+    if ((rc = tc_init_weights(m, w.arrays, msg)) != DP_OK) return fail_free(fail(rc, msg));
+  }
+  {
+    void* p;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return fail_free(fail(DP_ERR_CUDA, "cudaMalloc failed"));
+    m->d_err = reinterpret_cast<int*>(p);
+    cudaMemset(m->d_err, 0, sizeof(int));
+  }
+  if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail_free(fail(DP_ERR_CUDA, "stream creation failed"));
+  if ((rc = alloc_workspace(m, 256)) != DP_OK) return fail_free(rc);
+  *out = m;
+  return DP_OK;
+}
+
+int dp_reserve(dp_model* m, int max_atoms) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (max_atoms < 0) return fail(DP_ERR_ARG, "max_atoms < 0");
+  CUDA_TRY(cudaSetDevice(m->device));
+  if (max_atoms <= m->ws.cap) return DP_OK;
+  CUDA_TRY(cudaDeviceSynchronize());
+  return alloc_workspace(m, max_atoms);
+}
+
+int dp_set_precision(dp_model* m, int precision) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (precision != DP_PREC_FP32 && precision != DP_PREC_BF16) return fail(DP_ERR_ARG, "unknown precision");
+  if (precision == m->precision) return DP_OK;
+  if (precision == DP_PREC_BF16 && !m->tcw.ready)
+    return fail(DP_ERR_UNSUPPORTED, "model was loaded without the BF16 weights; reload with DP_PREC_BF16");
+  CUDA_TRY(cudaSetDevice(m->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  m->precision = precision;
+  return alloc_workspace(m, m->ws.cap);
+}
+
+int dp_compute_device(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
+                      double* d_energy, double* d_force, double* d_virial, double* d_atom_energy, void* stream) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (natoms < 0) return fail(DP_ERR_ARG, "natoms < 0");
+  if (!d_box || !d_energy || !d_virial || (natoms > 0 && (!d_coord || !d_atype || !d_force)))
+    return fail(DP_ERR_ARG, "null device pointer");
+  if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
+  CUDA_TRY(cudaSetDevice(m->device));
+  return run_device(m, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, d_atom_energy,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dp_compute(dp_model* m, int natoms, const double* coord, const double* box, const int* atype, double* energy,
+               double* force, double* virial, double* atom_energy) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (natoms < 0) return fail(DP_ERR_ARG, "natoms < 0");
+  if (!box || !energy || !virial || (natoms > 0 && (!coord || !atype || !force)))
+    return fail(DP_ERR_ARG, "null host pointer");
+  int rc = check_box_host(box, m->rcut);
+  if (rc != DP_OK) return rc;
+  for (int i = 0; i < natoms; ++i)
+    if (atype[i] < 0 || atype[i] >= m->nt) return fail(DP_ERR_ARG, "atom type out of range");
+  for (long long i = 0; i < 3LL * natoms; ++i)
+    if (!std::isfinite(coord[i])) return fail(DP_ERR_NAN, "non-finite coordinate");
+  CUDA_TRY(cudaSetDevice(m->device));
+  if (natoms > m->ws.cap && (rc = dp_reserve(m, natoms)) != DP_OK) return rc;
+  Workspace& ws = m->ws;
+  cudaStream_t st = m->stream;
+  if (natoms > 0) {
+    CUDA_TRY(cudaMemcpyAsync(ws.coord, coord, sizeof(double) * 3 * natoms, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(ws.atype, atype, sizeof(int) * natoms, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaMemcpyAsync(ws.box, box, sizeof(double) * 9, cudaMemcpyHostToDevice, st));
+  rc = run_device(m, natoms, ws.coord, ws.box, ws.atype, ws.energy, ws.force, ws.virial, ws.atom_energy, st);
+  if (rc != DP_OK) return rc;
+  CUDA_TRY(cudaMemcpyAsync(energy, ws.energy, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(virial, ws.virial, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+  if (natoms > 0) {
+    CUDA_TRY(cudaMemcpyAsync(force, ws.force, sizeof(double) * 3 * natoms, cudaMemcpyDeviceToHost, st));
+    if (atom_energy)
+      CUDA_TRY(cudaMemcpyAsync(atom_energy, ws.atom_energy, sizeof(double) * natoms, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return read_status(m);
+}
+
+int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coord, const double* box,
+                     const int* atype, double* energy, double* force, double* virial) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (nframes < 0 || (nframes > 0 && (!off || !box || !energy || !virial))) return fail(DP_ERR_ARG, "bad batch arguments");
+  for (int f = 0; f < nframes; ++f) {
+    const int n = off[f + 1] - off[f];
+    if (n < 0) return fail(DP_ERR_ARG, "atom_offsets must be non-decreasing");
+    int rc = dp_compute(m, n, coord + 3LL * off[f], box + 9LL * f, atype + off[f], energy + f, force + 3LL * off[f],
+                        virial + 9LL * f, nullptr);
+    if (rc != DP_OK) return rc;
+  }
+  return DP_OK;
+}
+
+int dp_get_status(dp_model* m) {
+  if (check_model(m)) return DP_ERR_ARG;
+  CUDA_TRY(cudaSetDevice(m->device));
+  if (m->last_stream) CUDA_TRY(cudaStreamSynchronize(m->last_stream));
+  CUDA_TRY(cudaDeviceSynchronize());
+  return read_status(m);
+}
+
+int dp_nlist_device(dp_model* m, int natoms, const double* d_coord, const double* d_box, int* d_nlist, int* d_nnei,
+                    void* stream) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (natoms < 0 || !d_box || (natoms > 0 && (!d_coord || !d_nlist || !d_nnei))) return fail(DP_ERR_ARG, "bad arguments");
+  if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
+  CUDA_TRY(cudaSetDevice(m->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // types are not needed for the list: pass a zero-type buffer of the workspace
+  CUDA_TRY(cudaMemsetAsync(m->ws.atype, 0, sizeof(int) * (size_t)(natoms > 0 ? natoms : 1), st));
+  run_neighbors(m, natoms, d_coord, d_box, m->ws.atype, st);
+  if (natoms > 0) {
+    CUDA_TRY(cudaMemcpyAsync(d_nlist, m->ws.nlist, sizeof(int) * (size_t)natoms * NP, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_nnei, m->ws.nnei, sizeof(int) * (size_t)natoms, cudaMemcpyDeviceToDevice, st));
+  }
+  m->last_stream = st;
+  m->last_natoms = natoms;
+  return DP_OK;
+}
+
+int dp_stats(const dp_model* m, int* max_nnei, long long* n_truncated) {
+  if (!m) return fail(DP_ERR_ARG, "model is null");
+  const int n = m->last_natoms;
+  std::vector<int> nc((size_t)(n > 0 ? n : 1), 0);
+  if (n > 0 && cudaMemcpy(nc.data(), m->ws.ncand, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(DP_ERR_CUDA, "cudaMemcpy failed");
+  int mx = 0;
+  long long tr = 0;
+  for (int i = 0; i < n; ++i) {
+    mx = std::max(mx, std::min(nc[i], m->sel));
+    if (nc[i] > m->sel) ++tr;
+  }
+  if (max_nnei) *max_nnei = mx;
+  if (n_truncated) *n_truncated = tr;
+  return DP_OK;
+}
+
+long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t bytes) {
+  if (check_model(m) || !name || !host_dst) return DP_ERR_ARG;
+  Workspace& ws = m->ws;
+  const size_t n = (size_t)m->last_natoms, rows = n * NP;
+  const void* src = nullptr;
+  size_t sz = 0;
+  std::string s(name);
+  if (s == "nlist") { src = ws.nlist; sz = rows * sizeof(int); }
+  else if (s == "env") { src = ws.R; sz = rows * 4 * sizeof(float); }
+  else if (s == "g") { src = ws.g; sz = rows * 4 * sizeof(float); }
+  else if (s == "e") { src = ws.e; sz = n * sizeof(float); }
+  else if (s == "D") { src = ws.X; sz = n * m->fit_in * sizeof(float); }
+  else if (s.size() == 2 && s[0] == 'G' && s[1] >= '0' && s[1] - '0' <= m->nattn && !ws.G.empty()) {
+    src = ws.G[s[1] - '0']; sz = rows * m->m1 * sizeof(float);
+  }
+  if (!src) return fail(DP_ERR_ARG, "unknown buffer name");
+  sz = std::min(sz, bytes);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(DP_ERR_CUDA, "sync failed");
+  if (cudaMemcpy(host_dst, src, sz, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(DP_ERR_CUDA, "copy failed");
+  return (long long)sz;
+}
+
+void dp_free(dp_model* m) {
+  if (!m) return;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  free_workspace(m->ws);
+  tc_free_weights(m);
+  for (void* p : m->allocations) cudaFree(p);
+  if (m->d_err) cudaFree(m->d_err);
+  if (m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Shared definitions of the DPA-1 CUDA path (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace dpa1 {
+
+// Rows reserved per centre atom: the neighbour cap sel (<= 128) padded to one
+// 128-row tile, so that every per-atom matrix has a fixed 128-row shape.
+constexpr int NP = 128;
+// Candidate capacity of the neighbour search per centre (before the sel cap).
+constexpr int NBR_CAP = 256;
+// Capacity of the reverse neighbour list per atom (centres that list it).
+constexpr int REV_CAP = 256;
+
+// Bits of the device status flag.
+enum ErrBits : int {
+  ERR_BOX = 1,       // box not orthorhombic or an edge <= 2 rcut
+  ERR_CAPACITY = 2,  // candidate / reverse-list / workspace overflow
+  ERR_NAN = 4,       // non-finite coordinate
+  ERR_TIMEOUT = 8,   // a bounded wait gave up
+  ERR_TYPE = 16,     // atom type out of range
+};
+
+// Cell grid derived on the device from the (device) box.
+struct CellGrid {
+  double L[3];
+  int nc[3];
+  int ncells;
+  int ok;
+};
+
+__device__ __forceinline__ void set_err(int* err, int bits) { atomicOr(err, bits); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Minimum-image displacement component d - L * rint(d / L), every operation
+// rounded separately (no FMA contraction) so that the host can reproduce it
+// bit for bit.
+__device__ __forceinline__ double mic(double d, double L) {
+  return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+}
+
+// (dx*dx + dy*dy) + dz*dz without contraction.
+__device__ __forceinline__ double sqdist(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+}  // namespace dpa1

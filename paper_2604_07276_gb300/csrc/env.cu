@@ -1,0 +1,189 @@
+// Stage a3 (smooth environment matrix), a14 (its adjoint: the per-pair
+// gradient g_ij = dE/dr_ij) and a15 (forces and virial), plus the FP64
+// energy reduction a9.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dpa1 {
+
+// Smooth environment matrix (Sec. II-B, DP-SE): s(r) = w(r)/r with the C2
+// switch w, a row R_ij = (s, s x/r, s y/r, s z/r) normalised per centre type
+// by (R - davg)/dstd.  Displacements come from the FP64 coordinates through
+// the minimum image; the row is evaluated in FP64 and stored in FP32.
+__global__ void k_env(EnvArgs a) {
+  long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (long long)a.n * NP) return;
+  const int i = (int)(row / NP);
+  const int j = a.nlist[row];
+  float4 R = make_float4(0.f, 0.f, 0.f, 0.f), rw = R, rv = R;
+  if (j >= 0) {
+    const CellGrid g = *a.grid;
+    double dx = mic(a.coord[3 * j] - a.coord[3 * i], g.L[0]);
+    double dy = mic(a.coord[3 * j + 1] - a.coord[3 * i + 1], g.L[1]);
+    double dz = mic(a.coord[3 * j + 2] - a.coord[3 * i + 2], g.L[2]);
+    double d = sqrt(dx * dx + dy * dy + dz * dz);
+    double rcs = a.rcs, rc = a.rc;
+    double sw;
+    if (d < rcs) {
+      sw = 1.0;
+    } else if (d < rc) {
+      double u = (d - rcs) / (rc - rcs);
+      sw = u * u * u * (-6.0 * u * u + 15.0 * u - 10.0) + 1.0;
+    } else {
+      sw = 0.0;
+    }
+    double s = sw / d;
+    double hx = dx / d, hy = dy / d, hz = dz / d;
+    const int t = a.atype[i];
+    const float* av = a.davg + 4 * t;
+    const float* sv = a.dstd + 4 * t;
+    R = make_float4((float)((s - av[0]) / sv[0]), (float)((s * hx - av[1]) / sv[1]),
+                    (float)((s * hy - av[2]) / sv[2]), (float)((s * hz - av[3]) / sv[3]));
+    rw = make_float4((float)hx, (float)hy, (float)hz, (float)sw);
+    rv = make_float4((float)dx, (float)dy, (float)dz, (float)d);
+  }
+  reinterpret_cast<float4*>(a.R)[row] = R;
+  reinterpret_cast<float4*>(a.rw)[row] = rw;
+  reinterpret_cast<float4*>(a.rv)[row] = rv;
+}
+
+void launch_env(const EnvArgs& a, cudaStream_t st) {
+  long long rows = (long long)a.n * NP;
+  if (rows == 0) return;
+  k_env<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+}
+
+// Chain rule from dE/dR (4 columns), dE/dw and dE/drhat back to r_ij:
+//   R0 = s(d), R1..3 = q(d) r with q = s/d, w = sw(d), rhat = r/d.
+__global__ void k_env_bwd(EnvBwdArgs a) {
+  long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (long long)a.n * NP) return;
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (a.nlist[row] >= 0) {
+    const float4 rv = reinterpret_cast<const float4*>(a.rv)[row];
+    const float4 dR = reinterpret_cast<const float4*>(a.dR)[row];
+    const float4 dg = reinterpret_cast<const float4*>(a.dgeo)[row];
+    const int t = a.atype[row / NP];
+    const float d = rv.w;
+    const float inv = 1.0f / d;
+    const float hx = rv.x * inv, hy = rv.y * inv, hz = rv.z * inv;
+    float sw, dsw;
+    if (d < a.rcs) {
+      sw = 1.f; dsw = 0.f;
+    } else if (d < a.rc) {
+      const float w = a.rc - a.rcs;
+      const float u = (d - a.rcs) / w;
+      sw = u * u * u * (-6.f * u * u + 15.f * u - 10.f) + 1.f;
+      dsw = -30.f * u * u * (u - 1.f) * (u - 1.f) / w;
+    } else {
+      sw = 0.f; dsw = 0.f;
+    }
+    const float ds = dsw * inv - sw * inv * inv;           // d s / d d
+    const float q = sw * inv * inv;                         // s / d
+    const float dq = dsw * inv * inv - 2.f * sw * inv * inv * inv;
+    const float* sv = a.dstd + 4 * t;
+    const float r0 = dR.x / sv[0], r1 = dR.y / sv[1], r2 = dR.z / sv[2], r3 = dR.w / sv[3];
+    const float vdotr = r1 * rv.x + r2 * rv.y + r3 * rv.z;
+    const float radial = r0 * ds + dq * vdotr + dg.w * dsw;  // coefficient of rhat
+    const float hdot = dg.x * hx + dg.y * hy + dg.z * hz;
+    out.x = radial * hx + q * r1 + (dg.x - hdot * hx) * inv;
+    out.y = radial * hy + q * r2 + (dg.y - hdot * hy) * inv;
+    out.z = radial * hz + q * r3 + (dg.z - hdot * hz) * inv;
+  }
+  reinterpret_cast<float4*>(a.g)[row] = out;
+}
+
+void launch_env_bwd(const EnvBwdArgs& a, cudaStream_t st) {
+  long long rows = (long long)a.n * NP;
+  if (rows == 0) return;
+  k_env_bwd<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+}
+
+// Forces F_k = sum_j g_kj - sum_{i: k in N(i)} g_ik (Eq. eq_forceAtomicEnergy
+// with e_i depending on r_ij = x_j - x_i) and virial W = -sum r_ij (x) g_ij.
+// One warp per atom; the reverse rows are sorted so that every sum runs in a
+// fixed order (bitwise reproducible, no atomics).
+constexpr int FWARPS = 4;
+__global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
+  __shared__ int srev[FWARPS][REV_CAP];
+  __shared__ double sred[FWARPS][10];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * FWARPS + warp;
+  double f0 = 0, f1 = 0, f2 = 0;
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double ek = 0;
+  if (k < a.n) {
+    const int nn = a.nnei[k];
+    for (int s = lane; s < nn; s += 32) {
+      const size_t row = (size_t)k * NP + s;
+      const float4 g = reinterpret_cast<const float4*>(a.g)[row];
+      const float4 r = reinterpret_cast<const float4*>(a.rv)[row];
+      f0 += g.x; f1 += g.y; f2 += g.z;
+      v[0] -= (double)r.x * g.x; v[1] -= (double)r.x * g.y; v[2] -= (double)r.x * g.z;
+      v[3] -= (double)r.y * g.x; v[4] -= (double)r.y * g.y; v[5] -= (double)r.y * g.z;
+      v[6] -= (double)r.z * g.x; v[7] -= (double)r.z * g.y; v[8] -= (double)r.z * g.z;
+    }
+    int cnt = a.rev_cnt[k];
+    if (cnt > REV_CAP) cnt = REV_CAP;
+    int* rows = srev[warp];
+    int P = 1;
+    while (P < cnt) P <<= 1;
+    for (int t = lane; t < P; t += 32) rows[t] = t < cnt ? a.rev_rows[(size_t)k * REV_CAP + t] : 0x7fffffff;
+    __syncwarp();
+    for (int kk = 2; kk <= P; kk <<= 1)
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int t = lane; t < P; t += 32) {
+          int o = t ^ jj;
+          if (o > t) {
+            bool asc = (t & kk) == 0;
+            int x = rows[t], y = rows[o];
+            if (asc ? x > y : x < y) { rows[t] = y; rows[o] = x; }
+          }
+        }
+        __syncwarp();
+      }
+    for (int t = lane; t < cnt; t += 32) {
+      const float4 g = reinterpret_cast<const float4*>(a.g)[rows[t]];
+      f0 -= g.x; f1 -= g.y; f2 -= g.z;
+    }
+    f0 = warp_sum_d(f0); f1 = warp_sum_d(f1); f2 = warp_sum_d(f2);
+    if (lane == 0) {
+      a.force[3 * k] = f0; a.force[3 * k + 1] = f1; a.force[3 * k + 2] = f2;
+      ek = (double)a.e[k];
+      if (a.atom_energy) a.atom_energy[k] = ek;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) v[c] = warp_sum_d(v[c]);
+  if (lane == 0) {
+    for (int c = 0; c < 9; ++c) sred[warp][c] = v[c];
+    sred[warp][9] = ek;
+  }
+  __syncthreads();
+  if (threadIdx.x < 10) {
+    double s = 0;
+    for (int w = 0; w < FWARPS; ++w) s += sred[w][threadIdx.x];
+    a.partials[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, double* __restrict__ energy,
+                           double* __restrict__ virial) {
+  __shared__ double red[10][32];
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;  // 10 warps, one per quantity
+  double s = 0;
+  for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * 10 + c];
+  s = warp_sum_d(s);
+  if (lane == 0) red[c][0] = s;
+  __syncthreads();
+  if (threadIdx.x < 9) virial[threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x == 9) *energy = red[9][0];
+}
+
+void launch_force_virial(const ForceArgs& a, cudaStream_t st) {
+  const int nb = a.n > 0 ? (a.n + FWARPS - 1) / FWARPS : 0;
+  if (nb > 0) k_force<<<nb, 32 * FWARPS, 0, st>>>(a);
+  k_finalize<<<1, 320, 0, st>>>(a.partials, nb, a.energy, a.virial);
+}
+
+}  // namespace dpa1

@@ -1,0 +1,136 @@
+// Host-side launchers of the DPA-1 kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace dpa1 {
+
+struct CellGrid;
+
+struct NbrArgs {
+  const double* coord;
+  const double* box;
+  const int* atype;
+  int n, ntypes, sel;
+  double rcut;
+  int cap_dim, cell_cap;
+  CellGrid* grid;
+  int *cell_of, *cell_count, *cell_start, *cell_cursor, *cell_atoms;
+  int *nlist, *nnei, *ncand;
+  int* err;
+};
+void launch_neighbors(const NbrArgs& a, cudaStream_t st);
+void launch_reverse(const int* nlist, int n, int* rev_cnt, int* rev_rows, int* err, cudaStream_t st);
+
+// --- environment matrix and its adjoint, forces, reductions (env.cu)
+struct EnvArgs {
+  const double* coord;
+  const int* atype;
+  const CellGrid* grid;
+  const int* nlist;
+  int n;
+  const float* davg;  // [ntypes][4]
+  const float* dstd;  // [ntypes][4]
+  float rcs, rc;
+  float* R;   // [n*NP][4] normalised environment rows
+  float* rw;  // [n*NP][4] (rhat_x, rhat_y, rhat_z, w)
+  float* rv;  // [n*NP][4] (x, y, z, |r|)
+};
+void launch_env(const EnvArgs& a, cudaStream_t st);
+
+struct EnvBwdArgs {
+  const float* rv;
+  const int* nlist;
+  const int* atype;
+  int n;
+  const float* dstd;
+  float rcs, rc;
+  const float* dR;    // [rows][4]
+  const float* dgeo;  // [rows][4] (d rhat xyz, d w)
+  float* g;           // [rows][4] dE/dr_ij (xyz, 0)
+};
+void launch_env_bwd(const EnvBwdArgs& a, cudaStream_t st);
+
+struct ForceArgs {
+  const float* g;
+  const float* rv;
+  const int* nnei;
+  const int* rev_cnt;
+  const int* rev_rows;
+  const float* e;  // [n] atomic energies
+  int n;
+  double* force;        // [n][3]
+  double* atom_energy;  // [n] or null
+  double* partials;     // [blocks][10] (9 virial + energy)
+  double* energy;       // [1]
+  double* virial;       // [9]
+  int* err;
+};
+void launch_force_virial(const ForceArgs& a, cudaStream_t st);
+
+// --- FP32 SIMT network kernels (simt.cu)
+enum Epi { EPI_BIAS = 0, EPI_TANH = 1, EPI_RES_TANH = 2, EPI_ACCUM = 3, EPI_RES = 4 };
+// C[M][N] (ldc) = epi(A[M][K] (lda) * B[K][N] (ldb) + bias[N]); R is the residual (ldr).
+void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bias, const float* R, int ldr,
+              float* C, int ldc, int M, int N, int K, int epi, cudaStream_t st);
+
+struct EmbedArgs {
+  const float* R;
+  const int* nlist;
+  const int* atype;
+  int n, ntypes, m1;
+  const float* w;   // packed embedding-net weights (W0 b0 W1 b1 W2 b2)
+  const float* Gt;  // [ntypes][ntypes][m1]
+  float* G0;        // [rows][m1]
+  const float* dG0;  // backward only
+  float* dR;         // backward only: dR[:,0] +=
+};
+bool launch_embed_fwd(const EmbedArgs& a, const int* widths, cudaStream_t st);
+bool launch_embed_bwd(const EmbedArgs& a, const int* widths, cudaStream_t st);
+
+void launch_ln_res_fwd(const float* Y, const float* Gin, const int* nlist, const float* gamma, const float* beta,
+                       float eps, float* Gout, float* stats, int rows, int m1, cudaStream_t st);
+void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const int* nlist, const float* gamma,
+                   float* dY, int rows, int m1, cudaStream_t st);
+
+struct AttnArgs {
+  const float* QKV;  // [rows][3A]
+  const float* rw;   // [rows][4]
+  const int* nnei;
+  int n, A;
+  float shift;
+  float* O;          // fwd: [rows][A]
+  const float* dO;   // bwd: [rows][A]
+  float* dQKV;       // bwd: [rows][3A]
+  float* dgeo;       // bwd: [rows][4] +=
+  float* scratch;    // bwd: per resident block 2 * NP * NP floats
+  int scratch_blocks;
+};
+void launch_attn_fwd_f32(const AttnArgs& a, cudaStream_t st);
+void launch_attn_bwd_f32(const AttnArgs& a, cudaStream_t st);
+
+struct DescArgs {
+  const float* R;
+  const float* G;
+  const int* nnei;
+  const int* atype;
+  const float* tebd;  // [ntypes][tebd_dim]
+  int n, m1, axis, tebd_dim, sel, fit_in;
+  float* T;   // [n][4][m1]
+  float* X;   // [n][fit_in]
+  const float* dX;  // bwd
+  float* dG;        // bwd [rows][m1]
+  float* dR;        // bwd [rows][4] (written)
+};
+void launch_desc_fwd(const DescArgs& a, cudaStream_t st);
+void launch_desc_bwd(const DescArgs& a, cudaStream_t st);
+
+void launch_energy_head(const float* H, int n, int width, const float* w_out, float b_out, float out_scale,
+                        const float* ebias, const int* atype, float* e, cudaStream_t st);
+// dZ = dH * (1 - t^2) with t = Hcur - Hprev (Hprev may be null: t = Hcur)
+void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, float* dZ, long long count,
+                     cudaStream_t st);
+void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream_t st);
+
+}  // namespace dpa1

@@ -1,0 +1,112 @@
+// Internal model and workspace layout of the DPA-1 engine, shared by the
+// C ABI (api.cu) and the tensor-core path (tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "dpa1.h"
+
+namespace dpa1 {
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0, cap = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+
+struct AttnLayerW {
+  float *Wqkv, *bqkv, *WqkvT, *Wo, *bo, *WoT, *ln_g, *ln_b;
+};
+
+struct TcWeights {
+  bool ready = false;
+  std::vector<void*> allocations;
+  // per attention layer: BF16 weights in the [out][in] (K-major) layout of the
+  // tcgen05 B operand
+  std::vector<void*> Wqkv_t, Wo_t, WoT_t, WqkvT_t;
+  std::vector<void*> fitW_t, fitWT_t;
+  void* emb_W1_t = nullptr;
+  void* emb_W2_t = nullptr;
+};
+
+struct TcBuffers {
+  void* p[32] = {};
+};
+
+struct Workspace {
+  int cap = 0;  // atoms
+  void* mem = nullptr;
+  size_t bytes = 0;
+  // neighbour search
+  CellGrid* grid;
+  int *cell_of, *cell_count, *cell_start, *cell_cursor, *cell_atoms;
+  int cell_cap, cap_dim;
+  int *nlist, *nnei, *ncand, *rev_cnt, *rev_rows;
+  // environment
+  float *R, *rw, *rv, *dR, *dgeo, *g;
+  // network
+  std::vector<float*> G, QKV, O, Y, stats;
+  float *dG, *dY, *dO, *dQKV;
+  float *T, *X, *dX, *e;
+  std::vector<float*> H;
+  float *dHa, *dHb, *dZ;
+  float* attn_scratch;
+  int attn_scratch_blocks;
+  double* partials;
+  // host-API staging
+  double *coord, *box, *force, *virial, *energy, *atom_energy;
+  int* atype;
+  // tensor-core path buffers
+  TcBuffers tc;
+};
+
+}  // namespace dpa1
+
+struct dp_model {
+  using AttnLayerW = dpa1::AttnLayerW;
+  using Workspace = dpa1::Workspace;
+  using TcWeights = dpa1::TcWeights;
+  int device = 0;
+  int precision = DP_PREC_FP32;
+  int ints[16];
+  double dbls[8];
+  std::vector<std::string> type_map;
+  int nt, td, sel, axis, nattn, A, nfit, m1, fit_in;
+  int emb[3], fit[3];
+  double rcut, rcs, shift, ln_eps, out_scale;
+  float b_out;
+  // device weights
+  float *emb_packed, *Gt, *tebd, *davg, *dstd, *ebias, *w_out;
+  std::vector<AttnLayerW> attn;
+  std::vector<float*> fitW, fitWT, fitb;
+  TcWeights tcw;
+  std::vector<void*> allocations;
+  Workspace ws;
+  int* d_err = nullptr;
+  cudaStream_t stream = nullptr;  // own stream of the host API
+  cudaStream_t last_stream = nullptr;
+  int last_natoms = 0;
+  int* h_ncand_max = nullptr;
+};
+
+
+namespace dpa1 {
+using HostArrays = std::vector<std::pair<std::string, std::vector<double>>>;
+// tensor-core (BF16) path, tc.cu
+int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg);
+void tc_plan_buffers(dp_model* m, Arena& a, int cap);
+void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st);
+void tc_free_weights(dp_model* m);
+}  // namespace dpa1

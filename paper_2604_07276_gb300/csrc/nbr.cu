@@ -1,0 +1,229 @@
+// Stages a1-a2: cell binning and the full neighbour list (Sec. II-C: DP
+// models need full lists; the O(N) cutoff search of Sec. II-A), plus the
+// reverse list used by the deterministic force gather.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dpa1 {
+
+// One thread: validate the box and derive the cell grid.  Cell edges are
+// >= rcut, so every neighbour of an atom lies in the 27 cells around it; an
+// axis with fewer than 3 cells is treated as a single cell (no cell would
+// otherwise be visited twice).
+__global__ void k_cell_setup(const double* __restrict__ box, double rcut, int cap_dim,
+                             CellGrid* __restrict__ cg, int* __restrict__ err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  CellGrid g;
+  g.ok = 1;
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b)
+      if (a != b && box[3 * a + b] != 0.0) g.ok = 0;
+    double L = box[4 * a];
+    g.L[a] = L;
+    if (!(L > 2.0 * rcut) || !isfinite(L)) g.ok = 0;
+    int nc = g.ok ? (int)floor(L / (rcut * (1.0 + 1e-9))) : 1;
+    if (nc < 3) nc = 1;
+    if (nc > cap_dim) nc = cap_dim;
+    g.nc[a] = nc;
+  }
+  g.ncells = g.nc[0] * g.nc[1] * g.nc[2];
+  if (!g.ok) {
+    set_err(err, ERR_BOX);
+    g.nc[0] = g.nc[1] = g.nc[2] = 1;
+    g.ncells = 1;
+    g.L[0] = g.L[1] = g.L[2] = 1.0;
+  }
+  *cg = g;
+}
+
+__device__ __forceinline__ int cell_coord(double x, double L, int nc) {
+  double w = x - L * floor(x / L);
+  int c = (int)(w * (double)nc / L);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void k_cell_count(const double* __restrict__ coord, const int* __restrict__ atype, int n,
+                             int ntypes, const CellGrid* __restrict__ cgp, int* __restrict__ cell_of,
+                             int* __restrict__ cell_count, int* __restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const CellGrid g = *cgp;
+  double x = coord[3 * i], y = coord[3 * i + 1], z = coord[3 * i + 2];
+  int c = 0;
+  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+    set_err(err, ERR_NAN);
+  } else {
+    int cx = cell_coord(x, g.L[0], g.nc[0]);
+    int cy = cell_coord(y, g.L[1], g.nc[1]);
+    int cz = cell_coord(z, g.L[2], g.nc[2]);
+    c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+  }
+  int t = atype[i];
+  if (t < 0 || t >= ntypes) set_err(err, ERR_TYPE);
+  cell_of[i] = c;
+  atomicAdd(&cell_count[c], 1);
+}
+
+// Exclusive scan of the cell counts (one block).
+__global__ void k_cell_scan(const int* __restrict__ cell_count, int* __restrict__ cell_start,
+                            const CellGrid* __restrict__ cgp) {
+  __shared__ int part[1024];
+  __shared__ int carry;
+  const int ncells = cgp->ncells;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ncells; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < ncells ? cell_count[i] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < ncells) cell_start[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cell_start[ncells] = carry;
+}
+
+__global__ void k_cell_fill(const int* __restrict__ cell_of, int n, const int* __restrict__ cell_start,
+                            int* __restrict__ cell_cursor, int* __restrict__ cell_atoms) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = cell_of[i];
+  int pos = cell_start[c] + atomicAdd(&cell_cursor[c], 1);
+  cell_atoms[pos] = i;
+}
+
+__device__ __forceinline__ bool key_gt(double da, int ja, double db, int jb) {
+  return da > db || (da == db && ja > jb);
+}
+
+// One warp per centre atom: gather every candidate j != i with d^2 < rc^2 from
+// the 27 surrounding cells (FP64, bit-reproducible), then bitonic-sort the
+// candidates by (d^2, j) and keep the first sel.
+constexpr int NBR_WARPS = 4;
+__global__ void __launch_bounds__(32 * NBR_WARPS)
+k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict__ cgp,
+            const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+            const int* __restrict__ cell_atoms, double rc2, int sel, int* __restrict__ nlist,
+            int* __restrict__ nnei, int* __restrict__ ncand, int* __restrict__ err) {
+  __shared__ double skey[NBR_WARPS][NBR_CAP];
+  __shared__ int sidx[NBR_WARPS][NBR_CAP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * NBR_WARPS + warp;
+  if (i >= n) return;
+  const CellGrid g = *cgp;
+  double* key = skey[warp];
+  int* idx = sidx[warp];
+  const double xi = coord[3 * i], yi = coord[3 * i + 1], zi = coord[3 * i + 2];
+  const int ci = cell_of[i];
+  const int cx = ci % g.nc[0], cy = (ci / g.nc[0]) % g.nc[1], cz = ci / (g.nc[0] * g.nc[1]);
+  const int ox = g.nc[0] >= 3 ? 1 : 0, oy = g.nc[1] >= 3 ? 1 : 0, oz = g.nc[2] >= 3 ? 1 : 0;
+  int cnt = 0;
+  for (int dz = -oz; dz <= oz; ++dz)
+    for (int dy = -oy; dy <= oy; ++dy)
+      for (int dx = -ox; dx <= ox; ++dx) {
+        int nx = (cx + dx + g.nc[0]) % g.nc[0];
+        int ny = (cy + dy + g.nc[1]) % g.nc[1];
+        int nz = (cz + dz + g.nc[2]) % g.nc[2];
+        int c = (nz * g.nc[1] + ny) * g.nc[0] + nx;
+        int b = cell_start[c], e = cell_start[c + 1];
+        for (int base = b; base < e; base += 32) {
+          int t = base + lane;
+          bool hit = false;
+          double d2 = 0.0;
+          int j = -1;
+          if (t < e) {
+            j = cell_atoms[t];
+            double ddx = mic(__dsub_rn(coord[3 * j], xi), g.L[0]);
+            double ddy = mic(__dsub_rn(coord[3 * j + 1], yi), g.L[1]);
+            double ddz = mic(__dsub_rn(coord[3 * j + 2], zi), g.L[2]);
+            d2 = sqdist(ddx, ddy, ddz);
+            hit = (j != i) && (d2 < rc2);
+          }
+          unsigned bal = __ballot_sync(0xffffffffu, hit);
+          int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+          if (hit && pos < NBR_CAP) {
+            key[pos] = d2;
+            idx[pos] = j;
+          }
+          cnt += __popc(bal);
+        }
+      }
+  if (lane == 0) ncand[i] = cnt;
+  if (cnt > NBR_CAP) {
+    if (lane == 0) set_err(err, ERR_CAPACITY);
+    cnt = NBR_CAP;
+  }
+  int P = 1;
+  while (P < cnt) P <<= 1;
+  for (int t = cnt + lane; t < P; t += 32) {
+    key[t] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    idx[t] = 0x7fffffff;
+  }
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int t = lane; t < P; t += 32) {
+        int o = t ^ jj;
+        if (o > t) {
+          bool asc = (t & k) == 0;
+          double ka = key[t], kb = key[o];
+          int ia = idx[t], ib = idx[o];
+          bool sw = asc ? key_gt(ka, ia, kb, ib) : key_gt(kb, ib, ka, ia);
+          if (sw) {
+            key[t] = kb; key[o] = ka;
+            idx[t] = ib; idx[o] = ia;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  const int keep = cnt < sel ? cnt : sel;
+  for (int s = lane; s < NP; s += 32) nlist[(size_t)i * NP + s] = s < keep ? idx[s] : -1;
+  if (lane == 0) nnei[i] = keep;
+}
+
+// Reverse list: for every kept pair (i, slot) -> j, record row i*NP+slot under j.
+__global__ void k_rev_fill(const int* __restrict__ nlist, int n, int* __restrict__ rev_cnt,
+                           int* __restrict__ rev_rows, int* __restrict__ err) {
+  long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (long long)n * NP) return;
+  int j = nlist[row];
+  if (j < 0) return;
+  int pos = atomicAdd(&rev_cnt[j], 1);
+  if (pos < REV_CAP)
+    rev_rows[(size_t)j * REV_CAP + pos] = (int)row;
+  else
+    set_err(err, ERR_CAPACITY);
+}
+
+void launch_neighbors(const NbrArgs& a, cudaStream_t st) {
+  cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)a.cell_cap, st);
+  cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)a.cell_cap, st);
+  k_cell_setup<<<1, 1, 0, st>>>(a.box, a.rcut, a.cap_dim, a.grid, a.err);
+  if (a.n == 0) return;
+  const int tb = 256;
+  k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of,
+                                                  a.cell_count, a.err);
+  k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid);
+  k_cell_fill<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.cell_of, a.n, a.cell_start, a.cell_cursor, a.cell_atoms);
+  k_neighbors<<<(a.n + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
+      a.coord, a.n, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist,
+      a.nnei, a.ncand, a.err);
+}
+
+void launch_reverse(const int* nlist, int n, int* rev_cnt, int* rev_rows, int* err, cudaStream_t st) {
+  cudaMemsetAsync(rev_cnt, 0, sizeof(int) * (size_t)(n > 0 ? n : 1), st);
+  if (n == 0) return;
+  long long rows = (long long)n * NP;
+  k_rev_fill<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(nlist, n, rev_cnt, rev_rows, err);
+}
+
+}  // namespace dpa1

@@ -1,0 +1,766 @@
+// FP32 SIMT kernels of the network stages a5-a13: embedding net, gated
+// attention (forward and adjoint), LayerNorm, descriptor, fitting helpers
+// and a general FP32 GEMM.  These form the FP32 path and provide the
+// stages the tensor-core path shares with it.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dpa1 {
+
+// ----------------------------------------------------------------- FP32 GEMM
+// 64x64 tile, K step 16, 256 threads, 4x4 outputs per thread.
+template <int EPI>
+__global__ void __launch_bounds__(256)
+k_sgemm(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb, const float* __restrict__ bias,
+        const float* __restrict__ R, int ldr, float* __restrict__ C, int ldc, int M, int N, int K) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long long m0 = (long long)blockIdx.x * 64;
+  const int n0 = blockIdx.y * 64;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  const int ar = threadIdx.x >> 2, ak = (threadIdx.x & 3) * 4;
+  const int bk = threadIdx.x >> 4, bn = (threadIdx.x & 15) * 4;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const long long gm = m0 + ar;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gk = k0 + ak + q;
+      As[ak + q][ar] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gk = k0 + bk, gn = n0 + bn + q;
+      Bs[bk][bn + q] = (gk < K && gn < N) ? B[(long long)gk * ldb + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      float* c = C + m * ldc + n;
+      if (EPI == EPI_BIAS) *c = v + (bias ? bias[n] : 0.f);
+      if (EPI == EPI_TANH) *c = tanhf(v + (bias ? bias[n] : 0.f));
+      if (EPI == EPI_RES_TANH) *c = R[m * ldr + n] + tanhf(v + (bias ? bias[n] : 0.f));
+      if (EPI == EPI_ACCUM) *c = *c + v;
+      if (EPI == EPI_RES) *c = R[m * ldr + n] + v;
+    }
+  }
+}
+
+void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bias, const float* R, int ldr,
+              float* C, int ldc, int M, int N, int K, int epi, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+  switch (epi) {
+    case EPI_BIAS: k_sgemm<EPI_BIAS><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_TANH: k_sgemm<EPI_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_RES_TANH: k_sgemm<EPI_RES_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_ACCUM: k_sgemm<EPI_ACCUM><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    default: k_sgemm<EPI_RES><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+  }
+}
+
+// ------------------------------------------------------------ embedding net
+// G0_ij = net_s(R_ij,0) * (1 + Gt[t_i, t_j]); net_s = 1 -> E0 -> E1 -> E2 with
+// tanh and the residual rule (keep width: x + f; double: [x, x] + f).
+template <int E0, int E1, int E2>
+struct EmbedLayout {
+  static constexpr int W0 = 0, B0 = E0, W1 = 2 * E0, B1 = W1 + E0 * E1, W2 = B1 + E1, B2 = W2 + E1 * E2,
+                       TOTAL = B2 + E2;
+};
+
+template <int E0, int E1, int E2>
+__global__ void __launch_bounds__(128) k_embed_fwd(EmbedArgs a) {
+  using Lw = EmbedLayout<E0, E1, E2>;
+  extern __shared__ float sw[];
+  for (int t = threadIdx.x; t < Lw::TOTAL; t += blockDim.x) sw[t] = a.w[t];
+  __syncthreads();
+  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (long long)a.n * NP) return;
+  float* out = a.G0 + row * a.m1;
+  const int j = a.nlist[row];
+  if (j < 0) {
+    for (int c = 0; c < E2; ++c) out[c] = 0.f;
+    return;
+  }
+  const float x = a.R[row * 4];
+  const int ti = a.atype[row / NP], tj = a.atype[j];
+  float h1[E0], h2[E1];
+#pragma unroll
+  for (int p = 0; p < E0; ++p) h1[p] = tanhf(fmaf(x, sw[Lw::W0 + p], sw[Lw::B0 + p]));
+#pragma unroll
+  for (int b = 0; b < E1; ++b) {
+    float z = sw[Lw::B1 + b];
+#pragma unroll
+    for (int p = 0; p < E0; ++p) z = fmaf(h1[p], sw[Lw::W1 + p * E1 + b], z);
+    h2[b] = ((E1 == E0) ? h1[b % E0] : (E1 == 2 * E0) ? h1[b % E0] : 0.f) + tanhf(z);
+  }
+  const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
+  if (E2 == E1 || E2 == 2 * E1) {
+    // output c = r*E1 + b carries the skip input h2[b]
+#pragma unroll 1
+    for (int r = 0; r < E2 / E1; ++r) {
+#pragma unroll
+      for (int b = 0; b < E1; ++b) {
+        const int c = r * E1 + b;
+        float z = sw[Lw::B2 + c];
+#pragma unroll
+        for (int q = 0; q < E1; ++q) z = fmaf(h2[q], sw[Lw::W2 + q * E2 + c], z);
+        out[c] = (h2[b] + tanhf(z)) * (1.f + gt[c]);
+      }
+    }
+  } else {
+    for (int c = 0; c < E2; ++c) {
+      float z = sw[Lw::B2 + c];
+#pragma unroll
+      for (int q = 0; q < E1; ++q) z = fmaf(h2[q], sw[Lw::W2 + q * E2 + c], z);
+      out[c] = tanhf(z) * (1.f + gt[c]);
+    }
+  }
+}
+
+// Adjoint of the embedding net: dR[:,0] += d(net_s)/dx . (dG0 * (1 + Gt)).
+// dz of the last layer is kept in thread-private shared memory columns.
+template <int E0, int E1, int E2>
+__global__ void __launch_bounds__(128) k_embed_bwd(EmbedArgs a) {
+  using Lw = EmbedLayout<E0, E1, E2>;
+  extern __shared__ float sm[];
+  float* sw = sm;
+  float* dzs = sm + Lw::TOTAL;  // [E2][blockDim]
+  for (int t = threadIdx.x; t < Lw::TOTAL; t += blockDim.x) sw[t] = a.w[t];
+  __syncthreads();
+  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (long long)a.n * NP) return;
+  const int j = a.nlist[row];
+  if (j < 0) return;
+  const float x = a.R[row * 4];
+  const int ti = a.atype[row / NP], tj = a.atype[j];
+  float h1[E0], h2[E1], dh2[E1];
+#pragma unroll
+  for (int p = 0; p < E0; ++p) h1[p] = tanhf(fmaf(x, sw[Lw::W0 + p], sw[Lw::B0 + p]));
+#pragma unroll
+  for (int b = 0; b < E1; ++b) {
+    float z = sw[Lw::B1 + b];
+#pragma unroll
+    for (int p = 0; p < E0; ++p) z = fmaf(h1[p], sw[Lw::W1 + p * E1 + b], z);
+    h2[b] = ((E1 == E0 || E1 == 2 * E0) ? h1[b % E0] : 0.f) + tanhf(z);
+  }
+  const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
+  const float* dG = a.dG0 + row * a.m1;
+  for (int c = 0; c < E2; ++c) {
+    float z = sw[Lw::B2 + c];
+#pragma unroll
+    for (int b = 0; b < E1; ++b) z = fmaf(h2[b], sw[Lw::W2 + b * E2 + c], z);
+    const float t = tanhf(z);
+    const float g = dG[c] * (1.f + gt[c]);
+    dzs[c * blockDim.x + threadIdx.x] = g * (1.f - t * t);
+  }
+#pragma unroll
+  for (int b = 0; b < E1; ++b) {
+    float s = 0.f;
+    if (E2 == E1 || E2 == 2 * E1) {
+      for (int c = b; c < E2; c += E1) s += dG[c] * (1.f + gt[c]);
+    }
+    dh2[b] = s;
+  }
+  for (int c = 0; c < E2; ++c) {
+    const float dz = dzs[c * blockDim.x + threadIdx.x];
+#pragma unroll
+    for (int b = 0; b < E1; ++b) dh2[b] = fmaf(sw[Lw::W2 + b * E2 + c], dz, dh2[b]);
+  }
+  // layer 2 (E0 -> E1): h2 = skip + tanh(z2), so tanh(z2) = h2 - skip
+  float dh1[E0];
+#pragma unroll
+  for (int p = 0; p < E0; ++p) dh1[p] = 0.f;
+#pragma unroll
+  for (int b = 0; b < E1; ++b) {
+    if (E1 == E0 || E1 == 2 * E0) dh1[b % E0] += dh2[b];
+    const float t = h2[b] - ((E1 == E0 || E1 == 2 * E0) ? h1[b % E0] : 0.f);
+    const float dz = dh2[b] * (1.f - t * t);
+#pragma unroll
+    for (int p = 0; p < E0; ++p) dh1[p] = fmaf(sw[Lw::W1 + p * E1 + b], dz, dh1[p]);
+  }
+  float dx = 0.f;
+#pragma unroll
+  for (int p = 0; p < E0; ++p) dx = fmaf(sw[Lw::W0 + p], dh1[p] * (1.f - h1[p] * h1[p]), dx);
+  a.dR[row * 4] += dx;
+}
+
+template <int E0, int E1, int E2>
+static void embed_launch(const EmbedArgs& a, bool bwd, cudaStream_t st) {
+  using Lw = EmbedLayout<E0, E1, E2>;
+  const long long rows = (long long)a.n * NP;
+  if (rows == 0) return;
+  const unsigned grid = (unsigned)((rows + 127) / 128);
+  if (!bwd) {
+    size_t sm = sizeof(float) * Lw::TOTAL;
+    cudaFuncSetAttribute(k_embed_fwd<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_embed_fwd<E0, E1, E2><<<grid, 128, sm, st>>>(a);
+  } else {
+    size_t sm = sizeof(float) * (Lw::TOTAL + E2 * 128);
+    cudaFuncSetAttribute(k_embed_bwd<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_embed_bwd<E0, E1, E2><<<grid, 128, sm, st>>>(a);
+  }
+}
+
+static bool embed_dispatch(const EmbedArgs& a, const int* w, bool bwd, cudaStream_t st) {
+  if (w[0] == 25 && w[1] == 50 && w[2] == 100) { embed_launch<25, 50, 100>(a, bwd, st); return true; }
+  if (w[0] == 16 && w[1] == 32 && w[2] == 64) { embed_launch<16, 32, 64>(a, bwd, st); return true; }
+  if (w[0] == 32 && w[1] == 64 && w[2] == 128) { embed_launch<32, 64, 128>(a, bwd, st); return true; }
+  return false;
+}
+bool launch_embed_fwd(const EmbedArgs& a, const int* widths, cudaStream_t st) { return embed_dispatch(a, widths, false, st); }
+bool launch_embed_bwd(const EmbedArgs& a, const int* widths, cudaStream_t st) { return embed_dispatch(a, widths, true, st); }
+
+// ---------------------------------------------------------------- LayerNorm
+// G_out = G_in + LN(Y) on rows with a neighbour, G_out = G_in elsewhere.
+__global__ void k_ln_res_fwd(const float* __restrict__ Y, const float* __restrict__ Gin, const int* __restrict__ nlist,
+                             const float* __restrict__ gamma, const float* __restrict__ beta, float eps,
+                             float* __restrict__ Gout, float* __restrict__ stats, long long rows, int m1) {
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const float* y = Y + row * m1;
+  float v[4];
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    v[q] = c < m1 ? y[c] : 0.f;
+    s += v[q];
+  }
+  const float mean = warp_sum(s) / (float)m1;
+  float s2 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    const float d = c < m1 ? v[q] - mean : 0.f;
+    s2 += d * d;
+  }
+  const float var = warp_sum(s2) / (float)m1;
+  const float rstd = 1.0f / sqrtf(var + eps);
+  const bool valid = nlist[row] >= 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    if (c < m1) {
+      const float gin = Gin[row * m1 + c];
+      Gout[row * m1 + c] = valid ? gin + (v[q] - mean) * rstd * gamma[c] + beta[c] : gin;
+    }
+  }
+  if (lane == 0) {
+    stats[2 * row] = mean;
+    stats[2 * row + 1] = rstd;
+  }
+}
+
+__global__ void k_ln_bwd(const float* __restrict__ dZ, const float* __restrict__ Y, const float* __restrict__ stats,
+                         const int* __restrict__ nlist, const float* __restrict__ gamma, float* __restrict__ dY,
+                         long long rows, int m1) {
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const bool valid = nlist[row] >= 0;
+  const float mean = stats[2 * row], rstd = stats[2 * row + 1];
+  float gz[4], yh[4];
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    if (c < m1 && valid) {
+      gz[q] = gamma[c] * dZ[row * m1 + c];
+      yh[q] = (Y[row * m1 + c] - mean) * rstd;
+    } else {
+      gz[q] = 0.f; yh[q] = 0.f;
+    }
+    s1 += gz[q];
+    s2 += gz[q] * yh[q];
+  }
+  s1 = warp_sum(s1) / (float)m1;
+  s2 = warp_sum(s2) / (float)m1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lane + 32 * q;
+    if (c < m1) dY[row * m1 + c] = valid ? rstd * (gz[q] - s1 - yh[q] * s2) : 0.f;
+  }
+}
+
+void launch_ln_res_fwd(const float* Y, const float* Gin, const int* nlist, const float* gamma, const float* beta,
+                       float eps, float* Gout, float* stats, int rows_i, int m1, cudaStream_t st) {
+  long long rows = rows_i;
+  if (rows == 0) return;
+  k_ln_res_fwd<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(Y, Gin, nlist, gamma, beta, eps, Gout, stats,
+                                                                      rows, m1);
+}
+void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const int* nlist, const float* gamma,
+                   float* dY, int rows_i, int m1, cudaStream_t st) {
+  long long rows = rows_i;
+  if (rows == 0) return;
+  k_ln_bwd<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(dZ, Y, stats, nlist, gamma, dY, rows, m1);
+}
+
+// ------------------------------------------------- gated attention (FP32)
+// Per centre atom, over its valid neighbour slots j, k < n_i:
+//   l_jk = Q_j.K_k / sqrt(A);  l'_jk = (l_jk + S) w_j w_k - S
+//   A_jk = softmax_k(l'_jk);   P_jk = A_jk w_j w_k (rhat_j . rhat_k);  O = P V
+constexpr int AW = 8;  // warps per block
+
+template <int A>
+__global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
+  extern __shared__ float sm[];
+  float* Ks = sm;                                   // [NP][A+1]
+  float* Vs = Ks + NP * (A + 1);                    // [NP][A]
+  float4* rws = reinterpret_cast<float4*>(Vs + NP * A);  // [NP]
+  float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][A]
+  float* prow = qrow + AW * A;                      // [AW][NP]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int FQ = A / 32;
+  const int ld = 3 * A;
+  for (int atom = blockIdx.x; atom < a.n; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const size_t base = (size_t)atom * NP;
+    for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
+      const int r = idx / A, f = idx % A;
+      Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
+      Vs[r * A + f] = a.QKV[(base + r) * ld + 2 * A + f];
+    }
+    for (int r = threadIdx.x; r < NP; r += blockDim.x)
+      rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int j = warp; j < NP; j += AW) {
+      float* o = a.O + (base + j) * A;
+      if (j >= nn) {
+        for (int f = lane; f < A; f += 32) o[f] = 0.f;
+        continue;
+      }
+      float* q = qrow + warp * A;
+      for (int f = lane; f < A; f += 32) q[f] = a.QKV[(base + j) * ld + f];
+      __syncwarp();
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int f = 0; f < A; ++f) {
+        const float qf = q[f];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) s[m] = fmaf(qf, Ks[(lane + 32 * m) * (A + 1) + f], s[m]);
+      }
+      const float4 rj = rws[j];
+      float lp[4], mx = -INFINITY;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int k = lane + 32 * m;
+        if (k < nn) {
+          const float ww = rj.w * rws[k].w;
+          lp[m] = (s[m] * scale + a.shift) * ww - a.shift;
+          mx = fmaxf(mx, lp[m]);
+        }
+      }
+      mx = warp_max(mx);
+      float e[4], sum = 0.f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int k = lane + 32 * m;
+        e[m] = k < nn ? expf(lp[m] - mx) : 0.f;
+        sum += e[m];
+      }
+      sum = warp_sum(sum);
+      const float inv = 1.0f / sum;
+      float* p = prow + warp * NP;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int k = lane + 32 * m;
+        float pv = 0.f;
+        if (k < nn) {
+          const float4 rk = rws[k];
+          pv = e[m] * inv * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z);
+        }
+        p[k] = pv;
+      }
+      __syncwarp();
+      float acc[FQ];
+#pragma unroll
+      for (int m = 0; m < FQ; ++m) acc[m] = 0.f;
+      for (int k = 0; k < nn; ++k) {
+        const float pk = p[k];
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) acc[m] = fmaf(pk, Vs[k * A + lane + 32 * m], acc[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < FQ; ++m) o[lane + 32 * m] = acc[m];
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// Adjoint of one attention layer for one centre.  Pass 1 (a warp per row j)
+// recomputes l, A and P, forms dP = dO_j . V_k, the softmax adjoint and dQ_j,
+// and the row / column parts of dE/dw and dE/drhat.  Pass 2 (a warp per key k)
+// forms dK_k = sum_j dS_jk Q_j and dV_k = sum_j P_jk dO_j from dS and P that
+// pass 1 left (transposed) in this block's global scratch slot.
+template <int A>
+__global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
+  extern __shared__ float sm[];
+  float* Ks = sm;                                   // [NP][A+1]   pass 2: Q
+  float* Vs = Ks + NP * (A + 1);                    // [NP][A+1]   pass 2: dO
+  float4* rws = reinterpret_cast<float4*>(Vs + NP * (A + 1));  // [NP]
+  float4* rowg = rws + NP;                          // [NP] (d rhat_j, d w_j) row parts
+  float* qrow = reinterpret_cast<float*>(rowg + NP);  // [AW][A]
+  float* dorow = qrow + AW * A;                     // [AW][A]
+  float* prow = dorow + AW * A;                     // [AW][NP]
+  float* colw = prow + AW * NP;                     // [AW][NP]
+  float* colr = colw + AW * NP;                     // [AW][NP][3]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int FQ = A / 32;
+  const int ld = 3 * A;
+  float* dST = a.scratch + (size_t)blockIdx.x * 2 * NP * NP;  // [NP k][NP j]
+  float* PT = dST + NP * NP;
+  for (int atom = blockIdx.x; atom < a.n; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const size_t base = (size_t)atom * NP;
+    for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
+      const int r = idx / A, f = idx % A;
+      Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
+      Vs[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
+    }
+    for (int r = threadIdx.x; r < NP; r += blockDim.x)
+      rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = threadIdx.x; t < AW * NP; t += blockDim.x) {
+      colw[t] = 0.f;
+      colr[3 * t] = 0.f; colr[3 * t + 1] = 0.f; colr[3 * t + 2] = 0.f;
+    }
+    __syncthreads();
+    for (int j = warp; j < nn; j += AW) {
+      float* q = qrow + warp * A;
+      float* dq = dorow + warp * A;
+      for (int f = lane; f < A; f += 32) {
+        q[f] = a.QKV[(base + j) * ld + f];
+        dq[f] = a.dO[(base + j) * A + f];
+      }
+      __syncwarp();
+      float s[4] = {0.f, 0.f, 0.f, 0.f}, dp[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int f = 0; f < A; ++f) {
+        const float qf = q[f], gf = dq[f];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int k = lane + 32 * m;
+          s[m] = fmaf(qf, Ks[k * (A + 1) + f], s[m]);
+          dp[m] = fmaf(gf, Vs[k * (A + 1) + f], dp[m]);
+        }
+      }
+      const float4 rj = rws[j];
+      float l[4], lp[4], ww[4], c[4], mx = -INFINITY;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int k = lane + 32 * m;
+        const float4 rk = rws[k];
+        ww[m] = rj.w * rk.w;
+        c[m] = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
+        l[m] = s[m] * scale;
+        lp[m] = (l[m] + a.shift) * ww[m] - a.shift;
+        if (k < nn) mx = fmaxf(mx, lp[m]);
+      }
+      mx = warp_max(mx);
+      float e[4], sum = 0.f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        e[m] = (lane + 32 * m) < nn ? expf(lp[m] - mx) : 0.f;
+        sum += e[m];
+      }
+      sum = warp_sum(sum);
+      const float inv = 1.0f / sum;
+      float At[4], dA[4], tsum = 0.f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        At[m] = e[m] * inv;
+        dA[m] = (lane + 32 * m) < nn ? dp[m] * ww[m] * c[m] : 0.f;
+        tsum += At[m] * dA[m];
+      }
+      tsum = warp_sum(tsum);
+      float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+      float* pr = prow + warp * NP;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int k = lane + 32 * m;
+        float dS = 0.f;
+        if (k < nn) {
+          const float dLp = At[m] * (dA[m] - tsum);
+          dS = dLp * ww[m] * scale;
+          const float H = dp[m] * At[m] * c[m] + dLp * (l[m] + a.shift);
+          const float dc = dp[m] * At[m] * ww[m];
+          const float4 rk = rws[k];
+          rw_ += H * rk.w;
+          rx += dc * rk.x; ry += dc * rk.y; rz += dc * rk.z;
+          colw[warp * NP + k] += H * rj.w;
+          colr[(warp * NP + k) * 3 + 0] += dc * rj.x;
+          colr[(warp * NP + k) * 3 + 1] += dc * rj.y;
+          colr[(warp * NP + k) * 3 + 2] += dc * rj.z;
+          dST[(size_t)k * NP + j] = dS;
+          PT[(size_t)k * NP + j] = At[m] * ww[m] * c[m];
+        }
+        pr[k] = dS;
+      }
+      rw_ = warp_sum(rw_); rx = warp_sum(rx); ry = warp_sum(ry); rz = warp_sum(rz);
+      if (lane == 0) rowg[j] = make_float4(rx, ry, rz, rw_);
+      __syncwarp();
+      float acc[FQ];
+#pragma unroll
+      for (int m = 0; m < FQ; ++m) acc[m] = 0.f;
+      for (int k = 0; k < nn; ++k) {
+        const float d = pr[k];
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) acc[m] = fmaf(d, Ks[k * (A + 1) + lane + 32 * m], acc[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < FQ; ++m) a.dQKV[(base + j) * ld + lane + 32 * m] = acc[m];
+      __syncwarp();
+    }
+    __syncthreads();
+    // pass 2: Q into Ks, dO into Vs
+    for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
+      const int r = idx / A, f = idx % A;
+      Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + f];
+      Vs[r * (A + 1) + f] = a.dO[(base + r) * A + f];
+    }
+    __syncthreads();
+    for (int k = warp; k < NP; k += AW) {
+      float* dq = a.dQKV + (base + k) * ld;
+      if (k >= nn) {
+        for (int f = lane; f < ld; f += 32) dq[f] = 0.f;
+        continue;
+      }
+      float dK[FQ], dV[FQ];
+#pragma unroll
+      for (int m = 0; m < FQ; ++m) { dK[m] = 0.f; dV[m] = 0.f; }
+      for (int jb = 0; jb < nn; jb += 32) {
+        const int jj = jb + lane;
+        const float dsv = jj < nn ? dST[(size_t)k * NP + jj] : 0.f;
+        const float pv = jj < nn ? PT[(size_t)k * NP + jj] : 0.f;
+        const int cnt = (nn - jb) < 32 ? (nn - jb) : 32;
+        for (int t = 0; t < cnt; ++t) {
+          const float d = __shfl_sync(0xffffffffu, dsv, t);
+          const float p = __shfl_sync(0xffffffffu, pv, t);
+          const int j = jb + t;
+#pragma unroll
+          for (int m = 0; m < FQ; ++m) {
+            dK[m] = fmaf(d, Ks[j * (A + 1) + lane + 32 * m], dK[m]);
+            dV[m] = fmaf(p, Vs[j * (A + 1) + lane + 32 * m], dV[m]);
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < FQ; ++m) {
+        dq[A + lane + 32 * m] = dK[m];
+        dq[2 * A + lane + 32 * m] = dV[m];
+      }
+      if (lane == 0) {
+        float cw = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+        for (int w = 0; w < AW; ++w) {
+          cw += colw[w * NP + k];
+          cx += colr[(w * NP + k) * 3 + 0];
+          cy += colr[(w * NP + k) * 3 + 1];
+          cz += colr[(w * NP + k) * 3 + 2];
+        }
+        const float4 rg = rowg[k];
+        float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + k;
+        float4 cur = *dg;
+        cur.x += rg.x + cx; cur.y += rg.y + cy; cur.z += rg.z + cz; cur.w += rg.w + cw;
+        *dg = cur;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static int sm_count() {
+  static int count = 0;
+  if (count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    if (count <= 0) count = 1;
+  }
+  return count;
+}
+
+void launch_attn_fwd_f32(const AttnArgs& a, cudaStream_t st) {
+  if (a.n == 0) return;
+  const float scale = (float)(1.0 / sqrt((double)a.A));
+  const int A = 128;
+  size_t smem = sizeof(float) * (NP * (A + 1) + NP * A + 4 * NP + AW * A + AW * NP);
+  cudaFuncSetAttribute(k_attn_fwd_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = a.n < sm_count() ? a.n : sm_count();
+  k_attn_fwd_f32<128><<<grid, 32 * AW, smem, st>>>(a, scale);
+}
+
+void launch_attn_bwd_f32(const AttnArgs& a, cudaStream_t st) {
+  if (a.n == 0) return;
+  const float scale = (float)(1.0 / sqrt((double)a.A));
+  const int A = 128;
+  size_t smem = sizeof(float) * (2 * NP * (A + 1) + 8 * NP + 2 * AW * A + 2 * AW * NP + 3 * AW * NP);
+  cudaFuncSetAttribute(k_attn_bwd_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = a.n < a.scratch_blocks ? a.n : a.scratch_blocks;
+  k_attn_bwd_f32<128><<<grid, 32 * AW, smem, st>>>(a, scale);
+}
+
+// ------------------------------------------------------------- descriptor
+// T = R^T G / sel (4 x m1); D = T^T T[:, :axis]; X = [D (row-major), Z[t_i]].
+__global__ void k_desc_fwd(DescArgs a) {
+  extern __shared__ float sm[];
+  float* Ts = sm;  // [4][m1]
+  const int atom = blockIdx.x;
+  const int nn = a.nnei[atom];
+  const size_t base = (size_t)atom * NP;
+  const float inv_sel = 1.0f / (float)a.sel;
+  for (int c = threadIdx.x; c < a.m1; c += blockDim.x) {
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    for (int s = 0; s < nn; ++s) {
+      const float4 r = reinterpret_cast<const float4*>(a.R)[base + s];
+      const float gv = a.G[(base + s) * a.m1 + c];
+      t0 = fmaf(r.x, gv, t0); t1 = fmaf(r.y, gv, t1); t2 = fmaf(r.z, gv, t2); t3 = fmaf(r.w, gv, t3);
+    }
+    Ts[c] = t0 * inv_sel; Ts[a.m1 + c] = t1 * inv_sel; Ts[2 * a.m1 + c] = t2 * inv_sel; Ts[3 * a.m1 + c] = t3 * inv_sel;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 4 * a.m1; t += blockDim.x) a.T[(size_t)atom * 4 * a.m1 + t] = Ts[t];
+  float* x = a.X + (size_t)atom * a.fit_in;
+  for (int idx = threadIdx.x; idx < a.m1 * a.axis; idx += blockDim.x) {
+    const int p = idx / a.axis, b = idx % a.axis;
+    float d = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d = fmaf(Ts[c * a.m1 + p], Ts[c * a.m1 + b], d);
+    x[idx] = d;
+  }
+  const int ti = a.atype[atom];
+  for (int t = threadIdx.x; t < a.tebd_dim; t += blockDim.x) x[a.m1 * a.axis + t] = a.tebd[ti * a.tebd_dim + t];
+}
+
+// dT[c][p] = sum_b<axis dD[p][b] T[c][b] + (p < axis) sum_q dD[q][p] T[c][q];
+// dG_s = R_s dT / sel; dR_s = G_s dT^T / sel.
+__global__ void k_desc_bwd(DescArgs a) {
+  extern __shared__ float sm[];
+  const int m1 = a.m1, ax = a.axis;
+  float* Ts = sm;              // [4][m1]
+  float* dTs = Ts + 4 * m1;    // [4][m1]
+  float* dD = dTs + 4 * m1;    // [m1][axis]
+  const int atom = blockIdx.x;
+  const int nn = a.nnei[atom];
+  const size_t base = (size_t)atom * NP;
+  const float inv_sel = 1.0f / (float)a.sel;
+  for (int t = threadIdx.x; t < 4 * m1; t += blockDim.x) Ts[t] = a.T[(size_t)atom * 4 * m1 + t];
+  for (int t = threadIdx.x; t < m1 * ax; t += blockDim.x) dD[t] = a.dX[(size_t)atom * a.fit_in + t];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 4 * m1; t += blockDim.x) {
+    const int c = t / m1, p = t % m1;
+    float v = 0.f;
+    for (int b = 0; b < ax; ++b) v = fmaf(dD[p * ax + b], Ts[c * m1 + b], v);
+    if (p < ax)
+      for (int q = 0; q < m1; ++q) v = fmaf(dD[q * ax + p], Ts[c * m1 + q], v);
+    dTs[t] = v * inv_sel;
+  }
+  __syncthreads();
+  // dG rows (all NP rows; zero on padding)
+  for (long long idx = threadIdx.x; idx < (long long)NP * m1; idx += blockDim.x) {
+    const int s = (int)(idx / m1), p = (int)(idx % m1);
+    float v = 0.f;
+    if (s < nn) {
+      const float4 r = reinterpret_cast<const float4*>(a.R)[base + s];
+      v = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
+    }
+    a.dG[(base + s) * m1 + p] = v;
+  }
+  // dR rows: a warp per row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int s = warp; s < NP; s += nw) {
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    if (s < nn) {
+      for (int p = lane; p < m1; p += 32) {
+        const float gv = a.G[(base + s) * m1 + p];
+        d0 = fmaf(gv, dTs[p], d0); d1 = fmaf(gv, dTs[m1 + p], d1);
+        d2 = fmaf(gv, dTs[2 * m1 + p], d2); d3 = fmaf(gv, dTs[3 * m1 + p], d3);
+      }
+    }
+    d0 = warp_sum(d0); d1 = warp_sum(d1); d2 = warp_sum(d2); d3 = warp_sum(d3);
+    if (lane == 0) reinterpret_cast<float4*>(a.dR)[base + s] = make_float4(d0, d1, d2, d3);
+  }
+}
+
+void launch_desc_fwd(const DescArgs& a, cudaStream_t st) {
+  if (a.n == 0) return;
+  k_desc_fwd<<<a.n, 128, sizeof(float) * 4 * a.m1, st>>>(a);
+}
+void launch_desc_bwd(const DescArgs& a, cudaStream_t st) {
+  if (a.n == 0) return;
+  size_t sm = sizeof(float) * (8 * a.m1 + a.m1 * a.axis);
+  k_desc_bwd<<<a.n, 128, sm, st>>>(a);
+}
+
+// ------------------------------------------------------------ fitting head
+__global__ void k_energy_head(const float* __restrict__ H, int n, int width, const float* __restrict__ w,
+                              float b, float out_scale, const float* __restrict__ ebias,
+                              const int* __restrict__ atype, float* __restrict__ e) {
+  const int atom = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (atom >= n) return;
+  float s = 0.f;
+  for (int c = lane; c < width; c += 32) s = fmaf(H[(size_t)atom * width + c], w[c], s);
+  s = warp_sum(s);
+  if (lane == 0) e[atom] = out_scale * (s + b) + ebias[atype[atom]];
+}
+
+void launch_energy_head(const float* H, int n, int width, const float* w_out, float b_out, float out_scale,
+                        const float* ebias, const int* atype, float* e, cudaStream_t st) {
+  if (n == 0) return;
+  k_energy_head<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(H, n, width, w_out, b_out, out_scale,
+                                                                          ebias, atype, e);
+}
+
+__global__ void k_tanh_bwd(const float* __restrict__ dH, const float* __restrict__ Hc, const float* __restrict__ Hp,
+                           float* __restrict__ dZ, long long count) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float t = Hp ? Hc[i] - Hp[i] : Hc[i];
+  dZ[i] = dH[i] * (1.f - t * t);
+}
+
+void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, float* dZ, long long count,
+                     cudaStream_t st) {
+  if (count == 0) return;
+  k_tanh_bwd<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dH, Hcur, Hprev, dZ, count);
+}
+
+__global__ void k_fill_rows(float* __restrict__ dst, const float* __restrict__ row, long long count, int width) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  dst[i] = row[i % width];
+}
+
+void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream_t st) {
+  long long count = (long long)n * width;
+  if (count == 0) return;
+  k_fill_rows<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dst, row, count, width);
+}
+
+}  // namespace dpa1

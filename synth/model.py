@@ -133,7 +133,7 @@ def make_weights(
         elif name in ("dstd",):
             w[name] = rng.uniform(0.7, 1.3, size=shape) if stats else np.ones(shape)
         elif name.endswith("ln_g"):
-            w[name] = 1.0 + (rng.normal(0.0, ln_scale, size=shape) if ln_scale > 0 else 0.0)
+            w[name] = np.ones(shape) + (rng.normal(0.0, ln_scale, size=shape) if ln_scale > 0 else 0.0)
         elif name.endswith("ln_b"):
             w[name] = rng.normal(0.0, ln_scale, size=shape) if ln_scale > 0 else np.zeros(shape)
         elif name == "ebias":
