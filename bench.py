@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""DPA-1 E+F(+virial) throughput on one GB300 per rank.
+
+Workload: the 15,668-atom solvated-protein-like periodic box (jittered
+lattice at 0.1 atoms/A^3, elemental fractions H .63 C .12 N .03 O .21
+S .01, seed 1) with the default DPA-1 model (5 types, type embedding 8,
+rcut 6 A, sel 120, embedding [25,50,100], axis 16, 2 gated attention
+layers of width 128, fitting [240,240,240], seed-0 Xavier weights).
+
+A step is one evaluation of the whole path: cell list and neighbour list,
+environment matrix, embedding, attention, descriptor, fitting, FP64 energy
+sum, the hand-written adjoint and the force / virial reduction.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank evaluates its own replica of the box (weak
+scaling, no collective on the data path); the timing is the maximum over
+ranks.  ``--impl reference`` times the FP64 CPU oracle on bounded samples
+of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DPA-1 E+F atom-steps/s at 15,668 atoms, BF16 vs FP32, force RMSE vs FP64"
+NATOMS = 15668
+WORKLOAD = "solvated-protein-like periodic box, 15,668 atoms, jittered lattice at 0.1/A^3, seed 1"
+MODEL = ("DPA-1 se_atten: 5 types, tebd 8, rcut 6.0/0.5 A, sel 120, embed [25,50,100], axis 16, "
+         "2 gated attention layers x 128, fitting [240,240,240]")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32"])
+    ap.add_argument("--natoms", type=int, default=NATOMS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=3072, help="oracle centres timed for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _system(natoms):
+    import synth
+
+    coord, atype, box = synth.lattice_system(natoms, seed=1)
+    return coord, atype, box
+
+
+# ----------------------------------------------------------------- oracle arm
+
+def _oracle_sample_rate(coord, atype, box, sample, seed=0):
+    """Atom-steps/s of the FP64 oracle: energy and forces of ``sample``
+    centres (their atomic energies and the gradient they contribute)."""
+    import torch
+
+    import synth
+    from oracle import OracleModel, energy_force_virial
+
+    cfg = synth.DEFAULT_CONFIG
+    om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=0))
+    rng = np.random.default_rng(seed)
+    centres = np.sort(rng.choice(len(coord), size=min(sample, len(coord)), replace=False))
+    t0 = time.perf_counter()
+    energy_force_virial(om, coord, box, atype, centres=centres)
+    dt = time.perf_counter() - t0
+    return len(centres) / dt, dt, torch.get_num_threads()
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    coord, atype, box = _system(a.natoms)
+    vals = []
+    for s in range(a.warmup + a.steps):
+        v, dt, cores = _oracle_sample_rate(coord, atype, box, a.ref_sample, seed=s)
+        if s >= a.warmup:
+            vals.append((v, dt))
+    rate = len(vals) * a.ref_sample / sum(dt for _, dt in vals)
+    sample = f"{a.ref_sample} random centres of the {a.natoms}-atom box per step (E, e_i and their force terms)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "atom-steps/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(dt for _, dt in vals) / len(vals),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "model": MODEL, "natoms": a.natoms},
+        "cpu_baseline": {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- our arm
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _flops_per_launch(stage, nn, cfg):
+    """Algorithmic FLOPs of one launch of ``stage`` over the whole box
+    (per attention layer for per-layer stages), from the real neighbour
+    counts n_i: attention core forward 2 n^2 A MAC, backward 4 n^2 A MAC,
+    projections per neighbour row 3 A M1 (QKV) and A M1 (output)."""
+    A, m1 = cfg.attn_dim, cfg.m1
+    n2 = float(np.sum(nn.astype(np.float64) ** 2))
+    n1 = float(np.sum(nn))
+    table = {
+        "attn_fwd": 2 * n2 * A,
+        "attn_bwd": 4 * n2 * A,
+        "attn_fwd_tc": 2 * n2 * A,
+        "attn_bwd_tc": 4 * n2 * A,
+        "qkv_gemm": n1 * 3 * A * m1,
+        "qkv_bwd_gemm": n1 * 3 * A * m1,
+    }
+    mac = table.get(stage)
+    return None if mac is None else 2.0 * mac
+
+
+def run_ours(a):
+    import torch
+
+    import synth
+    import paper_2604_07276_gb300 as dp
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.DEFAULT_CONFIG
+    wpath = os.path.join(tempfile.mkdtemp(prefix=f"dpa1b{rank}_"), "w.bin")
+    synth.write_weights(wpath, cfg, synth.make_weights(cfg, seed=0))
+    coord, atype, box = _system(a.natoms)
+    n = len(coord)
+
+    precisions = ["bf16", "fp32"] if a.precision == "auto" else [a.precision]
+    models = {}
+    for p in precisions:
+        try:
+            models[p] = dp.DPA1(wpath, precision=p, device=local)
+            models[p].reserve(n)
+        except dp.DPError as e:
+            if e.code != -8 or a.precision != "auto":
+                raise
+    head = "bf16" if "bf16" in models else "fp32"
+
+    c = torch.tensor(coord, dtype=torch.float64, device=dev)
+    t = torch.tensor(atype, dtype=torch.int32, device=dev)
+    b = torch.tensor(dp.box9(box), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    W = torch.zeros(9, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    results = {}
+    for p, m in models.items():
+        for _ in range(a.warmup):
+            m.compute_device(c, b, t, E, F, W, stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        m.status()
+        clk = Clocks(local) if p == head else None
+        barrier()
+        torch.cuda.synchronize(dev)
+        m.set_profiling(True)
+        l0 = dp.kernel_launches()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(a.steps):
+            m.compute_device(c, b, t, E, F, W, stream=stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        launches = dp.kernel_launches() - l0
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        clocks = clk.stop() if clk else None
+        stages = m.stage_times()
+        m.set_profiling(False)
+        m.status()
+        if ws > 1:
+            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        per_stage = {}
+        for name, v in stages:
+            s = per_stage.setdefault(name, [0.0, 0])
+            s[0] += v
+            s[1] += 1
+        results[p] = {"ms": ms, "launches": launches, "clocks": clocks, "stages": per_stage}
+
+    # e2e through the host-buffer entry point (pinned host memory)
+    m = models[head]
+    hc = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    hc[:] = coord
+    ht = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
+    ht[:] = atype
+    for _ in range(max(1, a.warmup // 2)):
+        m.compute(hc, box, ht)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, a.steps // 2)
+    for _ in range(e2e_steps):
+        m.compute(hc, box, ht)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    # parity of this run's forces against the FP64 oracle on sampled atoms
+    parity = {}
+    nl, nn = m.nlist_device(c, b)
+    nn = nn.cpu().numpy()
+    if rank == 0 and not a.no_parity:
+        from oracle import OracleModel, forces_on
+
+        om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=0))
+        rng = np.random.default_rng(7)
+        atoms = rng.choice(n, size=12, replace=False)
+        ref = forces_on(om, coord, box, atype, atoms)
+        for p, mm in models.items():
+            _, Fp, _, _ = mm.compute(coord, box, atype)
+            parity[p] = {"force_rmse_ev_per_A": float(np.sqrt(np.mean((Fp[atoms] - ref) ** 2))),
+                         "sampled_atoms": len(atoms)}
+
+    if rank != 0:
+        return 0
+    r = results[head]
+    ms_step = r["ms"] / a.steps
+    value = ws * n * a.steps / (r["ms"] / 1e3)
+    # dominant kernel stage and its roofline
+    peaks = _peaks()
+    st = r["stages"]
+    dom = max(st.items(), key=lambda kv: kv[1][0])[0]
+    dom_avg_ms = st[dom][0] / st[dom][1]
+    flops = _flops_per_launch(dom, nn, cfg)
+    roof = None
+    if flops is not None:
+        achieved = flops / (dom_avg_ms / 1e3) / 1e12
+        if head == "bf16":
+            peak = (peaks or {}).get("bf16_tflops_sustained", 1700.0)
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": dom, "peak_source": "measured bf16 sustained" if peaks else "fallback"}
+        else:
+            clock = (peaks or {}).get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * clock * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": dom,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    cpu = None
+    if not a.no_cpu_baseline and ws == 1:
+        v, dt, cores = _oracle_sample_rate(coord, atype, box, a.cpu_sample)
+        cpu = {"value": v, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{a.cpu_sample} random centres of the {n}-atom box (E, e_i and their force terms), {dt:.1f} s"}
+    h2d = n * 3 * 8 + n * 4 + 9 * 8
+    d2h = 8 + 9 * 8 + n * 3 * 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "model": MODEL, "natoms": n, "global_batch": ws * n,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "per-step working set is several GB of intermediates, far above the 129 MB L2"},
+        "clocks": r["clocks"],
+        "e2e": {"value": ws * n * e2e_steps / e2e_s, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": r["launches"],
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "precisions": {p: {"value": ws * n * a.steps / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / a.steps}
+                       for p, rr in results.items()},
+        "force_rmse_vs_fp64": parity,
+        "stage_ms_per_step": {p: {k: v[0] / a.steps for k, v in rr["stages"].items()} for p, rr in results.items()},
+        "neighbors": {"mean": float(nn.mean()), "max": int(nn.max())},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -136,6 +136,20 @@ DP_API int dp_inspect_weights(const char* weights_path, int* ints16, double* dbl
  * dp_status. */
 DP_API long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t bytes);
 
+/* Profiling: dp_set_profiling(m, 1) clears the record and makes every later
+ * call record a CUDA event on its stream after each stage (the per-region
+ * timing of the paper's profiling setup, Sec. V-D); 0 switches it off.
+ * dp_stage_times waits for the last recorded call and writes, for each
+ * stage of every call since profiling was switched on, in launch order, its
+ * name (static strings owned by the library) and device time in ms; it
+ * returns the number of stages written (0 when profiling is off).  A stage
+ * repeated per attention layer appears once per layer. */
+DP_API int dp_set_profiling(dp_model* m, int on);
+DP_API int dp_stage_times(dp_model* m, const char** names, float* ms, int max_stages);
+
+/* Number of CUDA kernels this library has launched in this process. */
+DP_API long long dp_kernel_launches(void);
+
 /* Text of the calling thread's last error ("" if none). */
 DP_API const char* dp_last_error(void);
 

@@ -6,8 +6,8 @@ binding.  Importing the package loads the library and fails loudly if it
 has not been built.
 """
 
-from .binding import DPA1, DPError, inspect_weights, load_library, LIB_PATH, EXPORTS, box9
+from .binding import DPA1, DPError, inspect_weights, kernel_launches, load_library, LIB_PATH, EXPORTS, box9
 
 load_library()
 
-__all__ = ["DPA1", "DPError", "inspect_weights", "load_library", "LIB_PATH", "EXPORTS", "box9"]
+__all__ = ["DPA1", "DPError", "inspect_weights", "kernel_launches", "load_library", "LIB_PATH", "EXPORTS", "box9"]

@@ -23,7 +23,7 @@ PRECISION = {"fp32": 0, "bf16": 1}
 
 EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_batch", "dp_reserve", "dp_set_precision",
            "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
-           "dp_last_error", "dp_free")
+           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_last_error", "dp_free")
 
 
 class DPError(RuntimeError):
@@ -58,12 +58,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dp_inspect_weights.argtypes = [ctypes.c_char_p, I, D]
     lib.dp_debug_copy.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t]
     lib.dp_debug_copy.restype = ctypes.c_longlong
+    lib.dp_set_profiling.argtypes = [P, ctypes.c_int]
+    lib.dp_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.dp_kernel_launches.argtypes = []
+    lib.dp_kernel_launches.restype = ctypes.c_longlong
     lib.dp_last_error.argtypes = []
     lib.dp_last_error.restype = ctypes.c_char_p
     lib.dp_free.argtypes = [P]
     lib.dp_free.restype = None
     for name in EXPORTS:
-        if name not in ("dp_debug_copy", "dp_last_error", "dp_free"):
+        if name not in ("dp_debug_copy", "dp_last_error", "dp_free", "dp_kernel_launches"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -87,6 +91,11 @@ def box9(box) -> np.ndarray:
     if b.shape == (3,):
         b = np.diag(b)
     return np.ascontiguousarray(b.reshape(9))
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().dp_kernel_launches())
 
 
 def inspect_weights(path: str) -> Tuple[np.ndarray, np.ndarray]:
@@ -187,6 +196,18 @@ class DPA1:
         if r < 0:
             _check(int(r))
         return out
+
+    def set_profiling(self, on: bool) -> None:
+        _check(self.lib.dp_set_profiling(self.h, 1 if on else 0))
+
+    def stage_times(self):
+        """[(stage, ms)] of every call since profiling was switched on."""
+        names = (ctypes.c_char_p * 8192)()
+        ms = (ctypes.c_float * 8192)()
+        k = self.lib.dp_stage_times(self.h, names, ms, 8192)
+        if k < 0:
+            _check(k)
+        return [(names[i].decode(), float(ms[i])) for i in range(k)]
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None and self.h.value:

@@ -2,6 +2,7 @@
 // orchestration of stages a1-a15 on one CUDA stream.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -161,6 +162,25 @@ __global__ void k_type_tables(const double* __restrict__ teW, const double* __re
 
 }  // namespace
 
+namespace dpa1 {
+static std::atomic<long long> g_launches{0};
+void note_launch(int count) { g_launches += count; }
+
+void prof_mark(dp_model* m, const char* stage, cudaStream_t st) {
+  Profiler& p = m->prof;
+  if (!p.on || p.count >= Profiler::MAXEV) return;
+  if ((int)p.ev.size() <= p.count) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    p.ev.push_back(e);
+    p.name.push_back(nullptr);
+  }
+  cudaEventRecord(p.ev[p.count], st);
+  p.name[p.count] = stage;
+  ++p.count;
+}
+}  // namespace dpa1
+
 namespace {
 
 template <class T>
@@ -213,11 +233,13 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.nlist = a.take<int>(rows);
     ws.nnei = a.take<int>(cap);
     ws.ncand = a.take<int>(cap);
+    ws.atype_c = a.take<int>(cap);
     ws.rev_cnt = a.take<int>(cap);
     ws.rev_rows = a.take<int>((size_t)cap * REV_CAP);
     ws.R = a.take<float>(rows * 4);
     ws.rw = a.take<float>(rows * 4);
     ws.rv = a.take<float>(rows * 4);
+    ws.w64 = a.take<double>(rows);
     ws.dR = a.take<float>(rows * 4);
     ws.dgeo = a.take<float>(rows * 4);
     ws.g = a.take<float>(rows * 4);
@@ -299,7 +321,7 @@ void run_neighbors(dp_model* m, int n, const double* coord, const double* box, c
   a.cap_dim = ws.cap_dim; a.cell_cap = ws.cell_cap; a.grid = ws.grid;
   a.cell_of = ws.cell_of; a.cell_count = ws.cell_count; a.cell_start = ws.cell_start;
   a.cell_cursor = ws.cell_cursor; a.cell_atoms = ws.cell_atoms;
-  a.nlist = ws.nlist; a.nnei = ws.nnei; a.ncand = ws.ncand; a.err = m->d_err;
+  a.nlist = ws.nlist; a.nnei = ws.nnei; a.ncand = ws.ncand; a.atype_c = ws.atype_c; a.err = m->d_err;
   launch_neighbors(a, st);
 }
 
@@ -313,17 +335,21 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   ea.R = ws.R; ea.nlist = ws.nlist; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
   ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
   launch_embed_fwd(ea, m->emb, st);
+  prof_mark(m, "embed_fwd", st);
   // a6: attention layers
   for (int l = 0; l < L; ++l) {
     const AttnLayerW& w = m->attn[l];
     gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, 3 * A, m1, EPI_BIAS, st);
+    prof_mark(m, "qkv_gemm", st);
     AttnArgs aa{};
-    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
+    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
     aa.O = ws.O[l];
     launch_attn_fwd_f32(aa, st);
+    prof_mark(m, "attn_fwd", st);
     gemm_f32(ws.O[l], A, w.Wo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, A, EPI_BIAS, st);
     launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
                       m1, st);
+    prof_mark(m, "wo_gemm_ln", st);
   }
   // a7: descriptor
   DescArgs da{};
@@ -331,6 +357,7 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   da.n = n; da.m1 = m1; da.axis = m->axis; da.tebd_dim = m->td; da.sel = m->sel; da.fit_in = m->fit_in;
   da.T = ws.T; da.X = ws.X; da.dX = ws.dX; da.dG = ws.dG; da.dR = ws.dR;
   launch_desc_fwd(da, st);
+  prof_mark(m, "desc_fwd", st);
   // a8: fitting forward
   int fan = m->fit_in;
   const float* hin = ws.X;
@@ -358,24 +385,30 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
              res ? EPI_RES : EPI_BIAS, st);
     std::swap(dH, dHn);
   }
+  prof_mark(m, "fitting", st);
   // a11: descriptor backward -> dG (w.r.t. G_L) and dR
   launch_desc_bwd(da, st);
+  prof_mark(m, "desc_bwd", st);
   // a12: attention backward
   cudaMemsetAsync(ws.dgeo, 0, sizeof(float) * (size_t)rows * 4, st);
   for (int l = L - 1; l >= 0; --l) {
     const AttnLayerW& w = m->attn[l];
     launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
     gemm_f32(ws.dY, m1, w.WoT, A, nullptr, nullptr, 0, ws.dO, A, rows, A, m1, EPI_BIAS, st);
+    prof_mark(m, "ln_wo_bwd", st);
     AttnArgs aa{};
-    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
+    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
     aa.dO = ws.dO; aa.dQKV = ws.dQKV; aa.dgeo = ws.dgeo; aa.scratch = ws.attn_scratch;
     aa.scratch_blocks = ws.attn_scratch_blocks;
     launch_attn_bwd_f32(aa, st);
+    prof_mark(m, "attn_bwd", st);
     gemm_f32(ws.dQKV, 3 * A, w.WqkvT, m1, nullptr, nullptr, 0, ws.dG, m1, rows, m1, 3 * A, EPI_ACCUM, st);
+    prof_mark(m, "qkv_bwd_gemm", st);
   }
   // a13: embedding backward -> dR[:,0]
   ea.dG0 = ws.dG; ea.dR = ws.dR;
   launch_embed_bwd(ea, m->emb, st);
+  prof_mark(m, "embed_bwd", st);
 }
 
 int run_device(dp_model* m, int n, const double* coord, const double* box, const int* atype, double* energy,
@@ -384,22 +417,28 @@ int run_device(dp_model* m, int n, const double* coord, const double* box, const
   if (n > ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
   m->last_stream = st;
   m->last_natoms = n;
+  prof_mark(m, "start", st);
   run_neighbors(m, n, coord, box, atype, st);
+  prof_mark(m, "neighbors", st);
+  atype = ws.atype_c;  // every later stage reads the range-checked types
   // a3: environment matrix
   EnvArgs ea{};
   ea.coord = coord; ea.atype = atype; ea.grid = ws.grid; ea.nlist = ws.nlist; ea.n = n;
   ea.davg = m->davg; ea.dstd = m->dstd; ea.rcs = (float)m->rcs; ea.rc = (float)m->rcut;
-  ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv;
+  ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv; ea.w64 = ws.w64;
   launch_env(ea, st);
+  prof_mark(m, "env", st);
   if (m->precision == DP_PREC_BF16)
     tc_run_network(m, n, atype, st);
   else
     run_network_f32(m, n, atype, st);
   // a14: per-pair gradient
   EnvBwdArgs eb{};
+  eb.coord = coord; eb.grid = ws.grid; eb.fp64 = m->precision == DP_PREC_FP32 ? 1 : 0;
   eb.rv = ws.rv; eb.nlist = ws.nlist; eb.atype = atype; eb.n = n; eb.dstd = m->dstd;
   eb.rcs = (float)m->rcs; eb.rc = (float)m->rcut; eb.dR = ws.dR; eb.dgeo = ws.dgeo; eb.g = ws.g;
   launch_env_bwd(eb, st);
+  prof_mark(m, "env_bwd", st);
   // a15: forces, virial, energy
   launch_reverse(ws.nlist, n, ws.rev_cnt, ws.rev_rows, m->d_err, st);
   ForceArgs fa{};
@@ -407,6 +446,7 @@ int run_device(dp_model* m, int n, const double* coord, const double* box, const
   fa.n = n; fa.force = force; fa.atom_energy = atom_energy; fa.partials = ws.partials; fa.energy = energy;
   fa.virial = virial; fa.err = m->d_err;
   launch_force_virial(fa, st);
+  prof_mark(m, "force_virial", st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
   return DP_OK;
@@ -729,6 +769,32 @@ long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t by
   return (long long)sz;
 }
 
+int dp_set_profiling(dp_model* m, int on) {
+  if (check_model(m)) return DP_ERR_ARG;
+  m->prof.on = on != 0;
+  m->prof.count = 0;
+  return DP_OK;
+}
+
+int dp_stage_times(dp_model* m, const char** names, float* ms, int max_stages) {
+  if (check_model(m)) return DP_ERR_ARG;
+  Profiler& p = m->prof;
+  if (!p.on || p.count < 2) return 0;
+  CUDA_TRY(cudaEventSynchronize(p.ev[p.count - 1]));
+  int k = 0;
+  for (int i = 1; i < p.count && k < max_stages; ++i) {
+    if (strcmp(p.name[i], "start") == 0) continue;  // the gap between two calls
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, p.ev[i - 1], p.ev[i]));
+    if (names) names[k] = p.name[i];
+    if (ms) ms[k] = t;
+    ++k;
+  }
+  return k;
+}
+
+long long dp_kernel_launches(void) { return g_launches.load(); }
+
 void dp_free(dp_model* m) {
   if (!m) return;
   cudaSetDevice(m->device);
@@ -738,6 +804,8 @@ void dp_free(dp_model* m) {
   for (void* p : m->allocations) cudaFree(p);
   if (m->d_err) cudaFree(m->d_err);
   if (m->stream) cudaStreamDestroy(m->stream);
+  for (auto& e : m->prof.ev)
+    if (e) cudaEventDestroy(e);
   delete m;
 }
 

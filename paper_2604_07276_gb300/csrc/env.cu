@@ -16,6 +16,7 @@ __global__ void k_env(EnvArgs a) {
   const int i = (int)(row / NP);
   const int j = a.nlist[row];
   float4 R = make_float4(0.f, 0.f, 0.f, 0.f), rw = R, rv = R;
+  double w64 = 0.0;
   if (j >= 0) {
     const CellGrid g = *a.grid;
     double dx = mic(a.coord[3 * j] - a.coord[3 * i], g.L[0]);
@@ -41,7 +42,9 @@ __global__ void k_env(EnvArgs a) {
                     (float)((s * hy - av[2]) / sv[2]), (float)((s * hz - av[3]) / sv[3]));
     rw = make_float4((float)hx, (float)hy, (float)hz, (float)sw);
     rv = make_float4((float)dx, (float)dy, (float)dz, (float)d);
+    w64 = sw;
   }
+  if (a.w64) a.w64[row] = w64;
   reinterpret_cast<float4*>(a.R)[row] = R;
   reinterpret_cast<float4*>(a.rw)[row] = rw;
   reinterpret_cast<float4*>(a.rv)[row] = rv;
@@ -51,44 +54,60 @@ void launch_env(const EnvArgs& a, cudaStream_t st) {
   long long rows = (long long)a.n * NP;
   if (rows == 0) return;
   k_env<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+  note_launch();
 }
 
 // Chain rule from dE/dR (4 columns), dE/dw and dE/drhat back to r_ij:
 //   R0 = s(d), R1..3 = q(d) r with q = s/d, w = sw(d), rhat = r/d.
+// Real = double recomputes r_ij from the FP64 coordinates (the FP32 path);
+// Real = float uses the stored FP32 displacement.
+template <typename Real>
 __global__ void k_env_bwd(EnvBwdArgs a) {
   long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= (long long)a.n * NP) return;
   float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (a.nlist[row] >= 0) {
-    const float4 rv = reinterpret_cast<const float4*>(a.rv)[row];
+  const int j = a.nlist[row];
+  if (j >= 0) {
+    const int i = (int)(row / NP);
+    Real rx, ry, rz;
+    if (sizeof(Real) == 8) {
+      const CellGrid g = *a.grid;
+      rx = (Real)mic(a.coord[3 * j] - a.coord[3 * i], g.L[0]);
+      ry = (Real)mic(a.coord[3 * j + 1] - a.coord[3 * i + 1], g.L[1]);
+      rz = (Real)mic(a.coord[3 * j + 2] - a.coord[3 * i + 2], g.L[2]);
+    } else {
+      const float4 rv = reinterpret_cast<const float4*>(a.rv)[row];
+      rx = rv.x; ry = rv.y; rz = rv.z;
+    }
     const float4 dR = reinterpret_cast<const float4*>(a.dR)[row];
     const float4 dg = reinterpret_cast<const float4*>(a.dgeo)[row];
-    const int t = a.atype[row / NP];
-    const float d = rv.w;
-    const float inv = 1.0f / d;
-    const float hx = rv.x * inv, hy = rv.y * inv, hz = rv.z * inv;
-    float sw, dsw;
-    if (d < a.rcs) {
-      sw = 1.f; dsw = 0.f;
-    } else if (d < a.rc) {
-      const float w = a.rc - a.rcs;
-      const float u = (d - a.rcs) / w;
-      sw = u * u * u * (-6.f * u * u + 15.f * u - 10.f) + 1.f;
-      dsw = -30.f * u * u * (u - 1.f) * (u - 1.f) / w;
+    const int t = a.atype[i];
+    const Real d = sqrt(rx * rx + ry * ry + rz * rz);
+    const Real inv = Real(1) / d;
+    const Real hx = rx * inv, hy = ry * inv, hz = rz * inv;
+    const Real rcs = a.rcs, rc = a.rc;
+    Real sw, dsw;
+    if (d < rcs) {
+      sw = 1; dsw = 0;
+    } else if (d < rc) {
+      const Real wdt = rc - rcs;
+      const Real u = (d - rcs) / wdt;
+      sw = u * u * u * (Real(-6) * u * u + Real(15) * u - Real(10)) + Real(1);
+      dsw = Real(-30) * u * u * (u - Real(1)) * (u - Real(1)) / wdt;
     } else {
-      sw = 0.f; dsw = 0.f;
+      sw = 0; dsw = 0;
     }
-    const float ds = dsw * inv - sw * inv * inv;           // d s / d d
-    const float q = sw * inv * inv;                         // s / d
-    const float dq = dsw * inv * inv - 2.f * sw * inv * inv * inv;
+    const Real ds = dsw * inv - sw * inv * inv;  // d s / d d
+    const Real q = sw * inv * inv;                // s / d
+    const Real dq = dsw * inv * inv - Real(2) * sw * inv * inv * inv;
     const float* sv = a.dstd + 4 * t;
-    const float r0 = dR.x / sv[0], r1 = dR.y / sv[1], r2 = dR.z / sv[2], r3 = dR.w / sv[3];
-    const float vdotr = r1 * rv.x + r2 * rv.y + r3 * rv.z;
-    const float radial = r0 * ds + dq * vdotr + dg.w * dsw;  // coefficient of rhat
-    const float hdot = dg.x * hx + dg.y * hy + dg.z * hz;
-    out.x = radial * hx + q * r1 + (dg.x - hdot * hx) * inv;
-    out.y = radial * hy + q * r2 + (dg.y - hdot * hy) * inv;
-    out.z = radial * hz + q * r3 + (dg.z - hdot * hz) * inv;
+    const Real r0 = (Real)dR.x / sv[0], r1 = (Real)dR.y / sv[1], r2 = (Real)dR.z / sv[2], r3 = (Real)dR.w / sv[3];
+    const Real vdotr = r1 * rx + r2 * ry + r3 * rz;
+    const Real radial = r0 * ds + dq * vdotr + (Real)dg.w * dsw;  // coefficient of rhat
+    const Real hdot = (Real)dg.x * hx + (Real)dg.y * hy + (Real)dg.z * hz;
+    out.x = (float)(radial * hx + q * r1 + ((Real)dg.x - hdot * hx) * inv);
+    out.y = (float)(radial * hy + q * r2 + ((Real)dg.y - hdot * hy) * inv);
+    out.z = (float)(radial * hz + q * r3 + ((Real)dg.z - hdot * hz) * inv);
   }
   reinterpret_cast<float4*>(a.g)[row] = out;
 }
@@ -96,7 +115,11 @@ __global__ void k_env_bwd(EnvBwdArgs a) {
 void launch_env_bwd(const EnvBwdArgs& a, cudaStream_t st) {
   long long rows = (long long)a.n * NP;
   if (rows == 0) return;
-  k_env_bwd<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+  if (a.fp64)
+    k_env_bwd<double><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+  else
+    k_env_bwd<float><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+  note_launch();
 }
 
 // Forces F_k = sum_j g_kj - sum_{i: k in N(i)} g_ik (Eq. eq_forceAtomicEnergy
@@ -182,8 +205,12 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, dou
 
 void launch_force_virial(const ForceArgs& a, cudaStream_t st) {
   const int nb = a.n > 0 ? (a.n + FWARPS - 1) / FWARPS : 0;
-  if (nb > 0) k_force<<<nb, 32 * FWARPS, 0, st>>>(a);
+  if (nb > 0) {
+    k_force<<<nb, 32 * FWARPS, 0, st>>>(a);
+    note_launch();
+  }
   k_finalize<<<1, 320, 0, st>>>(a.partials, nb, a.energy, a.virial);
+  note_launch();
 }
 
 }  // namespace dpa1

@@ -6,6 +6,9 @@
 
 namespace dpa1 {
 
+// Process-wide count of kernel launches made by this library.
+void note_launch(int count = 1);
+
 struct CellGrid;
 
 struct NbrArgs {
@@ -18,6 +21,7 @@ struct NbrArgs {
   CellGrid* grid;
   int *cell_of, *cell_count, *cell_start, *cell_cursor, *cell_atoms;
   int *nlist, *nnei, *ncand;
+  int* atype_c;  // out: types clamped to [0, ntypes)
   int* err;
 };
 void launch_neighbors(const NbrArgs& a, cudaStream_t st);
@@ -36,10 +40,14 @@ struct EnvArgs {
   float* R;   // [n*NP][4] normalised environment rows
   float* rw;  // [n*NP][4] (rhat_x, rhat_y, rhat_z, w)
   float* rv;  // [n*NP][4] (x, y, z, |r|)
+  double* w64;  // [n*NP] switch weight in FP64
 };
 void launch_env(const EnvArgs& a, cudaStream_t st);
 
 struct EnvBwdArgs {
+  const double* coord;
+  const CellGrid* grid;
+  int fp64;  // 1: recompute r_ij and the chain rule in FP64
   const float* rv;
   const int* nlist;
   const int* atype;
@@ -97,6 +105,7 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 struct AttnArgs {
   const float* QKV;  // [rows][3A]
   const float* rw;   // [rows][4]
+  const double* w64; // [rows] switch weights in FP64
   const int* nnei;
   int n, A;
   float shift;

@@ -54,8 +54,10 @@ struct Workspace {
   int *cell_of, *cell_count, *cell_start, *cell_cursor, *cell_atoms;
   int cell_cap, cap_dim;
   int *nlist, *nnei, *ncand, *rev_cnt, *rev_rows;
+  int* atype_c;  // device-checked copy of the atom types
   // environment
   float *R, *rw, *rv, *dR, *dgeo, *g;
+  double* w64;
   // network
   std::vector<float*> G, QKV, O, Y, stats;
   float *dG, *dY, *dO, *dQKV;
@@ -70,6 +72,16 @@ struct Workspace {
   int* atype;
   // tensor-core path buffers
   TcBuffers tc;
+};
+
+// Per-stage CUDA-event timing of one call (enabled with dp_set_profiling).
+// Stage boundaries accumulate over calls until profiling is switched on again.
+struct Profiler {
+  static constexpr int MAXEV = 8192;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char*> name;
+  int count = 0;
 };
 
 }  // namespace dpa1
@@ -98,8 +110,13 @@ struct dp_model {
   cudaStream_t stream = nullptr;  // own stream of the host API
   cudaStream_t last_stream = nullptr;
   int last_natoms = 0;
-  int* h_ncand_max = nullptr;
+  dpa1::Profiler prof;
 };
+
+namespace dpa1 {
+// Record a stage boundary on the stream (no-op unless profiling is on).
+void prof_mark(dp_model* m, const char* stage, cudaStream_t st);
+}  // namespace dpa1
 
 
 namespace dpa1 {

@@ -44,7 +44,7 @@ __device__ __forceinline__ int cell_coord(double x, double L, int nc) {
 
 __global__ void k_cell_count(const double* __restrict__ coord, const int* __restrict__ atype, int n,
                              int ntypes, const CellGrid* __restrict__ cgp, int* __restrict__ cell_of,
-                             int* __restrict__ cell_count, int* __restrict__ err) {
+                             int* __restrict__ cell_count, int* __restrict__ atype_c, int* __restrict__ err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const CellGrid g = *cgp;
@@ -59,7 +59,11 @@ __global__ void k_cell_count(const double* __restrict__ coord, const int* __rest
     c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
   }
   int t = atype[i];
-  if (t < 0 || t >= ntypes) set_err(err, ERR_TYPE);
+  if (t < 0 || t >= ntypes) {
+    set_err(err, ERR_TYPE);
+    t = t < 0 ? 0 : ntypes - 1;  // every later table lookup stays in bounds
+  }
+  atype_c[i] = t;
   cell_of[i] = c;
   atomicAdd(&cell_count[c], 1);
 }
@@ -208,15 +212,20 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t st) {
   cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)a.cell_cap, st);
   cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)a.cell_cap, st);
   k_cell_setup<<<1, 1, 0, st>>>(a.box, a.rcut, a.cap_dim, a.grid, a.err);
+  note_launch();
   if (a.n == 0) return;
   const int tb = 256;
   k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of,
-                                                  a.cell_count, a.err);
+                                                  a.cell_count, a.atype_c, a.err);
+  note_launch();
   k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid);
+  note_launch();
   k_cell_fill<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.cell_of, a.n, a.cell_start, a.cell_cursor, a.cell_atoms);
+  note_launch();
   k_neighbors<<<(a.n + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
       a.coord, a.n, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist,
       a.nnei, a.ncand, a.err);
+  note_launch();
 }
 
 void launch_reverse(const int* nlist, int n, int* rev_cnt, int* rev_rows, int* err, cudaStream_t st) {
@@ -224,6 +233,7 @@ void launch_reverse(const int* nlist, int n, int* rev_cnt, int* rev_rows, int* e
   if (n == 0) return;
   long long rows = (long long)n * NP;
   k_rev_fill<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(nlist, n, rev_cnt, rev_rows, err);
+  note_launch();
 }
 
 }  // namespace dpa1

@@ -76,11 +76,11 @@ void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bia
   if (M <= 0 || N <= 0) return;
   dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
   switch (epi) {
-    case EPI_BIAS: k_sgemm<EPI_BIAS><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    case EPI_TANH: k_sgemm<EPI_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    case EPI_RES_TANH: k_sgemm<EPI_RES_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    case EPI_ACCUM: k_sgemm<EPI_ACCUM><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    default: k_sgemm<EPI_RES><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_BIAS: k_sgemm<EPI_BIAS><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
+    case EPI_TANH: k_sgemm<EPI_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
+    case EPI_RES_TANH: k_sgemm<EPI_RES_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
+    case EPI_ACCUM: k_sgemm<EPI_ACCUM><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
+    default: k_sgemm<EPI_RES><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
   }
 }
 
@@ -220,10 +220,12 @@ static void embed_launch(const EmbedArgs& a, bool bwd, cudaStream_t st) {
     size_t sm = sizeof(float) * Lw::TOTAL;
     cudaFuncSetAttribute(k_embed_fwd<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_embed_fwd<E0, E1, E2><<<grid, 128, sm, st>>>(a);
+    note_launch();
   } else {
     size_t sm = sizeof(float) * (Lw::TOTAL + E2 * 128);
     cudaFuncSetAttribute(k_embed_bwd<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_embed_bwd<E0, E1, E2><<<grid, 128, sm, st>>>(a);
+    note_launch();
   }
 }
 
@@ -315,12 +317,14 @@ void launch_ln_res_fwd(const float* Y, const float* Gin, const int* nlist, const
   if (rows == 0) return;
   k_ln_res_fwd<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(Y, Gin, nlist, gamma, beta, eps, Gout, stats,
                                                                       rows, m1);
+  note_launch();
 }
 void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const int* nlist, const float* gamma,
                    float* dY, int rows_i, int m1, cudaStream_t st) {
   long long rows = rows_i;
   if (rows == 0) return;
   k_ln_bwd<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(dZ, Y, stats, nlist, gamma, dY, rows, m1);
+  note_launch();
 }
 
 // ------------------------------------------------- gated attention (FP32)
@@ -337,6 +341,7 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
   float4* rws = reinterpret_cast<float4*>(Vs + NP * A);  // [NP]
   float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][A]
   float* prow = qrow + AW * A;                      // [AW][NP]
+  double* w64s = reinterpret_cast<double*>(prow + AW * NP);  // [NP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int FQ = A / 32;
   const int ld = 3 * A;
@@ -348,8 +353,10 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
       Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
       Vs[r * A + f] = a.QKV[(base + r) * ld + 2 * A + f];
     }
-    for (int r = threadIdx.x; r < NP; r += blockDim.x)
+    for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      w64s[r] = r < nn ? a.w64[base + r] : 0.0;
+    }
     __syncthreads();
     for (int j = warp; j < NP; j += AW) {
       float* o = a.O + (base + j) * A;
@@ -367,22 +374,26 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
         for (int m = 0; m < 4; ++m) s[m] = fmaf(qf, Ks[(lane + 32 * m) * (A + 1) + f], s[m]);
       }
       const float4 rj = rws[j];
-      float lp[4], mx = -INFINITY;
+      // smooth logits (l + S) w_j w_k (the constant -S of every logit of a row
+      // cancels in the softmax) in FP64: S = 20 leaves the FP32 spacing near
+      // the logits at 2e-6, far coarser than the logit differences that matter
+      const double wj = w64s[j];
+      double lp[4], mx = -1e300;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int k = lane + 32 * m;
+        lp[m] = 0.0;
         if (k < nn) {
-          const float ww = rj.w * rws[k].w;
-          lp[m] = (s[m] * scale + a.shift) * ww - a.shift;
-          mx = fmaxf(mx, lp[m]);
+          lp[m] = ((double)(s[m] * scale) + (double)a.shift) * (wj * w64s[k]);
+          mx = fmax(mx, lp[m]);
         }
       }
-      mx = warp_max(mx);
+      mx = warp_max_d(mx);
       float e[4], sum = 0.f;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int k = lane + 32 * m;
-        e[m] = k < nn ? expf(lp[m] - mx) : 0.f;
+        e[m] = k < nn ? expf((float)(lp[m] - mx)) : 0.f;
         sum += e[m];
       }
       sum = warp_sum(sum);
@@ -432,6 +443,7 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
   float* prow = dorow + AW * A;                     // [AW][NP]
   float* colw = prow + AW * NP;                     // [AW][NP]
   float* colr = colw + AW * NP;                     // [AW][NP][3]
+  double* w64s = reinterpret_cast<double*>(colr + 3 * AW * NP);  // [NP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int FQ = A / 32;
   const int ld = 3 * A;
@@ -445,8 +457,10 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
       Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
       Vs[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
     }
-    for (int r = threadIdx.x; r < NP; r += blockDim.x)
+    for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      w64s[r] = r < nn ? a.w64[base + r] : 0.0;
+    }
     for (int t = threadIdx.x; t < AW * NP; t += blockDim.x) {
       colw[t] = 0.f;
       colr[3 * t] = 0.f; colr[3 * t + 1] = 0.f; colr[3 * t + 2] = 0.f;
@@ -471,7 +485,9 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
         }
       }
       const float4 rj = rws[j];
-      float l[4], lp[4], ww[4], c[4], mx = -INFINITY;
+      const double wj = w64s[j];
+      float l[4], ww[4], c[4];
+      double lp[4], mx = -1e300;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int k = lane + 32 * m;
@@ -479,14 +495,17 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
         ww[m] = rj.w * rk.w;
         c[m] = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
         l[m] = s[m] * scale;
-        lp[m] = (l[m] + a.shift) * ww[m] - a.shift;
-        if (k < nn) mx = fmaxf(mx, lp[m]);
+        lp[m] = 0.0;
+        if (k < nn) {
+          lp[m] = ((double)l[m] + (double)a.shift) * (wj * w64s[k]);  // as in the forward kernel
+          mx = fmax(mx, lp[m]);
+        }
       }
-      mx = warp_max(mx);
+      mx = warp_max_d(mx);
       float e[4], sum = 0.f;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        e[m] = (lane + 32 * m) < nn ? expf(lp[m] - mx) : 0.f;
+        e[m] = (lane + 32 * m) < nn ? expf((float)(lp[m] - mx)) : 0.f;
         sum += e[m];
       }
       sum = warp_sum(sum);
@@ -609,20 +628,23 @@ void launch_attn_fwd_f32(const AttnArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
   const float scale = (float)(1.0 / sqrt((double)a.A));
   const int A = 128;
-  size_t smem = sizeof(float) * (NP * (A + 1) + NP * A + 4 * NP + AW * A + AW * NP);
+  size_t smem = sizeof(float) * (NP * (A + 1) + NP * A + 4 * NP + AW * A + AW * NP) + sizeof(double) * NP;
   cudaFuncSetAttribute(k_attn_fwd_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = a.n < sm_count() ? a.n : sm_count();
   k_attn_fwd_f32<128><<<grid, 32 * AW, smem, st>>>(a, scale);
+  note_launch();
 }
 
 void launch_attn_bwd_f32(const AttnArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
   const float scale = (float)(1.0 / sqrt((double)a.A));
   const int A = 128;
-  size_t smem = sizeof(float) * (2 * NP * (A + 1) + 8 * NP + 2 * AW * A + 2 * AW * NP + 3 * AW * NP);
+  size_t smem = sizeof(float) * (2 * NP * (A + 1) + 8 * NP + 2 * AW * A + 2 * AW * NP + 3 * AW * NP) +
+                sizeof(double) * NP;
   cudaFuncSetAttribute(k_attn_bwd_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = a.n < a.scratch_blocks ? a.n : a.scratch_blocks;
   k_attn_bwd_f32<128><<<grid, 32 * AW, smem, st>>>(a, scale);
+  note_launch();
 }
 
 // ------------------------------------------------------------- descriptor
@@ -710,11 +732,13 @@ __global__ void k_desc_bwd(DescArgs a) {
 void launch_desc_fwd(const DescArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
   k_desc_fwd<<<a.n, 128, sizeof(float) * 4 * a.m1, st>>>(a);
+  note_launch();
 }
 void launch_desc_bwd(const DescArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
   size_t sm = sizeof(float) * (8 * a.m1 + a.m1 * a.axis);
   k_desc_bwd<<<a.n, 128, sm, st>>>(a);
+  note_launch();
 }
 
 // ------------------------------------------------------------ fitting head
@@ -735,6 +759,7 @@ void launch_energy_head(const float* H, int n, int width, const float* w_out, fl
   if (n == 0) return;
   k_energy_head<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(H, n, width, w_out, b_out, out_scale,
                                                                           ebias, atype, e);
+  note_launch();
 }
 
 __global__ void k_tanh_bwd(const float* __restrict__ dH, const float* __restrict__ Hc, const float* __restrict__ Hp,
@@ -749,6 +774,7 @@ void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, flo
                      cudaStream_t st) {
   if (count == 0) return;
   k_tanh_bwd<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dH, Hcur, Hprev, dZ, count);
+  note_launch();
 }
 
 __global__ void k_fill_rows(float* __restrict__ dst, const float* __restrict__ row, long long count, int width) {
@@ -761,6 +787,7 @@ void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream
   long long count = (long long)n * width;
   if (count == 0) return;
   k_fill_rows<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dst, row, count, width);
+  note_launch();
 }
 
 }  // namespace dpa1
