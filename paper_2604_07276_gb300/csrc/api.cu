@@ -325,32 +325,14 @@ void run_neighbors(dp_model* m, int n, const double* coord, const double* box, c
   launch_neighbors(a, st);
 }
 
-// The FP32 network path (stages a5-a13) between the environment matrix and
-// the per-pair gradient.
-void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
+}  // namespace
+
+namespace dpa1 {
+// Stages a7-a11 shared by both precisions: descriptor, fitting forward and
+// backward, descriptor backward (dE/dG of the last layer and dE/dR).
+void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t st) {
   Workspace& ws = m->ws;
-  const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
-  // a5: embedding
-  EmbedArgs ea{};
-  ea.R = ws.R; ea.nlist = ws.nlist; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
-  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
-  launch_embed_fwd(ea, m->emb, st);
-  prof_mark(m, "embed_fwd", st);
-  // a6: attention layers
-  for (int l = 0; l < L; ++l) {
-    const AttnLayerW& w = m->attn[l];
-    gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, 3 * A, m1, EPI_BIAS, st);
-    prof_mark(m, "qkv_gemm", st);
-    AttnArgs aa{};
-    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
-    aa.O = ws.O[l];
-    launch_attn_fwd_f32(aa, st);
-    prof_mark(m, "attn_fwd", st);
-    gemm_f32(ws.O[l], A, w.Wo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, A, EPI_BIAS, st);
-    launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
-                      m1, st);
-    prof_mark(m, "wo_gemm_ln", st);
-  }
+  const int L = m->nattn, m1 = m->m1;
   // a7: descriptor
   DescArgs da{};
   da.R = ws.R; da.G = ws.G[L]; da.nnei = ws.nnei; da.atype = atype; da.tebd = m->tebd;
@@ -389,6 +371,39 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   // a11: descriptor backward -> dG (w.r.t. G_L) and dR
   launch_desc_bwd(da, st);
   prof_mark(m, "desc_bwd", st);
+}
+
+}  // namespace dpa1
+
+namespace {
+
+// The FP32 network path (stages a5-a13) between the environment matrix and
+// the per-pair gradient.
+void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
+  // a5: embedding
+  EmbedArgs ea{};
+  ea.R = ws.R; ea.nlist = ws.nlist; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
+  launch_embed_fwd(ea, m->emb, st);
+  prof_mark(m, "embed_fwd", st);
+  // a6: attention layers
+  for (int l = 0; l < L; ++l) {
+    const AttnLayerW& w = m->attn[l];
+    gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, 3 * A, m1, EPI_BIAS, st);
+    prof_mark(m, "qkv_gemm", st);
+    AttnArgs aa{};
+    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
+    aa.O = ws.O[l];
+    launch_attn_fwd_f32(aa, st);
+    prof_mark(m, "attn_fwd", st);
+    gemm_f32(ws.O[l], A, w.Wo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, A, EPI_BIAS, st);
+    launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
+                      m1, st);
+    prof_mark(m, "wo_gemm_ln", st);
+  }
+  run_descriptor_fitting(m, n, atype, st);
   // a12: attention backward
   cudaMemsetAsync(ws.dgeo, 0, sizeof(float) * (size_t)rows * 4, st);
   for (int l = L - 1; l >= 0; --l) {

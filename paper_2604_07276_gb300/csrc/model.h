@@ -126,4 +126,6 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg);
 void tc_plan_buffers(dp_model* m, Arena& a, int cap);
 void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st);
 void tc_free_weights(dp_model* m);
+// stages a7-a11 (descriptor, fitting forward / backward, descriptor backward)
+void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t st);
 }  // namespace dpa1

@@ -1,19 +1,770 @@
-// Tensor-core (tcgen05, BF16 operands, FP32 accumulation) network path.
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation in TMEM) path of the
+// gated attention layers (stage a6) and their adjoint (stage a12).
+//
+// One persistent CTA per SM walks over centre atoms; an atom is one 128-row
+// tile (its neighbour slots).  Every product of a layer runs on the tensor
+// cores from 128x128 BF16 tiles in shared memory:
+//   forward : [Q K V] = G Wqkv, S = Q K^T, O = P V, Y = O Wo
+//   backward: [Q K V] = G Wqkv and S = Q K^T (recomputed), dO = dY Wo^T,
+//             dP = dO V^T, dV = P^T dO, dQ = dS K, dK = dS^T Q,
+//             dG = dQ Wq^T + dK Wk^T + dV Wv^T
+// The transposed operands are MN-major views of the same tiles, so no
+// transpose is ever materialised.  Softmax, LayerNorm and all element-wise
+// work run in FP32 on 256 threads (a thread owns half a row).
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
 #include "dpa1.h"
+#include "kernels.h"
 #include "model.h"
+#include "tc_ptx.cuh"
 
 namespace dpa1 {
 
-int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
-  (void)m; (void)arrays;
-  msg = "the BF16 tensor-core path is not available in this build";
-  return DP_ERR_UNSUPPORTED;
+using namespace tc;
+
+namespace {
+
+constexpr int NT = 256;           // threads per CTA
+constexpr int TILE = 32768;       // 128 x 128 bf16 SW128 tile
+constexpr int WO_ROWS = 112;      // Wo tile: M1 = 100 output rows padded to 112
+constexpr int WO_TILE = 2 * WO_ROWS * 128;  // 28 KB
+constexpr int WIMG = 3 * TILE + WO_TILE;     // per-layer weight image (bytes)
+constexpr int KS_M1 = 7;          // K-steps covering the M1 = 100 (<= 112) inputs
+
+struct LayerArgs {
+  const float* Gin;        // [rows][m1] layer input
+  float* Gout;             // fwd: [rows][m1] layer output
+  __nv_bfloat16* yhat;     // [rows][YLD] normalised LayerNorm input (fwd writes, bwd reads)
+  float* rstd;             // [rows]
+  float* dG;               // bwd: in dE/dG_{l+1}, out dE/dG_l (in place)
+  float* dgeo;             // bwd: [rows][4] += (d rhat, d w)
+  float* scratch;          // bwd: per-CTA column partials
+  const float* rw;         // [rows][4] (rhat, w)
+  const int* nnei;
+  int n, m1;
+  const uint4* wimg;       // swizzled weight image of this layer
+  const float* bqkv;       // [3*128]
+  const float* bo;         // [m1]
+  const float* gamma;      // [m1]
+  const float* beta;       // [m1]
+  float scale, shift, eps;
+  int* err;
+};
+
+constexpr int YLD = 104;  // row stride (elements) of yhat: 208 bytes, 16-byte aligned
+
+struct Sync {
+  uint64_t* bar;
+  uint32_t phase;
+  int* err;
+  bool ok = true;
+  __device__ bool wait() {
+    if (ok) ok = mbar_wait(bar, phase & 1u, err);
+    ++phase;
+    fence_after_sync();
+    return ok;
+  }
+};
+
+__device__ __forceinline__ void commit_and_sync(Sync& s, bool issuer) {
+  if (issuer) mma_commit(s.bar);
+  s.wait();
 }
-void tc_plan_buffers(dp_model*, Arena&, int) {}
-void tc_run_network(dp_model*, int, const int*, cudaStream_t) {}
+
+// All threads: make their generic shared-memory writes visible to the tensor
+// cores and finish their TMEM loads, then meet.
+__device__ __forceinline__ void handoff() {
+  fence_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+
+__device__ __forceinline__ void copy_image(uint8_t* dst, const uint4* src, int bytes) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < bytes / 16; i += NT) d[i] = src[i];
+}
+
+// Store 64 FP32 values (cols c0..c0+63 of row r) as bf16 into an SW128 tile.
+__device__ __forceinline__ void store_row64(uint8_t* tile, int r, int c0, const float* v) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    uint4 u;
+    u.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+    u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+    u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+    u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+    sw128_store8(tile, r, c0 + 8 * q, 128, u);
+  }
+}
+
+// Load row r of an FP32 [rows][m1] matrix, columns c0..c0+63 (zero past m1).
+__device__ __forceinline__ void load_row64(const float* src, int m1, int c0, float* v) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int c = c0 + 4 * q;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c < m1) x = *reinterpret_cast<const float4*>(src + c);  // m1 % 4 == 0
+    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+  }
+}
+
+// 64 TMEM columns of this thread's row (two 32-column loads).
+__device__ __forceinline__ void tmem_row64(uint32_t taddr, float* v) {
+  tmem_ld32(taddr, v);
+  tmem_ld32(taddr + 32, v + 32);
+}
+
+// Issue D = sum over K-steps of A * B for one 128 x N block.
+__device__ __forceinline__ void mma_block(uint32_t d, uint32_t a, bool a_mn, int a_rows, uint32_t b, bool b_mn,
+                                          int b_rows, int N, int ksteps, bool accumulate_first) {
+  const uint32_t id = idesc_bf16(128, N, a_mn, b_mn);
+  for (int s = 0; s < ksteps; ++s) {
+    const uint64_t ad = a_mn ? mnmajor_desc(a, s, a_rows) : kmajor_desc(a, s, a_rows);
+    const uint64_t bd = b_mn ? mnmajor_desc(b, s, b_rows) : kmajor_desc(b, s, b_rows);
+    mma_bf16(d, ad, bd, id, (s > 0 || accumulate_first) ? 1u : 0u);
+  }
+}
+
+// Exchange one float between the two threads (halves) that own row r.
+__device__ __forceinline__ float pair_sum(float* xch, int half, int row, float v) {
+  xch[half * 128 + row] = v;
+  __syncthreads();
+  const float o = xch[(half ^ 1) * 128 + row];
+  __syncthreads();
+  return v + o;
+}
+__device__ __forceinline__ float pair_max(float* xch, int half, int row, float v) {
+  xch[half * 128 + row] = v;
+  __syncthreads();
+  const float o = xch[(half ^ 1) * 128 + row];
+  __syncthreads();
+  return fmaxf(v, o);
+}
+
+// Sum over the 32 lanes of a warp of 32 values per lane; lane l returns the
+// sum of value l (a butterfly reduce-scatter, fixed order).
+__device__ __forceinline__ float reduce_scatter32(float* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = up ? v[i] : v[i + w];
+      const float keep = up ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// ------------------------------------------------------------------ forward
+// Shared memory: slot A [0,32K), slot B, slot C, Wq, Wk, Wv, Wo (28K), then
+// w[128], rhat[128][3], the half-row exchange and the barrier.
+constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_W = 3 * TILE;
+constexpr int F_SMALL = 3 * TILE + WIMG;
+constexpr int F_SMEM = F_SMALL + 512 + 1536 + 1024 + 64;
+
+__global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {  // tiles need 1024-byte alignment
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint8_t* sA = sm + F_SLOT_A;
+  uint8_t* sB = sm + F_SLOT_B;
+  uint8_t* sC = sm + F_SLOT_C;
+  uint8_t* sWq = sm + F_W;
+  uint8_t* sWk = sWq + TILE;
+  uint8_t* sWv = sWk + TILE;
+  uint8_t* sWo = sWv + TILE;
+  float* s_w = reinterpret_cast<float*>(sm + F_SMALL);
+  float* s_rh = s_w + 128;          // [128][3]
+  float* xch = s_rh + 384;          // [2][128]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + 256);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const int c0 = half * 64;
+  const bool issuer = tid == 0;
+
+  copy_image(sWq, a.wimg, WIMG);
+  if (issuer) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(s_tmem, 512);
+  handoff();
+  const uint32_t tm = *s_tmem;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC);
+  const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv), tWo = smem_u32(sWo);
+  Sync sy{bar, 0u, a.err};
+
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const size_t base = (size_t)atom * NP;
+    if (tid < 128) {
+      const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
+      const bool v = tid < nn;
+      s_w[tid] = v ? r.w : 0.f;
+      s_rh[3 * tid] = v ? r.x : 0.f;
+      s_rh[3 * tid + 1] = v ? r.y : 0.f;
+      s_rh[3 * tid + 2] = v ? r.z : 0.f;
+    }
+    float v[64];
+    // G_l (FP32) -> bf16 slot A
+    load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
+    store_row64(sA, row, c0, v);
+    handoff();
+    // [Q K V] = G Wqkv
+    if (issuer) {
+      mma_block(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
+      mma_block(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
+      mma_block(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
+    }
+    commit_and_sync(sy, issuer);
+    // Q -> A, K -> B, V -> C (with biases)
+#pragma unroll 1
+    for (int which = 0; which < 3; ++which) {
+      tmem_row64(tm + lane_off + which * 128 + c0, v);
+      const float* b = a.bqkv + which * 128 + c0;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) v[i] += b[i];
+      store_row64(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
+    }
+    handoff();
+    // S = Q K^T
+    if (issuer) mma_block(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
+    commit_and_sync(sy, issuer);
+    // smooth softmax and gate: P -> slot B
+    tmem_row64(tm + lane_off + 384 + c0, v);
+    {
+      const bool rv = row < nn;
+      const float wj = s_w[row];
+      float mx = -INFINITY;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int k = c0 + i;
+        const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_w[k]) : -INFINITY;
+        v[i] = l;
+        mx = fmaxf(mx, l);
+      }
+      mx = pair_max(xch, half, row, mx);
+      float sum = 0.f;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const float e = (v[i] == -INFINITY) ? 0.f : __expf(v[i] - mx);
+        v[i] = e;
+        sum += e;
+      }
+      sum = pair_sum(xch, half, row, sum);
+      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      const float hx = s_rh[3 * row], hy = s_rh[3 * row + 1], hz = s_rh[3 * row + 2];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int k = c0 + i;
+        const float c = hx * s_rh[3 * k] + hy * s_rh[3 * k + 1] + hz * s_rh[3 * k + 2];
+        v[i] = v[i] * inv * (wj * s_w[k]) * c;
+      }
+      store_row64(sB, row, c0, v);
+    }
+    handoff();
+    // O = P V  (V as an MN-major operand of slot C)
+    if (issuer) mma_block(tm + 0, tB, false, 128, tC, true, 128, 128, 8, false);
+    commit_and_sync(sy, issuer);
+    tmem_row64(tm + lane_off + 0 + c0, v);
+    store_row64(sA, row, c0, v);
+    handoff();
+    // Y = O Wo
+    if (issuer) mma_block(tm + 128, tA, false, 128, tWo, false, WO_ROWS, WO_ROWS, 8, false);
+    commit_and_sync(sy, issuer);
+    // LayerNorm, residual
+    {
+      tmem_row64(tm + lane_off + 128 + c0, v);
+      float s1 = 0.f;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int c = c0 + i;
+        v[i] = c < a.m1 ? v[i] + a.bo[c] : 0.f;
+        s1 += v[i];
+      }
+      const float mean = pair_sum(xch, half, row, s1) / (float)a.m1;
+      float s2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int c = c0 + i;
+        const float d = c < a.m1 ? v[i] - mean : 0.f;
+        s2 += d * d;
+      }
+      const float var = pair_sum(xch, half, row, s2) / (float)a.m1;
+      const float rs = 1.0f / sqrtf(var + a.eps);
+      const bool rv = row < nn;
+      const float* gin = a.Gin + (base + row) * a.m1;
+      float* gout = a.Gout + (base + row) * a.m1;
+      __nv_bfloat16* yh = a.yhat + (base + row) * YLD;
+#pragma unroll
+      for (int i = 0; i < 64; i += 4) {
+        const int c = c0 + i;
+        if (c < a.m1) {
+          float4 g = *reinterpret_cast<const float4*>(gin + c);
+          float y0 = (v[i] - mean) * rs, y1 = (v[i + 1] - mean) * rs, y2 = (v[i + 2] - mean) * rs,
+                y3 = (v[i + 3] - mean) * rs;
+          if (rv) {
+            g.x += y0 * a.gamma[c] + a.beta[c];
+            g.y += y1 * a.gamma[c + 1] + a.beta[c + 1];
+            g.z += y2 * a.gamma[c + 2] + a.beta[c + 2];
+            g.w += y3 * a.gamma[c + 3] + a.beta[c + 3];
+          }
+          *reinterpret_cast<float4*>(gout + c) = g;
+          uint2 u;
+          u.x = pack_bf16(y0, y1);
+          u.y = pack_bf16(y2, y3);
+          *reinterpret_cast<uint2*>(yh + c) = u;
+        }
+      }
+      if (half == 0) a.rstd[base + row] = rs;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+// ----------------------------------------------------------------- backward
+// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K, 224K), w, rhat, bar.
+// Wo is streamed per atom into slot D.  The half-row exchange borrows the
+// first 1 KB of whichever slot is free at that point.
+constexpr int B_SLOT_A = 0, B_SLOT_B = TILE, B_SLOT_C = 2 * TILE, B_SLOT_D = 3 * TILE, B_W = 4 * TILE;
+constexpr int B_SMALL = 4 * TILE + 3 * TILE;
+constexpr int B_SMEM = B_SMALL + 512 + 1536 + 64;
+constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 2 * 128 * 4;  // per CTA
+
+__global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint8_t* sA = sm + B_SLOT_A;
+  uint8_t* sB = sm + B_SLOT_B;
+  uint8_t* sC = sm + B_SLOT_C;
+  uint8_t* sD = sm + B_SLOT_D;
+  uint8_t* sWq = sm + B_W;
+  uint8_t* sWk = sWq + TILE;
+  uint8_t* sWv = sWk + TILE;
+  float* s_w = reinterpret_cast<float*>(sm + B_SMALL);
+  float* s_rh = s_w + 128;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_rh + 384);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const int c0 = half * 64;
+  const bool issuer = tid == 0;
+  float* colp = a.scratch + (size_t)blockIdx.x * SCRATCH_FLOATS;  // [quad][128 keys][4]
+  float* rowp = colp + 4 * 128 * 4;                                // [half][128 rows][4]
+
+  copy_image(sWq, a.wimg, 3 * TILE);
+  if (issuer) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(s_tmem, 512);
+  handoff();
+  const uint32_t tm = *s_tmem;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
+  const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
+  Sync sy{bar, 0u, a.err};
+  const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + 3 * TILE;
+
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const size_t base = (size_t)atom * NP;
+    const bool rv = row < nn;
+    if (tid < 128) {
+      const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
+      const bool vv = tid < nn;
+      s_w[tid] = vv ? r.w : 0.f;
+      s_rh[3 * tid] = vv ? r.x : 0.f;
+      s_rh[3 * tid + 1] = vv ? r.y : 0.f;
+      s_rh[3 * tid + 2] = vv ? r.z : 0.f;
+    }
+    float v[64];
+    // P0: G_l -> A, dY = LayerNorm adjoint of dZ -> C, Wo -> D
+    load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
+    store_row64(sA, row, c0, v);
+    copy_image(sD, reinterpret_cast<const uint4*>(wo_img), WO_TILE);
+    {
+      float* xch = reinterpret_cast<float*>(sB);
+      const float* dz = a.dG + (base + row) * a.m1;
+      const __nv_bfloat16* yh = a.yhat + (base + row) * YLD;
+      float yv[64];
+      float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const int c = c0 + i;
+        float g = 0.f, y = 0.f;
+        if (c < a.m1 && rv) {
+          g = a.gamma[c] * dz[c];
+          y = __bfloat162float(yh[c]);
+        }
+        v[i] = g;
+        yv[i] = y;
+        s1 += g;
+        s2 += g * y;
+      }
+      s1 = pair_sum(xch, half, row, s1) / (float)a.m1;
+      s2 = pair_sum(xch, half, row, s2) / (float)a.m1;
+      const float rs = rv ? a.rstd[base + row] : 0.f;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) v[i] = rv ? rs * (v[i] - s1 - yv[i] * s2) : 0.f;
+      store_row64(sC, row, c0, v);
+    }
+    handoff();
+    // M0: [Q K V] = G Wqkv ; dO = dY Wo^T (Wo tile as MN-major)
+    if (issuer) {
+      mma_block(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
+      mma_block(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
+      mma_block(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
+      mma_block(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+    }
+    commit_and_sync(sy, issuer);
+    // P1: Q -> A, K -> B, V -> C, dO -> D
+#pragma unroll 1
+    for (int which = 0; which < 4; ++which) {
+      tmem_row64(tm + lane_off + which * 128 + c0, v);
+      if (which < 3) {
+        const float* b = a.bqkv + which * 128 + c0;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] += b[i];
+      }
+      store_row64(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
+    }
+    handoff();
+    // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
+    if (issuer) {
+      mma_block(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
+      mma_block(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
+    }
+    commit_and_sync(sy, issuer);
+    // P2: softmax and its adjoint in 32-key passes that reload S and dP from
+    // TMEM; P -> slot C, dS -> TMEM over the consumed S columns
+    {
+      float* xch = reinterpret_cast<float*>(sC);  // V is dead after dP
+      const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
+      const float wj = s_w[row];
+      const float hx = s_rh[3 * row], hy = s_rh[3 * row + 1], hz = s_rh[3 * row + 2];
+      float t[32], u[32];
+      float mx = -INFINITY;
+#pragma unroll 1
+      for (int blk = 0; blk < 2; ++blk) {
+        tmem_ld32(tS + 32 * blk, t);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int k = c0 + 32 * blk + i;
+          if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_w[k]));
+        }
+      }
+      mx = pair_max(xch, half, row, mx);
+      float sum = 0.f;
+#pragma unroll 1
+      for (int blk = 0; blk < 2; ++blk) {
+        tmem_ld32(tS + 32 * blk, t);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int k = c0 + 32 * blk + i;
+          if (k < nn && rv) sum += __expf((t[i] * a.scale + a.shift) * (wj * s_w[k]) - mx);
+        }
+      }
+      sum = pair_sum(xch, half, row, sum);
+      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      float tsum = 0.f;
+#pragma unroll 1
+      for (int blk = 0; blk < 2; ++blk) {
+        tmem_ld32(tS + 32 * blk, t);
+        tmem_ld32(tP + 32 * blk, u);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int k = c0 + 32 * blk + i;
+          if (k < nn && rv) {
+            const float ww = wj * s_w[k];
+            const float A = __expf((t[i] * a.scale + a.shift) * ww - mx) * inv;
+            const float c = hx * s_rh[3 * k] + hy * s_rh[3 * k + 1] + hz * s_rh[3 * k + 2];
+            tsum += A * u[i] * ww * c;
+          }
+        }
+      }
+      tsum = pair_sum(xch, half, row, tsum);  // ends with a barrier: slot C is free
+      float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+      float4* cp = reinterpret_cast<float4*>(colp) + quad * 128 + c0;
+#pragma unroll 1
+      for (int blk = 0; blk < 2; ++blk) {
+        tmem_ld32(tS + 32 * blk, t);
+        tmem_ld32(tP + 32 * blk, u);
+        float cw[32], dcv[32], pv[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int k = c0 + 32 * blk + i;
+          float H = 0.f, dc = 0.f, P = 0.f, dS = 0.f;
+          const float wk = s_w[k];
+          const float kx = s_rh[3 * k], ky = s_rh[3 * k + 1], kz = s_rh[3 * k + 2];
+          if (k < nn && rv) {
+            const float l = t[i] * a.scale;
+            const float ww = wj * wk;
+            const float A = __expf((l + a.shift) * ww - mx) * inv;
+            const float c = hx * kx + hy * ky + hz * kz;
+            const float dP = u[i];
+            const float dLp = A * (dP * ww * c - tsum);
+            H = dP * A * c + dLp * (l + a.shift);
+            dc = dP * A * ww;
+            P = A * ww * c;
+            dS = dLp * ww * a.scale;
+          }
+          rw_ += H * wk;
+          rx += dc * kx; ry += dc * ky; rz += dc * kz;
+          cw[i] = H * wj;
+          dcv[i] = dc;
+          pv[i] = P;
+          t[i] = dS;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint4 w4;
+          w4.x = pack_bf16(pv[8 * q + 0], pv[8 * q + 1]);
+          w4.y = pack_bf16(pv[8 * q + 2], pv[8 * q + 3]);
+          w4.z = pack_bf16(pv[8 * q + 4], pv[8 * q + 5]);
+          w4.w = pack_bf16(pv[8 * q + 6], pv[8 * q + 7]);
+          sw128_store8(sC, row, c0 + 32 * blk + 8 * q, 128, w4);
+        }
+        tmem_st32(tS + 32 * blk, t);  // dS over this block's consumed S columns
+        const float sw_ = reduce_scatter32(cw);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * hx;
+        const float sx = reduce_scatter32(pv);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * hy;
+        const float sy_ = reduce_scatter32(pv);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * hz;
+        const float sz = reduce_scatter32(pv);
+        cp[blk * 32 + lane] = make_float4(sx, sy_, sz, sw_);
+      }
+      // row parts of dE/dw_j and dE/drhat_j, per half
+      reinterpret_cast<float4*>(rowp)[half * 128 + row] = make_float4(rx, ry, rz, rw_);
+    }
+    handoff();
+    // M2: dV = P^T dO -> [128,256)
+    if (issuer) mma_block(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
+    commit_and_sync(sy, issuer);
+    tmem_row64(tm + lane_off + 384 + c0, v);  // dS
+    store_row64(sC, row, c0, v);
+    handoff();
+    // M3: dQ = dS K -> [0,128) ; dK = dS^T Q -> [256,384)
+    if (issuer) {
+      mma_block(tm + 0, tC, false, 128, tB, true, 128, 128, 8, false);
+      mma_block(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
+    }
+    commit_and_sync(sy, issuer);
+    // P4: dQ -> B, dK -> A, dV -> D ; dgeo of this atom
+    tmem_row64(tm + lane_off + 0 + c0, v);
+    store_row64(sB, row, c0, v);
+    tmem_row64(tm + lane_off + 256 + c0, v);
+    store_row64(sA, row, c0, v);
+    tmem_row64(tm + lane_off + 128 + c0, v);
+    store_row64(sD, row, c0, v);
+    if (tid < 128) {
+      // key/row `tid`: row parts of both halves + column parts of the 4 quads
+      const float4* rp = reinterpret_cast<const float4*>(rowp);
+      const float4* cp = reinterpret_cast<const float4*>(colp);
+      float4 s = rp[tid];
+      const float4 s2 = rp[128 + tid];
+      s.x += s2.x; s.y += s2.y; s.z += s2.z; s.w += s2.w;
+      for (int q = 0; q < 4; ++q) {
+        const float4 c = cp[q * 128 + tid];
+        s.x += c.x; s.y += c.y; s.z += c.z; s.w += c.w;
+      }
+      if (tid < nn) {
+        float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
+        float4 cur = *dg;
+        cur.x += s.x; cur.y += s.y; cur.z += s.z; cur.w += s.w;
+        *dg = cur;
+      }
+    }
+    handoff();
+    // M4: dG = dQ Wq^T + dK Wk^T + dV Wv^T -> [384, 496)
+    if (issuer) {
+      mma_block(tm + 384, tB, false, 128, tWq, true, 128, WO_ROWS, 8, false);
+      mma_block(tm + 384, tA, false, 128, tWk, true, 128, WO_ROWS, 8, true);
+      mma_block(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
+    }
+    commit_and_sync(sy, issuer);
+    // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place
+    {
+      tmem_row64(tm + lane_off + 384 + c0, v);
+      float* dg = a.dG + (base + row) * a.m1;
+#pragma unroll
+      for (int i = 0; i < 64; i += 4) {
+        const int c = c0 + i;
+        if (c < a.m1) {
+          float4 g = *reinterpret_cast<const float4*>(dg + c);
+          g.x += v[i]; g.y += v[i + 1]; g.z += v[i + 2]; g.w += v[i + 3];
+          *reinterpret_cast<float4*>(dg + c) = g;
+        }
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+int sm_count_dev(int dev) {
+  int c = 0;
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c > 0 ? c : 1;
+}
+
+// Build the swizzled shared-memory image of one layer's weights:
+// Wq, Wk, Wv as [128 out][128 in] K-major tiles (in = M1 padded with zeros)
+// and Wo as a [112 out][128 in] K-major tile.
+std::vector<uint8_t> layer_image(const std::vector<double>& Wq, const std::vector<double>& Wk,
+                                 const std::vector<double>& Wv, const std::vector<double>& Wo, int m1, int A) {
+  std::vector<uint8_t> img(WIMG, 0);
+  auto put = [&](uint8_t* tile, int r, int c, int R, double x) {
+    __nv_bfloat16 h = __float2bfloat16((float)x);
+    memcpy(tile + sw128_offset(r, c, R), &h, 2);
+  };
+  const std::vector<double>* Ws[3] = {&Wq, &Wk, &Wv};
+  for (int t = 0; t < 3; ++t)
+    for (int f = 0; f < A; ++f)
+      for (int m = 0; m < m1; ++m) put(img.data() + t * TILE, f, m, 128, (*Ws[t])[(size_t)m * A + f]);
+  for (int m = 0; m < m1; ++m)
+    for (int f = 0; f < A; ++f) put(img.data() + 3 * TILE, m, f, WO_ROWS, Wo[(size_t)f * m1 + m]);
+  return img;
+}
+
+}  // namespace
+
+int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
+  if (m->A != 128 || m->m1 > WO_ROWS || m->m1 % 4 != 0 || m->m1 > 128) {
+    msg = "the tensor-core path needs attention width 128 and an embedding width <= 112 divisible by 4";
+    return DP_ERR_UNSUPPORTED;
+  }
+  auto get = [&](const std::string& name) -> const std::vector<double>& {
+    for (auto& kv : arrays)
+      if (kv.first == name) return kv.second;
+    static std::vector<double> empty;
+    return empty;
+  };
+  TcWeights& w = m->tcw;
+  for (int l = 0; l < m->nattn; ++l) {
+    const std::string p = "at" + std::to_string(l) + "_";
+    std::vector<uint8_t> img = layer_image(get(p + "Wq"), get(p + "Wk"), get(p + "Wv"), get(p + "Wo"), m->m1, m->A);
+    void* d = nullptr;
+    if (cudaMalloc(&d, img.size()) != cudaSuccess ||
+        cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      msg = "cudaMalloc of the BF16 weight image failed";
+      return DP_ERR_CUDA;
+    }
+    w.allocations.push_back(d);
+    w.Wqkv_t.push_back(d);
+  }
+  const int smem = std::max(F_SMEM, B_SMEM);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
+  if (optin < smem) {
+    msg = "device shared memory per block is below the tensor-core kernels' need";
+    return DP_ERR_UNSUPPORTED;
+  }
+  cudaFuncSetAttribute(k_layer_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
+  cudaFuncSetAttribute(k_layer_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
+  w.ready = true;
+  return DP_OK;
+}
+
+void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
+  Workspace& ws = m->ws;
+  const size_t rows = (size_t)cap * NP;
+  ws.tc.p[0] = a.take<__nv_bfloat16>(rows * YLD * (size_t)std::max(1, m->nattn));  // yhat per layer
+  ws.tc.p[1] = a.take<float>(rows * (size_t)std::max(1, m->nattn));                // rstd per layer
+  ws.tc.p[2] = a.take<float>((size_t)sm_count_dev(m->device) * SCRATCH_FLOATS);      // column partials
+}
+
+
+void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  const size_t rows = (size_t)n * NP;
+  const int L = m->nattn;
+  const int grid = std::min(n, sm_count_dev(m->device));
+  auto largs = [&](int l) {
+    LayerArgs la{};
+    la.Gin = ws.G[l];
+    la.Gout = ws.G[l + 1];
+    la.yhat = reinterpret_cast<__nv_bfloat16*>(ws.tc.p[0]) + (size_t)l * rows * YLD;
+    la.rstd = reinterpret_cast<float*>(ws.tc.p[1]) + (size_t)l * rows;
+    la.dG = ws.dG;
+    la.dgeo = ws.dgeo;
+    la.scratch = reinterpret_cast<float*>(ws.tc.p[2]);
+    la.rw = ws.rw;
+    la.nnei = ws.nnei;
+    la.n = n;
+    la.m1 = m->m1;
+    la.wimg = reinterpret_cast<const uint4*>(m->tcw.Wqkv_t[l]);
+    la.bqkv = m->attn[l].bqkv;
+    la.bo = m->attn[l].bo;
+    la.gamma = m->attn[l].ln_g;
+    la.beta = m->attn[l].ln_b;
+    la.scale = (float)(1.0 / std::sqrt((double)m->A));
+    la.shift = (float)m->shift;
+    la.eps = (float)m->ln_eps;
+    la.err = m->d_err;
+    return la;
+  };
+  // embedding, then the attention layers forward
+  EmbedArgs ea{};
+  ea.R = ws.R; ea.nlist = ws.nlist; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m->m1;
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
+  launch_embed_fwd(ea, m->emb, st);
+  prof_mark(m, "embed_fwd", st);
+  for (int l = 0; l < L && n > 0; ++l) {
+    k_layer_fwd_tc<<<grid, NT, F_SMEM, st>>>(largs(l));
+    note_launch();
+    prof_mark(m, "attn_fwd_tc", st);
+  }
+  run_descriptor_fitting(m, n, atype, st);
+  cudaMemsetAsync(ws.dgeo, 0, sizeof(float) * rows * 4, st);
+  for (int l = L - 1; l >= 0 && n > 0; --l) {
+    k_layer_bwd_tc<<<grid, NT, B_SMEM, st>>>(largs(l));
+    note_launch();
+    prof_mark(m, "attn_bwd_tc", st);
+  }
+  ea.dG0 = ws.dG;
+  ea.dR = ws.dR;
+  launch_embed_bwd(ea, m->emb, st);
+  prof_mark(m, "embed_bwd", st);
+}
+
 void tc_free_weights(dp_model* m) {
   for (void* p : m->tcw.allocations) cudaFree(p);
   m->tcw.allocations.clear();
+  m->tcw.Wqkv_t.clear();
+  m->tcw.ready = false;
 }
 
 }  // namespace dpa1

@@ -1,0 +1,109 @@
+"""Parity of the BF16 tensor-core path (tcgen05 attention layers) with the
+FP64 oracle: force RMSE <= 5e-3 eV/A and per-atom energy <= 1e-3 eV."""
+
+import numpy as np
+import pytest
+
+import synth
+import oracle
+from oracle import energy_force_virial
+
+from gpu_helpers import weight_file, force_rmse, BF16_FORCE_RMSE, BF16_ATOM_ENERGY
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2604_07276_gb300 as p
+
+    return p
+
+
+@pytest.fixture(scope="module")
+def bf16_model(lib, default_model):
+    cfg, w, _ = default_model
+    m = lib.DPA1(weight_file(cfg, w, "default"), precision="bf16")
+    yield m
+    m.close()
+
+
+@pytest.fixture(scope="module")
+def bf16_rich(lib, rich_model):
+    cfg, w, _ = rich_model
+    m = lib.DPA1(weight_file(cfg, w, "rich"), precision="bf16")
+    yield m
+    m.close()
+
+
+def _check(m, om, coord, atype, box):
+    E, F, W, e = m.compute(coord, box, atype, atom_energy=True)
+    rE, re, rF, rW = energy_force_virial(om, coord, box, atype)
+    frmse = force_rmse(F, rF)
+    emax = np.abs(e - re).max() if len(e) else 0.0
+    assert frmse <= BF16_FORCE_RMSE, frmse
+    assert emax <= BF16_ATOM_ENERGY, emax
+    assert np.abs(W - rW).max() <= 5e-3 * max(1.0, np.abs(rW).max())
+    return frmse, emax
+
+
+def test_bf16_water(bf16_model, default_model, water):
+    cfg, w, om = default_model
+    coord, atype, box = water
+    _check(bf16_model, om, coord, atype, box)
+
+
+def test_bf16_rich_weights(bf16_rich, rich_model, water):
+    cfg, w, om = rich_model
+    coord, atype, box = water
+    _check(bf16_rich, om, coord, atype, box)
+
+
+def test_bf16_lattice_ragged(bf16_model, default_model):
+    cfg, w, om = default_model
+    coord, atype, box = synth.lattice_system(1123, seed=31)
+    _check(bf16_model, om, coord, atype, box)
+
+
+def test_bf16_edge_cases(bf16_model, default_model):
+    cfg, w, om = default_model
+    box = np.array([30.0, 30.0, 30.0])
+    E, F, W, e = bf16_model.compute(np.zeros((0, 3)), box, np.zeros(0, np.int32), atom_energy=True)
+    assert E == 0.0 and F.shape == (0, 3)
+    for coord, atype in ((np.array([[3.0, 4.0, 5.0]]), np.array([2], np.int32)),
+                         (np.array([[1.0, 1.0, 1.0], [15.0, 15.0, 15.0]]), np.array([0, 4], np.int32)),
+                         (np.array([[10.0, 10.0, 10.0], [11.2, 10.3, 9.9], [20.0, 20.0, 20.0], [21.0, 20.2, 20.0],
+                                    [20.1, 21.1, 19.5]]), np.array([3, 0, 1, 2, 3], np.int32))):
+        _check(bf16_model, om, coord, atype, box)
+
+
+def test_bf16_deterministic(bf16_model, water):
+    coord, atype, box = water
+    a = bf16_model.compute(coord, box, atype, atom_energy=True)
+    b = bf16_model.compute(coord, box, atype, atom_energy=True)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_bf16_full_size_sampled(bf16_model, default_model):
+    cfg, w, om = default_model
+    coord, atype, box = synth.lattice_system(15668, seed=1)
+    E, F, W, e = bf16_model.compute(coord, box, atype, atom_energy=True)
+    rng = np.random.default_rng(5)
+    atoms = rng.choice(len(coord), size=8, replace=False)
+    rF = oracle.forces_on(om, coord, box, atype, atoms)
+    assert force_rmse(F[atoms], rF) <= BF16_FORCE_RMSE
+    centres = rng.choice(len(coord), size=32, replace=False)
+    _, re, _, _ = energy_force_virial(om, coord, box, atype, centres=centres)
+    assert np.abs(e[centres] - re).max() <= BF16_ATOM_ENERGY
+    assert np.abs(F.sum(axis=0)).max() < 1e-3
+
+
+def test_bf16_matches_fp32_path(lib, bf16_model, default_model):
+    cfg, w, _ = default_model
+    m32 = lib.DPA1(weight_file(cfg, w, "default"), precision="fp32")
+    coord, atype, box = synth.lattice_system(700, seed=3)
+    _, F16, _, e16 = bf16_model.compute(coord, box, atype, atom_energy=True)
+    _, F32, _, e32 = m32.compute(coord, box, atype, atom_energy=True)
+    m32.close()
+    assert force_rmse(F16, F32) <= BF16_FORCE_RMSE
+    assert np.abs(e16 - e32).max() <= BF16_ATOM_ENERGY
