@@ -55,8 +55,10 @@ enum dp_status {
 };
 
 enum dp_precision {
-  DP_PREC_FP32 = 0, /* every matrix product in FP32 SIMT arithmetic */
-  DP_PREC_BF16 = 1  /* network matrix products on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+  DP_PREC_FP32 = 0,  /* every matrix product in FP32 SIMT arithmetic */
+  DP_PREC_BF16 = 1,  /* attention-layer products on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+  DP_PREC_FP16X = 2  /* as DP_PREC_BF16 with FP16 operands and two-term (hi + lo) splits of the layer
+                        input and of the attention weights; FP32 accumulation */
 };
 
 /* Load a model.
@@ -67,7 +69,7 @@ enum dp_precision {
  *   rcut, rcut_smth, sel : must equal the file's values (Sec. II-C: the
  *                  cutoff of the full neighbour list and its cap), else
  *                  DP_ERR_ARG.  Pass a negative value to accept the file's.
- *   precision    : DP_PREC_FP32 or DP_PREC_BF16.
+ *   precision    : DP_PREC_FP32, DP_PREC_BF16 or DP_PREC_FP16X.
  *   device       : CUDA device ordinal; the model's memory lives there.
  * On success *out is a new model; release it with dp_free. */
 DP_API int dp_init(dp_model** out, const char* weights_path, const char* const* type_map, int ntypes,

@@ -276,7 +276,7 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.energy = a.take<double>(1);
     ws.atom_energy = a.take<double>(cap);
     ws.atype = a.take<int>(cap);
-    if (m->precision == DP_PREC_BF16) tc_plan_buffers(m, a, cap);
+    if (m->precision != DP_PREC_FP32) tc_plan_buffers(m, a, cap);
   };
   Arena probe;
   plan(probe);
@@ -443,7 +443,7 @@ int run_device(dp_model* m, int n, const double* coord, const double* box, const
   ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv; ea.w64 = ws.w64;
   launch_env(ea, st);
   prof_mark(m, "env", st);
-  if (m->precision == DP_PREC_BF16)
+  if (m->precision != DP_PREC_FP32)
     tc_run_network(m, n, atype, st);
   else
     run_network_f32(m, n, atype, st);
@@ -503,7 +503,7 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
   g_last_error.clear();
   if (!out) return fail(DP_ERR_ARG, "out is null");
   *out = nullptr;
-  if (precision != DP_PREC_FP32 && precision != DP_PREC_BF16) return fail(DP_ERR_ARG, "unknown precision");
+  if (precision < DP_PREC_FP32 || precision > DP_PREC_FP16X) return fail(DP_ERR_ARG, "unknown precision");
   HostWeights w;
   int rc = read_weights(weights_path, w, false);
   if (rc != DP_OK) return rc;
@@ -620,7 +620,7 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     if ((rc = dev_upload(m, &m->w_out, ws)) != DP_OK) return fail_free(rc);
     m->b_out = (float)((*w.get("fit_b" + std::to_string(m->nfit)))[0] * m->out_scale);
   }
-  if (precision == DP_PREC_BF16) {
+  if (precision != DP_PREC_FP32) {
     std::string msg;
     if ((rc = tc_init_weights(m, w.arrays, msg)) != DP_OK) return fail_free(fail(rc, msg));
   }
@@ -648,9 +648,9 @@ int dp_reserve(dp_model* m, int max_atoms) {
 
 int dp_set_precision(dp_model* m, int precision) {
   if (check_model(m)) return DP_ERR_ARG;
-  if (precision != DP_PREC_FP32 && precision != DP_PREC_BF16) return fail(DP_ERR_ARG, "unknown precision");
+  if (precision < DP_PREC_FP32 || precision > DP_PREC_FP16X) return fail(DP_ERR_ARG, "unknown precision");
   if (precision == m->precision) return DP_OK;
-  if (precision == DP_PREC_BF16 && !m->tcw.ready)
+  if (precision != DP_PREC_FP32 && !m->tcw.ready)
     return fail(DP_ERR_UNSUPPORTED, "model was loaded without the BF16 weights; reload with DP_PREC_BF16");
   CUDA_TRY(cudaSetDevice(m->device));
   CUDA_TRY(cudaDeviceSynchronize());

@@ -1,5 +1,8 @@
-// Tensor-core (tcgen05, BF16 operands, FP32 accumulation in TMEM) path of the
-// gated attention layers (stage a6) and their adjoint (stage a12).
+// Tensor-core (tcgen05, 16-bit operands, FP32 accumulation in TMEM) path of
+// the gated attention layers (stage a6) and their adjoint (stage a12).
+// Two operand modes: plain BF16, and FP16 with two-term (hi + lo) splits of
+// the layer input G and of the attention weights P, whose rounding the
+// LayerNorm of weakly attended rows amplifies.
 //
 // One persistent CTA per SM walks over centre atoms; an atom is one 128-row
 // tile (its neighbour slots).  Every product of a layer runs on the tensor
@@ -89,15 +92,21 @@ __device__ __forceinline__ void copy_image(uint8_t* dst, const uint4* src, int b
   for (int i = threadIdx.x; i < bytes / 16; i += NT) d[i] = src[i];
 }
 
-// Store 64 FP32 values (cols c0..c0+63 of row r) as bf16 into an SW128 tile.
+// Store 64 FP32 values (cols c0..c0+63 of row r) as the 16-bit operand type
+// into an SW128 tile; LO = true stores the rounding residue v - round16(v)
+// instead (the low part of a two-term split).
+template <bool F16, bool LO = false>
 __device__ __forceinline__ void store_row64(uint8_t* tile, int r, int c0, const float* v) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = LO ? v[8 * q + i] - round16<F16>(v[8 * q + i]) : v[8 * q + i];
     uint4 u;
-    u.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-    u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-    u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-    u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+    u.x = pack16<F16>(x[0], x[1]);
+    u.y = pack16<F16>(x[2], x[3]);
+    u.z = pack16<F16>(x[4], x[5]);
+    u.w = pack16<F16>(x[6], x[7]);
     sw128_store8(tile, r, c0 + 8 * q, 128, u);
   }
 }
@@ -120,9 +129,10 @@ __device__ __forceinline__ void tmem_row64(uint32_t taddr, float* v) {
 }
 
 // Issue D = sum over K-steps of A * B for one 128 x N block.
+template <bool F16>
 __device__ __forceinline__ void mma_block(uint32_t d, uint32_t a, bool a_mn, int a_rows, uint32_t b, bool b_mn,
                                           int b_rows, int N, int ksteps, bool accumulate_first) {
-  const uint32_t id = idesc_bf16(128, N, a_mn, b_mn);
+  const uint32_t id = idesc_16(128, N, a_mn, b_mn, F16);
   for (int s = 0; s < ksteps; ++s) {
     const uint64_t ad = a_mn ? mnmajor_desc(a, s, a_rows) : kmajor_desc(a, s, a_rows);
     const uint64_t bd = b_mn ? mnmajor_desc(b, s, b_rows) : kmajor_desc(b, s, b_rows);
@@ -170,6 +180,9 @@ constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_W = 3 * TILE
 constexpr int F_SMALL = 3 * TILE + WIMG;
 constexpr int F_SMEM = F_SMALL + 512 + 1536 + 1024 + 64;
 
+// F16 = true: FP16 operands with two-term splits of G (in [Q K V] = G Wqkv)
+// and of P (in O = P V); F16 = false: plain BF16 operands.
+template <bool F16>
 __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {  // tiles need 1024-byte alignment
@@ -222,13 +235,19 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
     float v[64];
     // G_l (FP32) -> bf16 slot A
     load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
-    store_row64(sA, row, c0, v);
+    store_row64<F16>(sA, row, c0, v);
+    if (F16) store_row64<F16, true>(sB, row, c0, v);
     handoff();
-    // [Q K V] = G Wqkv
+    // [Q K V] = G Wqkv (+ G_lo Wqkv)
     if (issuer) {
-      mma_block(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
-      mma_block(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
-      mma_block(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
+      mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
+      mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
+      mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
+      if (F16) {
+        mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
+        mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
+        mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
+      }
     }
     commit_and_sync(sy, issuer);
     // Q -> A, K -> B, V -> C (with biases)
@@ -238,11 +257,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
       const float* b = a.bqkv + which * 128 + c0;
 #pragma unroll
       for (int i = 0; i < 64; ++i) v[i] += b[i];
-      store_row64(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
+      store_row64<F16>(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
     }
     handoff();
     // S = Q K^T
-    if (issuer) mma_block(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
+    if (issuer) mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
     // smooth softmax and gate: P -> slot B
     tmem_row64(tm + lane_off + 384 + c0, v);
@@ -274,17 +293,21 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
         const float c = hx * s_rh[3 * k] + hy * s_rh[3 * k + 1] + hz * s_rh[3 * k + 2];
         v[i] = v[i] * inv * (wj * s_w[k]) * c;
       }
-      store_row64(sB, row, c0, v);
+      store_row64<F16>(sB, row, c0, v);
+      if (F16) store_row64<F16, true>(sA, row, c0, v);  // Q is dead after S
     }
     handoff();
-    // O = P V  (V as an MN-major operand of slot C)
-    if (issuer) mma_block(tm + 0, tB, false, 128, tC, true, 128, 128, 8, false);
+    // O = P V (+ P_lo V)  (V as an MN-major operand of slot C)
+    if (issuer) {
+      mma_block<F16>(tm + 0, tB, false, 128, tC, true, 128, 128, 8, false);
+      if (F16) mma_block<F16>(tm + 0, tA, false, 128, tC, true, 128, 128, 8, true);
+    }
     commit_and_sync(sy, issuer);
     tmem_row64(tm + lane_off + 0 + c0, v);
-    store_row64(sA, row, c0, v);
+    store_row64<F16>(sA, row, c0, v);
     handoff();
     // Y = O Wo
-    if (issuer) mma_block(tm + 128, tA, false, 128, tWo, false, WO_ROWS, WO_ROWS, 8, false);
+    if (issuer) mma_block<F16>(tm + 128, tA, false, 128, tWo, false, WO_ROWS, WO_ROWS, 8, false);
     commit_and_sync(sy, issuer);
     // LayerNorm, residual
     {
@@ -350,6 +373,7 @@ constexpr int B_SMALL = 4 * TILE + 3 * TILE;
 constexpr int B_SMEM = B_SMALL + 512 + 1536 + 64;
 constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 2 * 128 * 4;  // per CTA
 
+template <bool F16>
 __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {
@@ -405,7 +429,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
     float v[64];
     // P0: G_l -> A, dY = LayerNorm adjoint of dZ -> C, Wo -> D
     load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
-    store_row64(sA, row, c0, v);
+    store_row64<F16>(sA, row, c0, v);
     copy_image(sD, reinterpret_cast<const uint4*>(wo_img), WO_TILE);
     {
       float* xch = reinterpret_cast<float*>(sB);
@@ -431,15 +455,24 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
       const float rs = rv ? a.rstd[base + row] : 0.f;
 #pragma unroll
       for (int i = 0; i < 64; ++i) v[i] = rv ? rs * (v[i] - s1 - yv[i] * s2) : 0.f;
-      store_row64(sC, row, c0, v);
+      store_row64<F16>(sC, row, c0, v);
+    }
+    if (F16) {  // the exchange in slot B is finished (barrier inside pair_sum)
+      load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
+      store_row64<F16, true>(sB, row, c0, v);
     }
     handoff();
-    // M0: [Q K V] = G Wqkv ; dO = dY Wo^T (Wo tile as MN-major)
+    // M0: [Q K V] = G Wqkv (+ G_lo Wqkv) ; dO = dY Wo^T (Wo tile as MN-major)
     if (issuer) {
-      mma_block(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
-      mma_block(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
-      mma_block(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
-      mma_block(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+      mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
+      mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
+      mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
+      if (F16) {
+        mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
+        mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
+        mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
+      }
+      mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
     }
     commit_and_sync(sy, issuer);
     // P1: Q -> A, K -> B, V -> C, dO -> D
@@ -451,13 +484,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] += b[i];
       }
-      store_row64(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
+      store_row64<F16>(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
     }
     handoff();
     // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
     if (issuer) {
-      mma_block(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
-      mma_block(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
+      mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
     // P2: softmax and its adjoint in 32-key passes that reload S and dP from
@@ -543,10 +576,10 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           uint4 w4;
-          w4.x = pack_bf16(pv[8 * q + 0], pv[8 * q + 1]);
-          w4.y = pack_bf16(pv[8 * q + 2], pv[8 * q + 3]);
-          w4.z = pack_bf16(pv[8 * q + 4], pv[8 * q + 5]);
-          w4.w = pack_bf16(pv[8 * q + 6], pv[8 * q + 7]);
+          w4.x = pack16<F16>(pv[8 * q + 0], pv[8 * q + 1]);
+          w4.y = pack16<F16>(pv[8 * q + 2], pv[8 * q + 3]);
+          w4.z = pack16<F16>(pv[8 * q + 4], pv[8 * q + 5]);
+          w4.w = pack16<F16>(pv[8 * q + 6], pv[8 * q + 7]);
           sw128_store8(sC, row, c0 + 32 * blk + 8 * q, 128, w4);
         }
         tmem_st32(tS + 32 * blk, t);  // dS over this block's consumed S columns
@@ -567,24 +600,24 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
     }
     handoff();
     // M2: dV = P^T dO -> [128,256)
-    if (issuer) mma_block(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
+    if (issuer) mma_block<F16>(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
     tmem_row64(tm + lane_off + 384 + c0, v);  // dS
-    store_row64(sC, row, c0, v);
+    store_row64<F16>(sC, row, c0, v);
     handoff();
     // M3: dQ = dS K -> [0,128) ; dK = dS^T Q -> [256,384)
     if (issuer) {
-      mma_block(tm + 0, tC, false, 128, tB, true, 128, 128, 8, false);
-      mma_block(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
     // P4: dQ -> B, dK -> A, dV -> D ; dgeo of this atom
     tmem_row64(tm + lane_off + 0 + c0, v);
-    store_row64(sB, row, c0, v);
+    store_row64<F16>(sB, row, c0, v);
     tmem_row64(tm + lane_off + 256 + c0, v);
-    store_row64(sA, row, c0, v);
+    store_row64<F16>(sA, row, c0, v);
     tmem_row64(tm + lane_off + 128 + c0, v);
-    store_row64(sD, row, c0, v);
+    store_row64<F16>(sD, row, c0, v);
     if (tid < 128) {
       // key/row `tid`: row parts of both halves + column parts of the 4 quads
       const float4* rp = reinterpret_cast<const float4*>(rowp);
@@ -606,9 +639,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
     handoff();
     // M4: dG = dQ Wq^T + dK Wk^T + dV Wv^T -> [384, 496)
     if (issuer) {
-      mma_block(tm + 384, tB, false, 128, tWq, true, 128, WO_ROWS, 8, false);
-      mma_block(tm + 384, tA, false, 128, tWk, true, 128, WO_ROWS, 8, true);
-      mma_block(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
+      mma_block<F16>(tm + 384, tB, false, 128, tWq, true, 128, WO_ROWS, 8, false);
+      mma_block<F16>(tm + 384, tA, false, 128, tWk, true, 128, WO_ROWS, 8, true);
+      mma_block<F16>(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
     }
     commit_and_sync(sy, issuer);
     // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place
@@ -644,11 +677,17 @@ int sm_count_dev(int dev) {
 // Wq, Wk, Wv as [128 out][128 in] K-major tiles (in = M1 padded with zeros)
 // and Wo as a [112 out][128 in] K-major tile.
 std::vector<uint8_t> layer_image(const std::vector<double>& Wq, const std::vector<double>& Wk,
-                                 const std::vector<double>& Wv, const std::vector<double>& Wo, int m1, int A) {
+                                 const std::vector<double>& Wv, const std::vector<double>& Wo, int m1, int A,
+                                 bool f16) {
   std::vector<uint8_t> img(WIMG, 0);
   auto put = [&](uint8_t* tile, int r, int c, int R, double x) {
-    __nv_bfloat16 h = __float2bfloat16((float)x);
-    memcpy(tile + sw128_offset(r, c, R), &h, 2);
+    if (f16) {
+      __half h = __float2half((float)x);
+      memcpy(tile + sw128_offset(r, c, R), &h, 2);
+    } else {
+      __nv_bfloat16 h = __float2bfloat16((float)x);
+      memcpy(tile + sw128_offset(r, c, R), &h, 2);
+    }
   };
   const std::vector<double>* Ws[3] = {&Wq, &Wk, &Wv};
   for (int t = 0; t < 3; ++t)
@@ -673,18 +712,20 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
     return empty;
   };
   TcWeights& w = m->tcw;
-  for (int l = 0; l < m->nattn; ++l) {
-    const std::string p = "at" + std::to_string(l) + "_";
-    std::vector<uint8_t> img = layer_image(get(p + "Wq"), get(p + "Wk"), get(p + "Wv"), get(p + "Wo"), m->m1, m->A);
-    void* d = nullptr;
-    if (cudaMalloc(&d, img.size()) != cudaSuccess ||
-        cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-      msg = "cudaMalloc of the BF16 weight image failed";
-      return DP_ERR_CUDA;
+  for (int f16 = 0; f16 < 2; ++f16)
+    for (int l = 0; l < m->nattn; ++l) {
+      const std::string p = "at" + std::to_string(l) + "_";
+      std::vector<uint8_t> img =
+          layer_image(get(p + "Wq"), get(p + "Wk"), get(p + "Wv"), get(p + "Wo"), m->m1, m->A, f16 != 0);
+      void* d = nullptr;
+      if (cudaMalloc(&d, img.size()) != cudaSuccess ||
+          cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        msg = "cudaMalloc of the 16-bit weight image failed";
+        return DP_ERR_CUDA;
+      }
+      w.allocations.push_back(d);
+      (f16 ? w.Wo_t : w.Wqkv_t).push_back(d);  // images: [0] bf16 layers, [1] fp16 layers
     }
-    w.allocations.push_back(d);
-    w.Wqkv_t.push_back(d);
-  }
   const int smem = std::max(F_SMEM, B_SMEM);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
@@ -692,8 +733,10 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
     msg = "device shared memory per block is below the tensor-core kernels' need";
     return DP_ERR_UNSUPPORTED;
   }
-  cudaFuncSetAttribute(k_layer_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
-  cudaFuncSetAttribute(k_layer_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
+  cudaFuncSetAttribute(k_layer_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
+  cudaFuncSetAttribute(k_layer_bwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
+  cudaFuncSetAttribute(k_layer_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
+  cudaFuncSetAttribute(k_layer_bwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
   w.ready = true;
   return DP_OK;
 }
@@ -712,6 +755,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   const size_t rows = (size_t)n * NP;
   const int L = m->nattn;
   const int grid = std::min(n, sm_count_dev(m->device));
+  const bool f16 = m->precision == DP_PREC_FP16X;
   auto largs = [&](int l) {
     LayerArgs la{};
     la.Gin = ws.G[l];
@@ -725,7 +769,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.nnei = ws.nnei;
     la.n = n;
     la.m1 = m->m1;
-    la.wimg = reinterpret_cast<const uint4*>(m->tcw.Wqkv_t[l]);
+    la.wimg = reinterpret_cast<const uint4*>(f16 ? m->tcw.Wo_t[l] : m->tcw.Wqkv_t[l]);
     la.bqkv = m->attn[l].bqkv;
     la.bo = m->attn[l].bo;
     la.gamma = m->attn[l].ln_g;
@@ -743,14 +787,20 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   launch_embed_fwd(ea, m->emb, st);
   prof_mark(m, "embed_fwd", st);
   for (int l = 0; l < L && n > 0; ++l) {
-    k_layer_fwd_tc<<<grid, NT, F_SMEM, st>>>(largs(l));
+    if (f16)
+      k_layer_fwd_tc<true><<<grid, NT, F_SMEM, st>>>(largs(l));
+    else
+      k_layer_fwd_tc<false><<<grid, NT, F_SMEM, st>>>(largs(l));
     note_launch();
     prof_mark(m, "attn_fwd_tc", st);
   }
   run_descriptor_fitting(m, n, atype, st);
   cudaMemsetAsync(ws.dgeo, 0, sizeof(float) * rows * 4, st);
   for (int l = L - 1; l >= 0 && n > 0; --l) {
-    k_layer_bwd_tc<<<grid, NT, B_SMEM, st>>>(largs(l));
+    if (f16)
+      k_layer_bwd_tc<true><<<grid, NT, B_SMEM, st>>>(largs(l));
+    else
+      k_layer_bwd_tc<false><<<grid, NT, B_SMEM, st>>>(largs(l));
     note_launch();
     prof_mark(m, "attn_bwd_tc", st);
   }
@@ -764,6 +814,7 @@ void tc_free_weights(dp_model* m) {
   for (void* p : m->tcw.allocations) cudaFree(p);
   m->tcw.allocations.clear();
   m->tcw.Wqkv_t.clear();
+  m->tcw.Wo_t.clear();
   m->tcw.ready = false;
 }
 

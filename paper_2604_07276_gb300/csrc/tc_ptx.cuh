@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "common.cuh"
@@ -38,6 +39,20 @@ __device__ __forceinline__ void sw128_store8(uint8_t* tile, int r, int c, int R,
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+// Pack two values as the 16-bit operand type (F16 = true: fp16, else bf16).
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float a, float b) {
+  return F16 ? pack_f16(a, b) : pack_bf16(a, b);
+}
+// Value of x after rounding to the 16-bit operand type.
+template <bool F16>
+__device__ __forceinline__ float round16(float x) {
+  return F16 ? __half2float(__float2half_rn(x)) : __bfloat162float(__float2bfloat16_rn(x));
 }
 
 // ---------------------------------------------------------------- mbarrier
@@ -106,11 +121,15 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
   d |= (uint64_t)2 << 61;
   return d;
 }
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
-// operand majorness (false = K-major), N and M.
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B both BF16
+// (f16 = false) or both FP16 (f16 = true), operand majorness (false =
+// K-major), N and M.
+__host__ __device__ constexpr uint32_t idesc_16(int M, int N, bool a_mn, bool b_mn, bool f16) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  return idesc_16(M, N, a_mn, b_mn, false);
 }
 
 // Descriptor of K-step s (16 bf16 of K) of an operand stored as an SW128
