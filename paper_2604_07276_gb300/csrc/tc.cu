@@ -1,8 +1,8 @@
 // Tensor-core (tcgen05, 16-bit operands, FP32 accumulation in TMEM) path of
 // the gated attention layers (stage a6) and their adjoint (stage a12).
 // Two operand modes: plain BF16, and FP16 with two-term (hi + lo) splits of
-// the layer input G and of the attention weights P, whose rounding the
-// LayerNorm of weakly attended rows amplifies.
+// the layer input G, the attention weights P and the values V in the forward
+// products, whose rounding the LayerNorm of weakly attended rows amplifies.
 //
 // One persistent CTA per SM walks over centre atoms; an atom is one 128-row
 // tile (its neighbour slots).  Every product of a layer runs on the tensor
@@ -174,14 +174,15 @@ __device__ __forceinline__ float reduce_scatter32(float* v) {
 }
 
 // ------------------------------------------------------------------ forward
-// Shared memory: slot A [0,32K), slot B, slot C, Wq, Wk, Wv, Wo (28K), then
-// w[128], rhat[128][3], the half-row exchange and the barrier.
-constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_W = 3 * TILE;
-constexpr int F_SMALL = 3 * TILE + WIMG;
-constexpr int F_SMEM = F_SMALL + 512 + 1536 + 1024 + 64;
+// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K,224K), then w[128],
+// rhat[128][3] and the barrier.  Wo is streamed per atom into a free slot;
+// the half-row exchange borrows the first 1 KB of a slot that is free.
+constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_SLOT_D = 3 * TILE, F_W = 4 * TILE;
+constexpr int F_SMALL = 7 * TILE;
+constexpr int F_SMEM = F_SMALL + 512 + 1536 + 64;
 
-// F16 = true: FP16 operands with two-term splits of G (in [Q K V] = G Wqkv)
-// and of P (in O = P V); F16 = false: plain BF16 operands.
+// F16 = true: FP16 operands with two-term splits of G (in [Q K V] = G Wqkv),
+// of P and of V (in O = P V); F16 = false: plain BF16 operands.
 template <bool F16>
 __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -192,14 +193,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
   uint8_t* sA = sm + F_SLOT_A;
   uint8_t* sB = sm + F_SLOT_B;
   uint8_t* sC = sm + F_SLOT_C;
+  uint8_t* sD = sm + F_SLOT_D;
   uint8_t* sWq = sm + F_W;
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
-  uint8_t* sWo = sWv + TILE;
   float* s_w = reinterpret_cast<float*>(sm + F_SMALL);
-  float* s_rh = s_w + 128;          // [128][3]
-  float* xch = s_rh + 384;          // [2][128]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(xch + 256);
+  float* s_rh = s_w + 128;  // [128][3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_rh + 384);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
   const int c0 = half * 64;
   const bool issuer = tid == 0;
 
-  copy_image(sWq, a.wimg, WIMG);
+  copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -217,8 +217,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
   handoff();
   const uint32_t tm = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-  const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC);
-  const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv), tWo = smem_u32(sWo);
+  const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
+  const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
+  const uint4* wo_img = a.wimg + 3 * TILE / 16;
   Sync sy{bar, 0u, a.err};
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
       s_rh[3 * tid + 2] = v ? r.z : 0.f;
     }
     float v[64];
-    // G_l (FP32) -> bf16 slot A
+    // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B)
     load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
     store_row64<F16>(sA, row, c0, v);
     if (F16) store_row64<F16, true>(sB, row, c0, v);
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
       }
     }
     commit_and_sync(sy, issuer);
-    // Q -> A, K -> B, V -> C (with biases)
+    // Q -> A, K -> B, V -> C (+ V_lo -> D), with biases
 #pragma unroll 1
     for (int which = 0; which < 3; ++which) {
       tmem_row64(tm + lane_off + which * 128 + c0, v);
@@ -258,14 +259,16 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
 #pragma unroll
       for (int i = 0; i < 64; ++i) v[i] += b[i];
       store_row64<F16>(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
+      if (F16 && which == 2) store_row64<F16, true>(sD, row, c0, v);
     }
     handoff();
     // S = Q K^T
     if (issuer) mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
-    // smooth softmax and gate: P -> slot B
+    // smooth softmax and gate: P -> slot B (+ P_lo -> slot A); Q and K are dead
     tmem_row64(tm + lane_off + 384 + c0, v);
     {
+      float* xch = reinterpret_cast<float*>(sA);
       const bool rv = row < nn;
       const float wj = s_w[row];
       float mx = -INFINITY;
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
         v[i] = e;
         sum += e;
       }
-      sum = pair_sum(xch, half, row, sum);
+      sum = pair_sum(xch, half, row, sum);  // ends with a barrier: slot A is free
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
       const float hx = s_rh[3 * row], hy = s_rh[3 * row + 1], hz = s_rh[3 * row + 2];
 #pragma unroll
@@ -294,23 +297,35 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
         v[i] = v[i] * inv * (wj * s_w[k]) * c;
       }
       store_row64<F16>(sB, row, c0, v);
-      if (F16) store_row64<F16, true>(sA, row, c0, v);  // Q is dead after S
+      if (F16) store_row64<F16, true>(sA, row, c0, v);
     }
     handoff();
-    // O = P V (+ P_lo V)  (V as an MN-major operand of slot C)
+    // O = P V (+ P_lo V + P V_lo)  (V as an MN-major operand)
     if (issuer) {
       mma_block<F16>(tm + 0, tB, false, 128, tC, true, 128, 128, 8, false);
-      if (F16) mma_block<F16>(tm + 0, tA, false, 128, tC, true, 128, 128, 8, true);
+      if (F16) {
+        mma_block<F16>(tm + 0, tA, false, 128, tC, true, 128, 128, 8, true);
+        mma_block<F16>(tm + 0, tB, false, 128, tD, true, 128, 128, 8, true);
+      }
     }
     commit_and_sync(sy, issuer);
-    tmem_row64(tm + lane_off + 0 + c0, v);
-    store_row64<F16>(sA, row, c0, v);
+    {
+      // fetch this atom's copy of Wo while O leaves TMEM; O -> A, Wo -> D
+      uint4 wr[WO_TILE / 16 / NT];
+#pragma unroll
+      for (int q = 0; q < WO_TILE / 16 / NT; ++q) wr[q] = wo_img[q * NT + tid];
+      tmem_row64(tm + lane_off + 0 + c0, v);
+      store_row64<F16>(sA, row, c0, v);
+#pragma unroll
+      for (int q = 0; q < WO_TILE / 16 / NT; ++q) reinterpret_cast<uint4*>(sD)[q * NT + tid] = wr[q];
+    }
     handoff();
     // Y = O Wo
-    if (issuer) mma_block<F16>(tm + 128, tA, false, 128, tWo, false, WO_ROWS, WO_ROWS, 8, false);
+    if (issuer) mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, 8, false);
     commit_and_sync(sy, issuer);
     // LayerNorm, residual
     {
+      float* xch = reinterpret_cast<float*>(sB);  // P is dead
       tmem_row64(tm + lane_off + 128 + c0, v);
       float s1 = 0.f;
 #pragma unroll
