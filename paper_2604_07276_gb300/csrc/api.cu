@@ -384,7 +384,7 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
   // a5: embedding
   EmbedArgs ea{};
-  ea.R = ws.R; ea.nlist = ws.nlist; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
+  ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
   ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
   launch_embed_fwd(ea, m->emb, st);
   prof_mark(m, "embed_fwd", st);

@@ -86,6 +86,7 @@ void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bia
 struct EmbedArgs {
   const float* R;
   const int* nlist;
+  const int* nnei;
   const int* atype;
   int n, ntypes, m1;
   const float* w;   // packed embedding-net weights (W0 b0 W1 b1 W2 b2)

@@ -87,146 +87,198 @@ void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bia
 // ------------------------------------------------------------ embedding net
 // G0_ij = net_s(R_ij,0) * (1 + Gt[t_i, t_j]); net_s = 1 -> E0 -> E1 -> E2 with
 // tanh and the residual rule (keep width: x + f; double: [x, x] + f).
+// A CTA takes 64 neighbour rows of one atom; activations of the block live in
+// shared memory and every layer is a small tiled product over the block, so
+// global rows are read and written whole (coalesced).
 template <int E0, int E1, int E2>
-struct EmbedLayout {
+struct EmbedLayout {  // packed global weights: W0 b0 W1 b1 W2 b2
   static constexpr int W0 = 0, B0 = E0, W1 = 2 * E0, B1 = W1 + E0 * E1, W2 = B1 + E1, B2 = W2 + E1 * E2,
                        TOTAL = B2 + E2;
 };
 
+constexpr int EROWS = 64;  // neighbour rows per CTA
+constexpr int ETHREADS = 256;
+
+template <int IN, int OUT>
+__device__ __forceinline__ float skip_in(const float* x, int o) {
+  return OUT == IN ? x[o] : (OUT == 2 * IN ? x[o % IN] : 0.f);
+}
+
+// Shared layout (floats); W2 is kept with row stride E2 + 1 (bank-conflict
+// free for both of its access patterns), activations with row stride n + 1.
 template <int E0, int E1, int E2>
-__global__ void __launch_bounds__(128) k_embed_fwd(EmbedArgs a) {
+struct EmbedSmem {
+  static constexpr int P2 = E2 + 1;
+  static constexpr int W0 = 0, B0 = E0, W1 = 2 * E0, B1 = W1 + E0 * E1, W2 = B1 + E1, B2 = W2 + E1 * P2,
+                       X = B2 + E2, H1 = X + EROWS, H2 = H1 + EROWS * (E0 + 1), Z = H2 + EROWS * (E1 + 1),
+                       DH2 = Z + EROWS * (E2 + 1), DZ2 = DH2 + EROWS * (E1 + 1), DH1 = DZ2 + EROWS * (E1 + 1),
+                       TOTAL = DH1 + EROWS * (E0 + 1);
+};
+
+template <int E0, int E1, int E2>
+__device__ __forceinline__ void embed_load(float* sm, const EmbedArgs& a, size_t base, int cnt) {
   using Lw = EmbedLayout<E0, E1, E2>;
-  extern __shared__ float sw[];
-  for (int t = threadIdx.x; t < Lw::TOTAL; t += blockDim.x) sw[t] = a.w[t];
+  using S = EmbedSmem<E0, E1, E2>;
+  for (int t = threadIdx.x; t < Lw::W2; t += ETHREADS) sm[t] = a.w[t];  // W0 b0 W1 b1 share offsets
+  for (int t = threadIdx.x; t < E1 * E2; t += ETHREADS) sm[S::W2 + (t / E2) * S::P2 + t % E2] = a.w[Lw::W2 + t];
+  for (int t = threadIdx.x; t < E2; t += ETHREADS) sm[S::B2 + t] = a.w[Lw::B2 + t];
+  for (int r = threadIdx.x; r < EROWS; r += ETHREADS) sm[S::X + r] = r < cnt ? a.R[(base + r) * 4] : 0.f;
   __syncthreads();
-  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= (long long)a.n * NP) return;
-  float* out = a.G0 + row * a.m1;
-  const int j = a.nlist[row];
-  if (j < 0) {
-    for (int c = 0; c < E2; ++c) out[c] = 0.f;
-    return;
+}
+
+// Layers 1 and 2, then Z = H2 W2 + b2 (4 rows per thread per weight load).
+template <int E0, int E1, int E2>
+__device__ __forceinline__ void embed_forward(float* sm, int cnt) {
+  using S = EmbedSmem<E0, E1, E2>;
+  for (int idx = threadIdx.x; idx < EROWS * E0; idx += ETHREADS) {
+    const int r = idx / E0, p = idx % E0;
+    sm[S::H1 + r * (E0 + 1) + p] = r < cnt ? tanhf(fmaf(sm[S::X + r], sm[S::W0 + p], sm[S::B0 + p])) : 0.f;
   }
-  const float x = a.R[row * 4];
-  const int ti = a.atype[row / NP], tj = a.atype[j];
-  float h1[E0], h2[E1];
-#pragma unroll
-  for (int p = 0; p < E0; ++p) h1[p] = tanhf(fmaf(x, sw[Lw::W0 + p], sw[Lw::B0 + p]));
-#pragma unroll
-  for (int b = 0; b < E1; ++b) {
-    float z = sw[Lw::B1 + b];
-#pragma unroll
-    for (int p = 0; p < E0; ++p) z = fmaf(h1[p], sw[Lw::W1 + p * E1 + b], z);
-    h2[b] = ((E1 == E0) ? h1[b % E0] : (E1 == 2 * E0) ? h1[b % E0] : 0.f) + tanhf(z);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
+    const int r = idx / E1, b = idx % E1;
+    const float* h1 = sm + S::H1 + r * (E0 + 1);
+    float z = sm[S::B1 + b];
+#pragma unroll 5
+    for (int p = 0; p < E0; ++p) z = fmaf(h1[p], sm[S::W1 + p * E1 + b], z);
+    sm[S::H2 + r * (E1 + 1) + b] = r < cnt ? skip_in<E0, E1>(h1, b) + tanhf(z) : 0.f;
   }
-  const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
-  if (E2 == E1 || E2 == 2 * E1) {
-    // output c = r*E1 + b carries the skip input h2[b]
-#pragma unroll 1
-    for (int r = 0; r < E2 / E1; ++r) {
-#pragma unroll
-      for (int b = 0; b < E1; ++b) {
-        const int c = r * E1 + b;
-        float z = sw[Lw::B2 + c];
-#pragma unroll
-        for (int q = 0; q < E1; ++q) z = fmaf(h2[q], sw[Lw::W2 + q * E2 + c], z);
-        out[c] = (h2[b] + tanhf(z)) * (1.f + gt[c]);
-      }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < (EROWS / 4) * E2; idx += ETHREADS) {
+    const int r0 = (idx / E2) * 4, c = idx % E2;
+    float z0 = sm[S::B2 + c], z1 = z0, z2 = z0, z3 = z0;
+    const float* h = sm + S::H2 + r0 * (E1 + 1);
+#pragma unroll 5
+    for (int b = 0; b < E1; ++b) {
+      const float wv = sm[S::W2 + b * S::P2 + c];
+      z0 = fmaf(h[b], wv, z0);
+      z1 = fmaf(h[(E1 + 1) + b], wv, z1);
+      z2 = fmaf(h[2 * (E1 + 1) + b], wv, z2);
+      z3 = fmaf(h[3 * (E1 + 1) + b], wv, z3);
     }
-  } else {
-    for (int c = 0; c < E2; ++c) {
-      float z = sw[Lw::B2 + c];
-#pragma unroll
-      for (int q = 0; q < E1; ++q) z = fmaf(h2[q], sw[Lw::W2 + q * E2 + c], z);
-      out[c] = tanhf(z) * (1.f + gt[c]);
+    float* zr = sm + S::Z + r0 * (E2 + 1) + c;
+    zr[0] = z0; zr[E2 + 1] = z1; zr[2 * (E2 + 1)] = z2; zr[3 * (E2 + 1)] = z3;
+  }
+  __syncthreads();
+}
+
+template <int E0, int E1, int E2>
+__global__ void __launch_bounds__(ETHREADS) k_embed_fwd(EmbedArgs a) {
+  using S = EmbedSmem<E0, E1, E2>;
+  extern __shared__ float sm[];
+  const int atom = blockIdx.x >> 1, part = blockIdx.x & 1;
+  const int r0 = part * EROWS;
+  const int cnt = max(0, min(EROWS, a.nnei[atom] - r0));
+  const size_t base = (size_t)atom * NP + r0;
+  if (cnt > 0) {
+    embed_load<E0, E1, E2>(sm, a, base, cnt);
+    embed_forward<E0, E1, E2>(sm, cnt);
+  }
+  const int ti = a.atype[atom];
+  for (int idx = threadIdx.x; idx < EROWS * E2; idx += ETHREADS) {
+    const int r = idx / E2, c = idx % E2;
+    float g = 0.f;
+    if (r < cnt) {
+      const int tj = a.atype[a.nlist[base + r]];
+      const float h3 = skip_in<E1, E2>(sm + S::H2 + r * (E1 + 1), c) + tanhf(sm[S::Z + r * (E2 + 1) + c]);
+      g = h3 * (1.f + a.Gt[((size_t)ti * a.ntypes + tj) * E2 + c]);
     }
+    a.G0[(base + r) * a.m1 + c] = g;
   }
 }
 
-// Adjoint of the embedding net: dR[:,0] += d(net_s)/dx . (dG0 * (1 + Gt)).
-// dz of the last layer is kept in thread-private shared memory columns.
+// Adjoint: dR[:,0] += d net_s / dx . (dG0 * (1 + Gt)), recomputing the
+// forward activations of the block.
 template <int E0, int E1, int E2>
-__global__ void __launch_bounds__(128) k_embed_bwd(EmbedArgs a) {
-  using Lw = EmbedLayout<E0, E1, E2>;
+__global__ void __launch_bounds__(ETHREADS) k_embed_bwd(EmbedArgs a) {
+  using S = EmbedSmem<E0, E1, E2>;
   extern __shared__ float sm[];
-  float* sw = sm;
-  float* dzs = sm + Lw::TOTAL;  // [E2][blockDim]
-  for (int t = threadIdx.x; t < Lw::TOTAL; t += blockDim.x) sw[t] = a.w[t];
-  __syncthreads();
-  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= (long long)a.n * NP) return;
-  const int j = a.nlist[row];
-  if (j < 0) return;
-  const float x = a.R[row * 4];
-  const int ti = a.atype[row / NP], tj = a.atype[j];
-  float h1[E0], h2[E1], dh2[E1];
-#pragma unroll
-  for (int p = 0; p < E0; ++p) h1[p] = tanhf(fmaf(x, sw[Lw::W0 + p], sw[Lw::B0 + p]));
-#pragma unroll
-  for (int b = 0; b < E1; ++b) {
-    float z = sw[Lw::B1 + b];
-#pragma unroll
-    for (int p = 0; p < E0; ++p) z = fmaf(h1[p], sw[Lw::W1 + p * E1 + b], z);
-    h2[b] = ((E1 == E0 || E1 == 2 * E0) ? h1[b % E0] : 0.f) + tanhf(z);
-  }
-  const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
-  const float* dG = a.dG0 + row * a.m1;
-  for (int c = 0; c < E2; ++c) {
-    float z = sw[Lw::B2 + c];
-#pragma unroll
-    for (int b = 0; b < E1; ++b) z = fmaf(h2[b], sw[Lw::W2 + b * E2 + c], z);
-    const float t = tanhf(z);
-    const float g = dG[c] * (1.f + gt[c]);
-    dzs[c * blockDim.x + threadIdx.x] = g * (1.f - t * t);
-  }
-#pragma unroll
-  for (int b = 0; b < E1; ++b) {
-    float s = 0.f;
-    if (E2 == E1 || E2 == 2 * E1) {
-      for (int c = b; c < E2; c += E1) s += dG[c] * (1.f + gt[c]);
+  const int atom = blockIdx.x >> 1, part = blockIdx.x & 1;
+  const int r0 = part * EROWS;
+  const int cnt = max(0, min(EROWS, a.nnei[atom] - r0));
+  if (cnt == 0) return;
+  const size_t base = (size_t)atom * NP + r0;
+  embed_load<E0, E1, E2>(sm, a, base, cnt);
+  embed_forward<E0, E1, E2>(sm, cnt);
+  const int ti = a.atype[atom];
+  // Z <- dZ3 = g (1 - t3^2) with g = dG0 (1 + Gt); the skip part of dH2 is
+  // summed from g directly below
+  for (int idx = threadIdx.x; idx < EROWS * E2; idx += ETHREADS) {
+    const int r = idx / E2, c = idx % E2;
+    float dz = 0.f;
+    if (r < cnt) {
+      const int tj = a.atype[a.nlist[base + r]];
+      const float g = a.dG0[(base + r) * a.m1 + c] * (1.f + a.Gt[((size_t)ti * a.ntypes + tj) * E2 + c]);
+      const float t = tanhf(sm[S::Z + r * (E2 + 1) + c]);
+      dz = g * (1.f - t * t);
     }
-    dh2[b] = s;
+    sm[S::Z + r * (E2 + 1) + c] = dz;
   }
-  for (int c = 0; c < E2; ++c) {
-    const float dz = dzs[c * blockDim.x + threadIdx.x];
-#pragma unroll
-    for (int b = 0; b < E1; ++b) dh2[b] = fmaf(sw[Lw::W2 + b * E2 + c], dz, dh2[b]);
+  __syncthreads();
+  // dH2[r][b] = skip^T(g)[b] + sum_c W2[b][c] dZ3[r][c]
+  for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
+    const int r = idx / E1, b = idx % E1;
+    float s = 0.f;
+    if (r < cnt) {
+      const float* dz = sm + S::Z + r * (E2 + 1);
+      const float* w2 = sm + S::W2 + b * S::P2;
+#pragma unroll 4
+      for (int c = 0; c < E2; ++c) s = fmaf(w2[c], dz[c], s);
+      if (E2 == E1 || E2 == 2 * E1) {
+        const int tj = a.atype[a.nlist[base + r]];
+        const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
+        const float* dg = a.dG0 + (base + r) * a.m1;
+        for (int c = b; c < E2; c += E1) s += dg[c] * (1.f + gt[c]);
+      }
+    }
+    sm[S::DH2 + r * (E1 + 1) + b] = s;
   }
-  // layer 2 (E0 -> E1): h2 = skip + tanh(z2), so tanh(z2) = h2 - skip
-  float dh1[E0];
-#pragma unroll
-  for (int p = 0; p < E0; ++p) dh1[p] = 0.f;
-#pragma unroll
-  for (int b = 0; b < E1; ++b) {
-    if (E1 == E0 || E1 == 2 * E0) dh1[b % E0] += dh2[b];
-    const float t = h2[b] - ((E1 == E0 || E1 == 2 * E0) ? h1[b % E0] : 0.f);
-    const float dz = dh2[b] * (1.f - t * t);
-#pragma unroll
-    for (int p = 0; p < E0; ++p) dh1[p] = fmaf(sw[Lw::W1 + p * E1 + b], dz, dh1[p]);
+  __syncthreads();
+  // dZ2 = dH2 (1 - t2^2) with t2 = H2 - skip(H1)
+  for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
+    const int r = idx / E1, b = idx % E1;
+    const float t = sm[S::H2 + r * (E1 + 1) + b] - skip_in<E0, E1>(sm + S::H1 + r * (E0 + 1), b);
+    sm[S::DZ2 + r * (E1 + 1) + b] = sm[S::DH2 + r * (E1 + 1) + b] * (1.f - t * t);
   }
-  float dx = 0.f;
-#pragma unroll
-  for (int p = 0; p < E0; ++p) dx = fmaf(sw[Lw::W0 + p], dh1[p] * (1.f - h1[p] * h1[p]), dx);
-  a.dR[row * 4] += dx;
+  __syncthreads();
+  // dH1[r][p] = skip^T(dH2)[p] + sum_b W1[p][b] dZ2[r][b]; term of dx: W0[p] dH1 (1 - H1^2)
+  for (int idx = threadIdx.x; idx < EROWS * E0; idx += ETHREADS) {
+    const int r = idx / E0, p = idx % E0;
+    float s = 0.f;
+    if (r < cnt) {
+      const float* dz2 = sm + S::DZ2 + r * (E1 + 1);
+      const float* w1 = sm + S::W1 + p * E1;
+#pragma unroll 5
+      for (int b = 0; b < E1; ++b) s = fmaf(w1[b], dz2[b], s);
+      if (E1 == E0 || E1 == 2 * E0)
+        for (int b = p; b < E1; b += E0) s += sm[S::DH2 + r * (E1 + 1) + b];
+      const float h1 = sm[S::H1 + r * (E0 + 1) + p];
+      s = s * (1.f - h1 * h1) * sm[S::W0 + p];
+    }
+    sm[S::DH1 + r * (E0 + 1) + p] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < cnt; r += ETHREADS) {
+    float dx = 0.f;
+    for (int p = 0; p < E0; ++p) dx += sm[S::DH1 + r * (E0 + 1) + p];
+    a.dR[(base + r) * 4] += dx;
+  }
 }
 
 template <int E0, int E1, int E2>
 static void embed_launch(const EmbedArgs& a, bool bwd, cudaStream_t st) {
-  using Lw = EmbedLayout<E0, E1, E2>;
-  const long long rows = (long long)a.n * NP;
-  if (rows == 0) return;
-  const unsigned grid = (unsigned)((rows + 127) / 128);
+  using S = EmbedSmem<E0, E1, E2>;
+  if (a.n == 0) return;
+  const unsigned grid = (unsigned)a.n * 2;
+  const size_t sm = sizeof(float) * S::TOTAL;
   if (!bwd) {
-    size_t sm = sizeof(float) * Lw::TOTAL;
     cudaFuncSetAttribute(k_embed_fwd<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_embed_fwd<E0, E1, E2><<<grid, 128, sm, st>>>(a);
-    note_launch();
+    k_embed_fwd<E0, E1, E2><<<grid, ETHREADS, sm, st>>>(a);
   } else {
-    size_t sm = sizeof(float) * (Lw::TOTAL + E2 * 128);
     cudaFuncSetAttribute(k_embed_bwd<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_embed_bwd<E0, E1, E2><<<grid, 128, sm, st>>>(a);
-    note_launch();
+    k_embed_bwd<E0, E1, E2><<<grid, ETHREADS, sm, st>>>(a);
   }
+  note_launch();
 }
 
 static bool embed_dispatch(const EmbedArgs& a, const int* w, bool bwd, cudaStream_t st) {
