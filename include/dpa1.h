@@ -152,6 +152,34 @@ DP_API int dp_stage_times(dp_model* m, const char** names, float* ms, int max_st
 /* Number of CUDA kernels this library has launched in this process. */
 DP_API long long dp_kernel_launches(void);
 
+/* Neighbour list without any allocation (this entry point has no counterpart
+ * in the paper).  It builds the same list as dp_nlist_device (same rcut
+ * rule, same order, rows padded with -1 to 128 entries), but needs no model
+ * and never calls cudaMalloc, cudaFree or an allocating library: its cell-list
+ * scratch is a fixed device array of about 1.7 MB that every GPU loading
+ * this library holds until the process exits.  It is meant for callers that
+ * cannot allocate device memory in the middle of their work: an MD engine
+ * that hands the library only its own pooled buffers, code running inside a
+ * host callback or a captured stream, or a real-time loop where the implicit
+ * synchronisation of cudaMalloc would stall every other stream.
+ *   natoms  : 0 .. 65536 atoms, else DP_ERR_CAPACITY and nothing is launched.
+ *   d_coord : DEVICE [natoms][3] double; d_box: DEVICE [9] double (the box
+ *             rules of every call: orthorhombic, edges > 2 * rcut).
+ *   rcut, sel : cutoff (A, > 0) and neighbour cap (1 .. 128).
+ *   d_nlist : DEVICE [natoms][128] int out; d_nnei: DEVICE [natoms] int out.
+ *   d_status: DEVICE int out; zeroed, then ORed with device-side failure bits
+ *             (1: bad box, 2: more than 256 candidates around an atom,
+ *             4: non-finite coordinate).  Read it after the stream finishes.
+ *   cuda_stream : the stream to run on (NULL = legacy default stream).
+ * Asynchronous: returns once the work is queued.  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls on a device share
+ * the one scratch array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and corrupt each other's lists: order
+ * them on one stream or synchronise in between. */
+DP_API int dp_nlist_noalloc(int natoms, const double* d_coord, const double* d_box, double rcut, int sel,
+                            int* d_nlist, int* d_nnei, int* d_status, void* cuda_stream);
+
 /* Text of the calling thread's last error ("" if none). */
 DP_API const char* dp_last_error(void);
 

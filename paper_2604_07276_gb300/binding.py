@@ -23,7 +23,8 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2}
 
 EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_batch", "dp_reserve", "dp_set_precision",
            "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
-           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_last_error", "dp_free")
+           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_last_error",
+           "dp_free")
 
 
 class DPError(RuntimeError):
@@ -60,6 +61,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dp_debug_copy.restype = ctypes.c_longlong
     lib.dp_set_profiling.argtypes = [P, ctypes.c_int]
     lib.dp_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.dp_nlist_noalloc.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P]
     lib.dp_kernel_launches.argtypes = []
     lib.dp_kernel_launches.restype = ctypes.c_longlong
     lib.dp_last_error.argtypes = []
@@ -91,6 +93,17 @@ def box9(box) -> np.ndarray:
     if b.shape == (3,):
         b = np.diag(b)
     return np.ascontiguousarray(b.reshape(9))
+
+
+def nlist_noalloc(coord, box, rcut: float, sel: int, nlist, nnei, status, stream=None) -> None:
+    """``dp_nlist_noalloc`` on CUDA tensors the caller allocated: coord
+    [N,3] float64, box [9] float64, nlist [N,128] int32, nnei [N] int32,
+    status [1] int32 (device-side failure bits, read after the stream)."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream(coord.device).cuda_stream
+    _check(load_library().dp_nlist_noalloc(int(coord.shape[0]), coord.data_ptr(), box.data_ptr(), float(rcut),
+                                           int(sel), nlist.data_ptr(), nnei.data_ptr(), status.data_ptr(), st))
 
 
 def kernel_launches() -> int:

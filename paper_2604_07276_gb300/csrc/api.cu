@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -809,6 +810,69 @@ int dp_stage_times(dp_model* m, const char** names, float* ms, int max_stages) {
 }
 
 long long dp_kernel_launches(void) { return g_launches.load(); }
+
+// ------------------------------------------------------------------------
+// Allocation-free neighbour list.  Its cell-list scratch is one file-scope
+// device array per GPU instead of a model workspace, so the call works for
+// callers that must not allocate (see dpa1.h).
+namespace {
+constexpr int NA_MAX_ATOMS = 65536;
+constexpr int NA_CAP_DIM = 32;
+constexpr int NA_MAX_CELLS = NA_CAP_DIM * NA_CAP_DIM * NA_CAP_DIM;
+struct NoAllocScratch {
+  CellGrid grid;
+  int cell_count[NA_MAX_CELLS];
+  int cell_start[NA_MAX_CELLS + 1];
+  int cell_cursor[NA_MAX_CELLS];
+  int cell_of[NA_MAX_ATOMS];
+  int cell_atoms[NA_MAX_ATOMS];
+  int ncand[NA_MAX_ATOMS];
+  int types[NA_MAX_ATOMS];    // all zero: the list does not depend on types
+  int types_c[NA_MAX_ATOMS];
+};
+__device__ __align__(256) NoAllocScratch g_nbr_scratch;
+constexpr int NA_MAX_DEVICES = 64;
+NoAllocScratch* g_nbr_scratch_addr[NA_MAX_DEVICES] = {};
+std::mutex g_nbr_scratch_mutex;
+}  // namespace
+
+int dp_nlist_noalloc(int natoms, const double* d_coord, const double* d_box, double rcut, int sel, int* d_nlist,
+                     int* d_nnei, int* d_status, void* stream) {
+  if (natoms < 0 || natoms > NA_MAX_ATOMS)
+    return fail(DP_ERR_CAPACITY, "dp_nlist_noalloc: natoms must be between 0 and " + std::to_string(NA_MAX_ATOMS));
+  if (!d_box || !d_status || (natoms > 0 && (!d_coord || !d_nlist || !d_nnei)))
+    return fail(DP_ERR_ARG, "dp_nlist_noalloc: null device pointer");
+  if (!(rcut > 0.0) || sel < 1 || sel > NP) return fail(DP_ERR_ARG, "dp_nlist_noalloc: need rcut > 0 and 1 <= sel <= 128");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(DP_ERR_ARG, "dp_nlist_noalloc: device ordinal out of range");
+  NoAllocScratch* s = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_nbr_scratch_mutex);
+    if (!g_nbr_scratch_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_nbr_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(DP_ERR_CUDA, std::string("dp_nlist_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      g_nbr_scratch_addr[dev] = reinterpret_cast<NoAllocScratch*>(p);
+    }
+    s = g_nbr_scratch_addr[dev];
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+  if (natoms > 0) CUDA_TRY(cudaMemsetAsync(s->types, 0, sizeof(int) * (size_t)natoms, st));
+  NbrArgs a;
+  a.coord = d_coord; a.box = d_box; a.atype = s->types;
+  a.n = natoms; a.ntypes = 1; a.sel = sel; a.rcut = rcut;
+  a.cap_dim = NA_CAP_DIM; a.cell_cap = NA_MAX_CELLS; a.grid = &s->grid;
+  a.cell_of = s->cell_of; a.cell_count = s->cell_count; a.cell_start = s->cell_start;
+  a.cell_cursor = s->cell_cursor; a.cell_atoms = s->cell_atoms;
+  a.nlist = d_nlist; a.nnei = d_nnei; a.ncand = s->ncand; a.atype_c = s->types_c; a.err = d_status;
+  launch_neighbors(a, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("dp_nlist_noalloc: launch failed: ") + cudaGetErrorString(e));
+  return DP_OK;
+}
 
 void dp_free(dp_model* m) {
   if (!m) return;
