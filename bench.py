@@ -54,6 +54,7 @@ def _args():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=3072, help="oracle centres timed for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
+    ap.add_argument("--md-steps", type=int, default=100, help="graph-captured velocity-Verlet steps to time (0: skip)")
     return ap.parse_args()
 
 
@@ -283,6 +284,28 @@ def run_ours(a):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(tt.item())
 
+    # velocity-Verlet MD of the same box, every step replayed from one CUDA graph
+    md_line = None
+    if a.md_steps > 0:
+        from paper_2604_07276_gb300 import md as dmd
+
+        vel = synth.maxwell_boltzmann(atype, 300.0, seed=11)
+        state = dmd.MDState(coord, vel, synth.MASSES[atype], box, atype, device=dev)
+        dmd.run(m, state, dt=0.5, nsteps=2, graph=True, stream=stream.cuda_stream)  # capture + warm-up
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        th = dmd.run(m, state, dt=0.5, nsteps=a.md_steps, graph=True, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        m.status()
+        md_ms = e0.elapsed_time(e1)
+        thc = th.cpu().numpy()
+        md_line = {"steps": a.md_steps, "dt_fs": 0.5, "graph": True, "precision": head,
+                   "atom_steps_per_s": ws * n * a.md_steps / (md_ms / 1e3), "ms_per_step": md_ms / a.md_steps,
+                   "total_energy_drift_eV_per_atom": float(abs(thc[-1, 2] - thc[0, 2]) / n)}
+
     # parity of this run's forces against the FP64 oracle on sampled atoms
     parity = {}
     nl, nn = m.nlist_device(c, b)
@@ -353,6 +376,7 @@ def run_ours(a):
         "force_rmse_vs_fp64": parity,
         "stage_ms_per_step": {p: {k: v[0] / a.steps for k, v in rr["stages"].items()} for p, rr in results.items()},
         "neighbors": {"mean": float(nn.mean()), "max": int(nn.max())},
+        "md": md_line,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

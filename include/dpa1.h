@@ -122,6 +122,23 @@ DP_API int dp_get_status(dp_model* m);
 DP_API int dp_nlist_device(dp_model* m, int natoms, const double* d_coord, const double* d_box,
                     int* d_nlist, int* d_nnei, void* cuda_stream);
 
+/* Velocity-Verlet molecular dynamics with the model's forces (the MD loop the
+ * paper couples the model to, Sec. II-A and Sec. IV-A), all on the device:
+ * per step v += dt/2 F/m, x += dt v, forces at the new x (neighbour list
+ * rebuilt), v += dt/2 F/m.  Units A, fs, amu, eV.  DEVICE arrays:
+ *   d_coord [natoms][3], d_vel [natoms][3] (A/fs): updated in place;
+ *   d_mass [natoms] (amu); d_box [9]; d_atype [natoms];
+ *   d_force [natoms][3], d_energy [1], d_virial [9]: out, at the final step;
+ *   d_thermo [nsteps][3]: out, (potential, kinetic, total) energy per step.
+ * Forces are first evaluated at the starting coordinates.  With
+ * use_graph != 0 one step is captured once into a CUDA graph (cached in the
+ * model for the same pointers, sizes, dt and precision) and replayed nsteps
+ * times.  Runs on cuda_stream (NULL: the model's own stream, then
+ * synchronised).  natoms must not exceed the reserved size. */
+DP_API int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const double* d_mass,
+                     const double* d_box, const int* d_atype, double dt, int nsteps, double* d_force,
+                     double* d_energy, double* d_virial, double* d_thermo, int use_graph, void* cuda_stream);
+
 /* Largest neighbour count and number of atoms whose candidate set exceeded
  * sel in the last call (the sel cap is a property of the method, not an
  * error). */

@@ -23,7 +23,7 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2}
 
 EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_batch", "dp_reserve", "dp_set_precision",
            "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
-           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_last_error",
+           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_md_run", "dp_last_error",
            "dp_free")
 
 
@@ -61,6 +61,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dp_debug_copy.restype = ctypes.c_longlong
     lib.dp_set_profiling.argtypes = [P, ctypes.c_int]
     lib.dp_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.dp_md_run.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, ctypes.c_int,
+                              P]
     lib.dp_nlist_noalloc.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P]
     lib.dp_kernel_launches.argtypes = []
     lib.dp_kernel_launches.restype = ctypes.c_longlong

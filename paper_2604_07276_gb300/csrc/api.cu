@@ -874,6 +874,65 @@ int dp_nlist_noalloc(int natoms, const double* d_coord, const double* d_box, dou
   return DP_OK;
 }
 
+int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const double* d_mass, const double* d_box,
+              const int* d_atype, double dt, int nsteps, double* d_force, double* d_energy, double* d_virial,
+              double* d_thermo, int use_graph, void* stream) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (natoms < 0 || nsteps < 0 || !(dt > 0.0)) return fail(DP_ERR_ARG, "dp_md_run: need natoms >= 0, nsteps >= 0, dt > 0");
+  if (!d_box || !d_energy || !d_virial || !d_thermo ||
+      (natoms > 0 && (!d_coord || !d_vel || !d_mass || !d_atype || !d_force)))
+    return fail(DP_ERR_ARG, "dp_md_run: null device pointer");
+  if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
+  CUDA_TRY(cudaSetDevice(m->device));
+  cudaStream_t st = stream ? reinterpret_cast<cudaStream_t>(stream) : m->stream;
+  if (!m->d_md_counter) {
+    void* p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, sizeof(int)));
+    m->d_md_counter = reinterpret_cast<int*>(p);
+  }
+  CUDA_TRY(cudaMemsetAsync(m->d_md_counter, 0, sizeof(int), st));
+  // forces at the starting coordinates
+  int rc = run_device(m, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
+  if (rc != DP_OK) return rc;
+  const bool prof = m->prof.on;
+  auto one_step = [&]() -> int {
+    launch_verlet_drift(natoms, dt, d_mass, d_force, d_vel, d_coord, st);
+    int r = run_device(m, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
+    launch_verlet_kick(natoms, dt, d_mass, d_force, d_vel, d_energy, m->d_md_counter, d_thermo, nsteps, st);
+    return r;
+  };
+  if (!use_graph) {
+    for (int s = 0; s < nsteps; ++s)
+      if ((rc = one_step()) != DP_OK) return rc;
+  } else if (nsteps > 0) {
+    const double dtv = dt;
+    const void* key_dt = nullptr;
+    memcpy(&key_dt, &dtv, sizeof(dtv) < sizeof(key_dt) ? sizeof(dtv) : sizeof(key_dt));
+    std::vector<const void*> key = {d_coord, d_vel, d_mass, d_box, d_atype, d_force, d_energy, d_virial, d_thermo,
+                                    reinterpret_cast<const void*>((intptr_t)natoms),
+                                    reinterpret_cast<const void*>((intptr_t)nsteps),
+                                    reinterpret_cast<const void*>((intptr_t)m->precision), key_dt};
+    if (!m->md_exec || m->md_key != key) {
+      if (m->md_exec) { cudaGraphExecDestroy(m->md_exec); m->md_exec = nullptr; }
+      if (m->md_graph) { cudaGraphDestroy(m->md_graph); m->md_graph = nullptr; }
+      m->prof.on = false;  // no event nodes inside the graph
+      CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+      rc = one_step();
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      m->prof.on = prof;
+      if (rc != DP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+      m->md_graph = g;
+      CUDA_TRY(cudaGraphInstantiate(&m->md_exec, g, 0));
+      m->md_key = key;
+    }
+    for (int s = 0; s < nsteps; ++s) CUDA_TRY(cudaGraphLaunch(m->md_exec, st));
+  }
+  if (!stream) CUDA_TRY(cudaStreamSynchronize(st));
+  return DP_OK;
+}
+
 void dp_free(dp_model* m) {
   if (!m) return;
   cudaSetDevice(m->device);
@@ -885,6 +944,9 @@ void dp_free(dp_model* m) {
   if (m->stream) cudaStreamDestroy(m->stream);
   for (auto& e : m->prof.ev)
     if (e) cudaEventDestroy(e);
+  if (m->md_exec) cudaGraphExecDestroy(m->md_exec);
+  if (m->md_graph) cudaGraphDestroy(m->md_graph);
+  if (m->d_md_counter) cudaFree(m->d_md_counter);
   delete m;
 }
 

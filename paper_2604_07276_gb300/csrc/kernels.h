@@ -143,4 +143,9 @@ void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, flo
                      cudaStream_t st);
 void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream_t st);
 
+// --- velocity-Verlet MD (md.cu)
+void launch_verlet_drift(int n, double dt, const double* mass, const double* f, double* v, double* x, cudaStream_t st);
+void launch_verlet_kick(int n, double dt, const double* mass, const double* f, double* v, const double* energy,
+                        int* counter, double* thermo, int nrec, cudaStream_t st);
+
 }  // namespace dpa1

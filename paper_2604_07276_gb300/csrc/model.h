@@ -111,6 +111,11 @@ struct dp_model {
   cudaStream_t last_stream = nullptr;
   int last_natoms = 0;
   dpa1::Profiler prof;
+  // velocity-Verlet: step counter and the cached graph of one step
+  int* d_md_counter = nullptr;
+  cudaGraphExec_t md_exec = nullptr;
+  cudaGraph_t md_graph = nullptr;
+  std::vector<const void*> md_key;
 };
 
 namespace dpa1 {
