@@ -45,22 +45,25 @@ def test_graph_replay_matches_eager(default_model, precision):
 
 
 def test_nve_energy_conservation(default_model):
-    """200 steps of 0.5 fs at 300 K on the 192-atom water box (FP32 path):
-    the total energy stays within 2e-3 eV per atom of its start.  (The
-    smooth-attention reading leaves small jumps when neighbours cross rcut,
-    so exact conservation is not expected.)"""
+    """40 steps of 0.25 fs from 100 K on the 192-atom water box (FP32 path):
+    the total energy stays within 2e-4 eV per atom of its start while the
+    kinetic energy changes several times more.  A random-weight model has no
+    short-range repulsion, so long trajectories collapse atoms onto each other
+    (stiff 1/r terms, then no conservation); the window tested here ends well
+    before that."""
     import torch
     import paper_2604_07276_gb300 as p
     from paper_2604_07276_gb300 import md
 
     cfg, w, _ = default_model
     m = p.DPA1(weight_file(cfg, w, "default"), precision="fp32")
-    s = _state(p, torch)
-    th = md.run(m, s, dt=0.5, nsteps=200, graph=True).cpu().numpy()
+    coord, atype, box = synth.water_box(0)
+    s = md.MDState(coord, synth.maxwell_boltzmann(atype, 100.0, seed=11), synth.MASSES[atype], box, atype)
+    th = md.run(m, s, dt=0.25, nsteps=40, graph=True).cpu().numpy()
     m.status()
     n = s.coord.shape[0]
     drift = np.abs(th[:, 2] - th[0, 2]).max() / n
-    ke_fluct = (th[:, 1].max() - th[:, 1].min()) / n
-    assert drift < 2e-3, drift
-    assert ke_fluct > 10 * drift  # energy really flows between kinetic and potential
+    ke_change = (th[:, 1].max() - th[:, 1].min()) / n
+    assert drift < 2e-4, drift
+    assert ke_change > 20 * drift, (ke_change, drift)
     m.close()
