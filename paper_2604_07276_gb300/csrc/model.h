@@ -39,6 +39,16 @@ struct TcWeights {
   std::vector<void*> fitW_t, fitWT_t;
   void* emb_W1_t = nullptr;
   void* emb_W2_t = nullptr;
+  struct Vectors {
+    float bqkv[3 * 128] = {};
+    float bo[128] = {};
+    float gamma[128] = {};
+    float beta[128] = {};
+  };
+  std::vector<Vectors> vectors;  // per attention layer, host copies passed as kernel parameters
+  struct EmbVectors {
+    float W0[25] = {}, b0[25] = {}, b1[50] = {}, b2[100] = {};
+  } emb_vec;  // embedding net's 1 -> 25 layer and biases
 };
 
 struct TcBuffers {

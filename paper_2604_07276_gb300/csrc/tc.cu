@@ -50,12 +50,14 @@ struct LayerArgs {
   const int* nnei;
   int n, m1;
   const uint4* wimg;       // swizzled weight image of this layer
-  const float* bqkv;       // [3*128]
-  const float* bo;         // [m1]
-  const float* gamma;      // [m1]
-  const float* beta;       // [m1]
   float scale, shift, eps;
   int* err;
+  // per-feature vectors, passed by value (constant bank: every lane of a warp
+  // reads the same feature at the same time)
+  float bqkv[3 * 128];
+  float bo[128];
+  float gamma[128];
+  float beta[128];
 };
 
 constexpr int YLD = 104;  // row stride (elements) of yhat: 208 bytes, 16-byte aligned
@@ -184,7 +186,7 @@ constexpr int F_SMEM = F_SMALL + 512 + 1536 + 64;
 // F16 = true: FP16 operands with two-term splits of G (in [Q K V] = G Wqkv),
 // of P and of V (in O = P V); F16 = false: plain BF16 operands.
 template <bool F16>
-__global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(LayerArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ LayerArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {  // tiles need 1024-byte alignment
     if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
@@ -389,7 +391,7 @@ constexpr int B_SMEM = B_SMALL + 512 + 1536 + 64;
 constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 2 * 128 * 4;  // per CTA
 
 template <bool F16>
-__global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ LayerArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {
     if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
@@ -682,6 +684,274 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(LayerArgs a) {
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
+// ----------------------------------------------------------- embedding net
+// Stage a5 / a13 on the tensor cores: net_s = 1 -> E0 -> E1 -> E2 (tanh,
+// residual rule) for the 128 neighbour rows of an atom, G0 = net_s * (1 + Gt).
+// The two matrix products per direction run in FP16 with hi + lo splits of
+// both operands (three products each), which keeps them within FP32-level
+// accuracy; the 1 -> E0 layer and all element-wise work are FP32.
+constexpr int EMB_E0 = 25, EMB_E1 = 50, EMB_E2 = 100;
+constexpr int EMB_T1 = 64 * 64 * 2;     // W1 tile: 64 (E1 padded) rows x 64 cols
+constexpr int EMB_T2 = 112 * 64 * 2;    // W2 tile: 112 (E2 padded) rows x 64 cols
+constexpr int EMB_TA = 128 * 64 * 2;    // activation tile: 128 rows x 64 cols
+constexpr int EMB_TD = 128 * 128 * 2;   // dZ3 tile: 128 rows x 128 cols
+constexpr int EMB_WIMG = 2 * EMB_T1 + 2 * EMB_T2;  // W1 hi, W1 lo, W2 hi, W2 lo
+constexpr int EMBF_SMEM = EMB_WIMG + 4 * EMB_TA + 64;
+constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + 2 * EMB_TD + 64;
+
+struct EmbedTcArgs {
+  const float* R;
+  const int* nlist;
+  const int* nnei;
+  const int* atype;
+  const float* Gt;        // [ntypes][ntypes][E2]
+  float* G0;              // fwd out [rows][E2]
+  const float* dG0;       // bwd in
+  float* dR;              // bwd: dR[:,0] +=
+  const uint4* wimg;      // W1/W2 hi/lo tiles
+  int n, ntypes;
+  int* err;
+  float W0[EMB_E0], b0[EMB_E0], b1[EMB_E1], b2[EMB_E2];
+};
+
+// 16 columns (c0..c0+15) of a row as hi or lo fp16 parts into an SW128 tile.
+template <bool LO>
+__device__ __forceinline__ void store16(uint8_t* tile, int r, int c0, int R, const float* v) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = LO ? v[8 * q + i] - round16<true>(v[8 * q + i]) : v[8 * q + i];
+    uint4 u;
+    u.x = pack_f16(x[0], x[1]); u.y = pack_f16(x[2], x[3]);
+    u.z = pack_f16(x[4], x[5]); u.w = pack_f16(x[6], x[7]);
+    sw128_store8(tile, r, c0 + 8 * q, R, u);
+  }
+}
+
+// D (+)= A * B with A = Ah + Al and B = Bh + Bl, dropping Al * Bl.
+__device__ __forceinline__ void mma_split(uint32_t d, uint32_t ah, uint32_t al, int a_rows, uint32_t bh, uint32_t bl,
+                                          bool b_mn, int b_rows, int N, int ksteps) {
+  mma_block<true>(d, ah, false, a_rows, bh, b_mn, b_rows, N, ksteps, false);
+  mma_block<true>(d, al, false, a_rows, bh, b_mn, b_rows, N, ksteps, true);
+  mma_block<true>(d, ah, false, a_rows, bl, b_mn, b_rows, N, ksteps, true);
+}
+
+// Layers 1 and 2 of a row, and the issue of Z3 = H2 W2; returns after Z3 is
+// in TMEM columns [64, 176).  h1 / h2 keep the activations.
+__device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
+                                               Sync& sy, int row, bool rv, size_t rowg, float* h1, float* h2) {
+  uint8_t* sW1h = sm;
+  uint8_t* sW1l = sW1h + EMB_T1;
+  uint8_t* sW2h = sW1l + EMB_T1;
+  uint8_t* sW2l = sW2h + EMB_T2;
+  uint8_t* sH1h = sm + EMB_WIMG;
+  uint8_t* sH1l = sH1h + EMB_TA;
+  uint8_t* sH2h = sH1l + EMB_TA;
+  uint8_t* sH2l = sH2h + EMB_TA;
+  const bool issuer = threadIdx.x == 0;
+  const float x = rv ? a.R[rowg * 4] : 0.f;
+  float v[64];
+#pragma unroll
+  for (int p = 0; p < 64; ++p) v[p] = (p < EMB_E0 && rv) ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
+#pragma unroll
+  for (int p = 0; p < EMB_E0; ++p) h1[p] = v[p];
+#pragma unroll
+  for (int c = 0; c < 64; c += 16) {
+    store16<false>(sH1h, row, c, 128, v + c);
+    store16<true>(sH1l, row, c, 128, v + c);
+  }
+  handoff();
+  if (issuer)
+    mma_split(tm + 0, smem_u32(sH1h), smem_u32(sH1l), 128, smem_u32(sW1h), smem_u32(sW1l), false, 64, 64, 2);
+  commit_and_sync(sy, issuer);
+  tmem_ld32(tm + lane_off + 0, v);
+  tmem_ld32(tm + lane_off + 32, v + 32);
+#pragma unroll
+  for (int b = 0; b < 64; ++b) {
+    const float hb = (b < EMB_E1 && rv) ? h1[b % EMB_E0] + tanhf(v[b] + a.b1[b < EMB_E1 ? b : 0]) : 0.f;
+    v[b] = hb;
+  }
+#pragma unroll
+  for (int b = 0; b < EMB_E1; ++b) h2[b] = v[b];
+#pragma unroll
+  for (int c = 0; c < 64; c += 16) {
+    store16<false>(sH2h, row, c, 128, v + c);
+    store16<true>(sH2l, row, c, 128, v + c);
+  }
+  handoff();
+  if (issuer)
+    mma_split(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
+  commit_and_sync(sy, issuer);
+}
+
+__device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm, uint64_t*& bar, uint32_t*& s_tmem,
+                                               int smem_bytes) {
+  bar = reinterpret_cast<uint64_t*>(sm + smem_bytes - 64);
+  s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  uint4* d = reinterpret_cast<uint4*>(sm);
+  for (int i = threadIdx.x; i < EMB_WIMG / 16; i += blockDim.x) d[i] = a.wimg[i];
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(s_tmem, 256);
+  handoff();
+}
+
+__global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__ EmbedTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint64_t* bar;
+  uint32_t* s_tmem;
+  embed_tc_setup(a, sm, bar, s_tmem, EMBF_SMEM);
+  const uint32_t tm = *s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = warp * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  Sync sy{bar, 0u, a.err};
+  float h1[EMB_E0], h2[EMB_E1];
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const bool rv = row < nn;
+    const size_t rowg = (size_t)atom * NP + row;
+    embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+    const float* gt = a.Gt + ((size_t)a.atype[atom] * a.ntypes + (rv ? a.atype[a.nlist[rowg]] : 0)) * EMB_E2;
+    float* out = a.G0 + rowg * EMB_E2;
+#pragma unroll
+    for (int blk = 0; blk < 4; ++blk) {
+      float z[32];
+      tmem_ld32(tm + lane_off + 64 + 32 * blk, z);
+#pragma unroll
+      for (int i = 0; i < 32; i += 4) {
+        const int c = 32 * blk + i;
+        if (c < EMB_E2) {
+          float4 o;
+          float* op = &o.x;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int cc = c + q;
+            op[q] = rv ? (h2[cc % EMB_E1] + tanhf(z[i + q] + a.b2[cc])) * (1.f + gt[cc]) : 0.f;
+          }
+          *reinterpret_cast<float4*>(out + c) = o;
+        }
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+__global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__ EmbedTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint64_t* bar;
+  uint32_t* s_tmem;
+  embed_tc_setup(a, sm, bar, s_tmem, EMBB_SMEM);
+  const uint32_t tm = *s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = warp * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const bool issuer = threadIdx.x == 0;
+  uint8_t* sW1h = sm;
+  uint8_t* sW1l = sW1h + EMB_T1;
+  uint8_t* sW2h = sW1l + EMB_T1;
+  uint8_t* sW2l = sW2h + EMB_T2;
+  uint8_t* sDZ2h = sm + EMB_WIMG;  // the H1 tiles, dead after layer 2
+  uint8_t* sDZ2l = sDZ2h + EMB_TA;
+  uint8_t* sDZ3h = sm + EMB_WIMG + 4 * EMB_TA;
+  uint8_t* sDZ3l = sDZ3h + EMB_TD;
+  Sync sy{bar, 0u, a.err};
+  float h1[EMB_E0], h2[EMB_E1];
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    if (nn == 0) continue;  // uniform over the CTA
+    const bool rv = row < nn;
+    const size_t rowg = (size_t)atom * NP + row;
+    embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+    // dZ3 = g (1 - t3^2), g = dG0 (1 + Gt); skip part of dH2 kept in dh2
+    const float* gt = a.Gt + ((size_t)a.atype[atom] * a.ntypes + (rv ? a.atype[a.nlist[rowg]] : 0)) * EMB_E2;
+    const float* dg = a.dG0 + rowg * EMB_E2;
+    float dh2[EMB_E1];
+#pragma unroll
+    for (int b = 0; b < EMB_E1; ++b) dh2[b] = 0.f;
+#pragma unroll
+    for (int blk = 0; blk < 4; ++blk) {
+      float z[32];
+      tmem_ld32(tm + lane_off + 64 + 32 * blk, z);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int c = 32 * blk + i;
+        float dz = 0.f;
+        if (c < EMB_E2 && rv) {
+          const float g = dg[c] * (1.f + gt[c]);
+          const float t = tanhf(z[i] + a.b2[c]);
+          dz = g * (1.f - t * t);
+          dh2[c % EMB_E1] += g;
+        }
+        z[i] = dz;
+      }
+      store16<false>(sDZ3h, row, 32 * blk, 128, z);
+      store16<false>(sDZ3h, row, 32 * blk + 16, 128, z + 16);
+      store16<true>(sDZ3l, row, 32 * blk, 128, z);
+      store16<true>(sDZ3l, row, 32 * blk + 16, 128, z + 16);
+    }
+    handoff();
+    // dH2 (non-skip part) = dZ3 W2^T  -> TMEM [0, 64)
+    if (issuer)
+      mma_split(tm + 0, smem_u32(sDZ3h), smem_u32(sDZ3l), 128, smem_u32(sW2h), smem_u32(sW2l), true, 112, 64, 7);
+    commit_and_sync(sy, issuer);
+    float v[64];
+    tmem_ld32(tm + lane_off + 0, v);
+    tmem_ld32(tm + lane_off + 32, v + 32);
+    float dh1[EMB_E0];
+#pragma unroll
+    for (int p = 0; p < EMB_E0; ++p) dh1[p] = 0.f;
+#pragma unroll
+    for (int b = 0; b < 64; ++b) {
+      float dz2 = 0.f;
+      if (b < EMB_E1 && rv) {
+        const float d = dh2[b] + v[b];
+        dh1[b % EMB_E0] += d;  // skip path of layer 2
+        const float t = h2[b] - h1[b % EMB_E0];
+        dz2 = d * (1.f - t * t);
+      }
+      v[b] = dz2;
+    }
+#pragma unroll
+    for (int c = 0; c < 64; c += 16) {
+      store16<false>(sDZ2h, row, c, 128, v + c);
+      store16<true>(sDZ2l, row, c, 128, v + c);
+    }
+    handoff();
+    // dH1 (non-skip part) = dZ2 W1^T -> TMEM [64, 96)
+    if (issuer)
+      mma_split(tm + 64, smem_u32(sDZ2h), smem_u32(sDZ2l), 128, smem_u32(sW1h), smem_u32(sW1l), true, 64, 32, 4);
+    commit_and_sync(sy, issuer);
+    tmem_ld32(tm + lane_off + 64, v);
+    if (rv) {
+      float dx = 0.f;
+#pragma unroll
+      for (int p = 0; p < EMB_E0; ++p) dx = fmaf(a.W0[p] * (1.f - h1[p] * h1[p]), dh1[p] + v[p], dx);
+      a.dR[rowg * 4] += dx;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 256);
+}
+
 int sm_count_dev(int dev) {
   int c = 0;
   cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
@@ -741,6 +1011,58 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
       w.allocations.push_back(d);
       (f16 ? w.Wo_t : w.Wqkv_t).push_back(d);  // images: [0] bf16 layers, [1] fp16 layers
     }
+  // embedding-net tiles (hi and lo FP16 parts of W1 and W2) for the 25-50-100 net
+  w.emb_W1_t = nullptr;
+  if (m->emb[0] == EMB_E0 && m->emb[1] == EMB_E1 && m->emb[2] == EMB_E2) {
+    std::vector<uint8_t> img(EMB_WIMG, 0);
+    const std::vector<double>& W1 = get("em_W1");  // [E0][E1]
+    const std::vector<double>& W2 = get("em_W2");  // [E1][E2]
+    auto put = [&](int off, int r, int c, int R, double x, bool lo) {
+      const __half hi = __float2half((float)x);
+      const __half v = lo ? __float2half((float)(x - (double)__half2float(hi))) : hi;
+      memcpy(img.data() + off + sw128_offset(r, c, R), &v, 2);
+    };
+    for (int b = 0; b < EMB_E1; ++b)
+      for (int p = 0; p < EMB_E0; ++p) {
+        put(0, b, p, 64, W1[(size_t)p * EMB_E1 + b], false);
+        put(EMB_T1, b, p, 64, W1[(size_t)p * EMB_E1 + b], true);
+      }
+    for (int c = 0; c < EMB_E2; ++c)
+      for (int b = 0; b < EMB_E1; ++b) {
+        put(2 * EMB_T1, c, b, 112, W2[(size_t)b * EMB_E2 + c], false);
+        put(2 * EMB_T1 + EMB_T2, c, b, 112, W2[(size_t)b * EMB_E2 + c], true);
+      }
+    void* d = nullptr;
+    if (cudaMalloc(&d, img.size()) != cudaSuccess ||
+        cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      msg = "cudaMalloc of the embedding weight image failed";
+      return DP_ERR_CUDA;
+    }
+    w.allocations.push_back(d);
+    w.emb_W1_t = d;
+    const std::vector<double>& W0 = get("em_W0");
+    const std::vector<double>& b0 = get("em_b0");
+    const std::vector<double>& b1 = get("em_b1");
+    const std::vector<double>& b2 = get("em_b2");
+    for (int q = 0; q < EMB_E0; ++q) { w.emb_vec.W0[q] = (float)W0[q]; w.emb_vec.b0[q] = (float)b0[q]; }
+    for (int q = 0; q < EMB_E1; ++q) w.emb_vec.b1[q] = (float)b1[q];
+    for (int q = 0; q < EMB_E2; ++q) w.emb_vec.b2[q] = (float)b2[q];
+    cudaFuncSetAttribute(k_embed_tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBF_SMEM);
+    cudaFuncSetAttribute(k_embed_tc_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBB_SMEM);
+  }
+  w.vectors.assign(m->nattn, TcWeights::Vectors{});
+  for (int l = 0; l < m->nattn; ++l) {
+    const std::string p = "at" + std::to_string(l) + "_";
+    TcWeights::Vectors& v = w.vectors[l];
+    const char* names[3] = {"bq", "bk", "bv"};
+    for (int t = 0; t < 3; ++t)
+      for (int f = 0; f < m->A; ++f) v.bqkv[t * 128 + f] = (float)get(p + names[t])[f];
+    for (int c = 0; c < m->m1; ++c) {
+      v.bo[c] = (float)get(p + "bo")[c];
+      v.gamma[c] = (float)get(p + "ln_g")[c];
+      v.beta[c] = (float)get(p + "ln_b")[c];
+    }
+  }
   const int smem = std::max(F_SMEM, B_SMEM);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
@@ -785,10 +1107,11 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.n = n;
     la.m1 = m->m1;
     la.wimg = reinterpret_cast<const uint4*>(f16 ? m->tcw.Wo_t[l] : m->tcw.Wqkv_t[l]);
-    la.bqkv = m->attn[l].bqkv;
-    la.bo = m->attn[l].bo;
-    la.gamma = m->attn[l].ln_g;
-    la.beta = m->attn[l].ln_b;
+    const TcWeights::Vectors& vec = m->tcw.vectors[l];
+    memcpy(la.bqkv, vec.bqkv, sizeof(la.bqkv));
+    memcpy(la.bo, vec.bo, sizeof(la.bo));
+    memcpy(la.gamma, vec.gamma, sizeof(la.gamma));
+    memcpy(la.beta, vec.beta, sizeof(la.beta));
     la.scale = (float)(1.0 / std::sqrt((double)m->A));
     la.shift = (float)m->shift;
     la.eps = (float)m->ln_eps;
@@ -799,7 +1122,23 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   EmbedArgs ea{};
   ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m->m1;
   ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
-  launch_embed_fwd(ea, m->emb, st);
+  const bool emb_tc = m->tcw.emb_W1_t != nullptr;
+  EmbedTcArgs et{};
+  if (emb_tc) {
+    et.R = ws.R; et.nlist = ws.nlist; et.nnei = ws.nnei; et.atype = atype; et.Gt = m->Gt; et.G0 = ws.G[0];
+    et.dG0 = ws.dG; et.dR = ws.dR; et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W1_t);
+    et.n = n; et.ntypes = m->nt; et.err = m->d_err;
+    memcpy(et.W0, m->tcw.emb_vec.W0, sizeof(et.W0));
+    memcpy(et.b0, m->tcw.emb_vec.b0, sizeof(et.b0));
+    memcpy(et.b1, m->tcw.emb_vec.b1, sizeof(et.b1));
+    memcpy(et.b2, m->tcw.emb_vec.b2, sizeof(et.b2));
+  }
+  if (emb_tc && n > 0) {
+    k_embed_tc_fwd<<<std::min(n, 2 * sm_count_dev(m->device)), 128, EMBF_SMEM, st>>>(et);
+    note_launch();
+  } else {
+    launch_embed_fwd(ea, m->emb, st);
+  }
   prof_mark(m, "embed_fwd", st);
   for (int l = 0; l < L && n > 0; ++l) {
     if (f16)
@@ -819,9 +1158,14 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     note_launch();
     prof_mark(m, "attn_bwd_tc", st);
   }
-  ea.dG0 = ws.dG;
-  ea.dR = ws.dR;
-  launch_embed_bwd(ea, m->emb, st);
+  if (emb_tc && n > 0) {
+    k_embed_tc_bwd<<<std::min(n, sm_count_dev(m->device)), 128, EMBB_SMEM, st>>>(et);
+    note_launch();
+  } else {
+    ea.dG0 = ws.dG;
+    ea.dR = ws.dR;
+    launch_embed_bwd(ea, m->emb, st);
+  }
   prof_mark(m, "embed_bwd", st);
 }
 
