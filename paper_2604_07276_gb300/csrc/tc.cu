@@ -181,7 +181,7 @@ __device__ __forceinline__ float reduce_scatter32(float* v) {
 // the half-row exchange borrows the first 1 KB of a slot that is free.
 constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_SLOT_D = 3 * TILE, F_W = 4 * TILE;
 constexpr int F_SMALL = 7 * TILE;
-constexpr int F_SMEM = F_SMALL + 512 + 1536 + 64;
+constexpr int F_SMEM = F_SMALL + 2048 + 64;
 
 // F16 = true: FP16 operands with two-term splits of G (in [Q K V] = G Wqkv),
 // of P and of V (in O = P V); F16 = false: plain BF16 operands.
@@ -199,9 +199,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sWq = sm + F_W;
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
-  float* s_w = reinterpret_cast<float*>(sm + F_SMALL);
-  float* s_rh = s_w + 128;  // [128][3]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_rh + 384);
+  float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -229,11 +228,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     const size_t base = (size_t)atom * NP;
     if (tid < 128) {
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
-      const bool v = tid < nn;
-      s_w[tid] = v ? r.w : 0.f;
-      s_rh[3 * tid] = v ? r.x : 0.f;
-      s_rh[3 * tid + 1] = v ? r.y : 0.f;
-      s_rh[3 * tid + 2] = v ? r.z : 0.f;
+      s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float v[64];
     // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B)
@@ -272,12 +267,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     {
       float* xch = reinterpret_cast<float*>(sA);
       const bool rv = row < nn;
-      const float wj = s_w[row];
+      const float4 kj = s_key[row];
+      const float wj = kj.w;
       float mx = -INFINITY;
 #pragma unroll
       for (int i = 0; i < 64; ++i) {
         const int k = c0 + i;
-        const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_w[k]) : -INFINITY;
+        const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_key[k].w) : -INFINITY;
         v[i] = l;
         mx = fmaxf(mx, l);
       }
@@ -291,12 +287,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       }
       sum = pair_sum(xch, half, row, sum);  // ends with a barrier: slot A is free
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
-      const float hx = s_rh[3 * row], hy = s_rh[3 * row + 1], hz = s_rh[3 * row + 2];
 #pragma unroll
       for (int i = 0; i < 64; ++i) {
-        const int k = c0 + i;
-        const float c = hx * s_rh[3 * k] + hy * s_rh[3 * k + 1] + hz * s_rh[3 * k + 2];
-        v[i] = v[i] * inv * (wj * s_w[k]) * c;
+        const float4 kk = s_key[c0 + i];
+        const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+        v[i] = v[i] * inv * (wj * kk.w) * c;
       }
       store_row64<F16>(sB, row, c0, v);
       if (F16) store_row64<F16, true>(sA, row, c0, v);
@@ -387,7 +382,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 // first 1 KB of whichever slot is free at that point.
 constexpr int B_SLOT_A = 0, B_SLOT_B = TILE, B_SLOT_C = 2 * TILE, B_SLOT_D = 3 * TILE, B_W = 4 * TILE;
 constexpr int B_SMALL = 4 * TILE + 3 * TILE;
-constexpr int B_SMEM = B_SMALL + 512 + 1536 + 64;
+constexpr int B_SMEM = B_SMALL + 2048 + 64;
 constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 2 * 128 * 4;  // per CTA
 
 template <bool F16>
@@ -404,9 +399,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint8_t* sWq = sm + B_W;
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
-  float* s_w = reinterpret_cast<float*>(sm + B_SMALL);
-  float* s_rh = s_w + 128;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_rh + 384);
+  float4* s_key = reinterpret_cast<float4*>(sm + B_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -437,11 +431,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     const bool rv = row < nn;
     if (tid < 128) {
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
-      const bool vv = tid < nn;
-      s_w[tid] = vv ? r.w : 0.f;
-      s_rh[3 * tid] = vv ? r.x : 0.f;
-      s_rh[3 * tid + 1] = vv ? r.y : 0.f;
-      s_rh[3 * tid + 2] = vv ? r.z : 0.f;
+      s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float v[64];
     // P0: G_l -> A, dY = LayerNorm adjoint of dZ -> C, Wo -> D
@@ -455,17 +445,22 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       float yv[64];
       float s1 = 0.f, s2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
+      for (int i = 0; i < 64; i += 4) {
         const int c = c0 + i;
-        float g = 0.f, y = 0.f;
+        float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 y4 = g4;
         if (c < a.m1 && rv) {
-          g = a.gamma[c] * dz[c];
-          y = __bfloat162float(yh[c]);
+          g4 = *reinterpret_cast<const float4*>(dz + c);
+          const uint2 yy = *reinterpret_cast<const uint2*>(yh + c);
+          const __nv_bfloat162 y01 = *reinterpret_cast<const __nv_bfloat162*>(&yy.x);
+          const __nv_bfloat162 y23 = *reinterpret_cast<const __nv_bfloat162*>(&yy.y);
+          y4 = make_float4(__low2float(y01), __high2float(y01), __low2float(y23), __high2float(y23));
+          g4.x *= a.gamma[c]; g4.y *= a.gamma[c + 1]; g4.z *= a.gamma[c + 2]; g4.w *= a.gamma[c + 3];
         }
-        v[i] = g;
-        yv[i] = y;
-        s1 += g;
-        s2 += g * y;
+        v[i] = g4.x; v[i + 1] = g4.y; v[i + 2] = g4.z; v[i + 3] = g4.w;
+        yv[i] = y4.x; yv[i + 1] = y4.y; yv[i + 2] = y4.z; yv[i + 3] = y4.w;
+        s1 += (g4.x + g4.y) + (g4.z + g4.w);
+        s2 += (g4.x * y4.x + g4.y * y4.y) + (g4.z * y4.z + g4.w * y4.w);
       }
       s1 = pair_sum(xch, half, row, s1) / (float)a.m1;
       s2 = pair_sum(xch, half, row, s2) / (float)a.m1;
@@ -511,12 +506,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     }
     commit_and_sync(sy, issuer);
     // P2: softmax and its adjoint in 32-key passes that reload S and dP from
-    // TMEM; P -> slot C, dS -> TMEM over the consumed S columns
+    // TMEM (max; normaliser and sum_k A_jk dA_jk together; main pass); P ->
+    // slot C, dS -> TMEM over the consumed S columns
     {
       float* xch = reinterpret_cast<float*>(sC);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
-      const float wj = s_w[row];
-      const float hx = s_rh[3 * row], hy = s_rh[3 * row + 1], hz = s_rh[3 * row + 2];
+      const float4 kj = s_key[row];
+      const float wj = kj.w;
       float t[32], u[32];
       float mx = -INFINITY;
 #pragma unroll 1
@@ -525,23 +521,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int k = c0 + 32 * blk + i;
-          if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_w[k]));
+          if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_key[k].w));
         }
       }
       mx = pair_max(xch, half, row, mx);
-      float sum = 0.f;
-#pragma unroll 1
-      for (int blk = 0; blk < 2; ++blk) {
-        tmem_ld32(tS + 32 * blk, t);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int k = c0 + 32 * blk + i;
-          if (k < nn && rv) sum += __expf((t[i] * a.scale + a.shift) * (wj * s_w[k]) - mx);
-        }
-      }
-      sum = pair_sum(xch, half, row, sum);
-      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
-      float tsum = 0.f;
+      float sum = 0.f, wsum = 0.f;
 #pragma unroll 1
       for (int blk = 0; blk < 2; ++blk) {
         tmem_ld32(tS + 32 * blk, t);
@@ -550,14 +534,19 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
         for (int i = 0; i < 32; ++i) {
           const int k = c0 + 32 * blk + i;
           if (k < nn && rv) {
-            const float ww = wj * s_w[k];
-            const float A = __expf((t[i] * a.scale + a.shift) * ww - mx) * inv;
-            const float c = hx * s_rh[3 * k] + hy * s_rh[3 * k + 1] + hz * s_rh[3 * k + 2];
-            tsum += A * u[i] * ww * c;
+            const float4 kk = s_key[k];
+            const float ww = wj * kk.w;
+            const float e = __expf((t[i] * a.scale + a.shift) * ww - mx);
+            const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+            sum += e;
+            wsum += e * u[i] * ww * c;
           }
         }
       }
-      tsum = pair_sum(xch, half, row, tsum);  // ends with a barrier: slot C is free
+      sum = pair_sum(xch, half, row, sum);
+      wsum = pair_sum(xch, half, row, wsum);  // ends with a barrier: slot C is free
+      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      const float tsum = wsum * inv;  // sum_k A_jk dA_jk
       float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
       float4* cp = reinterpret_cast<float4*>(colp) + quad * 128 + c0;
 #pragma unroll 1
@@ -569,13 +558,12 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
         for (int i = 0; i < 32; ++i) {
           const int k = c0 + 32 * blk + i;
           float H = 0.f, dc = 0.f, P = 0.f, dS = 0.f;
-          const float wk = s_w[k];
-          const float kx = s_rh[3 * k], ky = s_rh[3 * k + 1], kz = s_rh[3 * k + 2];
+          const float4 kk = s_key[k];
           if (k < nn && rv) {
             const float l = t[i] * a.scale;
-            const float ww = wj * wk;
+            const float ww = wj * kk.w;
             const float A = __expf((l + a.shift) * ww - mx) * inv;
-            const float c = hx * kx + hy * ky + hz * kz;
+            const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
             const float dP = u[i];
             const float dLp = A * (dP * ww * c - tsum);
             H = dP * A * c + dLp * (l + a.shift);
@@ -583,8 +571,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
             P = A * ww * c;
             dS = dLp * ww * a.scale;
           }
-          rw_ += H * wk;
-          rx += dc * kx; ry += dc * ky; rz += dc * kz;
+          rw_ += H * kk.w;
+          rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
           cw[i] = H * wj;
           dcv[i] = dc;
           pv[i] = P;
@@ -602,13 +590,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
         tmem_st32(tS + 32 * blk, t);  // dS over this block's consumed S columns
         const float sw_ = reduce_scatter32(cw);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * hx;
+        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * kj.x;
         const float sx = reduce_scatter32(pv);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * hy;
+        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * kj.y;
         const float sy_ = reduce_scatter32(pv);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * hz;
+        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * kj.z;
         const float sz = reduce_scatter32(pv);
         cp[blk * 32 + lane] = make_float4(sx, sy_, sz, sw_);
       }
