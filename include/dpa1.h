@@ -139,6 +139,34 @@ DP_API int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, co
                      const double* d_box, const int* d_atype, double dt, int nsteps, double* d_force,
                      double* d_energy, double* d_virial, double* d_thermo, int use_graph, void* cuda_stream);
 
+/* Training of a model without attention layers in FP32 (the distilled
+ * student potential).  The trainable parameters form one FP32 vector:
+ * embedding net (em_W0 em_b0 em_W1 em_b1 em_W2 em_b2), fitting layers
+ * (fit_W fit_b per hidden layer), output layer (w, b) and per-type energy
+ * bias, in the order and shapes of the weight file; the type embedding and
+ * type-pair net stay fixed.
+ *   dp_param_count: number of entries.  dp_get_params / dp_set_params /
+ *   dp_get_grad copy the vector / its gradient to or from host memory
+ *   (count must equal dp_param_count).  dp_zero_grad clears the gradient.
+ *   dp_train_frame: for one frame with reference energy e_ref (eV) and
+ *   DEVICE reference forces d_force_ref [natoms][3], adds to the gradient
+ *   dL/dtheta of L = pe ((E - e_ref)/N)^2 + pf mean |F - F_ref|^2 and writes
+ *   (L, energy part, force part) to DEVICE d_loss [3].  The energy part is
+ *   exact; the force part uses -(2 pf / 3N) d/dtheta D_v E with v = F - F_ref
+ *   held fixed, evaluated as a central difference of exact energy-weight
+ *   gradients at x +- s v, s = fd_h / max|v| (fd_h in A).
+ *   dp_adam_step: one Adam update of the vector with the accumulated
+ *   gradient (then cleared). */
+DP_API int dp_param_count(const dp_model* m);
+DP_API int dp_get_params(dp_model* m, float* host, int count);
+DP_API int dp_set_params(dp_model* m, const float* host, int count);
+DP_API int dp_get_grad(dp_model* m, float* host, int count);
+DP_API int dp_zero_grad(dp_model* m, void* cuda_stream);
+DP_API int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
+                          double e_ref, const double* d_force_ref, double pe, double pf, double fd_h,
+                          double* d_loss, void* cuda_stream);
+DP_API int dp_adam_step(dp_model* m, double lr, double beta1, double beta2, double eps, void* cuda_stream);
+
 /* Largest neighbour count and number of atoms whose candidate set exceeded
  * sel in the last call (the sel cap is a property of the method, not an
  * error). */

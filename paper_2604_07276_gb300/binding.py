@@ -23,7 +23,8 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2}
 
 EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_batch", "dp_reserve", "dp_set_precision",
            "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
-           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_md_run", "dp_last_error",
+           "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_md_run", "dp_param_count", "dp_get_params",
+           "dp_set_params", "dp_get_grad", "dp_zero_grad", "dp_train_frame", "dp_adam_step", "dp_last_error",
            "dp_free")
 
 
@@ -61,6 +62,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dp_debug_copy.restype = ctypes.c_longlong
     lib.dp_set_profiling.argtypes = [P, ctypes.c_int]
     lib.dp_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.dp_param_count.argtypes = [P]
+    lib.dp_get_params.argtypes = [P, F, ctypes.c_int]
+    lib.dp_set_params.argtypes = [P, F, ctypes.c_int]
+    lib.dp_get_grad.argtypes = [P, F, ctypes.c_int]
+    lib.dp_zero_grad.argtypes = [P, P]
+    lib.dp_train_frame.argtypes = [P, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, P, P]
+    lib.dp_adam_step.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
     lib.dp_md_run.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, ctypes.c_int,
                               P]
     lib.dp_nlist_noalloc.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P]
@@ -211,6 +221,42 @@ class DPA1:
         if r < 0:
             _check(int(r))
         return out
+
+    # -- training (models without attention, FP32) ----------------------------
+    def param_count(self) -> int:
+        n = self.lib.dp_param_count(self.h)
+        if n < 0:
+            _check(n)
+        return n
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        _check(self.lib.dp_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(out)))
+        return out
+
+    def set_params(self, theta) -> None:
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(self.lib.dp_set_params(self.h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(t)))
+
+    def get_grad(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        _check(self.lib.dp_get_grad(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(out)))
+        return out
+
+    def zero_grad(self, stream=None) -> None:
+        _check(self.lib.dp_zero_grad(self.h, stream))
+
+    def train_frame(self, coord, box, atype, e_ref: float, force_ref, loss, pe=1.0, pf=1.0, fd_h=1e-3, stream=None):
+        """``dp_train_frame`` on CUDA tensors; ``loss`` is a float64 [3] tensor."""
+        import torch
+
+        st = stream if stream is not None else torch.cuda.current_stream(coord.device).cuda_stream
+        _check(self.lib.dp_train_frame(self.h, int(coord.shape[0]), coord.data_ptr(), box.data_ptr(),
+                                       atype.data_ptr(), float(e_ref), force_ref.data_ptr(), float(pe), float(pf),
+                                       float(fd_h), loss.data_ptr(), st))
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+        _check(self.lib.dp_adam_step(self.h, float(lr), float(beta1), float(beta2), float(eps), stream))
 
     def set_profiling(self, on: bool) -> None:
         _check(self.lib.dp_set_profiling(self.h, 1 if on else 0))

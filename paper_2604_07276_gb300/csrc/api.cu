@@ -202,6 +202,18 @@ std::vector<float> transpose_f(const std::vector<double>& v, int rows, int cols)
   return t;
 }
 
+// Transposed fitting weights and the output layer scaled by out_scale, from
+// the parameter vector.
+void refresh_derived(dp_model* m, cudaStream_t st) {
+  int fan = m->fit_in;
+  for (int l = 0; l < m->nfit; ++l) {
+    launch_transpose(m->fitW[l], fan, m->fit[l], m->fitWT[l], st);
+    fan = m->fit[l];
+  }
+  launch_scale_copy(m->theta + m->off_wout, m->w_out, fan, (float)m->out_scale, st);
+  launch_scale_copy(m->theta + m->off_bout, m->d_b_out, 1, (float)m->out_scale, st);
+}
+
 void free_workspace(Workspace& ws) {
   if (ws.mem) cudaFree(ws.mem);
   ws.mem = nullptr;
@@ -353,7 +365,12 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
     fan = out;
   }
   // w_out and b_out are stored multiplied by out_scale
-  launch_energy_head(ws.H[m->nfit - 1], n, fan, m->w_out, m->b_out, 1.0f, m->ebias, atype, ws.e, st);
+  launch_energy_head(ws.H[m->nfit - 1], n, fan, m->w_out, m->d_b_out, 1.0f, m->ebias, atype, ws.e, st);
+  const float* gs = m->grad_scale;  // non-null: add gs * dE/dtheta to the gradient
+  if (gs) {
+    launch_colsum(ws.H[m->nfit - 1], fan, m->grad + m->off_wout, fan, n, gs, (float)m->out_scale, st);
+    launch_head_bias_grad(atype, n, m->grad + m->off_ebias, m->grad + m->off_bout, gs, (float)m->out_scale, st);
+  }
   // a10: fitting backward, seeded with dE/dH_last = out_scale * w_out
   launch_fill_rows(ws.dHa, m->w_out, n, fan, st);
   float* dH = ws.dHa;
@@ -363,6 +380,11 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
     const int in = l > 0 ? m->fit[l - 1] : m->fit_in;
     const bool res = (l > 0 && out == in);
     launch_tanh_bwd(dH, ws.H[l], res ? ws.H[l - 1] : nullptr, ws.dZ, (long long)n * out, st);
+    if (gs) {
+      const float* input = l > 0 ? ws.H[l - 1] : ws.X;
+      launch_wgrad(input, in, ws.dZ, out, m->grad + m->off_fitW[l], out, in, out, n, gs, st);
+      launch_colsum(ws.dZ, out, m->grad + m->off_fitb[l], out, n, gs, 1.0f, st);
+    }
     float* dst = l > 0 ? dHn : ws.dX;
     gemm_f32(ws.dZ, out, m->fitWT[l], in, nullptr, res ? dH : nullptr, out, dst, in, n, in, out,
              res ? EPI_RES : EPI_BIAS, st);
@@ -424,6 +446,7 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   // a13: embedding backward -> dR[:,0]
   ea.dG0 = ws.dG; ea.dR = ws.dR;
   launch_embed_bwd(ea, m->emb, st);
+  if (m->grad_scale) launch_embed_wgrad(ea, m->emb, m->grad, m->grad_scale, st);
   prof_mark(m, "embed_bwd", st);
 }
 
@@ -546,18 +569,8 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
         (probe_widths[0] == 16 && probe_widths[1] == 32 && probe_widths[2] == 64) ||
         (probe_widths[0] == 32 && probe_widths[1] == 64 && probe_widths[2] == 128)))
     return fail_free(fail(DP_ERR_UNSUPPORTED, "embedding widths without a kernel instance"));
-  // embedding net packed as W0 b0 W1 b1 W2 b2
-  std::vector<float> packed;
-  for (int l = 0; l < 3; ++l) {
-    auto* W = w.get("em_W" + std::to_string(l));
-    auto* b = w.get("em_b" + std::to_string(l));
-    packed.insert(packed.end(), W->begin(), W->end());
-    packed.insert(packed.end(), b->begin(), b->end());
-  }
-  if ((rc = dev_upload(m, &m->emb_packed, packed)) != DP_OK) return fail_free(rc);
   if ((rc = dev_upload(m, &m->davg, to_f(*w.get("davg")))) != DP_OK) return fail_free(rc);
   if ((rc = dev_upload(m, &m->dstd, to_f(*w.get("dstd")))) != DP_OK) return fail_free(rc);
-  if ((rc = dev_upload(m, &m->ebias, to_f(*w.get("ebias")))) != DP_OK) return fail_free(rc);
   // type tables (a4) on the device
   {
     std::vector<double> tt;
@@ -603,23 +616,56 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     if ((rc = dev_upload(m, &L.ln_g, to_f(*w.get(p + "ln_g")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_b, to_f(*w.get(p + "ln_b")))) != DP_OK) return fail_free(rc);
   }
-  int fan = m->fit_in;
-  m->fitW.resize(m->nfit); m->fitWT.resize(m->nfit); m->fitb.resize(m->nfit);
-  for (int l = 0; l < m->nfit; ++l) {
-    auto* W = w.get("fit_W" + std::to_string(l));
-    if ((rc = dev_upload(m, &m->fitW[l], to_f(*W))) != DP_OK) return fail_free(rc);
-    if ((rc = dev_upload(m, &m->fitWT[l], transpose_f(*W, fan, m->fit[l]))) != DP_OK) return fail_free(rc);
-    if ((rc = dev_upload(m, &m->fitb[l], to_f(*w.get("fit_b" + std::to_string(l))))) != DP_OK) return fail_free(rc);
-    fan = m->fit[l];
-  }
+  // trainable parameter vector (layout in model.h) and its derived copies
   {
-    // output layer, stored multiplied by out_scale: the forward head and the
-    // backward seed dE/dH_last use the same FP32 vector
-    auto* W = w.get("fit_W" + std::to_string(m->nfit));
-    std::vector<float> ws((size_t)fan);
-    for (int c = 0; c < fan; ++c) ws[c] = (float)((*W)[c] * m->out_scale);
-    if ((rc = dev_upload(m, &m->w_out, ws)) != DP_OK) return fail_free(rc);
-    m->b_out = (float)((*w.get("fit_b" + std::to_string(m->nfit)))[0] * m->out_scale);
+    std::vector<float> th;
+    for (int l = 0; l < 3; ++l) {
+      auto* W = w.get("em_W" + std::to_string(l));
+      auto* b = w.get("em_b" + std::to_string(l));
+      th.insert(th.end(), W->begin(), W->end());
+      th.insert(th.end(), b->begin(), b->end());
+    }
+    m->off_fitW.resize(m->nfit);
+    m->off_fitb.resize(m->nfit);
+    for (int l = 0; l < m->nfit; ++l) {
+      auto* W = w.get("fit_W" + std::to_string(l));
+      auto* b = w.get("fit_b" + std::to_string(l));
+      m->off_fitW[l] = (int)th.size();
+      th.insert(th.end(), W->begin(), W->end());
+      m->off_fitb[l] = (int)th.size();
+      th.insert(th.end(), b->begin(), b->end());
+    }
+    auto* Wout = w.get("fit_W" + std::to_string(m->nfit));
+    m->off_wout = (int)th.size();
+    th.insert(th.end(), Wout->begin(), Wout->end());
+    m->off_bout = (int)th.size();
+    th.push_back((float)(*w.get("fit_b" + std::to_string(m->nfit)))[0]);
+    m->off_ebias = (int)th.size();
+    for (double x : *w.get("ebias")) th.push_back((float)x);
+    m->ntheta = (int)th.size();
+    if ((rc = dev_upload(m, &m->theta, th)) != DP_OK) return fail_free(rc);
+    std::vector<float> zeros(th.size(), 0.f);
+    if ((rc = dev_upload(m, &m->grad, zeros)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->adam_m, zeros)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->adam_v, zeros)) != DP_OK) return fail_free(rc);
+    std::vector<float> sc = {1.f, 0.f, 0.f, 0.f};
+    if ((rc = dev_upload(m, &m->d_scales, sc)) != DP_OK) return fail_free(rc);
+    m->emb_packed = m->theta;
+    m->ebias = m->theta + m->off_ebias;
+    m->fitW.resize(m->nfit); m->fitWT.resize(m->nfit); m->fitb.resize(m->nfit);
+    int fan = m->fit_in;
+    for (int l = 0; l < m->nfit; ++l) {
+      m->fitW[l] = m->theta + m->off_fitW[l];
+      m->fitb[l] = m->theta + m->off_fitb[l];
+      std::vector<float> wt((size_t)fan * m->fit[l], 0.f);
+      if ((rc = dev_upload(m, &m->fitWT[l], wt)) != DP_OK) return fail_free(rc);
+      fan = m->fit[l];
+    }
+    std::vector<float> wo((size_t)fan, 0.f), bo(1, 0.f);
+    if ((rc = dev_upload(m, &m->w_out, wo)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->d_b_out, bo)) != DP_OK) return fail_free(rc);
+    refresh_derived(m, nullptr);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(fail(DP_ERR_CUDA, "weight refresh failed"));
   }
   if (precision != DP_PREC_FP32) {
     std::string msg;
@@ -874,6 +920,93 @@ int dp_nlist_noalloc(int natoms, const double* d_coord, const double* d_box, dou
   return DP_OK;
 }
 
+int dp_param_count(const dp_model* m) { return m ? m->ntheta : DP_ERR_ARG; }
+
+int dp_get_params(dp_model* m, float* host, int count) {
+  if (check_model(m) || !host || count != m->ntheta) return fail(DP_ERR_ARG, "dp_get_params: bad buffer");
+  CUDA_TRY(cudaSetDevice(m->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(host, m->theta, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  return DP_OK;
+}
+
+int dp_set_params(dp_model* m, const float* host, int count) {
+  if (check_model(m) || !host || count != m->ntheta) return fail(DP_ERR_ARG, "dp_set_params: bad buffer");
+  CUDA_TRY(cudaSetDevice(m->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(m->theta, host, sizeof(float) * count, cudaMemcpyHostToDevice));
+  refresh_derived(m, nullptr);
+  CUDA_TRY(cudaDeviceSynchronize());
+  return DP_OK;
+}
+
+int dp_get_grad(dp_model* m, float* host, int count) {
+  if (check_model(m) || !host || count != m->ntheta) return fail(DP_ERR_ARG, "dp_get_grad: bad buffer");
+  CUDA_TRY(cudaSetDevice(m->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(host, m->grad, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  return DP_OK;
+}
+
+int dp_zero_grad(dp_model* m, void* stream) {
+  if (check_model(m)) return DP_ERR_ARG;
+  CUDA_TRY(cudaSetDevice(m->device));
+  CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * m->ntheta, reinterpret_cast<cudaStream_t>(stream)));
+  return DP_OK;
+}
+
+int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
+                   double e_ref, const double* d_force_ref, double pe, double pf, double fd_h, double* d_loss,
+                   void* stream) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (m->precision != DP_PREC_FP32 || m->nattn != 0)
+    return fail(DP_ERR_UNSUPPORTED, "dp_train_frame: training needs an FP32 model without attention layers");
+  if (natoms < 1 || !d_coord || !d_box || !d_atype || !d_force_ref || !d_loss || !(fd_h > 0.0))
+    return fail(DP_ERR_ARG, "dp_train_frame: bad arguments");
+  if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
+  CUDA_TRY(cudaSetDevice(m->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (m->t_cap < m->ws.cap) {
+    if (m->t_buf) cudaFree(m->t_buf);
+    m->t_buf = nullptr;
+    void* p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, sizeof(double) * (16 + 9 * (size_t)m->ws.cap)));
+    m->t_buf = reinterpret_cast<double*>(p);
+    m->t_cap = m->ws.cap;
+  }
+  double* t_energy = m->t_buf;
+  double* t_virial = m->t_buf + 1;
+  double* t_force = m->t_buf + 16;
+  double* coord_p = t_force + 3 * (size_t)m->t_cap;
+  double* coord_m = coord_p + 3 * (size_t)m->t_cap;
+  m->grad_scale = nullptr;
+  int rc = run_device(m, natoms, d_coord, d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
+  if (rc != DP_OK) return rc;
+  launch_train_prep(natoms, t_energy, e_ref, t_force, d_force_ref, d_coord, pe, pf, fd_h, coord_p, coord_m, d_loss,
+                    m->d_scales, st);
+  const double* xs[3] = {d_coord, coord_p, coord_m};
+  for (int k = 0; k < 3 && rc == DP_OK; ++k) {
+    m->grad_scale = m->d_scales + 1 + k;
+    rc = run_device(m, natoms, xs[k], d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
+  }
+  m->grad_scale = nullptr;
+  return rc;
+}
+
+int dp_adam_step(dp_model* m, double lr, double beta1, double beta2, double eps, void* stream) {
+  if (check_model(m)) return DP_ERR_ARG;
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+    return fail(DP_ERR_ARG, "dp_adam_step: bad hyper-parameters");
+  CUDA_TRY(cudaSetDevice(m->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int t = ++m->adam_t;
+  const float bc1 = (float)(1.0 - std::pow(beta1, t)), bc2 = (float)(1.0 - std::pow(beta2, t));
+  launch_adam(m->theta, m->grad, m->adam_m, m->adam_v, m->ntheta, (float)lr, (float)beta1, (float)beta2, (float)eps,
+              bc1, bc2, st);
+  refresh_derived(m, st);
+  return DP_OK;
+}
+
 int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const double* d_mass, const double* d_box,
               const int* d_atype, double dt, int nsteps, double* d_force, double* d_energy, double* d_virial,
               double* d_thermo, int use_graph, void* stream) {
@@ -947,6 +1080,7 @@ void dp_free(dp_model* m) {
   if (m->md_exec) cudaGraphExecDestroy(m->md_exec);
   if (m->md_graph) cudaGraphDestroy(m->md_graph);
   if (m->d_md_counter) cudaFree(m->d_md_counter);
+  if (m->t_buf) cudaFree(m->t_buf);
   delete m;
 }
 

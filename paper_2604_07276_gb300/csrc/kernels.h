@@ -136,12 +136,27 @@ struct DescArgs {
 void launch_desc_fwd(const DescArgs& a, cudaStream_t st);
 void launch_desc_bwd(const DescArgs& a, cudaStream_t st);
 
-void launch_energy_head(const float* H, int n, int width, const float* w_out, float b_out, float out_scale,
+void launch_energy_head(const float* H, int n, int width, const float* w_out, const float* b_out, float out_scale,
                         const float* ebias, const int* atype, float* e, cudaStream_t st);
 // dZ = dH * (1 - t^2) with t = Hcur - Hprev (Hprev may be null: t = Hcur)
 void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, float* dZ, long long count,
                      cudaStream_t st);
 void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream_t st);
+
+// --- training of the student (train.cu, simt.cu)
+bool launch_embed_wgrad(const EmbedArgs& a, const int* widths, float* grad, const float* scale, cudaStream_t st);
+void launch_wgrad(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int I, int O, int N,
+                  const float* scale, cudaStream_t st);
+void launch_colsum(const float* B, int ldb, float* c, int O, int N, const float* scale, float factor, cudaStream_t st);
+void launch_head_bias_grad(const int* atype, int n, float* g_ebias, float* g_bout, const float* scale, float out_scale,
+                           cudaStream_t st);
+void launch_train_prep(int n, const double* energy, double e_ref, const double* force, const double* force_ref,
+                       const double* coord, double pe, double pf, double h, double* coord_plus, double* coord_minus,
+                       double* loss, float* scales, cudaStream_t st);
+void launch_adam(float* theta, float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
+                 float bc1, float bc2, cudaStream_t st);
+void launch_transpose(const float* W, int R, int C, float* WT, cudaStream_t st);
+void launch_scale_copy(const float* src, float* dst, int n, float s, cudaStream_t st);
 
 // --- velocity-Verlet MD (md.cu)
 void launch_verlet_drift(int n, double dt, const double* mass, const double* f, double* v, double* x, cudaStream_t st);

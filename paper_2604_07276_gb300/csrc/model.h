@@ -108,7 +108,24 @@ struct dp_model {
   int nt, td, sel, axis, nattn, A, nfit, m1, fit_in;
   int emb[3], fit[3];
   double rcut, rcs, shift, ln_eps, out_scale;
-  float b_out;
+  float* d_b_out = nullptr;  // output bias times out_scale (device scalar)
+  // trainable parameters as one FP32 vector: the embedding net (packed W0 b0
+  // W1 b1 W2 b2), the fitting layers (W b per layer), the output layer (w,
+  // b) and the per-type energy bias.  The forward kernels read the embedding,
+  // fitting and bias weights from it; transposes and scaled copies are
+  // refreshed after every update.
+  float* theta = nullptr;
+  int ntheta = 0;
+  std::vector<int> off_fitW, off_fitb;
+  int off_wout = 0, off_bout = 0, off_ebias = 0;
+  float* grad = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  int adam_t = 0;
+  const float* grad_scale = nullptr;  // non-null: the next evaluation adds scale * dE/dtheta to grad
+  float* d_scales = nullptr;          // [4]: 1, energy-loss scale, +/- force-loss scales
+  double* t_buf = nullptr;            // training scratch: energy, virial, loss, forces, displaced coords
+  int t_cap = 0;
   // device weights
   float *emb_packed, *Gt, *tebd, *davg, *dstd, *ebias, *w_out;
   std::vector<AttnLayerW> attn;

@@ -7,6 +7,8 @@
 
 namespace dpa1 {
 
+static int sm_count();
+
 // ----------------------------------------------------------------- FP32 GEMM
 // 64x64 tile, K step 16, 256 threads, 4x4 outputs per thread.
 template <int EPI>
@@ -263,6 +265,122 @@ __global__ void __launch_bounds__(ETHREADS) k_embed_bwd(EmbedArgs a) {
     for (int p = 0; p < E0; ++p) dx += sm[S::DH1 + r * (E0 + 1) + p];
     a.dR[(base + r) * 4] += dx;
   }
+}
+
+// Weight gradients of the embedding net, scale * dE/d(W0 b0 W1 b1 W2 b2)
+// (packed layout), accumulated over every neighbour row.  Persistent CTAs
+// walk the 64-row blocks, keep per-CTA sums in shared memory and add them to
+// `grad` once at the end.
+template <int E0, int E1, int E2>
+__global__ void __launch_bounds__(ETHREADS) k_embed_wgrad(EmbedArgs a, float* grad, const float* scale) {
+  using Lw = EmbedLayout<E0, E1, E2>;
+  using S = EmbedSmem<E0, E1, E2>;
+  extern __shared__ float sm[];
+  float* acc = sm + S::TOTAL;
+  for (int t = threadIdx.x; t < Lw::TOTAL; t += ETHREADS) acc[t] = 0.f;
+  for (int blk = blockIdx.x; blk < 2 * a.n; blk += gridDim.x) {
+    const int atom = blk >> 1, part = blk & 1;
+    const int r0 = part * EROWS;
+    const int cnt = max(0, min(EROWS, a.nnei[atom] - r0));
+    if (cnt == 0) continue;  // uniform over the CTA
+    const size_t base = (size_t)atom * NP + r0;
+    __syncthreads();
+    embed_load<E0, E1, E2>(sm, a, base, cnt);
+    embed_forward<E0, E1, E2>(sm, cnt);
+    const int ti = a.atype[atom];
+    for (int idx = threadIdx.x; idx < EROWS * E2; idx += ETHREADS) {
+      const int r = idx / E2, c = idx % E2;
+      float dz = 0.f;
+      if (r < cnt) {
+        const int tj = a.atype[a.nlist[base + r]];
+        const float g = a.dG0[(base + r) * a.m1 + c] * (1.f + a.Gt[((size_t)ti * a.ntypes + tj) * E2 + c]);
+        const float t = tanhf(sm[S::Z + r * (E2 + 1) + c]);
+        dz = g * (1.f - t * t);
+      }
+      sm[S::Z + r * (E2 + 1) + c] = dz;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
+      const int r = idx / E1, b = idx % E1;
+      float sacc = 0.f;
+      if (r < cnt) {
+        const float* dz = sm + S::Z + r * (E2 + 1);
+        const float* w2 = sm + S::W2 + b * S::P2;
+        for (int c = 0; c < E2; ++c) sacc = fmaf(w2[c], dz[c], sacc);
+        if (E2 == E1 || E2 == 2 * E1) {
+          const int tj = a.atype[a.nlist[base + r]];
+          const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
+          const float* dg = a.dG0 + (base + r) * a.m1;
+          for (int c = b; c < E2; c += E1) sacc += dg[c] * (1.f + gt[c]);
+        }
+      }
+      sm[S::DH2 + r * (E1 + 1) + b] = sacc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
+      const int r = idx / E1, b = idx % E1;
+      const float t = sm[S::H2 + r * (E1 + 1) + b] - skip_in<E0, E1>(sm + S::H1 + r * (E0 + 1), b);
+      sm[S::DZ2 + r * (E1 + 1) + b] = r < cnt ? sm[S::DH2 + r * (E1 + 1) + b] * (1.f - t * t) : 0.f;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < EROWS * E0; idx += ETHREADS) {
+      const int r = idx / E0, q = idx % E0;
+      float sacc = 0.f;
+      if (r < cnt) {
+        const float* dz2 = sm + S::DZ2 + r * (E1 + 1);
+        const float* w1 = sm + S::W1 + q * E1;
+        for (int b = 0; b < E1; ++b) sacc = fmaf(w1[b], dz2[b], sacc);
+        if (E1 == E0 || E1 == 2 * E0)
+          for (int b = q; b < E1; b += E0) sacc += sm[S::DH2 + r * (E1 + 1) + b];
+        const float h1 = sm[S::H1 + r * (E0 + 1) + q];
+        sacc *= (1.f - h1 * h1);  // dz1
+      }
+      sm[S::DH1 + r * (E0 + 1) + q] = sacc;
+    }
+    __syncthreads();
+    // accumulate this block's weight gradients (rows >= cnt are zero everywhere)
+    for (int t = threadIdx.x; t < Lw::TOTAL; t += ETHREADS) {
+      float g = 0.f;
+      if (t < Lw::B0) {
+        for (int r = 0; r < EROWS; ++r) g = fmaf(sm[S::X + r], sm[S::DH1 + r * (E0 + 1) + t], g);
+      } else if (t < Lw::W1) {
+        for (int r = 0; r < EROWS; ++r) g += sm[S::DH1 + r * (E0 + 1) + (t - Lw::B0)];
+      } else if (t < Lw::B1) {
+        const int q = (t - Lw::W1) / E1, b = (t - Lw::W1) % E1;
+        for (int r = 0; r < EROWS; ++r) g = fmaf(sm[S::H1 + r * (E0 + 1) + q], sm[S::DZ2 + r * (E1 + 1) + b], g);
+      } else if (t < Lw::W2) {
+        for (int r = 0; r < EROWS; ++r) g += sm[S::DZ2 + r * (E1 + 1) + (t - Lw::B1)];
+      } else if (t < Lw::B2) {
+        const int b = (t - Lw::W2) / E2, c = (t - Lw::W2) % E2;
+        for (int r = 0; r < EROWS; ++r) g = fmaf(sm[S::H2 + r * (E1 + 1) + b], sm[S::Z + r * (E2 + 1) + c], g);
+      } else {
+        for (int r = 0; r < EROWS; ++r) g += sm[S::Z + r * (E2 + 1) + (t - Lw::B2)];
+      }
+      acc[t] += g;
+    }
+  }
+  __syncthreads();
+  const float sc = *scale;
+  for (int t = threadIdx.x; t < Lw::TOTAL; t += ETHREADS) atomicAdd(&grad[t], sc * acc[t]);
+}
+
+template <int E0, int E1, int E2>
+static void embed_wgrad_launch(const EmbedArgs& a, float* grad, const float* scale, cudaStream_t st) {
+  using Lw = EmbedLayout<E0, E1, E2>;
+  using S = EmbedSmem<E0, E1, E2>;
+  if (a.n == 0) return;
+  const size_t smem = sizeof(float) * (S::TOTAL + Lw::TOTAL);
+  cudaFuncSetAttribute(k_embed_wgrad<E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = std::min(2 * a.n, 2 * sm_count());
+  k_embed_wgrad<E0, E1, E2><<<grid, ETHREADS, smem, st>>>(a, grad, scale);
+  note_launch();
+}
+
+bool launch_embed_wgrad(const EmbedArgs& a, const int* w, float* grad, const float* scale, cudaStream_t st) {
+  if (w[0] == 25 && w[1] == 50 && w[2] == 100) { embed_wgrad_launch<25, 50, 100>(a, grad, scale, st); return true; }
+  if (w[0] == 16 && w[1] == 32 && w[2] == 64) { embed_wgrad_launch<16, 32, 64>(a, grad, scale, st); return true; }
+  if (w[0] == 32 && w[1] == 64 && w[2] == 128) { embed_wgrad_launch<32, 64, 128>(a, grad, scale, st); return true; }
+  return false;
 }
 
 template <int E0, int E1, int E2>
@@ -795,7 +913,7 @@ void launch_desc_bwd(const DescArgs& a, cudaStream_t st) {
 
 // ------------------------------------------------------------ fitting head
 __global__ void k_energy_head(const float* __restrict__ H, int n, int width, const float* __restrict__ w,
-                              float b, float out_scale, const float* __restrict__ ebias,
+                              const float* __restrict__ bptr, float out_scale, const float* __restrict__ ebias,
                               const int* __restrict__ atype, float* __restrict__ e) {
   const int atom = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -803,10 +921,10 @@ __global__ void k_energy_head(const float* __restrict__ H, int n, int width, con
   float s = 0.f;
   for (int c = lane; c < width; c += 32) s = fmaf(H[(size_t)atom * width + c], w[c], s);
   s = warp_sum(s);
-  if (lane == 0) e[atom] = out_scale * (s + b) + ebias[atype[atom]];
+  if (lane == 0) e[atom] = out_scale * (s + *bptr) + ebias[atype[atom]];
 }
 
-void launch_energy_head(const float* H, int n, int width, const float* w_out, float b_out, float out_scale,
+void launch_energy_head(const float* H, int n, int width, const float* w_out, const float* b_out, float out_scale,
                         const float* ebias, const int* atype, float* e, cudaStream_t st) {
   if (n == 0) return;
   k_energy_head<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, st>>>(H, n, width, w_out, b_out, out_scale,

@@ -1,0 +1,95 @@
+"""The distilled student (a model without attention) trained with the
+library's kernels: its loss gradient against the FP64 oracle, a training
+run against the full model's forces, and MD with the full-model check."""
+
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import OracleModel, energy_force_virial
+from oracle.student import loss_and_grad
+
+from gpu_helpers import weight_file
+
+pytestmark = pytest.mark.gpu
+
+
+def _student(p, seed=3, bias=0.1):
+    cfg = synth.STUDENT_CONFIG
+    w = synth.make_weights(cfg, seed=seed, bias_scale=bias)
+    return cfg, w, p.DPA1(weight_file(cfg, w, f"student{seed}_{bias}"), precision="fp32")
+
+
+def test_student_loss_gradient_matches_oracle(default_model):
+    import torch
+    import paper_2604_07276_gb300 as p
+
+    cfg_t, w_t, om_t = default_model
+    coord, atype, box = synth.water_box(0)
+    E_ref, _, F_ref, _ = energy_force_virial(om_t, coord, box, atype)
+    cfg, w, m = _student(p)
+    L, lE, lF, g_ref = loss_and_grad(OracleModel.from_numpy(cfg, w), coord, box, atype, E_ref, F_ref)
+    c = torch.tensor(coord, device="cuda")
+    b = torch.tensor(p.box9(box), device="cuda")
+    t = torch.tensor(atype, dtype=torch.int32, device="cuda")
+    fr = torch.tensor(F_ref, device="cuda")
+    loss = torch.zeros(3, dtype=torch.float64, device="cuda")
+    m.reserve(len(coord))
+    m.zero_grad()
+    m.train_frame(c, b, t, E_ref, fr, loss, fd_h=1e-3)
+    torch.cuda.synchronize()
+    m.status()
+    g = m.get_grad().astype(np.float64)
+    lo = loss.cpu().numpy()
+    assert abs(lo[0] - L) < 1e-5 * max(1.0, L)
+    assert abs(lo[1] - lE) < 1e-5 * max(1.0, lE) and abs(lo[2] - lF) < 1e-5 * max(1.0, lF)
+    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rel < 5e-3, rel
+    m.close()
+
+
+def test_student_training_and_fallback_md(lib=None):
+    import torch
+    import paper_2604_07276_gb300 as p
+    from paper_2604_07276_gb300 import md, student
+
+    tcfg = synth.DEFAULT_CONFIG
+    teacher = p.DPA1(weight_file(tcfg, synth.make_weights(tcfg, 0), "default"), precision="fp32")
+    systems = [synth.water_box(s) for s in range(3)]
+    frames = student.teacher_frames(teacher, systems, synth.MASSES, n_traj=2, steps=16, every=4, dt=0.25,
+                                    temperature=100.0, seed=1)
+    held = student.teacher_frames(teacher, [synth.water_box(7)], synth.MASSES, n_traj=1, steps=8, every=4, dt=0.25,
+                                  temperature=100.0, seed=2)
+    cfg, w, s = _student(p, seed=4, bias=0.0)
+    before = student.force_rmse(s, held)
+    hist = student.train(s, frames, epochs=40, batch=8, lr0=3e-3, lr_end=3e-4)
+    after = student.force_rmse(s, held)
+    assert hist[-5:, 0].mean() < 0.5 * hist[:5, 0].mean(), (hist[:5, 0], hist[-5:, 0])
+    assert after < 0.7 * before, (before, after)
+    # MD with the full-model check: a tight threshold forces fallbacks, a loose one none
+    coord, atype, box = synth.water_box(0)
+    vel = synth.maxwell_boltzmann(atype, 100.0, seed=11)
+    st1 = md.MDState(coord, vel, synth.MASSES[atype], box, atype)
+    used_s, used_t, checks = student.md_with_fallback(s, teacher, st1, nsteps=40, dt=0.25, check_every=10,
+                                                      threshold=1e-6)
+    assert used_t == 4 and used_s == 0
+    st2 = md.MDState(coord, vel, synth.MASSES[atype], box, atype)
+    used_s, used_t, checks = student.md_with_fallback(s, teacher, st2, nsteps=40, dt=0.25, check_every=10,
+                                                      threshold=1e6)
+    assert used_s == 4 and used_t == 0
+    # the student's step is cheaper than the full model's
+    big = synth.lattice_system(4000, seed=5)
+    times = {}
+    for name, mdl in (("teacher", teacher), ("student", s)):
+        stb = md.MDState(big[0], np.zeros_like(big[0]), synth.MASSES[big[1]], big[2], big[1])
+        md.run(mdl, stb, dt=0.25, nsteps=2, graph=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        md.run(mdl, stb, dt=0.25, nsteps=10, graph=True)
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t0
+    assert times["student"] < 0.5 * times["teacher"], times
+    teacher.close()
+    s.close()
