@@ -58,4 +58,4 @@ def loss_and_grad(model: OracleModel, coord, box, atype, e_ref: float, f_ref, pe
     L = lE + lF
     grads = torch.autograd.grad(L, [leaves[k] for k in names])
     g = np.concatenate([gi.detach().numpy().ravel() for gi in grads])
-    return float(L), float(lE), float(lF), g
+    return float(L.detach()), float(lE.detach()), float(lF.detach()), g

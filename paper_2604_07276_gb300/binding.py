@@ -246,7 +246,7 @@ class DPA1:
     def zero_grad(self, stream=None) -> None:
         _check(self.lib.dp_zero_grad(self.h, stream))
 
-    def train_frame(self, coord, box, atype, e_ref: float, force_ref, loss, pe=1.0, pf=1.0, fd_h=1e-3, stream=None):
+    def train_frame(self, coord, box, atype, e_ref: float, force_ref, loss, pe=1.0, pf=1.0, fd_h=1e-2, stream=None):
         """``dp_train_frame`` on CUDA tensors; ``loss`` is a float64 [3] tensor."""
         import torch
 

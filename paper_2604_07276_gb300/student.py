@@ -60,7 +60,7 @@ def _maxwell(atype, masses_of, temperature, rng):
 
 
 def train(student: DPA1, frames: Sequence[Frame], epochs: int, batch: int = 16, lr0: float = 1e-3,
-          lr_end: float = 1e-5, pe: float = 1.0, pf: float = 1.0, fd_h: float = 1e-3, seed: int = 0):
+          lr_end: float = 1e-5, pe: float = 1.0, pf: float = 1.0, fd_h: float = 1e-2, seed: int = 0):
     """Adam on mini-batches of frames (gradient = mean over the batch); the
     learning rate decays exponentially from lr0 to lr_end.  Returns the mean
     loss of every batch."""
