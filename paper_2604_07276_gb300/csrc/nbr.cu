@@ -129,6 +129,9 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
   const int ci = cell_of[i];
   const int cx = ci % g.nc[0], cy = (ci / g.nc[0]) % g.nc[1], cz = ci / (g.nc[0] * g.nc[1]);
   const int ox = g.nc[0] >= 3 ? 1 : 0, oy = g.nc[1] >= 3 ? 1 : 0, oz = g.nc[2] >= 3 ? 1 : 0;
+  const float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
+  const float iLf[3] = {1.0f / Lf[0], 1.0f / Lf[1], 1.0f / Lf[2]};
+  const float rc2_screen = (float)rc2 * 1.0001f + 1e-4f;
   int cnt = 0;
   for (int dz = -oz; dz <= oz; ++dz)
     for (int dy = -oy; dy <= oy; ++dy)
@@ -145,11 +148,23 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
           int j = -1;
           if (t < e) {
             j = cell_atoms[t];
-            double ddx = mic(__dsub_rn(coord[3 * j], xi), g.L[0]);
-            double ddy = mic(__dsub_rn(coord[3 * j + 1], yi), g.L[1]);
-            double ddz = mic(__dsub_rn(coord[3 * j + 2], zi), g.L[2]);
-            d2 = sqdist(ddx, ddy, ddz);
-            hit = (j != i) && (d2 < rc2);
+            const double ex = __dsub_rn(coord[3 * j], xi);
+            const double ey = __dsub_rn(coord[3 * j + 1], yi);
+            const double ez = __dsub_rn(coord[3 * j + 2], zi);
+            // FP32 screen: its distance is within ~1e-6 relative of the FP64
+            // one, so a pair rejected with this margin is never a neighbour
+            // (where the two pick different images, both distances exceed
+            // L/2 > rcut).  Survivors are decided exactly in FP64.
+            const float fx = (float)ex - Lf[0] * rintf((float)ex * iLf[0]);
+            const float fy = (float)ey - Lf[1] * rintf((float)ey * iLf[1]);
+            const float fz = (float)ez - Lf[2] * rintf((float)ez * iLf[2]);
+            if (j != i && fx * fx + fy * fy + fz * fz < rc2_screen) {
+              double ddx = mic(ex, g.L[0]);
+              double ddy = mic(ey, g.L[1]);
+              double ddz = mic(ez, g.L[2]);
+              d2 = sqdist(ddx, ddy, ddz);
+              hit = d2 < rc2;
+            }
           }
           unsigned bal = __ballot_sync(0xffffffffu, hit);
           int pos = cnt + __popc(bal & ((1u << lane) - 1u));

@@ -10,59 +10,80 @@ namespace dpa1 {
 static int sm_count();
 
 // ----------------------------------------------------------------- FP32 GEMM
-// 64x64 tile, K step 16, 256 threads, 4x4 outputs per thread.
+// 128x128 tile, K step 8, 256 threads with 8x8 outputs each (two 4x4
+// quadrants 64 apart), shared-memory double buffering.
 template <int EPI>
 __global__ void __launch_bounds__(256)
-k_sgemm(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb, const float* __restrict__ bias,
-        const float* __restrict__ R, int ldr, float* __restrict__ C, int ldc, int M, int N, int K) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const long long m0 = (long long)blockIdx.x * 64;
-  const int n0 = blockIdx.y * 64;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  const int ar = threadIdx.x >> 2, ak = (threadIdx.x & 3) * 4;
-  const int bk = threadIdx.x >> 4, bn = (threadIdx.x & 15) * 4;
-  for (int k0 = 0; k0 < K; k0 += 16) {
+k_sgemm128(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+           const float* __restrict__ bias, const float* __restrict__ R, int ldr, float* __restrict__ C, int ldc,
+           int M, int N, int K) {
+  __shared__ __align__(16) float As[2][8][128 + 4];
+  __shared__ __align__(16) float Bs[2][8][128 + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long long m0 = (long long)blockIdx.x * 128;
+  const int n0 = blockIdx.y * 128;
+  const int ar = tid >> 1, ak = (tid & 1) * 4;   // A: row, first k of 4
+  const int bk = tid >> 5, bc = (tid & 31) * 4;  // B: k, first column of 4
+  float ra[4], rb[4];
+  auto load = [&](int k0) {
     const long long gm = m0 + ar;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int gk = k0 + ak + q;
-      As[ak + q][ar] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
+      ra[q] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
     }
+    const int gk = k0 + bk;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int gk = k0 + bk, gn = n0 + bn + q;
-      Bs[bk][bn + q] = (gk < K && gn < N) ? B[(long long)gk * ldb + gn] : 0.f;
+      const int gn = n0 + bc + q;
+      rb[q] = (gk < K && gn < N) ? B[(long long)gk * ldb + gn] : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      float a[4], b[4];
+    for (int q = 0; q < 4; ++q) As[buf][ak + q][ar] = ra[q];
+    *reinterpret_cast<float4*>(&Bs[buf][bk][bc]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+  };
+  float acc[8][8];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    const bool more = k0 + 8 < K;
+    if (more) load(k0 + 8);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 8; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
-    __syncthreads();
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const long long m = m0 + ty * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const long long m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx * 4 + j;
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
       if (n >= N) continue;
-      float v = acc[i][j];
+      const float v = acc[i][j];
       float* c = C + m * ldc + n;
       if (EPI == EPI_BIAS) *c = v + (bias ? bias[n] : 0.f);
       if (EPI == EPI_TANH) *c = tanhf(v + (bias ? bias[n] : 0.f));
@@ -76,14 +97,15 @@ k_sgemm(const float* __restrict__ A, int lda, const float* __restrict__ B, int l
 void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bias, const float* R, int ldr,
               float* C, int ldc, int M, int N, int K, int epi, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+  dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + 127) / 128));
   switch (epi) {
-    case EPI_BIAS: k_sgemm<EPI_BIAS><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
-    case EPI_TANH: k_sgemm<EPI_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
-    case EPI_RES_TANH: k_sgemm<EPI_RES_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
-    case EPI_ACCUM: k_sgemm<EPI_ACCUM><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
-    default: k_sgemm<EPI_RES><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); note_launch(); break;
+    case EPI_BIAS: k_sgemm128<EPI_BIAS><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_TANH: k_sgemm128<EPI_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_RES_TANH: k_sgemm128<EPI_RES_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_ACCUM: k_sgemm128<EPI_ACCUM><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    default: k_sgemm128<EPI_RES><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
   }
+  note_launch();
 }
 
 // ------------------------------------------------------------ embedding net

@@ -816,12 +816,14 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__
       for (int i = 0; i < 32; i += 4) {
         const int c = 32 * blk + i;
         if (c < EMB_E2) {
+          const float4 g4 = *reinterpret_cast<const float4*>(gt + c);
+          const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
           float4 o;
           float* op = &o.x;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int cc = c + q;
-            op[q] = rv ? (h2[cc % EMB_E1] + tanhf(z[i + q] + a.b2[cc])) * (1.f + gt[cc]) : 0.f;
+            op[q] = rv ? (h2[cc % EMB_E1] + tanhf(z[i + q] + a.b2[cc])) * (1.f + gq[q]) : 0.f;
           }
           *reinterpret_cast<float4*>(out + c) = o;
         }
@@ -876,16 +878,26 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
       float z[32];
       tmem_ld32(tm + lane_off + 64 + 32 * blk, z);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int c = 32 * blk + i;
-        float dz = 0.f;
-        if (c < EMB_E2 && rv) {
-          const float g = dg[c] * (1.f + gt[c]);
-          const float t = tanhf(z[i] + a.b2[c]);
-          dz = g * (1.f - t * t);
-          dh2[c % EMB_E1] += g;
+      for (int i = 0; i < 32; i += 4) {
+        const int c0q = 32 * blk + i;
+        float gq[4] = {0.f, 0.f, 0.f, 0.f};
+        if (c0q < EMB_E2 && rv) {
+          const float4 d4 = *reinterpret_cast<const float4*>(dg + c0q);
+          const float4 t4 = *reinterpret_cast<const float4*>(gt + c0q);
+          gq[0] = d4.x * (1.f + t4.x); gq[1] = d4.y * (1.f + t4.y);
+          gq[2] = d4.z * (1.f + t4.z); gq[3] = d4.w * (1.f + t4.w);
         }
-        z[i] = dz;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = c0q + q;
+          float dz = 0.f;
+          if (c < EMB_E2 && rv) {
+            const float t = tanhf(z[i + q] + a.b2[c]);
+            dz = gq[q] * (1.f - t * t);
+            dh2[c % EMB_E1] += gq[q];
+          }
+          z[i + q] = dz;
+        }
       }
       store16<false>(sDZ3h, row, 32 * blk, 128, z);
       store16<false>(sDZ3h, row, 32 * blk + 16, 128, z + 16);
