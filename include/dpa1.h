@@ -179,7 +179,8 @@ DP_API int dp_inspect_weights(const char* weights_path, int* ints16, double* dbl
 
 /* Diagnostics: copy the named internal device buffer of the last call to
  * host memory (at most bytes bytes).  Names: "nlist", "env", "G0", "G1",
- * "G2", "D", "e", "g".  Returns the number of bytes copied, or a negative
+ * "G2", "D", "e", "g".  "G<l>" is returned as [rows][m1] row-major whatever
+ * the internal layout.  Returns the number of bytes copied, or a negative
  * dp_status. */
 DP_API long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t bytes);
 

@@ -351,6 +351,7 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
   da.R = ws.R; da.G = ws.G[L]; da.nnei = ws.nnei; da.atype = atype; da.tebd = m->tebd;
   da.n = n; da.m1 = m1; da.axis = m->axis; da.tebd_dim = m->td; da.sel = m->sel; da.fit_in = m->fit_in;
   da.T = ws.T; da.X = ws.X; da.dX = ws.dX; da.dG = ws.dG; da.dR = ws.dR;
+  da.cq = m->precision != DP_PREC_FP32 ? 1 : 0;  // the tensor-core path's layout
   launch_desc_fwd(da, st);
   prof_mark(m, "desc_fwd", st);
   // a8: fitting forward
@@ -827,6 +828,19 @@ long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t by
   if (!src) return fail(DP_ERR_ARG, "unknown buffer name");
   sz = std::min(sz, bytes);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(DP_ERR_CUDA, "sync failed");
+  if (s[0] == 'G' && m->precision != DP_PREC_FP32) {
+    // the tensor-core path keeps G column-quad interleaved per atom: return it row-major
+    const size_t m1 = (size_t)m->m1, full = rows * m1;
+    std::vector<float> raw(full), out(full);
+    if (cudaMemcpy(raw.data(), src, full * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(DP_ERR_CUDA, "copy failed");
+    for (size_t atom = 0; atom < n; ++atom)
+      for (int r = 0; r < NP; ++r)
+        for (size_t c = 0; c < m1; ++c)
+          out[(atom * NP + r) * m1 + c] = raw[atom * NP * m1 + cq_off(r, (int)c)];
+    memcpy(host_dst, out.data(), sz);
+    return (long long)sz;
+  }
   if (cudaMemcpy(host_dst, src, sz, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(DP_ERR_CUDA, "copy failed");
   return (long long)sz;
 }

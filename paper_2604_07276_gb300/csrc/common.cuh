@@ -9,6 +9,15 @@ namespace dpa1 {
 // Rows reserved per centre atom: the neighbour cap sel (<= 128) padded to one
 // 128-row tile, so that every per-atom matrix has a fixed 128-row shape.
 constexpr int NP = 128;
+// Per-atom [NP][W] FP32 matrices of the tensor-core path (the layer inputs
+// G_l and dE/dG) are stored column-quad interleaved: the 4 columns
+// 4q..4q+3 of a row are contiguous and the NP rows of one column quad follow
+// each other, so that one thread per row reading or writing 16 bytes makes a
+// warp access 512 contiguous bytes.  The atom block keeps the size NP * W.
+__host__ __device__ __forceinline__ size_t cq_off(int r, int c) {
+  return ((size_t)(c >> 2) * NP + (size_t)r) * 4 + (size_t)(c & 3);
+}
+
 // Candidate capacity of the neighbour search per centre (before the sel cap).
 constexpr int NBR_CAP = 256;
 // Capacity of the reverse neighbour list per atom (centres that list it).

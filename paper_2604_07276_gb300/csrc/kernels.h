@@ -132,6 +132,7 @@ struct DescArgs {
   const float* dX;  // bwd
   float* dG;        // bwd [rows][m1]
   float* dR;        // bwd [rows][4] (written)
+  int cq;           // G and dG column-quad interleaved per atom (else row-major)
 };
 void launch_desc_fwd(const DescArgs& a, cudaStream_t st);
 void launch_desc_bwd(const DescArgs& a, cudaStream_t st);

@@ -848,14 +848,40 @@ __global__ void k_desc_fwd(DescArgs a) {
   const int nn = a.nnei[atom];
   const size_t base = (size_t)atom * NP;
   const float inv_sel = 1.0f / (float)a.sel;
-  for (int c = threadIdx.x; c < a.m1; c += blockDim.x) {
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-    for (int s = 0; s < nn; ++s) {
-      const float4 r = reinterpret_cast<const float4*>(a.R)[base + s];
-      const float gv = a.G[(base + s) * a.m1 + c];
-      t0 = fmaf(r.x, gv, t0); t1 = fmaf(r.y, gv, t1); t2 = fmaf(r.z, gv, t2); t3 = fmaf(r.w, gv, t3);
+  if (a.cq) {
+    // a warp per column quad, its lanes over the rows
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float4* G4 = reinterpret_cast<const float4*>(a.G + base * a.m1);
+    const float4* R4 = reinterpret_cast<const float4*>(a.R) + base;
+    for (int q = warp; q < a.m1 / 4; q += nw) {
+      float t[4][4] = {};
+      for (int s = lane; s < nn; s += 32) {
+        const float4 r = R4[s];
+        const float4 g = G4[(size_t)q * NP + s];
+        const float rr[4] = {r.x, r.y, r.z, r.w}, gg[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) t[c][k] = fmaf(rr[c], gg[k], t[c][k]);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float v = warp_sum(t[c][k]);
+          if (lane == 0) Ts[c * a.m1 + 4 * q + k] = v * inv_sel;
+        }
     }
-    Ts[c] = t0 * inv_sel; Ts[a.m1 + c] = t1 * inv_sel; Ts[2 * a.m1 + c] = t2 * inv_sel; Ts[3 * a.m1 + c] = t3 * inv_sel;
+  } else {
+    for (int c = threadIdx.x; c < a.m1; c += blockDim.x) {
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      for (int s = 0; s < nn; ++s) {
+        const float4 r = reinterpret_cast<const float4*>(a.R)[base + s];
+        const float gv = a.G[(base + s) * a.m1 + c];
+        t0 = fmaf(r.x, gv, t0); t1 = fmaf(r.y, gv, t1); t2 = fmaf(r.z, gv, t2); t3 = fmaf(r.w, gv, t3);
+      }
+      Ts[c] = t0 * inv_sel; Ts[a.m1 + c] = t1 * inv_sel; Ts[2 * a.m1 + c] = t2 * inv_sel; Ts[3 * a.m1 + c] = t3 * inv_sel;
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < 4 * a.m1; t += blockDim.x) a.T[(size_t)atom * 4 * a.m1 + t] = Ts[t];
@@ -895,6 +921,44 @@ __global__ void k_desc_bwd(DescArgs a) {
     dTs[t] = v * inv_sel;
   }
   __syncthreads();
+  if (a.cq) {
+    // dG in column quads (consecutive threads -> consecutive rows), zero on padding
+    float4* dG4 = reinterpret_cast<float4*>(a.dG + base * m1);
+    const float4* R4 = reinterpret_cast<const float4*>(a.R) + base;
+    for (int idx = threadIdx.x; idx < NP * (m1 / 4); idx += blockDim.x) {
+      const int q = idx / NP, s = idx % NP;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s < nn) {
+        const float4 r = R4[s];
+        float* vp = &v.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int p = 4 * q + k;
+          vp[k] = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
+        }
+      }
+      dG4[idx] = v;
+    }
+    // dR rows: a thread per row
+    const float4* G4 = reinterpret_cast<const float4*>(a.G + base * m1);
+    for (int s = threadIdx.x; s < NP; s += blockDim.x) {
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+      if (s < nn) {
+        for (int q = 0; q < m1 / 4; ++q) {
+          const float4 g = G4[(size_t)q * NP + s];
+          const float gg[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int p = 4 * q + k;
+            d0 = fmaf(gg[k], dTs[p], d0); d1 = fmaf(gg[k], dTs[m1 + p], d1);
+            d2 = fmaf(gg[k], dTs[2 * m1 + p], d2); d3 = fmaf(gg[k], dTs[3 * m1 + p], d3);
+          }
+        }
+      }
+      reinterpret_cast<float4*>(a.dR)[base + s] = make_float4(d0, d1, d2, d3);
+    }
+    return;
+  }
   // dG rows (all NP rows; zero on padding)
   for (long long idx = threadIdx.x; idx < (long long)NP * m1; idx += blockDim.x) {
     const int s = (int)(idx / m1), p = (int)(idx % m1);

@@ -41,14 +41,14 @@ constexpr int KS_M1 = 7;          // K-steps covering the M1 = 100 (<= 112) inpu
 struct LayerArgs {
   const float* Gin;        // [rows][m1] layer input
   float* Gout;             // fwd: [rows][m1] layer output
-  __nv_bfloat16* yhat;     // [rows][YLD] normalised LayerNorm input (fwd writes, bwd reads)
+  __nv_bfloat16* yhat;     // normalised LayerNorm input, [NP][yld] per atom in 8-column groups (fwd writes, bwd reads)
   float* rstd;             // [rows]
   float* dG;               // bwd: in dE/dG_{l+1}, out dE/dG_l (in place)
   float* dgeo;             // bwd: [rows][4] += (d rhat, d w)
   float* scratch;          // bwd: per-CTA column partials
   const float* rw;         // [rows][4] (rhat, w)
   const int* nnei;
-  int n, m1;
+  int n, m1, yld;          // yld = m1 rounded up to a multiple of 8
   const uint4* wimg;       // swizzled weight image of this layer
   float scale, shift, eps;
   int* err;
@@ -60,7 +60,11 @@ struct LayerArgs {
   float beta[128];
 };
 
-constexpr int YLD = 104;  // row stride (elements) of yhat: 208 bytes, 16-byte aligned
+// G_l, G_{l+1} and dE/dG are column-quad interleaved per atom (cq_off);
+// yhat likewise in groups of 8 bf16 columns: element (r, c) of an atom at
+// ((c / 8) * NP + r) * 8 + c % 8.  A warp's per-row 16-byte accesses are then
+// 512 contiguous bytes.
+__host__ __device__ constexpr int yhat_ld(int m1) { return (m1 + 7) & ~7; }
 
 struct Sync {
   uint64_t* bar;
@@ -113,22 +117,21 @@ __device__ __forceinline__ void store_row64(uint8_t* tile, int r, int c0, const 
   }
 }
 
-// Load row r of an FP32 [rows][m1] matrix, columns c0..c0+63 (zero past m1).
-__device__ __forceinline__ void load_row64(const float* src, int m1, int c0, float* v) {
+// Load row r, columns c0..c0+63 (zero past m1), of an atom's column-quad
+// interleaved FP32 block.
+__device__ __forceinline__ void load_cq64(const float* blk, int m1, int r, int c0, float* v) {
+  const float4* b4 = reinterpret_cast<const float4*>(blk);
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int c = c0 + 4 * q;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < m1) x = *reinterpret_cast<const float4*>(src + c);  // m1 % 4 == 0
+    if (c < m1) x = b4[(c >> 2) * NP + r];  // m1 % 4 == 0
     v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
   }
 }
 
 // 64 TMEM columns of this thread's row (two 32-column loads).
-__device__ __forceinline__ void tmem_row64(uint32_t taddr, float* v) {
-  tmem_ld32(taddr, v);
-  tmem_ld32(taddr + 32, v + 32);
-}
+__device__ __forceinline__ void tmem_row64(uint32_t taddr, float* v) { tmem_ld64(taddr, v); }
 
 // Issue D = sum over K-steps of A * B for one 128 x N block.
 template <bool F16>
@@ -149,6 +152,13 @@ __device__ __forceinline__ float pair_sum(float* xch, int half, int row, float v
   const float o = xch[(half ^ 1) * 128 + row];
   __syncthreads();
   return v + o;
+}
+__device__ __forceinline__ float2 pair_sum2(float2* xch, int half, int row, float2 v) {
+  xch[half * 128 + row] = v;
+  __syncthreads();
+  const float2 o = xch[(half ^ 1) * 128 + row];
+  __syncthreads();
+  return make_float2(v.x + o.x, v.y + o.y);
 }
 __device__ __forceinline__ float pair_max(float* xch, int half, int row, float v) {
   xch[half * 128 + row] = v;
@@ -175,10 +185,27 @@ __device__ __forceinline__ float reduce_scatter32(float* v) {
   return v[0];
 }
 
+// Bring the per-row inputs of centre atom `atom` (if it exists) into L2 ahead
+// of its turn: one thread, bulk prefetches.
+__device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool bwd) {
+  if (atom >= a.n) return;
+  const size_t base = (size_t)atom * NP;
+  prefetch_l2(a.Gin + base * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
+  prefetch_l2(a.rw + base * 4, (uint32_t)(NP * 4 * sizeof(float)));
+  if (bwd) {
+    prefetch_l2(a.dG + base * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
+    prefetch_l2(a.yhat + base * a.yld, (uint32_t)(NP * a.yld * sizeof(__nv_bfloat16)));
+    prefetch_l2(a.rstd + base, (uint32_t)(NP * sizeof(float)));
+  }
+}
+
 // ------------------------------------------------------------------ forward
 // Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K,224K), then w[128],
-// rhat[128][3] and the barrier.  Wo is streamed per atom into a free slot;
-// the half-row exchange borrows the first 1 KB of a slot that is free.
+// rhat[128][3] and the barriers.  Wo is streamed per atom into slot D by a
+// bulk asynchronous copy; the half-row exchange borrows the first 1 KB of a
+// slot that is free.  TMEM columns: [Q K V] accumulators 0-383 (S, O reuse
+// 0-127, Y 128-239) and the FP32 layer input kept at 384-511 for the
+// residual.
 constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_SLOT_D = 3 * TILE, F_W = 4 * TILE;
 constexpr int F_SMALL = 7 * TILE;
 constexpr int F_SMEM = F_SMALL + 2048 + 64;
@@ -201,7 +228,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sWv = sWk + TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* bar_ld = bar + 1;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, half = warp >> 2;
@@ -212,6 +240,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
     mbar_init(bar, 1);
+    mbar_init(bar_ld, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -222,17 +251,23 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
   const uint4* wo_img = a.wimg + 3 * TILE / 16;
   Sync sy{bar, 0u, a.err};
+  Sync sl{bar_ld, 0u, a.err};
+  if (issuer) prefetch_atom(a, blockIdx.x, false);
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
+    if (issuer) prefetch_atom(a, atom + gridDim.x, false);
     if (tid < 128) {
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
       s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float v[64];
-    // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B)
-    load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
+    // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B), and
+    // kept in TMEM for the residual
+    load_cq64(a.Gin + base * a.m1, a.m1, row, c0, v);
+    tmem_st32(tm + lane_off + 384 + c0, v);
+    tmem_st32(tm + lane_off + 384 + c0 + 32, v + 32);
     store_row64<F16>(sA, row, c0, v);
     if (F16) store_row64<F16, true>(sB, row, c0, v);
     handoff();
@@ -260,10 +295,10 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     }
     handoff();
     // S = Q K^T
-    if (issuer) mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
+    if (issuer) mma_block<F16>(tm + 0, tA, false, 128, tB, false, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
     // smooth softmax and gate: P -> slot B (+ P_lo -> slot A); Q and K are dead
-    tmem_row64(tm + lane_off + 384 + c0, v);
+    tmem_row64(tm + lane_off + 0 + c0, v);
     {
       float* xch = reinterpret_cast<float*>(sA);
       const bool rv = row < nn;
@@ -306,19 +341,16 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       }
     }
     commit_and_sync(sy, issuer);
-    {
-      // fetch this atom's copy of Wo while O leaves TMEM; O -> A, Wo -> D
-      uint4 wr[WO_TILE / 16 / NT];
-#pragma unroll
-      for (int q = 0; q < WO_TILE / 16 / NT; ++q) wr[q] = wo_img[q * NT + tid];
-      tmem_row64(tm + lane_off + 0 + c0, v);
-      store_row64<F16>(sA, row, c0, v);
-#pragma unroll
-      for (int q = 0; q < WO_TILE / 16 / NT; ++q) reinterpret_cast<uint4*>(sD)[q * NT + tid] = wr[q];
+    // Wo -> slot D (bulk copy, V_lo is dead) while O leaves TMEM -> A
+    if (issuer) {
+      mbar_expect_tx(bar_ld, WO_TILE);
+      bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
     }
+    tmem_row64(tm + lane_off + 0 + c0, v);
+    store_row64<F16>(sA, row, c0, v);
     handoff();
     // Y = O Wo
-    if (issuer) mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, 8, false);
+    if (issuer && sl.wait()) mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, 8, false);
     commit_and_sync(sy, issuer);
     // LayerNorm, residual
     {
@@ -342,27 +374,37 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       const float var = pair_sum(xch, half, row, s2) / (float)a.m1;
       const float rs = 1.0f / sqrtf(var + a.eps);
       const bool rv = row < nn;
-      const float* gin = a.Gin + (base + row) * a.m1;
-      float* gout = a.Gout + (base + row) * a.m1;
-      __nv_bfloat16* yh = a.yhat + (base + row) * YLD;
+      float4* gout = reinterpret_cast<float4*>(a.Gout + base * a.m1);
+      uint4* yh = reinterpret_cast<uint4*>(a.yhat + base * a.yld);
+      float gin[64];
+      tmem_row64(tm + lane_off + 384 + c0, gin);
 #pragma unroll
-      for (int i = 0; i < 64; i += 4) {
+      for (int i = 0; i < 64; i += 8) {
         const int c = c0 + i;
         if (c < a.m1) {
-          float4 g = *reinterpret_cast<const float4*>(gin + c);
-          float y0 = (v[i] - mean) * rs, y1 = (v[i + 1] - mean) * rs, y2 = (v[i + 2] - mean) * rs,
-                y3 = (v[i + 3] - mean) * rs;
-          if (rv) {
-            g.x += y0 * a.gamma[c] + a.beta[c];
-            g.y += y1 * a.gamma[c + 1] + a.beta[c + 1];
-            g.z += y2 * a.gamma[c + 2] + a.beta[c + 2];
-            g.w += y3 * a.gamma[c + 3] + a.beta[c + 3];
+          float y[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) y[k] = c + k < a.m1 ? (v[i + k] - mean) * rs : 0.f;
+#pragma unroll
+          for (int h = 0; h < 8; h += 4) {
+            const int cc = c + h;
+            if (cc < a.m1) {
+              float4 g = make_float4(gin[i + h], gin[i + h + 1], gin[i + h + 2], gin[i + h + 3]);
+              if (rv) {
+                g.x += y[h] * a.gamma[cc] + a.beta[cc];
+                g.y += y[h + 1] * a.gamma[cc + 1] + a.beta[cc + 1];
+                g.z += y[h + 2] * a.gamma[cc + 2] + a.beta[cc + 2];
+                g.w += y[h + 3] * a.gamma[cc + 3] + a.beta[cc + 3];
+              }
+              gout[(cc >> 2) * NP + row] = g;
+            }
           }
-          *reinterpret_cast<float4*>(gout + c) = g;
-          uint2 u;
-          u.x = pack_bf16(y0, y1);
-          u.y = pack_bf16(y2, y3);
-          *reinterpret_cast<uint2*>(yh + c) = u;
+          uint4 u;
+          u.x = pack_bf16(y[0], y[1]);
+          u.y = pack_bf16(y[2], y[3]);
+          u.z = pack_bf16(y[4], y[5]);
+          u.w = pack_bf16(y[6], y[7]);
+          yh[(c >> 3) * NP + row] = u;
         }
       }
       if (half == 0) a.rstd[base + row] = rs;
@@ -401,7 +443,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint8_t* sWv = sWk + TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + B_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* bar_ld = bar + 1;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, half = warp >> 2;
@@ -414,6 +457,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
     mbar_init(bar, 1);
+    mbar_init(bar_ld, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -423,59 +467,81 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
   const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
   Sync sy{bar, 0u, a.err};
+  Sync sl{bar_ld, 0u, a.err};
   const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + 3 * TILE;
+  if (issuer) prefetch_atom(a, blockIdx.x, true);
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     const bool rv = row < nn;
+    if (issuer) {  // Wo -> slot D (bulk copy); the next atom's inputs -> L2
+      mbar_expect_tx(bar_ld, WO_TILE);
+      bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
+      prefetch_atom(a, atom + gridDim.x, true);
+    }
+    const float rs = rv ? a.rstd[base + row] : 0.f;
     if (tid < 128) {
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
       s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float v[64];
-    // P0: G_l -> A, dY = LayerNorm adjoint of dZ -> C, Wo -> D
-    load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
+    // P0: G_l -> A (+ G_lo -> B), dY = LayerNorm adjoint of dZ -> C
+    load_cq64(a.Gin + base * a.m1, a.m1, row, c0, v);
     store_row64<F16>(sA, row, c0, v);
-    copy_image(sD, reinterpret_cast<const uint4*>(wo_img), WO_TILE);
+    if (F16) store_row64<F16, true>(sB, row, c0, v);
     {
-      float* xch = reinterpret_cast<float*>(sB);
-      const float* dz = a.dG + (base + row) * a.m1;
-      const __nv_bfloat16* yh = a.yhat + (base + row) * YLD;
+      float2* xch = reinterpret_cast<float2*>(sC);  // dY is stored after the exchange
+      const float4* dz4 = reinterpret_cast<const float4*>(a.dG + base * a.m1);
+      const uint4* yh8 = reinterpret_cast<const uint4*>(a.yhat + base * a.yld);
       float yv[64];
       float s1 = 0.f, s2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; i += 4) {
+      for (int i = 0; i < 64; i += 8) {
         const int c = c0 + i;
-        float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 y4 = g4;
+        float g[8], y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = y[k] = 0.f;
         if (c < a.m1 && rv) {
-          g4 = *reinterpret_cast<const float4*>(dz + c);
-          const uint2 yy = *reinterpret_cast<const uint2*>(yh + c);
-          const __nv_bfloat162 y01 = *reinterpret_cast<const __nv_bfloat162*>(&yy.x);
-          const __nv_bfloat162 y23 = *reinterpret_cast<const __nv_bfloat162*>(&yy.y);
-          y4 = make_float4(__low2float(y01), __high2float(y01), __low2float(y23), __high2float(y23));
-          g4.x *= a.gamma[c]; g4.y *= a.gamma[c + 1]; g4.z *= a.gamma[c + 2]; g4.w *= a.gamma[c + 3];
+          const uint4 yy = yh8[(c >> 3) * NP + row];
+          const uint32_t yw[4] = {yy.x, yy.y, yy.z, yy.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162*>(&yw[k]);
+            y[2 * k] = __low2float(p2);
+            y[2 * k + 1] = __high2float(p2);
+          }
+#pragma unroll
+          for (int h = 0; h < 8; h += 4) {
+            const int cc = c + h;
+            if (cc < a.m1) {
+              const float4 g4 = dz4[(cc >> 2) * NP + row];
+              g[h] = g4.x * a.gamma[cc];
+              g[h + 1] = g4.y * a.gamma[cc + 1];
+              g[h + 2] = g4.z * a.gamma[cc + 2];
+              g[h + 3] = g4.w * a.gamma[cc + 3];
+            }
+          }
         }
-        v[i] = g4.x; v[i + 1] = g4.y; v[i + 2] = g4.z; v[i + 3] = g4.w;
-        yv[i] = y4.x; yv[i + 1] = y4.y; yv[i + 2] = y4.z; yv[i + 3] = y4.w;
-        s1 += (g4.x + g4.y) + (g4.z + g4.w);
-        s2 += (g4.x * y4.x + g4.y * y4.y) + (g4.z * y4.z + g4.w * y4.w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          v[i + k] = g[k];
+          yv[i + k] = y[k];
+        }
+        s1 += ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
+        s2 += ((g[0] * y[0] + g[1] * y[1]) + (g[2] * y[2] + g[3] * y[3])) +
+              ((g[4] * y[4] + g[5] * y[5]) + (g[6] * y[6] + g[7] * y[7]));
       }
-      s1 = pair_sum(xch, half, row, s1) / (float)a.m1;
-      s2 = pair_sum(xch, half, row, s2) / (float)a.m1;
-      const float rs = rv ? a.rstd[base + row] : 0.f;
+      const float2 ss = pair_sum2(xch, half, row, make_float2(s1, s2));
+      s1 = ss.x / (float)a.m1;
+      s2 = ss.y / (float)a.m1;
 #pragma unroll
       for (int i = 0; i < 64; ++i) v[i] = rv ? rs * (v[i] - s1 - yv[i] * s2) : 0.f;
       store_row64<F16>(sC, row, c0, v);
     }
-    if (F16) {  // the exchange in slot B is finished (barrier inside pair_sum)
-      load_row64(a.Gin + (base + row) * a.m1, a.m1, c0, v);
-      store_row64<F16, true>(sB, row, c0, v);
-    }
     handoff();
     // M0: [Q K V] = G Wqkv (+ G_lo Wqkv) ; dO = dY Wo^T (Wo tile as MN-major)
-    if (issuer) {
+    if (issuer && sl.wait()) {
       mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
       mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
       mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
@@ -652,14 +718,22 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place
     {
       tmem_row64(tm + lane_off + 384 + c0, v);
-      float* dg = a.dG + (base + row) * a.m1;
+      float4* dg4 = reinterpret_cast<float4*>(a.dG + base * a.m1);
 #pragma unroll
-      for (int i = 0; i < 64; i += 4) {
-        const int c = c0 + i;
-        if (c < a.m1) {
-          float4 g = *reinterpret_cast<const float4*>(dg + c);
-          g.x += v[i]; g.y += v[i + 1]; g.z += v[i + 2]; g.w += v[i + 3];
-          *reinterpret_cast<float4*>(dg + c) = g;
+      for (int h = 0; h < 64; h += 32) {  // all loads of a 32-column block before its stores
+        float4 g[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + h + 4 * q;
+          g[q] = c < a.m1 ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + h + 4 * q, i = h + 4 * q;
+          if (c < a.m1) {
+            g[q].x += v[i]; g[q].y += v[i + 1]; g[q].z += v[i + 2]; g[q].w += v[i + 3];
+            dg4[(c >> 2) * NP + row] = g[q];
+          }
         }
       }
     }
@@ -693,8 +767,8 @@ struct EmbedTcArgs {
   const int* nnei;
   const int* atype;
   const float* Gt;        // [ntypes][ntypes][E2]
-  float* G0;              // fwd out [rows][E2]
-  const float* dG0;       // bwd in
+  float* G0;              // fwd out, column-quad interleaved per atom
+  const float* dG0;       // bwd in, column-quad interleaved per atom
   float* dR;              // bwd: dR[:,0] +=
   const uint4* wimg;      // W1/W2 hi/lo tiles
   int n, ntypes;
@@ -807,7 +881,7 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__
     const size_t rowg = (size_t)atom * NP + row;
     embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
     const float* gt = a.Gt + ((size_t)a.atype[atom] * a.ntypes + (rv ? a.atype[a.nlist[rowg]] : 0)) * EMB_E2;
-    float* out = a.G0 + rowg * EMB_E2;
+    float4* out = reinterpret_cast<float4*>(a.G0 + (size_t)atom * NP * EMB_E2);
 #pragma unroll
     for (int blk = 0; blk < 4; ++blk) {
       float z[32];
@@ -825,7 +899,7 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__
             const int cc = c + q;
             op[q] = rv ? (h2[cc % EMB_E1] + tanhf(z[i + q] + a.b2[cc])) * (1.f + gq[q]) : 0.f;
           }
-          *reinterpret_cast<float4*>(out + c) = o;
+          out[(c >> 2) * NP + row] = o;
         }
       }
     }
@@ -869,7 +943,7 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
     embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
     // dZ3 = g (1 - t3^2), g = dG0 (1 + Gt); skip part of dH2 kept in dh2
     const float* gt = a.Gt + ((size_t)a.atype[atom] * a.ntypes + (rv ? a.atype[a.nlist[rowg]] : 0)) * EMB_E2;
-    const float* dg = a.dG0 + rowg * EMB_E2;
+    const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
     float dh2[EMB_E1];
 #pragma unroll
     for (int b = 0; b < EMB_E1; ++b) dh2[b] = 0.f;
@@ -882,7 +956,7 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
         const int c0q = 32 * blk + i;
         float gq[4] = {0.f, 0.f, 0.f, 0.f};
         if (c0q < EMB_E2 && rv) {
-          const float4 d4 = *reinterpret_cast<const float4*>(dg + c0q);
+          const float4 d4 = dg[(c0q >> 2) * NP + row];
           const float4 t4 = *reinterpret_cast<const float4*>(gt + c0q);
           gq[0] = d4.x * (1.f + t4.x); gq[1] = d4.y * (1.f + t4.y);
           gq[2] = d4.z * (1.f + t4.z); gq[3] = d4.w * (1.f + t4.w);
@@ -950,6 +1024,32 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+// Row-major [rows][m1] <-> column-quad interleaved per atom (to_cq = 1: row-major
+// src to interleaved dst), one float4 per thread in the interleaved order.
+__global__ void k_relayout(const float4* __restrict__ src, float4* __restrict__ dst, long long total4, int m1,
+                           int to_cq) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total4) return;
+  const int q4 = m1 / 4;
+  const long long per_atom = (long long)NP * q4;
+  const long long atom = i / per_atom;
+  const int rem = (int)(i % per_atom), q = rem / NP, r = rem % NP;
+  const long long rm = atom * per_atom + (long long)r * q4 + q;
+  if (to_cq)
+    dst[i] = src[rm];
+  else
+    dst[rm] = src[i];
+}
+
+void relayout(const float* src, float* dst, int n, int m1, bool to_cq, cudaStream_t st) {
+  const long long total4 = (long long)n * NP * (m1 / 4);
+  if (total4 == 0) return;
+  k_relayout<<<(unsigned)((total4 + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4*>(src),
+                                                               reinterpret_cast<float4*>(dst), total4, m1,
+                                                               to_cq ? 1 : 0);
+  note_launch();
 }
 
 int sm_count_dev(int dev) {
@@ -1081,9 +1181,11 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
 void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
   Workspace& ws = m->ws;
   const size_t rows = (size_t)cap * NP;
-  ws.tc.p[0] = a.take<__nv_bfloat16>(rows * YLD * (size_t)std::max(1, m->nattn));  // yhat per layer
+  ws.tc.p[0] = a.take<__nv_bfloat16>(rows * yhat_ld(m->m1) * (size_t)std::max(1, m->nattn));  // yhat per layer
   ws.tc.p[1] = a.take<float>(rows * (size_t)std::max(1, m->nattn));                // rstd per layer
   ws.tc.p[2] = a.take<float>((size_t)sm_count_dev(m->device) * SCRATCH_FLOATS);      // column partials
+  // row-major staging of G0 / dE/dG0 for the SIMT embedding net (nets other than 25-50-100)
+  ws.tc.p[3] = m->tcw.emb_W1_t ? nullptr : a.take<float>(rows * m->m1);
 }
 
 
@@ -1097,7 +1199,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     LayerArgs la{};
     la.Gin = ws.G[l];
     la.Gout = ws.G[l + 1];
-    la.yhat = reinterpret_cast<__nv_bfloat16*>(ws.tc.p[0]) + (size_t)l * rows * YLD;
+    la.yhat = reinterpret_cast<__nv_bfloat16*>(ws.tc.p[0]) + (size_t)l * rows * yhat_ld(m->m1);
     la.rstd = reinterpret_cast<float*>(ws.tc.p[1]) + (size_t)l * rows;
     la.dG = ws.dG;
     la.dgeo = ws.dgeo;
@@ -1106,6 +1208,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.nnei = ws.nnei;
     la.n = n;
     la.m1 = m->m1;
+    la.yld = yhat_ld(m->m1);
     la.wimg = reinterpret_cast<const uint4*>(f16 ? m->tcw.Wo_t[l] : m->tcw.Wqkv_t[l]);
     const TcWeights::Vectors& vec = m->tcw.vectors[l];
     memcpy(la.bqkv, vec.bqkv, sizeof(la.bqkv));
@@ -1120,8 +1223,9 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   };
   // embedding, then the attention layers forward
   EmbedArgs ea{};
+  float* rm_stage = reinterpret_cast<float*>(ws.tc.p[3]);
   ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m->m1;
-  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = rm_stage;
   const bool emb_tc = m->tcw.emb_W1_t != nullptr;
   EmbedTcArgs et{};
   if (emb_tc) {
@@ -1138,6 +1242,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     note_launch();
   } else {
     launch_embed_fwd(ea, m->emb, st);
+    relayout(rm_stage, ws.G[0], n, m->m1, true, st);
   }
   prof_mark(m, "embed_fwd", st);
   for (int l = 0; l < L && n > 0; ++l) {
@@ -1162,7 +1267,8 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     k_embed_tc_bwd<<<std::min(n, sm_count_dev(m->device)), 128, EMBB_SMEM, st>>>(et);
     note_launch();
   } else {
-    ea.dG0 = ws.dG;
+    relayout(ws.dG, rm_stage, n, m->m1, false, st);
+    ea.dG0 = rm_stage;
     ea.dR = ws.dR;
     launch_embed_bwd(ea, m->emb, st);
   }

@@ -127,3 +127,23 @@ def test_bf16_error_envelope(lib, default_model, water):
     rE, re, rF, rW = energy_force_virial(om, coord, box, atype)
     assert force_rmse(F, rF) < 0.1
     assert np.abs(e - re).max() < 0.03
+
+
+@pytest.mark.parametrize("attn_layers", [0, 1])
+def test_fp16x_other_embedding_net(lib, water, attn_layers):
+    """A 16-32-64 embedding net (run by the SIMT embedding kernels, whose
+    row-major G0 is re-laid for the tensor-core layers) with 0 or 1 attention
+    layers: relative force RMSE and per-atom energy against the oracle."""
+    from oracle import OracleModel
+
+    cfg = synth.ModelConfig(embed=(16, 32, 64), axis=8, attn_layers=attn_layers, fitting=(64, 64), out_scale=10.0)
+    w = synth.make_weights(cfg, seed=9, bias_scale=0.1, ln_scale=0.1, stats=True)
+    om = OracleModel.from_numpy(cfg, w)
+    m = lib.DPA1(weight_file(cfg, w, f"emb64_l{attn_layers}"), precision="fp16x")
+    coord, atype, box = water
+    E, F, W, e = m.compute(coord, box, atype, atom_energy=True)
+    rE, re, rF, rW = energy_force_virial(om, coord, box, atype)
+    rel = force_rmse(F, rF) / max(1e-12, float(np.sqrt(np.mean(rF ** 2))))
+    assert rel <= 5e-3, rel
+    assert np.abs(e - re).max() <= 1e-3 * max(1.0, np.abs(re).max())
+    m.close()
