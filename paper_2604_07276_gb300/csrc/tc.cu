@@ -43,6 +43,7 @@ struct LayerArgs {
   float* Gout;             // fwd: [rows][m1] layer output
   __nv_bfloat16* yhat;     // normalised LayerNorm input, [NP][yld] per atom in 8-column groups (fwd writes, bwd reads)
   float* rstd;             // [rows]
+  float2* smax;            // [rows] softmax row max and 1 / normaliser (fwd writes, bwd reads)
   float* dG;               // bwd: in dE/dG_{l+1}, out dE/dG_l (in place)
   float* dgeo;             // bwd: [rows][4] += (d rhat, d w)
   float* scratch;          // bwd: per-CTA column partials
@@ -196,6 +197,7 @@ __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool
     prefetch_l2(a.dG + base * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
     prefetch_l2(a.yhat + base * a.yld, (uint32_t)(NP * a.yld * sizeof(__nv_bfloat16)));
     prefetch_l2(a.rstd + base, (uint32_t)(NP * sizeof(float)));
+    prefetch_l2(a.smax + base, (uint32_t)(NP * sizeof(float2)));
   }
 }
 
@@ -322,6 +324,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       }
       sum = pair_sum(xch, half, row, sum);  // ends with a barrier: slot A is free
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      if (half == 0) a.smax[base + row] = make_float2(mx, inv);
 #pragma unroll
       for (int i = 0; i < 64; ++i) {
         const float4 kk = s_key[c0 + i];
@@ -481,6 +484,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       prefetch_atom(a, atom + gridDim.x, true);
     }
     const float rs = rv ? a.rstd[base + row] : 0.f;
+    const float2 sst = rv ? a.smax[base + row] : make_float2(0.f, 0.f);
     if (tid < 128) {
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
       s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -571,27 +575,19 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       mma_block<F16>(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
-    // P2: softmax and its adjoint in 32-key passes that reload S and dP from
-    // TMEM (max; normaliser and sum_k A_jk dA_jk together; main pass); P ->
-    // slot C, dS -> TMEM over the consumed S columns
+    // P2: softmax adjoint in two sweeps over 32-key blocks that reload S and
+    // dP from TMEM (sum_k A_jk dA_jk; main pass), with the row max and
+    // normaliser the forward pass stored; P -> slot C, dS -> TMEM over the
+    // consumed S columns
     {
       float* xch = reinterpret_cast<float*>(sC);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
       const float4 kj = s_key[row];
       const float wj = kj.w;
       float t[32], u[32];
-      float mx = -INFINITY;
-#pragma unroll 1
-      for (int blk = 0; blk < 2; ++blk) {
-        tmem_ld32(tS + 32 * blk, t);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int k = c0 + 32 * blk + i;
-          if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_key[k].w));
-        }
-      }
-      mx = pair_max(xch, half, row, mx);
-      float sum = 0.f, wsum = 0.f;
+      // row max and 1 / normaliser of the forward pass (same S up to rounding)
+      const float mx = sst.x, inv = sst.y;
+      float wsum = 0.f;
 #pragma unroll 1
       for (int blk = 0; blk < 2; ++blk) {
         tmem_ld32(tS + 32 * blk, t);
@@ -604,14 +600,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
             const float ww = wj * kk.w;
             const float e = __expf((t[i] * a.scale + a.shift) * ww - mx);
             const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
-            sum += e;
             wsum += e * u[i] * ww * c;
           }
         }
       }
-      sum = pair_sum(xch, half, row, sum);
       wsum = pair_sum(xch, half, row, wsum);  // ends with a barrier: slot C is free
-      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
       const float tsum = wsum * inv;  // sum_k A_jk dA_jk
       float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
       float4* cp = reinterpret_cast<float4*>(colp) + quad * 128 + c0;
@@ -759,7 +752,8 @@ constexpr int EMB_TA = 128 * 64 * 2;    // activation tile: 128 rows x 64 cols
 constexpr int EMB_TD = 128 * 128 * 2;   // dZ3 tile: 128 rows x 128 cols
 constexpr int EMB_WIMG = 2 * EMB_T1 + 2 * EMB_T2;  // W1 hi, W1 lo, W2 hi, W2 lo
 constexpr int EMBF_SMEM = EMB_WIMG + 4 * EMB_TA + 64;
-constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + 2 * EMB_TD + 64;
+constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + 64;  // dZ3 tiles reuse the four activation tiles
+static_assert(2 * EMB_TD == 4 * EMB_TA, "the dZ3 hi / lo tiles fill the activation tiles");
 
 struct EmbedTcArgs {
   const float* R;
@@ -929,10 +923,12 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
   uint8_t* sW1l = sW1h + EMB_T1;
   uint8_t* sW2h = sW1l + EMB_T1;
   uint8_t* sW2l = sW2h + EMB_T2;
-  uint8_t* sDZ2h = sm + EMB_WIMG;  // the H1 tiles, dead after layer 2
-  uint8_t* sDZ2l = sDZ2h + EMB_TA;
-  uint8_t* sDZ3h = sm + EMB_WIMG + 4 * EMB_TA;
+  // the activation tiles are dead once Z3 = H2 W2 is in TMEM: dZ3 (hi, lo)
+  // takes all four, then dZ2 (hi, lo) the first two once dH2 is computed
+  uint8_t* sDZ3h = sm + EMB_WIMG;
   uint8_t* sDZ3l = sDZ3h + EMB_TD;
+  uint8_t* sDZ2h = sm + EMB_WIMG;
+  uint8_t* sDZ2l = sDZ2h + EMB_TA;
   Sync sy{bar, 0u, a.err};
   float h1[EMB_E0], h2[EMB_E1];
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
@@ -1183,6 +1179,7 @@ void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
   const size_t rows = (size_t)cap * NP;
   ws.tc.p[0] = a.take<__nv_bfloat16>(rows * yhat_ld(m->m1) * (size_t)std::max(1, m->nattn));  // yhat per layer
   ws.tc.p[1] = a.take<float>(rows * (size_t)std::max(1, m->nattn));                // rstd per layer
+  ws.tc.p[4] = a.take<float2>(rows * (size_t)std::max(1, m->nattn));               // softmax stats per layer
   ws.tc.p[2] = a.take<float>((size_t)sm_count_dev(m->device) * SCRATCH_FLOATS);      // column partials
   // row-major staging of G0 / dE/dG0 for the SIMT embedding net (nets other than 25-50-100)
   ws.tc.p[3] = m->tcw.emb_W1_t ? nullptr : a.take<float>(rows * m->m1);
@@ -1201,6 +1198,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.Gout = ws.G[l + 1];
     la.yhat = reinterpret_cast<__nv_bfloat16*>(ws.tc.p[0]) + (size_t)l * rows * yhat_ld(m->m1);
     la.rstd = reinterpret_cast<float*>(ws.tc.p[1]) + (size_t)l * rows;
+    la.smax = reinterpret_cast<float2*>(ws.tc.p[4]) + (size_t)l * rows;
     la.dG = ws.dG;
     la.dgeo = ws.dgeo;
     la.scratch = reinterpret_cast<float*>(ws.tc.p[2]);
@@ -1264,7 +1262,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     prof_mark(m, "attn_bwd_tc", st);
   }
   if (emb_tc && n > 0) {
-    k_embed_tc_bwd<<<std::min(n, sm_count_dev(m->device)), 128, EMBB_SMEM, st>>>(et);
+    k_embed_tc_bwd<<<std::min(n, 2 * sm_count_dev(m->device)), 128, EMBB_SMEM, st>>>(et);
     note_launch();
   } else {
     relayout(ws.dG, rm_stage, n, m->m1, false, st);
