@@ -31,7 +31,7 @@ using namespace tc;
 
 namespace {
 
-constexpr int NT = 256;           // threads per CTA
+constexpr int NT = 512;           // threads per CTA of the layer kernels
 constexpr int TILE = 32768;       // 128 x 128 bf16 SW128 tile
 constexpr int WO_ROWS = 112;      // Wo tile: M1 = 100 output rows padded to 112
 constexpr int WO_TILE = 2 * WO_ROWS * 128;  // 28 KB
@@ -96,16 +96,16 @@ __device__ __forceinline__ void handoff() {
 
 __device__ __forceinline__ void copy_image(uint8_t* dst, const uint4* src, int bytes) {
   uint4* d = reinterpret_cast<uint4*>(dst);
-  for (int i = threadIdx.x; i < bytes / 16; i += NT) d[i] = src[i];
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = src[i];
 }
 
-// Store 64 FP32 values (cols c0..c0+63 of row r) as the 16-bit operand type
+// Store 32 FP32 values (cols c0..c0+31 of row r) as the 16-bit operand type
 // into an SW128 tile; LO = true stores the rounding residue v - round16(v)
 // instead (the low part of a two-term split).
 template <bool F16, bool LO = false>
-__device__ __forceinline__ void store_row64(uint8_t* tile, int r, int c0, const float* v) {
+__device__ __forceinline__ void store_row32(uint8_t* tile, int r, int c0, const float* v) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < 4; ++q) {
     float x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = LO ? v[8 * q + i] - round16<F16>(v[8 * q + i]) : v[8 * q + i];
@@ -118,21 +118,18 @@ __device__ __forceinline__ void store_row64(uint8_t* tile, int r, int c0, const 
   }
 }
 
-// Load row r, columns c0..c0+63 (zero past m1), of an atom's column-quad
+// Load row r, columns c0..c0+31 (zero past m1), of an atom's column-quad
 // interleaved FP32 block.
-__device__ __forceinline__ void load_cq64(const float* blk, int m1, int r, int c0, float* v) {
+__device__ __forceinline__ void load_cq32(const float* blk, int m1, int r, int c0, float* v) {
   const float4* b4 = reinterpret_cast<const float4*>(blk);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
+  for (int q = 0; q < 8; ++q) {
     const int c = c0 + 4 * q;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c < m1) x = b4[(c >> 2) * NP + r];  // m1 % 4 == 0
     v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
   }
 }
-
-// 64 TMEM columns of this thread's row (two 32-column loads).
-__device__ __forceinline__ void tmem_row64(uint32_t taddr, float* v) { tmem_ld64(taddr, v); }
 
 // Issue D = sum over K-steps of A * B for one 128 x N block.
 template <bool F16>
@@ -146,35 +143,48 @@ __device__ __forceinline__ void mma_block(uint32_t d, uint32_t a, bool a_mn, int
   }
 }
 
-// Exchange one float between the two threads (halves) that own row r.
-__device__ __forceinline__ float pair_sum(float* xch, int half, int row, float v) {
-  xch[half * 128 + row] = v;
-  __syncthreads();
-  const float o = xch[(half ^ 1) * 128 + row];
-  __syncthreads();
-  return v + o;
-}
-__device__ __forceinline__ float2 pair_sum2(float2* xch, int half, int row, float2 v) {
-  xch[half * 128 + row] = v;
-  __syncthreads();
-  const float2 o = xch[(half ^ 1) * 128 + row];
-  __syncthreads();
-  return make_float2(v.x + o.x, v.y + o.y);
-}
-__device__ __forceinline__ float pair_max(float* xch, int half, int row, float v) {
-  xch[half * 128 + row] = v;
-  __syncthreads();
-  const float o = xch[(half ^ 1) * 128 + row];
-  __syncthreads();
-  return fmaxf(v, o);
-}
+// Row exchange among the four threads (column quarters) that own a row.  The
+// four warps of one TMEM lane quadrant meet on their own named barrier; the
+// values are parked in the row's own 128-byte line of chunk 0 of an SW128
+// tile that only this row's threads write afterwards, at a word offset that
+// differs between the 32 rows of a warp (no bank conflicts).
+struct RowXchg {
+  uint8_t* line;  // this row's line in the parking tile
+  int part, lane, quad;
+  __device__ RowXchg(uint8_t* tile, int row, int part_, int lane_, int quad_)
+      : line(tile + (row >> 3) * 1024 + (row & 7) * 128), part(part_), lane(lane_), quad(quad_) {}
+  __device__ void sync() const { asm volatile("bar.sync %0, 128;" ::"r"(1 + quad) : "memory"); }
+  __device__ float* slot(int p) const { return reinterpret_cast<float*>(line) + ((lane + 8 * p) & 31); }
+  __device__ float2* slot2(int p) const { return reinterpret_cast<float2*>(line) + ((lane + 4 * p) & 15); }
+  __device__ float sum(float v) const {
+    *slot(part) = v;
+    sync();
+    const float r = (*slot(0) + *slot(1)) + (*slot(2) + *slot(3));
+    sync();
+    return r;
+  }
+  __device__ float max(float v) const {
+    *slot(part) = v;
+    sync();
+    const float r = fmaxf(fmaxf(*slot(0), *slot(1)), fmaxf(*slot(2), *slot(3)));
+    sync();
+    return r;
+  }
+  __device__ float2 sum2(float2 v) const {
+    *slot2(part) = v;
+    sync();
+    const float2 a = *slot2(0), b = *slot2(1), c = *slot2(2), d = *slot2(3);
+    sync();
+    return make_float2((a.x + b.x) + (c.x + d.x), (a.y + b.y) + (c.y + d.y));
+  }
+};
 
-// Sum over the 32 lanes of a warp of 32 values per lane; lane l returns the
-// sum of value l (a butterfly reduce-scatter, fixed order).
-__device__ __forceinline__ float reduce_scatter32(float* v) {
+// Sum over the 32 lanes of a warp of 16 values per lane; lanes l and l + 16
+// return the sum of value l % 16 (butterfly reduce-scatter, fixed order).
+__device__ __forceinline__ float reduce_scatter16(float* v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
+  for (int w = 8; w >= 1; w >>= 1) {
     const bool up = (lane & w) != 0;
 #pragma unroll
     for (int i = 0; i < w; ++i) {
@@ -183,7 +193,7 @@ __device__ __forceinline__ float reduce_scatter32(float* v) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
     }
   }
-  return v[0];
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 // Bring the per-row inputs of centre atom `atom` (if it exists) into L2 ahead
@@ -202,12 +212,12 @@ __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool
 }
 
 // ------------------------------------------------------------------ forward
-// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K,224K), then w[128],
-// rhat[128][3] and the barriers.  Wo is streamed per atom into slot D by a
-// bulk asynchronous copy; the half-row exchange borrows the first 1 KB of a
-// slot that is free.  TMEM columns: [Q K V] accumulators 0-383 (S, O reuse
-// 0-127, Y 128-239) and the FP32 layer input kept at 384-511 for the
-// residual.
+// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K,224K), then the
+// per-key (rhat, w) table and the barriers.  Wo is streamed per atom into
+// slot D by a bulk asynchronous copy.  TMEM columns: [Q K V] accumulators
+// 0-383 (S and O reuse 0-127, Y 128-239) and the FP32 layer input kept at
+// 384-511 for the residual.  Thread layout: warp w owns TMEM lane quadrant
+// w % 4 (rows 32 (w % 4) .. +31) and column quarter w / 4 (32 columns).
 constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_SLOT_D = 3 * TILE, F_W = 4 * TILE;
 constexpr int F_SMALL = 7 * TILE;
 constexpr int F_SMEM = F_SMALL + 2048 + 64;
@@ -234,9 +244,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, part = warp >> 2;
   const int row = quad * 32 + lane;
-  const int c0 = half * 64;
+  const int c0 = part * 32;
   const bool issuer = tid == 0;
 
   copy_image(sWq, a.wimg, 3 * TILE);
@@ -264,14 +274,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
       s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float v[64];
+    float v[32];
     // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B), and
     // kept in TMEM for the residual
-    load_cq64(a.Gin + base * a.m1, a.m1, row, c0, v);
+    load_cq32(a.Gin + base * a.m1, a.m1, row, c0, v);
     tmem_st32(tm + lane_off + 384 + c0, v);
-    tmem_st32(tm + lane_off + 384 + c0 + 32, v + 32);
-    store_row64<F16>(sA, row, c0, v);
-    if (F16) store_row64<F16, true>(sB, row, c0, v);
+    store_row32<F16>(sA, row, c0, v);
+    if (F16) store_row32<F16, true>(sB, row, c0, v);
     handoff();
     // [Q K V] = G Wqkv (+ G_lo Wqkv)
     if (issuer) {
@@ -288,51 +297,51 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     // Q -> A, K -> B, V -> C (+ V_lo -> D), with biases
 #pragma unroll 1
     for (int which = 0; which < 3; ++which) {
-      tmem_row64(tm + lane_off + which * 128 + c0, v);
+      tmem_ld32(tm + lane_off + which * 128 + c0, v);
       const float* b = a.bqkv + which * 128 + c0;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) v[i] += b[i];
-      store_row64<F16>(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
-      if (F16 && which == 2) store_row64<F16, true>(sD, row, c0, v);
+      for (int i = 0; i < 32; ++i) v[i] += b[i];
+      store_row32<F16>(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
+      if (F16 && which == 2) store_row32<F16, true>(sD, row, c0, v);
     }
     handoff();
-    // S = Q K^T
+    // S = Q K^T -> TMEM [0,128)
     if (issuer) mma_block<F16>(tm + 0, tA, false, 128, tB, false, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
     // smooth softmax and gate: P -> slot B (+ P_lo -> slot A); Q and K are dead
-    tmem_row64(tm + lane_off + 0 + c0, v);
+    tmem_ld32(tm + lane_off + 0 + c0, v);
     {
-      float* xch = reinterpret_cast<float*>(sA);
+      const RowXchg xr(sA, row, part, lane, quad);
       const bool rv = row < nn;
       const float4 kj = s_key[row];
       const float wj = kj.w;
       float mx = -INFINITY;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
+      for (int i = 0; i < 32; ++i) {
         const int k = c0 + i;
         const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_key[k].w) : -INFINITY;
         v[i] = l;
         mx = fmaxf(mx, l);
       }
-      mx = pair_max(xch, half, row, mx);
+      mx = xr.max(mx);
       float sum = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
+      for (int i = 0; i < 32; ++i) {
         const float e = (v[i] == -INFINITY) ? 0.f : __expf(v[i] - mx);
         v[i] = e;
         sum += e;
       }
-      sum = pair_sum(xch, half, row, sum);  // ends with a barrier: slot A is free
+      sum = xr.sum(sum);
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
-      if (half == 0) a.smax[base + row] = make_float2(mx, inv);
+      if (part == 0) a.smax[base + row] = make_float2(mx, inv);
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
+      for (int i = 0; i < 32; ++i) {
         const float4 kk = s_key[c0 + i];
         const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
         v[i] = v[i] * inv * (wj * kk.w) * c;
       }
-      store_row64<F16>(sB, row, c0, v);
-      if (F16) store_row64<F16, true>(sA, row, c0, v);
+      store_row32<F16>(sB, row, c0, v);
+      if (F16) store_row32<F16, true>(sA, row, c0, v);
     }
     handoff();
     // O = P V (+ P_lo V + P V_lo)  (V as an MN-major operand)
@@ -349,40 +358,40 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       mbar_expect_tx(bar_ld, WO_TILE);
       bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
     }
-    tmem_row64(tm + lane_off + 0 + c0, v);
-    store_row64<F16>(sA, row, c0, v);
+    tmem_ld32(tm + lane_off + 0 + c0, v);
+    store_row32<F16>(sA, row, c0, v);
     handoff();
-    // Y = O Wo
+    // Y = O Wo -> TMEM [128, 240)
     if (issuer && sl.wait()) mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, 8, false);
     commit_and_sync(sy, issuer);
     // LayerNorm, residual
     {
-      float* xch = reinterpret_cast<float*>(sB);  // P is dead
-      tmem_row64(tm + lane_off + 128 + c0, v);
+      const RowXchg xr(sB, row, part, lane, quad);  // P is dead
+      tmem_ld32(tm + lane_off + 128 + c0, v);
       float s1 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
+      for (int i = 0; i < 32; ++i) {
         const int c = c0 + i;
         v[i] = c < a.m1 ? v[i] + a.bo[c] : 0.f;
         s1 += v[i];
       }
-      const float mean = pair_sum(xch, half, row, s1) / (float)a.m1;
+      const float mean = xr.sum(s1) / (float)a.m1;
       float s2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
+      for (int i = 0; i < 32; ++i) {
         const int c = c0 + i;
         const float d = c < a.m1 ? v[i] - mean : 0.f;
         s2 += d * d;
       }
-      const float var = pair_sum(xch, half, row, s2) / (float)a.m1;
+      const float var = xr.sum(s2) / (float)a.m1;
       const float rs = 1.0f / sqrtf(var + a.eps);
       const bool rv = row < nn;
       float4* gout = reinterpret_cast<float4*>(a.Gout + base * a.m1);
       uint4* yh = reinterpret_cast<uint4*>(a.yhat + base * a.yld);
-      float gin[64];
-      tmem_row64(tm + lane_off + 384 + c0, gin);
+      float gin[32];
+      tmem_ld32(tm + lane_off + 384 + c0, gin);
 #pragma unroll
-      for (int i = 0; i < 64; i += 8) {
+      for (int i = 0; i < 32; i += 8) {
         const int c = c0 + i;
         if (c < a.m1) {
           float y[8];
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
           yh[(c >> 3) * NP + row] = u;
         }
       }
-      if (half == 0) a.rstd[base + row] = rs;
+      if (part == 0) a.rstd[base + row] = rs;
     }
     fence_before_sync();
     __syncthreads();
@@ -422,13 +431,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 }
 
 // ----------------------------------------------------------------- backward
-// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K, 224K), w, rhat, bar.
-// Wo is streamed per atom into slot D.  The half-row exchange borrows the
-// first 1 KB of whichever slot is free at that point.
+// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K, 224K), per-key table,
+// barriers.  Wo is streamed per atom into slot D.  Same thread layout as the
+// forward kernel.
 constexpr int B_SLOT_A = 0, B_SLOT_B = TILE, B_SLOT_C = 2 * TILE, B_SLOT_D = 3 * TILE, B_W = 4 * TILE;
 constexpr int B_SMALL = 4 * TILE + 3 * TILE;
 constexpr int B_SMEM = B_SMALL + 2048 + 64;
-constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 2 * 128 * 4;  // per CTA
+constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 4 * 128 * 4;  // per CTA: column parts per quadrant, row parts per quarter
 
 template <bool F16>
 __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ LayerArgs a) {
@@ -450,12 +459,12 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, part = warp >> 2;
   const int row = quad * 32 + lane;
-  const int c0 = half * 64;
+  const int c0 = part * 32;
   const bool issuer = tid == 0;
   float* colp = a.scratch + (size_t)blockIdx.x * SCRATCH_FLOATS;  // [quad][128 keys][4]
-  float* rowp = colp + 4 * 128 * 4;                                // [half][128 rows][4]
+  float* rowp = colp + 4 * 128 * 4;                                // [part][128 rows][4]
 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
@@ -489,19 +498,19 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
       s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float v[64];
+    float v[32];
     // P0: G_l -> A (+ G_lo -> B), dY = LayerNorm adjoint of dZ -> C
-    load_cq64(a.Gin + base * a.m1, a.m1, row, c0, v);
-    store_row64<F16>(sA, row, c0, v);
-    if (F16) store_row64<F16, true>(sB, row, c0, v);
+    load_cq32(a.Gin + base * a.m1, a.m1, row, c0, v);
+    store_row32<F16>(sA, row, c0, v);
+    if (F16) store_row32<F16, true>(sB, row, c0, v);
     {
-      float2* xch = reinterpret_cast<float2*>(sC);  // dY is stored after the exchange
+      const RowXchg xr(sC, row, part, lane, quad);  // dY is stored after the exchange
       const float4* dz4 = reinterpret_cast<const float4*>(a.dG + base * a.m1);
       const uint4* yh8 = reinterpret_cast<const uint4*>(a.yhat + base * a.yld);
-      float yv[64];
+      float yv[32];
       float s1 = 0.f, s2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; i += 8) {
+      for (int i = 0; i < 32; i += 8) {
         const int c = c0 + i;
         float g[8], y[8];
 #pragma unroll
@@ -536,12 +545,12 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
         s2 += ((g[0] * y[0] + g[1] * y[1]) + (g[2] * y[2] + g[3] * y[3])) +
               ((g[4] * y[4] + g[5] * y[5]) + (g[6] * y[6] + g[7] * y[7]));
       }
-      const float2 ss = pair_sum2(xch, half, row, make_float2(s1, s2));
+      const float2 ss = xr.sum2(make_float2(s1, s2));
       s1 = ss.x / (float)a.m1;
       s2 = ss.y / (float)a.m1;
 #pragma unroll
-      for (int i = 0; i < 64; ++i) v[i] = rv ? rs * (v[i] - s1 - yv[i] * s2) : 0.f;
-      store_row64<F16>(sC, row, c0, v);
+      for (int i = 0; i < 32; ++i) v[i] = rv ? rs * (v[i] - s1 - yv[i] * s2) : 0.f;
+      store_row32<F16>(sC, row, c0, v);
     }
     handoff();
     // M0: [Q K V] = G Wqkv (+ G_lo Wqkv) ; dO = dY Wo^T (Wo tile as MN-major)
@@ -560,13 +569,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     // P1: Q -> A, K -> B, V -> C, dO -> D
 #pragma unroll 1
     for (int which = 0; which < 4; ++which) {
-      tmem_row64(tm + lane_off + which * 128 + c0, v);
+      tmem_ld32(tm + lane_off + which * 128 + c0, v);
       if (which < 3) {
         const float* b = a.bqkv + which * 128 + c0;
 #pragma unroll
-        for (int i = 0; i < 64; ++i) v[i] += b[i];
+        for (int i = 0; i < 32; ++i) v[i] += b[i];
       }
-      store_row64<F16>(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
+      store_row32<F16>(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
     }
     handoff();
     // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
@@ -575,26 +584,24 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       mma_block<F16>(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
-    // P2: softmax adjoint in two sweeps over 32-key blocks that reload S and
-    // dP from TMEM (sum_k A_jk dA_jk; main pass), with the row max and
-    // normaliser the forward pass stored; P -> slot C, dS -> TMEM over the
-    // consumed S columns
+    // P2: softmax adjoint over this thread's 32 keys, with the row max and
+    // normaliser the forward pass stored: sum_k A_jk dA_jk first, then the
+    // main pass in two 16-key halves that reload S and dP from TMEM; P ->
+    // slot C, dS -> TMEM over the consumed S columns
     {
-      float* xch = reinterpret_cast<float*>(sC);  // V is dead after dP
+      const RowXchg xr(sC, row, part, lane, quad);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
       const float4 kj = s_key[row];
       const float wj = kj.w;
-      float t[32], u[32];
-      // row max and 1 / normaliser of the forward pass (same S up to rounding)
       const float mx = sst.x, inv = sst.y;
       float wsum = 0.f;
-#pragma unroll 1
-      for (int blk = 0; blk < 2; ++blk) {
-        tmem_ld32(tS + 32 * blk, t);
-        tmem_ld32(tP + 32 * blk, u);
+      {
+        float t[32], u[32];
+        tmem_ld32(tS, t);
+        tmem_ld32(tP, u);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int k = c0 + 32 * blk + i;
+          const int k = c0 + i;
           if (k < nn && rv) {
             const float4 kk = s_key[k];
             const float ww = wj * kk.w;
@@ -604,18 +611,18 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
           }
         }
       }
-      wsum = pair_sum(xch, half, row, wsum);  // ends with a barrier: slot C is free
+      wsum = xr.sum(wsum);  // ends with the quadrant's barrier: its rows of slot C are free
       const float tsum = wsum * inv;  // sum_k A_jk dA_jk
       float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
       float4* cp = reinterpret_cast<float4*>(colp) + quad * 128 + c0;
 #pragma unroll 1
-      for (int blk = 0; blk < 2; ++blk) {
-        tmem_ld32(tS + 32 * blk, t);
-        tmem_ld32(tP + 32 * blk, u);
-        float cw[32], dcv[32], pv[32];
+      for (int h = 0; h < 32; h += 16) {
+        float t[16], u[16], cw[16], dcv[16], pv[16];
+        tmem_ld16(tS + h, t);
+        tmem_ld16(tP + h, u);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int k = c0 + 32 * blk + i;
+        for (int i = 0; i < 16; ++i) {
+          const int k = c0 + h + i;
           float H = 0.f, dc = 0.f, P = 0.f, dS = 0.f;
           const float4 kk = s_key[k];
           if (k < nn && rv) {
@@ -638,36 +645,36 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
           t[i] = dS;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
           uint4 w4;
           w4.x = pack16<F16>(pv[8 * q + 0], pv[8 * q + 1]);
           w4.y = pack16<F16>(pv[8 * q + 2], pv[8 * q + 3]);
           w4.z = pack16<F16>(pv[8 * q + 4], pv[8 * q + 5]);
           w4.w = pack16<F16>(pv[8 * q + 6], pv[8 * q + 7]);
-          sw128_store8(sC, row, c0 + 32 * blk + 8 * q, 128, w4);
+          sw128_store8(sC, row, c0 + h + 8 * q, 128, w4);
         }
-        tmem_st32(tS + 32 * blk, t);  // dS over this block's consumed S columns
-        const float sw_ = reduce_scatter32(cw);
+        tmem_st16(tS + h, t);  // dS over this half's consumed S columns
+        const float sw_ = reduce_scatter16(cw);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * kj.x;
-        const float sx = reduce_scatter32(pv);
+        for (int i = 0; i < 16; ++i) pv[i] = dcv[i] * kj.x;
+        const float sx = reduce_scatter16(pv);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * kj.y;
-        const float sy_ = reduce_scatter32(pv);
+        for (int i = 0; i < 16; ++i) pv[i] = dcv[i] * kj.y;
+        const float sy_ = reduce_scatter16(pv);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) pv[i] = dcv[i] * kj.z;
-        const float sz = reduce_scatter32(pv);
-        cp[blk * 32 + lane] = make_float4(sx, sy_, sz, sw_);
+        for (int i = 0; i < 16; ++i) pv[i] = dcv[i] * kj.z;
+        const float sz = reduce_scatter16(pv);
+        if (lane < 16) cp[h + lane] = make_float4(sx, sy_, sz, sw_);
       }
-      // row parts of dE/dw_j and dE/drhat_j, per half
-      reinterpret_cast<float4*>(rowp)[half * 128 + row] = make_float4(rx, ry, rz, rw_);
+      // row parts of dE/dw_j and dE/drhat_j, per column quarter
+      reinterpret_cast<float4*>(rowp)[part * 128 + row] = make_float4(rx, ry, rz, rw_);
     }
     handoff();
     // M2: dV = P^T dO -> [128,256)
     if (issuer) mma_block<F16>(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
-    tmem_row64(tm + lane_off + 384 + c0, v);  // dS
-    store_row64<F16>(sC, row, c0, v);
+    tmem_ld32(tm + lane_off + 384 + c0, v);  // dS
+    store_row32<F16>(sC, row, c0, v);
     handoff();
     // M3: dQ = dS K -> [0,128) ; dK = dS^T Q -> [256,384)
     if (issuer) {
@@ -676,19 +683,21 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     }
     commit_and_sync(sy, issuer);
     // P4: dQ -> B, dK -> A, dV -> D ; dgeo of this atom
-    tmem_row64(tm + lane_off + 0 + c0, v);
-    store_row64<F16>(sB, row, c0, v);
-    tmem_row64(tm + lane_off + 256 + c0, v);
-    store_row64<F16>(sA, row, c0, v);
-    tmem_row64(tm + lane_off + 128 + c0, v);
-    store_row64<F16>(sD, row, c0, v);
+    tmem_ld32(tm + lane_off + 0 + c0, v);
+    store_row32<F16>(sB, row, c0, v);
+    tmem_ld32(tm + lane_off + 256 + c0, v);
+    store_row32<F16>(sA, row, c0, v);
+    tmem_ld32(tm + lane_off + 128 + c0, v);
+    store_row32<F16>(sD, row, c0, v);
     if (tid < 128) {
-      // key/row `tid`: row parts of both halves + column parts of the 4 quads
+      // key/row `tid`: row parts of the 4 quarters + column parts of the 4 quadrants
       const float4* rp = reinterpret_cast<const float4*>(rowp);
       const float4* cp = reinterpret_cast<const float4*>(colp);
-      float4 s = rp[tid];
-      const float4 s2 = rp[128 + tid];
-      s.x += s2.x; s.y += s2.y; s.z += s2.z; s.w += s2.w;
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < 4; ++q) {
+        const float4 r = rp[q * 128 + tid];
+        s.x += r.x; s.y += r.y; s.z += r.z; s.w += r.w;
+      }
       for (int q = 0; q < 4; ++q) {
         const float4 c = cp[q * 128 + tid];
         s.x += c.x; s.y += c.y; s.z += c.z; s.w += c.w;
@@ -710,23 +719,20 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     commit_and_sync(sy, issuer);
     // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place
     {
-      tmem_row64(tm + lane_off + 384 + c0, v);
+      tmem_ld32(tm + lane_off + 384 + c0, v);
       float4* dg4 = reinterpret_cast<float4*>(a.dG + base * a.m1);
+      float4 g[8];
 #pragma unroll
-      for (int h = 0; h < 64; h += 32) {  // all loads of a 32-column block before its stores
-        float4 g[8];
+      for (int q = 0; q < 8; ++q) {  // all loads before the stores
+        const int c = c0 + 4 * q;
+        g[q] = c < a.m1 ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + h + 4 * q;
-          g[q] = c < a.m1 ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + h + 4 * q, i = h + 4 * q;
-          if (c < a.m1) {
-            g[q].x += v[i]; g[q].y += v[i + 1]; g[q].z += v[i + 2]; g[q].w += v[i + 3];
-            dg4[(c >> 2) * NP + row] = g[q];
-          }
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + 4 * q, i = 4 * q;
+        if (c < a.m1) {
+          g[q].x += v[i]; g[q].y += v[i + 1]; g[q].z += v[i + 2]; g[q].w += v[i + 3];
+          dg4[(c >> 2) * NP + row] = g[q];
         }
       }
     }
