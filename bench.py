@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DPA-1 E+F atom-steps/s at 15,668 atoms, BF16 vs FP32, force RMSE vs FP64"
 NATOMS = 15668
-WORKLOAD = "solvated-protein-like periodic box, 15,668 atoms, jittered lattice at 0.1/A^3, seed 1"
+def workload(natoms):
+    return f"solvated-protein-like periodic box, {natoms:,} atoms, jittered lattice at 0.1/A^3, seed 1"
 MODEL = ("DPA-1 se_atten: 5 types, tebd 8, rcut 6.0/0.5 A, sel 120, embed [25,50,100], axis 16, "
          "2 gated attention layers x 128, fitting [240,240,240]")
 
@@ -54,7 +55,7 @@ def _args():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=3072, help="oracle centres timed for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
-    ap.add_argument("--md-steps", type=int, default=100, help="graph-captured velocity-Verlet steps to time (0: skip)")
+    ap.add_argument("--md-steps", type=int, default=1000, help="graph-captured velocity-Verlet steps to time (0: skip)")
     return ap.parse_args()
 
 
@@ -108,7 +109,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "atom-steps/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(dt for _, dt in vals) / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "model": MODEL, "natoms": a.natoms},
+        "config": {"workload": workload(a.natoms), "model": MODEL, "natoms": a.natoms},
         "cpu_baseline": {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -166,6 +167,29 @@ def _peaks():
         return None
 
 
+# ncu summary that holds the DRAM traffic of a stage's kernel, per atom
+TRAFFIC_PROFILES = {"attn_bwd_tc": ("profiles/k_layer_bwd_tc_fp16x_2000atoms.md", "paper_2604_07276_gb300/csrc/tc.cu")}
+
+
+def _traffic_per_launch(stage, natoms):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one launch, scaled from
+    the committed ncu capture by the atoms processed; None when there is no
+    capture or the kernel source changed since it was taken."""
+    import hashlib
+
+    if stage not in TRAFFIC_PROFILES:
+        return None
+    prof, src = (os.path.join(ROOT, x) for x in TRAFFIC_PROFILES[stage])
+    try:
+        text = open(prof).read()
+        want = text.split("source sha256 (csrc/tc.cu):")[1].split()[0]
+        per_atom = float(text.split("dram bytes per atom:")[1].split()[0])
+        have = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, IndexError, ValueError):
+        return None
+    return per_atom * natoms if have.startswith(want) else None
+
+
 def _flops_per_launch(stage, nn, cfg):
     """Algorithmic FLOPs of one launch of ``stage`` over the whole box
     (per attention layer for per-layer stages), from the real neighbour
@@ -208,10 +232,15 @@ def run_ours(a):
 
     precisions = ["fp16x", "bf16", "fp32"] if a.precision == "auto" else [a.precision]
     models = {}
+    mem_used = {}  # device bytes taken by each model (weights + workspace for n atoms)
     for p in precisions:
         try:
+            torch.cuda.synchronize(dev)
+            free0 = torch.cuda.mem_get_info(dev)[0]
             models[p] = dp.DPA1(wpath, precision=p, device=local)
             models[p].reserve(n)
+            torch.cuda.synchronize(dev)
+            mem_used[p] = free0 - torch.cuda.mem_get_info(dev)[0]
         except dp.DPError as e:
             if e.code != -8 or a.precision != "auto":
                 raise
@@ -299,12 +328,18 @@ def run_ours(a):
         th = dmd.run(m, state, dt=0.5, nsteps=a.md_steps, graph=True, stream=stream.cuda_stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        m.status()
+        md_status = "ok"
+        try:
+            m.status()
+        except dp.DPError as e:  # e.g. a non-finite coordinate once atoms collapse
+            md_status = str(e)
         md_ms = e0.elapsed_time(e1)
         thc = th.cpu().numpy()
         md_line = {"steps": a.md_steps, "dt_fs": 0.5, "graph": True, "precision": head,
                    "atom_steps_per_s": ws * n * a.md_steps / (md_ms / 1e3), "ms_per_step": md_ms / a.md_steps,
                    "total_energy_drift_eV_per_atom_first_20_steps": float(abs(thc[min(19, len(thc) - 1), 2] - thc[0, 2]) / n),
+                   "total_energy_drift_eV_per_atom_all_steps": float(abs(thc[-1, 2] - thc[0, 2]) / n),
+                   "status": md_status,
                    "note": "random weights have no short-range repulsion; long runs collapse atoms"}
 
     # parity of this run's forces against the FP64 oracle on sampled atoms
@@ -341,7 +376,8 @@ def run_ours(a):
             # FP16 and BF16 share the nominal dense rate: the measured BF16 figure applies
             peak = (peaks or {}).get("bf16_tflops_sustained", 1700.0)
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": dom, "peak_source": "measured bf16 sustained" if peaks else "fallback"}
+                    "traffic": _traffic_per_launch(dom, n), "kernel": dom,
+                    "peak_source": "measured bf16 sustained" if peaks else "fallback"}
         else:
             clock = (peaks or {}).get("sm_max_mhz", 2070.0)
             peak = 152 * 128 * 2 * clock * 1e6 / 1e12
@@ -359,7 +395,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp16x": "f16", "bf16": "bf16", "fp32": "f32"}[head], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "model": MODEL, "natoms": n, "global_batch": ws * n,
+        "config": {"workload": workload(n), "model": MODEL, "natoms": n, "global_batch": ws * n,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "per-step working set is several GB of intermediates, far above the 129 MB L2",
                    "arithmetic": {"fp16x": "attention layers on tcgen05: FP16 operands, two-term splits of G, P, V; "
@@ -377,6 +413,7 @@ def run_ours(a):
         "force_rmse_vs_fp64": parity,
         "stage_ms_per_step": {p: {k: v[0] / a.steps for k, v in rr["stages"].items()} for p, rr in results.items()},
         "neighbors": {"mean": float(nn.mean()), "max": int(nn.max())},
+        "device_memory_bytes": mem_used,
         "md": md_line,
     }
     print(json.dumps(line), flush=True)
