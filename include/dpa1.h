@@ -202,7 +202,7 @@ DP_API long long dp_kernel_launches(void);
  * in the paper).  It builds the same list as dp_nlist_device (same rcut
  * rule, same order, rows padded with -1 to 128 entries), but needs no model
  * and never calls cudaMalloc, cudaFree or an allocating library: its cell-list
- * scratch is a fixed device array of about 1.7 MB that every GPU loading
+ * scratch is a fixed device array of about 2.7 MB that every GPU loading
  * this library holds until the process exits.  It is meant for callers that
  * cannot allocate device memory in the middle of their work: an MD engine
  * that hands the library only its own pooled buffers, code running inside a

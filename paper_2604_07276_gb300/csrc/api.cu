@@ -243,6 +243,7 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.cell_start = a.take<int>(ws.cell_cap + 1);
     ws.cell_cursor = a.take<int>(ws.cell_cap);
     ws.cell_atoms = a.take<int>(cap);
+    ws.coordf = a.take<float4>(cap);
     ws.nlist = a.take<int>(rows);
     ws.nnei = a.take<int>(cap);
     ws.ncand = a.take<int>(cap);
@@ -334,7 +335,8 @@ void run_neighbors(dp_model* m, int n, const double* coord, const double* box, c
   a.cap_dim = ws.cap_dim; a.cell_cap = ws.cell_cap; a.grid = ws.grid;
   a.cell_of = ws.cell_of; a.cell_count = ws.cell_count; a.cell_start = ws.cell_start;
   a.cell_cursor = ws.cell_cursor; a.cell_atoms = ws.cell_atoms;
-  a.nlist = ws.nlist; a.nnei = ws.nnei; a.ncand = ws.ncand; a.atype_c = ws.atype_c; a.err = m->d_err;
+  a.nlist = ws.nlist; a.nnei = ws.nnei; a.ncand = ws.ncand; a.atype_c = ws.atype_c; a.coordf = ws.coordf;
+  a.err = m->d_err;
   launch_neighbors(a, st);
 }
 
@@ -889,6 +891,7 @@ struct NoAllocScratch {
   int ncand[NA_MAX_ATOMS];
   int types[NA_MAX_ATOMS];    // all zero: the list does not depend on types
   int types_c[NA_MAX_ATOMS];
+  float4 coordf[NA_MAX_ATOMS];  // FP32 coordinates for the candidate screen
 };
 __device__ __align__(256) NoAllocScratch g_nbr_scratch;
 constexpr int NA_MAX_DEVICES = 64;
@@ -927,7 +930,8 @@ int dp_nlist_noalloc(int natoms, const double* d_coord, const double* d_box, dou
   a.cap_dim = NA_CAP_DIM; a.cell_cap = NA_MAX_CELLS; a.grid = &s->grid;
   a.cell_of = s->cell_of; a.cell_count = s->cell_count; a.cell_start = s->cell_start;
   a.cell_cursor = s->cell_cursor; a.cell_atoms = s->cell_atoms;
-  a.nlist = d_nlist; a.nnei = d_nnei; a.ncand = s->ncand; a.atype_c = s->types_c; a.err = d_status;
+  a.nlist = d_nlist; a.nnei = d_nnei; a.ncand = s->ncand; a.atype_c = s->types_c; a.coordf = s->coordf;
+  a.err = d_status;
   launch_neighbors(a, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("dp_nlist_noalloc: launch failed: ") + cudaGetErrorString(e));

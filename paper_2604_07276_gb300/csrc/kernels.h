@@ -21,7 +21,8 @@ struct NbrArgs {
   CellGrid* grid;
   int *cell_of, *cell_count, *cell_start, *cell_cursor, *cell_atoms;
   int *nlist, *nnei, *ncand;
-  int* atype_c;  // out: types clamped to [0, ntypes)
+  int* atype_c;    // out: types clamped to [0, ntypes)
+  float4* coordf;  // scratch [n]: FP32 copy of the coordinates for the candidate screen
   int* err;
 };
 void launch_neighbors(const NbrArgs& a, cudaStream_t st);

@@ -65,6 +65,7 @@ struct Workspace {
   int cell_cap, cap_dim;
   int *nlist, *nnei, *ncand, *rev_cnt, *rev_rows;
   int* atype_c;  // device-checked copy of the atom types
+  float4* coordf;  // FP32 coordinates (neighbour screen)
   // environment
   float *R, *rw, *rv, *dR, *dgeo, *g;
   double* w64;

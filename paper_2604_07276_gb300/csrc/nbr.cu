@@ -44,11 +44,13 @@ __device__ __forceinline__ int cell_coord(double x, double L, int nc) {
 
 __global__ void k_cell_count(const double* __restrict__ coord, const int* __restrict__ atype, int n,
                              int ntypes, const CellGrid* __restrict__ cgp, int* __restrict__ cell_of,
-                             int* __restrict__ cell_count, int* __restrict__ atype_c, int* __restrict__ err) {
+                             int* __restrict__ cell_count, int* __restrict__ atype_c, float4* __restrict__ coordf,
+                             int* __restrict__ err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const CellGrid g = *cgp;
   double x = coord[3 * i], y = coord[3 * i + 1], z = coord[3 * i + 2];
+  coordf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
   int c = 0;
   if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
     set_err(err, ERR_NAN);
@@ -104,28 +106,41 @@ __global__ void k_cell_fill(const int* __restrict__ cell_of, int n, const int* _
   cell_atoms[pos] = i;
 }
 
-__device__ __forceinline__ bool key_gt(double da, int ja, double db, int jb) {
+// Sort keys: the bit pattern of d^2 >= 0 (+0 or positive, never NaN) read as an
+// unsigned integer orders like the value, so the sort needs no FP64 compare.
+__device__ __forceinline__ bool key_gt(unsigned long long da, int ja, unsigned long long db, int jb) {
   return da > db || (da == db && ja > jb);
 }
 
+// mic() without its division when no image shift is possible: for |d| < L/2
+// the rounded d / L lies in [-0.5, 0.5], rint gives 0 and mic returns d up to
+// the sign of a zero, which the squared distance does not see.
+__device__ __forceinline__ double mic_near(double d, double L) {
+  return fabs(d) < 0.5 * L ? d : mic(d, L);
+}
+
 // One warp per centre atom: gather every candidate j != i with d^2 < rc^2 from
-// the 27 surrounding cells (FP64, bit-reproducible), then bitonic-sort the
-// candidates by (d^2, j) and keep the first sel.
+// the 27 surrounding cells (screened in FP32, decided in FP64 and
+// bit-reproducible), then bitonic-sort the candidates by (d^2, j) and keep the
+// first sel.  FP64 is slow on this part, so it is kept to the ~11 % of
+// candidates that pass the screen.
 constexpr int NBR_WARPS = 4;
 __global__ void __launch_bounds__(32 * NBR_WARPS)
 k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict__ cgp,
             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
             const int* __restrict__ cell_atoms, double rc2, int sel, int* __restrict__ nlist,
-            int* __restrict__ nnei, int* __restrict__ ncand, int* __restrict__ err) {
-  __shared__ double skey[NBR_WARPS][NBR_CAP];
+            int* __restrict__ nnei, int* __restrict__ ncand, const float4* __restrict__ coordf,
+            int* __restrict__ err) {
+  __shared__ unsigned long long skey[NBR_WARPS][NBR_CAP];
   __shared__ int sidx[NBR_WARPS][NBR_CAP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * NBR_WARPS + warp;
   if (i >= n) return;
   const CellGrid g = *cgp;
-  double* key = skey[warp];
+  unsigned long long* key = skey[warp];
   int* idx = sidx[warp];
   const double xi = coord[3 * i], yi = coord[3 * i + 1], zi = coord[3 * i + 2];
+  const float4 pi = coordf[i];
   const int ci = cell_of[i];
   const int cx = ci % g.nc[0], cy = (ci / g.nc[0]) % g.nc[1], cz = ci / (g.nc[0] * g.nc[1]);
   const int ox = g.nc[0] >= 3 ? 1 : 0, oy = g.nc[1] >= 3 ? 1 : 0, oz = g.nc[2] >= 3 ? 1 : 0;
@@ -148,20 +163,21 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
           int j = -1;
           if (t < e) {
             j = cell_atoms[t];
-            const double ex = __dsub_rn(coord[3 * j], xi);
-            const double ey = __dsub_rn(coord[3 * j + 1], yi);
-            const double ez = __dsub_rn(coord[3 * j + 2], zi);
-            // FP32 screen: its distance is within ~1e-6 relative of the FP64
-            // one, so a pair rejected with this margin is never a neighbour
-            // (where the two pick different images, both distances exceed
-            // L/2 > rcut).  Survivors are decided exactly in FP64.
-            const float fx = (float)ex - Lf[0] * rintf((float)ex * iLf[0]);
-            const float fy = (float)ey - Lf[1] * rintf((float)ey * iLf[1]);
-            const float fz = (float)ez - Lf[2] * rintf((float)ez * iLf[2]);
+            // FP32 screen from the FP32 coordinates: a component is off by
+            // at most ~1e-5 A, the squared distance near rc^2 by ~1.3e-4 A^2,
+            // far inside the margin, so a pair rejected here is never a
+            // neighbour (where FP32 and FP64 pick different images, both
+            // distances exceed L/2 > rcut).  Survivors are decided exactly
+            // in FP64.
+            const float4 pj = coordf[j];
+            float fx = pj.x - pi.x, fy = pj.y - pi.y, fz = pj.z - pi.z;
+            fx -= Lf[0] * rintf(fx * iLf[0]);
+            fy -= Lf[1] * rintf(fy * iLf[1]);
+            fz -= Lf[2] * rintf(fz * iLf[2]);
             if (j != i && fx * fx + fy * fy + fz * fz < rc2_screen) {
-              double ddx = mic(ex, g.L[0]);
-              double ddy = mic(ey, g.L[1]);
-              double ddz = mic(ez, g.L[2]);
+              const double ddx = mic_near(__dsub_rn(coord[3 * j], xi), g.L[0]);
+              const double ddy = mic_near(__dsub_rn(coord[3 * j + 1], yi), g.L[1]);
+              const double ddz = mic_near(__dsub_rn(coord[3 * j + 2], zi), g.L[2]);
               d2 = sqdist(ddx, ddy, ddz);
               hit = d2 < rc2;
             }
@@ -169,7 +185,7 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
           unsigned bal = __ballot_sync(0xffffffffu, hit);
           int pos = cnt + __popc(bal & ((1u << lane) - 1u));
           if (hit && pos < NBR_CAP) {
-            key[pos] = d2;
+            key[pos] = (unsigned long long)__double_as_longlong(d2);
             idx[pos] = j;
           }
           cnt += __popc(bal);
@@ -183,7 +199,7 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
   int P = 1;
   while (P < cnt) P <<= 1;
   for (int t = cnt + lane; t < P; t += 32) {
-    key[t] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    key[t] = 0x7ff0000000000000ULL;  // +inf
     idx[t] = 0x7fffffff;
   }
   __syncwarp();
@@ -193,7 +209,7 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
         int o = t ^ jj;
         if (o > t) {
           bool asc = (t & k) == 0;
-          double ka = key[t], kb = key[o];
+          const unsigned long long ka = key[t], kb = key[o];
           int ia = idx[t], ib = idx[o];
           bool sw = asc ? key_gt(ka, ia, kb, ib) : key_gt(kb, ib, ka, ia);
           if (sw) {
@@ -231,7 +247,7 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
   const int tb = 256;
   k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of,
-                                                  a.cell_count, a.atype_c, a.err);
+                                                  a.cell_count, a.atype_c, a.coordf, a.err);
   note_launch();
   k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid);
   note_launch();
@@ -239,7 +255,7 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t st) {
   note_launch();
   k_neighbors<<<(a.n + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
       a.coord, a.n, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist,
-      a.nnei, a.ncand, a.err);
+      a.nnei, a.ncand, a.coordf, a.err);
   note_launch();
 }
 
