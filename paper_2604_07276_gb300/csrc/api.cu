@@ -467,7 +467,10 @@ int run_device(dp_model* m, int n, const double* coord, const double* box, const
   EnvArgs ea{};
   ea.coord = coord; ea.atype = atype; ea.grid = ws.grid; ea.nlist = ws.nlist; ea.n = n;
   ea.davg = m->davg; ea.dstd = m->dstd; ea.rcs = (float)m->rcs; ea.rc = (float)m->rcut;
-  ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv; ea.w64 = ws.w64;
+  ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv;
+  // the FP32 path evaluates R in FP64 and keeps w in FP64 for its smooth logits
+  ea.fp64 = m->precision == DP_PREC_FP32 ? 1 : 0;
+  ea.w64 = ea.fp64 ? ws.w64 : nullptr;
   launch_env(ea, st);
   prof_mark(m, "env", st);
   if (m->precision != DP_PREC_FP32)

@@ -9,7 +9,11 @@ namespace dpa1 {
 // Smooth environment matrix (Sec. II-B, DP-SE): s(r) = w(r)/r with the C2
 // switch w, a row R_ij = (s, s x/r, s y/r, s z/r) normalised per centre type
 // by (R - davg)/dstd.  Displacements come from the FP64 coordinates through
-// the minimum image; the row is evaluated in FP64 and stored in FP32.
+// the minimum image.  Real = double (the FP32 path) evaluates the row in FP64;
+// Real = float (the 16-bit paths) rounds the FP64 displacement to FP32 and
+// evaluates the rest in FP32, which keeps this part's error at ~1e-7
+// relative, far below those paths' operand rounding.  Both store FP32.
+template <typename Real>
 __global__ void k_env(EnvArgs a) {
   long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= (long long)a.n * NP) return;
@@ -19,27 +23,32 @@ __global__ void k_env(EnvArgs a) {
   double w64 = 0.0;
   if (j >= 0) {
     const CellGrid g = *a.grid;
-    double dx = mic(a.coord[3 * j] - a.coord[3 * i], g.L[0]);
-    double dy = mic(a.coord[3 * j + 1] - a.coord[3 * i + 1], g.L[1]);
-    double dz = mic(a.coord[3 * j + 2] - a.coord[3 * i + 2], g.L[2]);
-    double d = sqrt(dx * dx + dy * dy + dz * dz);
-    double rcs = a.rcs, rc = a.rc;
-    double sw;
+    const double ex = a.coord[3 * j] - a.coord[3 * i];
+    const double ey = a.coord[3 * j + 1] - a.coord[3 * i + 1];
+    const double ez = a.coord[3 * j + 2] - a.coord[3 * i + 2];
+    // no image shift inside half a box: skip the FP64 division of mic()
+    const Real dx = (Real)(fabs(ex) < 0.5 * g.L[0] ? ex : mic(ex, g.L[0]));
+    const Real dy = (Real)(fabs(ey) < 0.5 * g.L[1] ? ey : mic(ey, g.L[1]));
+    const Real dz = (Real)(fabs(ez) < 0.5 * g.L[2] ? ez : mic(ez, g.L[2]));
+    const Real d = sqrt(dx * dx + dy * dy + dz * dz);
+    const Real rcs = a.rcs, rc = a.rc;
+    Real sw;
     if (d < rcs) {
-      sw = 1.0;
+      sw = 1;
     } else if (d < rc) {
-      double u = (d - rcs) / (rc - rcs);
-      sw = u * u * u * (-6.0 * u * u + 15.0 * u - 10.0) + 1.0;
+      const Real u = (d - rcs) / (rc - rcs);
+      sw = u * u * u * ((Real)-6 * u * u + (Real)15 * u - (Real)10) + (Real)1;
     } else {
-      sw = 0.0;
+      sw = 0;
     }
-    double s = sw / d;
-    double hx = dx / d, hy = dy / d, hz = dz / d;
+    const Real inv_d = (Real)1 / d;
+    const Real s = sw * inv_d;
+    const Real hx = dx * inv_d, hy = dy * inv_d, hz = dz * inv_d;
     const int t = a.atype[i];
     const float* av = a.davg + 4 * t;
     const float* sv = a.dstd + 4 * t;
-    R = make_float4((float)((s - av[0]) / sv[0]), (float)((s * hx - av[1]) / sv[1]),
-                    (float)((s * hy - av[2]) / sv[2]), (float)((s * hz - av[3]) / sv[3]));
+    R = make_float4((float)((s - (Real)av[0]) / (Real)sv[0]), (float)((s * hx - (Real)av[1]) / (Real)sv[1]),
+                    (float)((s * hy - (Real)av[2]) / (Real)sv[2]), (float)((s * hz - (Real)av[3]) / (Real)sv[3]));
     rw = make_float4((float)hx, (float)hy, (float)hz, (float)sw);
     rv = make_float4((float)dx, (float)dy, (float)dz, (float)d);
     w64 = sw;
@@ -53,7 +62,10 @@ __global__ void k_env(EnvArgs a) {
 void launch_env(const EnvArgs& a, cudaStream_t st) {
   long long rows = (long long)a.n * NP;
   if (rows == 0) return;
-  k_env<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+  if (a.fp64)
+    k_env<double><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+  else
+    k_env<float><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
   note_launch();
 }
 

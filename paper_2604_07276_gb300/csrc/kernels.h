@@ -42,6 +42,7 @@ struct EnvArgs {
   float* rw;  // [n*NP][4] (rhat_x, rhat_y, rhat_z, w)
   float* rv;  // [n*NP][4] (x, y, z, |r|)
   double* w64;  // [n*NP] switch weight in FP64
+  int fp64;     // evaluate in FP64 (else FP32 from the FP64 displacement)
 };
 void launch_env(const EnvArgs& a, cudaStream_t st);
 
