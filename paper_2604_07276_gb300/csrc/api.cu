@@ -212,6 +212,7 @@ void refresh_derived(dp_model* m, cudaStream_t st) {
   }
   launch_scale_copy(m->theta + m->off_wout, m->w_out, fan, (float)m->out_scale, st);
   launch_scale_copy(m->theta + m->off_bout, m->d_b_out, 1, (float)m->out_scale, st);
+  fit_tc_refresh(m, st);  // tensor-core weight images of the 16-bit paths, if built
 }
 
 void free_workspace(Workspace& ws) {
@@ -359,11 +360,17 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
   // a8: fitting forward
   int fan = m->fit_in;
   const float* hin = ws.X;
+  // the 16-bit paths run the products on tcgen05 (TF32 with two-term splits)
+  const bool fit_tc = m->precision != DP_PREC_FP32 && !m->tcw.fitW_t.empty();
   for (int l = 0; l < m->nfit; ++l) {
     const int out = m->fit[l];
     const bool res = (l > 0 && out == fan);
-    gemm_f32(hin, fan, m->fitW[l], out, m->fitb[l], res ? hin : nullptr, fan, ws.H[l], out, n, out, fan,
-             res ? EPI_RES_TANH : EPI_TANH, st);
+    if (fit_tc)
+      fit_gemm_tc(m, l, false, hin, fan, m->fitb[l], res ? hin : nullptr, fan, ws.H[l], out, n,
+                  res ? EPI_RES_TANH : EPI_TANH, st);
+    else
+      gemm_f32(hin, fan, m->fitW[l], out, m->fitb[l], res ? hin : nullptr, fan, ws.H[l], out, n, out, fan,
+               res ? EPI_RES_TANH : EPI_TANH, st);
     hin = ws.H[l];
     fan = out;
   }
@@ -389,8 +396,11 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
       launch_colsum(ws.dZ, out, m->grad + m->off_fitb[l], out, n, gs, 1.0f, st);
     }
     float* dst = l > 0 ? dHn : ws.dX;
-    gemm_f32(ws.dZ, out, m->fitWT[l], in, nullptr, res ? dH : nullptr, out, dst, in, n, in, out,
-             res ? EPI_RES : EPI_BIAS, st);
+    if (fit_tc)
+      fit_gemm_tc(m, l, true, ws.dZ, out, nullptr, res ? dH : nullptr, out, dst, in, n, res ? EPI_RES : EPI_BIAS, st);
+    else
+      gemm_f32(ws.dZ, out, m->fitWT[l], in, nullptr, res ? dH : nullptr, out, dst, in, n, in, out,
+               res ? EPI_RES : EPI_BIAS, st);
     std::swap(dH, dHn);
   }
   prof_mark(m, "fitting", st);

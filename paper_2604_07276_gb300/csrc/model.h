@@ -159,6 +159,12 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg);
 void tc_plan_buffers(dp_model* m, Arena& a, int cap);
 void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st);
 void tc_free_weights(dp_model* m);
+// tcgen05 TF32 (two-term split) fitting-net products of the 16-bit paths (fit.cu)
+bool fit_tc_supported(const dp_model* m);
+int fit_tc_init(dp_model* m, std::string& msg);
+void fit_tc_refresh(dp_model* m, cudaStream_t st);
+int fit_gemm_tc(dp_model* m, int layer, bool backward, const float* A, int lda, const float* bias, const float* R,
+                int ldr, float* C, int ldc, int M, int epi, cudaStream_t st);
 // stages a7-a11 (descriptor, fitting forward / backward, descriptor backward)
 void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t st);
 }  // namespace dpa1

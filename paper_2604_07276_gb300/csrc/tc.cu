@@ -1176,6 +1176,7 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
   cudaFuncSetAttribute(k_layer_bwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
   cudaFuncSetAttribute(k_layer_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
   cudaFuncSetAttribute(k_layer_bwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SMEM);
+  if (int rc = fit_tc_init(m, msg)) return rc;
   w.ready = true;
   return DP_OK;
 }
@@ -1284,6 +1285,8 @@ void tc_free_weights(dp_model* m) {
   m->tcw.allocations.clear();
   m->tcw.Wqkv_t.clear();
   m->tcw.Wo_t.clear();
+  m->tcw.fitW_t.clear();
+  m->tcw.fitWT_t.clear();
   m->tcw.ready = false;
 }
 

@@ -147,3 +147,25 @@ def test_fp16x_other_embedding_net(lib, water, attn_layers):
     assert rel <= 5e-3, rel
     assert np.abs(e - re).max() <= 1e-3 * max(1.0, np.abs(re).max())
     m.close()
+
+
+def test_fp16x_without_attention_is_fp32_accurate(lib, water):
+    """With no attention layer, the only tensor-core products of the 16-bit
+    mode are the embedding net (FP16 hi + lo splits of both operands) and the
+    fitting net (tcgen05 TF32, two-term splits of both operands, activations
+    loaded by TMA).  Both keep FP32 accuracy, so the forces must meet the
+    FP32 path's bound."""
+    from oracle import OracleModel
+
+    cfg = synth.ModelConfig(attn_layers=0, out_scale=synth.DEFAULT_CONFIG.out_scale)
+    w = synth.make_weights(cfg, seed=6, bias_scale=0.1, stats=True)
+    om = OracleModel.from_numpy(cfg, w)
+    m = lib.DPA1(weight_file(cfg, w, "noattn"), precision="fp16x")
+    coord, atype, box = water
+    E, F, W, e = m.compute(coord, box, atype, atom_energy=True)
+    rE, re, rF, rW = energy_force_virial(om, coord, box, atype)
+    frmse = force_rmse(F, rF)
+    print(f"no-attention fp16x: force rmse {frmse:.3e}, max |de_i| {np.abs(e - re).max():.3e}")
+    assert frmse <= 1e-5, frmse
+    assert np.abs(e - re).max() <= 1e-4
+    m.close()
