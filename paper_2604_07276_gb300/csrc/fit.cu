@@ -11,11 +11,12 @@
 //   warp 0      : producer.  A tiles (128 rows x 32 K, FP32) by TMA with the
 //                 128-byte swizzle, B_hi / B_lo tiles by 1D bulk copies of
 //                 pre-swizzled images; two pipeline stages.
-//   warps 4-7   : split each A tile in place (A_hi) and into its A_lo tile,
-//                 then run the epilogue (TMEM -> bias, tanh, residual ->
-//                 global), one thread per row.
+//   warps 4-7   : split each A tile in place (A_hi) and into its A_lo tile.
 //   warp 1      : issues the MMAs (one thread), accumulator in TMEM.
 //   warp 2      : allocates / frees TMEM.
+//   all 8 warps : the epilogue (TMEM -> bias, tanh, residual -> global); warp
+//                 w reads TMEM lane quadrant w % 4 and every other 16-column
+//                 chunk, starting at chunk w / 4.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -164,7 +165,7 @@ k_fit_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ FitG
     }
     mma_commit(done);
   } else if (warp >= 4) {
-    // split A in place, then the epilogue
+    // split A in place
     const int r = (warp - 4) * 32 + lane;  // row in the tile = TMEM lane
     for (int kb = 0; kb < a.nkb && wt.ok; ++kb) {
       const int s = kb % FSTAGES, u = kb / FSTAGES;
@@ -185,11 +186,17 @@ k_fit_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ FitG
       fence_async_smem();
       mbar_arrive(conv + s);
     }
-    wt.wait(done, 0);
-    fence_after_sync();
+  }
+  // epilogue, all warps
+  __syncwarp();
+  Waiter wd{a.err};
+  wd.wait(done, 0);
+  fence_after_sync();
+  {
+    const int r = (warp & 3) * 32 + lane;  // row in the tile = TMEM lane
     const long long m = (long long)mb * FBM + r;
     const uint32_t taddr = tm + ((uint32_t)((warp & 3) * 32) << 16);
-    for (int c0 = 0; c0 < bn; c0 += 16) {
+    for (int c0 = (warp >> 2) * 16; c0 < bn; c0 += 32) {
       float v[16];
       tmem_ld16(taddr + c0, v);
       const int n0 = nb * FNMAX + c0;
