@@ -757,8 +757,10 @@ constexpr int EMB_T2 = 112 * 64 * 2;    // W2 tile: 112 (E2 padded) rows x 64 co
 constexpr int EMB_TA = 128 * 64 * 2;    // activation tile: 128 rows x 64 cols
 constexpr int EMB_TD = 128 * 128 * 2;   // dZ3 tile: 128 rows x 128 cols
 constexpr int EMB_WIMG = 2 * EMB_T1 + 2 * EMB_T2;  // W1 hi, W1 lo, W2 hi, W2 lo
-constexpr int EMBF_SMEM = EMB_WIMG + 4 * EMB_TA + 64;
-constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + 64;  // dZ3 tiles reuse the four activation tiles
+constexpr int EMB_MAXT = 8;                           // atom types the staged type-pair rows allow
+constexpr int EMB_GT = EMB_MAXT * EMB_E2 * 4;         // this atom's rows of the type-pair table
+constexpr int EMBF_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 64;
+constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 64;  // dZ3 tiles reuse the four activation tiles
 static_assert(2 * EMB_TD == 4 * EMB_TA, "the dZ3 hi / lo tiles fill the activation tiles");
 
 struct EmbedTcArgs {
@@ -847,6 +849,22 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
   commit_and_sync(sy, issuer);
 }
 
+// Per atom: copy the centre type's rows of the type-pair table Gt[t_i][*] to
+// shared memory (read as float4 by neighbour type afterwards), and bring the
+// next atom's per-row inputs into L2.
+__device__ __forceinline__ void embed_tc_atom_start(const EmbedTcArgs& a, float* s_gt, int atom, bool bwd) {
+  const float4* src = reinterpret_cast<const float4*>(a.Gt + (size_t)a.atype[atom] * a.ntypes * EMB_E2);
+  float4* dst = reinterpret_cast<float4*>(s_gt);
+  for (int i = threadIdx.x; i < a.ntypes * EMB_E2 / 4; i += blockDim.x) dst[i] = src[i];
+  const int next = atom + gridDim.x;
+  if (threadIdx.x == 0 && next < a.n) {
+    const size_t base = (size_t)next * NP;
+    prefetch_l2(a.R + base * 4, NP * 4 * sizeof(float));
+    prefetch_l2(a.nlist + base, NP * sizeof(int));
+    if (bwd) prefetch_l2(a.dG0 + base * EMB_E2, NP * EMB_E2 * sizeof(float));
+  }
+}
+
 __device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm, uint64_t*& bar, uint32_t*& s_tmem,
                                                int smem_bytes) {
   bar = reinterpret_cast<uint64_t*>(sm + smem_bytes - 64);
@@ -873,14 +891,17 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__
   const uint32_t tm = *s_tmem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = warp * 32 + lane;
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
   Sync sy{bar, 0u, a.err};
   float h1[EMB_E0], h2[EMB_E1];
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const bool rv = row < nn;
     const size_t rowg = (size_t)atom * NP + row;
+    const int tj = rv ? a.atype[a.nlist[rowg]] : 0;
+    embed_tc_atom_start(a, s_gt, atom, false);  // visible after the front's barriers
     embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
-    const float* gt = a.Gt + ((size_t)a.atype[atom] * a.ntypes + (rv ? a.atype[a.nlist[rowg]] : 0)) * EMB_E2;
+    const float* gt = s_gt + tj * EMB_E2;
     float4* out = reinterpret_cast<float4*>(a.G0 + (size_t)atom * NP * EMB_E2);
 #pragma unroll
     for (int blk = 0; blk < 4; ++blk) {
@@ -935,16 +956,21 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
   uint8_t* sDZ3l = sDZ3h + EMB_TD;
   uint8_t* sDZ2h = sm + EMB_WIMG;
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
+  float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
   Sync sy{bar, 0u, a.err};
   float h1[EMB_E0], h2[EMB_E1];
+  if (threadIdx.x == 0 && blockIdx.x < a.n)
+    prefetch_l2(a.dG0 + (size_t)blockIdx.x * NP * EMB_E2, NP * EMB_E2 * sizeof(float));
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     if (nn == 0) continue;  // uniform over the CTA
     const bool rv = row < nn;
     const size_t rowg = (size_t)atom * NP + row;
+    const int tj = rv ? a.atype[a.nlist[rowg]] : 0;
+    embed_tc_atom_start(a, s_gt, atom, true);  // visible after the front's barriers
     embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
     // dZ3 = g (1 - t3^2), g = dG0 (1 + Gt); skip part of dH2 kept in dh2
-    const float* gt = a.Gt + ((size_t)a.atype[atom] * a.ntypes + (rv ? a.atype[a.nlist[rowg]] : 0)) * EMB_E2;
+    const float* gt = s_gt + tj * EMB_E2;
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
     float dh2[EMB_E1];
 #pragma unroll
@@ -1115,7 +1141,7 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
     }
   // embedding-net tiles (hi and lo FP16 parts of W1 and W2) for the 25-50-100 net
   w.emb_W1_t = nullptr;
-  if (m->emb[0] == EMB_E0 && m->emb[1] == EMB_E1 && m->emb[2] == EMB_E2) {
+  if (m->emb[0] == EMB_E0 && m->emb[1] == EMB_E1 && m->emb[2] == EMB_E2 && m->nt <= EMB_MAXT) {
     std::vector<uint8_t> img(EMB_WIMG, 0);
     const std::vector<double>& W1 = get("em_W1");  // [E0][E1]
     const std::vector<double>& W2 = get("em_W2");  // [E1][E2]
