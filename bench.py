@@ -66,6 +66,25 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, device):
+    """Largest value of x over the ranks of the default process group (x
+    itself without one): the job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as td
+
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, natoms, steps, seconds):
+    """Whole-job throughput: every replica's atom-steps over the slowest
+    replica's time (weak scaling, one box per GPU)."""
+    return world * natoms * steps / seconds
+
+
 def _system(natoms):
     import synth
 
@@ -283,10 +302,7 @@ def run_ours(a):
         stages = m.stage_times()
         m.set_profiling(False)
         m.status()
-        if ws > 1:
-            tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ms, dev)
         per_stage = {}
         for name, v in stages:
             s = per_stage.setdefault(name, [0.0, 0])
@@ -308,10 +324,7 @@ def run_ours(a):
     for _ in range(e2e_steps):
         m.compute(hc, box, ht)
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
 
     # velocity-Verlet MD of the same box, every step replayed from one CUDA graph
     md_line = None
@@ -333,10 +346,10 @@ def run_ours(a):
             m.status()
         except dp.DPError as e:  # e.g. a non-finite coordinate once atoms collapse
             md_status = str(e)
-        md_ms = e0.elapsed_time(e1)
+        md_ms = max_over_ranks(e0.elapsed_time(e1), dev)
         thc = th.cpu().numpy()
         md_line = {"steps": a.md_steps, "dt_fs": 0.5, "graph": True, "precision": head,
-                   "atom_steps_per_s": ws * n * a.md_steps / (md_ms / 1e3), "ms_per_step": md_ms / a.md_steps,
+                   "atom_steps_per_s": job_rate(ws, n, a.md_steps, md_ms / 1e3), "ms_per_step": md_ms / a.md_steps,
                    "total_energy_drift_eV_per_atom_first_20_steps": float(abs(thc[min(19, len(thc) - 1), 2] - thc[0, 2]) / n),
                    "total_energy_drift_eV_per_atom_all_steps": float(abs(thc[-1, 2] - thc[0, 2]) / n),
                    "status": md_status,
@@ -362,7 +375,7 @@ def run_ours(a):
         return 0
     r = results[head]
     ms_step = r["ms"] / a.steps
-    value = ws * n * a.steps / (r["ms"] / 1e3)
+    value = job_rate(ws, n, a.steps, r["ms"] / 1e3)
     # dominant kernel stage and its roofline
     peaks = _peaks()
     st = r["stages"]
@@ -403,12 +416,12 @@ def run_ours(a):
                                   "bf16": "attention layers on tcgen05: BF16 operands, FP32 accumulation",
                                   "fp32": "FP32 SIMT"}[head]},
         "clocks": r["clocks"],
-        "e2e": {"value": ws * n * e2e_steps / e2e_s, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(ws, n, e2e_steps, e2e_s), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": r["launches"],
         "roofline": roof,
         "cpu_baseline": cpu,
-        "precisions": {p: {"value": ws * n * a.steps / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / a.steps}
+        "precisions": {p: {"value": job_rate(ws, n, a.steps, rr["ms"] / 1e3), "ms_per_step": rr["ms"] / a.steps}
                        for p, rr in results.items()},
         "force_rmse_vs_fp64": parity,
         "stage_ms_per_step": {p: {k: v[0] / a.steps for k, v in rr["stages"].items()} for p, rr in results.items()},
