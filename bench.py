@@ -56,6 +56,7 @@ def _args():
     ap.add_argument("--cpu-sample", type=int, default=3072, help="oracle centres timed for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
     ap.add_argument("--md-steps", type=int, default=1000, help="graph-captured velocity-Verlet steps to time (0: skip)")
+    ap.add_argument("--no-student", action="store_true", help="skip the distilled-student line")
     return ap.parse_args()
 
 
@@ -137,6 +138,72 @@ def run_reference(a):
 
 
 # -------------------------------------------------------------------- our arm
+
+def _student_line(dev, coord, atype, box, full_rates, batch=16, md_steps=100):
+    """Distilled student (embedding [16, 32, 64], axis 8, no attention,
+    fitting [128, 128]) on the same box: training throughput of
+    dp_train_frame + dp_adam_step on 16-frame batches (FP32, loss against
+    stand-in reference energies and forces: the cost does not depend on
+    their values) and graph-replayed MD throughput next to the full model's."""
+    import torch
+
+    import synth
+    import paper_2604_07276_gb300 as dp
+    from paper_2604_07276_gb300 import md as dmd
+
+    scfg = synth.STUDENT_CONFIG
+    path = os.path.join(tempfile.mkdtemp(prefix="dpa1s_"), "student.bin")
+    synth.write_weights(path, scfg, synth.make_weights(scfg, seed=4))
+    s = dp.DPA1(path, precision="fp32", device=dev.index)
+    n = len(coord)
+    s.reserve(n)
+    c = torch.tensor(coord, dtype=torch.float64, device=dev)
+    b = torch.tensor(dp.box9(box), dtype=torch.float64, device=dev)
+    t = torch.tensor(atype, dtype=torch.int32, device=dev)
+    f_ref = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    loss = torch.zeros(3, dtype=torch.float64, device=dev)
+
+    def one_batch():
+        s.zero_grad()
+        for _ in range(batch):
+            s.train_frame(c, b, t, 0.0, f_ref, loss)
+        s.adam_step(1e-5)
+
+    one_batch()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        one_batch()
+    torch.cuda.synchronize(dev)
+    s.status()
+    train_s = (time.perf_counter() - t0) / 2
+    s.close()
+
+    def md_rate(precision):
+        mdl = dp.DPA1(path, precision=precision, device=dev.index)
+        mdl.reserve(n)
+        state = dmd.MDState(coord, np.zeros_like(coord), synth.MASSES[atype], box, atype, device=dev)
+        dmd.run(mdl, state, dt=0.5, nsteps=2, graph=True)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dmd.run(mdl, state, dt=0.5, nsteps=md_steps, graph=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        mdl.status()
+        mdl.close()
+        return n * md_steps / (e0.elapsed_time(e1) / 1e3)
+
+    # training runs on the FP32 path; inference also in the 16-bit mode, whose
+    # tensor-core products (here only the fitting net) keep FP32 accuracy
+    rates = {p: md_rate(p) for p in ("fp32", "fp16x")}
+    return {"model": "embed [16,32,64], axis 8, no attention, fitting [128,128]", "train_precision": "fp32",
+            "train_batch_frames": batch, "train_ms_per_batch": 1e3 * train_s,
+            "train_frames_per_s": batch / train_s, "md_atom_steps_per_s": rates,
+            "md_speedup_vs_full_fp16x": {p: r / full_rates["fp16x"] for p, r in rates.items()} if "fp16x" in full_rates
+            else None}
+
 
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
@@ -355,6 +422,11 @@ def run_ours(a):
                    "status": md_status,
                    "note": "random weights have no short-range repulsion; long runs collapse atoms"}
 
+    student = None
+    if not a.no_student:
+        student = _student_line(dev, coord, atype, box,
+                                {p: job_rate(1, n, a.steps, rr["ms"] / 1e3) for p, rr in results.items()})
+
     # parity of this run's forces against the FP64 oracle on sampled atoms
     parity = {}
     nl, nn = m.nlist_device(c, b)
@@ -428,6 +500,7 @@ def run_ours(a):
         "neighbors": {"mean": float(nn.mean()), "max": int(nn.max())},
         "device_memory_bytes": mem_used,
         "md": md_line,
+        "student": student,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

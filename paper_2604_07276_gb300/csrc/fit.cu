@@ -165,23 +165,26 @@ k_fit_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ FitG
     }
     mma_commit(done);
   } else if (warp >= 4) {
-    // split A in place
-    const int r = (warp - 4) * 32 + lane;  // row in the tile = TMEM lane
+    // split A in place; thread t takes 16-byte pieces t, t + 128, ... of the
+    // tile, so that a warp touches 512 contiguous bytes (the swizzle only
+    // permutes pieces within a row, and the split is element-wise)
+    const int t = threadIdx.x - 128;
     for (int kb = 0; kb < a.nkb && wt.ok; ++kb) {
       const int s = kb % FSTAGES, u = kb / FSTAGES;
       wt.wait(full + s, u & 1);
-      uint4* hi = reinterpret_cast<uint4*>(sA(s) + r * 128);
-      uint4* lo = reinterpret_cast<uint4*>(sAl(s) + r * 128);
+      uint4* hi = reinterpret_cast<uint4*>(sA(s));
+      uint4* lo = reinterpret_cast<uint4*>(sAl(s));
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {  // the 16-byte pieces of this row (any swizzle order)
-        uint4 x = hi[c];
+      for (int i = 0; i < FA_TILE / 16 / 128; ++i) {
+        const int q = i * 128 + t;
+        const uint4 x = hi[q];
         uint4 h, l;
         h.x = tf32_trunc(x.x); l.x = tf32_trunc(__float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x)));
         h.y = tf32_trunc(x.y); l.y = tf32_trunc(__float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y)));
         h.z = tf32_trunc(x.z); l.z = tf32_trunc(__float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z)));
         h.w = tf32_trunc(x.w); l.w = tf32_trunc(__float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w)));
-        hi[c] = h;
-        lo[c] = l;
+        hi[q] = h;
+        lo[q] = l;
       }
       fence_async_smem();
       mbar_arrive(conv + s);
