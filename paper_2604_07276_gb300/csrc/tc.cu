@@ -760,7 +760,7 @@ constexpr int EMB_WIMG = 2 * EMB_T1 + 2 * EMB_T2;  // W1 hi, W1 lo, W2 hi, W2 lo
 constexpr int EMB_MAXT = 8;                           // atom types the staged type-pair rows allow
 constexpr int EMB_GT = EMB_MAXT * EMB_E2 * 4;         // this atom's rows of the type-pair table
 constexpr int EMBF_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 64;
-constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 64;  // dZ3 tiles reuse the four activation tiles
+constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 512 + 64;  // dZ3 tiles reuse the four activation tiles
 static_assert(2 * EMB_TD == 4 * EMB_TA, "the dZ3 hi / lo tiles fill the activation tiles");
 
 struct EmbedTcArgs {
@@ -778,19 +778,23 @@ struct EmbedTcArgs {
   float W0[EMB_E0], b0[EMB_E0], b1[EMB_E1], b2[EMB_E2];
 };
 
-// 16 columns (c0..c0+15) of a row as hi or lo fp16 parts into an SW128 tile.
-template <bool LO>
-__device__ __forceinline__ void store16(uint8_t* tile, int r, int c0, int R, const float* v) {
+// Thread layout (256 threads): warp w owns TMEM lane quadrant w % 4 (rows
+// 32 (w % 4) .. +31) and half H = w / 4 of the work of its row.  Half 0 owns
+// the layer-2 units b in [0, 24), half 1 those in [24, 50); a layer-3 output c
+// belongs to the owner of c % 50 (the residual input it needs), so no row
+// data crosses between the halves except one partial sum at the end of the
+// adjoint.  Both halves evaluate the 25 layer-1 units.
+constexpr int EMB_THREADS = 256;
+constexpr int EMB_SPLIT = 24;  // first layer-2 unit of half 1
+
+__device__ __forceinline__ void emb_store8(uint8_t* tile, int r, int c0, int R, const float* v, bool lo) {
+  float x[8];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    float x[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = LO ? v[8 * q + i] - round16<true>(v[8 * q + i]) : v[8 * q + i];
-    uint4 u;
-    u.x = pack_f16(x[0], x[1]); u.y = pack_f16(x[2], x[3]);
-    u.z = pack_f16(x[4], x[5]); u.w = pack_f16(x[6], x[7]);
-    sw128_store8(tile, r, c0 + 8 * q, R, u);
-  }
+  for (int i = 0; i < 8; ++i) x[i] = lo ? v[i] - round16<true>(v[i]) : v[i];
+  uint4 u;
+  u.x = pack_f16(x[0], x[1]); u.y = pack_f16(x[2], x[3]);
+  u.z = pack_f16(x[4], x[5]); u.w = pack_f16(x[6], x[7]);
+  sw128_store8(tile, r, c0, R, u);
 }
 
 // D (+)= A * B with A = Ah + Al and B = Bh + Bl, dropping Al * Bl.
@@ -801,10 +805,21 @@ __device__ __forceinline__ void mma_split(uint32_t d, uint32_t ah, uint32_t al, 
   mma_block<true>(d, ah, false, a_rows, bl, b_mn, b_rows, N, ksteps, true);
 }
 
-// Layers 1 and 2 of a row, and the issue of Z3 = H2 W2; returns after Z3 is
-// in TMEM columns [64, 176).  h1 / h2 keep the activations.
+template <int H>
+struct EmbOwn {
+  static constexpr int b0 = H == 0 ? 0 : EMB_SPLIT;          // first owned layer-2 unit
+  static constexpr int nb = H == 0 ? EMB_SPLIT : EMB_E1 - EMB_SPLIT;
+  __host__ __device__ static constexpr bool owns_b(int b) { return b >= b0 && b < b0 + nb; }
+  __host__ __device__ static constexpr bool owns_c(int c) { return c < EMB_E2 && owns_b(c % EMB_E1); }
+};
+
+// Layers 1 and 2 of a row and the issue of Z3 = H2 W2; returns once Z3 is in
+// TMEM columns [64, 176).  h1 gets all 25 layer-1 units, h2 the owned
+// layer-2 units.
+template <int H>
 __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
                                                Sync& sy, int row, bool rv, size_t rowg, float* h1, float* h2) {
+  using O = EmbOwn<H>;
   uint8_t* sW1h = sm;
   uint8_t* sW1l = sW1h + EMB_T1;
   uint8_t* sW2h = sW1l + EMB_T1;
@@ -815,38 +830,65 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sH2l = sH2h + EMB_TA;
   const bool issuer = threadIdx.x == 0;
   const float x = rv ? a.R[rowg * 4] : 0.f;
-  float v[64];
 #pragma unroll
-  for (int p = 0; p < 64; ++p) v[p] = (p < EMB_E0 && rv) ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
+  for (int p = 0; p < EMB_E0; ++p) h1[p] = rv ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
+  // H1 (K = 25, read as 32): half 0 stores the hi parts, half 1 the lo parts
 #pragma unroll
-  for (int p = 0; p < EMB_E0; ++p) h1[p] = v[p];
+  for (int g = 0; g < 4; ++g) {
+    float v[8];
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) {
-    store16<false>(sH1h, row, c, 128, v + c);
-    store16<true>(sH1l, row, c, 128, v + c);
+    for (int i = 0; i < 8; ++i) v[i] = 8 * g + i < EMB_E0 ? h1[8 * g + i] : 0.f;
+    emb_store8(H == 0 ? sH1h : sH1l, row, 8 * g, 128, v, H == 1);
   }
   handoff();
   if (issuer)
     mma_split(tm + 0, smem_u32(sH1h), smem_u32(sH1l), 128, smem_u32(sW1h), smem_u32(sW1l), false, 64, 64, 2);
   commit_and_sync(sy, issuer);
-  tmem_ld32(tm + lane_off + 0, v);
-  tmem_ld32(tm + lane_off + 32, v + 32);
+  // layer 2, owned units: h2 = h1[b % 25] + tanh(z2 + b1)
+  constexpr int g_lo = O::b0 / 8, g_hi = H == 0 ? EMB_SPLIT / 8 : 7;  // 8-column groups stored
 #pragma unroll
-  for (int b = 0; b < 64; ++b) {
-    const float hb = (b < EMB_E1 && rv) ? h1[b % EMB_E0] + tanhf(v[b] + a.b1[b < EMB_E1 ? b : 0]) : 0.f;
-    v[b] = hb;
-  }
+  for (int k = 0; k < 4; ++k) {  // 16-column TMEM chunks
+    if (16 * k + 15 < O::b0 || 16 * k >= 8 * g_hi) continue;
+    float z[16];
+    tmem_ld16(tm + lane_off + 16 * k, z);
 #pragma unroll
-  for (int b = 0; b < EMB_E1; ++b) h2[b] = v[b];
+    for (int gg = 0; gg < 2; ++gg) {
+      const int g = 2 * k + gg;
+      if (g < g_lo || g >= g_hi) continue;
+      float v[8];
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) {
-    store16<false>(sH2h, row, c, 128, v + c);
-    store16<true>(sH2l, row, c, 128, v + c);
+      for (int i = 0; i < 8; ++i) {
+        const int b = 8 * g + i;
+        float hb = 0.f;
+        if (b < EMB_E1 && rv) hb = h1[b % EMB_E0] + tanhf(z[8 * gg + i] + a.b1[b]);
+        if (O::owns_b(b)) h2[b - O::b0] = hb;
+        v[i] = hb;
+      }
+      emb_store8(sH2h, row, 8 * g, 128, v, false);
+      emb_store8(sH2l, row, 8 * g, 128, v, true);
+    }
   }
   handoff();
   if (issuer)
     mma_split(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
   commit_and_sync(sy, issuer);
+}
+
+__device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm, uint64_t*& bar, uint32_t*& s_tmem,
+                                               int smem_bytes) {
+  bar = reinterpret_cast<uint64_t*>(sm + smem_bytes - 64);
+  s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  uint4* d = reinterpret_cast<uint4*>(sm);
+  for (int i = threadIdx.x; i < EMB_WIMG / 16; i += blockDim.x) d[i] = a.wimg[i];
+  // activation tiles start at zero: columns never written later are read
+  // only against zero weight rows, which needs finite values there
+  for (int i = threadIdx.x; i < 4 * EMB_TA / 16; i += blockDim.x) d[EMB_WIMG / 16 + i] = make_uint4(0u, 0u, 0u, 0u);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(s_tmem, 256);
+  handoff();
 }
 
 // Per atom: copy the centre type's rows of the type-pair table Gt[t_i][*] to
@@ -865,21 +907,33 @@ __device__ __forceinline__ void embed_tc_atom_start(const EmbedTcArgs& a, float*
   }
 }
 
-__device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm, uint64_t*& bar, uint32_t*& s_tmem,
-                                               int smem_bytes) {
-  bar = reinterpret_cast<uint64_t*>(sm + smem_bytes - 64);
-  s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
-  uint4* d = reinterpret_cast<uint4*>(sm);
-  for (int i = threadIdx.x; i < EMB_WIMG / 16; i += blockDim.x) d[i] = a.wimg[i];
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
+// Layer 3 forward of the owned outputs: G0[c] = (h2[c % 50] + tanh(z3 + b2)) (1 + Gt[t_i][t_j][c]).
+template <int H>
+__device__ __forceinline__ void embed_fwd_out(const EmbedTcArgs& a, uint32_t taddr, const float* gt, const float* h2,
+                                              bool rv, float* out_blk, int row) {
+  using O = EmbOwn<H>;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) any |= O::owns_c(16 * k + i);
+    if (!any) continue;
+    float z[16];
+    tmem_ld16(taddr + 64 + 16 * k, z);
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+      const int c = 16 * k + i;
+      if (!O::owns_c(c)) continue;  // pairs never straddle an ownership boundary (24, 50, 74)
+      const float2 g2 = *reinterpret_cast<const float2*>(gt + c);
+      float2 o;
+      o.x = rv ? (h2[c % EMB_E1 - O::b0] + tanhf(z[i] + a.b2[c])) * (1.f + g2.x) : 0.f;
+      o.y = rv ? (h2[(c + 1) % EMB_E1 - O::b0] + tanhf(z[i + 1] + a.b2[c + 1])) * (1.f + g2.y) : 0.f;
+      *reinterpret_cast<float2*>(out_blk + cq_off(row, c)) = o;
+    }
   }
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(s_tmem, 256);
-  handoff();
 }
 
-__global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__ EmbedTcArgs a) {
+__global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_constant__ EmbedTcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {
     if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
@@ -889,41 +943,27 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__
   uint32_t* s_tmem;
   embed_tc_setup(a, sm, bar, s_tmem, EMBF_SMEM);
   const uint32_t tm = *s_tmem;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = warp * 32 + lane;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
   Sync sy{bar, 0u, a.err};
-  float h1[EMB_E0], h2[EMB_E1];
+  float h1[EMB_E0], h2[EMB_E1 - EMB_SPLIT];
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const bool rv = row < nn;
     const size_t rowg = (size_t)atom * NP + row;
     const int tj = rv ? a.atype[a.nlist[rowg]] : 0;
     embed_tc_atom_start(a, s_gt, atom, false);  // visible after the front's barriers
-    embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
-    const float* gt = s_gt + tj * EMB_E2;
-    float4* out = reinterpret_cast<float4*>(a.G0 + (size_t)atom * NP * EMB_E2);
-#pragma unroll
-    for (int blk = 0; blk < 4; ++blk) {
-      float z[32];
-      tmem_ld32(tm + lane_off + 64 + 32 * blk, z);
-#pragma unroll
-      for (int i = 0; i < 32; i += 4) {
-        const int c = 32 * blk + i;
-        if (c < EMB_E2) {
-          const float4 g4 = *reinterpret_cast<const float4*>(gt + c);
-          const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
-          float4 o;
-          float* op = &o.x;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int cc = c + q;
-            op[q] = rv ? (h2[cc % EMB_E1] + tanhf(z[i + q] + a.b2[cc])) * (1.f + gq[q]) : 0.f;
-          }
-          out[(c >> 2) * NP + row] = o;
-        }
-      }
-    }
+    if (half == 0)
+      embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+    else
+      embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+    float* out = a.G0 + (size_t)atom * NP * EMB_E2;
+    if (half == 0)
+      embed_fwd_out<0>(a, tm + lane_off, s_gt + tj * EMB_E2, h2, rv, out, row);
+    else
+      embed_fwd_out<1>(a, tm + lane_off, s_gt + tj * EMB_E2, h2, rv, out, row);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -933,18 +973,103 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_fwd(const __grid_constant__
   if (warp == 0) tmem_dealloc(tm, 256);
 }
 
-__global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__ EmbedTcArgs a) {
-  extern __shared__ __align__(1024) uint8_t sm[];
-  if ((smem_u32(sm) & 1023u) != 0) {
-    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
-    return;
+// Adjoint of layer 3 for one half: dZ3 = g (1 - t3^2) with g = dG0 (1 + Gt)
+// into the dZ3 tiles (8-column groups: half 0 takes columns [0, 56), half 1
+// [56, 104)), and the skip part dh2[c % 50] += g of the owned units.
+template <int H>
+__device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t taddr, const float* gt, const float4* dg,
+                                              bool rv, int row, uint8_t* sDZ3h, uint8_t* sDZ3l, float* dh2) {
+  using O = EmbOwn<H>;
+  constexpr int gs_lo = H == 0 ? 0 : 7, gs_hi = H == 0 ? 7 : 13;  // stored 8-column groups
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int c = 16 * k + i;
+      any |= O::owns_c(c) || ((c >> 3) >= gs_lo && (c >> 3) < gs_hi);
+    }
+    if (!any) continue;
+    float z[16];
+    tmem_ld16(taddr + 64 + 16 * k, z);
+#pragma unroll
+    for (int gg = 0; gg < 2; ++gg) {
+      const int g = 2 * k + gg;
+      const bool store = g >= gs_lo && g < gs_hi;
+      float dz[8];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c4 = 8 * g + 4 * q;
+        bool need = store;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) need |= O::owns_c(c4 + t);
+        float gq[4] = {0.f, 0.f, 0.f, 0.f};
+        if (need && c4 < EMB_E2 && rv) {
+          const float4 d4 = dg[(c4 >> 2) * NP + row];
+          const float4 t4 = *reinterpret_cast<const float4*>(gt + c4);
+          gq[0] = d4.x * (1.f + t4.x); gq[1] = d4.y * (1.f + t4.y);
+          gq[2] = d4.z * (1.f + t4.z); gq[3] = d4.w * (1.f + t4.w);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int c = c4 + t;
+          if (O::owns_c(c)) dh2[c % EMB_E1 - O::b0] += gq[t];
+          float d = 0.f;
+          if (store && c < EMB_E2 && rv) {
+            const float th = tanhf(z[8 * gg + 4 * q + t] + a.b2[c]);
+            d = gq[t] * (1.f - th * th);
+          }
+          dz[4 * q + t] = d;
+        }
+      }
+      if (store) {
+        emb_store8(sDZ3h, row, 8 * g, 128, dz, false);
+        emb_store8(sDZ3l, row, 8 * g, 128, dz, true);
+      }
+    }
   }
-  uint64_t* bar;
-  uint32_t* s_tmem;
-  embed_tc_setup(a, sm, bar, s_tmem, EMBB_SMEM);
-  const uint32_t tm = *s_tmem;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = warp * 32 + lane;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+}
+
+// Adjoint of layer 2 for one half: d = dh2 (skip) + dH2 (product), the skip
+// part of dh1, and dZ2 = d (1 - t2^2) into the dZ2 tiles for the owned units.
+template <int H>
+__device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, const float* h2, const float* dh2,
+                                              bool rv, int row, uint8_t* sDZ2h, uint8_t* sDZ2l, float* dh1) {
+  using O = EmbOwn<H>;
+  constexpr int g_lo = O::b0 / 8, g_hi = H == 0 ? EMB_SPLIT / 8 : 7;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (16 * k + 15 < O::b0 || 16 * k >= 8 * g_hi) continue;
+    float v[16];
+    tmem_ld16(taddr + 16 * k, v);
+#pragma unroll
+    for (int gg = 0; gg < 2; ++gg) {
+      const int g = 2 * k + gg;
+      if (g < g_lo || g >= g_hi) continue;
+      float dz[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int b = 8 * g + i;
+        float d2 = 0.f;
+        if (O::owns_b(b) && rv) {
+          const float d = dh2[b - O::b0] + v[8 * gg + i];
+          dh1[b % EMB_E0] += d;  // skip path of layer 2
+          const float t = h2[b - O::b0] - h1[b % EMB_E0];
+          d2 = d * (1.f - t * t);
+        }
+        dz[i] = d2;
+      }
+      emb_store8(sDZ2h, row, 8 * g, 128, dz, false);
+      emb_store8(sDZ2l, row, 8 * g, 128, dz, true);
+    }
+  }
+}
+
+template <int H>
+__device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
+                                               Sync& sy, int row, bool rv, size_t rowg, const float* gt,
+                                               const float4* dg, float* xch) {
+  using O = EmbOwn<H>;
   const bool issuer = threadIdx.x == 0;
   uint8_t* sW1h = sm;
   uint8_t* sW1l = sW1h + EMB_T1;
@@ -956,9 +1081,56 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
   uint8_t* sDZ3l = sDZ3h + EMB_TD;
   uint8_t* sDZ2h = sm + EMB_WIMG;
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
+  float h1[EMB_E0], h2[O::nb];
+  embed_tc_front<H>(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+  float dh2[O::nb];
+#pragma unroll
+  for (int b = 0; b < O::nb; ++b) dh2[b] = 0.f;
+  embed_bwd_dz3<H>(a, tm + lane_off, gt, dg, rv, row, sDZ3h, sDZ3l, dh2);
+  handoff();
+  // dH2 (product part) = dZ3 W2^T -> TMEM [0, 64)
+  if (issuer)
+    mma_split(tm + 0, smem_u32(sDZ3h), smem_u32(sDZ3l), 128, smem_u32(sW2h), smem_u32(sW2l), true, 112, 64, 7);
+  commit_and_sync(sy, issuer);
+  float dh1[EMB_E0];
+#pragma unroll
+  for (int p = 0; p < EMB_E0; ++p) dh1[p] = 0.f;
+  embed_bwd_dz2<H>(tm + lane_off, h1, h2, dh2, rv, row, sDZ2h, sDZ2l, dh1);
+  handoff();
+  // dH1 (product part) = dZ2 W1^T -> TMEM [64, 96)
+  if (issuer)
+    mma_split(tm + 64, smem_u32(sDZ2h), smem_u32(sDZ2l), 128, smem_u32(sW1h), smem_u32(sW1l), true, 64, 32, 4);
+  commit_and_sync(sy, issuer);
+  float v[32];
+  tmem_ld16(tm + lane_off + 64, v);
+  tmem_ld16(tm + lane_off + 80, v + 16);
+  float dx = 0.f;
+  if (rv) {
+#pragma unroll
+    for (int p = 0; p < EMB_E0; ++p) dx = fmaf(a.W0[p] * (1.f - h1[p] * h1[p]), dh1[p] + (H == 0 ? v[p] : 0.f), dx);
+  }
+  // half 1 hands its part to half 0, which owns the row's dR update
+  if (H == 1) xch[row] = dx;
+  __syncthreads();
+  if (H == 0 && rv) a.dR[rowg * 4] += dx + xch[row];
+}
+
+__global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_constant__ EmbedTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint64_t* bar;
+  uint32_t* s_tmem;
+  embed_tc_setup(a, sm, bar, s_tmem, EMBB_SMEM);
+  const uint32_t tm = *s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
+  float* xch = s_gt + EMB_MAXT * EMB_E2;  // [128] half 1's part of dE/dx
   Sync sy{bar, 0u, a.err};
-  float h1[EMB_E0], h2[EMB_E1];
   if (threadIdx.x == 0 && blockIdx.x < a.n)
     prefetch_l2(a.dG0 + (size_t)blockIdx.x * NP * EMB_E2, NP * EMB_E2 * sizeof(float));
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
@@ -968,83 +1140,11 @@ __global__ void __launch_bounds__(128, 1) k_embed_tc_bwd(const __grid_constant__
     const size_t rowg = (size_t)atom * NP + row;
     const int tj = rv ? a.atype[a.nlist[rowg]] : 0;
     embed_tc_atom_start(a, s_gt, atom, true);  // visible after the front's barriers
-    embed_tc_front(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
-    // dZ3 = g (1 - t3^2), g = dG0 (1 + Gt); skip part of dH2 kept in dh2
-    const float* gt = s_gt + tj * EMB_E2;
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
-    float dh2[EMB_E1];
-#pragma unroll
-    for (int b = 0; b < EMB_E1; ++b) dh2[b] = 0.f;
-#pragma unroll
-    for (int blk = 0; blk < 4; ++blk) {
-      float z[32];
-      tmem_ld32(tm + lane_off + 64 + 32 * blk, z);
-#pragma unroll
-      for (int i = 0; i < 32; i += 4) {
-        const int c0q = 32 * blk + i;
-        float gq[4] = {0.f, 0.f, 0.f, 0.f};
-        if (c0q < EMB_E2 && rv) {
-          const float4 d4 = dg[(c0q >> 2) * NP + row];
-          const float4 t4 = *reinterpret_cast<const float4*>(gt + c0q);
-          gq[0] = d4.x * (1.f + t4.x); gq[1] = d4.y * (1.f + t4.y);
-          gq[2] = d4.z * (1.f + t4.z); gq[3] = d4.w * (1.f + t4.w);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = c0q + q;
-          float dz = 0.f;
-          if (c < EMB_E2 && rv) {
-            const float t = tanhf(z[i + q] + a.b2[c]);
-            dz = gq[q] * (1.f - t * t);
-            dh2[c % EMB_E1] += gq[q];
-          }
-          z[i + q] = dz;
-        }
-      }
-      store16<false>(sDZ3h, row, 32 * blk, 128, z);
-      store16<false>(sDZ3h, row, 32 * blk + 16, 128, z + 16);
-      store16<true>(sDZ3l, row, 32 * blk, 128, z);
-      store16<true>(sDZ3l, row, 32 * blk + 16, 128, z + 16);
-    }
-    handoff();
-    // dH2 (non-skip part) = dZ3 W2^T  -> TMEM [0, 64)
-    if (issuer)
-      mma_split(tm + 0, smem_u32(sDZ3h), smem_u32(sDZ3l), 128, smem_u32(sW2h), smem_u32(sW2l), true, 112, 64, 7);
-    commit_and_sync(sy, issuer);
-    float v[64];
-    tmem_ld32(tm + lane_off + 0, v);
-    tmem_ld32(tm + lane_off + 32, v + 32);
-    float dh1[EMB_E0];
-#pragma unroll
-    for (int p = 0; p < EMB_E0; ++p) dh1[p] = 0.f;
-#pragma unroll
-    for (int b = 0; b < 64; ++b) {
-      float dz2 = 0.f;
-      if (b < EMB_E1 && rv) {
-        const float d = dh2[b] + v[b];
-        dh1[b % EMB_E0] += d;  // skip path of layer 2
-        const float t = h2[b] - h1[b % EMB_E0];
-        dz2 = d * (1.f - t * t);
-      }
-      v[b] = dz2;
-    }
-#pragma unroll
-    for (int c = 0; c < 64; c += 16) {
-      store16<false>(sDZ2h, row, c, 128, v + c);
-      store16<true>(sDZ2l, row, c, 128, v + c);
-    }
-    handoff();
-    // dH1 (non-skip part) = dZ2 W1^T -> TMEM [64, 96)
-    if (issuer)
-      mma_split(tm + 64, smem_u32(sDZ2h), smem_u32(sDZ2l), 128, smem_u32(sW1h), smem_u32(sW1l), true, 64, 32, 4);
-    commit_and_sync(sy, issuer);
-    tmem_ld32(tm + lane_off + 64, v);
-    if (rv) {
-      float dx = 0.f;
-#pragma unroll
-      for (int p = 0; p < EMB_E0; ++p) dx = fmaf(a.W0[p] * (1.f - h1[p] * h1[p]), dh1[p] + v[p], dx);
-      a.dR[rowg * 4] += dx;
-    }
+    if (half == 0)
+      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
+    else
+      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -1269,7 +1369,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     memcpy(et.b2, m->tcw.emb_vec.b2, sizeof(et.b2));
   }
   if (emb_tc && n > 0) {
-    k_embed_tc_fwd<<<std::min(n, 2 * sm_count_dev(m->device)), 128, EMBF_SMEM, st>>>(et);
+    k_embed_tc_fwd<<<std::min(n, 2 * sm_count_dev(m->device)), EMB_THREADS, EMBF_SMEM, st>>>(et);
     note_launch();
   } else {
     launch_embed_fwd(ea, m->emb, st);
@@ -1295,7 +1395,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     prof_mark(m, "attn_bwd_tc", st);
   }
   if (emb_tc && n > 0) {
-    k_embed_tc_bwd<<<std::min(n, 2 * sm_count_dev(m->device)), 128, EMBB_SMEM, st>>>(et);
+    k_embed_tc_bwd<<<std::min(n, 2 * sm_count_dev(m->device)), EMB_THREADS, EMBB_SMEM, st>>>(et);
     note_launch();
   } else {
     relayout(ws.dG, rm_stage, n, m->m1, false, st);
