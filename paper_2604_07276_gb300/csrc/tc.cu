@@ -213,8 +213,10 @@ __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool
 
 // ------------------------------------------------------------------ forward
 // Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K,224K), then the
-// per-key (rhat, w) table and the barriers.  Wo is streamed per atom into
-// slot D by a bulk asynchronous copy.  TMEM columns: [Q K V] accumulators
+// per-key (rhat, w) table and the barriers.  Slot use per atom: G (hi, lo)
+// in A, B; Q, K in C, D while V is still accumulating; V (hi, lo) in A, B;
+// P (hi, lo) in C, D; then O in A and Wo, streamed per atom by a bulk
+// asynchronous copy, in D.  TMEM columns: [Q K V] accumulators
 // 0-383 (S and O reuse 0-127, Y 128-239) and the FP32 layer input kept at
 // 384-511 for the residual.  Thread layout: warp w owns TMEM lane quadrant
 // w % 4 (rows 32 (w % 4) .. +31) and column quarter w / 4 (32 columns).
@@ -239,9 +241,10 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [5]: general, Wo copy, Q, K, V
   uint64_t* bar_ld = bar + 1;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* bar_q = bar + 2;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 5);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, part = warp >> 2;
@@ -251,8 +254,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
-    mbar_init(bar, 1);
-    mbar_init(bar_ld, 1);
+    for (int i = 0; i < 5; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -264,6 +266,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   const uint4* wo_img = a.wimg + 3 * TILE / 16;
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
+  Sync sq{bar_q, 0u, a.err}, sk{bar_q + 1, 0u, a.err}, sv{bar_q + 2, 0u, a.err};
   if (issuer) prefetch_atom(a, blockIdx.x, false);
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
@@ -282,36 +285,48 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
     handoff();
-    // [Q K V] = G Wqkv (+ G_lo Wqkv)
+    // [Q K V] = G Wqkv (+ G_lo Wqkv), one commit group each, so that Q and
+    // K leave TMEM while the later products run
     if (issuer) {
       mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
+      if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
+      mma_commit(bar_q);
       mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
+      if (F16) mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
+      mma_commit(bar_q + 1);
       mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
-      if (F16) {
-        mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
-        mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
-        mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
-      }
+      if (F16) mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
+      mma_commit(bar_q + 2);
     }
-    commit_and_sync(sy, issuer);
-    // Q -> A, K -> B, V -> C (+ V_lo -> D), with biases
-#pragma unroll 1
-    for (int which = 0; which < 3; ++which) {
-      tmem_ld32(tm + lane_off + which * 128 + c0, v);
-      const float* b = a.bqkv + which * 128 + c0;
+    // Q -> C, K -> D with biases (G in A, B is still being read)
+    sq.wait();
+    tmem_ld32(tm + lane_off + 0 + c0, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] += b[i];
-      store_row32<F16>(which == 0 ? sA : (which == 1 ? sB : sC), row, c0, v);
-      if (F16 && which == 2) store_row32<F16, true>(sD, row, c0, v);
-    }
+    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[c0 + i];
+    store_row32<F16>(sC, row, c0, v);
+    sk.wait();
+    tmem_ld32(tm + lane_off + 128 + c0, v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[128 + c0 + i];
+    store_row32<F16>(sD, row, c0, v);
     handoff();
-    // S = Q K^T -> TMEM [0,128)
-    if (issuer) mma_block<F16>(tm + 0, tA, false, 128, tB, false, 128, 128, 8, false);
-    commit_and_sync(sy, issuer);
-    // smooth softmax and gate: P -> slot B (+ P_lo -> slot A); Q and K are dead
+    // S = Q K^T -> TMEM [0,128) while V -> A (+ V_lo -> B)
+    if (issuer) {
+      mma_block<F16>(tm + 0, tC, false, 128, tD, false, 128, 128, 8, false);
+      mma_commit(bar);
+    }
+    sv.wait();
+    tmem_ld32(tm + lane_off + 256 + c0, v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[256 + c0 + i];
+    store_row32<F16>(sA, row, c0, v);
+    if (F16) store_row32<F16, true>(sB, row, c0, v);
+    handoff();
+    sy.wait();
+    // smooth softmax and gate: P -> slot C (+ P_lo -> slot D); Q and K are dead
     tmem_ld32(tm + lane_off + 0 + c0, v);
     {
-      const RowXchg xr(sA, row, part, lane, quad);
+      const RowXchg xr(sC, row, part, lane, quad);
       const bool rv = row < nn;
       const float4 kj = s_key[row];
       const float wj = kj.w;
@@ -340,20 +355,20 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
         const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
         v[i] = v[i] * inv * (wj * kk.w) * c;
       }
-      store_row32<F16>(sB, row, c0, v);
-      if (F16) store_row32<F16, true>(sA, row, c0, v);
+      store_row32<F16>(sC, row, c0, v);
+      if (F16) store_row32<F16, true>(sD, row, c0, v);
     }
     handoff();
     // O = P V (+ P_lo V + P V_lo)  (V as an MN-major operand)
     if (issuer) {
-      mma_block<F16>(tm + 0, tB, false, 128, tC, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tC, false, 128, tA, true, 128, 128, 8, false);
       if (F16) {
-        mma_block<F16>(tm + 0, tA, false, 128, tC, true, 128, 128, 8, true);
-        mma_block<F16>(tm + 0, tB, false, 128, tD, true, 128, 128, 8, true);
+        mma_block<F16>(tm + 0, tD, false, 128, tA, true, 128, 128, 8, true);
+        mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, 128, 8, true);
       }
     }
     commit_and_sync(sy, issuer);
-    // Wo -> slot D (bulk copy, V_lo is dead) while O leaves TMEM -> A
+    // Wo -> slot D (bulk copy, P_lo is dead) while O leaves TMEM -> A
     if (issuer) {
       mbar_expect_tx(bar_ld, WO_TILE);
       bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     commit_and_sync(sy, issuer);
     // LayerNorm, residual
     {
-      const RowXchg xr(sB, row, part, lane, quad);  // P is dead
+      const RowXchg xr(sB, row, part, lane, quad);  // V_lo is dead
       tmem_ld32(tm + lane_off + 128 + c0, v);
       float s1 = 0.f;
 #pragma unroll
@@ -454,9 +469,10 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + B_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [5]: general, Wo copy, dO, Q, K and V
   uint64_t* bar_ld = bar + 1;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* bar_o = bar + 2;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 5);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, part = warp >> 2;
@@ -468,8 +484,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
-    mbar_init(bar, 1);
-    mbar_init(bar_ld, 1);
+    for (int i = 0; i < 5; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -480,6 +495,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
+  Sync so{bar_o, 0u, a.err}, sq{bar_o + 1, 0u, a.err}, sv{bar_o + 2, 0u, a.err};
   const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + 3 * TILE;
   if (issuer) prefetch_atom(a, blockIdx.x, true);
 
@@ -553,43 +569,59 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       store_row32<F16>(sC, row, c0, v);
     }
     handoff();
-    // M0: [Q K V] = G Wqkv (+ G_lo Wqkv) ; dO = dY Wo^T (Wo tile as MN-major)
+    // M0: dO = dY Wo^T (Wo tile as MN-major), then [Q K V] = G Wqkv
+    // (+ G_lo Wqkv), committed as dO | Q | K and V so that dO and Q leave
+    // TMEM while the later products run
     if (issuer && sl.wait()) {
+      mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+      mma_commit(bar_o);
       mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
+      if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
+      mma_commit(bar_o + 1);
       mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
       mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
       if (F16) {
-        mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
         mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
         mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
       }
-      mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+      mma_commit(bar_o + 2);
+    } else if (issuer) {
+      mma_commit(bar_o);  // keep the phases of the waits below in step
+      mma_commit(bar_o + 1);
+      mma_commit(bar_o + 2);
     }
-    commit_and_sync(sy, issuer);
-    // P1: Q -> A, K -> B, V -> C, dO -> D
-#pragma unroll 1
-    for (int which = 0; which < 4; ++which) {
-      tmem_ld32(tm + lane_off + which * 128 + c0, v);
-      if (which < 3) {
-        const float* b = a.bqkv + which * 128 + c0;
+    // P1: dO -> C (dY is dead), Q -> D (Wo is dead), then K -> A and V -> B
+    // once the last products have read G
+    so.wait();
+    tmem_ld32(tm + lane_off + 384 + c0, v);
+    store_row32<F16>(sC, row, c0, v);
+    sq.wait();
+    tmem_ld32(tm + lane_off + 0 + c0, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += b[i];
-      }
-      store_row32<F16>(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
-    }
+    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[c0 + i];
+    store_row32<F16>(sD, row, c0, v);
+    sv.wait();
+    tmem_ld32(tm + lane_off + 128 + c0, v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[128 + c0 + i];
+    store_row32<F16>(sA, row, c0, v);
     handoff();
-    // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
-    if (issuer) {
-      mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
-      mma_block<F16>(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
-    }
+    // M1a: S = Q K^T -> [384,512) while V leaves TMEM
+    if (issuer) mma_block<F16>(tm + 384, tD, false, 128, tA, false, 128, 128, 8, false);
+    tmem_ld32(tm + lane_off + 256 + c0, v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[256 + c0 + i];
+    store_row32<F16>(sB, row, c0, v);
+    handoff();
+    // M1b: dP = dO V^T -> [0,128); the commit covers S too
+    if (issuer) mma_block<F16>(tm + 0, tC, false, 128, tB, false, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
     // P2: softmax adjoint over this thread's 32 keys, with the row max and
     // normaliser the forward pass stored: sum_k A_jk dA_jk first, then the
     // main pass in two 16-key halves that reload S and dP from TMEM; P ->
-    // slot C, dS -> TMEM over the consumed S columns
+    // slot B, dS -> TMEM over the consumed S columns
     {
-      const RowXchg xr(sC, row, part, lane, quad);  // V is dead after dP
+      const RowXchg xr(sB, row, part, lane, quad);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
       const float4 kj = s_key[row];
       const float wj = kj.w;
@@ -651,7 +683,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
           w4.y = pack16<F16>(pv[8 * q + 2], pv[8 * q + 3]);
           w4.z = pack16<F16>(pv[8 * q + 4], pv[8 * q + 5]);
           w4.w = pack16<F16>(pv[8 * q + 6], pv[8 * q + 7]);
-          sw128_store8(sC, row, c0 + h + 8 * q, 128, w4);
+          sw128_store8(sB, row, c0 + h + 8 * q, 128, w4);
         }
         tmem_st16(tS + h, t);  // dS over this half's consumed S columns
         const float sw_ = reduce_scatter16(cw);
@@ -671,20 +703,20 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     }
     handoff();
     // M2: dV = P^T dO -> [128,256)
-    if (issuer) mma_block<F16>(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
+    if (issuer) mma_block<F16>(tm + 128, tB, true, 128, tC, true, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
-    tmem_ld32(tm + lane_off + 384 + c0, v);  // dS
-    store_row32<F16>(sC, row, c0, v);
+    tmem_ld32(tm + lane_off + 384 + c0, v);  // dS -> B (P is dead)
+    store_row32<F16>(sB, row, c0, v);
     handoff();
     // M3: dQ = dS K -> [0,128) ; dK = dS^T Q -> [256,384)
     if (issuer) {
-      mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, 128, 8, false);
-      mma_block<F16>(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tB, false, 128, tA, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 256, tB, true, 128, tD, true, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
-    // P4: dQ -> B, dK -> A, dV -> D ; dgeo of this atom
+    // P4: dQ -> C, dK -> A, dV -> D ; dgeo of this atom
     tmem_ld32(tm + lane_off + 0 + c0, v);
-    store_row32<F16>(sB, row, c0, v);
+    store_row32<F16>(sC, row, c0, v);
     tmem_ld32(tm + lane_off + 256 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     tmem_ld32(tm + lane_off + 128 + c0, v);
@@ -712,7 +744,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     handoff();
     // M4: dG = dQ Wq^T + dK Wk^T + dV Wv^T -> [384, 496)
     if (issuer) {
-      mma_block<F16>(tm + 384, tB, false, 128, tWq, true, 128, WO_ROWS, 8, false);
+      mma_block<F16>(tm + 384, tC, false, 128, tWq, true, 128, WO_ROWS, 8, false);
       mma_block<F16>(tm + 384, tA, false, 128, tWk, true, 128, WO_ROWS, 8, true);
       mma_block<F16>(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
     }
