@@ -469,10 +469,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + B_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [5]: general, Wo copy, dO, Q, K and V
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
   uint64_t* bar_ld = bar + 1;
-  uint64_t* bar_o = bar + 2;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 5);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, part = warp >> 2;
@@ -484,7 +483,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
-    for (int i = 0; i < 5; ++i) mbar_init(bar + i, 1);
+    mbar_init(bar, 1);
+    mbar_init(bar_ld, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -495,7 +495,6 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
-  Sync so{bar_o, 0u, a.err}, sq{bar_o + 1, 0u, a.err}, sv{bar_o + 2, 0u, a.err};
   const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + 3 * TILE;
   if (issuer) prefetch_atom(a, blockIdx.x, true);
 
@@ -569,59 +568,43 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       store_row32<F16>(sC, row, c0, v);
     }
     handoff();
-    // M0: dO = dY Wo^T (Wo tile as MN-major), then [Q K V] = G Wqkv
-    // (+ G_lo Wqkv), committed as dO | Q | K and V so that dO and Q leave
-    // TMEM while the later products run
+    // M0: [Q K V] = G Wqkv (+ G_lo Wqkv) ; dO = dY Wo^T (Wo tile as MN-major)
     if (issuer && sl.wait()) {
-      mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
-      mma_commit(bar_o);
       mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
-      if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
-      mma_commit(bar_o + 1);
       mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
       mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
       if (F16) {
+        mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
         mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
         mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
       }
-      mma_commit(bar_o + 2);
-    } else if (issuer) {
-      mma_commit(bar_o);  // keep the phases of the waits below in step
-      mma_commit(bar_o + 1);
-      mma_commit(bar_o + 2);
+      mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
     }
-    // P1: dO -> C (dY is dead), Q -> D (Wo is dead), then K -> A and V -> B
-    // once the last products have read G
-    so.wait();
-    tmem_ld32(tm + lane_off + 384 + c0, v);
-    store_row32<F16>(sC, row, c0, v);
-    sq.wait();
-    tmem_ld32(tm + lane_off + 0 + c0, v);
+    commit_and_sync(sy, issuer);
+    // P1: Q -> A, K -> B, V -> C, dO -> D
+#pragma unroll 1
+    for (int which = 0; which < 4; ++which) {
+      tmem_ld32(tm + lane_off + which * 128 + c0, v);
+      if (which < 3) {
+        const float* b = a.bqkv + which * 128 + c0;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[c0 + i];
-    store_row32<F16>(sD, row, c0, v);
-    sv.wait();
-    tmem_ld32(tm + lane_off + 128 + c0, v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[128 + c0 + i];
-    store_row32<F16>(sA, row, c0, v);
+        for (int i = 0; i < 32; ++i) v[i] += b[i];
+      }
+      store_row32<F16>(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
+    }
     handoff();
-    // M1a: S = Q K^T -> [384,512) while V leaves TMEM
-    if (issuer) mma_block<F16>(tm + 384, tD, false, 128, tA, false, 128, 128, 8, false);
-    tmem_ld32(tm + lane_off + 256 + c0, v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[256 + c0 + i];
-    store_row32<F16>(sB, row, c0, v);
-    handoff();
-    // M1b: dP = dO V^T -> [0,128); the commit covers S too
-    if (issuer) mma_block<F16>(tm + 0, tC, false, 128, tB, false, 128, 128, 8, false);
+    // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
+    if (issuer) {
+      mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
+    }
     commit_and_sync(sy, issuer);
     // P2: softmax adjoint over this thread's 32 keys, with the row max and
     // normaliser the forward pass stored: sum_k A_jk dA_jk first, then the
     // main pass in two 16-key halves that reload S and dP from TMEM; P ->
-    // slot B, dS -> TMEM over the consumed S columns
+    // slot C, dS -> TMEM over the consumed S columns
     {
-      const RowXchg xr(sB, row, part, lane, quad);  // V is dead after dP
+      const RowXchg xr(sC, row, part, lane, quad);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
       const float4 kj = s_key[row];
       const float wj = kj.w;
@@ -683,7 +666,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
           w4.y = pack16<F16>(pv[8 * q + 2], pv[8 * q + 3]);
           w4.z = pack16<F16>(pv[8 * q + 4], pv[8 * q + 5]);
           w4.w = pack16<F16>(pv[8 * q + 6], pv[8 * q + 7]);
-          sw128_store8(sB, row, c0 + h + 8 * q, 128, w4);
+          sw128_store8(sC, row, c0 + h + 8 * q, 128, w4);
         }
         tmem_st16(tS + h, t);  // dS over this half's consumed S columns
         const float sw_ = reduce_scatter16(cw);
@@ -703,20 +686,20 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     }
     handoff();
     // M2: dV = P^T dO -> [128,256)
-    if (issuer) mma_block<F16>(tm + 128, tB, true, 128, tC, true, 128, 128, 8, false);
+    if (issuer) mma_block<F16>(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
     commit_and_sync(sy, issuer);
-    tmem_ld32(tm + lane_off + 384 + c0, v);  // dS -> B (P is dead)
-    store_row32<F16>(sB, row, c0, v);
+    tmem_ld32(tm + lane_off + 384 + c0, v);  // dS
+    store_row32<F16>(sC, row, c0, v);
     handoff();
     // M3: dQ = dS K -> [0,128) ; dK = dS^T Q -> [256,384)
     if (issuer) {
-      mma_block<F16>(tm + 0, tB, false, 128, tA, true, 128, 128, 8, false);
-      mma_block<F16>(tm + 256, tB, true, 128, tD, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
-    // P4: dQ -> C, dK -> A, dV -> D ; dgeo of this atom
+    // P4: dQ -> B, dK -> A, dV -> D ; dgeo of this atom
     tmem_ld32(tm + lane_off + 0 + c0, v);
-    store_row32<F16>(sC, row, c0, v);
+    store_row32<F16>(sB, row, c0, v);
     tmem_ld32(tm + lane_off + 256 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     tmem_ld32(tm + lane_off + 128 + c0, v);
@@ -744,7 +727,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     handoff();
     // M4: dG = dQ Wq^T + dK Wk^T + dV Wv^T -> [384, 496)
     if (issuer) {
-      mma_block<F16>(tm + 384, tC, false, 128, tWq, true, 128, WO_ROWS, 8, false);
+      mma_block<F16>(tm + 384, tB, false, 128, tWq, true, 128, WO_ROWS, 8, false);
       mma_block<F16>(tm + 384, tA, false, 128, tWk, true, 128, WO_ROWS, 8, true);
       mma_block<F16>(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
     }
