@@ -600,15 +600,18 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     }
     commit_and_sync(sy, issuer);
     // P2: softmax adjoint over this thread's 32 keys, with the row max and
-    // normaliser the forward pass stored: sum_k A_jk dA_jk first, then the
-    // main pass in two 16-key halves that reload S and dP from TMEM; P ->
-    // slot C, dS -> TMEM over the consumed S columns
+    // normaliser the forward pass stored: A and sum_k A_jk dA_jk first, then
+    // the main pass in 8-key pieces that reload S, dP, A and the gate cosine
+    // from TMEM; P -> slot C, dS -> TMEM over the consumed S columns
     {
       const RowXchg xr(sC, row, part, lane, quad);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
       const float4 kj = s_key[row];
       const float wj = kj.w;
       const float mx = sst.x, inv = sst.y;
+      // A and the gate cosine c of this thread's keys, kept in the dead K and
+      // V accumulator columns for the main pass
+      const uint32_t tAw = tm + lane_off + 128 + c0, tCs = tm + lane_off + 256 + c0;
       float wsum = 0.f;
       {
         float t[32], u[32];
@@ -617,68 +620,74 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int k = c0 + i;
+          const float4 kk = s_key[k];
+          const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+          float A = 0.f;
           if (k < nn && rv) {
-            const float4 kk = s_key[k];
             const float ww = wj * kk.w;
-            const float e = __expf((t[i] * a.scale + a.shift) * ww - mx);
-            const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
-            wsum += e * u[i] * ww * c;
+            A = __expf((t[i] * a.scale + a.shift) * ww - mx) * inv;
+            wsum += A * u[i] * ww * c;
           }
+          t[i] = A;
+          u[i] = c;
         }
+        tmem_st32(tAw, t);
+        tmem_st32(tCs, u);
       }
-      wsum = xr.sum(wsum);  // ends with the quadrant's barrier: its rows of slot C are free
-      const float tsum = wsum * inv;  // sum_k A_jk dA_jk
+      const float tsum = xr.sum(wsum);  // sum_k A_jk dA_jk; ends with the quadrant's barrier
       float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
       float4* cp = reinterpret_cast<float4*>(colp) + quad * 128 + c0;
 #pragma unroll 1
       for (int h = 0; h < 32; h += 16) {
-        float t[16], u[16], cw[16], dcv[16], pv[16];
-        tmem_ld16(tS + h, t);
-        tmem_ld16(tP + h, u);
+        float cw[16], dcv[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int k = c0 + h + i;
-          float H = 0.f, dc = 0.f, P = 0.f, dS = 0.f;
-          const float4 kk = s_key[k];
-          if (k < nn && rv) {
-            const float l = t[i] * a.scale;
-            const float ww = wj * kk.w;
-            const float A = __expf((l + a.shift) * ww - mx) * inv;
-            const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
-            const float dP = u[i];
-            const float dLp = A * (dP * ww * c - tsum);
-            H = dP * A * c + dLp * (l + a.shift);
-            dc = dP * A * ww;
-            P = A * ww * c;
-            dS = dLp * ww * a.scale;
+        for (int e8 = 0; e8 < 16; e8 += 8) {
+          float t[8], u[8], Av[8], cv[8], pv[8];
+          tmem_ld8(tS + h + e8, t);
+          tmem_ld8(tP + h + e8, u);
+          tmem_ld8(tAw + h + e8, Av);
+          tmem_ld8(tCs + h + e8, cv);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = c0 + h + e8 + i;
+            float H = 0.f, dc = 0.f, P = 0.f, dS = 0.f;
+            const float4 kk = s_key[k];
+            if (k < nn && rv) {
+              const float l = t[i] * a.scale;
+              const float ww = wj * kk.w;
+              const float A = Av[i], c = cv[i], dP = u[i];
+              const float dLp = A * (dP * ww * c - tsum);
+              H = dP * A * c + dLp * (l + a.shift);
+              dc = dP * A * ww;
+              P = A * ww * c;
+              dS = dLp * ww * a.scale;
+            }
+            rw_ += H * kk.w;
+            rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
+            cw[e8 + i] = H * wj;
+            dcv[e8 + i] = dc;
+            pv[i] = P;
+            t[i] = dS;
           }
-          rw_ += H * kk.w;
-          rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
-          cw[i] = H * wj;
-          dcv[i] = dc;
-          pv[i] = P;
-          t[i] = dS;
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
           uint4 w4;
-          w4.x = pack16<F16>(pv[8 * q + 0], pv[8 * q + 1]);
-          w4.y = pack16<F16>(pv[8 * q + 2], pv[8 * q + 3]);
-          w4.z = pack16<F16>(pv[8 * q + 4], pv[8 * q + 5]);
-          w4.w = pack16<F16>(pv[8 * q + 6], pv[8 * q + 7]);
-          sw128_store8(sC, row, c0 + h + 8 * q, 128, w4);
+          w4.x = pack16<F16>(pv[0], pv[1]);
+          w4.y = pack16<F16>(pv[2], pv[3]);
+          w4.z = pack16<F16>(pv[4], pv[5]);
+          w4.w = pack16<F16>(pv[6], pv[7]);
+          sw128_store8(sC, row, c0 + h + e8, 128, w4);
+          tmem_st8(tS + h + e8, t);  // dS over these consumed S columns
         }
-        tmem_st16(tS + h, t);  // dS over this half's consumed S columns
         const float sw_ = reduce_scatter16(cw);
+        float tmp[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) pv[i] = dcv[i] * kj.x;
-        const float sx = reduce_scatter16(pv);
+        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
+        const float sx = reduce_scatter16(tmp);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) pv[i] = dcv[i] * kj.y;
-        const float sy_ = reduce_scatter16(pv);
+        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
+        const float sy_ = reduce_scatter16(tmp);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) pv[i] = dcv[i] * kj.z;
-        const float sz = reduce_scatter16(pv);
+        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
+        const float sz = reduce_scatter16(tmp);
         if (lane < 16) cp[h + lane] = make_float4(sx, sy_, sz, sw_);
       }
       // row parts of dE/dw_j and dE/drhat_j, per column quarter
