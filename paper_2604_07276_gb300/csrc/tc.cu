@@ -241,10 +241,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sWk = sWq + TILE;
   uint8_t* sWv = sWk + TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [5]: general, Wo copy, Q, K, V
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wo copy, Q, K, V, inputs
   uint64_t* bar_ld = bar + 1;
   uint64_t* bar_q = bar + 2;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 5);
+  uint64_t* bar_in = bar + 5;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 6);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, part = warp >> 2;
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 
   copy_image(sWq, a.wimg, 3 * TILE);
   if (issuer) {
-    for (int i = 0; i < 5; ++i) mbar_init(bar + i, 1);
+    for (int i = 0; i < 6; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -267,20 +268,28 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
   Sync sq{bar_q, 0u, a.err}, sk{bar_q + 1, 0u, a.err}, sv{bar_q + 2, 0u, a.err};
-  if (issuer) prefetch_atom(a, blockIdx.x, false);
+  Sync si{bar_in, 0u, a.err};
+  const uint32_t g_bytes = (uint32_t)(NP * a.m1 * sizeof(float)), k_bytes = NP * sizeof(float4);
+  // An atom's layer input (its column-quad interleaved block, as stored) and
+  // its per-key (rhat, w) rows (zero past nnei) arrive by bulk copies: into
+  // slots C..D and the key table, during the previous atom's LayerNorm.
+  auto fetch_inputs = [&](int at) {
+    const size_t b = (size_t)at * NP;
+    mbar_expect_tx(bar_in, g_bytes + k_bytes);
+    bulk_g2s(sC, a.Gin + b * a.m1, g_bytes, bar_in);
+    bulk_g2s(s_key, a.rw + b * 4, k_bytes, bar_in);
+  };
+  if (issuer && (int)blockIdx.x < a.n) fetch_inputs(blockIdx.x);
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     if (issuer) prefetch_atom(a, atom + gridDim.x, false);
-    if (tid < 128) {
-      const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
-      s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    si.wait();
     float v[32];
     // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B), and
     // kept in TMEM for the residual
-    load_cq32(a.Gin + base * a.m1, a.m1, row, c0, v);
+    load_cq32(reinterpret_cast<const float*>(sC), a.m1, row, c0, v);
     tmem_st32(tm + lane_off + 384 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
@@ -379,6 +388,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     // Y = O Wo -> TMEM [128, 240)
     if (issuer && sl.wait()) mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, 8, false);
     commit_and_sync(sy, issuer);
+    // C, D and the key table are dead: the next atom's inputs start to arrive
+    if (issuer && atom + (int)gridDim.x < a.n) fetch_inputs(atom + gridDim.x);
     // LayerNorm, residual
     {
       const RowXchg xr(sB, row, part, lane, quad);  // V_lo is dead
