@@ -63,6 +63,24 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Sum over the 32 lanes of a warp of 16 values per lane; lanes l and l + 16
+// return the sum of value l % 16 (butterfly reduce-scatter, fixed order;
+// 16 shuffles instead of 16 full reductions).
+__device__ __forceinline__ float warp_reduce_scatter16(float* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = up ? v[i] : v[i + w];
+      const float keep = up ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 // Minimum-image displacement component d - L * rint(d / L), every operation
 // rounded separately (no FMA contraction) so that the host can reproduce it
 // bit for bit.

@@ -864,13 +864,13 @@ __global__ void k_desc_fwd(DescArgs a) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) t[c][k] = fmaf(rr[c], gg[k], t[c][k]);
       }
+      float tv[16];
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float v = warp_sum(t[c][k]);
-          if (lane == 0) Ts[c * a.m1 + 4 * q + k] = v * inv_sel;
-        }
+        for (int k = 0; k < 4; ++k) tv[4 * c + k] = t[c][k];
+      const float v = warp_reduce_scatter16(tv);  // lane l: entry l % 16 = (c, k) = (l / 4, l % 4)
+      if (lane < 16) Ts[(lane >> 2) * a.m1 + 4 * q + (lane & 3)] = v * inv_sel;
     }
   } else {
     for (int c = threadIdx.x; c < a.m1; c += blockDim.x) {

@@ -179,23 +179,6 @@ struct RowXchg {
   }
 };
 
-// Sum over the 32 lanes of a warp of 16 values per lane; lanes l and l + 16
-// return the sum of value l % 16 (butterfly reduce-scatter, fixed order).
-__device__ __forceinline__ float reduce_scatter16(float* v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int w = 8; w >= 1; w >>= 1) {
-    const bool up = (lane & w) != 0;
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const float send = up ? v[i] : v[i + w];
-      const float keep = up ? v[i + w] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
-}
-
 // Bring the per-row inputs of centre atom `atom` (if it exists) into L2 ahead
 // of its turn: one thread, bulk prefetches.
 __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool bwd) {
@@ -688,17 +671,17 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
           sw128_store8(sC, row, c0 + h + e8, 128, w4);
           tmem_st8(tS + h + e8, t);  // dS over these consumed S columns
         }
-        const float sw_ = reduce_scatter16(cw);
+        const float sw_ = warp_reduce_scatter16(cw);
         float tmp[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
-        const float sx = reduce_scatter16(tmp);
+        const float sx = warp_reduce_scatter16(tmp);
 #pragma unroll
         for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
-        const float sy_ = reduce_scatter16(tmp);
+        const float sy_ = warp_reduce_scatter16(tmp);
 #pragma unroll
         for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
-        const float sz = reduce_scatter16(tmp);
+        const float sz = warp_reduce_scatter16(tmp);
         if (lane < 16) cp[h + lane] = make_float4(sx, sy_, sz, sw_);
       }
       // row parts of dE/dw_j and dE/drhat_j, per column quarter
