@@ -147,7 +147,11 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
   const float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
   const float iLf[3] = {1.0f / Lf[0], 1.0f / Lf[1], 1.0f / Lf[2]};
   const float rc2_screen = (float)rc2 * 1.0001f + 1e-4f;
-  int cnt = 0;
+  // pass 1: FP32 screen of every candidate in the 27 cells; survivors are
+  // compacted into idx[] so that the FP64 decision below runs on full warps
+  // (this part's FP64 rate is low, and a divergent FP64 branch costs the whole
+  // warp)
+  int ns = 0;
   for (int dz = -oz; dz <= oz; ++dz)
     for (int dy = -oy; dy <= oy; ++dy)
       for (int dx = -ox; dx <= ox; ++dx) {
@@ -158,44 +162,59 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
         int b = cell_start[c], e = cell_start[c + 1];
         for (int base = b; base < e; base += 32) {
           int t = base + lane;
-          bool hit = false;
-          double d2 = 0.0;
+          bool pass = false;
           int j = -1;
           if (t < e) {
             j = cell_atoms[t];
-            // FP32 screen from the FP32 coordinates: a component is off by
-            // at most ~1e-5 A, the squared distance near rc^2 by ~1.3e-4 A^2,
-            // far inside the margin, so a pair rejected here is never a
-            // neighbour (where FP32 and FP64 pick different images, both
-            // distances exceed L/2 > rcut).  Survivors are decided exactly
-            // in FP64.
+            // a component of the FP32 difference is off by at most ~1e-5 A
+            // and the squared distance near rc^2 by ~1.3e-4 A^2, far inside
+            // the margin, so a pair rejected here is never a neighbour (where
+            // FP32 and FP64 pick different images, both distances exceed
+            // L/2 > rcut)
             const float4 pj = coordf[j];
             float fx = pj.x - pi.x, fy = pj.y - pi.y, fz = pj.z - pi.z;
             fx -= Lf[0] * rintf(fx * iLf[0]);
             fy -= Lf[1] * rintf(fy * iLf[1]);
             fz -= Lf[2] * rintf(fz * iLf[2]);
-            if (j != i && fx * fx + fy * fy + fz * fz < rc2_screen) {
-              const double ddx = mic_near(__dsub_rn(coord[3 * j], xi), g.L[0]);
-              const double ddy = mic_near(__dsub_rn(coord[3 * j + 1], yi), g.L[1]);
-              const double ddz = mic_near(__dsub_rn(coord[3 * j + 2], zi), g.L[2]);
-              d2 = sqdist(ddx, ddy, ddz);
-              hit = d2 < rc2;
-            }
+            pass = j != i && fx * fx + fy * fy + fz * fz < rc2_screen;
           }
-          unsigned bal = __ballot_sync(0xffffffffu, hit);
-          int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-          if (hit && pos < NBR_CAP) {
-            key[pos] = (unsigned long long)__double_as_longlong(d2);
-            idx[pos] = j;
-          }
-          cnt += __popc(bal);
+          const unsigned bal = __ballot_sync(0xffffffffu, pass);
+          const int pos = ns + __popc(bal & ((1u << lane) - 1u));
+          if (pass && pos < NBR_CAP) idx[pos] = j;
+          ns += __popc(bal);
         }
       }
-  if (lane == 0) ncand[i] = cnt;
-  if (cnt > NBR_CAP) {
+  if (ns > NBR_CAP) {
     if (lane == 0) set_err(err, ERR_CAPACITY);
-    cnt = NBR_CAP;
+    ns = NBR_CAP;
   }
+  __syncwarp();
+  // pass 2: the exact FP64 decision on the survivors, compacted in place
+  // (a write never reaches an entry that is still to be read)
+  int cnt = 0;
+  for (int base = 0; base < ns; base += 32) {
+    const int t = base + lane;
+    bool hit = false;
+    double d2 = 0.0;
+    int j = -1;
+    if (t < ns) {
+      j = idx[t];
+      const double ddx = mic_near(__dsub_rn(coord[3 * j], xi), g.L[0]);
+      const double ddy = mic_near(__dsub_rn(coord[3 * j + 1], yi), g.L[1]);
+      const double ddz = mic_near(__dsub_rn(coord[3 * j + 2], zi), g.L[2]);
+      d2 = sqdist(ddx, ddy, ddz);
+      hit = d2 < rc2;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+    if (hit) {
+      key[pos] = (unsigned long long)__double_as_longlong(d2);
+      idx[pos] = j;
+    }
+    cnt += __popc(bal);
+    __syncwarp();
+  }
+  if (lane == 0) ncand[i] = cnt;
   int P = 1;
   while (P < cnt) P <<= 1;
   for (int t = cnt + lane; t < P; t += 32) {
