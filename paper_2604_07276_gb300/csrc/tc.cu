@@ -315,13 +315,18 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     if (F16) store_row32<F16, true>(sB, row, c0, v);
     handoff();
     sy.wait();
-    // smooth softmax and gate: P -> slot C (+ P_lo -> slot D); Q and K are dead
+    // smooth softmax and gate: P -> slot C (+ P_lo -> slot D); Q and K are dead.
+    // Row j of P carries the factor w_j, which vanishes for neighbours near
+    // rcut; the tiles hold P / w_j instead (no FP16 subnormals), and w_j is
+    // applied to Y = (P / w_j) V Wo in FP32 before the LayerNorm.
     tmem_ld32(tm + lane_off + 0 + c0, v);
+    float w_row;
     {
       const RowXchg xr(sC, row, part, lane, quad);
       const bool rv = row < nn;
       const float4 kj = s_key[row];
       const float wj = kj.w;
+      w_row = wj;
       float mx = -INFINITY;
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
@@ -345,7 +350,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       for (int i = 0; i < 32; ++i) {
         const float4 kk = s_key[c0 + i];
         const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
-        v[i] = v[i] * inv * (wj * kk.w) * c;
+        v[i] = v[i] * inv * kk.w * c;
       }
       store_row32<F16>(sC, row, c0, v);
       if (F16) store_row32<F16, true>(sD, row, c0, v);
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int c = c0 + i;
-        v[i] = c < a.m1 ? v[i] + a.bo[c] : 0.f;
+        v[i] = c < a.m1 ? w_row * v[i] + a.bo[c] : 0.f;
         s1 += v[i];
       }
       const float mean = xr.sum(s1) / (float)a.m1;
