@@ -94,6 +94,25 @@ DP_API int dp_compute_device(dp_model* m, int natoms, const double* d_coord, con
                       const int* d_atype, double* d_energy, double* d_force, double* d_virial,
                       double* d_atom_energy, void* cuda_stream);
 
+/* Local and ghost atoms (Sec. II-C, Eq. eq_forcesLocalGhost): atoms
+ * [0, nlocal) are local, atoms [nlocal, natoms) are ghost copies that a
+ * domain-decomposed caller imports from its neighbours.  Neighbour lists run
+ * over all natoms atoms, but only local atoms' energies count (m_j = 1 for
+ * local j, 0 for ghosts): energy = sum of e_j over local j; force on every
+ * atom k, local or ghost, = -d(energy)/dx_k (ghost forces are for the caller
+ * to add to their owners); virial = -sum over local centres i of
+ * sum_j r_ij (x) dE/dr_ij; atom_energy is e_j for local atoms and 0 for
+ * ghosts.  0 <= nlocal <= natoms, else DP_ERR_ARG; nlocal == natoms is
+ * dp_compute / dp_compute_device.  A caller with explicit ghost images
+ * passes a box whose edges exceed the extent of all atoms plus rcut along
+ * every non-periodic direction. */
+DP_API int dp_compute_local(dp_model* m, int natoms, int nlocal, const double* coord, const double* box,
+                            const int* atype, double* energy, double* force, double* virial,
+                            double* atom_energy);
+DP_API int dp_compute_device_local(dp_model* m, int natoms, int nlocal, const double* d_coord,
+                                   const double* d_box, const int* d_atype, double* d_energy, double* d_force,
+                                   double* d_virial, double* d_atom_energy, void* cuda_stream);
+
 /* Several independent frames of uneven size from HOST arrays.  Frame f owns
  * atoms [atom_offsets[f], atom_offsets[f+1]) of coord / atype / force and
  * box[9f .. 9f+8], energy[f], virial[9f .. 9f+8].  Frames never interact. */

@@ -21,7 +21,7 @@ STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_IO", -3: "DP_ERR_BOX", -4: "
           -5: "DP_ERR_CUDA", -6: "DP_ERR_TIMEOUT", -7: "DP_ERR_NAN", -8: "DP_ERR_UNSUPPORTED"}
 PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2}
 
-EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_batch", "dp_reserve", "dp_set_precision",
+EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_local", "dp_compute_device_local", "dp_compute_batch", "dp_reserve", "dp_set_precision",
            "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
            "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_md_run", "dp_param_count", "dp_get_params",
            "dp_set_params", "dp_get_grad", "dp_zero_grad", "dp_train_frame", "dp_adam_step", "dp_last_error",
@@ -51,6 +51,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.dp_compute.argtypes = [P, ctypes.c_int, D, D, I, D, D, D, D]
     lib.dp_compute_device.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.dp_compute_local.argtypes = [P, ctypes.c_int, ctypes.c_int, D, D, I, D, D, D, D]
+    lib.dp_compute_device_local.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, P]
     lib.dp_compute_batch.argtypes = [P, ctypes.c_int, I, D, D, I, D, D, D]
     lib.dp_reserve.argtypes = [P, ctypes.c_int]
     lib.dp_set_precision.argtypes = [P, ctypes.c_int]
@@ -150,8 +152,9 @@ class DPA1:
         self.device = device
 
     # -- host arrays ---------------------------------------------------------
-    def compute(self, coord, box, atype, atom_energy: bool = False):
-        """(E, F [N,3], W [3,3], e [N] or None) from host arrays (``dp_compute``)."""
+    def compute(self, coord, box, atype, atom_energy: bool = False, nlocal: Optional[int] = None):
+        """(E, F [N,3], W [3,3], e [N] or None) from host arrays (``dp_compute``;
+        with ``nlocal``, ``dp_compute_local``: atoms [nlocal, N) are ghosts)."""
         c = np.ascontiguousarray(coord, dtype=np.float64).reshape(-1, 3)
         t = np.ascontiguousarray(atype, dtype=np.int32)
         b = box9(box)
@@ -160,8 +163,12 @@ class DPA1:
         f = np.zeros((n, 3))
         w = np.zeros(9)
         ae = np.zeros(n) if atom_energy else None
-        _check(self.lib.dp_compute(self.h, n, _dptr(c), _dptr(b), _iptr(t), _dptr(e), _dptr(f), _dptr(w),
-                                   _dptr(ae) if ae is not None else None))
+        aep = _dptr(ae) if ae is not None else None
+        if nlocal is None:
+            _check(self.lib.dp_compute(self.h, n, _dptr(c), _dptr(b), _iptr(t), _dptr(e), _dptr(f), _dptr(w), aep))
+        else:
+            _check(self.lib.dp_compute_local(self.h, n, int(nlocal), _dptr(c), _dptr(b), _iptr(t), _dptr(e), _dptr(f),
+                                             _dptr(w), aep))
         return float(e[0]), f, w.reshape(3, 3), ae
 
     def compute_batch(self, frames):
@@ -180,14 +187,21 @@ class DPA1:
         return e, [f[offs[i]:offs[i + 1]] for i in range(len(frames))], w.reshape(-1, 3, 3)
 
     # -- device arrays (torch tensors) ----------------------------------------
-    def compute_device(self, coord, box, atype, energy, force, virial, atom_energy=None, stream=None):
-        """``dp_compute_device`` on CUDA tensors; no host synchronisation."""
+    def compute_device(self, coord, box, atype, energy, force, virial, atom_energy=None, stream=None, nlocal=None):
+        """``dp_compute_device`` (``dp_compute_device_local`` with ``nlocal``) on
+        CUDA tensors; no host synchronisation."""
         import torch
 
         st = stream if stream is not None else torch.cuda.current_stream(coord.device).cuda_stream
-        _check(self.lib.dp_compute_device(self.h, int(coord.shape[0]), coord.data_ptr(), box.data_ptr(),
-                                          atype.data_ptr(), energy.data_ptr(), force.data_ptr(), virial.data_ptr(),
-                                          atom_energy.data_ptr() if atom_energy is not None else None, st))
+        n = int(coord.shape[0])
+        ae = atom_energy.data_ptr() if atom_energy is not None else None
+        if nlocal is None:
+            _check(self.lib.dp_compute_device(self.h, n, coord.data_ptr(), box.data_ptr(), atype.data_ptr(),
+                                              energy.data_ptr(), force.data_ptr(), virial.data_ptr(), ae, st))
+        else:
+            _check(self.lib.dp_compute_device_local(self.h, n, int(nlocal), coord.data_ptr(), box.data_ptr(),
+                                                    atype.data_ptr(), energy.data_ptr(), force.data_ptr(),
+                                                    virial.data_ptr(), ae, st))
 
     def nlist_device(self, coord, box, stream=None):
         import torch

@@ -382,7 +382,7 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
     launch_head_bias_grad(atype, n, m->grad + m->off_ebias, m->grad + m->off_bout, gs, (float)m->out_scale, st);
   }
   // a10: fitting backward, seeded with dE/dH_last = out_scale * w_out
-  launch_fill_rows(ws.dHa, m->w_out, n, fan, st);
+  launch_fill_rows(ws.dHa, m->w_out, n, m->call_nlocal, fan, st);
   float* dH = ws.dHa;
   float* dHn = ws.dHb;
   for (int l = m->nfit - 1; l >= 0; --l) {
@@ -463,12 +463,13 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   prof_mark(m, "embed_bwd", st);
 }
 
-int run_device(dp_model* m, int n, const double* coord, const double* box, const int* atype, double* energy,
+int run_device(dp_model* m, int n, int nlocal, const double* coord, const double* box, const int* atype, double* energy,
                double* force, double* virial, double* atom_energy, cudaStream_t st) {
   Workspace& ws = m->ws;
   if (n > ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
   m->last_stream = st;
   m->last_natoms = n;
+  m->call_nlocal = nlocal;
   prof_mark(m, "start", st);
   run_neighbors(m, n, coord, box, atype, st);
   prof_mark(m, "neighbors", st);
@@ -498,7 +499,7 @@ int run_device(dp_model* m, int n, const double* coord, const double* box, const
   launch_reverse(ws.nlist, n, ws.rev_cnt, ws.rev_rows, m->d_err, st);
   ForceArgs fa{};
   fa.g = ws.g; fa.rv = ws.rv; fa.nnei = ws.nnei; fa.rev_cnt = ws.rev_cnt; fa.rev_rows = ws.rev_rows; fa.e = ws.e;
-  fa.n = n; fa.force = force; fa.atom_energy = atom_energy; fa.partials = ws.partials; fa.energy = energy;
+  fa.n = n; fa.nlocal = nlocal; fa.force = force; fa.atom_energy = atom_energy; fa.partials = ws.partials; fa.energy = energy;
   fa.virial = virial; fa.err = m->d_err;
   launch_force_virial(fa, st);
   prof_mark(m, "force_virial", st);
@@ -721,22 +722,31 @@ int dp_set_precision(dp_model* m, int precision) {
   return alloc_workspace(m, m->ws.cap);
 }
 
-int dp_compute_device(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
-                      double* d_energy, double* d_force, double* d_virial, double* d_atom_energy, void* stream) {
+int dp_compute_device_local(dp_model* m, int natoms, int nlocal, const double* d_coord, const double* d_box,
+                            const int* d_atype, double* d_energy, double* d_force, double* d_virial,
+                            double* d_atom_energy, void* stream) {
   if (check_model(m)) return DP_ERR_ARG;
   if (natoms < 0) return fail(DP_ERR_ARG, "natoms < 0");
+  if (nlocal < 0 || nlocal > natoms) return fail(DP_ERR_ARG, "nlocal must be between 0 and natoms");
   if (!d_box || !d_energy || !d_virial || (natoms > 0 && (!d_coord || !d_atype || !d_force)))
     return fail(DP_ERR_ARG, "null device pointer");
   if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
   CUDA_TRY(cudaSetDevice(m->device));
-  return run_device(m, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, d_atom_energy,
+  return run_device(m, natoms, nlocal, d_coord, d_box, d_atype, d_energy, d_force, d_virial, d_atom_energy,
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
-int dp_compute(dp_model* m, int natoms, const double* coord, const double* box, const int* atype, double* energy,
-               double* force, double* virial, double* atom_energy) {
+int dp_compute_device(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
+                      double* d_energy, double* d_force, double* d_virial, double* d_atom_energy, void* stream) {
+  return dp_compute_device_local(m, natoms, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial,
+                                 d_atom_energy, stream);
+}
+
+int dp_compute_local(dp_model* m, int natoms, int nlocal, const double* coord, const double* box, const int* atype,
+                     double* energy, double* force, double* virial, double* atom_energy) {
   if (check_model(m)) return DP_ERR_ARG;
   if (natoms < 0) return fail(DP_ERR_ARG, "natoms < 0");
+  if (nlocal < 0 || nlocal > natoms) return fail(DP_ERR_ARG, "nlocal must be between 0 and natoms");
   if (!box || !energy || !virial || (natoms > 0 && (!coord || !atype || !force)))
     return fail(DP_ERR_ARG, "null host pointer");
   int rc = check_box_host(box, m->rcut);
@@ -754,7 +764,7 @@ int dp_compute(dp_model* m, int natoms, const double* coord, const double* box, 
     CUDA_TRY(cudaMemcpyAsync(ws.atype, atype, sizeof(int) * natoms, cudaMemcpyHostToDevice, st));
   }
   CUDA_TRY(cudaMemcpyAsync(ws.box, box, sizeof(double) * 9, cudaMemcpyHostToDevice, st));
-  rc = run_device(m, natoms, ws.coord, ws.box, ws.atype, ws.energy, ws.force, ws.virial, ws.atom_energy, st);
+  rc = run_device(m, natoms, nlocal, ws.coord, ws.box, ws.atype, ws.energy, ws.force, ws.virial, ws.atom_energy, st);
   if (rc != DP_OK) return rc;
   CUDA_TRY(cudaMemcpyAsync(energy, ws.energy, sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(virial, ws.virial, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
@@ -765,6 +775,11 @@ int dp_compute(dp_model* m, int natoms, const double* coord, const double* box, 
   }
   CUDA_TRY(cudaStreamSynchronize(st));
   return read_status(m);
+}
+
+int dp_compute(dp_model* m, int natoms, const double* coord, const double* box, const int* atype, double* energy,
+               double* force, double* virial, double* atom_energy) {
+  return dp_compute_local(m, natoms, natoms, coord, box, atype, energy, force, virial, atom_energy);
 }
 
 int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coord, const double* box,
@@ -1011,14 +1026,14 @@ int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double*
   double* coord_p = t_force + 3 * (size_t)m->t_cap;
   double* coord_m = coord_p + 3 * (size_t)m->t_cap;
   m->grad_scale = nullptr;
-  int rc = run_device(m, natoms, d_coord, d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
+  int rc = run_device(m, natoms, natoms, d_coord, d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
   if (rc != DP_OK) return rc;
   launch_train_prep(natoms, t_energy, e_ref, t_force, d_force_ref, d_coord, pe, pf, fd_h, coord_p, coord_m, d_loss,
                     m->d_scales, st);
   const double* xs[3] = {d_coord, coord_p, coord_m};
   for (int k = 0; k < 3 && rc == DP_OK; ++k) {
     m->grad_scale = m->d_scales + 1 + k;
-    rc = run_device(m, natoms, xs[k], d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
+    rc = run_device(m, natoms, natoms, xs[k], d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
   }
   m->grad_scale = nullptr;
   return rc;
@@ -1056,12 +1071,12 @@ int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const dou
   }
   CUDA_TRY(cudaMemsetAsync(m->d_md_counter, 0, sizeof(int), st));
   // forces at the starting coordinates
-  int rc = run_device(m, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
+  int rc = run_device(m, natoms, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
   if (rc != DP_OK) return rc;
   const bool prof = m->prof.on;
   auto one_step = [&]() -> int {
     launch_verlet_drift(natoms, dt, d_mass, d_force, d_vel, d_coord, st);
-    int r = run_device(m, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
+    int r = run_device(m, natoms, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
     launch_verlet_kick(natoms, dt, d_mass, d_force, d_vel, d_energy, m->d_md_counter, d_thermo, nsteps, st);
     return r;
   };

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
     f0 = warp_sum_d(f0); f1 = warp_sum_d(f1); f2 = warp_sum_d(f2);
     if (lane == 0) {
       a.force[3 * k] = f0; a.force[3 * k + 1] = f1; a.force[3 * k + 2] = f2;
-      ek = (double)a.e[k];
+      ek = k < a.nlocal ? (double)a.e[k] : 0.0;  // ghost atoms: m_k = 0 (Eq. eq_forcesLocalGhost)
       if (a.atom_energy) a.atom_energy[k] = ek;
     }
   }

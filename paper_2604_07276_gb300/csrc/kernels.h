@@ -70,6 +70,7 @@ struct ForceArgs {
   const int* rev_rows;
   const float* e;  // [n] atomic energies
   int n;
+  int nlocal;           // atoms [0, nlocal) are local: only their energies count
   double* force;        // [n][3]
   double* atom_energy;  // [n] or null
   double* partials;     // [blocks][10] (9 virial + energy)
@@ -144,7 +145,8 @@ void launch_energy_head(const float* H, int n, int width, const float* w_out, co
 // dZ = dH * (1 - t^2) with t = Hcur - Hprev (Hprev may be null: t = Hcur)
 void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, float* dZ, long long count,
                      cudaStream_t st);
-void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream_t st);
+// dst[i][:] = row for i < nlocal, 0 for nlocal <= i < n (ghost atoms seed no energy)
+void launch_fill_rows(float* dst, const float* row, int n, int nlocal, int width, cudaStream_t st);
 
 // --- training of the student (train.cu, simt.cu)
 bool launch_embed_wgrad(const EmbedArgs& a, const int* widths, float* grad, const float* scale, cudaStream_t st);

@@ -98,6 +98,7 @@ struct Profiler {
 }  // namespace dpa1
 
 struct dp_model {
+  int call_nlocal = 0;  // local atoms of the running evaluation (the rest are ghosts)
   using AttnLayerW = dpa1::AttnLayerW;
   using Workspace = dpa1::Workspace;
   using TcWeights = dpa1::TcWeights;

@@ -1033,16 +1033,17 @@ void launch_tanh_bwd(const float* dH, const float* Hcur, const float* Hprev, flo
   note_launch();
 }
 
-__global__ void k_fill_rows(float* __restrict__ dst, const float* __restrict__ row, long long count, int width) {
+__global__ void k_fill_rows(float* __restrict__ dst, const float* __restrict__ row, long long count, long long nlocal_el,
+                            int width) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  dst[i] = row[i % width];
+  dst[i] = i < nlocal_el ? row[i % width] : 0.f;
 }
 
-void launch_fill_rows(float* dst, const float* row, int n, int width, cudaStream_t st) {
+void launch_fill_rows(float* dst, const float* row, int n, int nlocal, int width, cudaStream_t st) {
   long long count = (long long)n * width;
   if (count == 0) return;
-  k_fill_rows<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dst, row, count, width);
+  k_fill_rows<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dst, row, count, (long long)nlocal * width, width);
   note_launch();
 }
 

@@ -14,6 +14,7 @@ from .systems import (
     frame_batch,
     maxwell_boltzmann,
     isolated_cluster,
+    slab_subdomains,
     MASSES,
     TYPE_MAP,
 )
@@ -29,6 +30,7 @@ __all__ = [
     "frame_batch",
     "maxwell_boltzmann",
     "isolated_cluster",
+    "slab_subdomains",
     "MASSES",
     "TYPE_MAP",
 ]

@@ -134,3 +134,38 @@ def isolated_cluster(seed: int, natoms: int = 12, radius: float = 3.0, box: floa
     coord = np.array(pts) + box / 2.0
     atype = rng.integers(0, ntypes, size=natoms).astype(np.int32)
     return coord, atype, np.array([box, box, box])
+
+
+def slab_subdomains(coord, atype, box, nslab: int, halo: float, pad: float = 10.0):
+    """Split a periodic orthorhombic box into ``nslab`` slabs along x, each
+    with the ghost atoms within ``halo`` of its faces, for local/ghost
+    evaluations.  Returns a list of (coord, atype, box, nlocal, owner):
+    the slab's local atoms come first, then the ghosts (periodic images in x
+    written out explicitly); ``owner`` maps every row to its atom of the
+    original box.  The slab boxes keep y and z periodic and stretch x so
+    that no x image comes within reach."""
+    coord = np.asarray(coord, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64).reshape(3)
+    L = box[0]
+    x = coord[:, 0] - L * np.floor(coord[:, 0] / L)
+    out = []
+    for s in range(nslab):
+        lo, hi = s * L / nslab, (s + 1) * L / nslab
+        local = np.nonzero((x >= lo) & (x < hi))[0]
+        ghosts, shifts = [], []
+        for t in (-1, 0, 1):
+            xs = x + t * L
+            sel = np.nonzero((xs >= lo - halo) & (xs < hi + halo))[0]
+            for j in sel:
+                if t == 0 and lo <= x[j] < hi:
+                    continue
+                ghosts.append(j)
+                shifts.append(t)
+        ghosts = np.asarray(ghosts, dtype=np.int64)
+        c = np.concatenate([coord[local], coord[ghosts]])
+        c[:, 0] = np.concatenate([x[local], x[ghosts] + L * np.asarray(shifts, dtype=np.float64)])
+        owner = np.concatenate([local, ghosts])
+        sub_box = np.array([L / nslab + 2 * halo + 2 * pad + L, box[1], box[2]])
+        c[:, 0] += halo + pad - lo  # inside the stretched box, away from its x faces
+        out.append((c, np.asarray(atype)[owner].astype(np.int32), sub_box, len(local), owner))
+    return out

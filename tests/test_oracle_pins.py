@@ -354,3 +354,27 @@ def test_synthetic_systems_recipes():
     d -= b * np.rint(d / b)
     r = np.sqrt((d ** 2).sum(-1)) + np.eye(192) * 10
     assert r.min() >= 0.9 - 1e-12  # inter-molecular >= 0.9 A, intra-molecular O-H 0.96 A
+
+
+def test_local_ghost_decomposition_reassembles_the_box():
+    """Eq. eq_forcesLocalGhost: a periodic box split into two x slabs, each
+    evaluated with its ghost atoms within rcut and only its local atoms'
+    energies counted, gives back the whole box: energies and virials add up,
+    and the forces on local and ghost rows summed per original atom are the
+    full forces."""
+    import synth
+    from oracle import OracleModel, energy_force_virial
+
+    cfg = synth.DEFAULT_CONFIG
+    om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=1))
+    coord, atype, box = synth.lattice_system(420, seed=23)
+    E, _, F, W = energy_force_virial(om, coord, box, atype)
+    Es, Fs, Ws = 0.0, np.zeros_like(F), np.zeros((3, 3))
+    for c, t, b, nloc, owner in synth.slab_subdomains(coord, atype, box, 2, cfg.rcut):
+        e, _, f, w = energy_force_virial(om, c, b, t, centres=np.arange(nloc))
+        Es += e
+        Ws += w
+        np.add.at(Fs, owner, f)
+    assert abs(Es - E) < 1e-10 * max(1.0, abs(E))
+    assert np.abs(Fs - F).max() < 1e-10
+    assert np.abs(Ws - W).max() < 1e-9
