@@ -40,7 +40,6 @@ struct TcWeights {
   void* emb_W1_t = nullptr;
   void* emb_W2_t = nullptr;
   struct Vectors {
-    float bqkv[3 * 128] = {};
     float bo[128] = {};
     float gamma[128] = {};
     float beta[128] = {};

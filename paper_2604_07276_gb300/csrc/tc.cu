@@ -46,7 +46,6 @@ struct LayerArgs {
   float2* smax;            // [rows] softmax row max and 1 / normaliser (fwd writes, bwd reads)
   float* dG;               // bwd: in dE/dG_{l+1}, out dE/dG_l (in place)
   float* dgeo;             // bwd: [rows][4] += (d rhat, d w)
-  float* scratch;          // bwd: per-CTA column partials
   const float* rw;         // [rows][4] (rhat, w)
   const int* nnei;
   int n, m1, yld;          // yld = m1 rounded up to a multiple of 8
@@ -55,7 +54,6 @@ struct LayerArgs {
   int* err;
   // per-feature vectors, passed by value (constant bank: every lane of a warp
   // reads the same feature at the same time)
-  float bqkv[3 * 128];
   float bo[128];
   float gamma[128];
   float beta[128];
@@ -94,6 +92,17 @@ __device__ __forceinline__ void handoff() {
   fence_after_sync();
 }
 
+// A warp's share of a handoff to the MMA issuer through an mbarrier that
+// expects one arrival per warp: its shared-memory writes made visible to the
+// tensor cores and its TMEM accesses ordered, then lane 0 arrives.  Unlike
+// handoff(), no thread waits.
+__device__ __forceinline__ void warp_arrive(uint64_t* bar) {
+  fence_async_smem();
+  fence_before_sync();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
 __device__ __forceinline__ void copy_image(uint8_t* dst, const uint4* src, int bytes) {
   uint4* d = reinterpret_cast<uint4*>(dst);
   for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = src[i];
@@ -129,6 +138,25 @@ __device__ __forceinline__ void load_cq32(const float* blk, int m1, int r, int c
     if (c < m1) x = b4[(c >> 2) * NP + r];  // m1 % 4 == 0
     v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
   }
+}
+
+// e^x as 2^(x log2 e) on the special-function unit, subnormal results
+// flushed to zero (the attention weights are normalised by sums >= 1, so
+// that loses nothing), exp(-inf) = 0.  Relative error a few units in the
+// last place of FP32 for the arguments of the softmax (|x| below ~100).
+__device__ __forceinline__ float exp_sfu(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 1.4426950408889634f));
+  return y;
+}
+
+// Columns m1 and m1 + 1 of a layer-input row carry the constant 1 that picks
+// up the Q, K, V biases stored in the weight tiles (the columns are zero
+// padding of the embedding width otherwise).
+__device__ __forceinline__ void set_bias_ones(float* v, int c0, int m1) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (c0 + i == m1 || c0 + i == m1 + 1) v[i] = 1.f;
 }
 
 // Issue D = sum over K-steps of A * B for one 128 x N block.
@@ -220,9 +248,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sB = sm + F_SLOT_B;
   uint8_t* sC = sm + F_SLOT_C;
   uint8_t* sD = sm + F_SLOT_D;
-  uint8_t* sWq = sm + F_W;
-  uint8_t* sWk = sWq + TILE;
-  uint8_t* sWv = sWk + TILE;
+  uint8_t* sWqk = sm + F_W;  // [Wq; Wk], 256 rows
+  uint8_t* sWv = sWqk + 2 * TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wo copy, Q, K, V, inputs
   uint64_t* bar_ld = bar + 1;
@@ -234,9 +261,12 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   const int quad = warp & 3, part = warp >> 2;
   const int row = quad * 32 + lane;
   const int c0 = part * 32;
-  const bool issuer = tid == 0;
+  // The MMA issuer stalls while the tensor pipe's queue is full: it lives in
+  // the warp with the least element-wise work (rows 96-127 are past the
+  // last neighbour of most atoms, columns 96-127 past the embedding width)
+  const bool issuer = tid == NT - 32;
 
-  copy_image(sWq, a.wimg, 3 * TILE);
+  copy_image(sWqk, a.wimg, 3 * TILE);
   if (issuer) {
     for (int i = 0; i < 6; ++i) mbar_init(bar + i, 1);
     fence_mbar_init();
@@ -246,11 +276,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   const uint32_t tm = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
-  const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
+  const uint32_t tWqk = smem_u32(sWqk), tWv = smem_u32(sWv);
   const uint4* wo_img = a.wimg + 3 * TILE / 16;
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
-  Sync sq{bar_q, 0u, a.err}, sk{bar_q + 1, 0u, a.err}, sv{bar_q + 2, 0u, a.err};
+  Sync sq{bar_q, 0u, a.err}, sv{bar_q + 2, 0u, a.err};
   Sync si{bar_in, 0u, a.err};
   const uint32_t g_bytes = (uint32_t)(NP * a.m1 * sizeof(float)), k_bytes = NP * sizeof(float4);
   // An atom's layer input (its column-quad interleaved block, as stored) and
@@ -274,32 +304,25 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     // kept in TMEM for the residual
     load_cq32(reinterpret_cast<const float*>(sC), a.m1, row, c0, v);
     tmem_st32(tm + lane_off + 384 + c0, v);
+    set_bias_ones(v, c0, a.m1);
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
     handoff();
-    // [Q K V] = G Wqkv (+ G_lo Wqkv), one commit group each, so that Q and
-    // K leave TMEM while the later products run
+    // [Q K] = G [Wq Wk] (N = 256) and V = G Wv (+ the G_lo products), one
+    // commit group each, so that Q and K leave TMEM while V's products run
     if (issuer) {
-      mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
-      if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
+      mma_block<F16>(tm + 0, tA, false, 128, tWqk, false, 256, 256, KS_M1, false);
+      if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWqk, false, 256, 256, KS_M1, true);
       mma_commit(bar_q);
-      mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
-      if (F16) mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
-      mma_commit(bar_q + 1);
       mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
       if (F16) mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
       mma_commit(bar_q + 2);
     }
-    // Q -> C, K -> D with biases (G in A, B is still being read)
+    // Q -> C, K -> D (G in A, B is still being read)
     sq.wait();
     tmem_ld32(tm + lane_off + 0 + c0, v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[c0 + i];
     store_row32<F16>(sC, row, c0, v);
-    sk.wait();
     tmem_ld32(tm + lane_off + 128 + c0, v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[128 + c0 + i];
     store_row32<F16>(sD, row, c0, v);
     handoff();
     // S = Q K^T -> TMEM [0,128) while V -> A (+ V_lo -> B)
@@ -309,8 +332,6 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     }
     sv.wait();
     tmem_ld32(tm + lane_off + 256 + c0, v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += a.bqkv[256 + c0 + i];
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
     handoff();
@@ -327,30 +348,42 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       const float4 kj = s_key[row];
       const float wj = kj.w;
       w_row = wj;
+      // a column quarter past the last neighbour has nothing to compute
+      const bool live = c0 < nn;
       float mx = -INFINITY;
+      if (live) {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int k = c0 + i;
-        const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_key[k].w) : -INFINITY;
-        v[i] = l;
-        mx = fmaxf(mx, l);
+        for (int i = 0; i < 32; ++i) {
+          const int k = c0 + i;
+          const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_key[k].w) : -INFINITY;
+          v[i] = l;
+          mx = fmaxf(mx, l);
+        }
       }
       mx = xr.max(mx);
+      const float mxs = mx == -INFINITY ? 0.f : mx;  // a row without neighbours: every term -inf
       float sum = 0.f;
+      if (live) {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float e = (v[i] == -INFINITY) ? 0.f : __expf(v[i] - mx);
-        v[i] = e;
-        sum += e;
+        for (int i = 0; i < 32; ++i) {
+          const float e = exp_sfu(v[i] - mxs);
+          v[i] = e;
+          sum += e;
+        }
       }
       sum = xr.sum(sum);
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
       if (part == 0) a.smax[base + row] = make_float2(mx, inv);
+      if (live) {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float4 kk = s_key[c0 + i];
-        const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
-        v[i] = v[i] * inv * kk.w * c;
+        for (int i = 0; i < 32; ++i) {
+          const float4 kk = s_key[c0 + i];
+          const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+          v[i] = v[i] * inv * kk.w * c;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
       }
       store_row32<F16>(sC, row, c0, v);
       if (F16) store_row32<F16, true>(sD, row, c0, v);
@@ -451,7 +484,6 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 constexpr int B_SLOT_A = 0, B_SLOT_B = TILE, B_SLOT_C = 2 * TILE, B_SLOT_D = 3 * TILE, B_W = 4 * TILE;
 constexpr int B_SMALL = 4 * TILE + 3 * TILE;
 constexpr int B_SMEM = B_SMALL + 2048 + 64;
-constexpr int SCRATCH_FLOATS = 4 * 128 * 4 + 4 * 128 * 4;  // per CTA: column parts per quadrant, row parts per quarter
 
 template <bool F16>
 __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ LayerArgs a) {
@@ -464,26 +496,32 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint8_t* sB = sm + B_SLOT_B;
   uint8_t* sC = sm + B_SLOT_C;
   uint8_t* sD = sm + B_SLOT_D;
-  uint8_t* sWq = sm + B_W;
-  uint8_t* sWk = sWq + TILE;
-  uint8_t* sWv = sWk + TILE;
+  uint8_t* sWqk = sm + B_W;  // [Wq; Wk], 256 rows
+  uint8_t* sWv = sWqk + 2 * TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + B_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
+  // [5]: general, Wo copy, Q K V, G ready, dY ready (the last two take one
+  // arrival per warp; each sees exactly one phase per atom)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
   uint64_t* bar_ld = bar + 1;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* bar_q = bar + 2;
+  uint64_t* bar_g = bar + 3;
+  uint64_t* bar_dy = bar + 4;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 5);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quad = warp & 3, part = warp >> 2;
   const int row = quad * 32 + lane;
   const int c0 = part * 32;
-  const bool issuer = tid == 0;
-  float* colp = a.scratch + (size_t)blockIdx.x * SCRATCH_FLOATS;  // [quad][128 keys][4]
-  float* rowp = colp + 4 * 128 * 4;                                // [part][128 rows][4]
+  // The MMA issuer stalls while the tensor pipe's queue is full: it lives in
+  // the warp with the least element-wise work (rows 96-127 are past the
+  // last neighbour of most atoms, columns 96-127 past the embedding width)
+  const bool issuer = tid == NT - 32;
 
-  copy_image(sWq, a.wimg, 3 * TILE);
+  copy_image(sWqk, a.wimg, 3 * TILE);
   if (issuer) {
-    mbar_init(bar, 1);
-    mbar_init(bar_ld, 1);
+    for (int i = 0; i < 3; ++i) mbar_init(bar + i, 1);
+    mbar_init(bar_g, NT / 32);
+    mbar_init(bar_dy, NT / 32);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -491,73 +529,111 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   const uint32_t tm = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
-  const uint32_t tWq = smem_u32(sWq), tWk = smem_u32(sWk), tWv = smem_u32(sWv);
+  const uint32_t tWqk = smem_u32(sWqk), tWv = smem_u32(sWv);
+  const uint32_t tWk = tWqk + 128 * 128;  // rows 128-255 of the [Wq; Wk] tile
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
+  Sync sq{bar_q, 0u, a.err};
+  Sync sg{bar_g, 0u, a.err}, sd{bar_dy, 0u, a.err};  // waited on by the issuer only
   const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + 3 * TILE;
-  if (issuer) prefetch_atom(a, blockIdx.x, true);
-
-  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
-    const int nn = a.nnei[atom];
-    const size_t base = (size_t)atom * NP;
-    const bool rv = row < nn;
-    if (issuer) {  // Wo -> slot D (bulk copy); the next atom's inputs -> L2
+  // An atom's Wo copy (slot D) and its layer-input rows (parked in TMEM
+  // columns [0, 128)) arrive during the previous atom's last phase; the
+  // first atom's here
+  int nn_next = (int)blockIdx.x < a.n ? a.nnei[blockIdx.x] : 0;
+  if ((int)blockIdx.x < a.n) {
+    if (issuer) {
       mbar_expect_tx(bar_ld, WO_TILE);
       bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
-      prefetch_atom(a, atom + gridDim.x, true);
+      prefetch_atom(a, blockIdx.x, true);
     }
-    const float rs = rv ? a.rstd[base + row] : 0.f;
-    const float2 sst = rv ? a.smax[base + row] : make_float2(0.f, 0.f);
-    if (tid < 128) {
-      const float4 r = reinterpret_cast<const float4*>(a.rw)[base + tid];
-      s_key[tid] = tid < nn ? r : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    float gn[32];
+    load_cq32(a.Gin + (size_t)blockIdx.x * NP * a.m1, a.m1, row, c0, gn);
+    tmem_st32(tm + lane_off + 0 + c0, gn);
+  }
+
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = nn_next;
+    const size_t base = (size_t)atom * NP;
+    const bool rv = row < nn;
+    const int next = atom + (int)gridDim.x;
+    if (issuer) prefetch_atom(a, next, true);  // the next atom's inputs -> L2
+    // Every per-row input of the atom in one round trip (the NP-row blocks
+    // exist past nnei; what is read there is masked, never used)
     float v[32];
-    // P0: G_l -> A (+ G_lo -> B), dY = LayerNorm adjoint of dZ -> C
-    load_cq32(a.Gin + base * a.m1, a.m1, row, c0, v);
-    store_row32<F16>(sA, row, c0, v);
-    if (F16) store_row32<F16, true>(sB, row, c0, v);
+    tmem_ld32(tm + lane_off + 0 + c0, v);
+    const float rs_in = a.rstd[base + row];
+    const float2 sst_in = a.smax[base + row];
+    float4 kr = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < 128) kr = reinterpret_cast<const float4*>(a.rw)[base + tid];
+    if (next < a.n) nn_next = a.nnei[next];
+    float4 dz[8];
+    uint4 yy[4];
     {
-      const RowXchg xr(sC, row, part, lane, quad);  // dY is stored after the exchange
       const float4* dz4 = reinterpret_cast<const float4*>(a.dG + base * a.m1);
       const uint4* yh8 = reinterpret_cast<const uint4*>(a.yhat + base * a.yld);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + 4 * q;
+        dz[q] = c < a.m1 ? dz4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 8 * q;
+        yy[q] = c < a.m1 ? yh8[(c >> 3) * NP + row] : make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    const float rs = rv ? rs_in : 0.f;
+    const float2 sst = rv ? sst_in : make_float2(0.f, 0.f);
+    if (tid < 128) s_key[tid] = tid < nn ? kr : make_float4(0.f, 0.f, 0.f, 0.f);
+    // P0a: G_l -> A (+ G_lo -> B), the bias columns set to 1
+    set_bias_ones(v, c0, a.m1);
+    store_row32<F16>(sA, row, c0, v);
+    if (F16) store_row32<F16, true>(sB, row, c0, v);
+    // The two handoffs to the issuer in P0 are arrivals on mbarriers, not CTA
+    // barriers: no warp waits while the issuer is held up issuing M0a
+    warp_arrive(bar_g);
+    // M0a: [Q K] = G [Wq Wk] (N = 256), V = G Wv (+ the G_lo products) -> [0, 384)
+    if (issuer) {
+      if (sg.wait()) {
+        mma_block<F16>(tm + 0, tA, false, 128, tWqk, false, 256, 256, KS_M1, false);
+        mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
+        if (F16) {
+          mma_block<F16>(tm + 0, tB, false, 128, tWqk, false, 256, 256, KS_M1, true);
+          mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
+        }
+      }
+      mma_commit(bar_q);
+    }
+    // P0b, while M0a runs: dY = LayerNorm adjoint of dZ -> C
+    {
+      const RowXchg xr(sC, row, part, lane, quad);  // dY is stored after the exchange
       float yv[32];
       float s1 = 0.f, s2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < 32; i += 8) {
-        const int c = c0 + i;
-        float g[8], y[8];
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t yw[4] = {yy[q].x, yy[q].y, yy[q].z, yy[q].w};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) g[k] = y[k] = 0.f;
+        for (int k = 0; k < 4; ++k) {
+          const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162*>(&yw[k]);
+          yv[8 * q + 2 * k] = __low2float(p2);
+          yv[8 * q + 2 * k + 1] = __high2float(p2);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + 4 * q;
+        const float4 g4 = dz[q];
+        float* g = v + 4 * q;
         if (c < a.m1 && rv) {
-          const uint4 yy = yh8[(c >> 3) * NP + row];
-          const uint32_t yw[4] = {yy.x, yy.y, yy.z, yy.w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const __nv_bfloat162 p2 = *reinterpret_cast<const __nv_bfloat162*>(&yw[k]);
-            y[2 * k] = __low2float(p2);
-            y[2 * k + 1] = __high2float(p2);
-          }
-#pragma unroll
-          for (int h = 0; h < 8; h += 4) {
-            const int cc = c + h;
-            if (cc < a.m1) {
-              const float4 g4 = dz4[(cc >> 2) * NP + row];
-              g[h] = g4.x * a.gamma[cc];
-              g[h + 1] = g4.y * a.gamma[cc + 1];
-              g[h + 2] = g4.z * a.gamma[cc + 2];
-              g[h + 3] = g4.w * a.gamma[cc + 3];
-            }
-          }
+          g[0] = g4.x * a.gamma[c];
+          g[1] = g4.y * a.gamma[c + 1];
+          g[2] = g4.z * a.gamma[c + 2];
+          g[3] = g4.w * a.gamma[c + 3];
+        } else {
+          g[0] = g[1] = g[2] = g[3] = 0.f;
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          v[i + k] = g[k];
-          yv[i + k] = y[k];
-        }
-        s1 += ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
-        s2 += ((g[0] * y[0] + g[1] * y[1]) + (g[2] * y[2] + g[3] * y[3])) +
-              ((g[4] * y[4] + g[5] * y[5]) + (g[6] * y[6] + g[7] * y[7]));
+        s1 += (g[0] + g[1]) + (g[2] + g[3]);
+        s2 += (g[0] * yv[4 * q] + g[1] * yv[4 * q + 1]) + (g[2] * yv[4 * q + 2] + g[3] * yv[4 * q + 3]);
       }
       const float2 ss = xr.sum2(make_float2(s1, s2));
       s1 = ss.x / (float)a.m1;
@@ -566,31 +642,24 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       for (int i = 0; i < 32; ++i) v[i] = rv ? rs * (v[i] - s1 - yv[i] * s2) : 0.f;
       store_row32<F16>(sC, row, c0, v);
     }
-    handoff();
-    // M0: [Q K V] = G Wqkv (+ G_lo Wqkv) ; dO = dY Wo^T (Wo tile as MN-major)
-    if (issuer && sl.wait()) {
-      mma_block<F16>(tm + 0, tA, false, 128, tWq, false, 128, 128, KS_M1, false);
-      mma_block<F16>(tm + 128, tA, false, 128, tWk, false, 128, 128, KS_M1, false);
-      mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
-      if (F16) {
-        mma_block<F16>(tm + 0, tB, false, 128, tWq, false, 128, 128, KS_M1, true);
-        mma_block<F16>(tm + 128, tB, false, 128, tWk, false, 128, 128, KS_M1, true);
-        mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
-      }
-      mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+    warp_arrive(bar_dy);
+    // M0b: dO = dY Wo^T -> [384, 512) (Wo tile as MN-major)
+    if (issuer) {
+      if (sd.wait() && sl.wait()) mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+      mma_commit(bar);
     }
-    commit_and_sync(sy, issuer);
-    // P1: Q -> A, K -> B, V -> C, dO -> D
-#pragma unroll 1
-    for (int which = 0; which < 4; ++which) {
-      tmem_ld32(tm + lane_off + which * 128 + c0, v);
-      if (which < 3) {
-        const float* b = a.bqkv + which * 128 + c0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += b[i];
-      }
-      store_row32<F16>(which == 0 ? sA : which == 1 ? sB : which == 2 ? sC : sD, row, c0, v);
-    }
+    // P1: Q -> A, K -> B once M0a is done (G is dead); V -> C, dO -> D once
+    // M0b is done (dY and Wo are dead)
+    sq.wait();
+    tmem_ld32(tm + lane_off + 0 + c0, v);
+    store_row32<F16>(sA, row, c0, v);
+    tmem_ld32(tm + lane_off + 128 + c0, v);
+    store_row32<F16>(sB, row, c0, v);
+    sy.wait();
+    tmem_ld32(tm + lane_off + 256 + c0, v);
+    store_row32<F16>(sC, row, c0, v);
+    tmem_ld32(tm + lane_off + 384 + c0, v);
+    store_row32<F16>(sD, row, c0, v);
     handoff();
     // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
     if (issuer) {
@@ -601,7 +670,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     // P2: softmax adjoint over this thread's 32 keys, with the row max and
     // normaliser the forward pass stored: A and sum_k A_jk dA_jk first, then
     // the main pass in 8-key pieces that reload S, dP, A and the gate cosine
-    // from TMEM; P -> slot C, dS -> TMEM over the consumed S columns
+    // from TMEM; P -> slot C, dS -> TMEM over the consumed S columns.  Key
+    // halves past the last neighbour only write their zeros.  The row parts
+    // (this thread's row) and column parts (lanes 0-15: key c0 + h + lane)
+    // of dE/drhat and dE/dw stay in registers until slot C is free.
+    float4 rpart, cpart[2];
     {
       const RowXchg xr(sC, row, part, lane, quad);  // V is dead after dP
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
@@ -612,10 +685,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       // V accumulator columns for the main pass
       const uint32_t tAw = tm + lane_off + 128 + c0, tCs = tm + lane_off + 256 + c0;
       float wsum = 0.f;
-      {
+      if (c0 < nn) {
         float t[32], u[32];
-        tmem_ld32(tS, t);
-        tmem_ld32(tP, u);
+        tmem_ld32x2(tS, tP, t, u);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int k = c0 + i;
@@ -624,7 +696,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
           float A = 0.f;
           if (k < nn && rv) {
             const float ww = wj * kk.w;
-            A = __expf((t[i] * a.scale + a.shift) * ww - mx) * inv;
+            A = exp_sfu((t[i] * a.scale + a.shift) * ww - mx) * inv;
             wsum += A * u[i] * ww * c;
           }
           t[i] = A;
@@ -635,62 +707,67 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       }
       const float tsum = xr.sum(wsum);  // sum_k A_jk dA_jk; ends with the quadrant's barrier
       float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-      float4* cp = reinterpret_cast<float4*>(colp) + quad * 128 + c0;
 #pragma unroll 1
       for (int h = 0; h < 32; h += 16) {
-        float cw[16], dcv[16];
+        float4 cph = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + h < nn) {
+          float cw[16], dcv[16];
 #pragma unroll
-        for (int e8 = 0; e8 < 16; e8 += 8) {
-          float t[8], u[8], Av[8], cv[8], pv[8];
-          tmem_ld8(tS + h + e8, t);
-          tmem_ld8(tP + h + e8, u);
-          tmem_ld8(tAw + h + e8, Av);
-          tmem_ld8(tCs + h + e8, cv);
+          for (int e8 = 0; e8 < 16; e8 += 8) {
+            float t[8], u[8], Av[8], cv[8], pv[8];
+            tmem_ld8x4(tS + h + e8, tP + h + e8, tAw + h + e8, tCs + h + e8, t, u, Av, cv);
+            // No masks: A is 0 past the last neighbour and on rows past it
+            // (first pass), and S, dP and c are finite there, so every term
+            // below vanishes on its own
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = c0 + h + e8 + i;
-            float H = 0.f, dc = 0.f, P = 0.f, dS = 0.f;
-            const float4 kk = s_key[k];
-            if (k < nn && rv) {
-              const float l = t[i] * a.scale;
+            for (int i = 0; i < 8; ++i) {
+              const float4 kk = s_key[c0 + h + e8 + i];
+              const float A = Av[i], c = cv[i];
               const float ww = wj * kk.w;
-              const float A = Av[i], c = cv[i], dP = u[i];
-              const float dLp = A * (dP * ww * c - tsum);
-              H = dP * A * c + dLp * (l + a.shift);
-              dc = dP * A * ww;
-              P = A * ww * c;
-              dS = dLp * ww * a.scale;
+              const float e = A * u[i];                           // A dP
+              const float dc = e * ww;                            // dE/dc_jk
+              const float dLp = fmaf(dc, c, -A * tsum);           // A (dA - sum_k A dA), dA = dP ww c
+              const float H = fmaf(dLp, fmaf(t[i], a.scale, a.shift), e * c);  // dE/d(w_j w_k)
+              const float P = A * ww * c;
+              const float dS = dLp * ww * a.scale;
+              rw_ += H * kk.w;
+              rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
+              cw[e8 + i] = H * wj;
+              dcv[e8 + i] = dc;
+              pv[i] = P;
+              t[i] = dS;
             }
-            rw_ += H * kk.w;
-            rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
-            cw[e8 + i] = H * wj;
-            dcv[e8 + i] = dc;
-            pv[i] = P;
-            t[i] = dS;
+            uint4 w4;
+            w4.x = pack16<F16>(pv[0], pv[1]);
+            w4.y = pack16<F16>(pv[2], pv[3]);
+            w4.z = pack16<F16>(pv[4], pv[5]);
+            w4.w = pack16<F16>(pv[6], pv[7]);
+            sw128_store8(sC, row, c0 + h + e8, 128, w4);
+            tmem_st8_async(tS + h + e8, t);  // dS over these consumed S columns
           }
-          uint4 w4;
-          w4.x = pack16<F16>(pv[0], pv[1]);
-          w4.y = pack16<F16>(pv[2], pv[3]);
-          w4.z = pack16<F16>(pv[4], pv[5]);
-          w4.w = pack16<F16>(pv[6], pv[7]);
-          sw128_store8(sC, row, c0 + h + e8, 128, w4);
-          tmem_st8(tS + h + e8, t);  // dS over these consumed S columns
+          cph.w = warp_reduce_scatter16(cw);
+          float tmp[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
+          cph.x = warp_reduce_scatter16(tmp);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
+          cph.y = warp_reduce_scatter16(tmp);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
+          cph.z = warp_reduce_scatter16(tmp);
+        } else {
+          const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int e8 = 0; e8 < 16; e8 += 8) {
+            sw128_store8(sC, row, c0 + h + e8, 128, make_uint4(0u, 0u, 0u, 0u));
+            tmem_st8_async(tS + h + e8, z);
+          }
         }
-        const float sw_ = warp_reduce_scatter16(cw);
-        float tmp[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
-        const float sx = warp_reduce_scatter16(tmp);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
-        const float sy_ = warp_reduce_scatter16(tmp);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
-        const float sz = warp_reduce_scatter16(tmp);
-        if (lane < 16) cp[h + lane] = make_float4(sx, sy_, sz, sw_);
+        cpart[h >> 4] = cph;
       }
-      // row parts of dE/dw_j and dE/drhat_j, per column quarter
-      reinterpret_cast<float4*>(rowp)[part * 128 + row] = make_float4(rx, ry, rz, rw_);
+      rpart = make_float4(rx, ry, rz, rw_);
+      tmem_wait_st();
     }
     handoff();
     // M2: dV = P^T dO -> [128,256)
@@ -705,57 +782,75 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       mma_block<F16>(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
-    // P4: dQ -> B, dK -> A, dV -> D ; dgeo of this atom
+    // P4: dQ -> B, dK -> A, dV -> D; the row and column parts -> slot C
+    // (dS is dead): [quadrant][128 keys] column parts, then [quarter][128
+    // rows] row parts, float4 (x, y, z, w) each
     tmem_ld32(tm + lane_off + 0 + c0, v);
     store_row32<F16>(sB, row, c0, v);
     tmem_ld32(tm + lane_off + 256 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     tmem_ld32(tm + lane_off + 128 + c0, v);
     store_row32<F16>(sD, row, c0, v);
-    if (tid < 128) {
-      // key/row `tid`: row parts of the 4 quarters + column parts of the 4 quadrants
-      const float4* rp = reinterpret_cast<const float4*>(rowp);
-      const float4* cp = reinterpret_cast<const float4*>(colp);
-      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int q = 0; q < 4; ++q) {
-        const float4 r = rp[q * 128 + tid];
-        s.x += r.x; s.y += r.y; s.z += r.z; s.w += r.w;
-      }
-      for (int q = 0; q < 4; ++q) {
-        const float4 c = cp[q * 128 + tid];
-        s.x += c.x; s.y += c.y; s.z += c.z; s.w += c.w;
-      }
-      if (tid < nn) {
-        float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
-        float4 cur = *dg;
-        cur.x += s.x; cur.y += s.y; cur.z += s.z; cur.w += s.w;
-        *dg = cur;
-      }
+    float4* parts = reinterpret_cast<float4*>(sC);
+    if (lane < 16) {
+      parts[quad * 128 + c0 + lane] = cpart[0];
+      parts[quad * 128 + c0 + 16 + lane] = cpart[1];
     }
+    parts[512 + part * 128 + row] = rpart;
     handoff();
     // M4: dG = dQ Wq^T + dK Wk^T + dV Wv^T -> [384, 496)
     if (issuer) {
-      mma_block<F16>(tm + 384, tB, false, 128, tWq, true, 128, WO_ROWS, 8, false);
-      mma_block<F16>(tm + 384, tA, false, 128, tWk, true, 128, WO_ROWS, 8, true);
+      mma_block<F16>(tm + 384, tB, false, 128, tWqk, true, 256, WO_ROWS, 8, false);
+      mma_block<F16>(tm + 384, tA, false, 128, tWk, true, 256, WO_ROWS, 8, true);
       mma_block<F16>(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
+      mma_commit(bar);
     }
-    commit_and_sync(sy, issuer);
-    // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place
-    {
-      tmem_ld32(tm + lane_off + 384 + c0, v);
-      float4* dg4 = reinterpret_cast<float4*>(a.dG + base * a.m1);
-      float4 g[8];
+    // while M4 runs: dZ for the residual, and dgeo of this atom (key `tid`:
+    // the four quarters' row parts + the four quadrants' column parts)
+    float4* dg4 = reinterpret_cast<float4*>(a.dG + base * a.m1);
+    float4 g[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {  // all loads before the stores
-        const int c = c0 + 4 * q;
-        g[q] = c < a.m1 ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < 8; ++q) {
+      const int c = c0 + 4 * q;
+      g[q] = c < a.m1 ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // the next atom's layer-input row, parked in TMEM [0, 128) (dQ is dead
+    // since P4)
+    if (next < a.n) {
+      float gn[32];
+      load_cq32(a.Gin + (size_t)next * NP * a.m1, a.m1, row, c0, gn);
+      tmem_st32(tm + lane_off + 0 + c0, gn);
+    }
+    if (tid < nn) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 r = parts[512 + q * 128 + tid];
+        const float4 c = parts[q * 128 + tid];
+        s.x += r.x + c.x; s.y += r.y + c.y; s.z += r.z + c.z; s.w += r.w + c.w;
       }
+      float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
+      float4 cur = *dg;
+      cur.x += s.x; cur.y += s.y; cur.z += s.z; cur.w += s.w;
+      *dg = cur;
+    }
+    sy.wait();
+    // Slot D is free: the next atom's Wo copy
+    if (issuer && next < a.n) {
+      mbar_expect_tx(bar_ld, WO_TILE);
+      bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
+    }
+    // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place, 16 columns at a time
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = c0 + 4 * q, i = 4 * q;
+    for (int h = 0; h < 32; h += 16) {
+      tmem_ld16(tm + lane_off + 384 + c0 + h, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + h + 4 * q, i = 4 * q;
+        float4& gq = g[(h >> 2) + q];
         if (c < a.m1) {
-          g[q].x += v[i]; g[q].y += v[i + 1]; g[q].z += v[i + 2]; g[q].w += v[i + 3];
-          dg4[(c >> 2) * NP + row] = g[q];
+          gq.x += v[i]; gq.y += v[i + 1]; gq.z += v[i + 2]; gq.w += v[i + 3];
+          dg4[(c >> 2) * NP + row] = gq;
         }
       }
     }
@@ -1210,12 +1305,17 @@ int sm_count_dev(int dev) {
 }
 
 // Build the swizzled shared-memory image of one layer's weights:
-// Wq, Wk, Wv as [128 out][128 in] K-major tiles (in = M1 padded with zeros)
-// and Wo as a [112 out][128 in] K-major tile.
-std::vector<uint8_t> layer_image(const std::vector<double>& Wq, const std::vector<double>& Wk,
-                                 const std::vector<double>& Wv, const std::vector<double>& Wo, int m1, int A,
-                                 bool f16) {
+// [Wq; Wk] as a [256 out][128 in] K-major tile, Wv as a [128 out][128 in]
+// one (in = M1 padded with zeros) and Wo as a [112 out][128 in] one.  Inputs M1 and M1 + 1 of Wq,
+// Wk, Wv hold the 16-bit high and low parts of the biases bq, bk, bv: the
+// kernels set the layer input's columns M1 and M1 + 1 to 1, so the products
+// carry the biases (to about 22 bits in FP16, 16 in BF16).
+std::vector<uint8_t> layer_image(const std::vector<double>* Ws[3], const std::vector<double>* bs[3],
+                                 const std::vector<double>& Wo, int m1, int A, bool f16) {
   std::vector<uint8_t> img(WIMG, 0);
+  auto r16 = [&](double x) -> double {
+    return f16 ? (double)__half2float(__float2half((float)x)) : (double)__bfloat162float(__float2bfloat16((float)x));
+  };
   auto put = [&](uint8_t* tile, int r, int c, int R, double x) {
     if (f16) {
       __half h = __float2half((float)x);
@@ -1225,10 +1325,18 @@ std::vector<uint8_t> layer_image(const std::vector<double>& Wq, const std::vecto
       memcpy(tile + sw128_offset(r, c, R), &h, 2);
     }
   };
-  const std::vector<double>* Ws[3] = {&Wq, &Wk, &Wv};
-  for (int t = 0; t < 3; ++t)
-    for (int f = 0; f < A; ++f)
-      for (int m = 0; m < m1; ++m) put(img.data() + t * TILE, f, m, 128, (*Ws[t])[(size_t)m * A + f]);
+  for (int t = 0; t < 3; ++t) {
+    // Wq and Wk form one 256-row tile (outputs 0-127: Q, 128-255: K), so that
+    // [Q K] is one N = 256 product; Wv is a 128-row tile after it
+    uint8_t* tile = img.data() + (t < 2 ? 0 : 2 * TILE);
+    const int R = t < 2 ? 256 : 128, r0 = t == 1 ? 128 : 0;
+    for (int f = 0; f < A; ++f) {
+      for (int m = 0; m < m1; ++m) put(tile, r0 + f, m, R, (*Ws[t])[(size_t)m * A + f]);
+      const double b = (*bs[t])[f], hi = r16(b);
+      put(tile, r0 + f, m1, R, hi);
+      put(tile, r0 + f, m1 + 1, R, b - hi);
+    }
+  }
   for (int m = 0; m < m1; ++m)
     for (int f = 0; f < A; ++f) put(img.data() + 3 * TILE, m, f, WO_ROWS, Wo[(size_t)f * m1 + m]);
   return img;
@@ -1237,8 +1345,8 @@ std::vector<uint8_t> layer_image(const std::vector<double>& Wq, const std::vecto
 }  // namespace
 
 int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
-  if (m->A != 128 || m->m1 > WO_ROWS || m->m1 % 4 != 0 || m->m1 > 128) {
-    msg = "the tensor-core path needs attention width 128 and an embedding width <= 112 divisible by 4";
+  if (m->A != 128 || m->m1 + 2 > 16 * KS_M1 || m->m1 % 4 != 0) {
+    msg = "the tensor-core path needs attention width 128 and an embedding width <= 108 divisible by 4";
     return DP_ERR_UNSUPPORTED;
   }
   auto get = [&](const std::string& name) -> const std::vector<double>& {
@@ -1251,8 +1359,9 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
   for (int f16 = 0; f16 < 2; ++f16)
     for (int l = 0; l < m->nattn; ++l) {
       const std::string p = "at" + std::to_string(l) + "_";
-      std::vector<uint8_t> img =
-          layer_image(get(p + "Wq"), get(p + "Wk"), get(p + "Wv"), get(p + "Wo"), m->m1, m->A, f16 != 0);
+      const std::vector<double>* Ws[3] = {&get(p + "Wq"), &get(p + "Wk"), &get(p + "Wv")};
+      const std::vector<double>* bs[3] = {&get(p + "bq"), &get(p + "bk"), &get(p + "bv")};
+      std::vector<uint8_t> img = layer_image(Ws, bs, get(p + "Wo"), m->m1, m->A, f16 != 0);
       void* d = nullptr;
       if (cudaMalloc(&d, img.size()) != cudaSuccess ||
           cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1305,9 +1414,6 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
   for (int l = 0; l < m->nattn; ++l) {
     const std::string p = "at" + std::to_string(l) + "_";
     TcWeights::Vectors& v = w.vectors[l];
-    const char* names[3] = {"bq", "bk", "bv"};
-    for (int t = 0; t < 3; ++t)
-      for (int f = 0; f < m->A; ++f) v.bqkv[t * 128 + f] = (float)get(p + names[t])[f];
     for (int c = 0; c < m->m1; ++c) {
       v.bo[c] = (float)get(p + "bo")[c];
       v.gamma[c] = (float)get(p + "ln_g")[c];
@@ -1336,7 +1442,7 @@ void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
   ws.tc.p[0] = a.take<__nv_bfloat16>(rows * yhat_ld(m->m1) * (size_t)std::max(1, m->nattn));  // yhat per layer
   ws.tc.p[1] = a.take<float>(rows * (size_t)std::max(1, m->nattn));                // rstd per layer
   ws.tc.p[4] = a.take<float2>(rows * (size_t)std::max(1, m->nattn));               // softmax stats per layer
-  ws.tc.p[2] = a.take<float>((size_t)sm_count_dev(m->device) * SCRATCH_FLOATS);      // column partials
+  ws.tc.p[2] = nullptr;
   // row-major staging of G0 / dE/dG0 for the SIMT embedding net (nets other than 25-50-100)
   ws.tc.p[3] = m->tcw.emb_W1_t ? nullptr : a.take<float>(rows * m->m1);
 }
@@ -1357,7 +1463,6 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.smax = reinterpret_cast<float2*>(ws.tc.p[4]) + (size_t)l * rows;
     la.dG = ws.dG;
     la.dgeo = ws.dgeo;
-    la.scratch = reinterpret_cast<float*>(ws.tc.p[2]);
     la.rw = ws.rw;
     la.nnei = ws.nnei;
     la.n = n;
@@ -1365,7 +1470,6 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.yld = yhat_ld(m->m1);
     la.wimg = reinterpret_cast<const uint4*>(f16 ? m->tcw.Wo_t[l] : m->tcw.Wqkv_t[l]);
     const TcWeights::Vectors& vec = m->tcw.vectors[l];
-    memcpy(la.bqkv, vec.bqkv, sizeof(la.bqkv));
     memcpy(la.bo, vec.bo, sizeof(la.bo));
     memcpy(la.gamma, vec.gamma, sizeof(la.gamma));
     memcpy(la.beta, vec.beta, sizeof(la.beta));
