@@ -604,8 +604,15 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       }
       mma_commit(bar_q);
     }
-    // P0b, while M0a runs: dY = LayerNorm adjoint of dZ -> C
-    {
+    // P0b, while M0a runs: dY = LayerNorm adjoint of dZ -> C.  A lane
+    // quadrant whose rows are all past the last neighbour (the same for its
+    // four warps) stores zeros and skips the exchange: the issuer's quadrant
+    // then does not hold M0b back while the issuer waits to queue M0a.
+    if (quad * 32 >= nn) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      store_row32<F16>(sC, row, c0, v);
+    } else {
       const RowXchg xr(sC, row, part, lane, quad);  // dY is stored after the exchange
       float yv[32];
       float s1 = 0.f, s2 = 0.f;
