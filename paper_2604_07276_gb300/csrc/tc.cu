@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sWqk = sm + F_W;  // [Wq; Wk], 256 rows
   uint8_t* sWv = sWqk + 2 * TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wo copy, Q, K, V, inputs
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wo copy, Q K, Q K out, V, inputs
   uint64_t* bar_ld = bar + 1;
   uint64_t* bar_q = bar + 2;
   uint64_t* bar_in = bar + 5;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 
   copy_image(sWqk, a.wimg, 3 * TILE);
   if (issuer) {
-    for (int i = 0; i < 6; ++i) mbar_init(bar + i, 1);
+    for (int i = 0; i < 6; ++i) mbar_init(bar + i, i == 3 ? NT / 32 : 1);  // [3]: one arrival per warp
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(s_tmem, 512);
@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
   Sync sq{bar_q, 0u, a.err}, sv{bar_q + 2, 0u, a.err};
+  Sync so{bar_q + 1, 0u, a.err};  // Q and K are out of TMEM: waited on by the issuer only
   Sync si{bar_in, 0u, a.err};
   const uint32_t g_bytes = (uint32_t)(NP * a.m1 * sizeof(float)), k_bytes = NP * sizeof(float4);
   // An atom's layer input (its column-quad interleaved block, as stored) and
@@ -324,17 +325,19 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     store_row32<F16>(sC, row, c0, v);
     tmem_ld32(tm + lane_off + 128 + c0, v);
     store_row32<F16>(sD, row, c0, v);
-    handoff();
-    // S = Q K^T -> TMEM [0,128) while V -> A (+ V_lo -> B)
+    // an arrival, not a CTA barrier: no warp waits while the issuer is still
+    // queueing V's products
+    warp_arrive(bar_q + 1);
+    // S = Q K^T -> TMEM [0,128) while V -> A (+ V_lo -> B); the tiles of V
+    // reach the tensor cores through the handoff after the softmax
     if (issuer) {
-      mma_block<F16>(tm + 0, tC, false, 128, tD, false, 128, 128, 8, false);
+      if (so.wait()) mma_block<F16>(tm + 0, tC, false, 128, tD, false, 128, 128, 8, false);
       mma_commit(bar);
     }
     sv.wait();
     tmem_ld32(tm + lane_off + 256 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
-    handoff();
     sy.wait();
     // smooth softmax and gate: P -> slot C (+ P_lo -> slot D); Q and K are dead.
     // Row j of P carries the factor w_j, which vanishes for neighbours near
