@@ -944,9 +944,10 @@ struct EmbOwn {
 // Layers 1 and 2 of a row and the issue of Z3 = H2 W2; returns once Z3 is in
 // TMEM columns [64, 176).  h1 gets all 25 layer-1 units, h2 the owned
 // layer-2 units.
-template <int H>
+template <int H, class BeforeZ3>
 __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
-                                               Sync& sy, int row, bool rv, size_t rowg, float* h1, float* h2) {
+                                               Sync& sy, int row, bool rv, float x, float* h1, float* h2,
+                                               BeforeZ3 before_z3) {
   using O = EmbOwn<H>;
   uint8_t* sW1h = sm;
   uint8_t* sW1l = sW1h + EMB_T1;
@@ -957,7 +958,6 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sH2h = sH1l + EMB_TA;
   uint8_t* sH2l = sH2h + EMB_TA;
   const bool issuer = threadIdx.x == 0;
-  const float x = rv ? a.R[rowg * 4] : 0.f;
 #pragma unroll
   for (int p = 0; p < EMB_E0; ++p) h1[p] = rv ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
   // H1 (K = 25, read as 32): half 0 stores the hi parts, half 1 the lo parts
@@ -997,10 +997,34 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
     }
   }
   handoff();
-  if (issuer)
+  if (issuer) {
     mma_split(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
-  commit_and_sync(sy, issuer);
+    mma_commit(sy.bar);
+  }
+  before_z3();  // work that does not need Z3 (the adjoint's first dE/dG0 loads)
+  sy.wait();
 }
+
+// A row's inputs of the embedding net (s of the neighbour, its type), read
+// for the next atom while the current one is processed: the neighbour
+// count, s and the neighbour index at its start, the type at its end.
+struct EmbRowIn {
+  int nn = 0, nl = 0, tj = 0;
+  float x = 0.f;
+  __device__ void count(const EmbedTcArgs& a, int atom) { nn = atom < a.n ? a.nnei[atom] : 0; }
+  __device__ void rows(const EmbedTcArgs& a, int atom, int row) {
+    if (atom < a.n) {  // the NP-row blocks exist past nnei: read unmasked, used masked
+      const size_t rg = (size_t)atom * NP + row;
+      x = a.R[rg * 4];
+      nl = a.nlist[rg];
+    }
+  }
+  __device__ void type(const EmbedTcArgs& a, int row) {
+    const bool rv = row < nn;
+    x = rv ? x : 0.f;
+    tj = rv ? a.atype[nl] : 0;
+  }
+};
 
 __device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm, uint64_t*& bar, uint32_t*& s_tmem,
                                                int smem_bytes) {
@@ -1077,21 +1101,27 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_co
   float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
   Sync sy{bar, 0u, a.err};
   float h1[EMB_E0], h2[EMB_E1 - EMB_SPLIT];
+  EmbRowIn in;
+  in.count(a, blockIdx.x);
+  in.rows(a, blockIdx.x, row);
+  in.type(a, row);
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
-    const int nn = a.nnei[atom];
+    const EmbRowIn cur = in;
+    const int nn = cur.nn, tj = cur.tj, next = atom + gridDim.x;
     const bool rv = row < nn;
-    const size_t rowg = (size_t)atom * NP + row;
-    const int tj = rv ? a.atype[a.nlist[rowg]] : 0;
+    in.count(a, next);
     embed_tc_atom_start(a, s_gt, atom, false);  // visible after the front's barriers
+    auto rows_next = [&] { in.rows(a, next, row); };
     if (half == 0)
-      embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+      embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, cur.x, h1, h2, rows_next);
     else
-      embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+      embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, cur.x, h1, h2, rows_next);
     float* out = a.G0 + (size_t)atom * NP * EMB_E2;
     if (half == 0)
       embed_fwd_out<0>(a, tm + lane_off, s_gt + tj * EMB_E2, h2, rv, out, row);
     else
       embed_fwd_out<1>(a, tm + lane_off, s_gt + tj * EMB_E2, h2, rv, out, row);
+    in.type(a, row);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -1105,19 +1135,55 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_co
 // into the dZ3 tiles (8-column groups: half 0 takes columns [0, 56), half 1
 // [56, 104)), and the skip part dh2[c % 50] += g of the owned units.
 template <int H>
-__device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t taddr, const float* gt, const float4* dg,
-                                              bool rv, int row, uint8_t* sDZ3h, uint8_t* sDZ3l, float* dh2) {
+struct EmbDz3 {
   using O = EmbOwn<H>;
-  constexpr int gs_lo = H == 0 ? 0 : 7, gs_hi = H == 0 ? 7 : 13;  // stored 8-column groups
+  static constexpr int gs_lo = H == 0 ? 0 : 7, gs_hi = H == 0 ? 7 : 13;  // stored 8-column groups
+  // column quad c4 of dE/dG0 is read by this half
+  __host__ __device__ static constexpr bool need4(int c4) {
+    return c4 < EMB_E2 && ((((c4 >> 3) >= gs_lo && (c4 >> 3) < gs_hi)) || O::owns_c(c4) || O::owns_c(c4 + 1) ||
+                           O::owns_c(c4 + 2) || O::owns_c(c4 + 3));
+  }
+  __host__ __device__ static constexpr bool any16(int k) {
+    return need4(16 * k) || need4(16 * k + 4) || need4(16 * k + 8) || need4(16 * k + 12);
+  }
+};
+
+// This half's dE/dG0 column quads of 16-column chunk k of a row (zero where
+// not read, or past nnei).
+template <int H>
+__device__ __forceinline__ void embed_bwd_load16(const float4* dg, int k, int row, bool rv, float4* d) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c4 = 16 * k + 4 * q;
+    d[q] = EmbDz3<H>::need4(c4) && rv ? dg[(c4 >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Bring this half's dE/dG0 column quads of chunk k of a row into L1.
+template <int H>
+__device__ __forceinline__ void embed_bwd_prefetch16(const float4* dg, int k, int row, bool rv) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c4 = 16 * k + 4 * q;
+    if (EmbDz3<H>::need4(c4) && rv)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(dg + (c4 >> 2) * NP + row));
+  }
+}
+
+// dE/dG0 of chunk 0 is loaded (and chunk 1 brought into L1) by the caller
+// before it waits for Z3; chunk k + 1 is brought into L1 while chunk k is
+// processed.
+template <int H>
+__device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t taddr, const float* gt, const float4* dg,
+                                              bool rv, int row, uint8_t* sDZ3h, uint8_t* sDZ3l, float* dh2,
+                                              float4* dcur) {
+  using O = EmbOwn<H>;
+  constexpr int gs_lo = EmbDz3<H>::gs_lo, gs_hi = EmbDz3<H>::gs_hi;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    bool any = false;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int c = 16 * k + i;
-      any |= O::owns_c(c) || ((c >> 3) >= gs_lo && (c >> 3) < gs_hi);
-    }
-    if (!any) continue;
+    if (k > 0 && EmbDz3<H>::any16(k)) embed_bwd_load16<H>(dg, k, row, rv, dcur);
+    if (k + 2 < 7 && EmbDz3<H>::any16(k + 2)) embed_bwd_prefetch16<H>(dg, k + 2, row, rv);
+    if (EmbDz3<H>::any16(k)) {
     float z[16];
     tmem_ld16(taddr + 64 + 16 * k, z);
 #pragma unroll
@@ -1133,7 +1199,7 @@ __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t tad
         for (int t = 0; t < 4; ++t) need |= O::owns_c(c4 + t);
         float gq[4] = {0.f, 0.f, 0.f, 0.f};
         if (need && c4 < EMB_E2 && rv) {
-          const float4 d4 = dg[(c4 >> 2) * NP + row];
+          const float4 d4 = dcur[2 * gg + q];
           const float4 t4 = *reinterpret_cast<const float4*>(gt + c4);
           gq[0] = d4.x * (1.f + t4.x); gq[1] = d4.y * (1.f + t4.y);
           gq[2] = d4.z * (1.f + t4.z); gq[3] = d4.w * (1.f + t4.w);
@@ -1154,6 +1220,7 @@ __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t tad
         emb_store8(sDZ3h, row, 8 * g, 128, dz, false);
         emb_store8(sDZ3l, row, 8 * g, 128, dz, true);
       }
+    }
     }
   }
 }
@@ -1195,7 +1262,7 @@ __device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, c
 
 template <int H>
 __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
-                                               Sync& sy, int row, bool rv, size_t rowg, const float* gt,
+                                               Sync& sy, int row, bool rv, size_t rowg, float x, const float* gt,
                                                const float4* dg, float* xch) {
   using O = EmbOwn<H>;
   const bool issuer = threadIdx.x == 0;
@@ -1210,11 +1277,15 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sDZ2h = sm + EMB_WIMG;
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
   float h1[EMB_E0], h2[O::nb];
-  embed_tc_front<H>(a, sm, tm, lane_off, sy, row, rv, rowg, h1, h2);
+  float4 d0[4];
+  embed_tc_front<H>(a, sm, tm, lane_off, sy, row, rv, x, h1, h2, [&] {
+    embed_bwd_load16<H>(dg, 0, row, rv, d0);
+    embed_bwd_prefetch16<H>(dg, 1, row, rv);
+  });
   float dh2[O::nb];
 #pragma unroll
   for (int b = 0; b < O::nb; ++b) dh2[b] = 0.f;
-  embed_bwd_dz3<H>(a, tm + lane_off, gt, dg, rv, row, sDZ3h, sDZ3l, dh2);
+  embed_bwd_dz3<H>(a, tm + lane_off, gt, dg, rv, row, sDZ3h, sDZ3l, dh2, d0);
   handoff();
   // dH2 (product part) = dZ3 W2^T -> TMEM [0, 64)
   if (issuer)
@@ -1261,18 +1332,28 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_co
   Sync sy{bar, 0u, a.err};
   if (threadIdx.x == 0 && blockIdx.x < a.n)
     prefetch_l2(a.dG0 + (size_t)blockIdx.x * NP * EMB_E2, NP * EMB_E2 * sizeof(float));
+  EmbRowIn in;
+  in.count(a, blockIdx.x);
+  in.rows(a, blockIdx.x, row);
+  in.type(a, row);
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
-    const int nn = a.nnei[atom];
-    if (nn == 0) continue;  // uniform over the CTA
+    const EmbRowIn cur = in;
+    const int nn = cur.nn, tj = cur.tj, next = atom + gridDim.x;
+    in.count(a, next);
+    in.rows(a, next, row);
+    if (nn == 0) {  // uniform over the CTA
+      in.type(a, row);
+      continue;
+    }
     const bool rv = row < nn;
     const size_t rowg = (size_t)atom * NP + row;
-    const int tj = rv ? a.atype[a.nlist[rowg]] : 0;
     embed_tc_atom_start(a, s_gt, atom, true);  // visible after the front's barriers
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
     if (half == 0)
-      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, s_gt + tj * EMB_E2, dg, xch);
     else
-      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, s_gt + tj * EMB_E2, dg, xch);
+    in.type(a, row);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
