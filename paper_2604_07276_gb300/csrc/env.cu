@@ -137,28 +137,30 @@ void launch_env_bwd(const EnvBwdArgs& a, cudaStream_t st) {
 // Forces F_k = sum_j g_kj - sum_{i: k in N(i)} g_ik (Eq. eq_forceAtomicEnergy
 // with e_i depending on r_ij = x_j - x_i) and virial W = -sum r_ij (x) g_ij.
 // One warp per atom; the reverse rows are sorted so that every sum runs in a
-// fixed order (bitwise reproducible, no atomics).
+// fixed order (bitwise reproducible, no atomics).  A lane adds its few terms
+// and the warp its 32 lane sums in FP32 (a fixed tree; the FP64 pipe of this
+// GPU is narrow), the per-block virial and energy in FP64.
 constexpr int FWARPS = 4;
 __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
   __shared__ int srev[FWARPS][REV_CAP];
   __shared__ double sred[FWARPS][10];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * FWARPS + warp;
-  double f0 = 0, f1 = 0, f2 = 0;
-  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+  float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   double ek = 0;
   if (k < a.n) {
     const int nn = a.nnei[k];
+    int cnt = a.rev_cnt[k];
     for (int s = lane; s < nn; s += 32) {
       const size_t row = (size_t)k * NP + s;
       const float4 g = reinterpret_cast<const float4*>(a.g)[row];
       const float4 r = reinterpret_cast<const float4*>(a.rv)[row];
       f0 += g.x; f1 += g.y; f2 += g.z;
-      v[0] -= (double)r.x * g.x; v[1] -= (double)r.x * g.y; v[2] -= (double)r.x * g.z;
-      v[3] -= (double)r.y * g.x; v[4] -= (double)r.y * g.y; v[5] -= (double)r.y * g.z;
-      v[6] -= (double)r.z * g.x; v[7] -= (double)r.z * g.y; v[8] -= (double)r.z * g.z;
+      v[0] -= r.x * g.x; v[1] -= r.x * g.y; v[2] -= r.x * g.z;
+      v[3] -= r.y * g.x; v[4] -= r.y * g.y; v[5] -= r.y * g.z;
+      v[6] -= r.z * g.x; v[7] -= r.z * g.y; v[8] -= r.z * g.z;
     }
-    int cnt = a.rev_cnt[k];
     if (cnt > REV_CAP) cnt = REV_CAP;
     int* rows = srev[warp];
     int P = 1;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
       const float4 g = reinterpret_cast<const float4*>(a.g)[rows[t]];
       f0 -= g.x; f1 -= g.y; f2 -= g.z;
     }
-    f0 = warp_sum_d(f0); f1 = warp_sum_d(f1); f2 = warp_sum_d(f2);
+    f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
     if (lane == 0) {
       a.force[3 * k] = f0; a.force[3 * k + 1] = f1; a.force[3 * k + 2] = f2;
       ek = k < a.nlocal ? (double)a.e[k] : 0.0;  // ghost atoms: m_k = 0 (Eq. eq_forcesLocalGhost)
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
     }
   }
 #pragma unroll
-  for (int c = 0; c < 9; ++c) v[c] = warp_sum_d(v[c]);
+  for (int c = 0; c < 9; ++c) v[c] = warp_sum(v[c]);
   if (lane == 0) {
     for (int c = 0; c < 9; ++c) sred[warp][c] = v[c];
     sred[warp][9] = ek;
@@ -206,8 +208,16 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, dou
                            double* __restrict__ virial) {
   __shared__ double red[10][32];
   const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;  // 10 warps, one per quantity
-  double s = 0;
-  for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * 10 + c];
+  // eight independent partial sums per lane (eight loads in flight), added
+  // in a fixed order
+  double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int b = lane;
+  for (; b + 7 * 32 < nblocks; b += 8 * 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s8[u] += partials[(size_t)(b + 32 * u) * 10 + c];
+  }
+  for (; b < nblocks; b += 32) s8[0] += partials[(size_t)b * 10 + c];
+  double s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
   s = warp_sum_d(s);
   if (lane == 0) red[c][0] = s;
   __syncthreads();
