@@ -855,10 +855,18 @@ __global__ void k_desc_fwd(DescArgs a) {
     const float4* R4 = reinterpret_cast<const float4*>(a.R) + base;
     for (int q = warp; q < a.m1 / 4; q += nw) {
       float t[4][4] = {};
-      for (int s = lane; s < nn; s += 32) {
-        const float4 r = R4[s];
-        const float4 g = G4[(size_t)q * NP + s];
-        const float rr[4] = {r.x, r.y, r.z, r.w}, gg[4] = {g.x, g.y, g.z, g.w};
+      // the lane's (at most NP / 32) rows, their loads issued together
+      float4 rq[NP / 32], gq[NP / 32];
+#pragma unroll
+      for (int it = 0; it < NP / 32; ++it) {
+        const int s = lane + 32 * it;
+        rq[it] = s < nn ? R4[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        gq[it] = s < nn ? G4[(size_t)q * NP + s] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int it = 0; it < NP / 32; ++it) {
+        const float rr[4] = {rq[it].x, rq[it].y, rq[it].z, rq[it].w};
+        const float gg[4] = {gq[it].x, gq[it].y, gq[it].z, gq[it].w};
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -944,6 +952,7 @@ __global__ void k_desc_bwd(DescArgs a) {
     for (int s = threadIdx.x; s < NP; s += blockDim.x) {
       float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
       if (s < nn) {
+#pragma unroll 5
         for (int q = 0; q < m1 / 4; ++q) {
           const float4 g = G4[(size_t)q * NP + s];
           const float gg[4] = {g.x, g.y, g.z, g.w};
