@@ -958,19 +958,33 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sH2h = sH1l + EMB_TA;
   uint8_t* sH2l = sH2h + EMB_TA;
   const bool issuer = threadIdx.x == 0;
+  // layer 1: half 0 evaluates units 0-15, half 1 units 16-24; each stores the
+  // hi and lo parts of its 8-column groups of H1 (K = 25, read as 32) and
+  // leaves its units in TMEM columns [176, 208) (free in both kernels), where
+  // the other half reads them after the hand-off
+  constexpr int p0 = H == 0 ? 0 : 16, np = H == 0 ? 16 : EMB_E0 - 16;
 #pragma unroll
-  for (int p = 0; p < EMB_E0; ++p) h1[p] = rv ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
-  // H1 (K = 25, read as 32): half 0 stores the hi parts, half 1 the lo parts
+  for (int p = p0; p < p0 + np; ++p) h1[p] = rv ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
+  {
+    float v[16];
 #pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    float v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = 8 * g + i < EMB_E0 ? h1[8 * g + i] : 0.f;
-    emb_store8(H == 0 ? sH1h : sH1l, row, 8 * g, 128, v, H == 1);
+    for (int i = 0; i < 16; ++i) v[i] = p0 + i < EMB_E0 ? h1[p0 + i] : 0.f;
+    emb_store8(sH1h, row, p0, 128, v, false);
+    emb_store8(sH1l, row, p0, 128, v, true);
+    emb_store8(sH1h, row, p0 + 8, 128, v + 8, false);
+    emb_store8(sH1l, row, p0 + 8, 128, v + 8, true);
+    tmem_st16(tm + lane_off + 176 + p0, v);
   }
   handoff();
   if (issuer)
     mma_split(tm + 0, smem_u32(sH1h), smem_u32(sH1l), 128, smem_u32(sW1h), smem_u32(sW1l), false, 64, 64, 2);
+  {
+    constexpr int q0 = H == 0 ? 16 : 0, nq = H == 0 ? EMB_E0 - 16 : 16;
+    float v[16];
+    tmem_ld16(tm + lane_off + 176 + q0, v);
+#pragma unroll
+    for (int i = 0; i < nq; ++i) h1[q0 + i] = v[i];
+  }
   commit_and_sync(sy, issuer);
   // layer 2, owned units: h2 = h1[b % 25] + tanh(z2 + b1)
   constexpr int g_lo = O::b0 / 8, g_hi = H == 0 ? EMB_SPLIT / 8 : 7;  // 8-column groups stored
