@@ -6,14 +6,16 @@
 //
 // One persistent CTA per SM walks over centre atoms; an atom is one 128-row
 // tile (its neighbour slots).  Every product of a layer runs on the tensor
-// cores from 128x128 BF16 tiles in shared memory:
+// cores from 128x128 16-bit tiles in shared memory:
 //   forward : [Q K V] = G Wqkv, S = Q K^T, O = P V, Y = O Wo
 //   backward: [Q K V] = G Wqkv and S = Q K^T (recomputed), dO = dY Wo^T,
 //             dP = dO V^T, dV = P^T dO, dQ = dS K, dK = dS^T Q,
 //             dG = dQ Wq^T + dK Wk^T + dV Wv^T
 // The transposed operands are MN-major views of the same tiles, so no
 // transpose is ever materialised.  Softmax, LayerNorm and all element-wise
-// work run in FP32 on 256 threads (a thread owns half a row).
+// work run in FP32 on 512 threads (a thread owns a quarter of a row: 32
+// columns of one TMEM lane).  The embedding net (stages a5, a13) is at the
+// end of this file.
 #include <cuda_bf16.h>
 
 #include <cstring>
