@@ -140,6 +140,8 @@ def env_matrix(rij: torch.Tensor, mask: torch.Tensor, tcentre: torch.Tensor,
 #    embedding into G).  Reading (strip mode): Z[t] = tanh(onehot(t) W + b);
 #    type-pair table Gt[a, b] = net_t([Z[b], Z[a]]) (neighbour type first,
 #    centre type second); G0_ij = net_s(R_ij,0) * (1 + Gt[t_i, t_j]).
+#    Reading (concat mode, the original DPA-1 form): the embedding net reads
+#    the row [R_ij,0, Z[t_j], Z[t_i]] and G0_ij is its output.
 #    Both nets: dense + tanh layers with the residual rule y = x + f(x)
 #    when the width is kept, y = [x, x] + f(x) when it doubles, else f(x).
 # ---------------------------------------------------------------------------
@@ -262,11 +264,21 @@ def atomic_energies(model: OracleModel, rij: torch.Tensor, nlist: np.ndarray, at
     tn = torch.as_tensor(np.where(nlist >= 0, np.asarray(atype_all)[np.maximum(nlist, 0)], 0).astype(np.int64))
     R, w, rhat = env_matrix(rij, mask, tc, t["davg"], t["dstd"], cfg.rcut_smth, cfg.rcut)
     tebd = type_embedding(t["te_W"], t["te_b"])
-    Gt = type_pair_table(tebd, model.layers("tt", len(cfg.embed)))
-    Gs = embedding_net(R[..., 0:1], model.layers("em", len(cfg.embed)))
-    G = Gs * (1.0 + Gt[tc[:, None], tn]) * mask.to(F64)[..., None]
+    if getattr(cfg, "tebd_input_mode", "strip") == "concat":
+        # concat mode: the embedding net reads [s, T_j, T_i]
+        Gt = None
+        tj = tebd[tn]
+        ti = tebd[tc][:, None, :].expand_as(tj)
+        Gs = embedding_net(torch.cat([R[..., 0:1], tj, ti], dim=-1), model.layers("em", len(cfg.embed)))
+        G = Gs * mask.to(F64)[..., None]
+    else:
+        Gt = type_pair_table(tebd, model.layers("tt", len(cfg.embed)))
+        Gs = embedding_net(R[..., 0:1], model.layers("em", len(cfg.embed)))
+        G = Gs * (1.0 + Gt[tc[:, None], tn]) * mask.to(F64)[..., None]
     if stages is not None:
-        stages.update(R=R, w=w, rhat=rhat, G0=G, tebd=tebd, Gt=Gt)
+        stages.update(R=R, w=w, rhat=rhat, G0=G, tebd=tebd)
+        if Gt is not None:
+            stages["Gt"] = Gt
     for l in range(cfg.attn_layers):
         G = gated_attention(G, w, rhat, mask, model.attn(l), cfg.attn_shift, cfg.ln_eps)
         if stages is not None:

@@ -13,7 +13,8 @@ Weight file layout (little endian), read by ``dp_init``:
     char    magic[8]      = b"DPA1WTS1"
     int32   ints[16]      = version(1), ntypes, tebd_dim, sel, axis,
                             n_embed, embed[0..2], n_attn, attn_dim,
-                            n_fit, fit[0..2], reserved
+                            n_fit, fit[0..2], type-embedding mode
+                            (0: strip, 1: concat)
     float64 dbls[8]       = rcut, rcut_smth, attn_shift, ln_eps,
                             out_scale, 0, 0, 0
     char    type_map[ntypes][8]
@@ -51,6 +52,10 @@ class ModelConfig:
     ln_eps: float = 1e-5
     # Output scale of the fitting net (1.0 unless a calibrated value is given).
     out_scale: float = 1.0
+    # How the type embedding enters the embedding net: "strip" (the paper's
+    # model: G0 = net_s(s) * (1 + net_t([T_j, T_i]))) or "concat" (the
+    # embedding net's input is [s, T_j, T_i]).
+    tebd_input_mode: str = "strip"
 
     @property
     def m1(self) -> int:
@@ -78,11 +83,13 @@ def tensor_order(cfg: ModelConfig) -> List[Tuple[str, Tuple[int, ...]]]:
     out: List[Tuple[str, Tuple[int, ...]]] = []
     nt, td = cfg.ntypes, cfg.tebd_dim
     out += [("te_W", (nt, td)), ("te_b", (td,))]
-    fan = 2 * td
-    for l, w in enumerate(cfg.embed):
-        out += [(f"tt_W{l}", (fan, w)), (f"tt_b{l}", (w,))]
-        fan = w
-    fan = 1
+    concat = cfg.tebd_input_mode == "concat"
+    if not concat:
+        fan = 2 * td
+        for l, w in enumerate(cfg.embed):
+            out += [(f"tt_W{l}", (fan, w)), (f"tt_b{l}", (w,))]
+            fan = w
+    fan = 1 + 2 * td if concat else 1
     for l, w in enumerate(cfg.embed):
         out += [(f"em_W{l}", (fan, w)), (f"em_b{l}", (w,))]
         fan = w
@@ -151,8 +158,10 @@ def write_weights(path: str, cfg: ModelConfig, weights: Dict[str, np.ndarray]) -
     if len(cfg.embed) != 3 or len(cfg.fitting) not in (2, 3):
         raise ValueError("file format holds 3 embedding layers and 2 or 3 fitting layers")
     fit = list(cfg.fitting) + [0] * (3 - len(cfg.fitting))
+    if cfg.tebd_input_mode not in ("strip", "concat"):
+        raise ValueError("tebd_input_mode is strip or concat")
     ints = [1, cfg.ntypes, cfg.tebd_dim, cfg.sel, cfg.axis, len(cfg.embed), *cfg.embed,
-            cfg.attn_layers, cfg.attn_dim, len(cfg.fitting), *fit, 0]
+            cfg.attn_layers, cfg.attn_dim, len(cfg.fitting), *fit, 1 if cfg.tebd_input_mode == "concat" else 0]
     assert len(ints) == 16
     out_scale = float(np.asarray(weights.get("out_scale", cfg.out_scale)))
     dbls = [cfg.rcut, cfg.rcut_smth, cfg.attn_shift, cfg.ln_eps, out_scale, 0.0, 0.0, 0.0]

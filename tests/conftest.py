@@ -36,6 +36,20 @@ def rich_model():
 
 
 @pytest.fixture(scope="session")
+def concat_model():
+    """Default sizes with the concat type-embedding mode (the embedding net
+    reads [s, T_j, T_i]) and non-zero biases."""
+    import dataclasses
+
+    import synth
+    from oracle import OracleModel
+
+    cfg = dataclasses.replace(synth.DEFAULT_CONFIG, tebd_input_mode="concat")
+    w = synth.make_weights(cfg, seed=7, bias_scale=0.1)
+    return cfg, w, OracleModel.from_numpy(cfg, w)
+
+
+@pytest.fixture(scope="session")
 def water():
     import synth
 

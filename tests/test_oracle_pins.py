@@ -378,3 +378,84 @@ def test_local_ghost_decomposition_reassembles_the_box():
     assert abs(Es - E) < 1e-10 * max(1.0, abs(E))
     assert np.abs(Fs - F).max() < 1e-10
     assert np.abs(Ws - W).max() < 1e-9
+
+
+def _one_type(cfg, mode):
+    import dataclasses
+
+    return dataclasses.replace(cfg, ntypes=1, type_map=("X",), embed=(16, 32, 64), axis=8, attn_layers=1,
+                               fitting=(64, 64), tebd_input_mode=mode)
+
+
+def test_concat_single_type_reduces_to_strip():
+    """With one atom type the concat input [s, T, T] adds a constant to the
+    first layer: concat mode equals strip mode with that constant in the
+    first bias, G0 divided by strip mode's (1 + Gt[0, 0]).  The two modes
+    build G0 by separate code, so this checks the concat path's input."""
+    base = synth.DEFAULT_CONFIG
+    cc, cs = _one_type(base, "concat"), _one_type(base, "strip")
+    wc = synth.make_weights(cc, seed=11, bias_scale=0.2)
+    ws = synth.make_weights(cs, seed=12, bias_scale=0.2)
+    for k in wc:
+        if k in ws and not k.startswith("em_W0") and not k.startswith("em_b0"):
+            ws[k] = wc[k]
+    td = cc.tebd_dim
+    T = np.tanh(wc["te_W"][0] + wc["te_b"])
+    ws["em_W0"] = wc["em_W0"][0:1]
+    ws["em_b0"] = wc["em_b0"] + T @ wc["em_W0"][1:1 + td] + T @ wc["em_W0"][1 + td:]
+    mc, ms = OracleModel.from_numpy(cc, wc), OracleModel.from_numpy(cs, ws)
+    coord, atype, box = synth.water_box(seed=3)
+    atype = np.zeros_like(atype)
+    stc, sts = {}, {}
+    energy_force_virial(mc, coord[:40], box, atype[:40], stages=stc)
+    energy_force_virial(ms, coord[:40], box, atype[:40], stages=sts)
+    gt = sts["Gt"][0, 0]
+    assert torch.allclose(stc["G0"] * (1.0 + gt), sts["G0"], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("block", ["neighbour", "centre"])
+def test_concat_input_orders_neighbour_then_centre(concat_model, block):
+    """With only the neighbour block (columns 1..td of the input) of the
+    first layer non-zero, a row of G0 depends on the neighbour's type and
+    not on the centre's; with only the centre block, the other way round."""
+    import dataclasses
+
+    cfg, w, _ = concat_model
+    td = cfg.tebd_dim
+    w = dict(w)
+    W0 = w["em_W0"].copy()
+    if block == "neighbour":
+        W0[1 + td:] = 0.0
+    else:
+        W0[1:1 + td] = 0.0
+    w["em_W0"] = W0
+    m = OracleModel.from_numpy(cfg, w)
+    box = np.array([30.0, 30.0, 30.0])
+    coord = np.array([[10.0, 10.0, 10.0], [11.5, 10.0, 10.0]])  # centre 0, neighbour 1 at 1.5 A
+    g = {}
+    for tc in (0, 3):
+        for tn in (1, 4):
+            st = {}
+            energy_force_virial(m, coord, box, np.array([tc, tn], np.int32), centres=np.array([0]), stages=st)
+            g[tc, tn] = st["G0"][0, 0]
+    if block == "neighbour":
+        assert torch.equal(g[0, 1], g[3, 1]) and not torch.allclose(g[0, 1], g[0, 4])
+    else:
+        assert torch.equal(g[0, 1], g[0, 4]) and not torch.allclose(g[0, 1], g[3, 1])
+
+
+def test_concat_forces_central_difference(concat_model, water):
+    cfg, w, m = concat_model
+    coord, atype, box = water
+    E, e, F, W = energy_force_virial(m, coord, box, atype)
+    nl, _, _ = oracle.neighbor_list(coord, box, cfg.rcut, cfg.sel)
+    h = 1e-4
+
+    def en(a, k, t):
+        c = coord.copy(); c[a, k] += t
+        return energy_force_virial(m, c, box, atype, nlist=nl)[0]
+
+    for a in (5, 77):
+        for k in range(3):
+            fd4 = -(-en(a, k, 2 * h) + 8 * en(a, k, h) - 8 * en(a, k, -h) + en(a, k, -2 * h)) / (12 * h)
+            assert abs(fd4 - F[a, k]) < 1e-8 * max(1.0, abs(F[a, k])), (a, k, fd4, F[a, k])
