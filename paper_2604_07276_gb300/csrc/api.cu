@@ -57,13 +57,14 @@ std::vector<Shape> tensor_order(const int* I) {
   std::vector<Shape> out;
   out.push_back({"te_W", (size_t)nt * td});
   out.push_back({"te_b", (size_t)td});
+  const bool concat = I[15] == 1;  // the embedding net reads [s, T_j, T_i]; no type-pair net
   int fan = 2 * td;
-  for (int l = 0; l < nemb; ++l) {
+  for (int l = 0; l < nemb && !concat; ++l) {
     out.push_back({"tt_W" + std::to_string(l), (size_t)fan * emb[l]});
     out.push_back({"tt_b" + std::to_string(l), (size_t)emb[l]});
     fan = emb[l];
   }
-  fan = 1;
+  fan = concat ? 1 + 2 * td : 1;
   for (int l = 0; l < nemb; ++l) {
     out.push_back({"em_W" + std::to_string(l), (size_t)fan * emb[l]});
     out.push_back({"em_b" + std::to_string(l), (size_t)emb[l]});
@@ -101,7 +102,7 @@ int read_weights(const char* path, HostWeights& w, bool header_only) {
   if (!ok) { fclose(f); return fail(DP_ERR_IO, "bad weight file header"); }
   const int* I = w.ints;
   if (I[0] != 1 || I[1] < 1 || I[1] > 64 || I[2] < 1 || I[2] > 16 || I[3] < 1 || I[5] != 3 || I[9] < 0 ||
-      I[9] > 8 || I[11] < 1 || I[11] > 3 || I[4] < 1 || I[4] > I[8]) {
+      I[9] > 8 || I[11] < 1 || I[11] > 3 || I[4] < 1 || I[4] > I[8] || I[15] < 0 || I[15] > 1) {
     fclose(f);
     return fail(DP_ERR_IO, "weight file header out of range");
   }
@@ -421,7 +422,7 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   // a5: embedding
   EmbedArgs ea{};
   ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
-  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = ws.G[0];
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.b0t = m->b0t; ea.G0 = ws.G[0];
   launch_embed_fwd(ea, m->emb, st);
   prof_mark(m, "embed_fwd", st);
   // a6: attention layers
@@ -588,8 +589,36 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     return fail_free(fail(DP_ERR_UNSUPPORTED, "embedding widths without a kernel instance"));
   if ((rc = dev_upload(m, &m->davg, to_f(*w.get("davg")))) != DP_OK) return fail_free(rc);
   if ((rc = dev_upload(m, &m->dstd, to_f(*w.get("dstd")))) != DP_OK) return fail_free(rc);
+  m->concat = I[15] == 1;
+  if (m->concat) {
+    // concat mode: the type embedding Z on the host, the type-pair table of
+    // strip mode replaced by zeros (G0 = net output), and the part of the
+    // first layer that the types contribute folded into a bias per (centre
+    // type a, neighbour type b): b0 + Z[b] W0[1 .. td] + Z[a] W0[1 + td ..]
+    const std::vector<double>& teW = *w.get("te_W");
+    const std::vector<double>& teb = *w.get("te_b");
+    const std::vector<double>& W0 = *w.get("em_W0");  // [1 + 2 td][E0]
+    const std::vector<double>& b0 = *w.get("em_b0");
+    const int nt = m->nt, td = m->td, e0 = m->emb[0];
+    std::vector<double> Z((size_t)nt * td);
+    for (int t = 0; t < nt; ++t)
+      for (int c = 0; c < td; ++c) Z[(size_t)t * td + c] = std::tanh(teW[(size_t)t * td + c] + teb[c]);
+    std::vector<float> z((size_t)nt * td), gt((size_t)nt * nt * m->m1, 0.f), b0t((size_t)nt * nt * e0);
+    for (size_t i = 0; i < z.size(); ++i) z[i] = (float)Z[i];
+    for (int a = 0; a < nt; ++a)
+      for (int b = 0; b < nt; ++b)
+        for (int p = 0; p < e0; ++p) {
+          double v = b0[p];
+          for (int c = 0; c < td; ++c)
+            v += Z[(size_t)b * td + c] * W0[(size_t)(1 + c) * e0 + p] + Z[(size_t)a * td + c] * W0[(size_t)(1 + td + c) * e0 + p];
+          b0t[((size_t)a * nt + b) * e0 + p] = (float)v;
+        }
+    if ((rc = dev_upload(m, &m->tebd, z)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->Gt, gt)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->b0t, b0t)) != DP_OK) return fail_free(rc);
+  }
   // type tables (a4) on the device
-  {
+  if (!m->concat) {
     std::vector<double> tt;
     for (int l = 0; l < 3; ++l) {
       auto* W = w.get("tt_W" + std::to_string(l));
@@ -639,7 +668,8 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     for (int l = 0; l < 3; ++l) {
       auto* W = w.get("em_W" + std::to_string(l));
       auto* b = w.get("em_b" + std::to_string(l));
-      th.insert(th.end(), W->begin(), W->end());
+      // concat mode: only the s row of the first layer (its type rows are in b0t)
+      th.insert(th.end(), W->begin(), l == 0 && m->concat ? W->begin() + m->emb[0] : W->end());
       th.insert(th.end(), b->begin(), b->end());
     }
     m->off_fitW.resize(m->nfit);
@@ -1005,8 +1035,9 @@ int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double*
                    double e_ref, const double* d_force_ref, double pe, double pf, double fd_h, double* d_loss,
                    void* stream) {
   if (check_model(m)) return DP_ERR_ARG;
-  if (m->precision != DP_PREC_FP32 || m->nattn != 0)
-    return fail(DP_ERR_UNSUPPORTED, "dp_train_frame: training needs an FP32 model without attention layers");
+  if (m->precision != DP_PREC_FP32 || m->nattn != 0 || m->concat)
+    return fail(DP_ERR_UNSUPPORTED,
+                "dp_train_frame: training needs an FP32 model without attention layers in strip type-embedding mode");
   if (natoms < 1 || !d_coord || !d_box || !d_atype || !d_force_ref || !d_loss || !(fd_h > 0.0))
     return fail(DP_ERR_ARG, "dp_train_frame: bad arguments");
   if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");

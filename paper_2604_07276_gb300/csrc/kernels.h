@@ -94,6 +94,8 @@ struct EmbedArgs {
   int n, ntypes, m1;
   const float* w;   // packed embedding-net weights (W0 b0 W1 b1 W2 b2)
   const float* Gt;  // [ntypes][ntypes][m1]
+  const float* b0t; // concat type-embedding mode: first-layer bias per (centre, neighbour)
+                    // type [ntypes][ntypes][E0]; null: the b0 of the packed weights
   float* G0;        // [rows][m1]
   const float* dG0;  // backward only
   float* dR;         // backward only: dR[:,0] +=

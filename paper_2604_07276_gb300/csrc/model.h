@@ -129,6 +129,8 @@ struct dp_model {
   int t_cap = 0;
   // device weights
   float *emb_packed, *Gt, *tebd, *davg, *dstd, *ebias, *w_out;
+  bool concat = false;     // type-embedding mode: the embedding net reads [s, T_j, T_i]
+  float* b0t = nullptr;    // concat mode: first-layer bias per (centre, neighbour) type [nt][nt][E0]
   std::vector<AttnLayerW> attn;
   std::vector<float*> fitW, fitWT, fitb;
   TcWeights tcw;

@@ -136,7 +136,7 @@ struct EmbedSmem {
   static constexpr int W0 = 0, B0 = E0, W1 = 2 * E0, B1 = W1 + E0 * E1, W2 = B1 + E1, B2 = W2 + E1 * P2,
                        X = B2 + E2, H1 = X + EROWS, H2 = H1 + EROWS * (E0 + 1), Z = H2 + EROWS * (E1 + 1),
                        DH2 = Z + EROWS * (E2 + 1), DZ2 = DH2 + EROWS * (E1 + 1), DH1 = DZ2 + EROWS * (E1 + 1),
-                       TOTAL = DH1 + EROWS * (E0 + 1);
+                       TJ = DH1 + EROWS * (E0 + 1), TOTAL = TJ + EROWS;  // TJ: the rows' neighbour types (int)
 };
 
 template <int E0, int E1, int E2>
@@ -146,17 +146,24 @@ __device__ __forceinline__ void embed_load(float* sm, const EmbedArgs& a, size_t
   for (int t = threadIdx.x; t < Lw::W2; t += ETHREADS) sm[t] = a.w[t];  // W0 b0 W1 b1 share offsets
   for (int t = threadIdx.x; t < E1 * E2; t += ETHREADS) sm[S::W2 + (t / E2) * S::P2 + t % E2] = a.w[Lw::W2 + t];
   for (int t = threadIdx.x; t < E2; t += ETHREADS) sm[S::B2 + t] = a.w[Lw::B2 + t];
-  for (int r = threadIdx.x; r < EROWS; r += ETHREADS) sm[S::X + r] = r < cnt ? a.R[(base + r) * 4] : 0.f;
+  for (int r = threadIdx.x; r < EROWS; r += ETHREADS) {
+    sm[S::X + r] = r < cnt ? a.R[(base + r) * 4] : 0.f;
+    reinterpret_cast<int*>(sm + S::TJ)[r] = r < cnt ? a.atype[a.nlist[base + r]] : 0;
+  }
   __syncthreads();
 }
 
 // Layers 1 and 2, then Z = H2 W2 + b2 (4 rows per thread per weight load).
+// b0t: the centre type's rows of the concat mode's first-layer bias table
+// ([neighbour type][E0]), or null (strip mode: b0).
 template <int E0, int E1, int E2>
-__device__ __forceinline__ void embed_forward(float* sm, int cnt) {
+__device__ __forceinline__ void embed_forward(float* sm, int cnt, const float* b0t) {
   using S = EmbedSmem<E0, E1, E2>;
+  const int* tj = reinterpret_cast<const int*>(sm + S::TJ);
   for (int idx = threadIdx.x; idx < EROWS * E0; idx += ETHREADS) {
     const int r = idx / E0, p = idx % E0;
-    sm[S::H1 + r * (E0 + 1) + p] = r < cnt ? tanhf(fmaf(sm[S::X + r], sm[S::W0 + p], sm[S::B0 + p])) : 0.f;
+    const float b = b0t ? b0t[tj[r] * E0 + p] : sm[S::B0 + p];
+    sm[S::H1 + r * (E0 + 1) + p] = r < cnt ? tanhf(fmaf(sm[S::X + r], sm[S::W0 + p], b)) : 0.f;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(ETHREADS) k_embed_fwd(EmbedArgs a) {
   const size_t base = (size_t)atom * NP + r0;
   if (cnt > 0) {
     embed_load<E0, E1, E2>(sm, a, base, cnt);
-    embed_forward<E0, E1, E2>(sm, cnt);
+    embed_forward<E0, E1, E2>(sm, cnt, a.b0t ? a.b0t + (size_t)a.atype[atom] * a.ntypes * E0 : nullptr);
   }
   const int ti = a.atype[atom];
   for (int idx = threadIdx.x; idx < EROWS * E2; idx += ETHREADS) {
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(ETHREADS) k_embed_bwd(EmbedArgs a) {
   if (cnt == 0) return;
   const size_t base = (size_t)atom * NP + r0;
   embed_load<E0, E1, E2>(sm, a, base, cnt);
-  embed_forward<E0, E1, E2>(sm, cnt);
+  embed_forward<E0, E1, E2>(sm, cnt, a.b0t ? a.b0t + (size_t)a.atype[atom] * a.ntypes * E0 : nullptr);
   const int ti = a.atype[atom];
   // Z <- dZ3 = g (1 - t3^2) with g = dG0 (1 + Gt); the skip part of dH2 is
   // summed from g directly below
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(ETHREADS) k_embed_wgrad(EmbedArgs a, float* gr
     const size_t base = (size_t)atom * NP + r0;
     __syncthreads();
     embed_load<E0, E1, E2>(sm, a, base, cnt);
-    embed_forward<E0, E1, E2>(sm, cnt);
+    embed_forward<E0, E1, E2>(sm, cnt, a.b0t ? a.b0t + (size_t)a.atype[atom] * a.ntypes * E0 : nullptr);
     const int ti = a.atype[atom];
     for (int idx = threadIdx.x; idx < EROWS * E2; idx += ETHREADS) {
       const int r = idx / E2, c = idx % E2;

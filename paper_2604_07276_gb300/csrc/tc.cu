@@ -889,8 +889,11 @@ constexpr int EMB_TD = 128 * 128 * 2;   // dZ3 tile: 128 rows x 128 cols
 constexpr int EMB_WIMG = 2 * EMB_T1 + 2 * EMB_T2;  // W1 hi, W1 lo, W2 hi, W2 lo
 constexpr int EMB_MAXT = 8;                           // atom types the staged type-pair rows allow
 constexpr int EMB_GT = EMB_MAXT * EMB_E2 * 4;         // this atom's rows of the type-pair table
-constexpr int EMBF_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 64;
-constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 512 + 64;  // dZ3 tiles reuse the four activation tiles
+constexpr int EMB_B0 = EMB_MAXT * EMB_E0 * 4;         // concat mode: this atom's rows of the first-layer bias table
+constexpr int EMBF_B0 = EMB_WIMG + 4 * EMB_TA + EMB_GT;             // forward: bias rows after the type-pair rows
+constexpr int EMBB_B0 = EMB_WIMG + 4 * EMB_TA + EMB_GT + 512;       // adjoint: after them and the dE/dx exchange
+constexpr int EMBF_SMEM = EMBF_B0 + EMB_B0 + 64;
+constexpr int EMBB_SMEM = EMBB_B0 + EMB_B0 + 64;  // dZ3 tiles reuse the four activation tiles
 static_assert(2 * EMB_TD == 4 * EMB_TA, "the dZ3 hi / lo tiles fill the activation tiles");
 
 struct EmbedTcArgs {
@@ -902,6 +905,8 @@ struct EmbedTcArgs {
   float* G0;              // fwd out, column-quad interleaved per atom
   const float* dG0;       // bwd in, column-quad interleaved per atom
   float* dR;              // bwd: dR[:,0] +=
+  const float* b0t;       // concat type-embedding mode: first-layer bias per (centre,
+                          // neighbour) type [ntypes][ntypes][E0]; null: b0 below
   const uint4* wimg;      // W1/W2 hi/lo tiles
   int n, ntypes;
   int* err;
@@ -948,8 +953,8 @@ struct EmbOwn {
 // layer-2 units.
 template <int H, class BeforeZ3>
 __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
-                                               Sync& sy, int row, bool rv, float x, float* h1, float* h2,
-                                               BeforeZ3 before_z3) {
+                                               Sync& sy, int row, bool rv, float x, const float* b0row, float* h1,
+                                               float* h2, BeforeZ3 before_z3) {
   using O = EmbOwn<H>;
   uint8_t* sW1h = sm;
   uint8_t* sW1l = sW1h + EMB_T1;
@@ -966,7 +971,7 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
   // the other half reads them after the hand-off
   constexpr int p0 = H == 0 ? 0 : 16, np = H == 0 ? 16 : EMB_E0 - 16;
 #pragma unroll
-  for (int p = p0; p < p0 + np; ++p) h1[p] = rv ? tanhf(fmaf(x, a.W0[p], a.b0[p])) : 0.f;
+  for (int p = p0; p < p0 + np; ++p) h1[p] = rv ? tanhf(fmaf(x, a.W0[p], b0row ? b0row[p] : a.b0[p])) : 0.f;
   {
     float v[16];
 #pragma unroll
@@ -1059,13 +1064,20 @@ __device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm
   handoff();
 }
 
-// Per atom: copy the centre type's rows of the type-pair table Gt[t_i][*] to
-// shared memory (read as float4 by neighbour type afterwards), and bring the
-// next atom's per-row inputs into L2.
-__device__ __forceinline__ void embed_tc_atom_start(const EmbedTcArgs& a, float* s_gt, int atom, bool bwd) {
+// Per atom: copy the centre type's rows of the type-pair table Gt[t_i][*]
+// (and, in concat mode, of the first-layer bias table) to shared memory,
+// read by neighbour type afterwards, and bring the next atom's per-row inputs
+// into L2.
+__device__ __forceinline__ void embed_tc_atom_start(const EmbedTcArgs& a, float* s_gt, float* s_b0, int atom,
+                                                    bool bwd) {
   const float4* src = reinterpret_cast<const float4*>(a.Gt + (size_t)a.atype[atom] * a.ntypes * EMB_E2);
   float4* dst = reinterpret_cast<float4*>(s_gt);
   for (int i = threadIdx.x; i < a.ntypes * EMB_E2 / 4; i += blockDim.x) dst[i] = src[i];
+  if (a.b0t) {  // read by layer 1 right away: a barrier of its own
+    const float* b0 = a.b0t + (size_t)a.atype[atom] * a.ntypes * EMB_E0;
+    for (int i = threadIdx.x; i < a.ntypes * EMB_E0; i += blockDim.x) s_b0[i] = b0[i];
+    __syncthreads();
+  }
   const int next = atom + gridDim.x;
   if (threadIdx.x == 0 && next < a.n) {
     const size_t base = (size_t)next * NP;
@@ -1115,6 +1127,7 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_co
   const int row = quad * 32 + lane;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
+  float* s_b0 = reinterpret_cast<float*>(sm + EMBF_B0);
   Sync sy{bar, 0u, a.err};
   float h1[EMB_E0], h2[EMB_E1 - EMB_SPLIT];
   EmbRowIn in;
@@ -1126,12 +1139,13 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_co
     const int nn = cur.nn, tj = cur.tj, next = atom + gridDim.x;
     const bool rv = row < nn;
     in.count(a, next);
-    embed_tc_atom_start(a, s_gt, atom, false);  // visible after the front's barriers
+    embed_tc_atom_start(a, s_gt, s_b0, atom, false);  // visible after the front's barriers
     auto rows_next = [&] { in.rows(a, next, row); };
+    const float* b0row = a.b0t ? s_b0 + tj * EMB_E0 : nullptr;
     if (half == 0)
-      embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, cur.x, h1, h2, rows_next);
+      embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
     else
-      embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, cur.x, h1, h2, rows_next);
+      embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
     float* out = a.G0 + (size_t)atom * NP * EMB_E2;
     if (half == 0)
       embed_fwd_out<0>(a, tm + lane_off, s_gt + tj * EMB_E2, h2, rv, out, row);
@@ -1278,8 +1292,8 @@ __device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, c
 
 template <int H>
 __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
-                                               Sync& sy, int row, bool rv, size_t rowg, float x, const float* gt,
-                                               const float4* dg, float* xch) {
+                                               Sync& sy, int row, bool rv, size_t rowg, float x, const float* b0row,
+                                               const float* gt, const float4* dg, float* xch) {
   using O = EmbOwn<H>;
   const bool issuer = threadIdx.x == 0;
   uint8_t* sW1h = sm;
@@ -1294,7 +1308,7 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
   float h1[EMB_E0], h2[O::nb];
   float4 d0[4];
-  embed_tc_front<H>(a, sm, tm, lane_off, sy, row, rv, x, h1, h2, [&] {
+  embed_tc_front<H>(a, sm, tm, lane_off, sy, row, rv, x, b0row, h1, h2, [&] {
     embed_bwd_load16<H>(dg, 0, row, rv, d0);
     embed_bwd_prefetch16<H>(dg, 1, row, rv);
   });
@@ -1345,6 +1359,7 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_co
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
   float* xch = s_gt + EMB_MAXT * EMB_E2;  // [128] half 1's part of dE/dx
+  float* s_b0 = reinterpret_cast<float*>(sm + EMBB_B0);
   Sync sy{bar, 0u, a.err};
   if (threadIdx.x == 0 && blockIdx.x < a.n)
     prefetch_l2(a.dG0 + (size_t)blockIdx.x * NP * EMB_E2, NP * EMB_E2 * sizeof(float));
@@ -1363,12 +1378,13 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_co
     }
     const bool rv = row < nn;
     const size_t rowg = (size_t)atom * NP + row;
-    embed_tc_atom_start(a, s_gt, atom, true);  // visible after the front's barriers
+    embed_tc_atom_start(a, s_gt, s_b0, atom, true);  // visible after the front's barriers
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
+    const float* b0row = a.b0t ? s_b0 + tj * EMB_E0 : nullptr;
     if (half == 0)
-      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, b0row, s_gt + tj * EMB_E2, dg, xch);
     else
-      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, b0row, s_gt + tj * EMB_E2, dg, xch);
     in.type(a, row);
     fence_before_sync();
     __syncthreads();
@@ -1590,13 +1606,13 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   EmbedArgs ea{};
   float* rm_stage = reinterpret_cast<float*>(ws.tc.p[3]);
   ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m->m1;
-  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.G0 = rm_stage;
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.b0t = m->b0t; ea.G0 = rm_stage;
   const bool emb_tc = m->tcw.emb_W1_t != nullptr;
   EmbedTcArgs et{};
   if (emb_tc) {
     et.R = ws.R; et.nlist = ws.nlist; et.nnei = ws.nnei; et.atype = atype; et.Gt = m->Gt; et.G0 = ws.G[0];
     et.dG0 = ws.dG; et.dR = ws.dR; et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W1_t);
-    et.n = n; et.ntypes = m->nt; et.err = m->d_err;
+    et.n = n; et.ntypes = m->nt; et.err = m->d_err; et.b0t = m->b0t;
     memcpy(et.W0, m->tcw.emb_vec.W0, sizeof(et.W0));
     memcpy(et.b0, m->tcw.emb_vec.b0, sizeof(et.b0));
     memcpy(et.b1, m->tcw.emb_vec.b1, sizeof(et.b1));
