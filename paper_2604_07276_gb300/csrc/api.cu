@@ -561,7 +561,8 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
   if (sel >= 0 && sel != I[3]) return fail(DP_ERR_ARG, "sel differs from the weight file");
   if (I[3] > NP) return fail(DP_ERR_UNSUPPORTED, "sel above 128 is not supported");
   if (I[8] > 128) return fail(DP_ERR_UNSUPPORTED, "embedding width above 128 is not supported");
-  if (I[9] > 0 && I[10] != 128) return fail(DP_ERR_UNSUPPORTED, "attention width other than 128 is not supported");
+  if (I[9] > 0 && I[10] != 128 && I[10] != 256)
+    return fail(DP_ERR_UNSUPPORTED, "attention widths other than 128 and 256 are not supported");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();

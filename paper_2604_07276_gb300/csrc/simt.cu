@@ -532,12 +532,15 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 //   A_jk = softmax_k(l'_jk);   P_jk = A_jk w_j w_k (rhat_j . rhat_k);  O = P V
 constexpr int AW = 8;  // warps per block
 
+// Above an attention width of 128, K alone fills shared memory: V is then
+// read from global memory (through L1) instead (VG).
 template <int A>
 __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
+  constexpr bool VG = A > 128;
   extern __shared__ float sm[];
   float* Ks = sm;                                   // [NP][A+1]
-  float* Vs = Ks + NP * (A + 1);                    // [NP][A]
-  float4* rws = reinterpret_cast<float4*>(Vs + NP * A);  // [NP]
+  float* Vs = Ks + NP * (A + 1);                    // [NP][A] (not with VG)
+  float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * A));  // [NP]
   float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][A]
   float* prow = qrow + AW * A;                      // [AW][NP]
   double* w64s = reinterpret_cast<double*>(prow + AW * NP);  // [NP]
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
       Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
-      Vs[r * A + f] = a.QKV[(base + r) * ld + 2 * A + f];
+      if (!VG) Vs[r * A + f] = a.QKV[(base + r) * ld + 2 * A + f];
     }
     for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -614,8 +617,9 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
       for (int m = 0; m < FQ; ++m) acc[m] = 0.f;
       for (int k = 0; k < nn; ++k) {
         const float pk = p[k];
+        const float* vk = VG ? a.QKV + (base + k) * ld + 2 * A : Vs + k * A;
 #pragma unroll
-        for (int m = 0; m < FQ; ++m) acc[m] = fmaf(pk, Vs[k * A + lane + 32 * m], acc[m]);
+        for (int m = 0; m < FQ; ++m) acc[m] = fmaf(pk, vk[lane + 32 * m], acc[m]);
       }
 #pragma unroll
       for (int m = 0; m < FQ; ++m) o[lane + 32 * m] = acc[m];
@@ -632,10 +636,11 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
 // pass 1 left (transposed) in this block's global scratch slot.
 template <int A>
 __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
+  constexpr bool VG = A > 128;  // V and dO from global memory, as in the forward
   extern __shared__ float sm[];
   float* Ks = sm;                                   // [NP][A+1]   pass 2: Q
-  float* Vs = Ks + NP * (A + 1);                    // [NP][A+1]   pass 2: dO
-  float4* rws = reinterpret_cast<float4*>(Vs + NP * (A + 1));  // [NP]
+  float* Vs = Ks + NP * (A + 1);                    // [NP][A+1]   pass 2: dO (not with VG)
+  float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * (A + 1)));  // [NP]
   float4* rowg = rws + NP;                          // [NP] (d rhat_j, d w_j) row parts
   float* qrow = reinterpret_cast<float*>(rowg + NP);  // [AW][A]
   float* dorow = qrow + AW * A;                     // [AW][A]
@@ -654,7 +659,7 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
       Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
-      Vs[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
+      if (!VG) Vs[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
     }
     for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -674,13 +679,37 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
       }
       __syncwarp();
       float s[4] = {0.f, 0.f, 0.f, 0.f}, dp[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int f = 0; f < A; ++f) {
-        const float qf = q[f], gf = dq[f];
+      if (VG) {
+        for (int f = 0; f < A; ++f) {
+          const float qf = q[f];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) s[m] = fmaf(qf, Ks[(lane + 32 * m) * (A + 1) + f], s[m]);
+        }
+        // dp = dO_j . V_k: each lane walks its keys' rows of V (rows past nnei
+        // are never read)
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const int k = lane + 32 * m;
-          s[m] = fmaf(qf, Ks[k * (A + 1) + f], s[m]);
-          dp[m] = fmaf(gf, Vs[k * (A + 1) + f], dp[m]);
+          if (k < nn) {
+            const float4* v4 = reinterpret_cast<const float4*>(a.QKV + (base + k) * ld + 2 * A);
+            const float4* g4 = reinterpret_cast<const float4*>(dq);
+            float d = 0.f;
+            for (int f4 = 0; f4 < A / 4; ++f4) {
+              const float4 vv = v4[f4], gg = g4[f4];
+              d = fmaf(gg.x, vv.x, fmaf(gg.y, vv.y, fmaf(gg.z, vv.z, fmaf(gg.w, vv.w, d))));
+            }
+            dp[m] = d;
+          }
+        }
+      } else {
+        for (int f = 0; f < A; ++f) {
+          const float qf = q[f], gf = dq[f];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const int k = lane + 32 * m;
+            s[m] = fmaf(qf, Ks[k * (A + 1) + f], s[m]);
+            dp[m] = fmaf(gf, Vs[k * (A + 1) + f], dp[m]);
+          }
         }
       }
       const float4 rj = rws[j];
@@ -756,11 +785,11 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
       __syncwarp();
     }
     __syncthreads();
-    // pass 2: Q into Ks, dO into Vs
+    // pass 2: Q into Ks, dO into Vs (dO from global memory with VG)
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
       Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + f];
-      Vs[r * (A + 1) + f] = a.dO[(base + r) * A + f];
+      if (!VG) Vs[r * (A + 1) + f] = a.dO[(base + r) * A + f];
     }
     __syncthreads();
     for (int k = warp; k < NP; k += AW) {
@@ -781,10 +810,11 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
           const float d = __shfl_sync(0xffffffffu, dsv, t);
           const float p = __shfl_sync(0xffffffffu, pv, t);
           const int j = jb + t;
+          const float* doj = VG ? a.dO + (base + j) * A : Vs + j * (A + 1);
 #pragma unroll
           for (int m = 0; m < FQ; ++m) {
             dK[m] = fmaf(d, Ks[j * (A + 1) + lane + 32 * m], dK[m]);
-            dV[m] = fmaf(p, Vs[j * (A + 1) + lane + 32 * m], dV[m]);
+            dV[m] = fmaf(p, doj[lane + 32 * m], dV[m]);
           }
         }
       }
@@ -823,27 +853,40 @@ static int sm_count() {
   return count;
 }
 
+template <int A>
+static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
+  constexpr bool VG = A > 128;
+  const float scale = (float)(1.0 / sqrt((double)A));
+  // the adjoint's blocks each own a slot of the dS / P scratch
+  const int cap = bwd ? a.scratch_blocks : sm_count();
+  const int grid = a.n < cap ? a.n : cap;
+  if (!bwd) {
+    const size_t smem = sizeof(float) * (NP * (A + 1) + (VG ? 0 : NP * A) + 4 * NP + AW * A + AW * NP) +
+                        sizeof(double) * NP;
+    cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_attn_fwd_f32<A><<<grid, 32 * AW, smem, st>>>(a, scale);
+  } else {
+    const size_t smem = sizeof(float) * (NP * (A + 1) * (VG ? 1 : 2) + 8 * NP + 2 * AW * A + 2 * AW * NP +
+                                         3 * AW * NP) +
+                        sizeof(double) * NP;
+    cudaFuncSetAttribute(k_attn_bwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_attn_bwd_f32<A><<<grid, 32 * AW, smem, st>>>(a, scale);
+  }
+  note_launch();
+}
+
+// Attention widths with a kernel instance: 128 (the measured model) and 256
+// (the paper's own model size).
 void launch_attn_fwd_f32(const AttnArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
-  const float scale = (float)(1.0 / sqrt((double)a.A));
-  const int A = 128;
-  size_t smem = sizeof(float) * (NP * (A + 1) + NP * A + 4 * NP + AW * A + AW * NP) + sizeof(double) * NP;
-  cudaFuncSetAttribute(k_attn_fwd_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int grid = a.n < sm_count() ? a.n : sm_count();
-  k_attn_fwd_f32<128><<<grid, 32 * AW, smem, st>>>(a, scale);
-  note_launch();
+  if (a.A == 256) attn_f32_launch<256>(a, false, st);
+  else attn_f32_launch<128>(a, false, st);
 }
 
 void launch_attn_bwd_f32(const AttnArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
-  const float scale = (float)(1.0 / sqrt((double)a.A));
-  const int A = 128;
-  size_t smem = sizeof(float) * (2 * NP * (A + 1) + 8 * NP + 2 * AW * A + 2 * AW * NP + 3 * AW * NP) +
-                sizeof(double) * NP;
-  cudaFuncSetAttribute(k_attn_bwd_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int grid = a.n < a.scratch_blocks ? a.n : a.scratch_blocks;
-  k_attn_bwd_f32<128><<<grid, 32 * AW, smem, st>>>(a, scale);
-  note_launch();
+  if (a.A == 256) attn_f32_launch<256>(a, true, st);
+  else attn_f32_launch<128>(a, true, st);
 }
 
 // ------------------------------------------------------------- descriptor
