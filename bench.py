@@ -41,6 +41,25 @@ def workload(natoms):
     return f"solvated-protein-like periodic box, {natoms:,} atoms, jittered lattice at 0.1/A^3, seed 1"
 MODEL = ("DPA-1 se_atten: 5 types, tebd 8, rcut 6.0/0.5 A, sel 120, embed [25,50,100], axis 16, "
          "2 gated attention layers x 128, fitting [240,240,240]")
+# --model: the measured model (default) and the widened variants; weights are
+# seeded, as for the default
+MODELS = {
+    "dpa1": (MODEL, {}),
+    "paper-size": ("DPA-1 se_atten at the paper's size: 5 types, tebd 8, rcut 6.0/0.5 A, sel 120, embed [32,64,128], "
+                   "axis 16, 3 gated attention layers x 256, fitting [256,256,256] (FP32 path only)",
+                   dict(embed=(32, 64, 128), attn_layers=3, attn_dim=256, fitting=(256, 256, 256))),
+    "concat": ("DPA-1 se_atten, concat type embedding (embedding net input [s, T_j, T_i]); otherwise the default "
+               "model", dict(tebd_input_mode="concat")),
+}
+
+
+def model_cfg(name):
+    import dataclasses
+
+    import synth
+
+    desc, kw = MODELS[name]
+    return dataclasses.replace(synth.DEFAULT_CONFIG, **kw), desc
 
 
 def _args():
@@ -57,6 +76,7 @@ def _args():
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
     ap.add_argument("--md-steps", type=int, default=1000, help="graph-captured velocity-Verlet steps to time (0: skip)")
     ap.add_argument("--no-student", action="store_true", help="skip the distilled-student line")
+    ap.add_argument("--model", default="dpa1", choices=sorted(MODELS), help="dpa1: the measured model")
     return ap.parse_args()
 
 
@@ -95,7 +115,7 @@ def _system(natoms):
 
 # ----------------------------------------------------------------- oracle arm
 
-def _oracle_sample_rate(coord, atype, box, sample, seed=0):
+def _oracle_sample_rate(coord, atype, box, sample, seed=0, model="dpa1"):
     """Atom-steps/s of the FP64 oracle: energy and forces of ``sample``
     centres (their atomic energies and the gradient they contribute)."""
     import torch
@@ -103,7 +123,7 @@ def _oracle_sample_rate(coord, atype, box, sample, seed=0):
     import synth
     from oracle import OracleModel, energy_force_virial
 
-    cfg = synth.DEFAULT_CONFIG
+    cfg, _ = model_cfg(model)
     om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=0))
     rng = np.random.default_rng(seed)
     centres = np.sort(rng.choice(len(coord), size=min(sample, len(coord)), replace=False))
@@ -120,7 +140,7 @@ def run_reference(a):
     coord, atype, box = _system(a.natoms)
     vals = []
     for s in range(a.warmup + a.steps):
-        v, dt, cores = _oracle_sample_rate(coord, atype, box, a.ref_sample, seed=s)
+        v, dt, cores = _oracle_sample_rate(coord, atype, box, a.ref_sample, seed=s, model=a.model)
         if s >= a.warmup:
             vals.append((v, dt))
     rate = len(vals) * a.ref_sample / sum(dt for _, dt in vals)
@@ -129,7 +149,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "atom-steps/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(dt for _, dt in vals) / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload(a.natoms), "model": MODEL, "natoms": a.natoms},
+        "config": {"workload": workload(a.natoms), "model": model_cfg(a.model)[1], "natoms": a.natoms},
         "cpu_baseline": {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -310,7 +330,7 @@ def run_ours(a):
         tdist.init_process_group(backend="nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = synth.DEFAULT_CONFIG
+    cfg, model_desc = model_cfg(a.model)
     wpath = os.path.join(tempfile.mkdtemp(prefix=f"dpa1b{rank}_"), "w.bin")
     synth.write_weights(wpath, cfg, synth.make_weights(cfg, seed=0))
     coord, atype, box = _system(a.natoms)
@@ -471,7 +491,7 @@ def run_ours(a):
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
     cpu = None
     if not a.no_cpu_baseline and ws == 1:
-        v, dt, cores = _oracle_sample_rate(coord, atype, box, a.cpu_sample)
+        v, dt, cores = _oracle_sample_rate(coord, atype, box, a.cpu_sample, model=a.model)
         cpu = {"value": v, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{a.cpu_sample} random centres of the {n}-atom box (E, e_i and their force terms), {dt:.1f} s"}
     h2d = n * 3 * 8 + n * 4 + 9 * 8
@@ -480,7 +500,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp16x": "f16", "bf16": "bf16", "fp32": "f32"}[head], "data": "synthetic",
-        "config": {"workload": workload(n), "model": MODEL, "natoms": n, "global_batch": ws * n,
+        "config": {"workload": workload(n), "model": model_desc, "natoms": n, "global_batch": ws * n,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "per-step working set is several GB of intermediates, far above the 129 MB L2",
                    "arithmetic": {"fp16x": "attention layers on tcgen05: FP16 operands, two-term splits of G, P, V; "
