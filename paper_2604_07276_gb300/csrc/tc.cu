@@ -891,9 +891,10 @@ constexpr int EMB_MAXT = 8;                           // atom types the staged t
 constexpr int EMB_GT = EMB_MAXT * EMB_E2 * 4;         // this atom's rows of the type-pair table
 constexpr int EMB_B0 = EMB_MAXT * EMB_E0 * 4;         // concat mode: this atom's rows of the first-layer bias table
 constexpr int EMBF_B0 = EMB_WIMG + 4 * EMB_TA + EMB_GT;             // forward: bias rows after the type-pair rows
-constexpr int EMBB_B0 = EMB_WIMG + 4 * EMB_TA + EMB_GT + 512;       // adjoint: after them and the dE/dx exchange
 constexpr int EMBF_SMEM = EMBF_B0 + EMB_B0 + 64;
-constexpr int EMBB_SMEM = EMBB_B0 + EMB_B0 + 64;  // dZ3 tiles reuse the four activation tiles
+// the adjoint reads layers 1 and 2 as stored (no bias rows); its dZ3 tiles
+// reuse the four activation tiles
+constexpr int EMBB_SMEM = EMB_WIMG + 4 * EMB_TA + EMB_GT + 512 + 64;
 static_assert(2 * EMB_TD == 4 * EMB_TA, "the dZ3 hi / lo tiles fill the activation tiles");
 
 struct EmbedTcArgs {
@@ -907,6 +908,8 @@ struct EmbedTcArgs {
   float* dR;              // bwd: dR[:,0] +=
   const float* b0t;       // concat type-embedding mode: first-layer bias per (centre,
                           // neighbour) type [ntypes][ntypes][E0]; null: b0 below
+  float* H12;             // [atom][E0 + E1 units][NP rows]: layers 1 and 2 of the net,
+                          // written by the forward, read by the adjoint
   const uint4* wimg;      // W1/W2 hi/lo tiles
   int n, ntypes;
   int* err;
@@ -1026,6 +1029,44 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
   sy.wait();
 }
 
+// The adjoint's front: layers 1 and 2 as the forward stored them (all 25
+// layer-1 units, the owned layer-2 units), the H2 tiles, and the issue of
+// Z3 = H2 W2; returns once Z3 is in TMEM columns [64, 176).
+template <int H, class BeforeZ3>
+__device__ __forceinline__ void embed_bwd_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, Sync& sy, int row,
+                                                int atom, float* h1, float* h2, BeforeZ3 before_z3) {
+  using O = EmbOwn<H>;
+  uint8_t* sW2h = sm + 2 * EMB_T1;
+  uint8_t* sW2l = sW2h + EMB_T2;
+  uint8_t* sH2h = sm + EMB_WIMG + 2 * EMB_TA;
+  uint8_t* sH2l = sH2h + EMB_TA;
+  const bool issuer = threadIdx.x == 0;
+  const float* hs = a.H12 + (size_t)atom * (EMB_E0 + EMB_E1) * NP + row;
+#pragma unroll
+  for (int p = 0; p < EMB_E0; ++p) h1[p] = hs[p * NP];
+#pragma unroll
+  for (int i = 0; i < O::nb; ++i) h2[i] = hs[(EMB_E0 + O::b0 + i) * NP];
+  constexpr int g_lo = O::b0 / 8, g_hi = H == 0 ? EMB_SPLIT / 8 : 7;  // 8-column groups stored
+#pragma unroll
+  for (int g = g_lo; g < g_hi; ++g) {
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int b = 8 * g + i;
+      v[i] = b < EMB_E1 ? h2[b - O::b0] : 0.f;
+    }
+    emb_store8(sH2h, row, 8 * g, 128, v, false);
+    emb_store8(sH2l, row, 8 * g, 128, v, true);
+  }
+  handoff();
+  if (issuer) {
+    mma_split(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
+    mma_commit(sy.bar);
+  }
+  before_z3();
+  sy.wait();
+}
+
 // A row's inputs of the embedding net (s of the neighbour, its type), read
 // for the next atom while the current one is processed: the neighbour
 // count, s and the neighbour index at its start, the type at its end.
@@ -1065,15 +1106,15 @@ __device__ __forceinline__ void embed_tc_setup(const EmbedTcArgs& a, uint8_t* sm
 }
 
 // Per atom: copy the centre type's rows of the type-pair table Gt[t_i][*]
-// (and, in concat mode, of the first-layer bias table) to shared memory,
-// read by neighbour type afterwards, and bring the next atom's per-row inputs
-// into L2.
+// (and, in concat mode and given s_b0, of the first-layer bias table) to
+// shared memory, read by neighbour type afterwards, and bring the next atom's
+// per-row inputs into L2.
 __device__ __forceinline__ void embed_tc_atom_start(const EmbedTcArgs& a, float* s_gt, float* s_b0, int atom,
                                                     bool bwd) {
   const float4* src = reinterpret_cast<const float4*>(a.Gt + (size_t)a.atype[atom] * a.ntypes * EMB_E2);
   float4* dst = reinterpret_cast<float4*>(s_gt);
   for (int i = threadIdx.x; i < a.ntypes * EMB_E2 / 4; i += blockDim.x) dst[i] = src[i];
-  if (a.b0t) {  // read by layer 1 right away: a barrier of its own
+  if (a.b0t && s_b0) {  // read by layer 1 right away: a barrier of its own
     const float* b0 = a.b0t + (size_t)a.atype[atom] * a.ntypes * EMB_E0;
     for (int i = threadIdx.x; i < a.ntypes * EMB_E0; i += blockDim.x) s_b0[i] = b0[i];
     __syncthreads();
@@ -1083,7 +1124,10 @@ __device__ __forceinline__ void embed_tc_atom_start(const EmbedTcArgs& a, float*
     const size_t base = (size_t)next * NP;
     prefetch_l2(a.R + base * 4, NP * 4 * sizeof(float));
     prefetch_l2(a.nlist + base, NP * sizeof(int));
-    if (bwd) prefetch_l2(a.dG0 + base * EMB_E2, NP * EMB_E2 * sizeof(float));
+    if (bwd) {
+      prefetch_l2(a.dG0 + base * EMB_E2, NP * EMB_E2 * sizeof(float));
+      prefetch_l2(a.H12 + base * (EMB_E0 + EMB_E1), NP * (EMB_E0 + EMB_E1) * sizeof(float));
+    }
   }
 }
 
@@ -1146,6 +1190,20 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_co
       embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
     else
       embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
+    {  // layers 1 and 2 for the adjoint: this half's layer-1 units, its layer-2 units
+      float* hs = a.H12 + (size_t)atom * (EMB_E0 + EMB_E1) * NP + row;
+      if (half == 0) {
+#pragma unroll
+        for (int p = 0; p < 16; ++p) hs[p * NP] = h1[p];
+#pragma unroll
+        for (int i = 0; i < EMB_SPLIT; ++i) hs[(EMB_E0 + i) * NP] = h2[i];
+      } else {
+#pragma unroll
+        for (int p = 16; p < EMB_E0; ++p) hs[p * NP] = h1[p];
+#pragma unroll
+        for (int i = 0; i < EMB_E1 - EMB_SPLIT; ++i) hs[(EMB_E0 + EMB_SPLIT + i) * NP] = h2[i];
+      }
+    }
     float* out = a.G0 + (size_t)atom * NP * EMB_E2;
     if (half == 0)
       embed_fwd_out<0>(a, tm + lane_off, s_gt + tj * EMB_E2, h2, rv, out, row);
@@ -1292,8 +1350,8 @@ __device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, c
 
 template <int H>
 __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
-                                               Sync& sy, int row, bool rv, size_t rowg, float x, const float* b0row,
-                                               const float* gt, const float4* dg, float* xch) {
+                                               Sync& sy, int row, bool rv, size_t rowg, const float* gt,
+                                               const float4* dg, float* xch) {
   using O = EmbOwn<H>;
   const bool issuer = threadIdx.x == 0;
   uint8_t* sW1h = sm;
@@ -1308,7 +1366,7 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
   float h1[EMB_E0], h2[O::nb];
   float4 d0[4];
-  embed_tc_front<H>(a, sm, tm, lane_off, sy, row, rv, x, b0row, h1, h2, [&] {
+  embed_bwd_front<H>(a, sm, tm, sy, row, (int)(rowg / NP), h1, h2, [&] {
     embed_bwd_load16<H>(dg, 0, row, rv, d0);
     embed_bwd_prefetch16<H>(dg, 1, row, rv);
   });
@@ -1359,7 +1417,6 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_co
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   float* s_gt = reinterpret_cast<float*>(sm + EMB_WIMG + 4 * EMB_TA);
   float* xch = s_gt + EMB_MAXT * EMB_E2;  // [128] half 1's part of dE/dx
-  float* s_b0 = reinterpret_cast<float*>(sm + EMBB_B0);
   Sync sy{bar, 0u, a.err};
   if (threadIdx.x == 0 && blockIdx.x < a.n)
     prefetch_l2(a.dG0 + (size_t)blockIdx.x * NP * EMB_E2, NP * EMB_E2 * sizeof(float));
@@ -1378,13 +1435,12 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_co
     }
     const bool rv = row < nn;
     const size_t rowg = (size_t)atom * NP + row;
-    embed_tc_atom_start(a, s_gt, s_b0, atom, true);  // visible after the front's barriers
+    embed_tc_atom_start(a, s_gt, nullptr, atom, true);  // visible after the front's barriers
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
-    const float* b0row = a.b0t ? s_b0 + tj * EMB_E0 : nullptr;
     if (half == 0)
-      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, b0row, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
     else
-      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.x, b0row, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
     in.type(a, row);
     fence_before_sync();
     __syncthreads();
@@ -1568,6 +1624,8 @@ void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
   ws.tc.p[2] = nullptr;
   // row-major staging of G0 / dE/dG0 for the SIMT embedding net (nets other than 25-50-100)
   ws.tc.p[3] = m->tcw.emb_W1_t ? nullptr : a.take<float>(rows * m->m1);
+  // layers 1 and 2 of the tensor-core embedding net, for its adjoint
+  ws.tc.p[5] = m->tcw.emb_W1_t ? a.take<float>(rows * (EMB_E0 + EMB_E1)) : nullptr;
 }
 
 
@@ -1613,6 +1671,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     et.R = ws.R; et.nlist = ws.nlist; et.nnei = ws.nnei; et.atype = atype; et.Gt = m->Gt; et.G0 = ws.G[0];
     et.dG0 = ws.dG; et.dR = ws.dR; et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W1_t);
     et.n = n; et.ntypes = m->nt; et.err = m->d_err; et.b0t = m->b0t;
+    et.H12 = reinterpret_cast<float*>(ws.tc.p[5]);
     memcpy(et.W0, m->tcw.emb_vec.W0, sizeof(et.W0));
     memcpy(et.b0, m->tcw.emb_vec.b0, sizeof(et.b0));
     memcpy(et.b1, m->tcw.emb_vec.b1, sizeof(et.b1));
