@@ -77,6 +77,7 @@ def _args():
     ap.add_argument("--md-steps", type=int, default=1000, help="graph-captured velocity-Verlet steps to time (0: skip)")
     ap.add_argument("--no-student", action="store_true", help="skip the distilled-student line")
     ap.add_argument("--model", default="dpa1", choices=sorted(MODELS), help="dpa1: the measured model")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-frame dp_compute_batch line")
     return ap.parse_args()
 
 
@@ -442,6 +443,22 @@ def run_ours(a):
                    "status": md_status,
                    "note": "random weights have no short-range repulsion; long runs collapse atoms"}
 
+    batch = None
+    if rank == 0 and not a.no_batch:
+        # 32 independent frames of U{200..3000} atoms through dp_compute_batch
+        # (host arrays, copies included), as a user of the batch call sees it
+        frames = synth.frame_batch(seed=2, nframes=32)
+        mb = models[head]
+        mb.compute_batch(frames)
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mb.compute_batch(frames)
+        dtb = (time.perf_counter() - t0) / reps
+        natb = sum(len(t) for _, t, _ in frames)
+        batch = {"frames": len(frames), "atoms": natb, "precision": head, "ms_per_batch": 1e3 * dtb,
+                 "frames_per_s": len(frames) / dtb, "atom_steps_per_s": natb / dtb,
+                 "api": "dp_compute_batch, host arrays (copies included)"}
     student = None
     if not a.no_student:
         student = _student_line(dev, coord, atype, box,
@@ -521,6 +538,7 @@ def run_ours(a):
         "device_memory_bytes": mem_used,
         "md": md_line,
         "student": student,
+        "batch": batch,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

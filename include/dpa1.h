@@ -115,7 +115,13 @@ DP_API int dp_compute_device_local(dp_model* m, int natoms, int nlocal, const do
 
 /* Several independent frames of uneven size from HOST arrays.  Frame f owns
  * atoms [atom_offsets[f], atom_offsets[f+1]) of coord / atype / force and
- * box[9f .. 9f+8], energy[f], virial[9f .. 9f+8].  Frames never interact. */
+ * box[9f .. 9f+8], energy[f], virial[9f .. 9f+8].  Frames never interact.
+ * Every frame's arguments are checked before any frame runs (DP_ERR_ARG /
+ * DP_ERR_BOX / DP_ERR_NAN name the first bad one); the batch is then copied
+ * to the device once, its frames run back to back on the model's stream and
+ * the results come back once.  A device-side error in any frame is returned
+ * for the batch.  The library keeps a device buffer for the largest batch
+ * seen until dp_free. */
 DP_API int dp_compute_batch(dp_model* m, int nframes, const int* atom_offsets, const double* coord,
                      const double* box, const int* atype, double* energy, double* force,
                      double* virial);

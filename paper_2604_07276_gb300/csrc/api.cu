@@ -817,14 +817,63 @@ int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coo
                      const int* atype, double* energy, double* force, double* virial) {
   if (check_model(m)) return DP_ERR_ARG;
   if (nframes < 0 || (nframes > 0 && (!off || !box || !energy || !virial))) return fail(DP_ERR_ARG, "bad batch arguments");
+  if (nframes == 0) return DP_OK;
+  // every frame is checked on the host before any of them runs
+  int maxn = 0;
   for (int f = 0; f < nframes; ++f) {
     const int n = off[f + 1] - off[f];
     if (n < 0) return fail(DP_ERR_ARG, "atom_offsets must be non-decreasing");
-    int rc = dp_compute(m, n, coord + 3LL * off[f], box + 9LL * f, atype + off[f], energy + f, force + 3LL * off[f],
-                        virial + 9LL * f, nullptr);
+    maxn = std::max(maxn, n);
+    int rc = check_box_host(box + 9LL * f, m->rcut);
     if (rc != DP_OK) return rc;
   }
-  return DP_OK;
+  const long long a0 = off[0], total = (long long)off[nframes] - a0;
+  if (total > 0 && (!coord || !atype || !force)) return fail(DP_ERR_ARG, "null host pointer");
+  for (long long i = 0; i < total; ++i)
+    if (atype[a0 + i] < 0 || atype[a0 + i] >= m->nt) return fail(DP_ERR_ARG, "atom type out of range");
+  for (long long i = 0; i < 3 * total; ++i)
+    if (!std::isfinite(coord[3 * a0 + i])) return fail(DP_ERR_NAN, "non-finite coordinate");
+  CUDA_TRY(cudaSetDevice(m->device));
+  int rc;
+  if (maxn > m->ws.cap && (rc = dp_reserve(m, maxn)) != DP_OK) return rc;
+  // one upload of the whole batch, the frames back to back on the model's
+  // stream (sharing the workspace in stream order), one download
+  auto up16 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_coord = up16(sizeof(double) * 3 * total), b_force = b_coord, b_type = up16(sizeof(int) * total),
+               b_box = up16(sizeof(double) * 9 * nframes), b_e = up16(sizeof(double) * nframes), b_vir = b_box;
+  const size_t need = b_coord + b_force + b_type + b_box + b_e + b_vir;
+  if (need > m->batch_cap) {
+    if (m->batch_buf) CUDA_TRY(cudaFree(m->batch_buf));
+    m->batch_buf = nullptr;
+    m->batch_cap = 0;
+    if (cudaMalloc(&m->batch_buf, need) != cudaSuccess) return fail(DP_ERR_CUDA, "cudaMalloc of the batch buffer failed");
+    m->batch_cap = need;
+  }
+  char* p = reinterpret_cast<char*>(m->batch_buf);
+  double* d_coord = reinterpret_cast<double*>(p);
+  double* d_force = reinterpret_cast<double*>(p += b_coord);
+  int* d_type = reinterpret_cast<int*>(p += b_force);
+  double* d_box = reinterpret_cast<double*>(p += b_type);
+  double* d_e = reinterpret_cast<double*>(p += b_box);
+  double* d_vir = reinterpret_cast<double*>(p += b_e);
+  cudaStream_t st = m->stream;
+  if (total > 0) {
+    CUDA_TRY(cudaMemcpyAsync(d_coord, coord + 3 * a0, sizeof(double) * 3 * total, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_type, atype + a0, sizeof(int) * total, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_box, box, sizeof(double) * 9 * nframes, cudaMemcpyHostToDevice, st));
+  for (int f = 0; f < nframes; ++f) {
+    const int n = off[f + 1] - off[f];
+    const long long o = off[f] - a0;
+    rc = run_device(m, n, n, d_coord + 3 * o, d_box + 9LL * f, d_type + o, d_e + f, d_force + 3 * o, d_vir + 9LL * f,
+                    nullptr, st);
+    if (rc != DP_OK) return rc;
+  }
+  CUDA_TRY(cudaMemcpyAsync(energy, d_e, sizeof(double) * nframes, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(virial, d_vir, sizeof(double) * 9 * nframes, cudaMemcpyDeviceToHost, st));
+  if (total > 0) CUDA_TRY(cudaMemcpyAsync(force + 3 * a0, d_force, sizeof(double) * 3 * total, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return read_status(m);
 }
 
 int dp_get_status(dp_model* m) {
@@ -1158,6 +1207,7 @@ void dp_free(dp_model* m) {
   if (m->md_exec) cudaGraphExecDestroy(m->md_exec);
   if (m->md_graph) cudaGraphDestroy(m->md_graph);
   if (m->d_md_counter) cudaFree(m->d_md_counter);
+  if (m->batch_buf) cudaFree(m->batch_buf);
   if (m->t_buf) cudaFree(m->t_buf);
   delete m;
 }

@@ -143,6 +143,9 @@ struct dp_model {
   dpa1::Profiler prof;
   // velocity-Verlet: step counter and the cached graph of one step
   int* d_md_counter = nullptr;
+  // dp_compute_batch: device copies of a batch's inputs and results, grown on demand
+  void* batch_buf = nullptr;
+  size_t batch_cap = 0;
   cudaGraphExec_t md_exec = nullptr;
   cudaGraph_t md_graph = nullptr;
   std::vector<const void*> md_key;
