@@ -118,10 +118,16 @@ DP_API int dp_compute_device_local(dp_model* m, int natoms, int nlocal, const do
  * box[9f .. 9f+8], energy[f], virial[9f .. 9f+8].  Frames never interact.
  * Every frame's arguments are checked before any frame runs (DP_ERR_ARG /
  * DP_ERR_BOX / DP_ERR_NAN name the first bad one); the batch is then copied
- * to the device once, its frames run back to back on the model's stream and
- * the results come back once.  A device-side error in any frame is returned
- * for the batch.  The library keeps a device buffer for the largest batch
- * seen until dp_free. */
+ * to the device once and evaluated in packed passes: each frame's neighbour
+ * list is built in its own box, and every later stage runs once over all the
+ * frames of a pass (frames are padded to multiples of 4 atoms, so that each
+ * frame's energy, forces and virial are bitwise those of a call on that frame
+ * alone).  A pass holds as many atoms as the workspace; the call grows the
+ * workspace to min(padded atoms, 65,536) atoms, at least the largest frame,
+ * and runs a larger batch as several passes of consecutive frames.  The
+ * results come back once.  A device-side error in any frame is returned for
+ * the batch.  The library keeps a device buffer for the largest batch seen
+ * until dp_free. */
 DP_API int dp_compute_batch(dp_model* m, int nframes, const int* atom_offsets, const double* coord,
                      const double* box, const int* atype, double* energy, double* force,
                      double* virial);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <climits>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -18,6 +19,10 @@
 using namespace dpa1;
 
 namespace {
+
+// dp_compute_batch packs its frames into passes of up to this many atom slots
+// (more when the workspace already holds more)
+constexpr long long BATCH_PACK_ATOMS = 65536;
 
 thread_local std::string g_last_error;
 
@@ -329,17 +334,50 @@ int translate_err(int bits) {
 }
 
 // Stages a1-a2 on the stream.
-void run_neighbors(dp_model* m, int n, const double* coord, const double* box, const int* atype, cudaStream_t st) {
+// Neighbour-stage arguments for n atoms at coord, with the list, counts,
+// clamped types and FP32 coordinates written from workspace slot rel on.
+NbrArgs nbr_args(dp_model* m, int n, const double* coord, const double* box, const int* atype, CellGrid* grid,
+                 int rel) {
   Workspace& ws = m->ws;
   NbrArgs a;
   a.coord = coord; a.box = box; a.atype = atype;
   a.n = n; a.ntypes = m->nt; a.sel = m->sel; a.rcut = m->rcut;
-  a.cap_dim = ws.cap_dim; a.cell_cap = ws.cell_cap; a.grid = ws.grid;
+  a.cap_dim = ws.cap_dim; a.cell_cap = ws.cell_cap; a.grid = grid;
   a.cell_of = ws.cell_of; a.cell_count = ws.cell_count; a.cell_start = ws.cell_start;
   a.cell_cursor = ws.cell_cursor; a.cell_atoms = ws.cell_atoms;
-  a.nlist = ws.nlist; a.nnei = ws.nnei; a.ncand = ws.ncand; a.atype_c = ws.atype_c; a.coordf = ws.coordf;
+  a.nlist = ws.nlist + (size_t)rel * NP; a.nnei = ws.nnei + rel; a.ncand = ws.ncand + rel;
+  a.atype_c = ws.atype_c + rel; a.coordf = ws.coordf + rel;
   a.err = m->d_err;
-  launch_neighbors(a, st);
+  return a;
+}
+
+void run_neighbors(dp_model* m, int n, const double* coord, const double* box, const int* atype, cudaStream_t st) {
+  launch_neighbors(nbr_args(m, n, coord, box, atype, m->ws.grid, 0), st);
+}
+
+// Gathers a batch from the caller's layout (frames back to back) into the
+// slots of the packed layout, pos[i] being atom i's slot, and scatters the
+// forces back.
+__global__ void k_batch_pack(const double* __restrict__ coord, const int* __restrict__ atype,
+                             const int* __restrict__ pos, long long total, double* __restrict__ coordP,
+                             int* __restrict__ typeP) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const long long q = pos[i];
+  coordP[3 * q] = coord[3 * i];
+  coordP[3 * q + 1] = coord[3 * i + 1];
+  coordP[3 * q + 2] = coord[3 * i + 2];
+  typeP[q] = atype[i];
+}
+
+__global__ void k_batch_unpack(const double* __restrict__ forceP, const int* __restrict__ pos, long long total,
+                               double* __restrict__ force) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const long long q = pos[i];
+  force[3 * i] = forceP[3 * q];
+  force[3 * i + 1] = forceP[3 * q + 1];
+  force[3 * i + 2] = forceP[3 * q + 2];
 }
 
 }  // namespace
@@ -464,20 +502,18 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   prof_mark(m, "embed_bwd", st);
 }
 
-int run_device(dp_model* m, int n, int nlocal, const double* coord, const double* box, const int* atype, double* energy,
-               double* force, double* virial, double* atom_energy, cudaStream_t st) {
+// Stages a3-a15 on n atoms whose neighbour list is built.  grid is the cell
+// grid of the box (frame non-null: grid[frame[i]] is atom i's box, a packed
+// batch); force holds n atoms, energy and virial one frame (seg null) or the
+// nseg frames of a packed batch.
+int run_after_neighbors(dp_model* m, int n, const double* coord, const CellGrid* grid, const int* frame,
+                        const int* seg, int nseg, double* energy, double* force, double* virial,
+                        double* atom_energy, cudaStream_t st) {
   Workspace& ws = m->ws;
-  if (n > ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
-  m->last_stream = st;
-  m->last_natoms = n;
-  m->call_nlocal = nlocal;
-  prof_mark(m, "start", st);
-  run_neighbors(m, n, coord, box, atype, st);
-  prof_mark(m, "neighbors", st);
-  atype = ws.atype_c;  // every later stage reads the range-checked types
+  const int* atype = ws.atype_c;  // every later stage reads the range-checked types
   // a3: environment matrix
   EnvArgs ea{};
-  ea.coord = coord; ea.atype = atype; ea.grid = ws.grid; ea.nlist = ws.nlist; ea.n = n;
+  ea.coord = coord; ea.atype = atype; ea.grid = grid; ea.frame = frame; ea.nlist = ws.nlist; ea.n = n;
   ea.davg = m->davg; ea.dstd = m->dstd; ea.rcs = (float)m->rcs; ea.rc = (float)m->rcut;
   ea.R = ws.R; ea.rw = ws.rw; ea.rv = ws.rv;
   // the FP32 path evaluates R in FP64 and keeps w in FP64 for its smooth logits
@@ -491,7 +527,7 @@ int run_device(dp_model* m, int n, int nlocal, const double* coord, const double
     run_network_f32(m, n, atype, st);
   // a14: per-pair gradient
   EnvBwdArgs eb{};
-  eb.coord = coord; eb.grid = ws.grid; eb.fp64 = m->precision == DP_PREC_FP32 ? 1 : 0;
+  eb.coord = coord; eb.grid = grid; eb.frame = frame; eb.fp64 = m->precision == DP_PREC_FP32 ? 1 : 0;
   eb.rv = ws.rv; eb.nlist = ws.nlist; eb.atype = atype; eb.n = n; eb.dstd = m->dstd;
   eb.rcs = (float)m->rcs; eb.rc = (float)m->rcut; eb.dR = ws.dR; eb.dgeo = ws.dgeo; eb.g = ws.g;
   launch_env_bwd(eb, st);
@@ -500,13 +536,27 @@ int run_device(dp_model* m, int n, int nlocal, const double* coord, const double
   launch_reverse(ws.nlist, n, ws.rev_cnt, ws.rev_rows, m->d_err, st);
   ForceArgs fa{};
   fa.g = ws.g; fa.rv = ws.rv; fa.nnei = ws.nnei; fa.rev_cnt = ws.rev_cnt; fa.rev_rows = ws.rev_rows; fa.e = ws.e;
-  fa.n = n; fa.nlocal = nlocal; fa.force = force; fa.atom_energy = atom_energy; fa.partials = ws.partials; fa.energy = energy;
-  fa.virial = virial; fa.err = m->d_err;
+  fa.n = n; fa.nlocal = m->call_nlocal; fa.force = force; fa.atom_energy = atom_energy; fa.partials = ws.partials;
+  fa.energy = energy; fa.virial = virial; fa.err = m->d_err;
+  fa.frame = frame; fa.seg = seg; fa.nseg = nseg;
   launch_force_virial(fa, st);
   prof_mark(m, "force_virial", st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
   return DP_OK;
+}
+
+int run_device(dp_model* m, int n, int nlocal, const double* coord, const double* box, const int* atype, double* energy,
+               double* force, double* virial, double* atom_energy, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  if (n > ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
+  m->last_stream = st;
+  m->last_natoms = n;
+  m->call_nlocal = nlocal;
+  prof_mark(m, "start", st);
+  run_neighbors(m, n, coord, box, atype, st);
+  prof_mark(m, "neighbors", st);
+  return run_after_neighbors(m, n, coord, ws.grid, nullptr, nullptr, 0, energy, force, virial, atom_energy, st);
 }
 
 int read_status(dp_model* m) {
@@ -834,41 +884,109 @@ int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coo
   for (long long i = 0; i < 3 * total; ++i)
     if (!std::isfinite(coord[3 * a0 + i])) return fail(DP_ERR_NAN, "non-finite coordinate");
   CUDA_TRY(cudaSetDevice(m->device));
+  // The packed layout: frame f at slots [po[f], po[f+1]), its atom count
+  // rounded up to whole force blocks, so that no block of the force kernel
+  // holds atoms of two frames and every frame's sums run in the order of a
+  // call on that frame alone.
+  constexpr int PB = FORCE_BLOCK_ATOMS;
+  auto padded = [](long long n) { return (n + PB - 1) / PB * PB; };
+  std::vector<long long> po(nframes + 1, 0);
+  for (int f = 0; f < nframes; ++f) po[f + 1] = po[f] + padded(off[f + 1] - off[f]);
+  const long long P = po[nframes];
+  if (P > (long long)INT_MAX) return fail(DP_ERR_CAPACITY, "batch too large");
+  // One packed pass holds up to the workspace's atoms; the workspace grows to
+  // min(P, BATCH_PACK_ATOMS) slots (at least the largest frame), and a larger
+  // batch runs as several passes of consecutive frames.
+  const long long want = std::max(padded(maxn), std::min(P, (long long)BATCH_PACK_ATOMS));
   int rc;
-  if (maxn > m->ws.cap && (rc = dp_reserve(m, maxn)) != DP_OK) return rc;
-  // one upload of the whole batch, the frames back to back on the model's
-  // stream (sharing the workspace in stream order), one download
-  auto up16 = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t b_coord = up16(sizeof(double) * 3 * total), b_force = b_coord, b_type = up16(sizeof(int) * total),
-               b_box = up16(sizeof(double) * 9 * nframes), b_e = up16(sizeof(double) * nframes), b_vir = b_box;
-  const size_t need = b_coord + b_force + b_type + b_box + b_e + b_vir;
+  if (want > m->ws.cap && (rc = dp_reserve(m, (int)want)) != DP_OK) {
+    if (want == padded(maxn) || (rc = dp_reserve(m, (int)padded(maxn))) != DP_OK) return rc;
+  }
+  const long long cap = m->ws.cap;
+  // host-side maps: pos[i] = the slot of atom i, frame of each slot (-1:
+  // padding), and the first force block of each frame
+  std::vector<int> pos((size_t)total), frame_of((size_t)P, -1), seg(nframes + 1);
+  for (int f = 0; f < nframes; ++f) {
+    const long long o = off[f] - a0;
+    for (long long k = 0; k < off[f + 1] - off[f]; ++k) {
+      pos[(size_t)(o + k)] = (int)(po[f] + k);
+      frame_of[(size_t)(po[f] + k)] = f;
+    }
+  }
+  for (int f = 0; f <= nframes; ++f) seg[f] = (int)(po[f] / PB);
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_coord = up(sizeof(double) * 3 * total), b_type = up(sizeof(int) * total),
+               b_box = up(sizeof(double) * 9 * nframes), b_e = up(sizeof(double) * nframes),
+               b_coordP = up(sizeof(double) * 3 * P), b_typeP = up(sizeof(int) * P),
+               b_grid = up(sizeof(CellGrid) * nframes), b_seg = up(sizeof(int) * (nframes + 1));
+  const size_t need = 2 * b_coord + 2 * b_type + 2 * b_box + b_e + 2 * b_coordP + 2 * b_typeP + b_grid + b_seg;
   if (need > m->batch_cap) {
     if (m->batch_buf) CUDA_TRY(cudaFree(m->batch_buf));
     m->batch_buf = nullptr;
     m->batch_cap = 0;
-    if (cudaMalloc(&m->batch_buf, need) != cudaSuccess) return fail(DP_ERR_CUDA, "cudaMalloc of the batch buffer failed");
+    if (cudaMalloc(&m->batch_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DP_ERR_CUDA, "cudaMalloc of the batch buffer failed");
+    }
     m->batch_cap = need;
   }
   char* p = reinterpret_cast<char*>(m->batch_buf);
-  double* d_coord = reinterpret_cast<double*>(p);
-  double* d_force = reinterpret_cast<double*>(p += b_coord);
-  int* d_type = reinterpret_cast<int*>(p += b_force);
-  double* d_box = reinterpret_cast<double*>(p += b_type);
-  double* d_e = reinterpret_cast<double*>(p += b_box);
-  double* d_vir = reinterpret_cast<double*>(p += b_e);
+  auto take = [&p](size_t b) { char* q = p; p += b; return q; };
+  double* d_coord = reinterpret_cast<double*>(take(b_coord));
+  double* d_force = reinterpret_cast<double*>(take(b_coord));
+  int* d_type = reinterpret_cast<int*>(take(b_type));
+  int* d_pos = reinterpret_cast<int*>(take(b_type));
+  double* d_box = reinterpret_cast<double*>(take(b_box));
+  double* d_vir = reinterpret_cast<double*>(take(b_box));
+  double* d_e = reinterpret_cast<double*>(take(b_e));
+  double* d_coordP = reinterpret_cast<double*>(take(b_coordP));
+  double* d_forceP = reinterpret_cast<double*>(take(b_coordP));
+  int* d_typeP = reinterpret_cast<int*>(take(b_typeP));
+  int* d_frame = reinterpret_cast<int*>(take(b_typeP));
+  CellGrid* d_grid = reinterpret_cast<CellGrid*>(take(b_grid));
+  int* d_seg = reinterpret_cast<int*>(take(b_seg));
   cudaStream_t st = m->stream;
+  Workspace& ws = m->ws;
   if (total > 0) {
     CUDA_TRY(cudaMemcpyAsync(d_coord, coord + 3 * a0, sizeof(double) * 3 * total, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(d_type, atype + a0, sizeof(int) * total, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_pos, pos.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st));
+    k_batch_pack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d_coord, d_type, d_pos, total, d_coordP, d_typeP);
+    note_launch();
   }
+  if (P > 0) CUDA_TRY(cudaMemcpyAsync(d_frame, frame_of.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(d_seg, seg.data(), sizeof(int) * (nframes + 1), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(d_box, box, sizeof(double) * 9 * nframes, cudaMemcpyHostToDevice, st));
-  for (int f = 0; f < nframes; ++f) {
-    const int n = off[f + 1] - off[f];
-    const long long o = off[f] - a0;
-    rc = run_device(m, n, n, d_coord + 3 * o, d_box + 9LL * f, d_type + o, d_e + f, d_force + 3 * o, d_vir + 9LL * f,
-                    nullptr, st);
+  for (int f0 = 0; f0 < nframes;) {
+    int f1 = f0 + 1;
+    while (f1 < nframes && po[f1 + 1] - po[f0] <= cap) ++f1;
+    const long long P0 = po[f0];
+    const int Pc = (int)(po[f1] - P0);
+    m->last_stream = st;
+    m->last_natoms = Pc;
+    m->call_nlocal = Pc;  // every slot counts; padding is masked by its frame of -1
+    prof_mark(m, "start", st);
+    // a1-a2 per frame (each has its own box and cell grid), written into
+    // the pass's slots with indices relative to the pass
+    for (int f = f0; f < f1; ++f) {
+      const int rel = (int)(po[f] - P0);
+      NbrArgs a = nbr_args(m, off[f + 1] - off[f], d_coordP + 3 * po[f], d_box + 9LL * f, d_typeP + po[f], d_grid + f,
+                           rel);
+      a.n_out = (int)(po[f + 1] - po[f]);
+      a.base = rel;
+      launch_neighbors(a, st);
+    }
+    prof_mark(m, "neighbors", st);
+    rc = run_after_neighbors(m, Pc, d_coordP + 3 * P0, d_grid, d_frame + P0, d_seg + f0, f1 - f0, d_e + f0,
+                             d_forceP + 3 * P0, d_vir + 9LL * f0, nullptr, st);
     if (rc != DP_OK) return rc;
+    f0 = f1;
   }
+  if (total > 0) {
+    k_batch_unpack<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d_forceP, d_pos, total, d_force);
+    note_launch();
+  }
+  CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(energy, d_e, sizeof(double) * nframes, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(virial, d_vir, sizeof(double) * 9 * nframes, cudaMemcpyDeviceToHost, st));
   if (total > 0) CUDA_TRY(cudaMemcpyAsync(force + 3 * a0, d_force, sizeof(double) * 3 * total, cudaMemcpyDeviceToHost, st));

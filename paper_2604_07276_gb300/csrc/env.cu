@@ -22,7 +22,7 @@ __global__ void k_env(EnvArgs a) {
   float4 R = make_float4(0.f, 0.f, 0.f, 0.f), rw = R, rv = R;
   double w64 = 0.0;
   if (j >= 0) {
-    const CellGrid g = *a.grid;
+    const CellGrid g = a.frame ? a.grid[a.frame[i]] : *a.grid;
     const double ex = a.coord[3 * j] - a.coord[3 * i];
     const double ey = a.coord[3 * j + 1] - a.coord[3 * i + 1];
     const double ez = a.coord[3 * j + 2] - a.coord[3 * i + 2];
@@ -83,7 +83,7 @@ __global__ void k_env_bwd(EnvBwdArgs a) {
     const int i = (int)(row / NP);
     Real rx, ry, rz;
     if (sizeof(Real) == 8) {
-      const CellGrid g = *a.grid;
+      const CellGrid g = a.frame ? a.grid[a.frame[i]] : *a.grid;
       rx = (Real)mic(a.coord[3 * j] - a.coord[3 * i], g.L[0]);
       ry = (Real)mic(a.coord[3 * j + 1] - a.coord[3 * i + 1], g.L[1]);
       rz = (Real)mic(a.coord[3 * j + 2] - a.coord[3 * i + 2], g.L[2]);
@@ -140,7 +140,7 @@ void launch_env_bwd(const EnvBwdArgs& a, cudaStream_t st) {
 // fixed order (bitwise reproducible, no atomics).  A lane adds its few terms
 // and the warp its 32 lane sums in FP32 (a fixed tree; the FP64 pipe of this
 // GPU is narrow), the per-block virial and energy in FP64.
-constexpr int FWARPS = 4;
+constexpr int FWARPS = FORCE_BLOCK_ATOMS;
 __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
   __shared__ int srev[FWARPS][REV_CAP];
   __shared__ double sred[FWARPS][10];
@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
     f0 = warp_sum(f0); f1 = warp_sum(f1); f2 = warp_sum(f2);
     if (lane == 0) {
       a.force[3 * k] = f0; a.force[3 * k + 1] = f1; a.force[3 * k + 2] = f2;
-      ek = k < a.nlocal ? (double)a.e[k] : 0.0;  // ghost atoms: m_k = 0 (Eq. eq_forcesLocalGhost)
+      // ghost atoms: m_k = 0 (Eq. eq_forcesLocalGhost); padding of a packed batch: no atom
+      ek = k < a.nlocal && (!a.frame || a.frame[k] >= 0) ? (double)a.e[k] : 0.0;
       if (a.atom_energy) a.atom_energy[k] = ek;
     }
   }
@@ -204,25 +205,34 @@ __global__ void __launch_bounds__(32 * FWARPS) k_force(ForceArgs a) {
   }
 }
 
-__global__ void k_finalize(const double* __restrict__ partials, int nblocks, double* __restrict__ energy,
-                           double* __restrict__ virial) {
+// Sums the block partials in a fixed order: one block per frame of a packed
+// batch (seg non-null: frame b owns partial rows [seg[b] - seg[0],
+// seg[b+1] - seg[0])), else one block over rows [0, nblocks).
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, const int* __restrict__ seg,
+                           double* __restrict__ energy, double* __restrict__ virial) {
   __shared__ double red[10][32];
   const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;  // 10 warps, one per quantity
+  int b0 = 0, cnt = nblocks;
+  if (seg) {
+    b0 = seg[blockIdx.x] - seg[0];
+    cnt = seg[blockIdx.x + 1] - seg[blockIdx.x];
+  }
+  const double* p = partials + (size_t)b0 * 10 + c;
   // eight independent partial sums per lane (eight loads in flight), added
   // in a fixed order
   double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int b = lane;
-  for (; b + 7 * 32 < nblocks; b += 8 * 32) {
+  for (; b + 7 * 32 < cnt; b += 8 * 32) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s8[u] += partials[(size_t)(b + 32 * u) * 10 + c];
+    for (int u = 0; u < 8; ++u) s8[u] += p[(size_t)(b + 32 * u) * 10];
   }
-  for (; b < nblocks; b += 32) s8[0] += partials[(size_t)b * 10 + c];
+  for (; b < cnt; b += 32) s8[0] += p[(size_t)b * 10];
   double s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
   s = warp_sum_d(s);
   if (lane == 0) red[c][0] = s;
   __syncthreads();
-  if (threadIdx.x < 9) virial[threadIdx.x] = red[threadIdx.x][0];
-  if (threadIdx.x == 9) *energy = red[9][0];
+  if (threadIdx.x < 9) virial[9 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x == 9) energy[blockIdx.x] = red[9][0];
 }
 
 void launch_force_virial(const ForceArgs& a, cudaStream_t st) {
@@ -231,8 +241,15 @@ void launch_force_virial(const ForceArgs& a, cudaStream_t st) {
     k_force<<<nb, 32 * FWARPS, 0, st>>>(a);
     note_launch();
   }
-  k_finalize<<<1, 320, 0, st>>>(a.partials, nb, a.energy, a.virial);
-  note_launch();
+  if (a.seg) {
+    if (a.nseg > 0) {
+      k_finalize<<<a.nseg, 320, 0, st>>>(a.partials, nb, a.seg, a.energy, a.virial);
+      note_launch();
+    }
+  } else {
+    k_finalize<<<1, 320, 0, st>>>(a.partials, nb, nullptr, a.energy, a.virial);
+    note_launch();
+  }
 }
 
 }  // namespace dpa1

@@ -24,6 +24,9 @@ struct NbrArgs {
   int* atype_c;    // out: types clamped to [0, ntypes)
   float4* coordf;  // scratch [n]: FP32 copy of the coordinates for the candidate screen
   int* err;
+  // packed batches: atoms [n, n_out) are padding (no neighbours, type 0) and
+  // base is added to every neighbour index written (0 and 0: plain call)
+  int n_out = 0, base = 0;
 };
 void launch_neighbors(const NbrArgs& a, cudaStream_t st);
 void launch_reverse(const int* nlist, int n, int* rev_cnt, int* rev_rows, int* err, cudaStream_t st);
@@ -43,6 +46,7 @@ struct EnvArgs {
   float* rv;  // [n*NP][4] (x, y, z, |r|)
   double* w64;  // [n*NP] switch weight in FP64
   int fp64;     // evaluate in FP64 (else FP32 from the FP64 displacement)
+  const int* frame = nullptr;  // packed batches: frame of each atom, indexing grid[]
 };
 void launch_env(const EnvArgs& a, cudaStream_t st);
 
@@ -59,9 +63,13 @@ struct EnvBwdArgs {
   const float* dR;    // [rows][4]
   const float* dgeo;  // [rows][4] (d rhat xyz, d w)
   float* g;           // [rows][4] dE/dr_ij (xyz, 0)
+  const int* frame = nullptr;  // packed batches: frame of each atom, indexing grid[]
 };
 void launch_env_bwd(const EnvBwdArgs& a, cudaStream_t st);
 
+// atoms per block of the force kernel: a packed batch pads every frame to a
+// multiple of it, so that no block holds atoms of two frames
+constexpr int FORCE_BLOCK_ATOMS = 4;
 struct ForceArgs {
   const float* g;
   const float* rv;
@@ -74,9 +82,15 @@ struct ForceArgs {
   double* force;        // [n][3]
   double* atom_energy;  // [n] or null
   double* partials;     // [blocks][10] (9 virial + energy)
-  double* energy;       // [1]
-  double* virial;       // [9]
+  double* energy;       // [1], or [nseg] with seg
+  double* virial;       // [9], or [nseg][9] with seg
   int* err;
+  // packed batches: atoms whose frame is < 0 are padding (their energies do
+  // not count); frame f owns the force blocks [seg[f] - seg[0], seg[f+1] - seg[0])
+  // and gets energy[f] and virial[9f..9f+8]
+  const int* frame = nullptr;
+  const int* seg = nullptr;
+  int nseg = 0;
 };
 void launch_force_virial(const ForceArgs& a, cudaStream_t st);
 

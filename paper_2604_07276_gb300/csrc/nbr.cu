@@ -126,16 +126,27 @@ __device__ __forceinline__ double mic_near(double d, double L) {
 // candidates that pass the screen.
 constexpr int NBR_WARPS = 4;
 __global__ void __launch_bounds__(32 * NBR_WARPS)
-k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict__ cgp,
+k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const CellGrid* __restrict__ cgp,
             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
             const int* __restrict__ cell_atoms, double rc2, int sel, int* __restrict__ nlist,
-            int* __restrict__ nnei, int* __restrict__ ncand, const float4* __restrict__ coordf,
-            int* __restrict__ err) {
+            int* __restrict__ nnei, int* __restrict__ ncand, int* __restrict__ atype_c,
+            const float4* __restrict__ coordf, int* __restrict__ err) {
   __shared__ unsigned long long skey[NBR_WARPS][NBR_CAP];
   __shared__ int sidx[NBR_WARPS][NBR_CAP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * NBR_WARPS + warp;
-  if (i >= n) return;
+  if (i >= n) {
+    // padding atoms of a packed batch: no neighbours, a valid type
+    if (i < n_out) {
+      for (int s = lane; s < NP; s += 32) nlist[(size_t)i * NP + s] = -1;
+      if (lane == 0) {
+        nnei[i] = 0;
+        ncand[i] = 0;
+        atype_c[i] = 0;
+      }
+    }
+    return;
+  }
   const CellGrid g = *cgp;
   unsigned long long* key = skey[warp];
   int* idx = sidx[warp];
@@ -240,7 +251,7 @@ k_neighbors(const double* __restrict__ coord, int n, const CellGrid* __restrict_
       __syncwarp();
     }
   const int keep = cnt < sel ? cnt : sel;
-  for (int s = lane; s < NP; s += 32) nlist[(size_t)i * NP + s] = s < keep ? idx[s] : -1;
+  for (int s = lane; s < NP; s += 32) nlist[(size_t)i * NP + s] = s < keep ? idx[s] + base : -1;
   if (lane == 0) nnei[i] = keep;
 }
 
@@ -263,18 +274,21 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t st) {
   cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)a.cell_cap, st);
   k_cell_setup<<<1, 1, 0, st>>>(a.box, a.rcut, a.cap_dim, a.grid, a.err);
   note_launch();
-  if (a.n == 0) return;
+  const int n_out = a.n_out > a.n ? a.n_out : a.n;
+  if (n_out == 0) return;
   const int tb = 256;
-  k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of,
-                                                  a.cell_count, a.atype_c, a.coordf, a.err);
-  note_launch();
-  k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid);
-  note_launch();
-  k_cell_fill<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.cell_of, a.n, a.cell_start, a.cell_cursor, a.cell_atoms);
-  note_launch();
-  k_neighbors<<<(a.n + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
-      a.coord, a.n, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist,
-      a.nnei, a.ncand, a.coordf, a.err);
+  if (a.n > 0) {
+    k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of,
+                                                    a.cell_count, a.atype_c, a.coordf, a.err);
+    note_launch();
+    k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid);
+    note_launch();
+    k_cell_fill<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.cell_of, a.n, a.cell_start, a.cell_cursor, a.cell_atoms);
+    note_launch();
+  }
+  k_neighbors<<<(n_out + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
+      a.coord, a.n, n_out, a.base, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist,
+      a.nnei, a.ncand, a.atype_c, a.coordf, a.err);
   note_launch();
 }
 

@@ -96,4 +96,53 @@ def test_batch_fp16x_oracle(default_model, frames, sampled):
     got = np.concatenate([F[k][atoms] for k, (atoms, _) in enumerate(sampled)])
     ref = np.concatenate([rF for _, rF in sampled])
     assert force_rmse(got, ref) <= BF16_FORCE_RMSE
+    for k, (c, t, b) in enumerate(frames):
+        Ek, Fk, Wk, _ = m.compute(c, b, t)  # the packed pass gives each frame's own result
+        assert Ek == E[k] and np.array_equal(Fk, F[k]) and np.array_equal(Wk, W[k])
+    m.close()
+
+
+def _same_as_alone(m, frames):
+    E, F, W = m.compute_batch(frames)
+    assert len(E) == len(frames) and W.shape == (len(frames), 3, 3)
+    for k, (c, t, b) in enumerate(frames):
+        Ek, Fk, Wk, _ = m.compute(c, b, t)
+        assert Ek == E[k] and np.array_equal(Fk, F[k]) and np.array_equal(Wk, W[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x"])
+def test_batch_edge_frames(default_model, precision):
+    """Empty frames, frames of 1, 2 and 5 atoms (padding in every force
+    block), isolated atoms and a ragged lattice frame, mixed in one batch."""
+    import paper_2604_07276_gb300 as p
+
+    cfg, w, _ = default_model
+    box = np.array([30.0, 30.0, 30.0])
+    c2 = np.array([[1.0, 1.0, 1.0], [15.0, 15.0, 15.0]])
+    c5 = np.array([[10.0, 10.0, 10.0], [11.2, 10.3, 9.9], [20.0, 20.0, 20.0], [21.0, 20.2, 20.0],
+                   [20.1, 21.1, 19.5]])
+    lat = synth.lattice_system(301, seed=5)
+    frames = [(np.zeros((0, 3)), np.zeros(0, np.int32), box),
+              (np.array([[3.0, 4.0, 5.0]]), np.array([2], np.int32), box),
+              (c5, np.array([3, 0, 1, 2, 3], np.int32), box),
+              (np.zeros((0, 3)), np.zeros(0, np.int32), box),
+              (lat[0], lat[1], lat[2]),
+              (c2, np.array([0, 4], np.int32), box * 1.5)]
+    m = p.DPA1(weight_file(cfg, w, "default"), precision=precision)
+    _same_as_alone(m, frames)
+    E, F, W = m.compute_batch(frames[:1])  # a batch of one empty frame
+    assert E[0] == 0.0 and np.all(W == 0.0) and F[0].shape == (0, 3)
+    m.close()
+
+
+def test_batch_several_passes(default_model):
+    """Three frames of 25,001 atoms: 75,012 padded slots, more than one pass
+    holds, so the batch runs as two passes (frames 0-1, then frame 2)."""
+    import paper_2604_07276_gb300 as p
+
+    cfg, w, _ = default_model
+    frames = [synth.lattice_system(25001, seed=s) for s in (41, 42, 43)]
+    frames = [(c, t, b) for c, t, b in frames]
+    m = p.DPA1(weight_file(cfg, w, "default"), precision="fp16x")
+    _same_as_alone(m, frames)
     m.close()
