@@ -185,10 +185,11 @@ DP_API int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, co
  *   dp_train_frame: for one frame with reference energy e_ref (eV) and
  *   DEVICE reference forces d_force_ref [natoms][3], adds to the gradient
  *   dL/dtheta of L = pe ((E - e_ref)/N)^2 + pf mean |F - F_ref|^2 and writes
- *   (L, energy part, force part) to DEVICE d_loss [3].  The energy part is
- *   exact; the force part uses -(2 pf / 3N) d/dtheta D_v E with v = F - F_ref
- *   held fixed, evaluated as a central difference of exact energy-weight
- *   gradients at x +- s v, s = fd_h / max|v| (fd_h in A).
+ *   (L, energy part, force part) to DEVICE d_loss [3].  Both parts are
+ *   exact: the force part is -(2 pf / 3N) times the derivative of
+ *   dE/dtheta along the displacement field v = F - F_ref (held fixed),
+ *   evaluated in forward mode over the adjoint (one energy evaluation with
+ *   its weight gradient, then one tangent pass).
  *   dp_adam_step: one Adam update of the vector with the accumulated
  *   gradient (then cleared). */
 DP_API int dp_param_count(const dp_model* m);
@@ -197,8 +198,8 @@ DP_API int dp_set_params(dp_model* m, const float* host, int count);
 DP_API int dp_get_grad(dp_model* m, float* host, int count);
 DP_API int dp_zero_grad(dp_model* m, void* cuda_stream);
 DP_API int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
-                          double e_ref, const double* d_force_ref, double pe, double pf, double fd_h,
-                          double* d_loss, void* cuda_stream);
+                          double e_ref, const double* d_force_ref, double pe, double pf, double* d_loss,
+                          void* cuda_stream);
 DP_API int dp_adam_step(dp_model* m, double lr, double beta1, double beta2, double eps, void* cuda_stream);
 
 /* Largest neighbour count and number of atoms whose candidate set exceeded

@@ -71,7 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dp_get_grad.argtypes = [P, F, ctypes.c_int]
     lib.dp_zero_grad.argtypes = [P, P]
     lib.dp_train_frame.argtypes = [P, ctypes.c_int, P, P, P, ctypes.c_double, P, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double, P, P]
+                                   P, P]
     lib.dp_adam_step.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
     lib.dp_md_run.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_double, ctypes.c_int, P, P, P, P, ctypes.c_int,
                               P]
@@ -260,14 +260,14 @@ class DPA1:
     def zero_grad(self, stream=None) -> None:
         _check(self.lib.dp_zero_grad(self.h, stream))
 
-    def train_frame(self, coord, box, atype, e_ref: float, force_ref, loss, pe=1.0, pf=1.0, fd_h=1e-2, stream=None):
+    def train_frame(self, coord, box, atype, e_ref: float, force_ref, loss, pe=1.0, pf=1.0, stream=None):
         """``dp_train_frame`` on CUDA tensors; ``loss`` is a float64 [3] tensor."""
         import torch
 
         st = stream if stream is not None else torch.cuda.current_stream(coord.device).cuda_stream
         _check(self.lib.dp_train_frame(self.h, int(coord.shape[0]), coord.data_ptr(), box.data_ptr(),
                                        atype.data_ptr(), float(e_ref), force_ref.data_ptr(), float(pe), float(pf),
-                                       float(fd_h), loss.data_ptr(), st))
+                                       loss.data_ptr(), st))
 
     def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
         _check(self.lib.dp_adam_step(self.h, float(lr), float(beta1), float(beta2), float(eps), stream))

@@ -559,6 +559,68 @@ int run_device(dp_model* m, int n, int nlocal, const double* coord, const double
   return run_after_neighbors(m, n, coord, ws.grid, nullptr, nullptr, 0, energy, force, virial, atom_energy, st);
 }
 
+// The tangent, along the atom displacement field v, of the energy-weight
+// gradient of the evaluation that just ran (FP32 path, no attention layer,
+// its intermediates still in the workspace), added to grad times *scale.
+void run_force_tangent(dp_model* m, int n, const double* coord, const double* v, float* Rd, float* Gd, float* dGd,
+                       float* Td, float* Xd, float* dXd, const std::vector<float*>& Hd, float* const* dH,
+                       float* const* dHd, float* dZ, float* dZd, float* Zd, const float* scale, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  JvpArgs a{};
+  a.coord = coord; a.grid = ws.grid; a.nlist = ws.nlist; a.nnei = ws.nnei; a.atype = ws.atype_c;
+  a.n = n; a.ntypes = m->nt; a.m1 = m->m1; a.axis = m->axis; a.fit_in = m->fit_in; a.sel = m->sel;
+  a.dstd = m->dstd; a.rcs = (float)m->rcs; a.rc = (float)m->rcut;
+  a.R = ws.R; a.G = ws.G[0]; a.T = ws.T; a.dX = ws.dX; a.dG = ws.dG; a.w = m->emb_packed; a.Gt = m->Gt; a.v = v;
+  a.Rd = Rd; a.Gd = Gd; a.Td = Td; a.Xd = Xd; a.dXd = dXd; a.dGd = dGd;
+  // forward: R', G', T' and X'
+  launch_env_jvp(a, st);
+  launch_embed_jvp(a, m->emb, 0, nullptr, scale, st);
+  launch_desc_jvp_fwd(a, st);
+  // fitting forward: H_l' = (1 - t_l^2) H_{l-1}' W_l (+ H_{l-1}')
+  const float* hin = Xd;
+  int fan = m->fit_in;
+  for (int l = 0; l < m->nfit; ++l) {
+    const int out = m->fit[l];
+    const bool res = (l > 0 && out == fan);
+    gemm_f32(hin, fan, m->fitW[l], out, nullptr, nullptr, 0, Zd, out, n, out, fan, EPI_BIAS, st);
+    launch_tanh_jvp(Zd, ws.H[l], res ? ws.H[l - 1] : nullptr, res ? hin : nullptr, Hd[l], (long long)n * out, st);
+    hin = Hd[l];
+    fan = out;
+  }
+  // energy head: (dE/dw_out)' = out_scale sum_i H_last,i'
+  launch_colsum(Hd[m->nfit - 1], fan, m->grad + m->off_wout, fan, n, scale, (float)m->out_scale, st);
+  // fitting adjoint and its tangent (dE/dH_last = out_scale w_out is constant)
+  launch_fill_rows(dH[0], m->w_out, n, n, fan, st);
+  cudaMemsetAsync(dHd[0], 0, sizeof(float) * (size_t)n * fan, st);
+  int cur = 0;
+  for (int l = m->nfit - 1; l >= 0; --l) {
+    const int out = m->fit[l];
+    const int in = l > 0 ? m->fit[l - 1] : m->fit_in;
+    const bool res = (l > 0 && out == in);
+    const float* Hprev = res ? ws.H[l - 1] : nullptr;
+    const float* Hprevd = res ? Hd[l - 1] : nullptr;
+    launch_tanh_bwd_jvp(dH[cur], dHd[cur], ws.H[l], Hprev, Hd[l], Hprevd, dZ, dZd, (long long)n * out, st);
+    const float* input = l > 0 ? ws.H[l - 1] : ws.X;
+    const float* inputd = l > 0 ? Hd[l - 1] : Xd;
+    launch_wgrad(inputd, in, dZ, out, m->grad + m->off_fitW[l], out, in, out, n, scale, st);
+    launch_wgrad(input, in, dZd, out, m->grad + m->off_fitW[l], out, in, out, n, scale, st);
+    launch_colsum(dZd, out, m->grad + m->off_fitb[l], out, n, scale, 1.0f, st);
+    if (l > 0) {
+      gemm_f32(dZ, out, m->fitWT[l], in, nullptr, res ? dH[cur] : nullptr, out, dH[1 - cur], in, n, in, out,
+               res ? EPI_RES : EPI_BIAS, st);
+      gemm_f32(dZd, out, m->fitWT[l], in, nullptr, res ? dHd[cur] : nullptr, out, dHd[1 - cur], in, n, in, out,
+               res ? EPI_RES : EPI_BIAS, st);
+      cur = 1 - cur;
+    } else {
+      // dE/dX itself is still in the workspace from the evaluation
+      gemm_f32(dZd, out, m->fitWT[l], in, nullptr, nullptr, 0, dXd, in, n, in, out, EPI_BIAS, st);
+    }
+  }
+  // descriptor adjoint's tangent -> (dE/dG)'; the embedding weights' tangent gradients
+  launch_desc_jvp_bwd(a, st);
+  launch_embed_jvp(a, m->emb, 1, m->grad, scale, st);
+}
+
 int read_status(dp_model* m) {
   int bits = 0;
   CUDA_TRY(cudaMemcpy(&bits, m->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1200,42 +1262,81 @@ int dp_zero_grad(dp_model* m, void* stream) {
 }
 
 int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
-                   double e_ref, const double* d_force_ref, double pe, double pf, double fd_h, double* d_loss,
-                   void* stream) {
+                   double e_ref, const double* d_force_ref, double pe, double pf, double* d_loss, void* stream) {
   if (check_model(m)) return DP_ERR_ARG;
   if (m->precision != DP_PREC_FP32 || m->nattn != 0 || m->concat)
     return fail(DP_ERR_UNSUPPORTED,
                 "dp_train_frame: training needs an FP32 model without attention layers in strip type-embedding mode");
-  if (natoms < 1 || !d_coord || !d_box || !d_atype || !d_force_ref || !d_loss || !(fd_h > 0.0))
+  if (natoms < 1 || !d_coord || !d_box || !d_atype || !d_force_ref || !d_loss)
     return fail(DP_ERR_ARG, "dp_train_frame: bad arguments");
   if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");
   CUDA_TRY(cudaSetDevice(m->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (m->t_cap < m->ws.cap) {
-    if (m->t_buf) cudaFree(m->t_buf);
+  const int cap = m->ws.cap, m1 = m->m1, nfit = m->nfit;
+  const size_t rows = (size_t)cap * NP;
+  int fmax = m->fit_in;
+  for (int l = 0; l < nfit; ++l) fmax = std::max(fmax, m->fit[l]);
+  struct TrainBufs {
+    double *energy, *virial, *force, *v;
+    float *gE, *Rd, *Gd, *dGd, *Td, *Xd, *dXd, *dH[2], *dHd[2], *dZ, *dZd, *Zd;
+    std::vector<float*> Hd;
+  } b;
+  auto plan = [&](Arena& a) {
+    b.energy = a.take<double>(1);
+    b.virial = a.take<double>(9);
+    b.force = a.take<double>((size_t)cap * 3);
+    b.v = a.take<double>((size_t)cap * 3);
+    b.gE = a.take<float>((size_t)m->ntheta);
+    b.Rd = a.take<float>(rows * 4);
+    b.Gd = a.take<float>(rows * m1);
+    b.dGd = a.take<float>(rows * m1);
+    b.Td = a.take<float>((size_t)cap * 4 * m1);
+    b.Xd = a.take<float>((size_t)cap * m->fit_in);
+    b.dXd = a.take<float>((size_t)cap * m->fit_in);
+    b.Hd.assign(nfit, nullptr);
+    for (int l = 0; l < nfit; ++l) b.Hd[l] = a.take<float>((size_t)cap * m->fit[l]);
+    for (int k = 0; k < 2; ++k) {
+      b.dH[k] = a.take<float>((size_t)cap * fmax);
+      b.dHd[k] = a.take<float>((size_t)cap * fmax);
+    }
+    b.dZ = a.take<float>((size_t)cap * fmax);
+    b.dZd = a.take<float>((size_t)cap * fmax);
+    b.Zd = a.take<float>((size_t)cap * fmax);
+  };
+  Arena probe;
+  plan(probe);
+  if (m->t_cap != cap || !m->t_buf) {
+    if (m->t_buf) CUDA_TRY(cudaFree(m->t_buf));
     m->t_buf = nullptr;
-    void* p = nullptr;
-    CUDA_TRY(cudaMalloc(&p, sizeof(double) * (16 + 9 * (size_t)m->ws.cap)));
-    m->t_buf = reinterpret_cast<double*>(p);
-    m->t_cap = m->ws.cap;
+    m->t_cap = 0;
+    if (cudaMalloc(&m->t_buf, probe.off) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DP_ERR_CUDA, "dp_train_frame: cudaMalloc of the training buffer failed");
+    }
+    m->t_cap = cap;
   }
-  double* t_energy = m->t_buf;
-  double* t_virial = m->t_buf + 1;
-  double* t_force = m->t_buf + 16;
-  double* coord_p = t_force + 3 * (size_t)m->t_cap;
-  double* coord_m = coord_p + 3 * (size_t)m->t_cap;
+  Arena real;
+  real.base = reinterpret_cast<char*>(m->t_buf);
+  real.cap = probe.off;
+  plan(real);
+  // 1. the energy evaluation, with dE/dtheta (unscaled) into gE
+  CUDA_TRY(cudaMemsetAsync(b.gE, 0, sizeof(float) * (size_t)m->ntheta, st));
+  float* grad_keep = m->grad;
+  m->grad = b.gE;
+  m->grad_scale = m->d_scales;  // 1
+  int rc = run_device(m, natoms, natoms, d_coord, d_box, d_atype, b.energy, b.force, b.virial, nullptr, st);
+  m->grad = grad_keep;
   m->grad_scale = nullptr;
-  int rc = run_device(m, natoms, natoms, d_coord, d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
   if (rc != DP_OK) return rc;
-  launch_train_prep(natoms, t_energy, e_ref, t_force, d_force_ref, d_coord, pe, pf, fd_h, coord_p, coord_m, d_loss,
-                    m->d_scales, st);
-  const double* xs[3] = {d_coord, coord_p, coord_m};
-  for (int k = 0; k < 3 && rc == DP_OK; ++k) {
-    m->grad_scale = m->d_scales + 1 + k;
-    rc = run_device(m, natoms, natoms, xs[k], d_box, d_atype, t_energy, t_force, t_virial, nullptr, st);
-  }
-  m->grad_scale = nullptr;
-  return rc;
+  // 2. loss, scales and v = F - F_ref; the energy term of the gradient
+  launch_train_prep(natoms, b.energy, e_ref, b.force, d_force_ref, pe, pf, b.v, d_loss, m->d_scales, st);
+  launch_axpy(m->grad, b.gE, m->ntheta, m->d_scales + 1, st);
+  // 3. the force term: the tangent of dE/dtheta along v, scaled by -2 pf / 3N
+  run_force_tangent(m, natoms, d_coord, b.v, b.Rd, b.Gd, b.dGd, b.Td, b.Xd, b.dXd, b.Hd, b.dH, b.dHd, b.dZ, b.dZd,
+                    b.Zd, m->d_scales + 2, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DP_ERR_CUDA, std::string("dp_train_frame: launch failed: ") + cudaGetErrorString(e));
+  return DP_OK;
 }
 
 int dp_adam_step(dp_model* m, double lr, double beta1, double beta2, double eps, void* stream) {

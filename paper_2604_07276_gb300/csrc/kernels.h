@@ -171,9 +171,51 @@ void launch_wgrad(const float* A, int lda, const float* B, int ldb, float* C, in
 void launch_colsum(const float* B, int ldb, float* c, int O, int N, const float* scale, float factor, cudaStream_t st);
 void launch_head_bias_grad(const int* atype, int n, float* g_ebias, float* g_bout, const float* scale, float out_scale,
                            cudaStream_t st);
+// loss of one frame, the gradient scales (1, energy term, force term) and
+// the direction v = F - F_ref of the force term
 void launch_train_prep(int n, const double* energy, double e_ref, const double* force, const double* force_ref,
-                       const double* coord, double pe, double pf, double h, double* coord_plus, double* coord_minus,
-                       double* loss, float* scales, cudaStream_t st);
+                       double pe, double pf, double* v, double* loss, float* scales, cudaStream_t st);
+// g[i] += *scale * src[i]
+void launch_axpy(float* g, const float* src, int n, const float* scale, cudaStream_t st);
+
+// Tangents (forward mode) of an energy evaluation of the FP32 path without
+// attention layers, along the atom displacement field v, and of its adjoint.
+struct JvpArgs {
+  const double* coord;  // [n][3]
+  const CellGrid* grid;
+  const int* nlist;     // [rows]
+  const int* nnei;      // [n]
+  const int* atype;     // [n] (range-checked)
+  int n, ntypes, m1, axis, fit_in, sel;
+  const float* dstd;    // [ntypes][4]
+  float rcs, rc;
+  const float* R;       // [rows][4] environment rows
+  const float* G;       // [rows][m1] embedding output (row-major)
+  const float* T;       // [n][4][m1]
+  const float* dX;      // [n][fit_in] dE/dX
+  const float* dG;      // [rows][m1] dE/dG
+  const float* w;       // packed embedding-net weights (W0 b0 W1 b1 W2 b2)
+  const float* Gt;      // [ntypes][ntypes][m1]
+  const double* v;      // [n][3] the direction
+  float* Rd;            // [rows][4]   R'
+  float* Gd;            // [rows][m1]  G'
+  float* Td;            // [n][4][m1]  T'
+  float* Xd;            // [n][fit_in] X'
+  const float* dXd;     // [n][fit_in] (dE/dX)'
+  float* dGd;           // [rows][m1]  (dE/dG)'
+};
+void launch_env_jvp(const JvpArgs& a, cudaStream_t st);
+// mode 0: G'; mode 1: grad += *scale * (dE/d(embedding weights))'
+bool launch_embed_jvp(const JvpArgs& a, const int* widths, int mode, float* grad, const float* scale,
+                      cudaStream_t st);
+void launch_desc_jvp_fwd(const JvpArgs& a, cudaStream_t st);
+void launch_desc_jvp_bwd(const JvpArgs& a, cudaStream_t st);
+// H' = (1 - t^2) Z' + Hprev' with t = H - Hprev (Hprev, Hprev' null: t = H, no skip)
+void launch_tanh_jvp(const float* Zd, const float* H, const float* Hprev, const float* Hprevd, float* Hd,
+                     long long count, cudaStream_t st);
+// dZ = dH (1 - t^2), dZ' = dH' (1 - t^2) - 2 dH t t' with t = H - Hprev, t' = H' - Hprev'
+void launch_tanh_bwd_jvp(const float* dH, const float* dHd, const float* H, const float* Hprev, const float* Hd,
+                         const float* Hprevd, float* dZ, float* dZd, long long count, cudaStream_t st);
 void launch_adam(float* theta, float* g, float* m1, float* m2, int n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, cudaStream_t st);
 void launch_transpose(const float* W, int R, int C, float* WT, cudaStream_t st);

@@ -124,9 +124,10 @@ struct dp_model {
   float* adam_v = nullptr;
   int adam_t = 0;
   const float* grad_scale = nullptr;  // non-null: the next evaluation adds scale * dE/dtheta to grad
-  float* d_scales = nullptr;          // [4]: 1, energy-loss scale, +/- force-loss scales
-  double* t_buf = nullptr;            // training scratch: energy, virial, loss, forces, displaced coords
-  int t_cap = 0;
+  float* d_scales = nullptr;          // [4]: 1, energy-loss scale, force-loss scale, 0
+  void* t_buf = nullptr;              // training scratch: energy, virial, forces, the direction
+                                      // v = F - F_ref, dE/dtheta, and the tangents of the evaluation
+  int t_cap = 0;                      // atoms t_buf is laid out for
   // device weights
   float *emb_packed, *Gt, *tebd, *davg, *dstd, *ebias, *w_out;
   bool concat = false;     // type-embedding mode: the embedding net reads [s, T_j, T_i]

@@ -60,7 +60,7 @@ def _maxwell(atype, masses_of, temperature, rng):
 
 
 def train(student: DPA1, frames: Sequence[Frame], epochs: int, batch: int = 16, lr0: float = 1e-3,
-          lr_end: float = 1e-5, pe: float = 1.0, pf: float = 1.0, fd_h: float = 1e-2, seed: int = 0):
+          lr_end: float = 1e-5, pe: float = 1.0, pf: float = 1.0, seed: int = 0):
     """Adam on mini-batches of frames (gradient = mean over the batch); the
     learning rate decays exponentially from lr0 to lr_end.  Returns the mean
     loss of every batch."""
@@ -82,7 +82,7 @@ def train(student: DPA1, frames: Sequence[Frame], epochs: int, batch: int = 16, 
             student.zero_grad()
             for i in idx:
                 f = frames[i]
-                student.train_frame(f.coord, f.box, f.atype, f.energy, f.force, loss, pe=pe, pf=pf, fd_h=fd_h,
+                student.train_frame(f.coord, f.box, f.atype, f.energy, f.force, loss, pe=pe, pf=pf,
                                     stream=torch.cuda.current_stream().cuda_stream)
                 acc += loss
             # mean over the batch: scale the learning rate (Adam is invariant to
