@@ -469,16 +469,23 @@ def run_ours(a):
     nl, nn = m.nlist_device(c, b)
     nn = nn.cpu().numpy()
     if rank == 0 and not a.no_parity:
-        from oracle import OracleModel, forces_on
+        from oracle import OracleModel, energy_force_virial, reverse_centres
 
         om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=0))
         rng = np.random.default_rng(7)
         atoms = rng.choice(n, size=12, replace=False)
-        ref = forces_on(om, coord, box, atype, atoms)
+        # the centres whose atomic energies depend on the sampled atoms: their
+        # e_i and the exact forces on the sampled atoms
+        cs = reverse_centres(coord, box, cfg.rcut, cfg.sel, atoms)
+        _, e_ref, f_ref, _ = energy_force_virial(om, coord, box, atype, centres=cs)
+        ref = f_ref[atoms]
         for p, mm in models.items():
-            _, Fp, _, _ = mm.compute(coord, box, atype)
+            _, Fp, _, ep = mm.compute(coord, box, atype, atom_energy=True)
             parity[p] = {"force_rmse_ev_per_A": float(np.sqrt(np.mean((Fp[atoms] - ref) ** 2))),
-                         "sampled_atoms": len(atoms)}
+                         "sampled_atoms": len(atoms),
+                         "atomic_energy_max_abs_err_eV": float(np.abs(ep[cs] - e_ref).max()),
+                         "atomic_energy_rms_err_eV": float(np.sqrt(np.mean((ep[cs] - e_ref) ** 2))),
+                         "atomic_energy_centres": int(len(cs))}
 
     if rank != 0:
         return 0
