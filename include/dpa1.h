@@ -175,10 +175,11 @@ DP_API int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, co
  * embedding net (em_W0 em_b0 em_W1 em_b1 em_W2 em_b2), fitting layers
  * (fit_W fit_b per hidden layer), output layer (w, b) and per-type energy
  * bias, in the order and shapes of the weight file; the type embedding and
- * type-pair net stay fixed.  Training needs the strip type-embedding mode
- * (a concat-mode model, whose embedding net reads [s, T_j, T_i], returns
- * DP_ERR_UNSUPPORTED from dp_train_frame; its parameter vector holds the s
- * row of em_W0 only).
+ * type-pair net stay fixed.  In the concat type-embedding mode (the
+ * embedding net reads [s, T_j, T_i]) the vector holds the s row of em_W0
+ * only: the type rows stay fixed with the type embedding, and the library
+ * keeps their contribution plus em_b0 as a bias per type pair, refreshed
+ * after every update.
  *   dp_param_count: number of entries.  dp_get_params / dp_set_params /
  *   dp_get_grad copy the vector / its gradient to or from host memory
  *   (count must equal dp_param_count).  dp_zero_grad clears the gradient.

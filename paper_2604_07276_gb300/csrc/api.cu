@@ -218,6 +218,9 @@ void refresh_derived(dp_model* m, cudaStream_t st) {
   }
   launch_scale_copy(m->theta + m->off_wout, m->w_out, fan, (float)m->out_scale, st);
   launch_scale_copy(m->theta + m->off_bout, m->d_b_out, 1, (float)m->out_scale, st);
+  // concat mode: the first-layer bias per type pair follows em_b0 (entries E0 .. 2 E0 of the vector)
+  if (m->concat && m->b0t_type)
+    launch_add_rows(m->b0t_type, m->theta + m->emb[0], m->nt * m->nt, m->emb[0], m->b0t, st);
   fit_tc_refresh(m, st);  // tensor-core weight images of the 16-bit paths, if built
 }
 
@@ -570,7 +573,8 @@ void run_force_tangent(dp_model* m, int n, const double* coord, const double* v,
   a.coord = coord; a.grid = ws.grid; a.nlist = ws.nlist; a.nnei = ws.nnei; a.atype = ws.atype_c;
   a.n = n; a.ntypes = m->nt; a.m1 = m->m1; a.axis = m->axis; a.fit_in = m->fit_in; a.sel = m->sel;
   a.dstd = m->dstd; a.rcs = (float)m->rcs; a.rc = (float)m->rcut;
-  a.R = ws.R; a.G = ws.G[0]; a.T = ws.T; a.dX = ws.dX; a.dG = ws.dG; a.w = m->emb_packed; a.Gt = m->Gt; a.v = v;
+  a.R = ws.R; a.G = ws.G[0]; a.T = ws.T; a.dX = ws.dX; a.dG = ws.dG; a.w = m->emb_packed; a.Gt = m->Gt;
+  a.b0t = m->b0t; a.v = v;
   a.Rd = Rd; a.Gd = Gd; a.Td = Td; a.Xd = Xd; a.dXd = dXd; a.dGd = dGd;
   // forward: R', G', T' and X'
   launch_env_jvp(a, st);
@@ -716,19 +720,22 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     std::vector<double> Z((size_t)nt * td);
     for (int t = 0; t < nt; ++t)
       for (int c = 0; c < td; ++c) Z[(size_t)t * td + c] = std::tanh(teW[(size_t)t * td + c] + teb[c]);
-    std::vector<float> z((size_t)nt * td), gt((size_t)nt * nt * m->m1, 0.f), b0t((size_t)nt * nt * e0);
+    std::vector<float> z((size_t)nt * td), gt((size_t)nt * nt * m->m1, 0.f), b0t((size_t)nt * nt * e0),
+        b0t_type((size_t)nt * nt * e0);
     for (size_t i = 0; i < z.size(); ++i) z[i] = (float)Z[i];
     for (int a = 0; a < nt; ++a)
       for (int b = 0; b < nt; ++b)
         for (int p = 0; p < e0; ++p) {
-          double v = b0[p];
+          double v = 0.0;
           for (int c = 0; c < td; ++c)
             v += Z[(size_t)b * td + c] * W0[(size_t)(1 + c) * e0 + p] + Z[(size_t)a * td + c] * W0[(size_t)(1 + td + c) * e0 + p];
-          b0t[((size_t)a * nt + b) * e0 + p] = (float)v;
+          b0t_type[((size_t)a * nt + b) * e0 + p] = (float)v;
+          b0t[((size_t)a * nt + b) * e0 + p] = (float)(v + b0[p]);
         }
     if ((rc = dev_upload(m, &m->tebd, z)) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &m->Gt, gt)) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &m->b0t, b0t)) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &m->b0t_type, b0t_type)) != DP_OK) return fail_free(rc);
   }
   // type tables (a4) on the device
   if (!m->concat) {
@@ -1264,9 +1271,8 @@ int dp_zero_grad(dp_model* m, void* stream) {
 int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
                    double e_ref, const double* d_force_ref, double pe, double pf, double* d_loss, void* stream) {
   if (check_model(m)) return DP_ERR_ARG;
-  if (m->precision != DP_PREC_FP32 || m->nattn != 0 || m->concat)
-    return fail(DP_ERR_UNSUPPORTED,
-                "dp_train_frame: training needs an FP32 model without attention layers in strip type-embedding mode");
+  if (m->precision != DP_PREC_FP32 || m->nattn != 0)
+    return fail(DP_ERR_UNSUPPORTED, "dp_train_frame: training needs an FP32 model without attention layers");
   if (natoms < 1 || !d_coord || !d_box || !d_atype || !d_force_ref || !d_loss)
     return fail(DP_ERR_ARG, "dp_train_frame: bad arguments");
   if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");

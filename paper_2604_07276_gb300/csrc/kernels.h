@@ -196,6 +196,7 @@ struct JvpArgs {
   const float* dG;      // [rows][m1] dE/dG
   const float* w;       // packed embedding-net weights (W0 b0 W1 b1 W2 b2)
   const float* Gt;      // [ntypes][ntypes][m1]
+  const float* b0t;     // concat mode: first-layer bias per (centre, neighbour) type, or null
   const double* v;      // [n][3] the direction
   float* Rd;            // [rows][4]   R'
   float* Gd;            // [rows][m1]  G'
@@ -220,6 +221,8 @@ void launch_adam(float* theta, float* g, float* m1, float* m2, int n, float lr, 
                  float bc1, float bc2, cudaStream_t st);
 void launch_transpose(const float* W, int R, int C, float* WT, cudaStream_t st);
 void launch_scale_copy(const float* src, float* dst, int n, float s, cudaStream_t st);
+// out[r][p] = rows[r][p] + vec[p] for r < nrows, p < width
+void launch_add_rows(const float* rows, const float* vec, int nrows, int width, float* out, cudaStream_t st);
 
 // --- velocity-Verlet MD (md.cu)
 void launch_verlet_drift(int n, double dt, const double* mass, const double* f, double* v, double* x, cudaStream_t st);

@@ -132,6 +132,7 @@ struct dp_model {
   float *emb_packed, *Gt, *tebd, *davg, *dstd, *ebias, *w_out;
   bool concat = false;     // type-embedding mode: the embedding net reads [s, T_j, T_i]
   float* b0t = nullptr;    // concat mode: first-layer bias per (centre, neighbour) type [nt][nt][E0]
+  float* b0t_type = nullptr;  // concat mode: the types' part of b0t (b0t = b0t_type + em_b0)
   std::vector<AttnLayerW> attn;
   std::vector<float*> fitW, fitWT, fitb;
   TcWeights tcw;

@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(JTHREADS) k_embed_jvp(JvpArgs a, int mode, flo
       const int r = idx / E0, p = idx % E0;
       float h = 0.f, hd = 0.f;
       if (r < cnt) {
-        h = tanhf(fmaf(sm[S::X + r], sm[S::W0 + p], sm[S::B0 + p]));
+        const float b0 = a.b0t ? a.b0t[((size_t)ti * a.ntypes + a.atype[a.nlist[base + r]]) * E0 + p] : sm[S::B0 + p];
+        h = tanhf(fmaf(sm[S::X + r], sm[S::W0 + p], b0));
         hd = (1.f - h * h) * sm[S::XD + r] * sm[S::W0 + p];
       }
       sm[S::H1 + r * S::Q0 + p] = h;
@@ -528,6 +529,12 @@ __global__ void k_scale_copy(const float* __restrict__ src, float* __restrict__ 
   if (t < n) dst[t] = s * src[t];
 }
 
+__global__ void k_add_rows(const float* __restrict__ rows, const float* __restrict__ vec, int nrows, int width,
+                           float* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nrows * width) out[t] = rows[t] + vec[t % width];
+}
+
 static int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_wgrad(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int I, int O, int N,
@@ -640,6 +647,12 @@ void launch_transpose(const float* W, int R, int C, float* WT, cudaStream_t st) 
 void launch_scale_copy(const float* src, float* dst, int n, float s, cudaStream_t st) {
   if (n <= 0) return;
   k_scale_copy<<<blocks(n, 256), 256, 0, st>>>(src, dst, n, s);
+  note_launch();
+}
+
+void launch_add_rows(const float* rows, const float* vec, int nrows, int width, float* out, cudaStream_t st) {
+  if (nrows * width <= 0) return;
+  k_add_rows<<<blocks((long long)nrows * width, 256), 256, 0, st>>>(rows, vec, nrows, width, out);
   note_launch();
 }
 
