@@ -983,12 +983,37 @@ int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coo
     }
   }
   for (int f = 0; f <= nframes; ++f) seg[f] = (int)(po[f] / PB);
+  // Every frame's cell grid (cell edge >= rcut, as the device sets it up for
+  // a single frame) and the first cell of each frame in a batch-wide count:
+  // a pass searches all its frames at once when its cells fit the workspace.
+  std::vector<CellGrid> grids(nframes);
+  std::vector<long long> cum(nframes + 1, 0);
+  std::vector<char> finite(nframes, 1);
+  for (int f = 0; f < nframes; ++f) {
+    CellGrid g{};
+    g.ok = 1;
+    for (int d = 0; d < 3; ++d) {
+      const double L = box[9LL * f + 4 * d];
+      g.L[d] = L;
+      if (!std::isfinite(L)) finite[f] = 0;
+      int nc = finite[f] ? (int)std::floor(L / (m->rcut * (1.0 + 1e-9))) : 1;
+      if (nc < 3) nc = 1;
+      if (nc > m->ws.cap_dim) nc = m->ws.cap_dim;
+      g.nc[d] = nc;
+    }
+    g.ncells = g.nc[0] * g.nc[1] * g.nc[2];
+    grids[f] = g;
+    cum[f + 1] = cum[f] + g.ncells;
+  }
+  const bool cells_fit_int = cum[nframes] <= (long long)INT_MAX;
+  std::vector<int> cbase(nframes + 1);
+  for (int f = 0; f <= nframes; ++f) cbase[f] = cells_fit_int ? (int)cum[f] : 0;
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t b_coord = up(sizeof(double) * 3 * total), b_type = up(sizeof(int) * total),
                b_box = up(sizeof(double) * 9 * nframes), b_e = up(sizeof(double) * nframes),
                b_coordP = up(sizeof(double) * 3 * P), b_typeP = up(sizeof(int) * P),
                b_grid = up(sizeof(CellGrid) * nframes), b_seg = up(sizeof(int) * (nframes + 1));
-  const size_t need = 2 * b_coord + 2 * b_type + 2 * b_box + b_e + 2 * b_coordP + 2 * b_typeP + b_grid + b_seg;
+  const size_t need = 2 * b_coord + 2 * b_type + 2 * b_box + b_e + 2 * b_coordP + 2 * b_typeP + b_grid + 2 * b_seg;
   if (need > m->batch_cap) {
     if (m->batch_buf) CUDA_TRY(cudaFree(m->batch_buf));
     m->batch_buf = nullptr;
@@ -1014,6 +1039,7 @@ int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coo
   int* d_frame = reinterpret_cast<int*>(take(b_typeP));
   CellGrid* d_grid = reinterpret_cast<CellGrid*>(take(b_grid));
   int* d_seg = reinterpret_cast<int*>(take(b_seg));
+  int* d_cbase = reinterpret_cast<int*>(take(b_seg));
   cudaStream_t st = m->stream;
   Workspace& ws = m->ws;
   if (total > 0) {
@@ -1025,6 +1051,8 @@ int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coo
   }
   if (P > 0) CUDA_TRY(cudaMemcpyAsync(d_frame, frame_of.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(d_seg, seg.data(), sizeof(int) * (nframes + 1), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(d_cbase, cbase.data(), sizeof(int) * (nframes + 1), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(d_grid, grids.data(), sizeof(CellGrid) * nframes, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(d_box, box, sizeof(double) * 9 * nframes, cudaMemcpyHostToDevice, st));
   for (int f0 = 0; f0 < nframes;) {
     int f1 = f0 + 1;
@@ -1035,15 +1063,23 @@ int dp_compute_batch(dp_model* m, int nframes, const int* off, const double* coo
     m->last_natoms = Pc;
     m->call_nlocal = Pc;  // every slot counts; padding is masked by its frame of -1
     prof_mark(m, "start", st);
-    // a1-a2 per frame (each has its own box and cell grid), written into
-    // the pass's slots with indices relative to the pass
-    for (int f = f0; f < f1; ++f) {
-      const int rel = (int)(po[f] - P0);
-      NbrArgs a = nbr_args(m, off[f + 1] - off[f], d_coordP + 3 * po[f], d_box + 9LL * f, d_typeP + po[f], d_grid + f,
-                           rel);
-      a.n_out = (int)(po[f + 1] - po[f]);
-      a.base = rel;
-      launch_neighbors(a, st);
+    // a1-a2: every frame in its own box and cell grid, neighbour indices
+    // relative to the pass; one search over the pass when its cells fit,
+    // else one per frame
+    bool packed = cells_fit_int && cum[f1] - cum[f0] <= (long long)m->ws.cell_cap;
+    for (int f = f0; f < f1 && packed; ++f) packed = finite[f] != 0;
+    if (packed) {
+      NbrArgs a = nbr_args(m, Pc, d_coordP + 3 * P0, d_box, d_typeP + P0, d_grid, 0);
+      launch_neighbors_packed(a, d_frame + P0, d_cbase, cbase[f0], (int)(cum[f1] - cum[f0]), st);
+    } else {
+      for (int f = f0; f < f1; ++f) {
+        const int rel = (int)(po[f] - P0);
+        NbrArgs a = nbr_args(m, off[f + 1] - off[f], d_coordP + 3 * po[f], d_box + 9LL * f, d_typeP + po[f],
+                             d_grid + f, rel);
+        a.n_out = (int)(po[f + 1] - po[f]);
+        a.base = rel;
+        launch_neighbors(a, st);
+      }
     }
     prof_mark(m, "neighbors", st);
     rc = run_after_neighbors(m, Pc, d_coordP + 3 * P0, d_grid, d_frame + P0, d_seg + f0, f1 - f0, d_e + f0,

@@ -24,11 +24,18 @@ struct NbrArgs {
   int* atype_c;    // out: types clamped to [0, ntypes)
   float4* coordf;  // scratch [n]: FP32 copy of the coordinates for the candidate screen
   int* err;
-  // packed batches: atoms [n, n_out) are padding (no neighbours, type 0) and
-  // base is added to every neighbour index written (0 and 0: plain call)
+  // packed batches, one frame per call: atoms [n, n_out) are padding (no
+  // neighbours, type 0) and base is added to every neighbour index written
+  // (0 and 0: plain call)
   int n_out = 0, base = 0;
 };
 void launch_neighbors(const NbrArgs& a, cudaStream_t st);
+// Packed batches, all frames of a pass in one search: slot i belongs to frame
+// frame[i] (-1: padding), whose cell grid is grid[frame[i]] (set up by the
+// caller) and whose cells are [cell_base[f] - cb0, + ncells) of the pass's cell
+// arrays (ncells_total of them, at most cell_cap).  n is the pass's slots.
+void launch_neighbors_packed(const NbrArgs& a, const int* frame, const int* cell_base, int cb0, int ncells_total,
+                             cudaStream_t st);
 void launch_reverse(const int* nlist, int n, int* rev_cnt, int* rev_rows, int* err, cudaStream_t st);
 
 // --- environment matrix and its adjoint, forces, reductions (env.cu)

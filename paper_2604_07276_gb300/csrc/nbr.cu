@@ -42,13 +42,28 @@ __device__ __forceinline__ int cell_coord(double x, double L, int nc) {
   return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// frame non-null (packed batches): slot i belongs to frame frame[i] (-1:
+// padding, no cell) with grid cgp[f] and cells from cell_base[f] - cb0 on.
 __global__ void k_cell_count(const double* __restrict__ coord, const int* __restrict__ atype, int n,
                              int ntypes, const CellGrid* __restrict__ cgp, int* __restrict__ cell_of,
                              int* __restrict__ cell_count, int* __restrict__ atype_c, float4* __restrict__ coordf,
-                             int* __restrict__ err) {
+                             int* __restrict__ err, const int* __restrict__ frame, const int* __restrict__ cell_base,
+                             int cb0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const CellGrid g = *cgp;
+  int cbase = 0;
+  const CellGrid* gp = cgp;
+  if (frame) {
+    const int f = frame[i];
+    if (f < 0) {
+      atype_c[i] = 0;
+      cell_of[i] = -1;
+      return;
+    }
+    gp = cgp + f;
+    cbase = cell_base[f] - cb0;
+  }
+  const CellGrid g = *gp;
   double x = coord[3 * i], y = coord[3 * i + 1], z = coord[3 * i + 2];
   coordf[i] = make_float4((float)x, (float)y, (float)z, 0.f);
   int c = 0;
@@ -60,6 +75,7 @@ __global__ void k_cell_count(const double* __restrict__ coord, const int* __rest
     int cz = cell_coord(z, g.L[2], g.nc[2]);
     c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
   }
+  c += cbase;
   int t = atype[i];
   if (t < 0 || t >= ntypes) {
     set_err(err, ERR_TYPE);
@@ -72,10 +88,10 @@ __global__ void k_cell_count(const double* __restrict__ coord, const int* __rest
 
 // Exclusive scan of the cell counts (one block).
 __global__ void k_cell_scan(const int* __restrict__ cell_count, int* __restrict__ cell_start,
-                            const CellGrid* __restrict__ cgp) {
+                            const CellGrid* __restrict__ cgp, int ncells_given) {
   __shared__ int part[1024];
   __shared__ int carry;
-  const int ncells = cgp->ncells;
+  const int ncells = ncells_given >= 0 ? ncells_given : cgp->ncells;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int base = 0; base < ncells; base += 1024) {
@@ -102,6 +118,7 @@ __global__ void k_cell_fill(const int* __restrict__ cell_of, int n, const int* _
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c = cell_of[i];
+  if (c < 0) return;  // padding of a packed batch
   int pos = cell_start[c] + atomicAdd(&cell_cursor[c], 1);
   cell_atoms[pos] = i;
 }
@@ -130,14 +147,16 @@ k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const 
             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
             const int* __restrict__ cell_atoms, double rc2, int sel, int* __restrict__ nlist,
             int* __restrict__ nnei, int* __restrict__ ncand, int* __restrict__ atype_c,
-            const float4* __restrict__ coordf, int* __restrict__ err) {
+            const float4* __restrict__ coordf, int* __restrict__ err, const int* __restrict__ frame,
+            const int* __restrict__ cell_base, int cb0) {
   __shared__ unsigned long long skey[NBR_WARPS][NBR_CAP];
   __shared__ int sidx[NBR_WARPS][NBR_CAP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * NBR_WARPS + warp;
-  if (i >= n) {
+  const int fi = frame && i < n ? frame[i] : 0;
+  if (i >= n || fi < 0) {
     // padding atoms of a packed batch: no neighbours, a valid type
-    if (i < n_out) {
+    if (i < n_out || (i < n && fi < 0)) {
       for (int s = lane; s < NP; s += 32) nlist[(size_t)i * NP + s] = -1;
       if (lane == 0) {
         nnei[i] = 0;
@@ -147,12 +166,13 @@ k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const 
     }
     return;
   }
-  const CellGrid g = *cgp;
+  const CellGrid g = cgp[frame ? fi : 0];
+  const int cbase = frame ? cell_base[fi] - cb0 : 0;  // the frame's first cell
   unsigned long long* key = skey[warp];
   int* idx = sidx[warp];
   const double xi = coord[3 * i], yi = coord[3 * i + 1], zi = coord[3 * i + 2];
   const float4 pi = coordf[i];
-  const int ci = cell_of[i];
+  const int ci = cell_of[i] - cbase;
   const int cx = ci % g.nc[0], cy = (ci / g.nc[0]) % g.nc[1], cz = ci / (g.nc[0] * g.nc[1]);
   const int ox = g.nc[0] >= 3 ? 1 : 0, oy = g.nc[1] >= 3 ? 1 : 0, oz = g.nc[2] >= 3 ? 1 : 0;
   const float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
@@ -169,7 +189,7 @@ k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const 
         int nx = (cx + dx + g.nc[0]) % g.nc[0];
         int ny = (cy + dy + g.nc[1]) % g.nc[1];
         int nz = (cz + dz + g.nc[2]) % g.nc[2];
-        int c = (nz * g.nc[1] + ny) * g.nc[0] + nx;
+        int c = cbase + (nz * g.nc[1] + ny) * g.nc[0] + nx;
         int b = cell_start[c], e = cell_start[c + 1];
         for (int base = b; base < e; base += 32) {
           int t = base + lane;
@@ -279,16 +299,35 @@ void launch_neighbors(const NbrArgs& a, cudaStream_t st) {
   const int tb = 256;
   if (a.n > 0) {
     k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of,
-                                                    a.cell_count, a.atype_c, a.coordf, a.err);
+                                                    a.cell_count, a.atype_c, a.coordf, a.err, nullptr, nullptr, 0);
     note_launch();
-    k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid);
+    k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid, -1);
     note_launch();
     k_cell_fill<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.cell_of, a.n, a.cell_start, a.cell_cursor, a.cell_atoms);
     note_launch();
   }
   k_neighbors<<<(n_out + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
       a.coord, a.n, n_out, a.base, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist,
-      a.nnei, a.ncand, a.atype_c, a.coordf, a.err);
+      a.nnei, a.ncand, a.atype_c, a.coordf, a.err, nullptr, nullptr, 0);
+  note_launch();
+}
+
+void launch_neighbors_packed(const NbrArgs& a, const int* frame, const int* cell_base, int cb0, int ncells_total,
+                             cudaStream_t st) {
+  if (a.n == 0) return;
+  cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)ncells_total, st);
+  cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)ncells_total, st);
+  const int tb = 256;
+  k_cell_count<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.coord, a.atype, a.n, a.ntypes, a.grid, a.cell_of, a.cell_count,
+                                                  a.atype_c, a.coordf, a.err, frame, cell_base, cb0);
+  note_launch();
+  k_cell_scan<<<1, 1024, 0, st>>>(a.cell_count, a.cell_start, a.grid, ncells_total);
+  note_launch();
+  k_cell_fill<<<(a.n + tb - 1) / tb, tb, 0, st>>>(a.cell_of, a.n, a.cell_start, a.cell_cursor, a.cell_atoms);
+  note_launch();
+  k_neighbors<<<(a.n + NBR_WARPS - 1) / NBR_WARPS, 32 * NBR_WARPS, 0, st>>>(
+      a.coord, a.n, a.n, 0, a.grid, a.cell_of, a.cell_start, a.cell_atoms, a.rcut * a.rcut, a.sel, a.nlist, a.nnei,
+      a.ncand, a.atype_c, a.coordf, a.err, frame, cell_base, cb0);
   note_launch();
 }
 
