@@ -65,7 +65,7 @@ def model_cfg(name):
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp16x", "bf16", "fp32"])
@@ -227,7 +227,9 @@ def _student_line(dev, coord, atype, box, full_rates, batch=16, md_steps=100):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+    """nvidia-smi sampling of SM clocks and throttle reasons (every 100 ms).
+    ``mark()`` is called as the timed region starts; only samples written
+    after it count."""
 
     def __init__(self, index):
         self.path = tempfile.mktemp(suffix=".csv")
@@ -237,9 +239,24 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        self.start_line = 0
+        # the sampler is running once its first line is out (bounded wait)
+        t0 = time.time()
+        while self.p is not None and self._lines() == 0 and time.time() - t0 < 5.0 and self.p.poll() is None:
+            time.sleep(0.02)
+
+    def _lines(self):
+        try:
+            with open(self.path) as fh:
+                return sum(1 for _ in fh)
+        except OSError:
+            return 0
+
+    def mark(self):
+        self.start_line = self._lines()
 
     def stop(self):
         if self.p is None:
@@ -249,7 +266,10 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        if len(lines) > self.start_line:
+            lines = lines[self.start_line:]
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -378,6 +398,8 @@ def run_ours(a):
         l0 = dp.kernel_launches()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        if clk:
+            clk.mark()
         ev0.record(stream)
         for _ in range(a.steps):
             m.compute_device(c, b, t, E, F, W, stream=stream.cuda_stream)

@@ -533,7 +533,11 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 constexpr int AW = 8;  // warps per block
 
 // Above an attention width of 128, K alone fills shared memory: V is then
-// read from global memory (through L1) instead (VG).
+// read from global memory (through L1) instead (VG).  A warp takes RQ rows j
+// at a time, so that every K and V element it loads serves RQ rows; each
+// output is still accumulated in the order of its own sum.
+constexpr int RQ = 4;
+
 template <int A>
 __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
   constexpr bool VG = A > 128;
@@ -541,9 +545,9 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
   float* Ks = sm;                                   // [NP][A+1]
   float* Vs = Ks + NP * (A + 1);                    // [NP][A] (not with VG)
   float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * A));  // [NP]
-  float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][A]
-  float* prow = qrow + AW * A;                      // [AW][NP]
-  double* w64s = reinterpret_cast<double*>(prow + AW * NP);  // [NP]
+  float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][RQ][A]
+  float* prow = qrow + AW * RQ * A;                 // [AW][RQ][NP]
+  double* w64s = reinterpret_cast<double*>(prow + AW * RQ * NP);  // [NP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int FQ = A / 32;
   const int ld = 3 * A;
@@ -560,92 +564,129 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
       w64s[r] = r < nn ? a.w64[base + r] : 0.0;
     }
     __syncthreads();
-    for (int j = warp; j < NP; j += AW) {
-      float* o = a.O + (base + j) * A;
-      if (j >= nn) {
-        for (int f = lane; f < A; f += 32) o[f] = 0.f;
+    for (int j0 = warp * RQ; j0 < NP; j0 += AW * RQ) {
+      if (j0 >= nn) {
+        for (int t = lane; t < RQ * A; t += 32) a.O[(base + j0) * A + t] = 0.f;
         continue;
       }
-      float* q = qrow + warp * A;
-      for (int f = lane; f < A; f += 32) q[f] = a.QKV[(base + j) * ld + f];
+      float* q = qrow + warp * RQ * A;
+      for (int t = lane; t < RQ * A; t += 32) {
+        const int r = t / A, f = t % A;
+        q[t] = j0 + r < nn ? a.QKV[(base + j0 + r) * ld + f] : 0.f;
+      }
       __syncwarp();
-      float s[4] = {0.f, 0.f, 0.f, 0.f};
+      float s[RQ][4];
+#pragma unroll
+      for (int r = 0; r < RQ; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) s[r][m] = 0.f;
       for (int f = 0; f < A; ++f) {
-        const float qf = q[f];
+        float kf[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) s[m] = fmaf(qf, Ks[(lane + 32 * m) * (A + 1) + f], s[m]);
-      }
-      const float4 rj = rws[j];
-      // smooth logits (l + S) w_j w_k (the constant -S of every logit of a row
-      // cancels in the softmax) in FP64: S = 20 leaves the FP32 spacing near
-      // the logits at 2e-6, far coarser than the logit differences that matter
-      const double wj = w64s[j];
-      double lp[4], mx = -1e300;
+        for (int m = 0; m < 4; ++m) kf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int k = lane + 32 * m;
-        lp[m] = 0.0;
-        if (k < nn) {
-          lp[m] = ((double)(s[m] * scale) + (double)a.shift) * (wj * w64s[k]);
-          mx = fmax(mx, lp[m]);
+        for (int r = 0; r < RQ; ++r) {
+          const float qf = q[r * A + f];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) s[r][m] = fmaf(qf, kf[m], s[r][m]);
         }
       }
-      mx = warp_max_d(mx);
-      float e[4], sum = 0.f;
+      float* p = prow + warp * RQ * NP;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int k = lane + 32 * m;
-        e[m] = k < nn ? expf((float)(lp[m] - mx)) : 0.f;
-        sum += e[m];
-      }
-      sum = warp_sum(sum);
-      const float inv = 1.0f / sum;
-      float* p = prow + warp * NP;
+      for (int r = 0; r < RQ; ++r) {
+        const int j = j0 + r;
+        if (j >= nn) {  // uniform over the warp
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int k = lane + 32 * m;
-        float pv = 0.f;
-        if (k < nn) {
-          const float4 rk = rws[k];
-          pv = e[m] * inv * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z);
+          for (int m = 0; m < 4; ++m) p[r * NP + lane + 32 * m] = 0.f;
+          continue;
         }
-        p[k] = pv;
+        const float4 rj = rws[j];
+        // smooth logits (l + S) w_j w_k (the constant -S of every logit of a
+        // row cancels in the softmax) in FP64: S = 20 leaves the FP32 spacing
+        // near the logits at 2e-6, far coarser than the logit differences
+        // that matter
+        const double wj = w64s[j];
+        double lp[4], mx = -1e300;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int k = lane + 32 * m;
+          lp[m] = 0.0;
+          if (k < nn) {
+            lp[m] = ((double)(s[r][m] * scale) + (double)a.shift) * (wj * w64s[k]);
+            mx = fmax(mx, lp[m]);
+          }
+        }
+        mx = warp_max_d(mx);
+        float e[4], sum = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int k = lane + 32 * m;
+          e[m] = k < nn ? expf((float)(lp[m] - mx)) : 0.f;
+          sum += e[m];
+        }
+        sum = warp_sum(sum);
+        const float inv = 1.0f / sum;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int k = lane + 32 * m;
+          float pv = 0.f;
+          if (k < nn) {
+            const float4 rk = rws[k];
+            pv = e[m] * inv * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z);
+          }
+          p[r * NP + k] = pv;
+        }
       }
       __syncwarp();
-      float acc[FQ];
+      float acc[RQ][FQ];
 #pragma unroll
-      for (int m = 0; m < FQ; ++m) acc[m] = 0.f;
+      for (int r = 0; r < RQ; ++r)
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) acc[r][m] = 0.f;
       for (int k = 0; k < nn; ++k) {
-        const float pk = p[k];
         const float* vk = VG ? a.QKV + (base + k) * ld + 2 * A : Vs + k * A;
+        float vv[FQ];
 #pragma unroll
-        for (int m = 0; m < FQ; ++m) acc[m] = fmaf(pk, vk[lane + 32 * m], acc[m]);
+        for (int m = 0; m < FQ; ++m) vv[m] = vk[lane + 32 * m];
+#pragma unroll
+        for (int r = 0; r < RQ; ++r) {
+          const float pk = p[r * NP + k];
+#pragma unroll
+          for (int m = 0; m < FQ; ++m) acc[r][m] = fmaf(pk, vv[m], acc[r][m]);
+        }
       }
 #pragma unroll
-      for (int m = 0; m < FQ; ++m) o[lane + 32 * m] = acc[m];
+      for (int r = 0; r < RQ; ++r) {
+        float* o = a.O + (base + j0 + r) * A;
+        const bool live = j0 + r < nn;
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) o[lane + 32 * m] = live ? acc[r][m] : 0.f;
+      }
       __syncwarp();
     }
     __syncthreads();
   }
 }
 
-// Adjoint of one attention layer for one centre.  Pass 1 (a warp per row j)
-// recomputes l, A and P, forms dP = dO_j . V_k, the softmax adjoint and dQ_j,
-// and the row / column parts of dE/dw and dE/drhat.  Pass 2 (a warp per key k)
-// forms dK_k = sum_j dS_jk Q_j and dV_k = sum_j P_jk dO_j from dS and P that
-// pass 1 left (transposed) in this block's global scratch slot.
+// Adjoint of one attention layer for one centre.  Pass 1 (a warp per RB rows
+// j) recomputes l, A and P, forms dP = dO_j . V_k, the softmax adjoint and
+// dQ_j, and the row / column parts of dE/dw and dE/drhat.  Pass 2 (a warp per
+// RB keys k) forms dK_k = sum_j dS_jk Q_j and dV_k = sum_j P_jk dO_j from dS
+// and P that pass 1 left (transposed) in this block's global scratch slot.
+// Every K, V, Q and dO element a warp loads serves its RB rows or keys.
 template <int A>
 __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
   constexpr bool VG = A > 128;  // V and dO from global memory, as in the forward
+  constexpr int RB = VG ? 2 : 4;
   extern __shared__ float sm[];
   float* Ks = sm;                                   // [NP][A+1]   pass 2: Q
   float* Vs = Ks + NP * (A + 1);                    // [NP][A+1]   pass 2: dO (not with VG)
   float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * (A + 1)));  // [NP]
   float4* rowg = rws + NP;                          // [NP] (d rhat_j, d w_j) row parts
-  float* qrow = reinterpret_cast<float*>(rowg + NP);  // [AW][A]
-  float* dorow = qrow + AW * A;                     // [AW][A]
-  float* prow = dorow + AW * A;                     // [AW][NP]
-  float* colw = prow + AW * NP;                     // [AW][NP]
+  float* qrow = reinterpret_cast<float*>(rowg + NP);  // [AW][RB][A]
+  float* dorow = qrow + AW * RB * A;                // [AW][RB][A]
+  float* prow = dorow + AW * RB * A;                // [AW][RB][NP]
+  float* colw = prow + AW * RB * NP;                // [AW][NP]
   float* colr = colw + AW * NP;                     // [AW][NP][3]
   double* w64s = reinterpret_cast<double*>(colr + 3 * AW * NP);  // [NP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -670,20 +711,32 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
       colr[3 * t] = 0.f; colr[3 * t + 1] = 0.f; colr[3 * t + 2] = 0.f;
     }
     __syncthreads();
-    for (int j = warp; j < nn; j += AW) {
-      float* q = qrow + warp * A;
-      float* dq = dorow + warp * A;
-      for (int f = lane; f < A; f += 32) {
-        q[f] = a.QKV[(base + j) * ld + f];
-        dq[f] = a.dO[(base + j) * A + f];
+    for (int j0 = warp * RB; j0 < nn; j0 += AW * RB) {
+      float* q = qrow + warp * RB * A;
+      float* dq = dorow + warp * RB * A;
+      for (int t = lane; t < RB * A; t += 32) {
+        const int r = t / A, f = t % A;
+        const bool live = j0 + r < nn;
+        q[t] = live ? a.QKV[(base + j0 + r) * ld + f] : 0.f;
+        dq[t] = live ? a.dO[(base + j0 + r) * A + f] : 0.f;
       }
       __syncwarp();
-      float s[4] = {0.f, 0.f, 0.f, 0.f}, dp[4] = {0.f, 0.f, 0.f, 0.f};
+      float s[RB][4], dp[RB][4];
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) { s[r][m] = 0.f; dp[r][m] = 0.f; }
       if (VG) {
         for (int f = 0; f < A; ++f) {
-          const float qf = q[f];
+          float kf[4];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) s[m] = fmaf(qf, Ks[(lane + 32 * m) * (A + 1) + f], s[m]);
+          for (int m = 0; m < 4; ++m) kf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const float qf = q[r * A + f];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s[r][m] = fmaf(qf, kf[m], s[r][m]);
+          }
         }
         // dp = dO_j . V_k: each lane walks its keys' rows of V (rows past nnei
         // are never read)
@@ -692,96 +745,130 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
           const int k = lane + 32 * m;
           if (k < nn) {
             const float4* v4 = reinterpret_cast<const float4*>(a.QKV + (base + k) * ld + 2 * A);
-            const float4* g4 = reinterpret_cast<const float4*>(dq);
-            float d = 0.f;
+            float d[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) d[r] = 0.f;
             for (int f4 = 0; f4 < A / 4; ++f4) {
-              const float4 vv = v4[f4], gg = g4[f4];
-              d = fmaf(gg.x, vv.x, fmaf(gg.y, vv.y, fmaf(gg.z, vv.z, fmaf(gg.w, vv.w, d))));
+              const float4 vv = v4[f4];
+#pragma unroll
+              for (int r = 0; r < RB; ++r) {
+                const float4 gg = reinterpret_cast<const float4*>(dq + r * A)[f4];
+                d[r] = fmaf(gg.x, vv.x, fmaf(gg.y, vv.y, fmaf(gg.z, vv.z, fmaf(gg.w, vv.w, d[r]))));
+              }
             }
-            dp[m] = d;
+#pragma unroll
+            for (int r = 0; r < RB; ++r) dp[r][m] = d[r];
           }
         }
       } else {
         for (int f = 0; f < A; ++f) {
-          const float qf = q[f], gf = dq[f];
+          float kf[4], vf[4];
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
-            const int k = lane + 32 * m;
-            s[m] = fmaf(qf, Ks[k * (A + 1) + f], s[m]);
-            dp[m] = fmaf(gf, Vs[k * (A + 1) + f], dp[m]);
+            kf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
+            vf[m] = Vs[(lane + 32 * m) * (A + 1) + f];
+          }
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const float qf = q[r * A + f], gf = dq[r * A + f];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              s[r][m] = fmaf(qf, kf[m], s[r][m]);
+              dp[r][m] = fmaf(gf, vf[m], dp[r][m]);
+            }
           }
         }
       }
-      const float4 rj = rws[j];
-      const double wj = w64s[j];
-      float l[4], ww[4], c[4];
-      double lp[4], mx = -1e300;
+      float* pr = prow + warp * RB * NP;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int k = lane + 32 * m;
-        const float4 rk = rws[k];
-        ww[m] = rj.w * rk.w;
-        c[m] = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
-        l[m] = s[m] * scale;
-        lp[m] = 0.0;
-        if (k < nn) {
-          lp[m] = ((double)l[m] + (double)a.shift) * (wj * w64s[k]);  // as in the forward kernel
-          mx = fmax(mx, lp[m]);
+      for (int r = 0; r < RB; ++r) {
+        const int j = j0 + r;
+        if (j >= nn) {  // uniform over the warp
+#pragma unroll
+          for (int m = 0; m < 4; ++m) pr[r * NP + lane + 32 * m] = 0.f;
+          continue;
         }
-      }
-      mx = warp_max_d(mx);
-      float e[4], sum = 0.f;
+        const float4 rj = rws[j];
+        const double wj = w64s[j];
+        float l[4], ww[4], c[4];
+        double lp[4], mx = -1e300;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        e[m] = (lane + 32 * m) < nn ? expf((float)(lp[m] - mx)) : 0.f;
-        sum += e[m];
-      }
-      sum = warp_sum(sum);
-      const float inv = 1.0f / sum;
-      float At[4], dA[4], tsum = 0.f;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        At[m] = e[m] * inv;
-        dA[m] = (lane + 32 * m) < nn ? dp[m] * ww[m] * c[m] : 0.f;
-        tsum += At[m] * dA[m];
-      }
-      tsum = warp_sum(tsum);
-      float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-      float* pr = prow + warp * NP;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int k = lane + 32 * m;
-        float dS = 0.f;
-        if (k < nn) {
-          const float dLp = At[m] * (dA[m] - tsum);
-          dS = dLp * ww[m] * scale;
-          const float H = dp[m] * At[m] * c[m] + dLp * (l[m] + a.shift);
-          const float dc = dp[m] * At[m] * ww[m];
+        for (int m = 0; m < 4; ++m) {
+          const int k = lane + 32 * m;
           const float4 rk = rws[k];
-          rw_ += H * rk.w;
-          rx += dc * rk.x; ry += dc * rk.y; rz += dc * rk.z;
-          colw[warp * NP + k] += H * rj.w;
-          colr[(warp * NP + k) * 3 + 0] += dc * rj.x;
-          colr[(warp * NP + k) * 3 + 1] += dc * rj.y;
-          colr[(warp * NP + k) * 3 + 2] += dc * rj.z;
-          dST[(size_t)k * NP + j] = dS;
-          PT[(size_t)k * NP + j] = At[m] * ww[m] * c[m];
+          ww[m] = rj.w * rk.w;
+          c[m] = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
+          l[m] = s[r][m] * scale;
+          lp[m] = 0.0;
+          if (k < nn) {
+            lp[m] = ((double)l[m] + (double)a.shift) * (wj * w64s[k]);  // as in the forward kernel
+            mx = fmax(mx, lp[m]);
+          }
         }
-        pr[k] = dS;
+        mx = warp_max_d(mx);
+        float e[4], sum = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          e[m] = (lane + 32 * m) < nn ? expf((float)(lp[m] - mx)) : 0.f;
+          sum += e[m];
+        }
+        sum = warp_sum(sum);
+        const float inv = 1.0f / sum;
+        float At[4], dA[4], tsum = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          At[m] = e[m] * inv;
+          dA[m] = (lane + 32 * m) < nn ? dp[r][m] * ww[m] * c[m] : 0.f;
+          tsum += At[m] * dA[m];
+        }
+        tsum = warp_sum(tsum);
+        float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int k = lane + 32 * m;
+          float dS = 0.f;
+          if (k < nn) {
+            const float dLp = At[m] * (dA[m] - tsum);
+            dS = dLp * ww[m] * scale;
+            const float H = dp[r][m] * At[m] * c[m] + dLp * (l[m] + a.shift);
+            const float dc = dp[r][m] * At[m] * ww[m];
+            const float4 rk = rws[k];
+            rw_ += H * rk.w;
+            rx += dc * rk.x; ry += dc * rk.y; rz += dc * rk.z;
+            colw[warp * NP + k] += H * rj.w;
+            colr[(warp * NP + k) * 3 + 0] += dc * rj.x;
+            colr[(warp * NP + k) * 3 + 1] += dc * rj.y;
+            colr[(warp * NP + k) * 3 + 2] += dc * rj.z;
+            dST[(size_t)k * NP + j] = dS;
+            PT[(size_t)k * NP + j] = At[m] * ww[m] * c[m];
+          }
+          pr[r * NP + k] = dS;
+        }
+        rw_ = warp_sum(rw_); rx = warp_sum(rx); ry = warp_sum(ry); rz = warp_sum(rz);
+        if (lane == 0) rowg[j] = make_float4(rx, ry, rz, rw_);
       }
-      rw_ = warp_sum(rw_); rx = warp_sum(rx); ry = warp_sum(ry); rz = warp_sum(rz);
-      if (lane == 0) rowg[j] = make_float4(rx, ry, rz, rw_);
       __syncwarp();
-      float acc[FQ];
+      float acc[RB][FQ];
 #pragma unroll
-      for (int m = 0; m < FQ; ++m) acc[m] = 0.f;
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) acc[r][m] = 0.f;
       for (int k = 0; k < nn; ++k) {
-        const float d = pr[k];
+        float kk[FQ];
 #pragma unroll
-        for (int m = 0; m < FQ; ++m) acc[m] = fmaf(d, Ks[k * (A + 1) + lane + 32 * m], acc[m]);
+        for (int m = 0; m < FQ; ++m) kk[m] = Ks[k * (A + 1) + lane + 32 * m];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const float d = pr[r * NP + k];
+#pragma unroll
+          for (int m = 0; m < FQ; ++m) acc[r][m] = fmaf(d, kk[m], acc[r][m]);
+        }
       }
 #pragma unroll
-      for (int m = 0; m < FQ; ++m) a.dQKV[(base + j) * ld + lane + 32 * m] = acc[m];
+      for (int r = 0; r < RB; ++r)
+        if (j0 + r < nn)
+#pragma unroll
+          for (int m = 0; m < FQ; ++m) a.dQKV[(base + j0 + r) * ld + lane + 32 * m] = acc[r][m];
       __syncwarp();
     }
     __syncthreads();
@@ -792,50 +879,74 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
       if (!VG) Vs[r * (A + 1) + f] = a.dO[(base + r) * A + f];
     }
     __syncthreads();
-    for (int k = warp; k < NP; k += AW) {
-      float* dq = a.dQKV + (base + k) * ld;
-      if (k >= nn) {
-        for (int f = lane; f < ld; f += 32) dq[f] = 0.f;
+    for (int k0 = warp * RB; k0 < NP; k0 += AW * RB) {
+      if (k0 >= nn) {
+        for (int t = lane; t < RB * ld; t += 32) a.dQKV[(base + k0) * ld + t] = 0.f;
         continue;
       }
-      float dK[FQ], dV[FQ];
+      float dK[RB][FQ], dV[RB][FQ];
 #pragma unroll
-      for (int m = 0; m < FQ; ++m) { dK[m] = 0.f; dV[m] = 0.f; }
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) { dK[r][m] = 0.f; dV[r][m] = 0.f; }
       for (int jb = 0; jb < nn; jb += 32) {
         const int jj = jb + lane;
-        const float dsv = jj < nn ? dST[(size_t)k * NP + jj] : 0.f;
-        const float pv = jj < nn ? PT[(size_t)k * NP + jj] : 0.f;
+        float dsv[RB], pv[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const bool live = jj < nn && k0 + r < nn;
+          dsv[r] = live ? dST[(size_t)(k0 + r) * NP + jj] : 0.f;
+          pv[r] = live ? PT[(size_t)(k0 + r) * NP + jj] : 0.f;
+        }
         const int cnt = (nn - jb) < 32 ? (nn - jb) : 32;
         for (int t = 0; t < cnt; ++t) {
-          const float d = __shfl_sync(0xffffffffu, dsv, t);
-          const float p = __shfl_sync(0xffffffffu, pv, t);
           const int j = jb + t;
           const float* doj = VG ? a.dO + (base + j) * A : Vs + j * (A + 1);
+          float qv[FQ], dv[FQ];
 #pragma unroll
           for (int m = 0; m < FQ; ++m) {
-            dK[m] = fmaf(d, Ks[j * (A + 1) + lane + 32 * m], dK[m]);
-            dV[m] = fmaf(p, doj[lane + 32 * m], dV[m]);
+            qv[m] = Ks[j * (A + 1) + lane + 32 * m];
+            dv[m] = doj[lane + 32 * m];
+          }
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const float d = __shfl_sync(0xffffffffu, dsv[r], t);
+            const float p = __shfl_sync(0xffffffffu, pv[r], t);
+#pragma unroll
+            for (int m = 0; m < FQ; ++m) {
+              dK[r][m] = fmaf(d, qv[m], dK[r][m]);
+              dV[r][m] = fmaf(p, dv[m], dV[r][m]);
+            }
           }
         }
       }
 #pragma unroll
-      for (int m = 0; m < FQ; ++m) {
-        dq[A + lane + 32 * m] = dK[m];
-        dq[2 * A + lane + 32 * m] = dV[m];
-      }
-      if (lane == 0) {
-        float cw = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-        for (int w = 0; w < AW; ++w) {
-          cw += colw[w * NP + k];
-          cx += colr[(w * NP + k) * 3 + 0];
-          cy += colr[(w * NP + k) * 3 + 1];
-          cz += colr[(w * NP + k) * 3 + 2];
+      for (int r = 0; r < RB; ++r) {
+        const int k = k0 + r;
+        float* dqk = a.dQKV + (base + k) * ld;
+        if (k >= nn) {
+          for (int f = lane; f < ld; f += 32) dqk[f] = 0.f;
+          continue;
         }
-        const float4 rg = rowg[k];
-        float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + k;
-        float4 cur = *dg;
-        cur.x += rg.x + cx; cur.y += rg.y + cy; cur.z += rg.z + cz; cur.w += rg.w + cw;
-        *dg = cur;
+#pragma unroll
+        for (int m = 0; m < FQ; ++m) {
+          dqk[A + lane + 32 * m] = dK[r][m];
+          dqk[2 * A + lane + 32 * m] = dV[r][m];
+        }
+        if (lane == 0) {
+          float cw = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+          for (int w = 0; w < AW; ++w) {
+            cw += colw[w * NP + k];
+            cx += colr[(w * NP + k) * 3 + 0];
+            cy += colr[(w * NP + k) * 3 + 1];
+            cz += colr[(w * NP + k) * 3 + 2];
+          }
+          const float4 rg = rowg[k];
+          float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + k;
+          float4 cur = *dg;
+          cur.x += rg.x + cx; cur.y += rg.y + cy; cur.z += rg.z + cz; cur.w += rg.w + cw;
+          *dg = cur;
+        }
       }
     }
     __syncthreads();
@@ -861,13 +972,14 @@ static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
   const int cap = bwd ? a.scratch_blocks : sm_count();
   const int grid = a.n < cap ? a.n : cap;
   if (!bwd) {
-    const size_t smem = sizeof(float) * (NP * (A + 1) + (VG ? 0 : NP * A) + 4 * NP + AW * A + AW * NP) +
+    const size_t smem = sizeof(float) * (NP * (A + 1) + (VG ? 0 : NP * A) + 4 * NP + AW * RQ * A + AW * RQ * NP) +
                         sizeof(double) * NP;
     cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_attn_fwd_f32<A><<<grid, 32 * AW, smem, st>>>(a, scale);
   } else {
-    const size_t smem = sizeof(float) * (NP * (A + 1) * (VG ? 1 : 2) + 8 * NP + 2 * AW * A + 2 * AW * NP +
-                                         3 * AW * NP) +
+    constexpr int RB = VG ? 2 : 4;  // rows / keys per warp of the adjoint
+    const size_t smem = sizeof(float) * (NP * (A + 1) * (VG ? 1 : 2) + 8 * NP + 2 * AW * RB * A + AW * RB * NP +
+                                         4 * AW * NP) +
                         sizeof(double) * NP;
     cudaFuncSetAttribute(k_attn_bwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_attn_bwd_f32<A><<<grid, 32 * AW, smem, st>>>(a, scale);
