@@ -280,7 +280,7 @@ int alloc_workspace(dp_model* m, int cap) {
       ws.dY = a.take<float>(rows * m1);
       ws.dO = a.take<float>(rows * (L > 0 ? A : 1));
       ws.dQKV = a.take<float>(rows * (L > 0 ? 3 * A : 1));
-      ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 2 * NP * NP);
+      ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 3 * NP * NP);  // dS^T, P^T, dP per block
     }
     ws.dG = a.take<float>(rows * m1);
     ws.T = a.take<float>((size_t)cap * 4 * m1);

@@ -530,17 +530,21 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 // Per centre atom, over its valid neighbour slots j, k < n_i:
 //   l_jk = Q_j.K_k / sqrt(A);  l'_jk = (l_jk + S) w_j w_k - S
 //   A_jk = softmax_k(l'_jk);   P_jk = A_jk w_j w_k (rhat_j . rhat_k);  O = P V
-constexpr int AW = 8;  // warps per block
 
 // Above an attention width of 128, K alone fills shared memory: V is then
 // read from global memory (through L1) instead (VG).  A warp takes RQ rows j
 // at a time, so that every K and V element it loads serves RQ rows; each
 // output is still accumulated in the order of its own sum.
-constexpr int RQ = 4;
+// Forward: 16 warps per block; 4 rows per warp (2 at width 256, for shared
+// memory).
+constexpr int AWF = 16;
+template <int A>
+__host__ __device__ constexpr int fwd_rows() { return A > 128 ? 2 : 4; }
 
 template <int A>
-__global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
+__global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
   constexpr bool VG = A > 128;
+  constexpr int AW = AWF, RQ = fwd_rows<A>();
   extern __shared__ float sm[];
   float* Ks = sm;                                   // [NP][A+1]
   float* Vs = Ks + NP * (A + 1);                    // [NP][A] (not with VG)
@@ -669,15 +673,20 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_fwd_f32(AttnArgs a, float s
 }
 
 // Adjoint of one attention layer for one centre.  Pass 1 (a warp per RB rows
-// j) recomputes l, A and P, forms dP = dO_j . V_k, the softmax adjoint and
+// j) recomputes l, A and P, forms dP = dO_j . V_k (at width 256 in a pass 0
+// with V in shared memory, into the scratch slot), the softmax adjoint and
 // dQ_j, and the row / column parts of dE/dw and dE/drhat.  Pass 2 (a warp per
 // RB keys k) forms dK_k = sum_j dS_jk Q_j and dV_k = sum_j P_jk dO_j from dS
 // and P that pass 1 left (transposed) in this block's global scratch slot.
-// Every K, V, Q and dO element a warp loads serves its RB rows or keys.
+// Every K, V, Q and dO element a warp loads serves its RB rows or keys; 16
+// warps per block (8 at width 256, for shared memory).
 template <int A>
-__global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
+__host__ __device__ constexpr int bwd_warps() { return A > 128 ? 8 : 16; }
+
+template <int A>
+__global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArgs a, float scale) {
   constexpr bool VG = A > 128;  // V and dO from global memory, as in the forward
-  constexpr int RB = VG ? 2 : 4;
+  constexpr int AW = bwd_warps<A>(), RB = 2;
   extern __shared__ float sm[];
   float* Ks = sm;                                   // [NP][A+1]   pass 2: Q
   float* Vs = Ks + NP * (A + 1);                    // [NP][A+1]   pass 2: dO (not with VG)
@@ -692,11 +701,51 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int FQ = A / 32;
   const int ld = 3 * A;
-  float* dST = a.scratch + (size_t)blockIdx.x * 2 * NP * NP;  // [NP k][NP j]
+  float* dST = a.scratch + (size_t)blockIdx.x * 3 * NP * NP;  // [NP k][NP j]
   float* PT = dST + NP * NP;
+  float* dPs = PT + NP * NP;  // VG: [NP j][NP k] dP = dO V^T from pass 0
   for (int atom = blockIdx.x; atom < a.n; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
+    if (VG) {
+      // pass 0: V into Ks, dP_jk = dO_j . V_k for every live row
+      for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
+        const int r = idx / A, f = idx % A;
+        Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
+      }
+      __syncthreads();
+      for (int j0 = warp * RB; j0 < nn; j0 += AW * RB) {
+        float* dq = dorow + warp * RB * A;
+        for (int t = lane; t < RB * A; t += 32) {
+          const int r = t / A, f = t % A;
+          dq[t] = j0 + r < nn ? a.dO[(base + j0 + r) * A + f] : 0.f;
+        }
+        __syncwarp();
+        float d[RB][4];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) d[r][m] = 0.f;
+        for (int f = 0; f < A; ++f) {
+          float vf[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) vf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const float gf = dq[r * A + f];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) d[r][m] = fmaf(gf, vf[m], d[r][m]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (j0 + r < nn)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) dPs[(size_t)(j0 + r) * NP + lane + 32 * m] = d[r][m];
+        __syncwarp();
+      }
+      __syncthreads();
+    }
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
       Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
@@ -718,7 +767,7 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
         const int r = t / A, f = t % A;
         const bool live = j0 + r < nn;
         q[t] = live ? a.QKV[(base + j0 + r) * ld + f] : 0.f;
-        dq[t] = live ? a.dO[(base + j0 + r) * A + f] : 0.f;
+        if (!VG) dq[t] = live ? a.dO[(base + j0 + r) * A + f] : 0.f;
       }
       __syncwarp();
       float s[RB][4], dp[RB][4];
@@ -738,28 +787,13 @@ __global__ void __launch_bounds__(32 * AW, 1) k_attn_bwd_f32(AttnArgs a, float s
             for (int m = 0; m < 4; ++m) s[r][m] = fmaf(qf, kf[m], s[r][m]);
           }
         }
-        // dp = dO_j . V_k: each lane walks its keys' rows of V (rows past nnei
-        // are never read)
+        // dp from pass 0 (the scratch rows of this block, written by this
+        // block before the barrier)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = lane + 32 * m;
-          if (k < nn) {
-            const float4* v4 = reinterpret_cast<const float4*>(a.QKV + (base + k) * ld + 2 * A);
-            float d[RB];
+        for (int r = 0; r < RB; ++r)
+          if (j0 + r < nn)
 #pragma unroll
-            for (int r = 0; r < RB; ++r) d[r] = 0.f;
-            for (int f4 = 0; f4 < A / 4; ++f4) {
-              const float4 vv = v4[f4];
-#pragma unroll
-              for (int r = 0; r < RB; ++r) {
-                const float4 gg = reinterpret_cast<const float4*>(dq + r * A)[f4];
-                d[r] = fmaf(gg.x, vv.x, fmaf(gg.y, vv.y, fmaf(gg.z, vv.z, fmaf(gg.w, vv.w, d[r]))));
-              }
-            }
-#pragma unroll
-            for (int r = 0; r < RB; ++r) dp[r][m] = d[r];
-          }
-        }
+            for (int m = 0; m < 4; ++m) dp[r][m] = dPs[(size_t)(j0 + r) * NP + lane + 32 * m];
       } else {
         for (int f = 0; f < A; ++f) {
           float kf[4], vf[4];
@@ -972,12 +1006,13 @@ static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
   const int cap = bwd ? a.scratch_blocks : sm_count();
   const int grid = a.n < cap ? a.n : cap;
   if (!bwd) {
-    const size_t smem = sizeof(float) * (NP * (A + 1) + (VG ? 0 : NP * A) + 4 * NP + AW * RQ * A + AW * RQ * NP) +
+    constexpr int RQ = fwd_rows<A>();
+    const size_t smem = sizeof(float) * (NP * (A + 1) + (VG ? 0 : NP * A) + 4 * NP + AWF * RQ * A + AWF * RQ * NP) +
                         sizeof(double) * NP;
     cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_attn_fwd_f32<A><<<grid, 32 * AW, smem, st>>>(a, scale);
+    k_attn_fwd_f32<A><<<grid, 32 * AWF, smem, st>>>(a, scale);
   } else {
-    constexpr int RB = VG ? 2 : 4;  // rows / keys per warp of the adjoint
+    constexpr int RB = 2, AW = bwd_warps<A>();  // rows / keys per warp, warps of the adjoint
     const size_t smem = sizeof(float) * (NP * (A + 1) * (VG ? 1 : 2) + 8 * NP + 2 * AW * RB * A + AW * RB * NP +
                                          4 * AW * NP) +
                         sizeof(double) * NP;
