@@ -546,8 +546,9 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
   constexpr bool VG = A > 128;
   constexpr int AW = AWF, RQ = fwd_rows<A>();
   extern __shared__ float sm[];
-  float* Ks = sm;                                   // [NP][A+1]
-  float* Vs = Ks + NP * (A + 1);                    // [NP][A] (not with VG)
+  constexpr int KS = A + 4;                         // K row stride: 16-byte rows, 4-way LDS.128 at most
+  float* Ks = sm;                                   // [NP][KS]
+  float* Vs = Ks + NP * KS;                         // [NP][A] (not with VG)
   float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * A));  // [NP]
   float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][RQ][A]
   float* prow = qrow + AW * RQ * A;                 // [AW][RQ][NP]
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
     const size_t base = (size_t)atom * NP;
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
-      Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
+      Ks[r * KS + f] = a.QKV[(base + r) * ld + A + f];
       if (!VG) Vs[r * A + f] = a.QKV[(base + r) * ld + 2 * A + f];
     }
     for (int r = threadIdx.x; r < NP; r += blockDim.x) {
@@ -584,15 +585,21 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
       for (int r = 0; r < RQ; ++r)
 #pragma unroll
         for (int m = 0; m < 4; ++m) s[r][m] = 0.f;
-      for (int f = 0; f < A; ++f) {
-        float kf[4];
+      // four features per shared load (the sums still run over f in order)
+      for (int f = 0; f < A; f += 4) {
+        float4 kf[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) kf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
+        for (int m = 0; m < 4; ++m) kf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
 #pragma unroll
         for (int r = 0; r < RQ; ++r) {
-          const float qf = q[r * A + f];
+          const float4 qf = *reinterpret_cast<const float4*>(q + r * A + f);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) s[r][m] = fmaf(qf, kf[m], s[r][m]);
+          for (int m = 0; m < 4; ++m) {
+            s[r][m] = fmaf(qf.x, kf[m].x, s[r][m]);
+            s[r][m] = fmaf(qf.y, kf[m].y, s[r][m]);
+            s[r][m] = fmaf(qf.z, kf[m].z, s[r][m]);
+            s[r][m] = fmaf(qf.w, kf[m].w, s[r][m]);
+          }
         }
       }
       float* p = prow + warp * RQ * NP;
@@ -647,7 +654,28 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
       for (int r = 0; r < RQ; ++r)
 #pragma unroll
         for (int m = 0; m < FQ; ++m) acc[r][m] = 0.f;
-      for (int k = 0; k < nn; ++k) {
+      // four keys per load of P; keys past nnei are never touched (their V
+      // rows hold nothing of this atom)
+      const int nn4 = nn & ~3;
+      for (int k = 0; k < nn4; k += 4) {
+        float4 p4[RQ];
+#pragma unroll
+        for (int r = 0; r < RQ; ++r) p4[r] = *reinterpret_cast<const float4*>(p + r * NP + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float* vk = VG ? a.QKV + (base + k + u) * ld + 2 * A : Vs + (k + u) * A;
+          float vv[FQ];
+#pragma unroll
+          for (int m = 0; m < FQ; ++m) vv[m] = vk[lane + 32 * m];
+#pragma unroll
+          for (int r = 0; r < RQ; ++r) {
+            const float pk = u == 0 ? p4[r].x : u == 1 ? p4[r].y : u == 2 ? p4[r].z : p4[r].w;
+#pragma unroll
+            for (int m = 0; m < FQ; ++m) acc[r][m] = fmaf(pk, vv[m], acc[r][m]);
+          }
+        }
+      }
+      for (int k = nn4; k < nn; ++k) {
         const float* vk = VG ? a.QKV + (base + k) * ld + 2 * A : Vs + k * A;
         float vv[FQ];
 #pragma unroll
@@ -1007,7 +1035,7 @@ static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
   const int grid = a.n < cap ? a.n : cap;
   if (!bwd) {
     constexpr int RQ = fwd_rows<A>();
-    const size_t smem = sizeof(float) * (NP * (A + 1) + (VG ? 0 : NP * A) + 4 * NP + AWF * RQ * A + AWF * RQ * NP) +
+    const size_t smem = sizeof(float) * (NP * (A + 4) + (VG ? 0 : NP * A) + 4 * NP + AWF * RQ * A + AWF * RQ * NP) +
                         sizeof(double) * NP;
     cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_attn_fwd_f32<A><<<grid, 32 * AWF, smem, st>>>(a, scale);
