@@ -716,9 +716,10 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
   constexpr bool VG = A > 128;  // V and dO from global memory, as in the forward
   constexpr int AW = bwd_warps<A>(), RB = 2;
   extern __shared__ float sm[];
-  float* Ks = sm;                                   // [NP][A+1]   pass 2: Q
-  float* Vs = Ks + NP * (A + 1);                    // [NP][A+1]   pass 2: dO (not with VG)
-  float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * (A + 1)));  // [NP]
+  constexpr int KS = A + 4;                         // row stride: 16-byte rows for 128-bit loads
+  float* Ks = sm;                                   // [NP][KS]   pass 0: V, pass 2: Q
+  float* Vs = Ks + NP * KS;                         // [NP][KS]   pass 2: dO (not with VG)
+  float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * KS));  // [NP]
   float4* rowg = rws + NP;                          // [NP] (d rhat_j, d w_j) row parts
   float* qrow = reinterpret_cast<float*>(rowg + NP);  // [AW][RB][A]
   float* dorow = qrow + AW * RB * A;                // [AW][RB][A]
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
       // pass 0: V into Ks, dP_jk = dO_j . V_k for every live row
       for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
         const int r = idx / A, f = idx % A;
-        Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
+        Ks[r * KS + f] = a.QKV[(base + r) * ld + 2 * A + f];
       }
       __syncthreads();
       for (int j0 = warp * RB; j0 < nn; j0 += AW * RB) {
@@ -754,15 +755,20 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
         for (int r = 0; r < RB; ++r)
 #pragma unroll
           for (int m = 0; m < 4; ++m) d[r][m] = 0.f;
-        for (int f = 0; f < A; ++f) {
-          float vf[4];
+        for (int f = 0; f < A; f += 4) {
+          float4 vf[4];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) vf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
+          for (int m = 0; m < 4; ++m) vf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
 #pragma unroll
           for (int r = 0; r < RB; ++r) {
-            const float gf = dq[r * A + f];
+            const float4 gf = *reinterpret_cast<const float4*>(dq + r * A + f);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) d[r][m] = fmaf(gf, vf[m], d[r][m]);
+            for (int m = 0; m < 4; ++m) {
+              d[r][m] = fmaf(gf.x, vf[m].x, d[r][m]);
+              d[r][m] = fmaf(gf.y, vf[m].y, d[r][m]);
+              d[r][m] = fmaf(gf.z, vf[m].z, d[r][m]);
+              d[r][m] = fmaf(gf.w, vf[m].w, d[r][m]);
+            }
           }
         }
 #pragma unroll
@@ -776,8 +782,8 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
     }
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
-      Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + A + f];
-      if (!VG) Vs[r * (A + 1) + f] = a.QKV[(base + r) * ld + 2 * A + f];
+      Ks[r * KS + f] = a.QKV[(base + r) * ld + A + f];
+      if (!VG) Vs[r * KS + f] = a.QKV[(base + r) * ld + 2 * A + f];
     }
     for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -804,15 +810,20 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
 #pragma unroll
         for (int m = 0; m < 4; ++m) { s[r][m] = 0.f; dp[r][m] = 0.f; }
       if (VG) {
-        for (int f = 0; f < A; ++f) {
-          float kf[4];
+        for (int f = 0; f < A; f += 4) {
+          float4 kf[4];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) kf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
+          for (int m = 0; m < 4; ++m) kf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
 #pragma unroll
           for (int r = 0; r < RB; ++r) {
-            const float qf = q[r * A + f];
+            const float4 qf = *reinterpret_cast<const float4*>(q + r * A + f);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) s[r][m] = fmaf(qf, kf[m], s[r][m]);
+            for (int m = 0; m < 4; ++m) {
+              s[r][m] = fmaf(qf.x, kf[m].x, s[r][m]);
+              s[r][m] = fmaf(qf.y, kf[m].y, s[r][m]);
+              s[r][m] = fmaf(qf.z, kf[m].z, s[r][m]);
+              s[r][m] = fmaf(qf.w, kf[m].w, s[r][m]);
+            }
           }
         }
         // dp from pass 0 (the scratch rows of this block, written by this
@@ -823,20 +834,27 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
 #pragma unroll
             for (int m = 0; m < 4; ++m) dp[r][m] = dPs[(size_t)(j0 + r) * NP + lane + 32 * m];
       } else {
-        for (int f = 0; f < A; ++f) {
-          float kf[4], vf[4];
+        for (int f = 0; f < A; f += 4) {
+          float4 kf[4], vf[4];
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
-            kf[m] = Ks[(lane + 32 * m) * (A + 1) + f];
-            vf[m] = Vs[(lane + 32 * m) * (A + 1) + f];
+            kf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
+            vf[m] = *reinterpret_cast<const float4*>(Vs + (lane + 32 * m) * KS + f);
           }
 #pragma unroll
           for (int r = 0; r < RB; ++r) {
-            const float qf = q[r * A + f], gf = dq[r * A + f];
+            const float4 qf = *reinterpret_cast<const float4*>(q + r * A + f);
+            const float4 gf = *reinterpret_cast<const float4*>(dq + r * A + f);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-              s[r][m] = fmaf(qf, kf[m], s[r][m]);
-              dp[r][m] = fmaf(gf, vf[m], dp[r][m]);
+              s[r][m] = fmaf(qf.x, kf[m].x, s[r][m]);
+              s[r][m] = fmaf(qf.y, kf[m].y, s[r][m]);
+              s[r][m] = fmaf(qf.z, kf[m].z, s[r][m]);
+              s[r][m] = fmaf(qf.w, kf[m].w, s[r][m]);
+              dp[r][m] = fmaf(gf.x, vf[m].x, dp[r][m]);
+              dp[r][m] = fmaf(gf.y, vf[m].y, dp[r][m]);
+              dp[r][m] = fmaf(gf.z, vf[m].z, dp[r][m]);
+              dp[r][m] = fmaf(gf.w, vf[m].w, dp[r][m]);
             }
           }
         }
@@ -918,7 +936,7 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
       for (int k = 0; k < nn; ++k) {
         float kk[FQ];
 #pragma unroll
-        for (int m = 0; m < FQ; ++m) kk[m] = Ks[k * (A + 1) + lane + 32 * m];
+        for (int m = 0; m < FQ; ++m) kk[m] = Ks[k * KS + lane + 32 * m];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
           const float d = pr[r * NP + k];
@@ -937,8 +955,8 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
     // pass 2: Q into Ks, dO into Vs (dO from global memory with VG)
     for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
       const int r = idx / A, f = idx % A;
-      Ks[r * (A + 1) + f] = a.QKV[(base + r) * ld + f];
-      if (!VG) Vs[r * (A + 1) + f] = a.dO[(base + r) * A + f];
+      Ks[r * KS + f] = a.QKV[(base + r) * ld + f];
+      if (!VG) Vs[r * KS + f] = a.dO[(base + r) * A + f];
     }
     __syncthreads();
     for (int k0 = warp * RB; k0 < NP; k0 += AW * RB) {
@@ -963,11 +981,11 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
         const int cnt = (nn - jb) < 32 ? (nn - jb) : 32;
         for (int t = 0; t < cnt; ++t) {
           const int j = jb + t;
-          const float* doj = VG ? a.dO + (base + j) * A : Vs + j * (A + 1);
+          const float* doj = VG ? a.dO + (base + j) * A : Vs + j * KS;
           float qv[FQ], dv[FQ];
 #pragma unroll
           for (int m = 0; m < FQ; ++m) {
-            qv[m] = Ks[j * (A + 1) + lane + 32 * m];
+            qv[m] = Ks[j * KS + lane + 32 * m];
             dv[m] = doj[lane + 32 * m];
           }
 #pragma unroll
@@ -1041,7 +1059,7 @@ static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
     k_attn_fwd_f32<A><<<grid, 32 * AWF, smem, st>>>(a, scale);
   } else {
     constexpr int RB = 2, AW = bwd_warps<A>();  // rows / keys per warp, warps of the adjoint
-    const size_t smem = sizeof(float) * (NP * (A + 1) * (VG ? 1 : 2) + 8 * NP + 2 * AW * RB * A + AW * RB * NP +
+    const size_t smem = sizeof(float) * (NP * (A + 4) * (VG ? 1 : 2) + 8 * NP + 2 * AW * RB * A + AW * RB * NP +
                                          4 * AW * NP) +
                         sizeof(double) * NP;
     cudaFuncSetAttribute(k_attn_bwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
