@@ -1,7 +1,10 @@
 """Pin of the oracle's student-loss gradient (double backward through the
 forces) against central finite differences of the loss in weight space."""
 
+import dataclasses
+
 import numpy as np
+import pytest
 
 import synth
 import oracle
@@ -9,8 +12,9 @@ from oracle import OracleModel
 from oracle.student import loss_and_grad, trainable_names
 
 
-def test_student_loss_gradient_matches_weight_space_differences():
-    cfg = synth.STUDENT_CONFIG
+@pytest.mark.parametrize("mode", ["strip", "concat"])
+def test_student_loss_gradient_matches_weight_space_differences(mode):
+    cfg = dataclasses.replace(synth.STUDENT_CONFIG, tebd_input_mode=mode)
     w = synth.make_weights(cfg, seed=3, bias_scale=0.1)
     coord, atype, box = synth.isolated_cluster(seed=9, natoms=10)
     rng = np.random.default_rng(0)
