@@ -535,6 +535,46 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 // read from global memory (through L1) instead (VG).  A warp takes RQ rows j
 // at a time, so that every K and V element it loads serves RQ rows; each
 // output is still accumulated in the order of its own sum.
+// Smooth logits l'_jk = (l_jk + S) w_j w_k carry the shift S = 20, whose
+// FP32 spacing (2e-6) is far coarser than the logit differences that matter.
+// They are evaluated as unevaluated float pairs (h + l): l + S exactly by a
+// two-sum, the product of the switch weights (FP64, held as float pairs) and
+// the final product with their rounding errors by FMA; ~44 bits, without the
+// FP64 pipe (narrow on this GPU).  Only differences to the row maximum are
+// used, as floats.
+__device__ __forceinline__ float2 split_pair(double w) {
+  const float h = (float)w;
+  return make_float2(h, (float)(w - (double)h));
+}
+
+__device__ __forceinline__ float2 smooth_logit(float t, float S, float2 wj, float2 wk) {
+  const float uh = t + S;
+  const float bb = uh - t;
+  const float ul = (t - (uh - bb)) + (S - bb);
+  const float ph = wj.x * wk.x;
+  float pl = fmaf(wj.x, wk.x, -ph);
+  pl = fmaf(wj.x, wk.y, pl);
+  pl = fmaf(wj.y, wk.x, pl);
+  const float hh = uh * ph;
+  float hl = fmaf(uh, ph, -hh);
+  hl = fmaf(uh, pl, hl);
+  hl = fmaf(ul, ph, hl);
+  return make_float2(hh, hl);
+}
+
+// the largest pair (ordered by h, then l) over the warp; every lane gets the same
+__device__ __forceinline__ float2 warp_max_pair(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, v.x, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, v.y, o);
+    if (oh > v.x || (oh == v.x && ol > v.y)) v = make_float2(oh, ol);
+  }
+  return v;
+}
+
+__device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+
 // Forward: 16 warps per block; 4 rows per warp (2 at width 256, for shared
 // memory).
 constexpr int AWF = 16;
@@ -552,7 +592,7 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
   float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * A));  // [NP]
   float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][RQ][A]
   float* prow = qrow + AW * RQ * A;                 // [AW][RQ][NP]
-  double* w64s = reinterpret_cast<double*>(prow + AW * RQ * NP);  // [NP]
+  float2* w2s = reinterpret_cast<float2*>(prow + AW * RQ * NP);  // [NP] switch weights as float pairs
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int FQ = A / 32;
   const int ld = 3 * A;
@@ -566,7 +606,7 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
     }
     for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-      w64s[r] = r < nn ? a.w64[base + r] : 0.0;
+      w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
     __syncthreads();
     for (int j0 = warp * RQ; j0 < NP; j0 += AW * RQ) {
@@ -612,27 +652,25 @@ __global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float 
           continue;
         }
         const float4 rj = rws[j];
-        // smooth logits (l + S) w_j w_k (the constant -S of every logit of a
-        // row cancels in the softmax) in FP64: S = 20 leaves the FP32 spacing
-        // near the logits at 2e-6, far coarser than the logit differences
-        // that matter
-        const double wj = w64s[j];
-        double lp[4], mx = -1e300;
+        // smooth logits (l + S) w_j w_k as float pairs (the constant -S of
+        // every logit of a row cancels in the softmax)
+        const float2 wj = w2s[j];
+        float2 lp[4], mx = make_float2(-3.0e38f, 0.f);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const int k = lane + 32 * m;
-          lp[m] = 0.0;
+          lp[m] = make_float2(-3.0e38f, 0.f);
           if (k < nn) {
-            lp[m] = ((double)(s[r][m] * scale) + (double)a.shift) * (wj * w64s[k]);
-            mx = fmax(mx, lp[m]);
+            lp[m] = smooth_logit(s[r][m] * scale, a.shift, wj, w2s[k]);
+            if (lp[m].x > mx.x || (lp[m].x == mx.x && lp[m].y > mx.y)) mx = lp[m];
           }
         }
-        mx = warp_max_d(mx);
+        mx = warp_max_pair(mx);
         float e[4], sum = 0.f;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const int k = lane + 32 * m;
-          e[m] = k < nn ? expf((float)(lp[m] - mx)) : 0.f;
+          e[m] = k < nn ? expf(pair_diff(lp[m], mx)) : 0.f;
           sum += e[m];
         }
         sum = warp_sum(sum);
@@ -726,7 +764,7 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
   float* prow = dorow + AW * RB * A;                // [AW][RB][NP]
   float* colw = prow + AW * RB * NP;                // [AW][NP]
   float* colr = colw + AW * NP;                     // [AW][NP][3]
-  double* w64s = reinterpret_cast<double*>(colr + 3 * AW * NP);  // [NP]
+  float2* w2s = reinterpret_cast<float2*>(colr + 3 * AW * NP);  // [NP] switch weights as float pairs
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int FQ = A / 32;
   const int ld = 3 * A;
@@ -787,7 +825,7 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
     }
     for (int r = threadIdx.x; r < NP; r += blockDim.x) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-      w64s[r] = r < nn ? a.w64[base + r] : 0.0;
+      w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
     for (int t = threadIdx.x; t < AW * NP; t += blockDim.x) {
       colw[t] = 0.f;
@@ -869,9 +907,9 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
           continue;
         }
         const float4 rj = rws[j];
-        const double wj = w64s[j];
+        const float2 wj = w2s[j];
         float l[4], ww[4], c[4];
-        double lp[4], mx = -1e300;
+        float2 lp[4], mx = make_float2(-3.0e38f, 0.f);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const int k = lane + 32 * m;
@@ -879,17 +917,17 @@ __global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArg
           ww[m] = rj.w * rk.w;
           c[m] = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
           l[m] = s[r][m] * scale;
-          lp[m] = 0.0;
+          lp[m] = make_float2(-3.0e38f, 0.f);
           if (k < nn) {
-            lp[m] = ((double)l[m] + (double)a.shift) * (wj * w64s[k]);  // as in the forward kernel
-            mx = fmax(mx, lp[m]);
+            lp[m] = smooth_logit(l[m], a.shift, wj, w2s[k]);  // as in the forward kernel
+            if (lp[m].x > mx.x || (lp[m].x == mx.x && lp[m].y > mx.y)) mx = lp[m];
           }
         }
-        mx = warp_max_d(mx);
+        mx = warp_max_pair(mx);
         float e[4], sum = 0.f;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          e[m] = (lane + 32 * m) < nn ? expf((float)(lp[m] - mx)) : 0.f;
+          e[m] = (lane + 32 * m) < nn ? expf(pair_diff(lp[m], mx)) : 0.f;
           sum += e[m];
         }
         sum = warp_sum(sum);
