@@ -531,10 +531,6 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 //   l_jk = Q_j.K_k / sqrt(A);  l'_jk = (l_jk + S) w_j w_k - S
 //   A_jk = softmax_k(l'_jk);   P_jk = A_jk w_j w_k (rhat_j . rhat_k);  O = P V
 
-// Above an attention width of 128, K alone fills shared memory: V is then
-// read from global memory (through L1) instead (VG).  A warp takes RQ rows j
-// at a time, so that every K and V element it loads serves RQ rows; each
-// output is still accumulated in the order of its own sum.
 // Smooth logits l'_jk = (l_jk + S) w_j w_k carry the shift S = 20, whose
 // FP32 spacing (2e-6) is far coarser than the logit differences that matter.
 // They are evaluated as unevaluated float pairs (h + l): l + S exactly by a
@@ -575,166 +571,157 @@ __device__ __forceinline__ float2 warp_max_pair(float2 v) {
 
 __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
-// Forward: 16 warps per block; 4 rows per warp (2 at width 256, for shared
-// memory).
-constexpr int AWF = 16;
-template <int A>
-__host__ __device__ constexpr int fwd_rows() { return A > 128 ? 2 : 4; }
+// Forward, register-tiled: 256 threads as a 16 x 16 grid.  Thread (ty, tx)
+// owns rows 8 ty .. 8 ty + 7 and keys 8 tx .. 8 tx + 7 of S (128 x 128), then
+// rows 8 ty .. and features 8 tx .. of each 128-feature part of O.  Q and K
+// pass through shared memory feature-major, 128 features at a time; P stays
+// row-major and V comes in 128-feature parts, key-major.  S sums over the
+// features and O over the keys in order, as a plain loop would.
+constexpr int FT = 256;        // threads of the forward
+constexpr int TLD = NP + 4;    // row stride of its shared tiles (16-byte rows)
 
 template <int A>
-__global__ void __launch_bounds__(32 * AWF, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
-  constexpr bool VG = A > 128;
-  constexpr int AW = AWF, RQ = fwd_rows<A>();
+__global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
   extern __shared__ float sm[];
-  constexpr int KS = A + 4;                         // K row stride: 16-byte rows, 4-way LDS.128 at most
-  float* Ks = sm;                                   // [NP][KS]
-  float* Vs = Ks + NP * KS;                         // [NP][A] (not with VG)
-  float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * A));  // [NP]
-  float* qrow = reinterpret_cast<float*>(rws + NP);      // [AW][RQ][A]
-  float* prow = qrow + AW * RQ * A;                 // [AW][RQ][NP]
-  float2* w2s = reinterpret_cast<float2*>(prow + AW * RQ * NP);  // [NP] switch weights as float pairs
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int FQ = A / 32;
+  float* X = sm;                 // [128][TLD]: Q chunk (feature-major), then P (row-major)
+  float* Y = X + 128 * TLD;      // [128][TLD]: K chunk (feature-major), then a part of V (key-major)
+  float4* rws = reinterpret_cast<float4*>(Y + 128 * TLD);  // [NP]
+  float2* w2s = reinterpret_cast<float2*>(rws + NP);       // [NP] switch weights as float pairs
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int ld = 3 * A;
   for (int atom = blockIdx.x; atom < a.n; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
-    for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
-      const int r = idx / A, f = idx % A;
-      Ks[r * KS + f] = a.QKV[(base + r) * ld + A + f];
-      if (!VG) Vs[r * A + f] = a.QKV[(base + r) * ld + 2 * A + f];
-    }
-    for (int r = threadIdx.x; r < NP; r += blockDim.x) {
+    __syncthreads();  // the previous atom is done with every shared array
+    for (int r = tid; r < NP; r += FT) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
       w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
-    __syncthreads();
-    for (int j0 = warp * RQ; j0 < NP; j0 += AW * RQ) {
-      if (j0 >= nn) {
-        for (int t = lane; t < RQ * A; t += 32) a.O[(base + j0) * A + t] = 0.f;
-        continue;
+    float s[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) s[i][jj] = 0.f;
+    const bool live = 8 * ty < nn && 8 * tx < nn;
+    for (int c0 = 0; c0 < A; c0 += 128) {
+      if (c0 > 0) __syncthreads();  // the previous chunk's products are done
+      // row j, features f .. f + 3 of Q and K -> X[f + u][j], Y[f + u][j]
+      for (int idx = tid; idx < NP * 32; idx += FT) {
+        const int j = idx & (NP - 1), f = 4 * (idx >> 7);
+        float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
+        if (j < nn) {
+          qv = *reinterpret_cast<const float4*>(a.QKV + (base + j) * ld + c0 + f);
+          kv = *reinterpret_cast<const float4*>(a.QKV + (base + j) * ld + A + c0 + f);
+        }
+        X[(f + 0) * TLD + j] = qv.x; X[(f + 1) * TLD + j] = qv.y;
+        X[(f + 2) * TLD + j] = qv.z; X[(f + 3) * TLD + j] = qv.w;
+        Y[(f + 0) * TLD + j] = kv.x; Y[(f + 1) * TLD + j] = kv.y;
+        Y[(f + 2) * TLD + j] = kv.z; Y[(f + 3) * TLD + j] = kv.w;
       }
-      float* q = qrow + warp * RQ * A;
-      for (int t = lane; t < RQ * A; t += 32) {
-        const int r = t / A, f = t % A;
-        q[t] = j0 + r < nn ? a.QKV[(base + j0 + r) * ld + f] : 0.f;
-      }
-      __syncwarp();
-      float s[RQ][4];
+      __syncthreads();
+      if (live) {
+        for (int f = 0; f < 128; ++f) {
+          const float4 a0 = *reinterpret_cast<const float4*>(X + f * TLD + 8 * ty);
+          const float4 a1 = *reinterpret_cast<const float4*>(X + f * TLD + 8 * ty + 4);
+          const float4 b0 = *reinterpret_cast<const float4*>(Y + f * TLD + 8 * tx);
+          const float4 b1 = *reinterpret_cast<const float4*>(Y + f * TLD + 8 * tx + 4);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int r = 0; r < RQ; ++r)
+          for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) s[r][m] = 0.f;
-      // four features per shared load (the sums still run over f in order)
-      for (int f = 0; f < A; f += 4) {
-        float4 kf[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) kf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
-#pragma unroll
-        for (int r = 0; r < RQ; ++r) {
-          const float4 qf = *reinterpret_cast<const float4*>(q + r * A + f);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            s[r][m] = fmaf(qf.x, kf[m].x, s[r][m]);
-            s[r][m] = fmaf(qf.y, kf[m].y, s[r][m]);
-            s[r][m] = fmaf(qf.z, kf[m].z, s[r][m]);
-            s[r][m] = fmaf(qf.w, kf[m].w, s[r][m]);
-          }
+            for (int jj = 0; jj < 8; ++jj) s[i][jj] = fmaf(av[i], bv[jj], s[i][jj]);
         }
       }
-      float* p = prow + warp * RQ * NP;
-#pragma unroll
-      for (int r = 0; r < RQ; ++r) {
-        const int j = j0 + r;
-        if (j >= nn) {  // uniform over the warp
-#pragma unroll
-          for (int m = 0; m < 4; ++m) p[r * NP + lane + 32 * m] = 0.f;
-          continue;
-        }
-        const float4 rj = rws[j];
-        // smooth logits (l + S) w_j w_k as float pairs (the constant -S of
-        // every logit of a row cancels in the softmax)
-        const float2 wj = w2s[j];
-        float2 lp[4], mx = make_float2(-3.0e38f, 0.f);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = lane + 32 * m;
-          lp[m] = make_float2(-3.0e38f, 0.f);
-          if (k < nn) {
-            lp[m] = smooth_logit(s[r][m] * scale, a.shift, wj, w2s[k]);
-            if (lp[m].x > mx.x || (lp[m].x == mx.x && lp[m].y > mx.y)) mx = lp[m];
-          }
-        }
-        mx = warp_max_pair(mx);
-        float e[4], sum = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = lane + 32 * m;
-          e[m] = k < nn ? expf(pair_diff(lp[m], mx)) : 0.f;
-          sum += e[m];
-        }
-        sum = warp_sum(sum);
-        const float inv = 1.0f / sum;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = lane + 32 * m;
-          float pv = 0.f;
-          if (k < nn) {
-            const float4 rk = rws[k];
-            pv = e[m] * inv * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z);
-          }
-          p[r * NP + k] = pv;
-        }
-      }
-      __syncwarp();
-      float acc[RQ][FQ];
-#pragma unroll
-      for (int r = 0; r < RQ; ++r)
-#pragma unroll
-        for (int m = 0; m < FQ; ++m) acc[r][m] = 0.f;
-      // four keys per load of P; keys past nnei are never touched (their V
-      // rows hold nothing of this atom)
-      const int nn4 = nn & ~3;
-      for (int k = 0; k < nn4; k += 4) {
-        float4 p4[RQ];
-#pragma unroll
-        for (int r = 0; r < RQ; ++r) p4[r] = *reinterpret_cast<const float4*>(p + r * NP + k);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float* vk = VG ? a.QKV + (base + k + u) * ld + 2 * A : Vs + (k + u) * A;
-          float vv[FQ];
-#pragma unroll
-          for (int m = 0; m < FQ; ++m) vv[m] = vk[lane + 32 * m];
-#pragma unroll
-          for (int r = 0; r < RQ; ++r) {
-            const float pk = u == 0 ? p4[r].x : u == 1 ? p4[r].y : u == 2 ? p4[r].z : p4[r].w;
-#pragma unroll
-            for (int m = 0; m < FQ; ++m) acc[r][m] = fmaf(pk, vv[m], acc[r][m]);
-          }
-        }
-      }
-      for (int k = nn4; k < nn; ++k) {
-        const float* vk = VG ? a.QKV + (base + k) * ld + 2 * A : Vs + k * A;
-        float vv[FQ];
-#pragma unroll
-        for (int m = 0; m < FQ; ++m) vv[m] = vk[lane + 32 * m];
-#pragma unroll
-        for (int r = 0; r < RQ; ++r) {
-          const float pk = p[r * NP + k];
-#pragma unroll
-          for (int m = 0; m < FQ; ++m) acc[r][m] = fmaf(pk, vv[m], acc[r][m]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < RQ; ++r) {
-        float* o = a.O + (base + j0 + r) * A;
-        const bool live = j0 + r < nn;
-#pragma unroll
-        for (int m = 0; m < FQ; ++m) o[lane + 32 * m] = live ? acc[r][m] : 0.f;
-      }
-      __syncwarp();
     }
-    __syncthreads();
+    __syncthreads();  // X and Y are free: P goes to X
+    // softmax per row over the 16 threads of a half warp (every lane takes
+    // part in the shuffles; rows and keys past nnei come out zero)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = 8 * ty + i;
+      const float4 rj = rws[j];
+      const float2 wj = w2s[j];
+      float2 lp[8], mx = make_float2(-3.0e38f, 0.f);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int k = 8 * tx + jj;
+        lp[jj] = make_float2(-3.0e38f, 0.f);
+        if (k < nn) {
+          lp[jj] = smooth_logit(s[i][jj] * scale, a.shift, wj, w2s[k]);
+          if (lp[jj].x > mx.x || (lp[jj].x == mx.x && lp[jj].y > mx.y)) mx = lp[jj];
+        }
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, mx.x, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, mx.y, o);
+        if (oh > mx.x || (oh == mx.x && ol > mx.y)) mx = make_float2(oh, ol);
+      }
+      float e[8], sum = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        e[jj] = 8 * tx + jj < nn ? expf(pair_diff(lp[jj], mx)) : 0.f;
+        sum += e[jj];
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      float pv[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int k = 8 * tx + jj;
+        pv[jj] = 0.f;
+        if (j < nn && k < nn) {
+          const float4 rk = rws[k];
+          pv[jj] = e[jj] * inv * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z);
+        }
+      }
+      *reinterpret_cast<float4*>(X + j * TLD + 8 * tx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      *reinterpret_cast<float4*>(X + j * TLD + 8 * tx + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
+    }
+    // O = P V, 128 features at a time
+    const int nn4 = (nn + 3) & ~3;
+    for (int c0 = 0; c0 < A; c0 += 128) {
+      if (c0 > 0) __syncthreads();  // the previous part's products are done
+      for (int idx = tid; idx < NP * 32; idx += FT) {
+        const int k = idx >> 5, f = 4 * (idx & 31);
+        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < nn) vv = *reinterpret_cast<const float4*>(a.QKV + (base + k) * ld + 2 * A + c0 + f);
+        *reinterpret_cast<float4*>(Y + k * TLD + f) = vv;
+      }
+      __syncthreads();  // P (first part) and this part of V are in place
+      float acc[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
+      if (8 * ty < nn) {
+        for (int k = 0; k < nn4; k += 4) {
+          float4 pa[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pa[i] = *reinterpret_cast<const float4*>(X + (8 * ty + i) * TLD + k);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 v0 = *reinterpret_cast<const float4*>(Y + (k + u) * TLD + 8 * tx);
+            const float4 v1 = *reinterpret_cast<const float4*>(Y + (k + u) * TLD + 8 * tx + 4);
+            const float vb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float pk = u == 0 ? pa[i].x : u == 1 ? pa[i].y : u == 2 ? pa[i].z : pa[i].w;
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(pk, vb[jj], acc[i][jj]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float* o = a.O + (base + 8 * ty + i) * A + c0 + 8 * tx;
+        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      }
+    }
   }
 }
 
@@ -1090,11 +1077,9 @@ static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
   const int cap = bwd ? a.scratch_blocks : sm_count();
   const int grid = a.n < cap ? a.n : cap;
   if (!bwd) {
-    constexpr int RQ = fwd_rows<A>();
-    const size_t smem = sizeof(float) * (NP * (A + 4) + (VG ? 0 : NP * A) + 4 * NP + AWF * RQ * A + AWF * RQ * NP) +
-                        sizeof(double) * NP;
+    const size_t smem = sizeof(float) * (2 * 128 * TLD + 4 * NP) + sizeof(float2) * NP;
     cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_attn_fwd_f32<A><<<grid, 32 * AWF, smem, st>>>(a, scale);
+    k_attn_fwd_f32<A><<<grid, FT, smem, st>>>(a, scale);
   } else {
     constexpr int RB = 2, AW = bwd_warps<A>();  // rows / keys per warp, warps of the adjoint
     const size_t smem = sizeof(float) * (NP * (A + 4) * (VG ? 1 : 2) + 8 * NP + 2 * AW * RB * A + AW * RB * NP +
