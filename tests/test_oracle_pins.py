@@ -232,13 +232,25 @@ def test_energy_continuous_across_cutoff(default_model):
 
 # ------------------------------------------------------------ special cases
 
-def test_two_atom_closed_form(rich_model):
+@pytest.mark.parametrize("stats", [False, True])
+def test_two_atom_closed_form(rich_model, stats):
     """One neighbour each: softmax over one key is 1 and the gate is 1, so a
-    layer is G <- G + LN((w^2 (G Wv + bv)) Wo + bo), and |R_j|^2 = 2 s^2 makes
-    D = 2 s^2 G (x) G_< / sel^2 (davg = 0, dstd = 1)."""
+    layer is G <- G + LN((w^2 (G Wv + bv)) Wo + bo), and with the single row
+    R_j = ((s - davg_0)/dstd_0, (s x/r - davg_1)/dstd_1, ...) of the centre's
+    type (Sec. II-B: R in invariant coordinates, normalised per centre type)
+    D = |R_j|^2 G (x) G_< / sel^2, where G's input is the normalised R_j0.
+    With ``stats`` the rich model's davg/dstd (non-zero, non-unit, different
+    for the two centre types) are kept; the pair lies along (1, 1, 1), so
+    the two centres see displacement components of opposite sign and a
+    wrong sign, scale, column or type index in the normalisation changes e."""
     cfg, w0, _ = rich_model
     w = dict(w0)
-    w["davg"] = np.zeros_like(w["davg"]); w["dstd"] = np.ones_like(w["dstd"])
+    if not stats:
+        w["davg"] = np.zeros_like(w["davg"]); w["dstd"] = np.ones_like(w["dstd"])
+    else:
+        # the pin needs every column's mean and spread to differ between types
+        assert np.all(np.abs(w["davg"][3] - w["davg"][1]) > 1e-3)
+        assert np.all(np.abs(w["dstd"][[1, 3]] - 1.0) > 1e-2)
     m = OracleModel.from_numpy(cfg, w)
     box = np.array([40.0, 40.0, 40.0])
     ta, tb = 3, 1
@@ -261,13 +273,15 @@ def test_two_atom_closed_form(rich_model):
         return x
 
     z = np.tanh(w["te_W"] + w["te_b"])
-    for centre, other in ((ta, tb), (tb, ta)):
-        G = net(np.array([s]), "em") * (1 + net(np.concatenate([z[other], z[centre]]), "tt"))
+    for centre, other, sign in ((ta, tb, 1.0), (tb, ta, -1.0)):
+        raw = np.array([s, sign * s / math.sqrt(3), sign * s / math.sqrt(3), sign * s / math.sqrt(3)])
+        Rj = (raw - w["davg"][centre]) / w["dstd"][centre]
+        G = net(np.array([Rj[0]]), "em") * (1 + net(np.concatenate([z[other], z[centre]]), "tt"))
         for l in range(cfg.attn_layers):
             y = (sw * sw * (G @ w[f"at{l}_Wv"] + w[f"at{l}_bv"])) @ w[f"at{l}_Wo"] + w[f"at{l}_bo"]
             zz = (y - y.mean()) / math.sqrt(y.var() + cfg.ln_eps)
             G = G + zz * w[f"at{l}_ln_g"] + w[f"at{l}_ln_b"]
-        D = 2 * s * s * np.outer(G, G[: cfg.axis]) / cfg.sel ** 2
+        D = float(Rj @ Rj) * np.outer(G, G[: cfg.axis]) / cfg.sel ** 2
         x = np.concatenate([D.ravel(), z[centre]])
         h = np.tanh(x @ w["fit_W0"] + w["fit_b0"])
         for l in (1, 2):
@@ -275,10 +289,12 @@ def test_two_atom_closed_form(rich_model):
         e_ref = cfg.out_scale * (h @ w["fit_W3"] + w["fit_b3"])[0] + w["ebias"][centre]
         idx = 0 if centre == ta else 1
         assert abs(e[idx] - e_ref) < 1e-12 * max(1.0, abs(e_ref))
-    # Newton's third law and a central force
+    # Newton's third law (translation invariance) always; a central force
+    # only without the per-column shift, which is not rotation invariant
     assert np.abs(F[0] + F[1]).max() < 1e-12
-    rhat = (coord[1] - coord[0]) / r
-    assert np.abs(F[0] - np.dot(F[0], rhat) * rhat).max() < 1e-12
+    if not stats:
+        rhat = (coord[1] - coord[0]) / r
+        assert np.abs(F[0] - np.dot(F[0], rhat) * rhat).max() < 1e-12
 
 
 def test_gated_attention_reduces_to_sdpa_and_layer_norm(rich_model):
