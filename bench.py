@@ -149,6 +149,8 @@ def run_reference(a):
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "atom-steps/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(dt for _, dt in vals) / len(vals),
+        "ms_per_step_is": f"the oracle's time for one {a.ref_sample}-centre sample, not for a whole {a.natoms}-atom step "
+                          f"(about {a.natoms / rate:.0f} s at this rate)",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload(a.natoms), "model": model_cfg(a.model)[1], "natoms": a.natoms},
         "cpu_baseline": {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
@@ -486,28 +488,31 @@ def run_ours(a):
         student = _student_line(dev, coord, atype, box,
                                 {p: job_rate(1, n, a.steps, rr["ms"] / 1e3) for p, rr in results.items()})
 
-    # parity of this run's forces against the FP64 oracle on sampled atoms
+    # parity of this run against the FP64 oracle over the whole box: every
+    # atomic energy, every force, the total energy and the virial
     parity = {}
     nl, nn = m.nlist_device(c, b)
     nn = nn.cpu().numpy()
     if rank == 0 and not a.no_parity:
-        from oracle import OracleModel, energy_force_virial, reverse_centres
+        from oracle import OracleModel, energy_force_virial
 
         om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=0))
-        rng = np.random.default_rng(7)
-        atoms = rng.choice(n, size=12, replace=False)
-        # the centres whose atomic energies depend on the sampled atoms: their
-        # e_i and the exact forces on the sampled atoms
-        cs = reverse_centres(coord, box, cfg.rcut, cfg.sel, atoms)
-        _, e_ref, f_ref, _ = energy_force_virial(om, coord, box, atype, centres=cs)
-        ref = f_ref[atoms]
+        t0 = time.perf_counter()
+        rE, e_ref, f_ref, w_ref = energy_force_virial(om, coord, box, atype)
+        t_oracle = time.perf_counter() - t0
         for p, mm in models.items():
-            _, Fp, _, ep = mm.compute(coord, box, atype, atom_energy=True)
-            parity[p] = {"force_rmse_ev_per_A": float(np.sqrt(np.mean((Fp[atoms] - ref) ** 2))),
-                         "sampled_atoms": len(atoms),
-                         "atomic_energy_max_abs_err_eV": float(np.abs(ep[cs] - e_ref).max()),
-                         "atomic_energy_rms_err_eV": float(np.sqrt(np.mean((ep[cs] - e_ref) ** 2))),
-                         "atomic_energy_centres": int(len(cs))}
+            Ep, Fp, Wp, ep = mm.compute(coord, box, atype, atom_energy=True)
+            parity[p] = {"force_rmse_ev_per_A": float(np.sqrt(np.mean((Fp - f_ref) ** 2))),
+                         "force_max_abs_err_ev_per_A": float(np.abs(Fp - f_ref).max()),
+                         "atomic_energy_max_abs_err_eV": float(np.abs(ep - e_ref).max()),
+                         "atomic_energy_rms_err_eV": float(np.sqrt(np.mean((ep - e_ref) ** 2))),
+                         "energy_abs_err_eV_per_atom": abs(Ep - rE) / n,
+                         "virial_max_rel_err": float(np.abs(Wp - w_ref).max() / np.abs(w_ref).max()),
+                         "atoms_compared": n,
+                         "within_16bit_bounds": bool(np.sqrt(np.mean((Fp - f_ref) ** 2)) <= 5e-3
+                                                     and np.abs(ep - e_ref).max() <= 1e-3),
+                         "within_fp32_bound": bool(np.sqrt(np.mean((Fp - f_ref) ** 2)) <= 1e-5)}
+        parity["oracle_seconds"] = t_oracle
 
     if rank != 0:
         return 0
@@ -525,10 +530,11 @@ def run_ours(a):
         achieved = flops / (dom_avg_ms / 1e3) / 1e12
         if head in ("bf16", "fp16x"):
             # FP16 and BF16 share the nominal dense rate: the measured BF16 figure applies
-            peak = (peaks or {}).get("bf16_tflops_sustained", 1700.0)
+            # a kernel of a few ms inside a sub-second timed region: the burst peak
+            peak = (peaks or {}).get("bf16_tflops", 1900.0)
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": _traffic_per_launch(dom, n), "kernel": dom,
-                    "peak_source": "measured bf16 sustained" if peaks else "fallback"}
+                    "peak_source": "measured bf16 burst" if peaks else "fallback"}
         else:
             clock = (peaks or {}).get("sm_max_mhz", 2070.0)
             peak = 152 * 128 * 2 * clock * 1e6 / 1e12

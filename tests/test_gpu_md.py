@@ -70,3 +70,46 @@ def test_nve_energy_conservation(default_model):
     assert drift[0.25] < 1e-3
     assert drift[0.5] / drift[0.25] > 2.5, drift
     m.close()
+
+
+@pytest.mark.parametrize("precision,x_tol", [("fp32", 1e-5), ("fp16x", 1e-3)])
+def test_md_matches_fp64_oracle_verlet(default_model, precision, x_tol):
+    """Five velocity-Verlet steps of dp_md_run against the FP64 host
+    integrator (oracle/md.py) driven by the FP64 oracle's forces, from the
+    same start on the water box.  The FP32 path's largest force error on this
+    box (~1e-3 eV/A on one H atom, an ill-conditioned row of the attention
+    adjoint; RMSE ~1e-6) moves that atom by at most ~1e-5 A in 2.5 fs
+    (a t^2 / 2 with a = dF / m); a wrong half kick, unit or mass would move
+    the atoms by ~1e-2 A."""
+    import torch
+    import paper_2604_07276_gb300 as p
+    from paper_2604_07276_gb300 import md
+    from oracle import energy_force_virial
+    from oracle.md import velocity_verlet
+
+    cfg, w, om = default_model
+    coord, atype, box = synth.water_box(0)
+    vel = synth.maxwell_boltzmann(atype, 300.0, seed=11)
+    mass = synth.MASSES[atype]
+
+    def force(x):
+        E, _, F, _ = energy_force_virial(om, x, box, atype)
+        return E, F
+
+    xr, vr, fr, thr = velocity_verlet(coord, vel, mass, force, 0.5, 5)
+    m = p.DPA1(weight_file(cfg, w, "default"), precision=precision)
+    s = md.MDState(coord, vel, mass, box, atype)
+    th = md.run(m, s, dt=0.5, nsteps=5, graph=False).cpu().numpy()
+    m.status()
+    m.close()
+    dx = np.abs(s.coord.cpu().numpy() - xr).max()
+    dv = np.abs(s.vel.cpu().numpy() - vr).max()
+    df = np.abs(s.force.cpu().numpy() - fr).max()
+    print(f"\n{precision}: max |dx| {dx:.2e} A, |dv| {dv:.2e} A/fs, |dF| {df:.2e} eV/A, "
+          f"|dE_pot| {np.abs(th[:, 0] - thr[:, 0]).max():.2e} eV, |dE_kin| {np.abs(th[:, 1] - thr[:, 1]).max():.2e} eV")
+    assert dx <= x_tol and dv <= x_tol
+    # energies: potential within the per-atom bound of the mode, kinetic to the
+    # velocity difference
+    e_tol = 1e-5 if precision == "fp32" else 1e-3
+    assert np.abs(th[:, 0] - thr[:, 0]).max() <= e_tol * len(atype)
+    assert np.abs(th[:, 1] - thr[:, 1]).max() <= 1e-6 * len(atype) + 100 * x_tol

@@ -1,8 +1,10 @@
 """Parity of the 16-bit tensor-core path (tcgen05 attention layers) with the
 FP64 oracle: force RMSE <= 5e-3 eV/A and per-atom energy <= 1e-3 eV for the
-FP16-operand mode with split layer input and attention weights ("fp16x").
-Plain BF16 operands cannot reach these bounds on this model (its error is
-checked against a recorded envelope instead, see test_bf16_error_envelope)."""
+FP16-operand mode with split layer input, attention weights, values and
+output projection ("fp16x").  Plain BF16 operands cannot reach these bounds
+on this model; their error is reported against its measured envelope (see
+test_bf16_plain_error_envelope).  The whole 15,668-atom box is compared in
+test_gpu_fullbox.py."""
 
 import numpy as np
 import pytest
@@ -24,7 +26,7 @@ def lib():
 
 
 @pytest.fixture(scope="module")
-def bf16_model(lib, default_model):
+def fp16x_model(lib, default_model):
     cfg, w, _ = default_model
     m = lib.DPA1(weight_file(cfg, w, "default"), precision="fp16x")
     yield m
@@ -32,7 +34,7 @@ def bf16_model(lib, default_model):
 
 
 @pytest.fixture(scope="module")
-def bf16_rich(lib, rich_model):
+def fp16x_rich(lib, rich_model):
     cfg, w, _ = rich_model
     m = lib.DPA1(weight_file(cfg, w, "rich"), precision="fp16x")
     yield m
@@ -50,82 +52,72 @@ def _check(m, om, coord, atype, box, e_tol=BF16_ATOM_ENERGY):
     return frmse, emax
 
 
-def test_bf16_water(bf16_model, default_model, water):
+def test_fp16x_water(fp16x_model, default_model, water):
     cfg, w, om = default_model
     coord, atype, box = water
-    _check(bf16_model, om, coord, atype, box)
+    _check(fp16x_model, om, coord, atype, box)
 
 
-def test_bf16_rich_weights(bf16_rich, rich_model, water):
-    """Non-zero biases, LayerNorm gains and davg/dstd.  Rounding the weights
-    themselves to FP16 shifts this model's atomic energies by up to ~1.7e-3 eV
-    (a fixed perturbation of the model, measured by emulating the rounding
-    on the CPU), so the per-atom bound here is 2.5e-3 eV."""
+def test_fp16x_rich_weights(fp16x_rich, rich_model, water):
+    """Non-zero biases, LayerNorm gains and davg/dstd, at the 16-bit bounds.
+    Rounding Wo to FP16 alone would shift this model's atomic energies by up
+    to ~1.3e-3 eV (a fixed perturbation of the model, found by emulating the
+    kernel's rounding points on the CPU); the forward kernel therefore adds
+    the product with Wo's rounding residue."""
     cfg, w, om = rich_model
     coord, atype, box = water
-    _check(bf16_rich, om, coord, atype, box, e_tol=2.5e-3)
+    frmse, emax = _check(fp16x_rich, om, coord, atype, box)
+    print(f"\nrich fp16x: force rmse {frmse:.2e}, max |de_i| {emax:.2e}")
 
 
-def test_bf16_lattice_ragged(bf16_model, default_model):
+def test_fp16x_lattice_ragged(fp16x_model, default_model):
     cfg, w, om = default_model
     coord, atype, box = synth.lattice_system(1123, seed=31)
-    _check(bf16_model, om, coord, atype, box)
+    _check(fp16x_model, om, coord, atype, box)
 
 
-def test_bf16_edge_cases(bf16_model, default_model):
+def test_fp16x_edge_cases(fp16x_model, default_model):
     cfg, w, om = default_model
     box = np.array([30.0, 30.0, 30.0])
-    E, F, W, e = bf16_model.compute(np.zeros((0, 3)), box, np.zeros(0, np.int32), atom_energy=True)
+    E, F, W, e = fp16x_model.compute(np.zeros((0, 3)), box, np.zeros(0, np.int32), atom_energy=True)
     assert E == 0.0 and F.shape == (0, 3)
     for coord, atype in ((np.array([[3.0, 4.0, 5.0]]), np.array([2], np.int32)),
                          (np.array([[1.0, 1.0, 1.0], [15.0, 15.0, 15.0]]), np.array([0, 4], np.int32)),
                          (np.array([[10.0, 10.0, 10.0], [11.2, 10.3, 9.9], [20.0, 20.0, 20.0], [21.0, 20.2, 20.0],
                                     [20.1, 21.1, 19.5]]), np.array([3, 0, 1, 2, 3], np.int32))):
-        _check(bf16_model, om, coord, atype, box)
+        _check(fp16x_model, om, coord, atype, box)
 
 
-def test_bf16_deterministic(bf16_model, water):
+def test_fp16x_deterministic(fp16x_model, water):
     coord, atype, box = water
-    a = bf16_model.compute(coord, box, atype, atom_energy=True)
-    b = bf16_model.compute(coord, box, atype, atom_energy=True)
+    a = fp16x_model.compute(coord, box, atype, atom_energy=True)
+    b = fp16x_model.compute(coord, box, atype, atom_energy=True)
     assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
 
 
-def test_bf16_full_size_sampled(bf16_model, default_model):
-    cfg, w, om = default_model
-    coord, atype, box = synth.lattice_system(15668, seed=1)
-    E, F, W, e = bf16_model.compute(coord, box, atype, atom_energy=True)
-    rng = np.random.default_rng(5)
-    atoms = rng.choice(len(coord), size=8, replace=False)
-    rF = oracle.forces_on(om, coord, box, atype, atoms)
-    assert force_rmse(F[atoms], rF) <= BF16_FORCE_RMSE
-    centres = rng.choice(len(coord), size=32, replace=False)
-    _, re, _, _ = energy_force_virial(om, coord, box, atype, centres=centres)
-    assert np.abs(e[centres] - re).max() <= BF16_ATOM_ENERGY
-    assert np.abs(F.sum(axis=0)).max() < 1e-3
-
-
-def test_bf16_matches_fp32_path(lib, bf16_model, default_model):
+def test_fp16x_matches_fp32_path(lib, fp16x_model, default_model):
     cfg, w, _ = default_model
     m32 = lib.DPA1(weight_file(cfg, w, "default"), precision="fp32")
     coord, atype, box = synth.lattice_system(700, seed=3)
-    _, F16, _, e16 = bf16_model.compute(coord, box, atype, atom_energy=True)
+    _, F16, _, e16 = fp16x_model.compute(coord, box, atype, atom_energy=True)
     _, F32, _, e32 = m32.compute(coord, box, atype, atom_energy=True)
     m32.close()
     assert force_rmse(F16, F32) <= BF16_FORCE_RMSE
     assert np.abs(e16 - e32).max() <= BF16_ATOM_ENERGY
 
 
-def test_bf16_error_envelope(lib, default_model, water):
-    """Plain BF16 operands: the error against FP64 stays within the envelope
-    measured for this model (about 6e-2 eV/A force RMSE), and the mode runs."""
+def test_bf16_plain_error_envelope(lib, default_model, water):
+    """Plain BF16 operands (no splits; reported, not held to the 16-bit
+    bounds): the error against FP64 on the water box stays within its
+    measured value (force RMSE 2.4e-2 eV/A) with a margin of 1.5x."""
     cfg, w, om = default_model
     coord, atype, box = water
     m = lib.DPA1(weight_file(cfg, w, "default"), precision="bf16")
     E, F, W, e = m.compute(coord, box, atype, atom_energy=True)
     m.close()
     rE, re, rF, rW = energy_force_virial(om, coord, box, atype)
-    assert force_rmse(F, rF) < 0.1
+    print(f"\nplain bf16 water: force rmse {force_rmse(F, rF):.2e}, max |de_i| {np.abs(e - re).max():.2e}")
+    assert force_rmse(F, rF) <= 1.5 * 2.4e-2
     assert np.abs(e - re).max() < 0.03
 
 
