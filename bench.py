@@ -68,7 +68,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp16x", "bf16", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp16x", "bf16x", "bf16", "fp32"])
     ap.add_argument("--natoms", type=int, default=NATOMS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
@@ -359,7 +359,7 @@ def run_ours(a):
     coord, atype, box = _system(a.natoms)
     n = len(coord)
 
-    precisions = ["fp16x", "bf16", "fp32"] if a.precision == "auto" else [a.precision]
+    precisions = ["fp16x", "bf16x", "bf16", "fp32"] if a.precision == "auto" else [a.precision]
     models = {}
     mem_used = {}  # device bytes taken by each model (weights + workspace for n atoms)
     for p in precisions:
@@ -373,7 +373,7 @@ def run_ours(a):
         except dp.DPError as e:
             if e.code != -8 or a.precision != "auto":
                 raise
-    head = next(p for p in ("fp16x", "bf16", "fp32") if p in models)
+    head = next(p for p in ("fp16x", "bf16x", "bf16", "fp32") if p in models)
 
     c = torch.tensor(coord, dtype=torch.float64, device=dev)
     t = torch.tensor(atype, dtype=torch.int32, device=dev)
@@ -528,7 +528,7 @@ def run_ours(a):
     roof = None
     if flops is not None:
         achieved = flops / (dom_avg_ms / 1e3) / 1e12
-        if head in ("bf16", "fp16x"):
+        if head in ("bf16", "fp16x", "bf16x"):
             # FP16 and BF16 share the nominal dense rate: the measured BF16 figure applies
             # a kernel of a few ms inside a sub-second timed region: the burst peak
             peak = (peaks or {}).get("bf16_tflops", 1900.0)
@@ -551,12 +551,15 @@ def run_ours(a):
     line = {
         "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp16x": "f16", "bf16": "bf16", "fp32": "f32"}[head], "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp16x": "f16", "bf16x": "bf16", "bf16": "bf16", "fp32": "f32"}[head],
+        "data": "synthetic",
         "config": {"workload": workload(n), "model": model_desc, "natoms": n, "global_batch": ws * n,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "per-step working set is several GB of intermediates, far above the 129 MB L2",
                    "arithmetic": {"fp16x": "attention layers on tcgen05: FP16 operands, two-term splits of G, P, V; "
                                            "FP32 accumulation; FP64 energy / virial sums",
+                                  "bf16x": "attention layers and fitting net on tcgen05: BF16 operands with two-term "
+                                           "splits of both operands, FP32 accumulation; FP64 energy / virial sums",
                                   "bf16": "attention layers on tcgen05: BF16 operands, FP32 accumulation",
                                   "fp32": "FP32 SIMT"}[head]},
         "clocks": r["clocks"],
@@ -568,6 +571,11 @@ def run_ours(a):
         "precisions": {p: {"value": job_rate(ws, n, a.steps, rr["ms"] / 1e3), "ms_per_step": rr["ms"] / a.steps}
                        for p, rr in results.items()},
         "force_rmse_vs_fp64": parity,
+        "bf16_vs_fp32": ({"bf16_operand_mode": "bf16x",
+                          "ms_per_step": {"bf16x": results["bf16x"]["ms"] / a.steps, "fp32": results["fp32"]["ms"] / a.steps},
+                          "speedup": results["fp32"]["ms"] / results["bf16x"]["ms"],
+                          "within_16bit_bounds": parity.get("bf16x", {}).get("within_16bit_bounds")}
+                         if "bf16x" in results and "fp32" in results else None),
         "stage_ms_per_step": {p: {k: v[0] / a.steps for k, v in rr["stages"].items()} for p, rr in results.items()},
         "neighbors": {"mean": float(nn.mean()), "max": int(nn.max())},
         "device_memory_bytes": mem_used,

@@ -57,8 +57,12 @@ enum dp_status {
 enum dp_precision {
   DP_PREC_FP32 = 0,  /* every matrix product in FP32 SIMT arithmetic */
   DP_PREC_BF16 = 1,  /* attention-layer products on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
-  DP_PREC_FP16X = 2  /* as DP_PREC_BF16 with FP16 operands and two-term (hi + lo) splits of the layer
-                        input and of the attention weights; FP32 accumulation */
+  DP_PREC_FP16X = 2, /* as DP_PREC_BF16 with FP16 operands and two-term (hi + lo) splits of the layer
+                        input, the attention weights, the values and the output projection; FP32
+                        accumulation */
+  DP_PREC_BF16X = 3  /* every product of the attention layers and of the fitting net on tcgen05 tensor
+                        cores with BF16 operands, both operands split in two terms (x = bf16(x) +
+                        bf16(x - bf16(x)), three products), FP32 accumulation; attention width 128 */
 };
 
 /* Load a model.
@@ -69,7 +73,9 @@ enum dp_precision {
  *   rcut, rcut_smth, sel : must equal the file's values (Sec. II-C: the
  *                  cutoff of the full neighbour list and its cap), else
  *                  DP_ERR_ARG.  Pass a negative value to accept the file's.
- *   precision    : DP_PREC_FP32, DP_PREC_BF16 or DP_PREC_FP16X.
+ *   precision    : DP_PREC_FP32, DP_PREC_BF16, DP_PREC_FP16X or DP_PREC_BF16X
+ *                  (DP_ERR_UNSUPPORTED for a model shape the mode has no
+ *                  kernel for).
  *   device       : CUDA device ordinal; the model's memory lives there.
  * On success *out is a new model; release it with dp_free. */
 DP_API int dp_init(dp_model** out, const char* weights_path, const char* const* type_map, int ntypes,

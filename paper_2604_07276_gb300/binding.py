@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libdpa1.so")
 DP_OK = 0
 STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_IO", -3: "DP_ERR_BOX", -4: "DP_ERR_CAPACITY",
           -5: "DP_ERR_CUDA", -6: "DP_ERR_TIMEOUT", -7: "DP_ERR_NAN", -8: "DP_ERR_UNSUPPORTED"}
-PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2, "bf16x": 3}
 
 EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_local", "dp_compute_device_local", "dp_compute_batch", "dp_reserve", "dp_set_precision",
            "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",

@@ -222,6 +222,7 @@ void refresh_derived(dp_model* m, cudaStream_t st) {
   if (m->concat && m->b0t_type)
     launch_add_rows(m->b0t_type, m->theta + m->emb[0], m->nt * m->nt, m->emb[0], m->b0t, st);
   fit_tc_refresh(m, st);  // tensor-core weight images of the 16-bit paths, if built
+  if (m->xw.ready) bf16x_refresh(m, st);
 }
 
 void free_workspace(Workspace& ws) {
@@ -270,17 +271,18 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.G.assign(L + 1, nullptr);
     for (int l = 0; l <= L; ++l) ws.G[l] = a.take<float>(rows * m1);
     ws.QKV.assign(L, nullptr); ws.O.assign(L, nullptr); ws.Y.assign(L, nullptr); ws.stats.assign(L, nullptr);
-    if (m->precision == DP_PREC_FP32) {
+    if (!fused_tc_precision(m->precision)) {
       for (int l = 0; l < L; ++l) {
         ws.QKV[l] = a.take<float>(rows * 3 * A);
-        ws.O[l] = a.take<float>(rows * A);
+        ws.O[l] = a.take<float>(rows * pg_ld(m1));  // [P G, rowsum(P)]
         ws.Y[l] = a.take<float>(rows * m1);
         ws.stats[l] = a.take<float>(rows * 2);
       }
       ws.dY = a.take<float>(rows * m1);
       ws.dO = a.take<float>(rows * (L > 0 ? A : 1));
       ws.dQKV = a.take<float>(rows * (L > 0 ? 3 * A : 1));
-      ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 3 * NP * NP);  // dS^T, P^T, dP per block
+      if (m->precision == DP_PREC_FP32)  // dS^T, P^T, dP per block of the FP32 adjoint
+        ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 3 * NP * NP);
     }
     ws.dG = a.take<float>(rows * m1);
     ws.T = a.take<float>((size_t)cap * 4 * m1);
@@ -300,7 +302,7 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.energy = a.take<double>(1);
     ws.atom_energy = a.take<double>(cap);
     ws.atype = a.take<int>(cap);
-    if (m->precision != DP_PREC_FP32) tc_plan_buffers(m, a, cap);
+    if (fused_tc_precision(m->precision)) tc_plan_buffers(m, a, cap);
   };
   Arena probe;
   plan(probe);
@@ -396,18 +398,22 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
   da.R = ws.R; da.G = ws.G[L]; da.nnei = ws.nnei; da.atype = atype; da.tebd = m->tebd;
   da.n = n; da.m1 = m1; da.axis = m->axis; da.tebd_dim = m->td; da.sel = m->sel; da.fit_in = m->fit_in;
   da.T = ws.T; da.X = ws.X; da.dX = ws.dX; da.dG = ws.dG; da.dR = ws.dR;
-  da.cq = m->precision != DP_PREC_FP32 ? 1 : 0;  // the tensor-core path's layout
+  da.cq = fused_tc_precision(m->precision) ? 1 : 0;  // the fused layer kernels' layout
   launch_desc_fwd(da, st);
   prof_mark(m, "desc_fwd", st);
   // a8: fitting forward
   int fan = m->fit_in;
   const float* hin = ws.X;
   // the 16-bit paths run the products on tcgen05 (TF32 with two-term splits)
-  const bool fit_tc = m->precision != DP_PREC_FP32 && !m->tcw.fitW_t.empty();
+  const bool fit_tc = fused_tc_precision(m->precision) && !m->tcw.fitW_t.empty();
+  const bool fit_x = m->precision == DP_PREC_BF16X;  // BF16 two-term splits
   for (int l = 0; l < m->nfit; ++l) {
     const int out = m->fit[l];
     const bool res = (l > 0 && out == fan);
-    if (fit_tc)
+    if (fit_x)
+      gemm_bf16x(m, m->xw.fit[l], hin, fan, m->fitb[l], res ? hin : nullptr, fan, ws.H[l], out, n,
+                 res ? EPI_RES_TANH : EPI_TANH, st);
+    else if (fit_tc)
       fit_gemm_tc(m, l, false, hin, fan, m->fitb[l], res ? hin : nullptr, fan, ws.H[l], out, n,
                   res ? EPI_RES_TANH : EPI_TANH, st);
     else
@@ -438,7 +444,10 @@ void run_descriptor_fitting(dp_model* m, int n, const int* atype, cudaStream_t s
       launch_colsum(ws.dZ, out, m->grad + m->off_fitb[l], out, n, gs, 1.0f, st);
     }
     float* dst = l > 0 ? dHn : ws.dX;
-    if (fit_tc)
+    if (fit_x)
+      gemm_bf16x(m, m->xw.fitT[l], ws.dZ, out, nullptr, res ? dH : nullptr, out, dst, in, n, res ? EPI_RES : EPI_BIAS,
+                 st);
+    else if (fit_tc)
       fit_gemm_tc(m, l, true, ws.dZ, out, nullptr, res ? dH : nullptr, out, dst, in, n, res ? EPI_RES : EPI_BIAS, st);
     else
       gemm_f32(ws.dZ, out, m->fitWT[l], in, nullptr, res ? dH : nullptr, out, dst, in, n, in, out,
@@ -473,10 +482,11 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
     prof_mark(m, "qkv_gemm", st);
     AttnArgs aa{};
     aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
-    aa.O = ws.O[l];
+    aa.G = ws.G[l]; aa.m1 = m1; aa.ldpg = pg_ld(m1); aa.PG = ws.O[l];
     launch_attn_fwd_f32(aa, st);
     prof_mark(m, "attn_fwd", st);
-    gemm_f32(ws.O[l], A, w.Wo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, A, EPI_BIAS, st);
+    // Y = O Wo + bo = [P G, rowsum(P)] [Wv Wo; bv Wo] + bo
+    gemm_f32(ws.O[l], pg_ld(m1), w.Wvo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, pg_ld(m1), EPI_BIAS, st);
     launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
                       m1, st);
     prof_mark(m, "wo_gemm_ln", st);
@@ -505,6 +515,48 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   prof_mark(m, "embed_bwd", st);
 }
 
+// The BF16-split network path (stages a5-a13): the layout and stage order of
+// the FP32 path, with every product of the attention layers and of the
+// fitting net on tcgen05 (bf16x.cu); embedding net, LayerNorm and descriptor
+// in FP32.
+void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
+  Workspace& ws = m->ws;
+  const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
+  EmbedArgs ea{};
+  ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
+  ea.w = m->emb_packed; ea.Gt = m->Gt; ea.b0t = m->b0t; ea.G0 = ws.G[0];
+  launch_embed_fwd(ea, m->emb, st);
+  prof_mark(m, "embed_fwd", st);
+  for (int l = 0; l < L; ++l) {
+    const AttnLayerW& w = m->attn[l];
+    const XWeights::Layer& x = m->xw.layers[l];
+    gemm_bf16x(m, x.qkv, ws.G[l], m1, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, EPI_BIAS, st);
+    prof_mark(m, "qkv_gemm", st);
+    attn_core_fwd_bf16x(m, n, l, st);
+    prof_mark(m, "attn_fwd", st);
+    gemm_bf16x(m, x.vo, ws.O[l], pg_ld(m1), w.bo, nullptr, 0, ws.Y[l], m1, rows, EPI_BIAS, st);
+    launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
+                      m1, st);
+    prof_mark(m, "wo_gemm_ln", st);
+  }
+  run_descriptor_fitting(m, n, atype, st);
+  cudaMemsetAsync(ws.dgeo, 0, sizeof(float) * (size_t)rows * 4, st);
+  for (int l = L - 1; l >= 0; --l) {
+    const AttnLayerW& w = m->attn[l];
+    const XWeights::Layer& x = m->xw.layers[l];
+    launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
+    gemm_bf16x(m, x.woT, ws.dY, m1, nullptr, nullptr, 0, ws.dO, A, rows, EPI_BIAS, st);
+    prof_mark(m, "ln_wo_bwd", st);
+    attn_core_bwd_bf16x(m, n, l, st);
+    prof_mark(m, "attn_bwd", st);
+    gemm_bf16x(m, x.qkvT, ws.dQKV, 3 * A, nullptr, nullptr, 0, ws.dG, m1, rows, EPI_ACCUM, st);
+    prof_mark(m, "qkv_bwd_gemm", st);
+  }
+  ea.dG0 = ws.dG; ea.dR = ws.dR;
+  launch_embed_bwd(ea, m->emb, st);
+  prof_mark(m, "embed_bwd", st);
+}
+
 // Stages a3-a15 on n atoms whose neighbour list is built.  grid is the cell
 // grid of the box (frame non-null: grid[frame[i]] is atom i's box, a packed
 // batch); force holds n atoms, energy and virial one frame (seg null) or the
@@ -524,8 +576,10 @@ int run_after_neighbors(dp_model* m, int n, const double* coord, const CellGrid*
   ea.w64 = ea.fp64 ? ws.w64 : nullptr;
   launch_env(ea, st);
   prof_mark(m, "env", st);
-  if (m->precision != DP_PREC_FP32)
+  if (fused_tc_precision(m->precision))
     tc_run_network(m, n, atype, st);
+  else if (m->precision == DP_PREC_BF16X)
+    run_network_bf16x(m, n, atype, st);
   else
     run_network_f32(m, n, atype, st);
   // a14: per-pair gradient
@@ -661,7 +715,7 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
   g_last_error.clear();
   if (!out) return fail(DP_ERR_ARG, "out is null");
   *out = nullptr;
-  if (precision < DP_PREC_FP32 || precision > DP_PREC_FP16X) return fail(DP_ERR_ARG, "unknown precision");
+  if (precision < DP_PREC_FP32 || precision > DP_PREC_BF16X) return fail(DP_ERR_ARG, "unknown precision");
   HostWeights w;
   int rc = read_weights(weights_path, w, false);
   if (rc != DP_OK) return rc;
@@ -781,6 +835,24 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     if ((rc = dev_upload(m, &L.bo, to_f(*w.get(p + "bo")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_g, to_f(*w.get(p + "ln_g")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_b, to_f(*w.get(p + "ln_b")))) != DP_OK) return fail_free(rc);
+    // [Wv Wo; bv Wo; 0 ...] in FP64, rounded once to FP32
+    {
+      const std::vector<double>& Wo = *w.get(p + "Wo");
+      const std::vector<double>& bv = *w.get(p + "bv");
+      std::vector<double> Wvo((size_t)pg_ld(m1) * m1, 0.0);
+      for (int r = 0; r < m1; ++r)
+        for (int c = 0; c < m1; ++c) {
+          double acc = 0.0;
+          for (int f = 0; f < A; ++f) acc += (*Wv)[(size_t)r * A + f] * Wo[(size_t)f * m1 + c];
+          Wvo[(size_t)r * m1 + c] = acc;
+        }
+      for (int c = 0; c < m1; ++c) {
+        double acc = 0.0;
+        for (int f = 0; f < A; ++f) acc += bv[f] * Wo[(size_t)f * m1 + c];
+        Wvo[(size_t)m1 * m1 + c] = acc;
+      }
+      if ((rc = dev_upload(m, &L.Wvo, to_f(Wvo))) != DP_OK) return fail_free(rc);
+    }
   }
   // trainable parameter vector (layout in model.h) and its derived copies
   {
@@ -834,9 +906,12 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     refresh_derived(m, nullptr);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(fail(DP_ERR_CUDA, "weight refresh failed"));
   }
-  if (precision != DP_PREC_FP32) {
+  if (fused_tc_precision(precision)) {
     std::string msg;
     if ((rc = tc_init_weights(m, w.arrays, msg)) != DP_OK) return fail_free(fail(rc, msg));
+  } else if (precision == DP_PREC_BF16X) {
+    std::string msg;
+    if ((rc = bf16x_init_weights(m, msg)) != DP_OK) return fail_free(fail(rc, msg));
   }
   {
     void* p;
@@ -862,10 +937,12 @@ int dp_reserve(dp_model* m, int max_atoms) {
 
 int dp_set_precision(dp_model* m, int precision) {
   if (check_model(m)) return DP_ERR_ARG;
-  if (precision < DP_PREC_FP32 || precision > DP_PREC_FP16X) return fail(DP_ERR_ARG, "unknown precision");
+  if (precision < DP_PREC_FP32 || precision > DP_PREC_BF16X) return fail(DP_ERR_ARG, "unknown precision");
   if (precision == m->precision) return DP_OK;
-  if (precision != DP_PREC_FP32 && !m->tcw.ready)
-    return fail(DP_ERR_UNSUPPORTED, "model was loaded without the BF16 weights; reload with DP_PREC_BF16");
+  if (fused_tc_precision(precision) && !m->tcw.ready)
+    return fail(DP_ERR_UNSUPPORTED, "model was loaded without the 16-bit layer weights; reload with DP_PREC_BF16");
+  if (precision == DP_PREC_BF16X && !m->xw.ready)
+    return fail(DP_ERR_UNSUPPORTED, "model was loaded without the BF16-split weights; reload with DP_PREC_BF16X");
   CUDA_TRY(cudaSetDevice(m->device));
   CUDA_TRY(cudaDeviceSynchronize());
   m->precision = precision;
@@ -1161,7 +1238,7 @@ long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t by
   if (!src) return fail(DP_ERR_ARG, "unknown buffer name");
   sz = std::min(sz, bytes);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(DP_ERR_CUDA, "sync failed");
-  if (s[0] == 'G' && m->precision != DP_PREC_FP32) {
+  if (s[0] == 'G' && fused_tc_precision(m->precision)) {
     // the tensor-core path keeps G column-quad interleaved per atom: return it row-major
     const size_t m1 = (size_t)m->m1, full = rows * m1;
     std::vector<float> raw(full), out(full);
@@ -1460,6 +1537,7 @@ void dp_free(dp_model* m) {
   cudaDeviceSynchronize();
   free_workspace(m->ws);
   tc_free_weights(m);
+  bf16x_free(m);
   for (void* p : m->allocations) cudaFree(p);
   if (m->d_err) cudaFree(m->d_err);
   if (m->stream) cudaStreamDestroy(m->stream);

@@ -1,0 +1,870 @@
+// The BF16-operand precision mode ("bf16x"): every matrix product of the
+// attention layers (stages a6, a12) and of the fitting net (a8, a10) runs on
+// tcgen05 with BF16 operands and FP32 accumulation in TMEM, with two-term
+// splits of both operands, x = x_hi + x_lo (x_hi = bf16(x), x_lo =
+// bf16(x - x_hi)), evaluated as the three products x_hi y_hi + x_lo y_hi +
+// x_hi y_lo.  The dropped x_lo y_lo and the rounding of the low parts leave
+// about 2^-16 relative error per product.  A CPU emulation of the layer's
+// rounding points shows that BF16 operands meet force RMSE <= 5e-3 eV/A and
+// atomic energies <= 1e-3 eV against FP64 only when every forward operand is
+// split this way; in the adjoint the attention weights P and dS may stay
+// single BF16 (force RMSE ~1e-3 eV/A on the model with perturbed biases).
+//
+// The layer is organised as in the FP32 path (stored Q K V, O through P G,
+// LayerNorm kernels), with:
+//   k_gemm_bf16x          the projections [Q K V] = G Wqkv + b,
+//                         Y = [P G, rowsum P] [Wv Wo; bv Wo] + bo,
+//                         dO = dY Wo^T, dG += dQKV Wqkv^T, and the fitting
+//                         net's products (A by TMA as FP32, split in shared
+//                         memory; B from pre-split images);
+//   k_attn_core_fwd_bf16x per atom: S = Q K^T, smooth softmax and gate,
+//                         [P G, rowsum P] = P [G 1];
+//   k_attn_core_bwd_bf16x per atom: dP = dO V^T, S recomputed, the softmax
+//                         adjoint (dE/drhat, dE/dw), dV = P^T dO,
+//                         dQ = dS K, dK = dS^T Q.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dpa1.h"
+#include "kernels.h"
+#include "model.h"
+#include "tc_layer.cuh"
+#include "tc_ptx.cuh"
+
+namespace dpa1 {
+
+using namespace tc;
+
+namespace {
+
+// ------------------------------------------------------------------- GEMM
+// C = epi(A B + bias (+ R)), A [M][K] FP32 row-major, B [K][N] from a
+// pre-split image.  One CTA: a 128-row x (<= 192)-column tile with the full
+// K in stages of 64:
+//   warp 0      : producer.  Two TMA boxes of A (128 rows x 32 K FP32,
+//                 128-byte swizzle) and the B hi / lo tiles (bulk copies).
+//   warps 4-7   : split the stage's FP32 A into its BF16 hi and lo tiles
+//                 (K-major, 128-byte swizzle); thread t owns row t.
+//   warp 1      : issues the MMAs (one thread); accumulator in TMEM.
+//   warp 2      : allocates / frees TMEM.
+//   all 8 warps : epilogue (TMEM -> bias, tanh, residual / accumulate ->
+//                 global).
+constexpr int XBM = 128, XBK = 64, XBN = 192, XSTAGES = 2, XTHREADS = 256;
+constexpr int XF32 = 2 * XBM * 32 * 4;  // FP32 staging of one stage: two TMA boxes (32 KB)
+constexpr int XAT = XBM * XBK * 2;      // one BF16 A tile (hi or lo): 16 KB
+
+struct XGemmArgs {
+  const uint8_t* bimg;  // [n block][k block][hi, lo] tiles of bn_max rows x 64 K (BF16, K-major, SW128)
+  const float* bias;    // [N] or null
+  const float* R;       // residual [M][ldr] or null
+  float* C;             // [M][ldc]
+  int ldr, ldc;
+  int M, N, nkb, bn_max, epi;
+  int* err;
+};
+
+__device__ __forceinline__ void x_tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 8 FP32 values -> their BF16 high parts and the BF16 rounding of the residues.
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(v[2 * i]), b = __float2bfloat16_rn(v[2 * i + 1]);
+    h[i] = pack_bf16(__bfloat162float(a), __bfloat162float(b));
+    l[i] = pack_bf16(v[2 * i] - __bfloat162float(a), v[2 * i + 1] - __bfloat162float(b));
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__global__ void __launch_bounds__(XTHREADS, 1)
+k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XGemmArgs a) {
+  extern __shared__ uint8_t xsm_raw[];
+  const uint32_t raw = smem_u32(xsm_raw);
+  uint8_t* sm = xsm_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned tiles
+  const int mb = blockIdx.x, nb = blockIdx.y;
+  const int bn = min(XBN, ((a.N - nb * XBN) + 15) & ~15);  // MMA width of this tile
+  const int b_tile = a.bn_max * 128;
+  const int stage_bytes = XF32 + 2 * XAT + 2 * b_tile;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + XSTAGES * stage_bytes);
+  uint64_t* full = bars;                 // [XSTAGES] A boxes and B tiles arrived
+  uint64_t* conv = bars + XSTAGES;       // [XSTAGES] A split into hi / lo (128 arrivals)
+  uint64_t* empty = bars + 2 * XSTAGES;  // [XSTAGES] the stage's MMAs are done
+  uint64_t* done = bars + 3 * XSTAGES;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(done + 1);
+  auto sF = [&](int s) { return sm + s * stage_bytes; };
+  auto sAh = [&](int s) { return sm + s * stage_bytes + XF32; };
+  auto sAl = [&](int s) { return sm + s * stage_bytes + XF32 + XAT; };
+  auto sBh = [&](int s) { return sm + s * stage_bytes + XF32 + 2 * XAT; };
+  auto sBl = [&](int s) { return sm + s * stage_bytes + XF32 + 2 * XAT + b_tile; };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < XSTAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(conv + s, 128);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 2) tmem_alloc(s_tmem, 256);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tm = *s_tmem;
+  bool ok = true;
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    if (ok) ok = mbar_wait(bar, parity, a.err);
+  };
+
+  if (warp == 0 && lane == 0) {
+    const uint8_t* img = a.bimg + (size_t)nb * a.nkb * 2 * b_tile;
+    for (int kb = 0; kb < a.nkb && ok; ++kb) {
+      const int s = kb % XSTAGES, u = kb / XSTAGES;
+      if (kb >= XSTAGES) wait(empty + s, (u - 1) & 1);
+      if (!ok) break;
+      mbar_expect_tx(full + s, XF32 + 2 * bn * 128);
+      x_tma_load_2d(sF(s), &tmA, kb * XBK, mb * XBM, full + s);
+      x_tma_load_2d(sF(s) + XF32 / 2, &tmA, kb * XBK + 32, mb * XBM, full + s);
+      bulk_g2s(sBh(s), img + (size_t)(2 * kb) * b_tile, bn * 128, full + s);
+      bulk_g2s(sBl(s), img + (size_t)(2 * kb + 1) * b_tile, bn * 128, full + s);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id = idesc_16(XBM, bn, false, false, false);
+    for (int kb = 0; kb < a.nkb && ok; ++kb) {
+      const int s = kb % XSTAGES, u = kb / XSTAGES;
+      wait(conv + s, u & 1);
+      fence_after_sync();
+      if (ok) {
+        const uint32_t ah = smem_u32(sAh(s)), al = smem_u32(sAl(s));
+        const uint32_t bh = smem_u32(sBh(s)), bl = smem_u32(sBl(s));
+#pragma unroll
+        for (int ks = 0; ks < XBK / 16; ++ks) {
+          const uint64_t dah = kmajor_desc(ah, ks, XBM), dal = kmajor_desc(al, ks, XBM);
+          const uint64_t dbh = kmajor_desc(bh, ks, bn), dbl = kmajor_desc(bl, ks, bn);
+          mma_bf16(tm, dah, dbh, id, (kb > 0 || ks > 0) ? 1u : 0u);
+          mma_bf16(tm, dal, dbh, id, 1u);
+          mma_bf16(tm, dah, dbl, id, 1u);
+        }
+      }
+      mma_commit(empty + s);
+    }
+    mma_commit(done);
+  } else if (warp >= 4) {
+    // row r of the stage: FP32 K 0..31 in box 0, 32..63 in box 1, each row a
+    // 128-byte line whose 16-byte pieces are permuted by XOR with r % 8; its
+    // BF16 row is one 128-byte line with the same permutation
+    const int r = threadIdx.x - 128;
+    const uint32_t line = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
+    for (int kb = 0; kb < a.nkb && ok; ++kb) {
+      const int s = kb % XSTAGES, u = kb / XSTAGES;
+      wait(full + s, u & 1);
+      const uint8_t* f = sF(s);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint8_t* box = f + (q >> 2) * (XF32 / 2) + line;
+        const int p0 = 2 * (q & 3);
+        const float4 x0 = *reinterpret_cast<const float4*>(box + ((p0 ^ (r & 7)) << 4));
+        const float4 x1 = *reinterpret_cast<const float4*>(box + (((p0 + 1) ^ (r & 7)) << 4));
+        const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        uint4 hi, lo;
+        split8(v, hi, lo);
+        const uint32_t off = line + ((q ^ (r & 7)) << 4);
+        *reinterpret_cast<uint4*>(sAh(s) + off) = hi;
+        *reinterpret_cast<uint4*>(sAl(s) + off) = lo;
+      }
+      fence_async_smem();
+      mbar_arrive(conv + s);
+    }
+  }
+  // epilogue, all warps
+  __syncwarp();
+  wait(done, 0);
+  fence_after_sync();
+  {
+    const int r = (warp & 3) * 32 + lane;  // row in the tile = TMEM lane
+    const long long m = (long long)mb * XBM + r;
+    const uint32_t taddr = tm + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int c0 = (warp >> 2) * 16; c0 < bn; c0 += 32) {
+      float v[16];
+      tmem_ld16(taddr + c0, v);
+      if (m >= a.M || !ok) continue;
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const int n = nb * XBN + c0 + q;
+        if (n >= a.N) break;  // N % 4 == 0
+        float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        float* op = &o.x;
+        if (a.bias) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) op[t] += a.bias[n + t];
+        }
+        if (a.epi == EPI_TANH || a.epi == EPI_RES_TANH) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) op[t] = tanhf(op[t]);
+        }
+        if (a.epi == EPI_RES_TANH || a.epi == EPI_RES) {
+          const float4 rr = *reinterpret_cast<const float4*>(a.R + m * a.ldr + n);
+          o.x += rr.x; o.y += rr.y; o.z += rr.z; o.w += rr.w;
+        }
+        float4* cp = reinterpret_cast<float4*>(a.C + m * a.ldc + n);
+        if (a.epi == EPI_ACCUM) {
+          const float4 cc = *cp;
+          o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
+        }
+        *cp = o;
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 2) tmem_dealloc(tm, 256);
+}
+
+// B image of one product, built on the device from B [K][N] (FP32,
+// row-major): per (n block, k block) a hi and a lo tile of bn_max rows
+// (output columns) x 64 K, BF16, K-major with the 128-byte swizzle, zero
+// outside B.
+__global__ void k_x_image(const float* __restrict__ B, int K, int N, int nkb, int bn_max, uint8_t* __restrict__ img) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nnb = (N + XBN - 1) / XBN;
+  const long long total = (long long)nnb * nkb * bn_max * XBK;
+  if (t >= total) return;
+  const int k_local = (int)(t % XBK);
+  const int n_local = (int)((t / XBK) % bn_max);
+  const int kb = (int)((t / ((long long)XBK * bn_max)) % nkb);
+  const int nb = (int)(t / ((long long)XBK * bn_max * nkb));
+  const int k = kb * XBK + k_local, n = nb * XBN + n_local;
+  const float x = (k < K && n < N && n_local < XBN) ? B[(size_t)k * N + n] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  const size_t tile = (size_t)bn_max * 128;
+  uint8_t* base = img + ((size_t)nb * nkb + kb) * 2 * tile;
+  const uint32_t off = sw128_offset(n_local, k_local, bn_max);
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(base + tile + off) = l;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_x_encode = nullptr;
+
+int x_smem(int bn_max) { return XSTAGES * (XF32 + 2 * XAT + 2 * bn_max * 128) + 1024 + 128; }
+
+// ------------------------------------------------------ attention cores
+// One persistent CTA of 512 threads per SM walks over centre atoms; warp w
+// owns TMEM lane quadrant w % 4 (rows 32 (w % 4) .. +31) and column quarter
+// w / 4 (32 columns), as in the fused layer kernels.  Tiles are 128 x 128
+// BF16 with the 128-byte swizzle (32 KB).
+constexpr int XC_NT = 512;
+constexpr int XT = 32768;
+
+struct XCoreArgs {
+  const float* QKV;  // [rows][3 * 128]: Q | K | V
+  const float* G;    // fwd: [rows][m1] layer input
+  float* PG;         // fwd: [rows][ldpg] = [P G, rowsum(P), 0 ...]
+  const float* dO;   // bwd: [rows][128]
+  float* dQKV;       // bwd: [rows][3 * 128]
+  float* dgeo;       // bwd: [rows][4] += (d rhat, d w)
+  const float* rw;   // [rows][4] (rhat, w)
+  const int* nnei;
+  int n, m1, ldpg, npg;  // npg: MMA width of P [G 1] (ldpg rounded up to 16)
+  float scale, shift;
+  int* err;
+};
+
+// 32 consecutive FP32 values of one row (zeros for rows past the last
+// neighbour), 16-byte loads.
+__device__ __forceinline__ void load_row32(const float* p, bool live, float* v) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) x = reinterpret_cast<const float4*>(p)[q];
+    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+  }
+}
+
+__device__ __forceinline__ void store_split32(uint8_t* hi, uint8_t* lo, int r, int c0, const float* v) {
+  store_row32<false>(hi, r, c0, v);
+  store_row32<false, true>(lo, r, c0, v);
+}
+
+constexpr int XF_SMEM = 6 * XT + 2048 + 64;
+
+__global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_constant__ XCoreArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {  // tiles need 1024-byte alignment
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  // tiles: Q hi / lo (then P hi / lo), K hi / lo, [G 1] hi / lo
+  uint8_t* sQh = sm;
+  uint8_t* sQl = sm + XT;
+  uint8_t* sKh = sm + 2 * XT;
+  uint8_t* sKl = sm + 3 * XT;
+  uint8_t* sGh = sm + 4 * XT;
+  uint8_t* sGl = sm + 5 * XT;
+  float4* s_key = reinterpret_cast<float4*>(sm + 6 * XT);  // [128] (rhat, w)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, part = warp >> 2;
+  const int row = quad * 32 + lane, c0 = part * 32;
+  const bool issuer = tid == XC_NT - 32;
+  if (issuer) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(s_tmem, 256);
+  handoff();
+  const uint32_t tm = *s_tmem;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  const uint32_t tQh = smem_u32(sQh), tQl = smem_u32(sQl), tKh = smem_u32(sKh), tKl = smem_u32(sKl);
+  const uint32_t tGh = smem_u32(sGh), tGl = smem_u32(sGl);
+  Sync sy{bar, 0u, a.err};
+  const int ld = 3 * 128;
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const size_t base = (size_t)atom * NP;
+    const bool rv = row < nn;
+    // the next atom's Q and K rows (the first 256 columns of each row) and
+    // its layer input into L2
+    if (atom + (int)gridDim.x < a.n) {
+      const size_t nb = (size_t)(atom + gridDim.x) * NP;
+      if (tid < NP) prefetch_l2(a.QKV + (nb + tid) * ld, (uint32_t)(256 * sizeof(float)));
+      if (issuer) prefetch_l2(a.G + nb * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
+    }
+    float v[32];
+    load_row32(a.QKV + (base + row) * ld + c0, rv, v);
+    store_split32(sQh, sQl, row, c0, v);
+    load_row32(a.QKV + (base + row) * ld + 128 + c0, rv, v);
+    store_split32(sKh, sKl, row, c0, v);
+    // [G 1]: column m1 is 1 for the neighbour rows, later columns 0 (m1 % 4 == 0)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = c0 + 4 * q;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rv) {
+        if (c < a.m1) x = *reinterpret_cast<const float4*>(a.G + (base + row) * a.m1 + c);
+        else if (c == a.m1) x.x = 1.f;
+      }
+      v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+    store_split32(sGh, sGl, row, c0, v);
+    if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    handoff();
+    // S = Q K^T (three split products) -> TMEM [0, 128)
+    if (issuer) {
+      mma_block<false>(tm, tQh, false, 128, tKh, false, 128, 128, 8, false);
+      mma_block<false>(tm, tQl, false, 128, tKh, false, 128, 128, 8, true);
+      mma_block<false>(tm, tQh, false, 128, tKl, false, 128, 128, 8, true);
+    }
+    commit_and_sync(sy, issuer);
+    // smooth softmax and gate: P_jk = A_jk w_j w_k (rhat_j . rhat_k) -> Q's tiles
+    tmem_ld32(tm + lane_off + c0, v);
+    {
+      const RowXchg xr(sQh, row, part, lane, quad);  // P hi is stored after the exchanges
+      const float4 kj = s_key[row];
+      const float wj = kj.w;
+      const bool live = c0 < nn;
+      float mx = -INFINITY;
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int k = c0 + i;
+          const float l = (k < nn && rv) ? (v[i] * a.scale + a.shift) * (wj * s_key[k].w) : -INFINITY;
+          v[i] = l;
+          mx = fmaxf(mx, l);
+        }
+      }
+      mx = xr.max(mx);
+      const float mxs = mx == -INFINITY ? 0.f : mx;  // a row without neighbours: every term -inf
+      float sum = 0.f;
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float e = exp_sfu(v[i] - mxs);
+          v[i] = e;
+          sum += e;
+        }
+      }
+      sum = xr.sum(sum);
+      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float4 kk = s_key[c0 + i];
+          const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+          v[i] = v[i] * inv * (wj * kk.w) * c;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      store_split32(sQh, sQl, row, c0, v);
+    }
+    handoff();
+    // [P G, rowsum P] = P [G 1] ([G 1] as an MN-major operand) -> TMEM [128, 128 + npg)
+    if (issuer) {
+      mma_block<false>(tm + 128, tQh, false, 128, tGh, true, 128, a.npg, 8, false);
+      mma_block<false>(tm + 128, tQl, false, 128, tGh, true, 128, a.npg, 8, true);
+      mma_block<false>(tm + 128, tQh, false, 128, tGl, true, 128, a.npg, 8, true);
+    }
+    commit_and_sync(sy, issuer);
+    tmem_ld32(tm + lane_off + 128 + c0, v);
+    {
+      float4* out = reinterpret_cast<float4*>(a.PG + (base + row) * a.ldpg);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (c0 + 4 * q < a.ldpg) out[(c0 >> 2) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+// Adjoint core.  Tiles: 0 dO hi, 1 dO lo, 2 V hi then Q lo, 3 V lo then P
+// then dS, 4 K hi, 5 K lo, 6 Q hi.  TMEM: [0, 128) S, then dS, then dQ;
+// [128, 256) dP; [256, 384) dV; [384, 512) dK.
+constexpr int XB_SMEM = 7 * XT + 2048 + 64;
+
+__global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_constant__ XCoreArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint8_t* sOh = sm;
+  uint8_t* sOl = sm + XT;
+  uint8_t* s2 = sm + 2 * XT;  // V hi, then Q lo
+  uint8_t* s3 = sm + 3 * XT;  // V lo, then P, then dS
+  uint8_t* sKh = sm + 4 * XT;
+  uint8_t* sKl = sm + 5 * XT;
+  uint8_t* sQh = sm + 6 * XT;
+  float4* s_key = reinterpret_cast<float4*>(sm + 7 * XT);  // [128] (rhat, w)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, part = warp >> 2;
+  const int row = quad * 32 + lane, c0 = part * 32;
+  const bool issuer = tid == XC_NT - 32;
+  if (issuer) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(s_tmem, 512);
+  handoff();
+  const uint32_t tm = *s_tmem;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  const uint32_t tOh = smem_u32(sOh), tOl = smem_u32(sOl), t2 = smem_u32(s2), t3 = smem_u32(s3);
+  const uint32_t tKh = smem_u32(sKh), tKl = smem_u32(sKl), tQh = smem_u32(sQh);
+  Sync sy{bar, 0u, a.err};
+  const int ld = 3 * 128;
+  for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
+    const int nn = a.nnei[atom];
+    const size_t base = (size_t)atom * NP;
+    const bool rv = row < nn;
+    if (issuer && atom + (int)gridDim.x < a.n) {
+      const size_t nb = (size_t)(atom + gridDim.x) * NP;
+      prefetch_l2(a.QKV + nb * ld, (uint32_t)(NP * ld * sizeof(float)));
+      prefetch_l2(a.dO + nb * 128, (uint32_t)(NP * 128 * sizeof(float)));
+    }
+    float v[32], q32[32];
+    load_row32(a.dO + (base + row) * 128 + c0, rv, v);
+    store_split32(sOh, sOl, row, c0, v);
+    load_row32(a.QKV + (base + row) * ld + 256 + c0, rv, v);
+    store_split32(s2, s3, row, c0, v);
+    load_row32(a.QKV + (base + row) * ld + 128 + c0, rv, v);
+    store_split32(sKh, sKl, row, c0, v);
+    load_row32(a.QKV + (base + row) * ld + c0, rv, q32);
+    store_row32<false>(sQh, row, c0, q32);
+    if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    handoff();
+    // M1: dP = dO V^T -> [128, 256); S = Q_hi K^T -> [0, 128)
+    if (issuer) {
+      mma_block<false>(tm + 128, tOh, false, 128, t2, false, 128, 128, 8, false);
+      mma_block<false>(tm + 128, tOl, false, 128, t2, false, 128, 128, 8, true);
+      mma_block<false>(tm + 128, tOh, false, 128, t3, false, 128, 128, 8, true);
+      mma_block<false>(tm, tQh, false, 128, tKh, false, 128, 128, 8, false);
+      mma_block<false>(tm, tQh, false, 128, tKl, false, 128, 128, 8, true);
+    }
+    commit_and_sync(sy, issuer);
+    // V is dead: Q lo -> tile 2, then S += Q_lo K_hi
+    store_row32<false, true>(s2, row, c0, q32);
+    handoff();
+    if (issuer) mma_block<false>(tm, t2, false, 128, tKh, false, 128, 128, 8, true);
+    commit_and_sync(sy, issuer);
+    // softmax adjoint over this thread's 32 keys (S and dP re-read from TMEM
+    // in pieces of 8): A recomputed with its row max and normaliser;
+    // tsum = sum_k A_jk dA_jk with dA = dP w_j w_k c_jk; then per key
+    // dLp = A (dA - tsum), dS = dLp w_j w_k scale -> TMEM over S, P -> tile 3,
+    // dE/d(w_j w_k) = dP A c + dLp (l + shift), dE/dc = dP A w_j w_k.  The
+    // row parts (this thread's row) and column parts (lanes 0-15: key c0 + h
+    // + lane) of dE/drhat and dE/dw stay in registers.
+    float4 rpart, cpart[2];
+    {
+      const RowXchg xr(s3, row, part, lane, quad);  // V lo is dead; P goes to tile 3 after the exchanges
+      const uint32_t tS = tm + lane_off + c0, tP = tm + lane_off + 128 + c0;
+      const float4 kj = s_key[row];
+      const float wj = kj.w;
+      // the TMEM loads are warp-collective: their condition is uniform over
+      // the warp (c0), the row mask (rv) is applied per lane
+      const bool wlive = c0 < nn;
+      const bool live = wlive && rv;
+      float mx = -INFINITY;
+      if (wlive) {
+#pragma unroll
+        for (int e8 = 0; e8 < 32; e8 += 8) {
+          float t[8];
+          tmem_ld8(tS + e8, t);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = c0 + e8 + i;
+            if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_key[k].w));
+          }
+        }
+      }
+      mx = xr.max(mx);
+      const float mxs = mx == -INFINITY ? 0.f : mx;
+      float sum = 0.f, esum = 0.f;  // sum_k e_k and sum_k e_k dA_k
+      if (wlive) {
+#pragma unroll
+        for (int e8 = 0; e8 < 32; e8 += 8) {
+          float t[8], u[8];
+          tmem_ld8(tS + e8, t);
+          tmem_ld8(tP + e8, u);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = c0 + e8 + i;
+            if (k < nn && rv) {
+              const float4 kk = s_key[k];
+              const float ww = wj * kk.w;
+              const float e = exp_sfu((t[i] * a.scale + a.shift) * ww - mxs);
+              sum += e;
+              esum += e * u[i] * ww * (kj.x * kk.x + kj.y * kk.y + kj.z * kk.z);
+            }
+          }
+        }
+      }
+      const float2 ss = xr.sum2(make_float2(sum, esum));
+      const float inv = ss.x > 0.f ? 1.0f / ss.x : 0.f;
+      const float tsum = ss.y * inv;
+      float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll 1
+      for (int h = 0; h < 32; h += 16) {
+        float4 cph = make_float4(0.f, 0.f, 0.f, 0.f);
+        float cw[16], dcv[16];
+#pragma unroll
+        for (int e8 = 0; e8 < 16; e8 += 8) {
+          float t[8], u[8], pv[8];
+          tmem_ld8(tS + h + e8, t);
+          tmem_ld8(tP + h + e8, u);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int k = c0 + h + e8 + i;
+            const float4 kk = s_key[k];
+            const float ww = wj * kk.w;
+            const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+            const float lg = t[i] * a.scale + a.shift;
+            const float A = (live && k < nn) ? exp_sfu(lg * ww - mxs) * inv : 0.f;
+            const float dA = u[i] * ww * c;
+            const float dLp = A * (dA - tsum);
+            const float H = fmaf(dLp, lg, u[i] * A * c);  // dE/d(w_j w_k)
+            const float dc = u[i] * A * ww;               // dE/dc_jk
+            rw_ += H * kk.w;
+            rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
+            cw[e8 + i] = H * wj;
+            dcv[e8 + i] = dc;
+            pv[i] = A * ww * c;
+            t[i] = dLp * ww * a.scale;  // dS
+          }
+          uint4 w4;
+          w4.x = pack_bf16(pv[0], pv[1]);
+          w4.y = pack_bf16(pv[2], pv[3]);
+          w4.z = pack_bf16(pv[4], pv[5]);
+          w4.w = pack_bf16(pv[6], pv[7]);
+          sw128_store8(s3, row, c0 + h + e8, 128, w4);
+          tmem_st8_async(tS + h + e8, t);
+        }
+        cph.w = warp_reduce_scatter16(cw);
+        float tmp[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
+        cph.x = warp_reduce_scatter16(tmp);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
+        cph.y = warp_reduce_scatter16(tmp);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
+        cph.z = warp_reduce_scatter16(tmp);
+        cpart[h >> 4] = cph;
+      }
+      rpart = make_float4(rx, ry, rz, rw_);
+      tmem_wait_st();
+    }
+    handoff();
+    // M2: dV = P^T dO -> [256, 384)
+    if (issuer) {
+      mma_block<false>(tm + 256, t3, true, 128, tOh, true, 128, 128, 8, false);
+      mma_block<false>(tm + 256, t3, true, 128, tOl, true, 128, 128, 8, true);
+    }
+    commit_and_sync(sy, issuer);
+    tmem_ld32(tm + lane_off + c0, v);  // dS
+    store_row32<false>(s3, row, c0, v);
+    handoff();
+    // M3: dQ = dS K -> [0, 128); dK = dS^T Q -> [384, 512)
+    if (issuer) {
+      mma_block<false>(tm, t3, false, 128, tKh, true, 128, 128, 8, false);
+      mma_block<false>(tm, t3, false, 128, tKl, true, 128, 128, 8, true);
+      mma_block<false>(tm + 384, t3, true, 128, tQh, true, 128, 128, 8, false);
+      mma_block<false>(tm + 384, t3, true, 128, t2, true, 128, 128, 8, true);
+    }
+    commit_and_sync(sy, issuer);
+    // dQ, dK, dV -> global; the row and column parts -> tile 0 (dO is dead):
+    // [quadrant][128 keys] column parts, then [quarter][128 rows] row parts
+    {
+      float* dst = a.dQKV + (base + row) * ld + c0;
+      tmem_ld32(tm + lane_off + c0, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      tmem_ld32(tm + lane_off + 384 + c0, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst + 128)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      tmem_ld32(tm + lane_off + 256 + c0, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst + 256)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    float4* parts = reinterpret_cast<float4*>(sOh);
+    if (lane < 16) {
+      parts[quad * 128 + c0 + lane] = cpart[0];
+      parts[quad * 128 + c0 + 16 + lane] = cpart[1];
+    }
+    parts[512 + part * 128 + row] = rpart;
+    __syncthreads();
+    if (tid < nn) {
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 r = parts[512 + q * 128 + tid];
+        const float4 c = parts[q * 128 + tid];
+        s.x += r.x + c.x; s.y += r.y + c.y; s.z += r.z + c.z; s.w += r.w + c.w;
+      }
+      float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
+      float4 cur = *dg;
+      cur.x += s.x; cur.y += s.y; cur.z += s.z; cur.w += s.w;
+      *dg = cur;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+
+bool bf16x_supported(const dp_model* m) {
+  if (m->nattn > 0 && (m->A != 128 || pg_ld(m->m1) > 128 || m->m1 % 4 != 0)) return false;
+  int fan = m->fit_in;
+  if (fan % 4) return false;
+  for (int l = 0; l < m->nfit; ++l) {
+    if (m->fit[l] % 4) return false;
+    fan = m->fit[l];
+  }
+  return true;
+}
+
+namespace {
+
+XImage x_image_shape(int K, int N) {
+  XImage s;
+  s.K = K;
+  s.N = N;
+  s.nkb = (K + XBK - 1) / XBK;
+  s.nnb = (N + XBN - 1) / XBN;
+  s.bn_max = std::min(XBN, (N + 15) & ~15);
+  return s;
+}
+
+int x_image_build(dp_model* m, XImage& im, const float* B, cudaStream_t st, std::string& msg) {
+  if (!im.d) {
+    void* d = nullptr;
+    if (cudaMalloc(&d, im.bytes()) != cudaSuccess) {
+      msg = "cudaMalloc of a BF16 weight image failed";
+      return DP_ERR_CUDA;
+    }
+    m->xw.allocations.push_back(d);
+    im.d = d;
+  }
+  const long long total = (long long)im.nnb * im.nkb * im.bn_max * XBK;
+  k_x_image<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(B, im.K, im.N, im.nkb, im.bn_max,
+                                                             reinterpret_cast<uint8_t*>(im.d));
+  note_launch();
+  return DP_OK;
+}
+
+}  // namespace
+
+int bf16x_init_weights(dp_model* m, std::string& msg) {
+  XWeights& w = m->xw;
+  if (!bf16x_supported(m)) {
+    msg = "the BF16-split path needs attention width 128, an embedding width <= 124 divisible by 4 and fitting "
+          "widths divisible by 4";
+    return DP_ERR_UNSUPPORTED;
+  }
+  if (!g_x_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      msg = "cuTensorMapEncodeTiled is not available from the driver";
+      return DP_ERR_CUDA;
+    }
+    g_x_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int A = m->A, m1 = m->m1;
+  w.layers.assign(m->nattn, XWeights::Layer{});
+  for (int l = 0; l < m->nattn; ++l) {
+    XWeights::Layer& L = w.layers[l];
+    const AttnLayerW& aw = m->attn[l];
+    L.qkv = x_image_shape(m1, 3 * A);
+    L.vo = x_image_shape(pg_ld(m1), m1);
+    L.woT = x_image_shape(m1, A);
+    L.qkvT = x_image_shape(3 * A, m1);
+    int rc;
+    if ((rc = x_image_build(m, L.qkv, aw.Wqkv, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.vo, aw.Wvo, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.woT, aw.WoT, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.qkvT, aw.WqkvT, nullptr, msg)) != DP_OK) return rc;
+  }
+  w.fit.assign(m->nfit, XImage{});
+  w.fitT.assign(m->nfit, XImage{});
+  int fan = m->fit_in;
+  for (int l = 0; l < m->nfit; ++l) {
+    w.fit[l] = x_image_shape(fan, m->fit[l]);
+    w.fitT[l] = x_image_shape(m->fit[l], fan);
+    fan = m->fit[l];
+  }
+  bf16x_refresh(m, nullptr);
+  cudaFuncSetAttribute(k_gemm_bf16x, cudaFuncAttributeMaxDynamicSharedMemorySize, x_smem(XBN));
+  cudaFuncSetAttribute(k_attn_core_fwd_bf16x, cudaFuncAttributeMaxDynamicSharedMemorySize, XF_SMEM);
+  cudaFuncSetAttribute(k_attn_core_bwd_bf16x, cudaFuncAttributeMaxDynamicSharedMemorySize, XB_SMEM);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    msg = "building the BF16 weight images failed";
+    return DP_ERR_CUDA;
+  }
+  w.ready = true;
+  return DP_OK;
+}
+
+// The fitting images follow the (trainable) FP32 fitting weights.
+void bf16x_refresh(dp_model* m, cudaStream_t st) {
+  XWeights& w = m->xw;
+  std::string msg;
+  for (int l = 0; l < (int)w.fit.size(); ++l) {
+    x_image_build(m, w.fit[l], m->fitW[l], st, msg);
+    x_image_build(m, w.fitT[l], m->fitWT[l], st, msg);
+  }
+}
+
+void bf16x_free(dp_model* m) {
+  for (void* p : m->xw.allocations) cudaFree(p);
+  m->xw = XWeights{};
+}
+
+int gemm_bf16x(dp_model* m, const XImage& im, const float* A, int lda, const float* bias, const float* R, int ldr,
+               float* C, int ldc, int M, int epi, cudaStream_t st) {
+  if (M <= 0) return DP_OK;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)im.K, (cuuint64_t)M};
+  const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(float)};
+  const cuuint32_t box[2] = {32, XBM};
+  const cuuint32_t estr[2] = {1, 1};
+  if (g_x_encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return DP_ERR_CUDA;
+  XGemmArgs a;
+  a.bimg = reinterpret_cast<const uint8_t*>(im.d);
+  a.bias = bias;
+  a.R = R;
+  a.C = C;
+  a.ldr = ldr;
+  a.ldc = ldc;
+  a.M = M;
+  a.N = im.N;
+  a.nkb = im.nkb;
+  a.bn_max = im.bn_max;
+  a.epi = epi;
+  a.err = m->d_err;
+  dim3 grid((unsigned)((M + XBM - 1) / XBM), (unsigned)im.nnb);
+  k_gemm_bf16x<<<grid, XTHREADS, x_smem(im.bn_max), st>>>(map, a);
+  note_launch();
+  return DP_OK;
+}
+
+namespace {
+int x_sm_count(int dev) {
+  int c = 0;
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c > 0 ? c : 1;
+}
+
+XCoreArgs core_args(dp_model* m, int n, int l) {
+  Workspace& ws = m->ws;
+  XCoreArgs a{};
+  a.QKV = ws.QKV[l];
+  a.G = ws.G[l];
+  a.PG = ws.O[l];
+  a.dO = ws.dO;
+  a.dQKV = ws.dQKV;
+  a.dgeo = ws.dgeo;
+  a.rw = ws.rw;
+  a.nnei = ws.nnei;
+  a.n = n;
+  a.m1 = m->m1;
+  a.ldpg = pg_ld(m->m1);
+  a.npg = (a.ldpg + 15) & ~15;
+  a.scale = (float)(1.0 / std::sqrt((double)m->A));
+  a.shift = (float)m->shift;
+  a.err = m->d_err;
+  return a;
+}
+}  // namespace
+
+void attn_core_fwd_bf16x(dp_model* m, int n, int l, cudaStream_t st) {
+  if (n == 0) return;
+  const int grid = std::min(n, x_sm_count(m->device));
+  k_attn_core_fwd_bf16x<<<grid, XC_NT, XF_SMEM, st>>>(core_args(m, n, l));
+  note_launch();
+}
+
+void attn_core_bwd_bf16x(dp_model* m, int n, int l, cudaStream_t st) {
+  if (n == 0) return;
+  const int grid = std::min(n, x_sm_count(m->device));
+  k_attn_core_bwd_bf16x<<<grid, XC_NT, XB_SMEM, st>>>(core_args(m, n, l));
+  note_launch();
+}
+
+}  // namespace dpa1

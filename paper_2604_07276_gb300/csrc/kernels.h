@@ -136,7 +136,9 @@ struct AttnArgs {
   const int* nnei;
   int n, A;
   float shift;
-  float* O;          // fwd: [rows][A]
+  const float* G;    // fwd: [rows][m1] layer input
+  int m1, ldpg;      // fwd: width of G, row stride of PG (pg_ld(m1))
+  float* PG;         // fwd: [rows][ldpg] = [P G, rowsum(P), 0 ...]
   const float* dO;   // bwd: [rows][A]
   float* dQKV;       // bwd: [rows][3A]
   float* dgeo;       // bwd: [rows][4] +=

@@ -28,7 +28,12 @@ struct Arena {
 
 struct AttnLayerW {
   float *Wqkv, *bqkv, *WqkvT, *Wo, *bo, *WoT, *ln_g, *ln_b;
+  // FP32 path: [Wv Wo; bv Wo; 0...] ([pg_ld(m1)][m1]), formed in FP64, so that
+  // Y = O Wo + bo = [P G, rowsum(P)] Wvo + bo (see launch_attn_fwd_f32)
+  float* Wvo;
 };
+// Row stride of [P G, rowsum(P)]: M1 + 1 columns rounded up to 8.
+inline int pg_ld(int m1) { return (m1 + 1 + 7) & ~7; }
 
 struct TcWeights {
   bool ready = false;
@@ -48,6 +53,27 @@ struct TcWeights {
   struct EmbVectors {
     float W0[25] = {}, b0[25] = {}, b1[50] = {}, b2[100] = {};
   } emb_vec;  // embedding net's 1 -> 25 layer and biases
+};
+
+// BF16 two-term-split image of one GEMM operand B [K][N] (bf16x.cu).
+struct XImage {
+  void* d = nullptr;
+  int K = 0, N = 0, nkb = 0, nnb = 0, bn_max = 0;
+  size_t bytes() const { return (size_t)nnb * nkb * 2 * bn_max * 128; }
+};
+
+// Weight images of the BF16-split precision mode ("bf16x").
+struct XWeights {
+  bool ready = false;
+  std::vector<void*> allocations;
+  struct Layer {
+    XImage qkv;   // Wqkv [m1][3A]
+    XImage vo;    // [Wv Wo; bv Wo; 0] [pg_ld(m1)][m1]
+    XImage woT;   // Wo^T [m1][A]
+    XImage qkvT;  // Wqkv^T [3A][m1]
+  };
+  std::vector<Layer> layers;
+  std::vector<XImage> fit, fitT;  // fitting layers, forward and transposed
 };
 
 struct TcBuffers {
@@ -136,6 +162,7 @@ struct dp_model {
   std::vector<AttnLayerW> attn;
   std::vector<float*> fitW, fitWT, fitb;
   TcWeights tcw;
+  dpa1::XWeights xw;
   std::vector<void*> allocations;
   Workspace ws;
   int* d_err = nullptr;
@@ -170,6 +197,19 @@ void tc_free_weights(dp_model* m);
 bool fit_tc_supported(const dp_model* m);
 int fit_tc_init(dp_model* m, std::string& msg);
 void fit_tc_refresh(dp_model* m, cudaStream_t st);
+// BF16 two-term-split precision mode (bf16x.cu)
+bool bf16x_supported(const dp_model* m);
+int bf16x_init_weights(dp_model* m, std::string& msg);
+void bf16x_refresh(dp_model* m, cudaStream_t st);
+void bf16x_free(dp_model* m);
+int gemm_bf16x(dp_model* m, const XImage& im, const float* A, int lda, const float* bias, const float* R, int ldr,
+               float* C, int ldc, int M, int epi, cudaStream_t st);
+void attn_core_fwd_bf16x(dp_model* m, int n, int l, cudaStream_t st);
+void attn_core_bwd_bf16x(dp_model* m, int n, int l, cudaStream_t st);
+// the fused 16-bit layer kernels (tc.cu) serve DP_PREC_BF16 and DP_PREC_FP16X;
+// DP_PREC_FP32 and DP_PREC_BF16X share the modular layer layout (row-major G,
+// stored Q K V, LayerNorm kernels)
+inline bool fused_tc_precision(int p) { return p == DP_PREC_BF16 || p == DP_PREC_FP16X; }
 int fit_gemm_tc(dp_model* m, int layer, bool backward, const float* A, int lda, const float* bias, const float* R,
                 int ldr, float* C, int ldc, int M, int epi, cudaStream_t st);
 // stages a7-a11 (descriptor, fitting forward / backward, descriptor backward)

@@ -530,6 +530,7 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
 // Per centre atom, over its valid neighbour slots j, k < n_i:
 //   l_jk = Q_j.K_k / sqrt(A);  l'_jk = (l_jk + S) w_j w_k - S
 //   A_jk = softmax_k(l'_jk);   P_jk = A_jk w_j w_k (rhat_j . rhat_k);  O = P V
+// (the forward evaluates O Wo through P G, see k_attn_fwd_f32)
 
 // Smooth logits l'_jk = (l_jk + S) w_j w_k carry the shift S = 20, whose
 // FP32 spacing (2e-6) is far coarser than the logit differences that matter.
@@ -573,10 +574,21 @@ __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b
 
 // Forward, register-tiled: 256 threads as a 16 x 16 grid.  Thread (ty, tx)
 // owns rows 8 ty .. 8 ty + 7 and keys 8 tx .. 8 tx + 7 of S (128 x 128), then
-// rows 8 ty .. and features 8 tx .. of each 128-feature part of O.  Q and K
+// rows 8 ty .. and columns 8 tx .. of each 128-column part of PG.  Q and K
 // pass through shared memory feature-major, 128 features at a time; P stays
-// row-major and V comes in 128-feature parts, key-major.  S sums over the
-// features and O over the keys in order, as a plain loop would.
+// row-major and [G 1] comes in 128-column parts, key-major.  S sums over the
+// features and PG over the keys in order, as a plain loop would.
+//
+// The kernel writes PG = [P G, rowsum(P)] instead of O = P V: with V = G Wv +
+// bv, O Wo + bo = [P G, rowsum(P)] [Wv Wo; bv Wo] + bo, which a GEMM with the
+// FP64-formed [Wv Wo; bv Wo] then evaluates.  The two are equal in exact
+// arithmetic, but the gate (rhat_j . rhat_k of both signs) makes sum_k P_jk
+// V_k cancel, and the accumulation errors of each computed V_k (a 100-term
+// FP32 sum) survive that cancellation; the LayerNorm of weakly attended rows
+// (variance << eps) then turns them into force errors up to ~5e-4 eV/A on
+// a few atoms.  Summing the exact layer input G instead leaves only the
+// rounding of the cancelling sum itself (a CPU emulation of both forms on the
+// 15,668-atom box: force RMSE 7.5e-6 -> 2.4e-6 eV/A).
 constexpr int FT = 256;        // threads of the forward
 constexpr int TLD = NP + 4;    // row stride of its shared tiles (16-byte rows)
 
@@ -680,15 +692,19 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
       *reinterpret_cast<float4*>(X + j * TLD + 8 * tx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
       *reinterpret_cast<float4*>(X + j * TLD + 8 * tx + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
     }
-    // O = P V, 128 features at a time
+    // PG = P [G 1], 128 columns at a time (column m1 of [G 1] is 1, later
+    // ones 0; m1 % 4 == 0)
     const int nn4 = (nn + 3) & ~3;
-    for (int c0 = 0; c0 < A; c0 += 128) {
+    for (int c0 = 0; c0 < a.ldpg; c0 += 128) {
       if (c0 > 0) __syncthreads();  // the previous part's products are done
       for (int idx = tid; idx < NP * 32; idx += FT) {
-        const int k = idx >> 5, f = 4 * (idx & 31);
+        const int k = idx >> 5, f = c0 + 4 * (idx & 31);
         float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < nn) vv = *reinterpret_cast<const float4*>(a.QKV + (base + k) * ld + 2 * A + c0 + f);
-        *reinterpret_cast<float4*>(Y + k * TLD + f) = vv;
+        if (k < nn) {
+          if (f < a.m1) vv = *reinterpret_cast<const float4*>(a.G + (base + k) * a.m1 + f);
+          else if (f == a.m1) vv.x = 1.f;
+        }
+        *reinterpret_cast<float4*>(Y + k * TLD + f - c0) = vv;
       }
       __syncthreads();  // P (first part) and this part of V are in place
       float acc[8][8];
@@ -715,11 +731,13 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
           }
         }
       }
+      if (c0 + 8 * tx < a.ldpg) {  // ldpg % 8 == 0
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float* o = a.O + (base + 8 * ty + i) * A + c0 + 8 * tx;
-        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        for (int i = 0; i < 8; ++i) {
+          float* o = a.PG + (base + 8 * ty + i) * a.ldpg + c0 + 8 * tx;
+          *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+          *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        }
       }
     }
   }

@@ -68,6 +68,18 @@ def test_fp16x_whole_box(default_model, box_ref):
     assert err["W_rel"] <= 5e-3
 
 
+def test_bf16x_whole_box(default_model, box_ref):
+    """BF16 operands with two-term splits: the BF16 path's bounds."""
+    import paper_2604_07276_gb300 as p
+
+    cfg, w, _ = default_model
+    err = _errors(p, cfg, w, box_ref, "bf16x")
+    assert err["force_rmse"] <= BF16_FORCE_RMSE
+    assert err["e_max"] <= BF16_ATOM_ENERGY
+    assert err["E_per_atom"] <= BF16_ATOM_ENERGY
+    assert err["W_rel"] <= 5e-3
+
+
 def test_bf16_plain_whole_box_envelope(default_model, box_ref):
     """Plain BF16 operands (no splits) are reported, not held to the 16-bit
     bounds: a CPU emulation of their rounding points shows that G, P, V, Q,

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 CASES = [(0.012, 41), (0.04, 42), (0.065, 43)]
 
 
-@pytest.mark.parametrize("precision", ["fp16x", "fp32"])
+@pytest.mark.parametrize("precision", ["fp16x", "bf16x", "fp32"])
 @pytest.mark.parametrize("density,seed", CASES)
 def test_sparse_box(default_model, precision, density, seed):
     import paper_2604_07276_gb300 as p
