@@ -6,7 +6,10 @@ that only lends its own pooled buffers, code inside a host callback or a
 captured stream), so this entry point keeps its scratch in a fixed device
 array.  Its list must be identical to the regular entry point's, on two
 calls in a row (the shared scratch keeps the previous call's contents).
-This file is named so that pytest collects it last."""
+
+The file name makes pytest collect it last, so that a run stopping at the
+first failure (-x) has run every other test before this one; the tests
+depend on no order and also pass alone in a fresh process."""
 
 import numpy as np
 import pytest
@@ -65,3 +68,35 @@ def test_noalloc_nlist_rejects_oversize():
         p.binding.nlist_noalloc(c, b, 6.0, 120, nl, nn, st)
     assert ei.value.code == -4
     assert "65536" in str(ei.value)
+
+
+def test_noalloc_nlist_empty_and_device_status():
+    """natoms == 0 accepts null coordinate and output pointers and leaves the
+    status at 0; a box edge <= 2 rcut sets status bit 1 and a non-finite
+    coordinate bit 4 (both found by the kernels, which skip the bad input)."""
+    import torch
+    import paper_2604_07276_gb300 as p
+
+    st = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+    b = torch.tensor(p.box9([30.0, 30.0, 30.0]), dtype=torch.float64, device="cuda")
+    lib = p.load_library()
+    p.binding._check(lib.dp_nlist_noalloc(0, None, b.data_ptr(), 6.0, 120, None, None, st.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+
+    coord, atype, box = synth.water_box(0)
+    c = torch.tensor(coord, dtype=torch.float64, device="cuda")
+    small = torch.tensor(p.box9([11.0, 12.4, 12.4]), dtype=torch.float64, device="cuda")
+    _, _, status = _run_noalloc(p, torch, c, small, 6.0, 120)
+    assert status & 1
+    bad = coord.copy()
+    bad[5, 2] = np.nan
+    cb = torch.tensor(bad, dtype=torch.float64, device="cuda")
+    b = torch.tensor(p.box9(box), dtype=torch.float64, device="cuda")
+    nl, nn, status = _run_noalloc(p, torch, cb, b, 6.0, 120)
+    assert status & 4
+    assert nn[5] == 0
+    # a good call afterwards starts from a cleared status
+    _, _, status = _run_noalloc(p, torch, c, b, 6.0, 120)
+    assert status == 0
