@@ -78,6 +78,8 @@ def _args():
     ap.add_argument("--no-student", action="store_true", help="skip the distilled-student line")
     ap.add_argument("--model", default="dpa1", choices=sorted(MODELS), help="dpa1: the measured model")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-frame dp_compute_batch line")
+    ap.add_argument("--scale-natoms", type=int, default=250000,
+                    help="atoms of the scale box timed after the main line (fp16x; 0: skip)")
     return ap.parse_args()
 
 
@@ -226,6 +228,63 @@ def _student_line(dev, coord, atype, box, full_rates, batch=16, md_steps=100):
             "train_frames_per_s": batch / train_s, "md_atom_steps_per_s": rates,
             "md_speedup_vs_full_fp16x": {p: r / full_rates["fp16x"] for p, r in rates.items()} if "fp16x" in full_rates
             else None}
+
+
+def _scale_line(a, dev, cfg, wpath, steps=5):
+    """The scale configuration: the same recipe at a.scale_natoms atoms (seed
+    4), fp16x, device-resident inputs; step time, device memory of the model
+    and sampled parity against the oracle (exact forces on 4 atoms from the
+    atomic energies of the centres that depend on them)."""
+    import torch
+
+    import synth
+    import paper_2604_07276_gb300 as dp
+
+    n = a.scale_natoms
+    coord, atype, box = synth.lattice_system(n, seed=4)
+    torch.cuda.synchronize(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    m = dp.DPA1(wpath, precision="fp16x", device=dev.index)
+    m.reserve(n)
+    torch.cuda.synchronize(dev)
+    mem = free0 - torch.cuda.mem_get_info(dev)[0]
+    c = torch.tensor(coord, dtype=torch.float64, device=dev)
+    t = torch.tensor(atype, dtype=torch.int32, device=dev)
+    b = torch.tensor(dp.box9(box), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    W = torch.zeros(9, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(2):
+        m.compute_device(c, b, t, E, F, W, stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    m.status()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        m.compute_device(c, b, t, E, F, W, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    m.status()
+    ms = e0.elapsed_time(e1) / steps
+    line = {"natoms": n, "precision": "fp16x", "steps": steps, "ms_per_step": ms, "atom_steps_per_s": n / (ms / 1e3),
+            "device_memory_bytes": mem, "workload": workload(n).replace("seed 1", "seed 4")}
+    if not a.no_parity:
+        from oracle import OracleModel, energy_force_virial, reverse_centres
+
+        _, Fh, _, eh = m.compute(coord, box, atype, atom_energy=True)
+        om = OracleModel.from_numpy(cfg, synth.make_weights(cfg, seed=0))
+        atoms = np.sort(np.random.default_rng(9).choice(n, size=4, replace=False))
+        cs = reverse_centres(coord, box, cfg.rcut, cfg.sel, atoms)
+        _, e_ref, f_ref, _ = energy_force_virial(om, coord, box, atype, centres=cs)
+        line["sampled_parity"] = {"force_rmse_ev_per_A": float(np.sqrt(np.mean((Fh[atoms] - f_ref[atoms]) ** 2))),
+                                  "atoms": len(atoms),
+                                  "atomic_energy_max_abs_err_eV": float(np.abs(eh[cs] - e_ref).max()),
+                                  "centres": int(len(cs)),
+                                  "sum_of_forces_max_abs": float(np.abs(Fh.sum(axis=0)).max())}
+    m.close()
+    return line
 
 
 class Clocks:
@@ -514,6 +573,13 @@ def run_ours(a):
                          "within_fp32_bound": bool(np.sqrt(np.mean((Fp - f_ref) ** 2)) <= 1e-5)}
         parity["oracle_seconds"] = t_oracle
 
+    scale = None
+    if rank == 0 and a.scale_natoms > 0 and "fp16x" in models:
+        for mm in models.values():
+            mm.close()
+        models.clear()
+        scale = _scale_line(a, dev, cfg, wpath)
+
     if rank != 0:
         return 0
     r = results[head]
@@ -582,6 +648,7 @@ def run_ours(a):
         "md": md_line,
         "student": student,
         "batch": batch,
+        "scale": scale,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -303,6 +303,9 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.atom_energy = a.take<double>(cap);
     ws.atype = a.take<int>(cap);
     if (fused_tc_precision(m->precision)) tc_plan_buffers(m, a, cap);
+    // bf16x with the tensor-core embedding net: its layers 1 and 2 for the adjoint
+    if (m->precision == DP_PREC_BF16X && m->tcw.emb_W2_t)
+      ws.tc.p[5] = a.take<float>(rows * (size_t)(m->emb[0] + m->emb[1]));
   };
   Arena probe;
   plan(probe);
@@ -516,16 +519,23 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
 }
 
 // The BF16-split network path (stages a5-a13): the layout and stage order of
-// the FP32 path, with every product of the attention layers and of the
-// fitting net on tcgen05 (bf16x.cu); embedding net, LayerNorm and descriptor
-// in FP32.
+// the FP32 path, with every product of the attention layers, of the fitting
+// net and of the embedding net on tcgen05 (bf16x.cu, tc.cu); LayerNorm and
+// descriptor in FP32.
 void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
   Workspace& ws = m->ws;
   const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
+  // the 25-50-100 embedding net on the tensor cores (BF16 two-term splits),
+  // other nets in FP32
+  const bool emb_tc = m->tcw.emb_W2_t != nullptr;
+  float* H12 = reinterpret_cast<float*>(ws.tc.p[5]);
   EmbedArgs ea{};
   ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
   ea.w = m->emb_packed; ea.Gt = m->Gt; ea.b0t = m->b0t; ea.G0 = ws.G[0];
-  launch_embed_fwd(ea, m->emb, st);
+  if (emb_tc)
+    tc_embed_bf16(m, n, atype, false, ws.G[0], nullptr, nullptr, H12, st);
+  else
+    launch_embed_fwd(ea, m->emb, st);
   prof_mark(m, "embed_fwd", st);
   for (int l = 0; l < L; ++l) {
     const AttnLayerW& w = m->attn[l];
@@ -553,7 +563,10 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
     prof_mark(m, "qkv_bwd_gemm", st);
   }
   ea.dG0 = ws.dG; ea.dR = ws.dR;
-  launch_embed_bwd(ea, m->emb, st);
+  if (emb_tc)
+    tc_embed_bf16(m, n, atype, true, nullptr, ws.dG, ws.dR, H12, st);
+  else
+    launch_embed_bwd(ea, m->emb, st);
   prof_mark(m, "embed_bwd", st);
 }
 
@@ -911,6 +924,7 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     if ((rc = tc_init_weights(m, w.arrays, msg)) != DP_OK) return fail_free(fail(rc, msg));
   } else if (precision == DP_PREC_BF16X) {
     std::string msg;
+    if ((rc = tc_init_embedding(m, w.arrays, msg)) != DP_OK) return fail_free(fail(rc, msg));
     if ((rc = bf16x_init_weights(m, msg)) != DP_OK) return fail_free(fail(rc, msg));
   }
   {

@@ -46,17 +46,20 @@ namespace {
 
 // ------------------------------------------------------------------- GEMM
 // C = epi(A B + bias (+ R)), A [M][K] FP32 row-major, B [K][N] from a
-// pre-split image.  One CTA: a 128-row x (<= 192)-column tile with the full
-// K in stages of 64:
+// pre-split image.  Persistent: CTA (x, y) keeps N block y (<= 192 columns)
+// and walks the 128-row tiles x, x + gridDim.x, ...; the K loop runs in
+// stages of 64 through a two-stage ring that continues across tiles, and
+// the accumulator alternates between two TMEM buffers, so that the epilogue
+// of one tile overlaps the loads and products of the next.
 //   warp 0      : producer.  Two TMA boxes of A (128 rows x 32 K FP32,
 //                 128-byte swizzle) and the B hi / lo tiles (bulk copies).
 //   warps 4-7   : split the stage's FP32 A into its BF16 hi and lo tiles
 //                 (K-major, 128-byte swizzle); thread t owns row t.
-//   warp 1      : issues the MMAs (one thread); accumulator in TMEM.
+//   warp 1      : issues the MMAs (one thread).
 //   warp 2      : allocates / frees TMEM.
-//   all 8 warps : epilogue (TMEM -> bias, tanh, residual / accumulate ->
-//                 global).
-constexpr int XBM = 128, XBK = 64, XBN = 192, XSTAGES = 2, XTHREADS = 256;
+//   warps 8-11  : epilogue (TMEM lane quadrant w - 8 -> bias, tanh,
+//                 residual / accumulate -> global).
+constexpr int XBM = 128, XBK = 64, XBN = 192, XSTAGES = 2, XTHREADS = 384;
 constexpr int XF32 = 2 * XBM * 32 * 4;  // FP32 staging of one stage: two TMA boxes (32 KB)
 constexpr int XAT = XBM * XBK * 2;      // one BF16 A tile (hi or lo): 16 KB
 
@@ -66,7 +69,7 @@ struct XGemmArgs {
   const float* R;       // residual [M][ldr] or null
   float* C;             // [M][ldc]
   int ldr, ldc;
-  int M, N, nkb, bn_max, epi;
+  int M, N, nkb, bn_max, epi, mtiles;
   int* err;
 };
 
@@ -96,16 +99,17 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
   extern __shared__ uint8_t xsm_raw[];
   const uint32_t raw = smem_u32(xsm_raw);
   uint8_t* sm = xsm_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned tiles
-  const int mb = blockIdx.x, nb = blockIdx.y;
-  const int bn = min(XBN, ((a.N - nb * XBN) + 15) & ~15);  // MMA width of this tile
+  const int nb = blockIdx.y;
+  const int bn = min(XBN, ((a.N - nb * XBN) + 15) & ~15);  // MMA width of this N block
   const int b_tile = a.bn_max * 128;
   const int stage_bytes = XF32 + 2 * XAT + 2 * b_tile;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + XSTAGES * stage_bytes);
   uint64_t* full = bars;                 // [XSTAGES] A boxes and B tiles arrived
   uint64_t* conv = bars + XSTAGES;       // [XSTAGES] A split into hi / lo (128 arrivals)
   uint64_t* empty = bars + 2 * XSTAGES;  // [XSTAGES] the stage's MMAs are done
-  uint64_t* done = bars + 3 * XSTAGES;
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = bars + 3 * XSTAGES;  // [2] accumulator buffer complete
+  uint64_t* tempty = tfull + 2;          // [2] accumulator buffer read out (4 warp arrivals)
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(tempty + 2);
   auto sF = [&](int s) { return sm + s * stage_bytes; };
   auto sAh = [&](int s) { return sm + s * stage_bytes + XF32; };
   auto sAl = [&](int s) { return sm + s * stage_bytes + XF32 + XAT; };
@@ -119,10 +123,13 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
       mbar_init(conv + s, 128);
       mbar_init(empty + s, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, 4);
+    }
     fence_mbar_init();
   }
-  if (warp == 2) tmem_alloc(s_tmem, 256);
+  if (warp == 2) tmem_alloc(s_tmem, 512);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -131,48 +138,58 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
   auto wait = [&](uint64_t* bar, uint32_t parity) {
     if (ok) ok = mbar_wait(bar, parity, a.err);
   };
+  const int ntile = a.mtiles > (int)blockIdx.x ? (a.mtiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0 && lane == 0) {
     const uint8_t* img = a.bimg + (size_t)nb * a.nkb * 2 * b_tile;
-    for (int kb = 0; kb < a.nkb && ok; ++kb) {
-      const int s = kb % XSTAGES, u = kb / XSTAGES;
-      if (kb >= XSTAGES) wait(empty + s, (u - 1) & 1);
-      if (!ok) break;
-      mbar_expect_tx(full + s, XF32 + 2 * bn * 128);
-      x_tma_load_2d(sF(s), &tmA, kb * XBK, mb * XBM, full + s);
-      x_tma_load_2d(sF(s) + XF32 / 2, &tmA, kb * XBK + 32, mb * XBM, full + s);
-      bulk_g2s(sBh(s), img + (size_t)(2 * kb) * b_tile, bn * 128, full + s);
-      bulk_g2s(sBl(s), img + (size_t)(2 * kb + 1) * b_tile, bn * 128, full + s);
+    for (int it = 0; it < ntile && ok; ++it) {
+      const int mb = blockIdx.x + it * gridDim.x;
+      for (int kb = 0; kb < a.nkb && ok; ++kb) {
+        const int g = it * a.nkb + kb, s = g % XSTAGES, u = g / XSTAGES;
+        if (g >= XSTAGES) wait(empty + s, (u - 1) & 1);
+        if (!ok) break;
+        mbar_expect_tx(full + s, XF32 + 2 * bn * 128);
+        x_tma_load_2d(sF(s), &tmA, kb * XBK, mb * XBM, full + s);
+        x_tma_load_2d(sF(s) + XF32 / 2, &tmA, kb * XBK + 32, mb * XBM, full + s);
+        bulk_g2s(sBh(s), img + (size_t)(2 * kb) * b_tile, bn * 128, full + s);
+        bulk_g2s(sBl(s), img + (size_t)(2 * kb + 1) * b_tile, bn * 128, full + s);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t id = idesc_16(XBM, bn, false, false, false);
-    for (int kb = 0; kb < a.nkb && ok; ++kb) {
-      const int s = kb % XSTAGES, u = kb / XSTAGES;
-      wait(conv + s, u & 1);
+    for (int it = 0; it < ntile && ok; ++it) {
+      const int b = it & 1;
+      const uint32_t acc = tm + (uint32_t)(b * 256);
+      if (it >= 2) wait(tempty + b, ((it >> 1) - 1) & 1);
       fence_after_sync();
-      if (ok) {
-        const uint32_t ah = smem_u32(sAh(s)), al = smem_u32(sAl(s));
-        const uint32_t bh = smem_u32(sBh(s)), bl = smem_u32(sBl(s));
+      for (int kb = 0; kb < a.nkb && ok; ++kb) {
+        const int g = it * a.nkb + kb, s = g % XSTAGES, u = g / XSTAGES;
+        wait(conv + s, u & 1);
+        fence_after_sync();
+        if (ok) {
+          const uint32_t ah = smem_u32(sAh(s)), al = smem_u32(sAl(s));
+          const uint32_t bh = smem_u32(sBh(s)), bl = smem_u32(sBl(s));
 #pragma unroll
-        for (int ks = 0; ks < XBK / 16; ++ks) {
-          const uint64_t dah = kmajor_desc(ah, ks, XBM), dal = kmajor_desc(al, ks, XBM);
-          const uint64_t dbh = kmajor_desc(bh, ks, bn), dbl = kmajor_desc(bl, ks, bn);
-          mma_bf16(tm, dah, dbh, id, (kb > 0 || ks > 0) ? 1u : 0u);
-          mma_bf16(tm, dal, dbh, id, 1u);
-          mma_bf16(tm, dah, dbl, id, 1u);
+          for (int ks = 0; ks < XBK / 16; ++ks) {
+            const uint64_t dah = kmajor_desc(ah, ks, XBM), dal = kmajor_desc(al, ks, XBM);
+            const uint64_t dbh = kmajor_desc(bh, ks, bn), dbl = kmajor_desc(bl, ks, bn);
+            mma_bf16(acc, dah, dbh, id, (kb > 0 || ks > 0) ? 1u : 0u);
+            mma_bf16(acc, dal, dbh, id, 1u);
+            mma_bf16(acc, dah, dbl, id, 1u);
+          }
         }
+        mma_commit(empty + s);
       }
-      mma_commit(empty + s);
+      mma_commit(tfull + b);
     }
-    mma_commit(done);
-  } else if (warp >= 4) {
+  } else if (warp >= 4 && warp < 8) {
     // row r of the stage: FP32 K 0..31 in box 0, 32..63 in box 1, each row a
     // 128-byte line whose 16-byte pieces are permuted by XOR with r % 8; its
     // BF16 row is one 128-byte line with the same permutation
     const int r = threadIdx.x - 128;
     const uint32_t line = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128);
-    for (int kb = 0; kb < a.nkb && ok; ++kb) {
-      const int s = kb % XSTAGES, u = kb / XSTAGES;
+    for (int g = 0; g < ntile * a.nkb && ok; ++g) {
+      const int s = g % XSTAGES, u = g / XSTAGES;
       wait(full + s, u & 1);
       const uint8_t* f = sF(s);
 #pragma unroll
@@ -191,49 +208,54 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
       fence_async_smem();
       mbar_arrive(conv + s);
     }
-  }
-  // epilogue, all warps
-  __syncwarp();
-  wait(done, 0);
-  fence_after_sync();
-  {
-    const int r = (warp & 3) * 32 + lane;  // row in the tile = TMEM lane
-    const long long m = (long long)mb * XBM + r;
-    const uint32_t taddr = tm + ((uint32_t)((warp & 3) * 32) << 16);
-    for (int c0 = (warp >> 2) * 16; c0 < bn; c0 += 32) {
-      float v[16];
-      tmem_ld16(taddr + c0, v);
-      if (m >= a.M || !ok) continue;
+  } else if (warp >= 8) {
+    const int quad = warp - 8;
+    const int r = quad * 32 + lane;  // row in the tile = TMEM lane
+    for (int it = 0; it < ntile && ok; ++it) {
+      const int b = it & 1;
+      wait(tfull + b, (it >> 1) & 1);
+      fence_after_sync();
+      const long long m = (long long)(blockIdx.x + it * gridDim.x) * XBM + r;
+      const uint32_t taddr = tm + (uint32_t)(b * 256) + ((uint32_t)(quad * 32) << 16);
+      for (int c0 = 0; c0 < bn; c0 += 16) {
+        float v[16];
+        tmem_ld16(taddr + c0, v);
+        if (m >= a.M || !ok) continue;
 #pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        const int n = nb * XBN + c0 + q;
-        if (n >= a.N) break;  // N % 4 == 0
-        float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        float* op = &o.x;
-        if (a.bias) {
+        for (int q = 0; q < 16; q += 4) {
+          const int n = nb * XBN + c0 + q;
+          if (n >= a.N) break;  // N % 4 == 0
+          float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          float* op = &o.x;
+          if (a.bias) {
 #pragma unroll
-          for (int t = 0; t < 4; ++t) op[t] += a.bias[n + t];
-        }
-        if (a.epi == EPI_TANH || a.epi == EPI_RES_TANH) {
+            for (int t = 0; t < 4; ++t) op[t] += a.bias[n + t];
+          }
+          if (a.epi == EPI_TANH || a.epi == EPI_RES_TANH) {
 #pragma unroll
-          for (int t = 0; t < 4; ++t) op[t] = tanhf(op[t]);
+            for (int t = 0; t < 4; ++t) op[t] = tanhf(op[t]);
+          }
+          if (a.epi == EPI_RES_TANH || a.epi == EPI_RES) {
+            const float4 rr = *reinterpret_cast<const float4*>(a.R + m * a.ldr + n);
+            o.x += rr.x; o.y += rr.y; o.z += rr.z; o.w += rr.w;
+          }
+          float4* cp = reinterpret_cast<float4*>(a.C + m * a.ldc + n);
+          if (a.epi == EPI_ACCUM) {
+            const float4 cc = *cp;
+            o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
+          }
+          *cp = o;
         }
-        if (a.epi == EPI_RES_TANH || a.epi == EPI_RES) {
-          const float4 rr = *reinterpret_cast<const float4*>(a.R + m * a.ldr + n);
-          o.x += rr.x; o.y += rr.y; o.z += rr.z; o.w += rr.w;
-        }
-        float4* cp = reinterpret_cast<float4*>(a.C + m * a.ldc + n);
-        if (a.epi == EPI_ACCUM) {
-          const float4 cc = *cp;
-          o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
-        }
-        *cp = o;
       }
+      // the buffer is read: the MMAs of tile it + 2 may overwrite it
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
     }
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 2) tmem_dealloc(tm, 256);
+  if (warp == 2) tmem_dealloc(tm, 512);
 }
 
 // B image of one product, built on the device from B [K][N] (FP32,
@@ -263,6 +285,12 @@ __global__ void k_x_image(const float* __restrict__ B, int K, int N, int nkb, in
 PFN_cuTensorMapEncodeTiled_v12000 g_x_encode = nullptr;
 
 int x_smem(int bn_max) { return XSTAGES * (XF32 + 2 * XAT + 2 * bn_max * 128) + 1024 + 128; }
+
+int x_sm_count(int dev) {
+  int c = 0;
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c > 0 ? c : 1;
+}
 
 // ------------------------------------------------------ attention cores
 // One persistent CTA of 512 threads per SM walks over centre atoms; warp w
@@ -817,20 +845,17 @@ int gemm_bf16x(dp_model* m, const XImage& im, const float* A, int lda, const flo
   a.nkb = im.nkb;
   a.bn_max = im.bn_max;
   a.epi = epi;
+  a.mtiles = (M + XBM - 1) / XBM;
   a.err = m->d_err;
-  dim3 grid((unsigned)((M + XBM - 1) / XBM), (unsigned)im.nnb);
+  // persistent: about one CTA per SM over the N blocks
+  const int per_n = std::max(1, x_sm_count(m->device) / im.nnb);
+  dim3 grid((unsigned)std::min(a.mtiles, per_n), (unsigned)im.nnb);
   k_gemm_bf16x<<<grid, XTHREADS, x_smem(im.bn_max), st>>>(map, a);
   note_launch();
   return DP_OK;
 }
 
 namespace {
-int x_sm_count(int dev) {
-  int c = 0;
-  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-  return c > 0 ? c : 1;
-}
-
 XCoreArgs core_args(dp_model* m, int n, int l) {
   Workspace& ws = m->ws;
   XCoreArgs a{};

@@ -42,8 +42,8 @@ struct TcWeights {
   // tcgen05 B operand
   std::vector<void*> Wqkv_t, Wo_t, WoT_t, WqkvT_t;
   std::vector<void*> fitW_t, fitWT_t;
-  void* emb_W1_t = nullptr;
-  void* emb_W2_t = nullptr;
+  void* emb_W1_t = nullptr;  // embedding net W1 / W2 hi + lo tiles, FP16 (fused 16-bit paths)
+  void* emb_W2_t = nullptr;  // the same in BF16 (bf16x)
   struct Vectors {
     float bo[128] = {};
     float gamma[128] = {};
@@ -190,6 +190,9 @@ namespace dpa1 {
 using HostArrays = std::vector<std::pair<std::string, std::vector<double>>>;
 // tensor-core (BF16) path, tc.cu
 int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg);
+int tc_init_embedding(dp_model* m, const HostArrays& arrays, std::string& msg);
+void tc_embed_bf16(dp_model* m, int n, const int* atype, bool bwd, float* G0, const float* dG0, float* dR,
+                   float* H12, cudaStream_t st);
 void tc_plan_buffers(dp_model* m, Arena& a, int cap);
 void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st);
 void tc_free_weights(dp_model* m);

@@ -770,15 +770,16 @@ struct EmbedTcArgs {
   const int* nnei;
   const int* atype;
   const float* Gt;        // [ntypes][ntypes][E2]
-  float* G0;              // fwd out, column-quad interleaved per atom
-  const float* dG0;       // bwd in, column-quad interleaved per atom
+  float* G0;              // fwd out, column-quad interleaved per atom (rm: row-major [rows][E2])
+  const float* dG0;       // bwd in, same layout as G0
   float* dR;              // bwd: dR[:,0] +=
   const float* b0t;       // concat type-embedding mode: first-layer bias per (centre,
                           // neighbour) type [ntypes][ntypes][E0]; null: b0 below
   float* H12;             // [atom][E0 + E1 units][NP rows]: layers 1 and 2 of the net,
                           // written by the forward, read by the adjoint
-  const uint4* wimg;      // W1/W2 hi/lo tiles
+  const uint4* wimg;      // W1/W2 hi/lo tiles (FP16 or BF16, as the kernel's operands)
   int n, ntypes;
+  int rm;                 // G0 and dG0 row-major (the modular layer layout) instead of interleaved
   int* err;
   float W0[EMB_E0], b0[EMB_E0], b1[EMB_E1], b2[EMB_E2];
 };
@@ -792,22 +793,24 @@ struct EmbedTcArgs {
 constexpr int EMB_THREADS = 256;
 constexpr int EMB_SPLIT = 24;  // first layer-2 unit of half 1
 
+template <bool F16>
 __device__ __forceinline__ void emb_store8(uint8_t* tile, int r, int c0, int R, const float* v, bool lo) {
   float x[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) x[i] = lo ? v[i] - round16<true>(v[i]) : v[i];
+  for (int i = 0; i < 8; ++i) x[i] = lo ? v[i] - round16<F16>(v[i]) : v[i];
   uint4 u;
-  u.x = pack_f16(x[0], x[1]); u.y = pack_f16(x[2], x[3]);
-  u.z = pack_f16(x[4], x[5]); u.w = pack_f16(x[6], x[7]);
+  u.x = pack16<F16>(x[0], x[1]); u.y = pack16<F16>(x[2], x[3]);
+  u.z = pack16<F16>(x[4], x[5]); u.w = pack16<F16>(x[6], x[7]);
   sw128_store8(tile, r, c0, R, u);
 }
 
 // D (+)= A * B with A = Ah + Al and B = Bh + Bl, dropping Al * Bl.
+template <bool F16>
 __device__ __forceinline__ void mma_split(uint32_t d, uint32_t ah, uint32_t al, int a_rows, uint32_t bh, uint32_t bl,
                                           bool b_mn, int b_rows, int N, int ksteps) {
-  mma_block<true>(d, ah, false, a_rows, bh, b_mn, b_rows, N, ksteps, false);
-  mma_block<true>(d, al, false, a_rows, bh, b_mn, b_rows, N, ksteps, true);
-  mma_block<true>(d, ah, false, a_rows, bl, b_mn, b_rows, N, ksteps, true);
+  mma_block<F16>(d, ah, false, a_rows, bh, b_mn, b_rows, N, ksteps, false);
+  mma_block<F16>(d, al, false, a_rows, bh, b_mn, b_rows, N, ksteps, true);
+  mma_block<F16>(d, ah, false, a_rows, bl, b_mn, b_rows, N, ksteps, true);
 }
 
 template <int H>
@@ -821,7 +824,7 @@ struct EmbOwn {
 // Layers 1 and 2 of a row and the issue of Z3 = H2 W2; returns once Z3 is in
 // TMEM columns [64, 176).  h1 gets all 25 layer-1 units, h2 the owned
 // layer-2 units.
-template <int H, class BeforeZ3>
+template <bool F16, int H, class BeforeZ3>
 __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
                                                Sync& sy, int row, bool rv, float x, const float* b0row, float* h1,
                                                float* h2, BeforeZ3 before_z3) {
@@ -846,15 +849,15 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
     float v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = p0 + i < EMB_E0 ? h1[p0 + i] : 0.f;
-    emb_store8(sH1h, row, p0, 128, v, false);
-    emb_store8(sH1l, row, p0, 128, v, true);
-    emb_store8(sH1h, row, p0 + 8, 128, v + 8, false);
-    emb_store8(sH1l, row, p0 + 8, 128, v + 8, true);
+    emb_store8<F16>(sH1h, row, p0, 128, v, false);
+    emb_store8<F16>(sH1l, row, p0, 128, v, true);
+    emb_store8<F16>(sH1h, row, p0 + 8, 128, v + 8, false);
+    emb_store8<F16>(sH1l, row, p0 + 8, 128, v + 8, true);
     tmem_st16(tm + lane_off + 176 + p0, v);
   }
   handoff();
   if (issuer)
-    mma_split(tm + 0, smem_u32(sH1h), smem_u32(sH1l), 128, smem_u32(sW1h), smem_u32(sW1l), false, 64, 64, 2);
+    mma_split<F16>(tm + 0, smem_u32(sH1h), smem_u32(sH1l), 128, smem_u32(sW1h), smem_u32(sW1l), false, 64, 64, 2);
   {
     constexpr int q0 = H == 0 ? 16 : 0, nq = H == 0 ? EMB_E0 - 16 : 16;
     float v[16];
@@ -883,13 +886,13 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
         if (O::owns_b(b)) h2[b - O::b0] = hb;
         v[i] = hb;
       }
-      emb_store8(sH2h, row, 8 * g, 128, v, false);
-      emb_store8(sH2l, row, 8 * g, 128, v, true);
+      emb_store8<F16>(sH2h, row, 8 * g, 128, v, false);
+      emb_store8<F16>(sH2l, row, 8 * g, 128, v, true);
     }
   }
   handoff();
   if (issuer) {
-    mma_split(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
+    mma_split<F16>(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
     mma_commit(sy.bar);
   }
   before_z3();  // work that does not need Z3 (the adjoint's first dE/dG0 loads)
@@ -899,7 +902,7 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
 // The adjoint's front: layers 1 and 2 as the forward stored them (all 25
 // layer-1 units, the owned layer-2 units), the H2 tiles, and the issue of
 // Z3 = H2 W2; returns once Z3 is in TMEM columns [64, 176).
-template <int H, class BeforeZ3>
+template <bool F16, int H, class BeforeZ3>
 __device__ __forceinline__ void embed_bwd_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, Sync& sy, int row,
                                                 int atom, float* h1, float* h2, BeforeZ3 before_z3) {
   using O = EmbOwn<H>;
@@ -922,12 +925,12 @@ __device__ __forceinline__ void embed_bwd_front(const EmbedTcArgs& a, uint8_t* s
       const int b = 8 * g + i;
       v[i] = b < EMB_E1 ? h2[b - O::b0] : 0.f;
     }
-    emb_store8(sH2h, row, 8 * g, 128, v, false);
-    emb_store8(sH2l, row, 8 * g, 128, v, true);
+    emb_store8<F16>(sH2h, row, 8 * g, 128, v, false);
+    emb_store8<F16>(sH2l, row, 8 * g, 128, v, true);
   }
   handoff();
   if (issuer) {
-    mma_split(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
+    mma_split<F16>(tm + 64, smem_u32(sH2h), smem_u32(sH2l), 128, smem_u32(sW2h), smem_u32(sW2l), false, 112, 112, 4);
     mma_commit(sy.bar);
   }
   before_z3();
@@ -1019,11 +1022,12 @@ __device__ __forceinline__ void embed_fwd_out(const EmbedTcArgs& a, uint32_t tad
       float2 o;
       o.x = rv ? (h2[c % EMB_E1 - O::b0] + tanhf(z[i] + a.b2[c])) * (1.f + g2.x) : 0.f;
       o.y = rv ? (h2[(c + 1) % EMB_E1 - O::b0] + tanhf(z[i + 1] + a.b2[c + 1])) * (1.f + g2.y) : 0.f;
-      *reinterpret_cast<float2*>(out_blk + cq_off(row, c)) = o;
+      *reinterpret_cast<float2*>(out_blk + (a.rm ? (size_t)row * EMB_E2 + c : cq_off(row, c))) = o;
     }
   }
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_constant__ EmbedTcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {
@@ -1054,9 +1058,9 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_fwd(const __grid_co
     auto rows_next = [&] { in.rows(a, next, row); };
     const float* b0row = a.b0t ? s_b0 + tj * EMB_E0 : nullptr;
     if (half == 0)
-      embed_tc_front<0>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
+      embed_tc_front<F16, 0>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
     else
-      embed_tc_front<1>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
+      embed_tc_front<F16, 1>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
     {  // layers 1 and 2 for the adjoint: this half's layer-1 units, its layer-2 units
       float* hs = a.H12 + (size_t)atom * (EMB_E0 + EMB_E1) * NP + row;
       if (half == 0) {
@@ -1105,30 +1109,35 @@ struct EmbDz3 {
 
 // This half's dE/dG0 column quads of 16-column chunk k of a row (zero where
 // not read, or past nnei).
+// (rm: row-major [NP][100] block, else column-quad interleaved)
+__device__ __forceinline__ int emb_dg4(bool rm, int c4, int row) {
+  return rm ? row * (EMB_E2 / 4) + (c4 >> 2) : (c4 >> 2) * NP + row;
+}
+
 template <int H>
-__device__ __forceinline__ void embed_bwd_load16(const float4* dg, int k, int row, bool rv, float4* d) {
+__device__ __forceinline__ void embed_bwd_load16(const float4* dg, bool rm, int k, int row, bool rv, float4* d) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int c4 = 16 * k + 4 * q;
-    d[q] = EmbDz3<H>::need4(c4) && rv ? dg[(c4 >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    d[q] = EmbDz3<H>::need4(c4) && rv ? dg[emb_dg4(rm, c4, row)] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
 // Bring this half's dE/dG0 column quads of chunk k of a row into L1.
 template <int H>
-__device__ __forceinline__ void embed_bwd_prefetch16(const float4* dg, int k, int row, bool rv) {
+__device__ __forceinline__ void embed_bwd_prefetch16(const float4* dg, bool rm, int k, int row, bool rv) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int c4 = 16 * k + 4 * q;
     if (EmbDz3<H>::need4(c4) && rv)
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(dg + (c4 >> 2) * NP + row));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(dg + emb_dg4(rm, c4, row)));
   }
 }
 
 // dE/dG0 of chunk 0 is loaded (and chunk 1 brought into L1) by the caller
 // before it waits for Z3; chunk k + 1 is brought into L1 while chunk k is
 // processed.
-template <int H>
+template <bool F16, int H>
 __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t taddr, const float* gt, const float4* dg,
                                               bool rv, int row, uint8_t* sDZ3h, uint8_t* sDZ3l, float* dh2,
                                               float4* dcur) {
@@ -1136,8 +1145,8 @@ __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t tad
   constexpr int gs_lo = EmbDz3<H>::gs_lo, gs_hi = EmbDz3<H>::gs_hi;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    if (k > 0 && EmbDz3<H>::any16(k)) embed_bwd_load16<H>(dg, k, row, rv, dcur);
-    if (k + 2 < 7 && EmbDz3<H>::any16(k + 2)) embed_bwd_prefetch16<H>(dg, k + 2, row, rv);
+    if (k > 0 && EmbDz3<H>::any16(k)) embed_bwd_load16<H>(dg, a.rm, k, row, rv, dcur);
+    if (k + 2 < 7 && EmbDz3<H>::any16(k + 2)) embed_bwd_prefetch16<H>(dg, a.rm, k + 2, row, rv);
     if (EmbDz3<H>::any16(k)) {
     float z[16];
     tmem_ld16(taddr + 64 + 16 * k, z);
@@ -1172,8 +1181,8 @@ __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t tad
         }
       }
       if (store) {
-        emb_store8(sDZ3h, row, 8 * g, 128, dz, false);
-        emb_store8(sDZ3l, row, 8 * g, 128, dz, true);
+        emb_store8<F16>(sDZ3h, row, 8 * g, 128, dz, false);
+        emb_store8<F16>(sDZ3l, row, 8 * g, 128, dz, true);
       }
     }
     }
@@ -1182,7 +1191,7 @@ __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t tad
 
 // Adjoint of layer 2 for one half: d = dh2 (skip) + dH2 (product), the skip
 // part of dh1, and dZ2 = d (1 - t2^2) into the dZ2 tiles for the owned units.
-template <int H>
+template <bool F16, int H>
 __device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, const float* h2, const float* dh2,
                                               bool rv, int row, uint8_t* sDZ2h, uint8_t* sDZ2l, float* dh1) {
   using O = EmbOwn<H>;
@@ -1209,13 +1218,13 @@ __device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, c
         }
         dz[i] = d2;
       }
-      emb_store8(sDZ2h, row, 8 * g, 128, dz, false);
-      emb_store8(sDZ2l, row, 8 * g, 128, dz, true);
+      emb_store8<F16>(sDZ2h, row, 8 * g, 128, dz, false);
+      emb_store8<F16>(sDZ2l, row, 8 * g, 128, dz, true);
     }
   }
 }
 
-template <int H>
+template <bool F16, int H>
 __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
                                                Sync& sy, int row, bool rv, size_t rowg, const float* gt,
                                                const float4* dg, float* xch) {
@@ -1233,27 +1242,27 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
   float h1[EMB_E0], h2[O::nb];
   float4 d0[4];
-  embed_bwd_front<H>(a, sm, tm, sy, row, (int)(rowg / NP), h1, h2, [&] {
-    embed_bwd_load16<H>(dg, 0, row, rv, d0);
-    embed_bwd_prefetch16<H>(dg, 1, row, rv);
+  embed_bwd_front<F16, H>(a, sm, tm, sy, row, (int)(rowg / NP), h1, h2, [&] {
+    embed_bwd_load16<H>(dg, a.rm, 0, row, rv, d0);
+    embed_bwd_prefetch16<H>(dg, a.rm, 1, row, rv);
   });
   float dh2[O::nb];
 #pragma unroll
   for (int b = 0; b < O::nb; ++b) dh2[b] = 0.f;
-  embed_bwd_dz3<H>(a, tm + lane_off, gt, dg, rv, row, sDZ3h, sDZ3l, dh2, d0);
+  embed_bwd_dz3<F16, H>(a, tm + lane_off, gt, dg, rv, row, sDZ3h, sDZ3l, dh2, d0);
   handoff();
   // dH2 (product part) = dZ3 W2^T -> TMEM [0, 64)
   if (issuer)
-    mma_split(tm + 0, smem_u32(sDZ3h), smem_u32(sDZ3l), 128, smem_u32(sW2h), smem_u32(sW2l), true, 112, 64, 7);
+    mma_split<F16>(tm + 0, smem_u32(sDZ3h), smem_u32(sDZ3l), 128, smem_u32(sW2h), smem_u32(sW2l), true, 112, 64, 7);
   commit_and_sync(sy, issuer);
   float dh1[EMB_E0];
 #pragma unroll
   for (int p = 0; p < EMB_E0; ++p) dh1[p] = 0.f;
-  embed_bwd_dz2<H>(tm + lane_off, h1, h2, dh2, rv, row, sDZ2h, sDZ2l, dh1);
+  embed_bwd_dz2<F16, H>(tm + lane_off, h1, h2, dh2, rv, row, sDZ2h, sDZ2l, dh1);
   handoff();
   // dH1 (product part) = dZ2 W1^T -> TMEM [64, 96)
   if (issuer)
-    mma_split(tm + 64, smem_u32(sDZ2h), smem_u32(sDZ2l), 128, smem_u32(sW1h), smem_u32(sW1l), true, 64, 32, 4);
+    mma_split<F16>(tm + 64, smem_u32(sDZ2h), smem_u32(sDZ2l), 128, smem_u32(sW1h), smem_u32(sW1l), true, 64, 32, 4);
   commit_and_sync(sy, issuer);
   float v[32];
   tmem_ld16(tm + lane_off + 64, v);
@@ -1269,6 +1278,7 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   if (H == 0 && rv) a.dR[rowg * 4] += dx + xch[row];
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_constant__ EmbedTcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {
@@ -1305,9 +1315,9 @@ __global__ void __launch_bounds__(EMB_THREADS, 2) k_embed_tc_bwd(const __grid_co
     embed_tc_atom_start(a, s_gt, nullptr, atom, true);  // visible after the front's barriers
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * EMB_E2);
     if (half == 0)
-      embed_bwd_tail<0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<F16, 0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
     else
-      embed_bwd_tail<1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
+      embed_bwd_tail<F16, 1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * EMB_E2, dg, xch);
     in.type(a, row);
     fence_before_sync();
     __syncthreads();
@@ -1395,6 +1405,70 @@ std::vector<uint8_t> layer_image(const std::vector<double>* Ws[3], const std::ve
 
 }  // namespace
 
+// Weight images of the tensor-core embedding net (the 25-50-100 net with at
+// most EMB_MAXT types): the hi and lo parts of W1 and W2 in FP16 (the fused
+// 16-bit paths) and in BF16 (the bf16x mode), and its per-unit vectors.
+int tc_init_embedding(dp_model* m, const HostArrays& arrays, std::string& msg) {
+  auto get = [&](const std::string& name) -> const std::vector<double>& {
+    for (auto& kv : arrays)
+      if (kv.first == name) return kv.second;
+    static std::vector<double> empty;
+    return empty;
+  };
+  TcWeights& w = m->tcw;
+  // embedding-net tiles (hi and lo FP16 parts of W1 and W2) for the 25-50-100 net
+  w.emb_W1_t = nullptr;
+  w.emb_W2_t = nullptr;
+  if (m->emb[0] == EMB_E0 && m->emb[1] == EMB_E1 && m->emb[2] == EMB_E2 && m->nt <= EMB_MAXT) {
+    const std::vector<double>& W1 = get("em_W1");  // [E0][E1]
+    const std::vector<double>& W2 = get("em_W2");  // [E1][E2]
+    for (int f16 = 1; f16 >= 0; --f16) {  // FP16 image (fused paths), BF16 image (bf16x)
+      std::vector<uint8_t> img(EMB_WIMG, 0);
+      auto put = [&](int off, int r, int c, int R, double x, bool lo) {
+        if (f16) {
+          const __half hi = __float2half((float)x);
+          const __half v = lo ? __float2half((float)(x - (double)__half2float(hi))) : hi;
+          memcpy(img.data() + off + sw128_offset(r, c, R), &v, 2);
+        } else {
+          const __nv_bfloat16 hi = __float2bfloat16((float)x);
+          const __nv_bfloat16 v = lo ? __float2bfloat16((float)(x - (double)__bfloat162float(hi))) : hi;
+          memcpy(img.data() + off + sw128_offset(r, c, R), &v, 2);
+        }
+      };
+      for (int b = 0; b < EMB_E1; ++b)
+        for (int p = 0; p < EMB_E0; ++p) {
+          put(0, b, p, 64, W1[(size_t)p * EMB_E1 + b], false);
+          put(EMB_T1, b, p, 64, W1[(size_t)p * EMB_E1 + b], true);
+        }
+      for (int c = 0; c < EMB_E2; ++c)
+        for (int b = 0; b < EMB_E1; ++b) {
+          put(2 * EMB_T1, c, b, 112, W2[(size_t)b * EMB_E2 + c], false);
+          put(2 * EMB_T1 + EMB_T2, c, b, 112, W2[(size_t)b * EMB_E2 + c], true);
+        }
+      void* d = nullptr;
+      if (cudaMalloc(&d, img.size()) != cudaSuccess ||
+          cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        msg = "cudaMalloc of the embedding weight image failed";
+        return DP_ERR_CUDA;
+      }
+      w.allocations.push_back(d);
+      (f16 ? w.emb_W1_t : w.emb_W2_t) = d;
+    }
+    const std::vector<double>& W0 = get("em_W0");
+    const std::vector<double>& b0 = get("em_b0");
+    const std::vector<double>& b1 = get("em_b1");
+    const std::vector<double>& b2 = get("em_b2");
+    for (int q = 0; q < EMB_E0; ++q) { w.emb_vec.W0[q] = (float)W0[q]; w.emb_vec.b0[q] = (float)b0[q]; }
+    for (int q = 0; q < EMB_E1; ++q) w.emb_vec.b1[q] = (float)b1[q];
+    for (int q = 0; q < EMB_E2; ++q) w.emb_vec.b2[q] = (float)b2[q];
+    cudaFuncSetAttribute(k_embed_tc_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBF_SMEM);
+    cudaFuncSetAttribute(k_embed_tc_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBB_SMEM);
+    cudaFuncSetAttribute(k_embed_tc_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBF_SMEM);
+    cudaFuncSetAttribute(k_embed_tc_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBB_SMEM);
+  }
+  return DP_OK;
+}
+
 int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
   if (m->A != 128 || m->m1 + 2 > 16 * KS_M1 || m->m1 % 4 != 0) {
     msg = "the tensor-core path needs attention width 128 and an embedding width <= 108 divisible by 4";
@@ -1422,45 +1496,7 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
       w.allocations.push_back(d);
       (f16 ? w.Wo_t : w.Wqkv_t).push_back(d);  // images: [0] bf16 layers, [1] fp16 layers
     }
-  // embedding-net tiles (hi and lo FP16 parts of W1 and W2) for the 25-50-100 net
-  w.emb_W1_t = nullptr;
-  if (m->emb[0] == EMB_E0 && m->emb[1] == EMB_E1 && m->emb[2] == EMB_E2 && m->nt <= EMB_MAXT) {
-    std::vector<uint8_t> img(EMB_WIMG, 0);
-    const std::vector<double>& W1 = get("em_W1");  // [E0][E1]
-    const std::vector<double>& W2 = get("em_W2");  // [E1][E2]
-    auto put = [&](int off, int r, int c, int R, double x, bool lo) {
-      const __half hi = __float2half((float)x);
-      const __half v = lo ? __float2half((float)(x - (double)__half2float(hi))) : hi;
-      memcpy(img.data() + off + sw128_offset(r, c, R), &v, 2);
-    };
-    for (int b = 0; b < EMB_E1; ++b)
-      for (int p = 0; p < EMB_E0; ++p) {
-        put(0, b, p, 64, W1[(size_t)p * EMB_E1 + b], false);
-        put(EMB_T1, b, p, 64, W1[(size_t)p * EMB_E1 + b], true);
-      }
-    for (int c = 0; c < EMB_E2; ++c)
-      for (int b = 0; b < EMB_E1; ++b) {
-        put(2 * EMB_T1, c, b, 112, W2[(size_t)b * EMB_E2 + c], false);
-        put(2 * EMB_T1 + EMB_T2, c, b, 112, W2[(size_t)b * EMB_E2 + c], true);
-      }
-    void* d = nullptr;
-    if (cudaMalloc(&d, img.size()) != cudaSuccess ||
-        cudaMemcpy(d, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-      msg = "cudaMalloc of the embedding weight image failed";
-      return DP_ERR_CUDA;
-    }
-    w.allocations.push_back(d);
-    w.emb_W1_t = d;
-    const std::vector<double>& W0 = get("em_W0");
-    const std::vector<double>& b0 = get("em_b0");
-    const std::vector<double>& b1 = get("em_b1");
-    const std::vector<double>& b2 = get("em_b2");
-    for (int q = 0; q < EMB_E0; ++q) { w.emb_vec.W0[q] = (float)W0[q]; w.emb_vec.b0[q] = (float)b0[q]; }
-    for (int q = 0; q < EMB_E1; ++q) w.emb_vec.b1[q] = (float)b1[q];
-    for (int q = 0; q < EMB_E2; ++q) w.emb_vec.b2[q] = (float)b2[q];
-    cudaFuncSetAttribute(k_embed_tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBF_SMEM);
-    cudaFuncSetAttribute(k_embed_tc_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, EMBB_SMEM);
-  }
+  if (int rc = tc_init_embedding(m, arrays, msg)) return rc;
   w.vectors.assign(m->nattn, TcWeights::Vectors{});
   for (int l = 0; l < m->nattn; ++l) {
     const std::string p = "at" + std::to_string(l) + "_";
@@ -1500,6 +1536,43 @@ void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
   ws.tc.p[5] = m->tcw.emb_W1_t ? a.take<float>(rows * (EMB_E0 + EMB_E1)) : nullptr;
 }
 
+
+namespace {
+// One launch of the tensor-core embedding net: forward or adjoint, FP16
+// operand splits (the fused 16-bit paths) or BF16 ones (bf16x).
+void tc_embed_launch(dp_model* m, const EmbedTcArgs& et, bool bwd, bool bf16, cudaStream_t st) {
+  const int grid = std::min(et.n, 2 * sm_count_dev(m->device));
+  if (!bwd && !bf16) k_embed_tc_fwd<true><<<grid, EMB_THREADS, EMBF_SMEM, st>>>(et);
+  if (!bwd && bf16) k_embed_tc_fwd<false><<<grid, EMB_THREADS, EMBF_SMEM, st>>>(et);
+  if (bwd && !bf16) k_embed_tc_bwd<true><<<grid, EMB_THREADS, EMBB_SMEM, st>>>(et);
+  if (bwd && bf16) k_embed_tc_bwd<false><<<grid, EMB_THREADS, EMBB_SMEM, st>>>(et);
+  note_launch();
+}
+
+EmbedTcArgs embed_tc_args(dp_model* m, int n, const int* atype) {
+  Workspace& ws = m->ws;
+  EmbedTcArgs et{};
+  et.R = ws.R; et.nlist = ws.nlist; et.nnei = ws.nnei; et.atype = atype; et.Gt = m->Gt;
+  et.n = n; et.ntypes = m->nt; et.err = m->d_err; et.b0t = m->b0t;
+  memcpy(et.W0, m->tcw.emb_vec.W0, sizeof(et.W0));
+  memcpy(et.b0, m->tcw.emb_vec.b0, sizeof(et.b0));
+  memcpy(et.b1, m->tcw.emb_vec.b1, sizeof(et.b1));
+  memcpy(et.b2, m->tcw.emb_vec.b2, sizeof(et.b2));
+  return et;
+}
+}  // namespace
+
+// The embedding net of the bf16x mode on the tensor cores (BF16 hi + lo
+// splits of both operands), G0 and dE/dG0 row-major: forward, or adjoint
+// (dR[:, 0] +=).  H12 holds the layers the adjoint reads back.
+void tc_embed_bf16(dp_model* m, int n, const int* atype, bool bwd, float* G0, const float* dG0, float* dR,
+                   float* H12, cudaStream_t st) {
+  if (n == 0) return;
+  EmbedTcArgs et = embed_tc_args(m, n, atype);
+  et.G0 = G0; et.dG0 = dG0; et.dR = dR; et.H12 = H12; et.rm = 1;
+  et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W2_t);
+  tc_embed_launch(m, et, bwd, true, st);
+}
 
 void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   Workspace& ws = m->ws;
@@ -1550,8 +1623,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     memcpy(et.b2, m->tcw.emb_vec.b2, sizeof(et.b2));
   }
   if (emb_tc && n > 0) {
-    k_embed_tc_fwd<<<std::min(n, 2 * sm_count_dev(m->device)), EMB_THREADS, EMBF_SMEM, st>>>(et);
-    note_launch();
+    tc_embed_launch(m, et, false, false, st);
   } else {
     launch_embed_fwd(ea, m->emb, st);
     relayout(rm_stage, ws.G[0], n, m->m1, true, st);
@@ -1576,8 +1648,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     prof_mark(m, "attn_bwd_tc", st);
   }
   if (emb_tc && n > 0) {
-    k_embed_tc_bwd<<<std::min(n, 2 * sm_count_dev(m->device)), EMB_THREADS, EMBB_SMEM, st>>>(et);
-    note_launch();
+    tc_embed_launch(m, et, true, false, st);
   } else {
     relayout(ws.dG, rm_stage, n, m->m1, false, st);
     ea.dG0 = rm_stage;
