@@ -526,8 +526,8 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
   Workspace& ws = m->ws;
   const int rows = n * NP, L = m->nattn, A = m->A, m1 = m->m1;
   // the 25-50-100 embedding net on the tensor cores (BF16 two-term splits),
-  // other nets in FP32
-  const bool emb_tc = m->tcw.emb_W2_t != nullptr;
+  // other nets, and any net while its weight gradient is wanted, in FP32
+  const bool emb_tc = m->tcw.emb_W2_t != nullptr && !m->grad_scale;
   float* H12 = reinterpret_cast<float*>(ws.tc.p[5]);
   EmbedArgs ea{};
   ea.R = ws.R; ea.nlist = ws.nlist; ea.nnei = ws.nnei; ea.atype = atype; ea.n = n; ea.ntypes = m->nt; ea.m1 = m1;
@@ -563,10 +563,12 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
     prof_mark(m, "qkv_bwd_gemm", st);
   }
   ea.dG0 = ws.dG; ea.dR = ws.dR;
-  if (emb_tc)
+  if (emb_tc) {
     tc_embed_bf16(m, n, atype, true, nullptr, ws.dG, ws.dR, H12, st);
-  else
+  } else {
     launch_embed_bwd(ea, m->emb, st);
+    if (m->grad_scale) launch_embed_wgrad(ea, m->emb, m->grad, m->grad_scale, st);
+  }
   prof_mark(m, "embed_bwd", st);
 }
 
@@ -643,6 +645,9 @@ void run_force_tangent(dp_model* m, int n, const double* coord, const double* v,
   a.R = ws.R; a.G = ws.G[0]; a.T = ws.T; a.dX = ws.dX; a.dG = ws.dG; a.w = m->emb_packed; a.Gt = m->Gt;
   a.b0t = m->b0t; a.v = v;
   a.Rd = Rd; a.Gd = Gd; a.Td = Td; a.Xd = Xd; a.dXd = dXd; a.dGd = dGd;
+  // the fitting net's products (and their tangents) in the model's mode:
+  // FP32, or BF16 two-term splits on the tensor cores
+  const bool x16 = m->precision == DP_PREC_BF16X;
   // forward: R', G', T' and X'
   launch_env_jvp(a, st);
   launch_embed_jvp(a, m->emb, 0, nullptr, scale, st);
@@ -653,7 +658,10 @@ void run_force_tangent(dp_model* m, int n, const double* coord, const double* v,
   for (int l = 0; l < m->nfit; ++l) {
     const int out = m->fit[l];
     const bool res = (l > 0 && out == fan);
-    gemm_f32(hin, fan, m->fitW[l], out, nullptr, nullptr, 0, Zd, out, n, out, fan, EPI_BIAS, st);
+    if (x16)
+      gemm_bf16x(m, m->xw.fit[l], hin, fan, nullptr, nullptr, 0, Zd, out, n, EPI_BIAS, st);
+    else
+      gemm_f32(hin, fan, m->fitW[l], out, nullptr, nullptr, 0, Zd, out, n, out, fan, EPI_BIAS, st);
     launch_tanh_jvp(Zd, ws.H[l], res ? ws.H[l - 1] : nullptr, res ? hin : nullptr, Hd[l], (long long)n * out, st);
     hin = Hd[l];
     fan = out;
@@ -677,11 +685,20 @@ void run_force_tangent(dp_model* m, int n, const double* coord, const double* v,
     launch_wgrad(input, in, dZd, out, m->grad + m->off_fitW[l], out, in, out, n, scale, st);
     launch_colsum(dZd, out, m->grad + m->off_fitb[l], out, n, scale, 1.0f, st);
     if (l > 0) {
-      gemm_f32(dZ, out, m->fitWT[l], in, nullptr, res ? dH[cur] : nullptr, out, dH[1 - cur], in, n, in, out,
-               res ? EPI_RES : EPI_BIAS, st);
-      gemm_f32(dZd, out, m->fitWT[l], in, nullptr, res ? dHd[cur] : nullptr, out, dHd[1 - cur], in, n, in, out,
-               res ? EPI_RES : EPI_BIAS, st);
+      if (x16) {
+        gemm_bf16x(m, m->xw.fitT[l], dZ, out, nullptr, res ? dH[cur] : nullptr, out, dH[1 - cur], in, n,
+                   res ? EPI_RES : EPI_BIAS, st);
+        gemm_bf16x(m, m->xw.fitT[l], dZd, out, nullptr, res ? dHd[cur] : nullptr, out, dHd[1 - cur], in, n,
+                   res ? EPI_RES : EPI_BIAS, st);
+      } else {
+        gemm_f32(dZ, out, m->fitWT[l], in, nullptr, res ? dH[cur] : nullptr, out, dH[1 - cur], in, n, in, out,
+                 res ? EPI_RES : EPI_BIAS, st);
+        gemm_f32(dZd, out, m->fitWT[l], in, nullptr, res ? dHd[cur] : nullptr, out, dHd[1 - cur], in, n, in, out,
+                 res ? EPI_RES : EPI_BIAS, st);
+      }
       cur = 1 - cur;
+    } else if (x16) {
+      gemm_bf16x(m, m->xw.fitT[l], dZd, out, nullptr, nullptr, 0, dXd, in, n, EPI_BIAS, st);
     } else {
       // dE/dX itself is still in the workspace from the evaluation
       gemm_f32(dZd, out, m->fitWT[l], in, nullptr, nullptr, 0, dXd, in, n, in, out, EPI_BIAS, st);
@@ -1398,8 +1415,9 @@ int dp_zero_grad(dp_model* m, void* stream) {
 int dp_train_frame(dp_model* m, int natoms, const double* d_coord, const double* d_box, const int* d_atype,
                    double e_ref, const double* d_force_ref, double pe, double pf, double* d_loss, void* stream) {
   if (check_model(m)) return DP_ERR_ARG;
-  if (m->precision != DP_PREC_FP32 || m->nattn != 0)
-    return fail(DP_ERR_UNSUPPORTED, "dp_train_frame: training needs an FP32 model without attention layers");
+  if ((m->precision != DP_PREC_FP32 && m->precision != DP_PREC_BF16X) || m->nattn != 0)
+    return fail(DP_ERR_UNSUPPORTED,
+                "dp_train_frame: training needs a model without attention layers in DP_PREC_FP32 or DP_PREC_BF16X");
   if (natoms < 1 || !d_coord || !d_box || !d_atype || !d_force_ref || !d_loss)
     return fail(DP_ERR_ARG, "dp_train_frame: bad arguments");
   if (natoms > m->ws.cap) return fail(DP_ERR_CAPACITY, "natoms exceeds the reserved workspace (call dp_reserve)");

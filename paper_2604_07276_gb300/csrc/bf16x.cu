@@ -110,6 +110,7 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
   uint64_t* tfull = bars + 3 * XSTAGES;  // [2] accumulator buffer complete
   uint64_t* tempty = tfull + 2;          // [2] accumulator buffer read out (4 warp arrivals)
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(tempty + 2);
+  float* s_bias = reinterpret_cast<float*>(bars + 16);  // [XBN] this N block's bias (0 without one)
   auto sF = [&](int s) { return sm + s * stage_bytes; };
   auto sAh = [&](int s) { return sm + s * stage_bytes + XF32; };
   auto sAl = [&](int s) { return sm + s * stage_bytes + XF32 + XAT; };
@@ -130,6 +131,10 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
     fence_mbar_init();
   }
   if (warp == 2) tmem_alloc(s_tmem, 512);
+  for (int c = threadIdx.x; c < XBN; c += blockDim.x) {
+    const int n = nb * XBN + c;
+    s_bias[c] = (a.bias && c < bn && n < a.N) ? a.bias[n] : 0.f;
+  }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -225,12 +230,9 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
         for (int q = 0; q < 16; q += 4) {
           const int n = nb * XBN + c0 + q;
           if (n >= a.N) break;  // N % 4 == 0
-          float4 o = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+          const float4 bb = *reinterpret_cast<const float4*>(s_bias + c0 + q);
+          float4 o = make_float4(v[q] + bb.x, v[q + 1] + bb.y, v[q + 2] + bb.z, v[q + 3] + bb.w);
           float* op = &o.x;
-          if (a.bias) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) op[t] += a.bias[n + t];
-          }
           if (a.epi == EPI_TANH || a.epi == EPI_RES_TANH) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) op[t] = tanhf(op[t]);
@@ -284,7 +286,8 @@ __global__ void k_x_image(const float* __restrict__ B, int K, int N, int nkb, in
 
 PFN_cuTensorMapEncodeTiled_v12000 g_x_encode = nullptr;
 
-int x_smem(int bn_max) { return XSTAGES * (XF32 + 2 * XAT + 2 * bn_max * 128) + 1024 + 128; }
+// the stages, 1024 bytes of alignment slack, the barriers (128 bytes) and the bias (XBN floats)
+int x_smem(int bn_max) { return XSTAGES * (XF32 + 2 * XAT + 2 * bn_max * 128) + 1024 + 128 + XBN * 4; }
 
 int x_sm_count(int dev) {
   int c = 0;
