@@ -165,69 +165,116 @@ def run_reference(a):
 # -------------------------------------------------------------------- our arm
 
 def _student_line(dev, coord, atype, box, full_rates, batch=16, md_steps=100):
-    """Distilled student (embedding [16, 32, 64], axis 8, no attention,
-    fitting [128, 128]) on the same box: training throughput of
-    dp_train_frame + dp_adam_step on 16-frame batches (FP32, loss against
-    stand-in reference energies and forces: the cost does not depend on
-    their values) and graph-replayed MD throughput next to the full model's."""
+    """The distilled student (embedding [16, 32, 64], axis 8, no attention,
+    fitting [128, 128]) and its teacher (the same sizes with one gated
+    attention layer of small LayerNorm gain, synth.teacher_weights).
+
+    On the measured box: teacher frame generation (velocity-Verlet at 10 K,
+    a frame every 2 steps), training throughput of dp_train_frame +
+    dp_adam_step on 16-frame batches with FP32 products and with the fitting
+    net as BF16 two-term splits on the tensor cores (bf16x), and MD
+    throughput of student, teacher and the full default model.  On the
+    water box (where 10 K trajectories stay physical for a random-weight
+    potential): training from perturbed weights to the family's floor and
+    MD with the full-model check at 0.05 eV/A."""
     import torch
 
     import synth
     import paper_2604_07276_gb300 as dp
-    from paper_2604_07276_gb300 import md as dmd
+    from paper_2604_07276_gb300 import md as dmd, student as stu
 
-    scfg = synth.STUDENT_CONFIG
-    path = os.path.join(tempfile.mkdtemp(prefix="dpa1s_"), "student.bin")
-    synth.write_weights(path, scfg, synth.make_weights(scfg, seed=4))
-    s = dp.DPA1(path, precision="fp32", device=dev.index)
+    d = tempfile.mkdtemp(prefix="dpa1s_")
+    tcfg, tw = synth.teacher_weights(ln_gain=3e-3)
+    scfg, bw = synth.teacher_base_weights(synth.TEACHER_BASE_OUT_SCALE)
+    sw = synth.perturbed(bw, 0.03, seed=21)
+    tpath, bpath, spath = (os.path.join(d, f) for f in ("teacher.bin", "base.bin", "student.bin"))
+    synth.write_weights(tpath, tcfg, tw)
+    synth.write_weights(bpath, scfg, bw)
+    synth.write_weights(spath, scfg, sw)
     n = len(coord)
-    s.reserve(n)
-    c = torch.tensor(coord, dtype=torch.float64, device=dev)
-    b = torch.tensor(dp.box9(box), dtype=torch.float64, device=dev)
-    t = torch.tensor(atype, dtype=torch.int32, device=dev)
-    f_ref = torch.zeros((n, 3), dtype=torch.float64, device=dev)
-    loss = torch.zeros(3, dtype=torch.float64, device=dev)
+    out = {"student": "embed [16,32,64], axis 8, no attention, fitting [128,128]",
+           "teacher": "the student's sizes plus one gated attention layer (width 128, LayerNorm gain 3e-3)",
+           "box_atoms": n}
 
-    def one_batch():
-        s.zero_grad()
-        for _ in range(batch):
-            s.train_frame(c, b, t, 0.0, f_ref, loss)
-        s.adam_step(1e-5)
-
-    one_batch()
-    torch.cuda.synchronize(dev)
+    # teacher frames on the measured box (10 K, dt 0.25 fs, a frame every 2 steps)
+    teacher = dp.DPA1(tpath, precision="fp16x", device=dev.index)
     t0 = time.perf_counter()
-    for _ in range(2):
-        one_batch()
+    frames = stu.teacher_frames(teacher, [(coord, atype, box)], synth.MASSES, n_traj=2, steps=2 * batch, every=2,
+                                dt=0.25, temperature=10.0, seed=1)
     torch.cuda.synchronize(dev)
-    s.status()
-    train_s = (time.perf_counter() - t0) / 2
-    s.close()
+    gen_s = time.perf_counter() - t0
+    out["teacher_frames_per_s"] = len(frames) / gen_s
+    train_rate = {}
+    for prec in ("fp32", "bf16x"):
+        s = dp.DPA1(spath, precision=prec, device=dev.index)
+        stu.train(s, frames[:batch], epochs=1, batch=batch, lr0=1e-6, lr_end=1e-6)  # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        stu.train(s, frames, epochs=1, batch=batch, lr0=1e-6, lr_end=1e-6)
+        torch.cuda.synchronize(dev)
+        train_rate[prec] = len(frames) / (time.perf_counter() - t0)
+        s.close()
+    out["train_batch_frames"] = batch
+    out["train_frames_per_s"] = train_rate
+    # the configuration's 20,000-frame run, extrapolated from the measured rates
+    out["hours_for_20000_frames_extrapolated"] = {
+        "generate": 20000 / out["teacher_frames_per_s"] / 3600,
+        "train_one_epoch_bf16x": 20000 / train_rate["bf16x"] / 3600}
 
-    def md_rate(precision):
+    def md_rate(path, precision):
         mdl = dp.DPA1(path, precision=precision, device=dev.index)
         mdl.reserve(n)
         state = dmd.MDState(coord, np.zeros_like(coord), synth.MASSES[atype], box, atype, device=dev)
-        dmd.run(mdl, state, dt=0.5, nsteps=2, graph=True)
+        dmd.run(mdl, state, dt=0.25, nsteps=2, graph=True)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        dmd.run(mdl, state, dt=0.5, nsteps=md_steps, graph=True)
+        dmd.run(mdl, state, dt=0.25, nsteps=md_steps, graph=True)
         e1.record()
         torch.cuda.synchronize(dev)
         mdl.status()
         mdl.close()
         return n * md_steps / (e0.elapsed_time(e1) / 1e3)
 
-    # training runs on the FP32 path; inference also in the 16-bit mode, whose
-    # tensor-core products (here only the fitting net) keep FP32 accuracy
-    rates = {p: md_rate(p) for p in ("fp32", "fp16x")}
-    return {"model": "embed [16,32,64], axis 8, no attention, fitting [128,128]", "train_precision": "fp32",
-            "train_batch_frames": batch, "train_ms_per_batch": 1e3 * train_s,
-            "train_frames_per_s": batch / train_s, "md_atom_steps_per_s": rates,
-            "md_speedup_vs_full_fp16x": {p: r / full_rates["fp16x"] for p, r in rates.items()} if "fp16x" in full_rates
-            else None}
+    teacher.close()
+    rates = {"student_fp16x": md_rate(spath, "fp16x"), "student_fp32": md_rate(spath, "fp32"),
+             "teacher_fp16x": md_rate(tpath, "fp16x")}
+    out["md_atom_steps_per_s"] = rates
+    if "fp16x" in full_rates:
+        out["md_speedup_vs_full_fp16x"] = rates["student_fp16x"] / full_rates["fp16x"]
+    out["md_speedup_vs_teacher_fp16x"] = rates["student_fp16x"] / rates["teacher_fp16x"]
+
+    # accuracy at the threshold: the water-box distillation
+    teacher = dp.DPA1(tpath, precision="fp32", device=dev.index)
+    base = dp.DPA1(bpath, precision="fp32", device=dev.index)
+    systems = [synth.water_box(k) for k in range(3)]
+    wf = stu.teacher_frames(teacher, systems, synth.MASSES, n_traj=6, steps=8, every=2, dt=0.25, temperature=10.0,
+                            seed=1)
+    held = stu.teacher_frames(teacher, systems, synth.MASSES, n_traj=2, steps=8, every=4, dt=0.25, temperature=10.0,
+                              seed=2)
+    acc = {"floor_force_rmse": stu.force_rmse(base, held)}
+    for prec in ("fp32", "bf16x"):
+        s = dp.DPA1(spath, precision=prec, device=dev.index)
+        s0 = dp.DPA1(spath, precision=prec, device=dev.index)
+        before = stu.force_rmse(s, held)
+        stu.train(s, wf, epochs=60, batch=8, lr0=1e-5, lr_end=1e-6)
+        c, t, b = synth.water_box(1)
+        vel = synth.maxwell_boltzmann(t, 10.0, seed=33)
+        runs = {}
+        for name, mdl in (("trained", s), ("untrained", s0)):
+            st = dmd.MDState(c, vel, synth.MASSES[t], b, t)
+            u_s, u_t, _ = stu.md_with_fallback(mdl, teacher, st, nsteps=12, dt=0.25, check_every=3, threshold=0.05)
+            runs[name] = {"student_segments": u_s, "fallback_segments": u_t}
+        acc[prec] = {"held_out_force_rmse_before": before, "held_out_force_rmse_after": stu.force_rmse(s, held),
+                     "md_at_0.05": runs}
+        s.close()
+        s0.close()
+    teacher.close()
+    base.close()
+    acc["frames"] = {"train": len(wf), "held_out": len(held), "system": "three 192-atom water boxes, 10 K"}
+    out["distillation"] = acc
+    return out
 
 
 def _scale_line(a, dev, cfg, wpath, steps=5):

@@ -181,3 +181,47 @@ def write_weights(path: str, cfg: ModelConfig, weights: Dict[str, np.ndarray]) -
 
 def with_out_scale(cfg: ModelConfig, out_scale: float) -> ModelConfig:
     return dataclasses.replace(cfg, out_scale=out_scale)
+
+
+# The distillation teacher (stage a17): a DPA-1 of the student's sizes with one
+# gated attention layer whose LayerNorm gain is small, so that the student
+# family (no attention) can represent it to within a known floor.  Its base
+# (every weight but the attention layer) is the seed-4 student model with
+# biases; the output scale below was written by oracle/calibrate_out_scale.py
+# (FP64 force RMS 1.0 eV/A of the base on the 192-atom water box).
+TEACHER_BASE_OUT_SCALE = 536.6297988626927
+
+
+def teacher_base_weights(out_scale: float = 1.0):
+    """(config, weights) of the teacher's base: the student family, seed 4."""
+    cfg = STUDENT_CONFIG
+    w = make_weights(cfg, seed=4, bias_scale=0.1)
+    w["out_scale"] = np.array(out_scale)
+    return cfg, w
+
+
+def teacher_weights(ln_gain: float, out_scale: float = TEACHER_BASE_OUT_SCALE):
+    """(config, weights) of the distillation teacher: the base plus one
+    attention layer (width 128, seed-12 weights with biases) whose LayerNorm
+    gain is ``ln_gain`` and shift 0."""
+    _, base = teacher_base_weights(out_scale)
+    cfg = dataclasses.replace(STUDENT_CONFIG, attn_layers=1, attn_dim=128)
+    att = make_weights(cfg, seed=12, bias_scale=0.1)
+    w = dict(base)
+    for k, v in att.items():
+        if k.startswith("at0_"):
+            w[k] = v
+    w["at0_ln_g"] = ln_gain * np.ones_like(w["at0_ln_g"])
+    w["at0_ln_b"] = np.zeros_like(w["at0_ln_b"])
+    return cfg, w
+
+
+def perturbed(weights: Dict[str, np.ndarray], sigma: float, seed: int) -> Dict[str, np.ndarray]:
+    """A copy of the weights with every embedding and fitting matrix scaled
+    elementwise by (1 + sigma N(0, 1)): the student's starting point."""
+    rng = np.random.default_rng(seed)
+    out = dict(weights)
+    for k, v in weights.items():
+        if (k.startswith("em_W") or k.startswith("fit_W")) and np.ndim(v) == 2:
+            out[k] = v * (1.0 + sigma * rng.normal(size=np.shape(v)))
+    return out

@@ -110,3 +110,55 @@ def test_student_training_and_fallback_md(lib=None):
     assert times["student"] < 0.5 * times["teacher"], times
     teacher.close()
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x"])
+def test_student_distils_teacher_within_threshold(precision):
+    """What the trained student gains: accuracy at the fallback threshold.
+
+    The teacher is a DPA-1 of the student's sizes with one gated attention
+    layer of small LayerNorm gain (synth.teacher_weights), so the student
+    family, which has no attention, can represent it to within a floor: the
+    force RMSE of the family's best member (the teacher without attention).
+    The student starts from perturbed weights, which fail the 0.05 eV/A
+    check; after training on the teacher's forces along its own short MD
+    trajectories (10 K: a random-weight potential has no short-range
+    repulsion, so longer or hotter runs collapse atoms), its held-out force
+    error must be near the floor and below the threshold, and MD with the
+    full-model check every 3 steps runs on the student, where the untrained
+    one falls back.  Trained with FP32 products and with the fitting net's
+    products as BF16 two-term splits on the tensor cores (bf16x)."""
+    import paper_2604_07276_gb300 as p
+    from paper_2604_07276_gb300 import md, student
+
+    tcfg, tw = synth.teacher_weights(ln_gain=3e-3)
+    scfg, bw = synth.teacher_base_weights(synth.TEACHER_BASE_OUT_SCALE)
+    teacher = p.DPA1(weight_file(tcfg, tw, "teacher_lg3e-3"), precision="fp32")
+    base = p.DPA1(weight_file(scfg, bw, "teacher_base"), precision="fp32")
+    systems = [synth.water_box(s) for s in range(3)]
+    frames = student.teacher_frames(teacher, systems, synth.MASSES, n_traj=6, steps=8, every=2, dt=0.25,
+                                    temperature=10.0, seed=1)
+    held = student.teacher_frames(teacher, systems, synth.MASSES, n_traj=2, steps=8, every=4, dt=0.25,
+                                  temperature=10.0, seed=2)
+    floor = student.force_rmse(base, held)
+    sw = synth.perturbed(bw, 0.03, seed=21)
+    s = p.DPA1(weight_file(scfg, sw, "student_perturbed"), precision=precision)
+    s0 = p.DPA1(weight_file(scfg, sw, "student_perturbed"), precision=precision)
+    before = student.force_rmse(s, held)
+    student.train(s, frames, epochs=60, batch=8, lr0=1e-5, lr_end=1e-6)
+    after = student.force_rmse(s, held)
+    coord, atype, box = synth.water_box(1)
+    vel = synth.maxwell_boltzmann(atype, 10.0, seed=33)
+    runs = {}
+    for name, mdl in (("trained", s), ("untrained", s0)):
+        st = md.MDState(coord, vel, synth.MASSES[atype], box, atype)
+        runs[name] = student.md_with_fallback(mdl, teacher, st, nsteps=12, dt=0.25, check_every=3, threshold=0.05)
+    print(f"\n{precision}: floor {floor:.4f}, held-out force RMSE {before:.4f} -> {after:.4f} eV/A; "
+          f"MD segments (student, fallback): trained {runs['trained'][:2]}, untrained {runs['untrained'][:2]}")
+    assert floor < 0.02
+    assert before > 0.05
+    assert after < 0.5 * 0.05 and after < 3 * floor
+    assert runs["trained"][1] == 0
+    assert runs["untrained"][1] >= 2
+    for mm in (teacher, base, s, s0):
+        mm.close()
