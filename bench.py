@@ -46,7 +46,7 @@ MODEL = ("DPA-1 se_atten: 5 types, tebd 8, rcut 6.0/0.5 A, sel 120, embed [25,50
 MODELS = {
     "dpa1": (MODEL, {}),
     "paper-size": ("DPA-1 se_atten at the paper's size: 5 types, tebd 8, rcut 6.0/0.5 A, sel 120, embed [32,64,128], "
-                   "axis 16, 3 gated attention layers x 256, fitting [256,256,256] (FP32 path only)",
+                   "axis 16, 3 gated attention layers x 256, fitting [256,256,256] (bf16x and FP32 paths)",
                    dict(embed=(32, 64, 128), attn_layers=3, attn_dim=256, fitting=(256, 256, 256))),
     "concat": ("DPA-1 se_atten, concat type embedding (embedding net input [s, T_j, T_i]); otherwise the default "
                "model", dict(tebd_input_mode="concat")),
@@ -59,7 +59,9 @@ def model_cfg(name):
     import synth
 
     desc, kw = MODELS[name]
-    return dataclasses.replace(synth.DEFAULT_CONFIG, **kw), desc
+    # the paper-size model has its own calibrated output scale
+    base = synth.PAPER_SIZE_CONFIG if name == "paper-size" else synth.DEFAULT_CONFIG
+    return dataclasses.replace(base, **kw), desc
 
 
 def _args():

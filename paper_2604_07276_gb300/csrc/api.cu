@@ -272,15 +272,18 @@ int alloc_workspace(dp_model* m, int cap) {
     for (int l = 0; l <= L; ++l) ws.G[l] = a.take<float>(rows * m1);
     ws.QKV.assign(L, nullptr); ws.O.assign(L, nullptr); ws.Y.assign(L, nullptr); ws.stats.assign(L, nullptr);
     if (!fused_tc_precision(m->precision)) {
+      // bf16x keeps Q | K only (V enters through [Wv Wo; bv Wo])
+      const size_t nqkv = (m->precision == DP_PREC_BF16X ? 2 : 3) * (size_t)A;
       for (int l = 0; l < L; ++l) {
-        ws.QKV[l] = a.take<float>(rows * 3 * A);
+        ws.QKV[l] = a.take<float>(rows * nqkv);
         ws.O[l] = a.take<float>(rows * pg_ld(m1));  // [P G, rowsum(P)]
         ws.Y[l] = a.take<float>(rows * m1);
         ws.stats[l] = a.take<float>(rows * 2);
       }
       ws.dY = a.take<float>(rows * m1);
-      ws.dO = a.take<float>(rows * (L > 0 ? A : 1));
-      ws.dQKV = a.take<float>(rows * (L > 0 ? 3 * A : 1));
+      // dO, or in bf16x dE/d[P G, rowsum P]
+      ws.dO = a.take<float>(rows * (L > 0 ? std::max(A, pg_ld(m1)) : 1));
+      ws.dQKV = a.take<float>(rows * (L > 0 ? nqkv : 1));
       if (m->precision == DP_PREC_FP32)  // dS^T, P^T, dP per block of the FP32 adjoint
         ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 3 * NP * NP);
     }
@@ -540,7 +543,7 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
   for (int l = 0; l < L; ++l) {
     const AttnLayerW& w = m->attn[l];
     const XWeights::Layer& x = m->xw.layers[l];
-    gemm_bf16x(m, x.qkv, ws.G[l], m1, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, EPI_BIAS, st);
+    gemm_bf16x(m, x.qk, ws.G[l], m1, w.bqkv, nullptr, 0, ws.QKV[l], 2 * A, rows, EPI_BIAS, st);
     prof_mark(m, "qkv_gemm", st);
     attn_core_fwd_bf16x(m, n, l, st);
     prof_mark(m, "attn_fwd", st);
@@ -555,11 +558,12 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
     const AttnLayerW& w = m->attn[l];
     const XWeights::Layer& x = m->xw.layers[l];
     launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
-    gemm_bf16x(m, x.woT, ws.dY, m1, nullptr, nullptr, 0, ws.dO, A, rows, EPI_BIAS, st);
+    // dE/d[P G, rowsum P] = dY [Wv Wo; bv Wo]^T (into the dO buffer)
+    gemm_bf16x(m, x.voT, ws.dY, m1, nullptr, nullptr, 0, ws.dO, pg_ld(m1), rows, EPI_BIAS, st);
     prof_mark(m, "ln_wo_bwd", st);
-    attn_core_bwd_bf16x(m, n, l, st);
+    attn_core_bwd_bf16x(m, n, l, st);  // dQ, dK; dE/dG += P^T dPG
     prof_mark(m, "attn_bwd", st);
-    gemm_bf16x(m, x.qkvT, ws.dQKV, 3 * A, nullptr, nullptr, 0, ws.dG, m1, rows, EPI_ACCUM, st);
+    gemm_bf16x(m, x.qkT, ws.dQKV, 2 * A, nullptr, nullptr, 0, ws.dG, m1, rows, EPI_ACCUM, st);
     prof_mark(m, "qkv_bwd_gemm", st);
   }
   ea.dG0 = ws.dG; ea.dR = ws.dR;
@@ -882,6 +886,7 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
         Wvo[(size_t)m1 * m1 + c] = acc;
       }
       if ((rc = dev_upload(m, &L.Wvo, to_f(Wvo))) != DP_OK) return fail_free(rc);
+      if ((rc = dev_upload(m, &L.WvoT, transpose_f(Wvo, pg_ld(m1), m1))) != DP_OK) return fail_free(rc);
     }
   }
   // trainable parameter vector (layout in model.h) and its derived copies

@@ -10,18 +10,23 @@
 // split this way; in the adjoint the attention weights P and dS may stay
 // single BF16 (force RMSE ~1e-3 eV/A on the model with perturbed biases).
 //
-// The layer is organised as in the FP32 path (stored Q K V, O through P G,
-// LayerNorm kernels), with:
-//   k_gemm_bf16x          the projections [Q K V] = G Wqkv + b,
+// The layer is organised as in the FP32 path (stored projections, O through
+// P G, LayerNorm kernels), for attention widths 128 and 256 (the cores take
+// the features in halves of 128), with:
+//   k_gemm_bf16x          the projections [Q K] = G [Wq Wk] + b (V only
+//                         enters through [Wv Wo; bv Wo]),
 //                         Y = [P G, rowsum P] [Wv Wo; bv Wo] + bo,
-//                         dO = dY Wo^T, dG += dQKV Wqkv^T, and the fitting
+//                         dPG = dY [Wv Wo; bv Wo]^T, dG += [dQ dK] [Wq Wk]^T,
+//                         and the fitting
 //                         net's products (A by TMA as FP32, split in shared
 //                         memory; B from pre-split images);
 //   k_attn_core_fwd_bf16x per atom: S = Q K^T, smooth softmax and gate,
-//                         [P G, rowsum P] = P [G 1];
-//   k_attn_core_bwd_bf16x per atom: dP = dO V^T, S recomputed, the softmax
-//                         adjoint (dE/drhat, dE/dw), dV = P^T dO,
-//                         dQ = dS K, dK = dS^T Q.
+//                         [P G, rowsum P] (P G on the tensor cores, the row
+//                         sums in FP32);
+//   k_attn_core_bwd_bf16x per atom: dP = dPG [G 1]^T, S recomputed, the
+//                         softmax adjoint (dE/drhat, dE/dw), dE/dG += P^T dPG,
+//                         dQ = dS K, dK = dS^T Q, with dPG = dE/d[P G,
+//                         rowsum P] from a GEMM of dY with [Wv Wo; bv Wo]^T.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -264,7 +269,8 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
 // row-major): per (n block, k block) a hi and a lo tile of bn_max rows
 // (output columns) x 64 K, BF16, K-major with the 128-byte swizzle, zero
 // outside B.
-__global__ void k_x_image(const float* __restrict__ B, int K, int N, int nkb, int bn_max, uint8_t* __restrict__ img) {
+__global__ void k_x_image(const float* __restrict__ B, int ldb, int K, int N, int nkb, int bn_max,
+                          uint8_t* __restrict__ img) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int nnb = (N + XBN - 1) / XBN;
   const long long total = (long long)nnb * nkb * bn_max * XBK;
@@ -274,7 +280,7 @@ __global__ void k_x_image(const float* __restrict__ B, int K, int N, int nkb, in
   const int kb = (int)((t / ((long long)XBK * bn_max)) % nkb);
   const int nb = (int)(t / ((long long)XBK * bn_max * nkb));
   const int k = kb * XBK + k_local, n = nb * XBN + n_local;
-  const float x = (k < K && n < N && n_local < XBN) ? B[(size_t)k * N + n] : 0.f;
+  const float x = (k < K && n < N && n_local < XBN) ? B[(size_t)k * ldb + n] : 0.f;
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
   const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
   const size_t tile = (size_t)bn_max * 128;
@@ -304,15 +310,16 @@ constexpr int XC_NT = 512;
 constexpr int XT = 32768;
 
 struct XCoreArgs {
-  const float* QKV;  // [rows][3 * 128]: Q | K | V
-  const float* G;    // fwd: [rows][m1] layer input
+  const float* QK;   // [rows][ldq]: Q | K (attention width each)
+  const float* G;    // [rows][m1] layer input
   float* PG;         // fwd: [rows][ldpg] = [P G, rowsum(P), 0 ...]
-  const float* dO;   // bwd: [rows][128]
-  float* dQKV;       // bwd: [rows][3 * 128]
+  const float* dPG;  // bwd: [rows][ldpg] dE/d[P G, rowsum P]
+  float* dQK;        // bwd: [rows][ldq] dQ | dK
+  float* dG;         // bwd: [rows][m1] += P^T dE/d(P G) (the path through the values)
   float* dgeo;       // bwd: [rows][4] += (d rhat, d w)
   const float* rw;   // [rows][4] (rhat, w)
   const int* nnei;
-  int n, m1, ldpg, npg;  // npg: MMA width of P [G 1] (ldpg rounded up to 16)
+  int n, m1, ldpg, npg, ldq;  // npg: MMA width of P G (m1 rounded up to 16)
   float scale, shift;
   int* err;
 };
@@ -335,13 +342,30 @@ __device__ __forceinline__ void store_split32(uint8_t* hi, uint8_t* lo, int r, i
 
 constexpr int XF_SMEM = 6 * XT + 2048 + 64;
 
+// Columns [c0, c0 + 32) of one row (p: the row's start): values for columns
+// below ncols, zeros past them and for rows past the last neighbour (ncols % 4
+// == 0, p 16-byte aligned).
+__device__ __forceinline__ void load_cols32(const float* p, int ncols, int c0, bool rv, float* v) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = c0 + 4 * q;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rv && c < ncols) x = *reinterpret_cast<const float4*>(p + c);
+    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+  }
+}
+
+// NH feature halves of 128 (attention width 128 NH).  Tiles: Q hi / lo of
+// one half (then P hi / lo), K hi / lo of one half, G hi / lo.  S is summed
+// over the halves in TMEM [0, 128); P G goes to TMEM [128, 128 + npg); the
+// row sums of P are taken in FP32 by the threads.
+template <int NH>
 __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_constant__ XCoreArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {  // tiles need 1024-byte alignment
     if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
     return;
   }
-  // tiles: Q hi / lo (then P hi / lo), K hi / lo, [G 1] hi / lo
   uint8_t* sQh = sm;
   uint8_t* sQl = sm + XT;
   uint8_t* sKh = sm + 2 * XT;
@@ -366,46 +390,39 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
   const uint32_t tQh = smem_u32(sQh), tQl = smem_u32(sQl), tKh = smem_u32(sKh), tKl = smem_u32(sKl);
   const uint32_t tGh = smem_u32(sGh), tGl = smem_u32(sGl);
   Sync sy{bar, 0u, a.err};
-  const int ld = 3 * 128;
+  const int ld = a.ldq;  // Q | K, 128 NH columns each
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     const bool rv = row < nn;
-    // the next atom's Q and K rows (the first 256 columns of each row) and
-    // its layer input into L2
+    // the next atom's Q and K rows and its layer input into L2
     if (atom + (int)gridDim.x < a.n) {
       const size_t nb = (size_t)(atom + gridDim.x) * NP;
-      if (tid < NP) prefetch_l2(a.QKV + (nb + tid) * ld, (uint32_t)(256 * sizeof(float)));
+      if (tid < NP) prefetch_l2(a.QK + (nb + tid) * ld, (uint32_t)(2 * NH * 128 * sizeof(float)));
       if (issuer) prefetch_l2(a.G + nb * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
     }
     float v[32];
-    load_row32(a.QKV + (base + row) * ld + c0, rv, v);
-    store_split32(sQh, sQl, row, c0, v);
-    load_row32(a.QKV + (base + row) * ld + 128 + c0, rv, v);
-    store_split32(sKh, sKl, row, c0, v);
-    // [G 1]: column m1 is 1 for the neighbour rows, later columns 0 (m1 % 4 == 0)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = c0 + 4 * q;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rv) {
-        if (c < a.m1) x = *reinterpret_cast<const float4*>(a.G + (base + row) * a.m1 + c);
-        else if (c == a.m1) x.x = 1.f;
-      }
-      v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-    }
+    load_cols32(a.G + (base + row) * a.m1, a.m1, c0, rv, v);
     store_split32(sGh, sGl, row, c0, v);
     if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
-    handoff();
-    // S = Q K^T (three split products) -> TMEM [0, 128)
-    if (issuer) {
-      mma_block<false>(tm, tQh, false, 128, tKh, false, 128, 128, 8, false);
-      mma_block<false>(tm, tQl, false, 128, tKh, false, 128, 128, 8, true);
-      mma_block<false>(tm, tQh, false, 128, tKl, false, 128, 128, 8, true);
+    // S = sum over the halves of Q_h K_h^T (three split products each) -> TMEM [0, 128)
+#pragma unroll 1
+    for (int h = 0; h < NH; ++h) {
+      load_row32(a.QK + (base + row) * ld + h * 128 + c0, rv, v);
+      store_split32(sQh, sQl, row, c0, v);
+      load_row32(a.QK + (base + row) * ld + NH * 128 + h * 128 + c0, rv, v);
+      store_split32(sKh, sKl, row, c0, v);
+      handoff();
+      if (issuer) {
+        mma_block<false>(tm, tQh, false, 128, tKh, false, 128, 128, 8, h > 0);
+        mma_block<false>(tm, tQl, false, 128, tKh, false, 128, 128, 8, true);
+        mma_block<false>(tm, tQh, false, 128, tKl, false, 128, 128, 8, true);
+      }
+      commit_and_sync(sy, issuer);
     }
-    commit_and_sync(sy, issuer);
     // smooth softmax and gate: P_jk = A_jk w_j w_k (rhat_j . rhat_k) -> Q's tiles
     tmem_ld32(tm + lane_off + c0, v);
+    float psum;
     {
       const RowXchg xr(sQh, row, part, lane, quad);  // P hi is stored after the exchanges
       const float4 kj = s_key[row];
@@ -434,33 +451,41 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
       }
       sum = xr.sum(sum);
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      psum = 0.f;
       if (live) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float4 kk = s_key[c0 + i];
           const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
           v[i] = v[i] * inv * (wj * kk.w) * c;
+          psum += v[i];
         }
       } else {
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.f;
       }
+      psum = xr.sum(psum);
       store_split32(sQh, sQl, row, c0, v);
     }
     handoff();
-    // [P G, rowsum P] = P [G 1] ([G 1] as an MN-major operand) -> TMEM [128, 128 + npg)
+    // P G = P G ([G] as an MN-major operand) -> TMEM [128, 128 + npg)
     if (issuer) {
       mma_block<false>(tm + 128, tQh, false, 128, tGh, true, 128, a.npg, 8, false);
       mma_block<false>(tm + 128, tQl, false, 128, tGh, true, 128, a.npg, 8, true);
       mma_block<false>(tm + 128, tQh, false, 128, tGl, true, 128, a.npg, 8, true);
     }
     commit_and_sync(sy, issuer);
-    tmem_ld32(tm + lane_off + 128 + c0, v);
+    // [P G, rowsum P, 0 ...] -> row of PG (ldpg columns)
     {
       float4* out = reinterpret_cast<float4*>(a.PG + (base + row) * a.ldpg);
+      if (c0 < a.m1) {  // warp-uniform
+        tmem_ld32(tm + lane_off + 128 + c0, v);
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (c0 + 4 * q < a.ldpg) out[(c0 >> 2) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 8; ++q)
+          if (c0 + 4 * q < a.m1) out[(c0 >> 2) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      if (part == 0)
+        for (int c = a.m1; c < a.ldpg; c += 4) out[c >> 2] = make_float4(c == a.m1 ? psum : 0.f, 0.f, 0.f, 0.f);
     }
     fence_before_sync();
     __syncthreads();
@@ -471,24 +496,154 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
   if (warp == 0) tmem_dealloc(tm, 256);
 }
 
-// Adjoint core.  Tiles: 0 dO hi, 1 dO lo, 2 V hi then Q lo, 3 V lo then P
-// then dS, 4 K hi, 5 K lo, 6 Q hi.  TMEM: [0, 128) S, then dS, then dQ;
-// [128, 256) dP; [256, 384) dV; [384, 512) dK.
+// The softmax adjoint over this thread's 32 keys of its row, S and dP
+// re-read from TMEM in pieces of 8: A is recomputed with its row max and
+// normaliser; tsum = sum_k A_jk dA_jk with dA = dP w_j w_k c_jk; then per key
+// dLp = A (dA - tsum), dS = dLp w_j w_k scale -> TMEM over S, P -> the tile
+// pt, dE/d(w_j w_k) = dP A c + dLp (l + shift), dE/dc = dP A w_j w_k.  dP
+// includes dpg1, the adjoint of the row sum of P (the same for every key).
+// The row part (this thread's row) and column parts (lanes 0-15: key c0 + h
+// + lane) of dE/drhat and dE/dw are returned.  pt's row lines also carry the
+// row exchanges, before P is stored.
+__device__ __forceinline__ void softmax_adjoint(const XCoreArgs& a, uint8_t* pt, const float4* s_key, uint32_t tS,
+                                                uint32_t tP, int row, int part, int lane, int quad, int nn, float dpg1,
+                                                float4& rpart, float4* cpart) {
+  const int c0 = part * 32;
+  const bool rv = row < nn;
+  const RowXchg xr(pt, row, part, lane, quad);
+  const float4 kj = s_key[row];
+  const float wj = kj.w;
+  // the TMEM loads are warp-collective: their condition is uniform over the
+  // warp (c0), the row mask (rv) is applied per lane
+  const bool wlive = c0 < nn;
+  const bool live = wlive && rv;
+  float mx = -INFINITY;
+  if (wlive) {
+#pragma unroll
+    for (int e8 = 0; e8 < 32; e8 += 8) {
+      float t[8];
+      tmem_ld8(tS + e8, t);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = c0 + e8 + i;
+        if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_key[k].w));
+      }
+    }
+  }
+  mx = xr.max(mx);
+  const float mxs = mx == -INFINITY ? 0.f : mx;
+  float sum = 0.f, esum = 0.f;  // sum_k e_k and sum_k e_k dA_k
+  if (wlive) {
+#pragma unroll
+    for (int e8 = 0; e8 < 32; e8 += 8) {
+      float t[8], u[8];
+      tmem_ld8(tS + e8, t);
+      tmem_ld8(tP + e8, u);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = c0 + e8 + i;
+        if (k < nn && rv) {
+          const float4 kk = s_key[k];
+          const float ww = wj * kk.w;
+          const float e = exp_sfu((t[i] * a.scale + a.shift) * ww - mxs);
+          sum += e;
+          esum += e * (u[i] + dpg1) * ww * (kj.x * kk.x + kj.y * kk.y + kj.z * kk.z);
+        }
+      }
+    }
+  }
+  const float2 ss = xr.sum2(make_float2(sum, esum));
+  const float inv = ss.x > 0.f ? 1.0f / ss.x : 0.f;
+  const float tsum = ss.y * inv;
+  float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll 1
+  for (int h = 0; h < 32; h += 16) {
+    float4 cph = make_float4(0.f, 0.f, 0.f, 0.f);
+    float cw[16], dcv[16];
+#pragma unroll
+    for (int e8 = 0; e8 < 16; e8 += 8) {
+      float t[8], u[8], pv[8];
+      tmem_ld8(tS + h + e8, t);
+      tmem_ld8(tP + h + e8, u);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = c0 + h + e8 + i;
+        const float4 kk = s_key[k];
+        const float ww = wj * kk.w;
+        const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
+        const float lg = t[i] * a.scale + a.shift;
+        const float A = (live && k < nn) ? exp_sfu(lg * ww - mxs) * inv : 0.f;
+        const float dp = u[i] + dpg1;
+        const float dA = dp * ww * c;
+        const float dLp = A * (dA - tsum);
+        const float H = fmaf(dLp, lg, dp * A * c);  // dE/d(w_j w_k)
+        const float dc = dp * A * ww;               // dE/dc_jk
+        rw_ += H * kk.w;
+        rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
+        cw[e8 + i] = H * wj;
+        dcv[e8 + i] = dc;
+        pv[i] = A * ww * c;
+        t[i] = dLp * ww * a.scale;  // dS
+      }
+      uint4 w4;
+      w4.x = pack_bf16(pv[0], pv[1]);
+      w4.y = pack_bf16(pv[2], pv[3]);
+      w4.z = pack_bf16(pv[4], pv[5]);
+      w4.w = pack_bf16(pv[6], pv[7]);
+      sw128_store8(pt, row, c0 + h + e8, 128, w4);
+      tmem_st8_async(tS + h + e8, t);
+    }
+    cph.w = warp_reduce_scatter16(cw);
+    float tmp[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
+    cph.x = warp_reduce_scatter16(tmp);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
+    cph.y = warp_reduce_scatter16(tmp);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
+    cph.z = warp_reduce_scatter16(tmp);
+    cpart[h >> 4] = cph;
+  }
+  rpart = make_float4(rx, ry, rz, rw_);
+  tmem_wait_st();
+}
+
+// TMEM columns [col, col + 32) of this warp's lanes -> 32 floats at dst.
+__device__ __forceinline__ void tmem_to_row32(uint32_t taddr, float* dst) {
+  float v[32];
+  tmem_ld32(taddr, v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// Adjoint core, in the form of the forward (Y = [P G, rowsum P] [Wv Wo; bv Wo]
+// + bo): with dPG = dE/d[P G, rowsum P] (a GEMM of dY with [Wv Wo; bv Wo]^T),
+// dP_jk = (dPG G^T)_jk + dPG_j,m1 and dE/dG += P^T dPG (columns below m1), so
+// the values V and their adjoint never appear.  NH feature halves of 128.
+// Tiles T0 .. T6:
+//   NH = 1: T0 / T1 dPG hi / lo, T2 G hi then Q lo, T3 G lo then P then dS,
+//           T4 Q hi, T5 / T6 K hi / lo.
+//   NH = 2: T0 / T1 dPG hi / lo (then K0, then Q0 hi / lo), T2 G hi then Q0 lo
+//           then P then dS, T3 G lo then Q1 hi, T4 Q0 hi then K1 hi, T5 K0 hi
+//           then Q1 lo, T6 K0 lo then K1 lo; the first half's K and Q come in
+//           again (from L2) for dQ and dK.
+// TMEM: [0, 128) S, then dS, then dQ (first half); [128, 256) dP, then dQ of
+// the second half; [256, 256 + npg) P^T dPG, then dK of the first half (NH =
+// 2); [384, 512) dK (of the last half).
 constexpr int XB_SMEM = 7 * XT + 2048 + 64;
 
+template <int NH>
 __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_constant__ XCoreArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   if ((smem_u32(sm) & 1023u) != 0) {
     if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
     return;
   }
-  uint8_t* sOh = sm;
-  uint8_t* sOl = sm + XT;
-  uint8_t* s2 = sm + 2 * XT;  // V hi, then Q lo
-  uint8_t* s3 = sm + 3 * XT;  // V lo, then P, then dS
-  uint8_t* sKh = sm + 4 * XT;
-  uint8_t* sKl = sm + 5 * XT;
-  uint8_t* sQh = sm + 6 * XT;
+  uint8_t* T[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) T[i] = sm + i * XT;
   float4* s_key = reinterpret_cast<float4*>(sm + 7 * XT);  // [128] (rhat, w)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
@@ -504,185 +659,150 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
   handoff();
   const uint32_t tm = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-  const uint32_t tOh = smem_u32(sOh), tOl = smem_u32(sOl), t2 = smem_u32(s2), t3 = smem_u32(s3);
-  const uint32_t tKh = smem_u32(sKh), tKl = smem_u32(sKl), tQh = smem_u32(sQh);
+  uint32_t t[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) t[i] = smem_u32(T[i]);
+  const int kg = a.npg / 16;  // K-steps of dPG G^T
   Sync sy{bar, 0u, a.err};
-  const int ld = 3 * 128;
+  const int ld = a.ldq;        // Q | K, 128 NH columns each; dQ | dK likewise
+  constexpr int AW = NH * 128;  // attention width
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     const bool rv = row < nn;
-    if (issuer && atom + (int)gridDim.x < a.n) {
+    const float* qk = a.QK + (base + row) * ld;
+    // the next atom's Q and K rows, dPG and layer input into L2
+    if (atom + (int)gridDim.x < a.n) {
       const size_t nb = (size_t)(atom + gridDim.x) * NP;
-      prefetch_l2(a.QKV + nb * ld, (uint32_t)(NP * ld * sizeof(float)));
-      prefetch_l2(a.dO + nb * 128, (uint32_t)(NP * 128 * sizeof(float)));
+      if (tid < NP) prefetch_l2(a.QK + (nb + tid) * ld, (uint32_t)(2 * AW * sizeof(float)));
+      if (issuer) {
+        prefetch_l2(a.dPG + nb * a.ldpg, (uint32_t)(NP * a.ldpg * sizeof(float)));
+        prefetch_l2(a.G + nb * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
+      }
     }
     float v[32], q32[32];
-    load_row32(a.dO + (base + row) * 128 + c0, rv, v);
-    store_split32(sOh, sOl, row, c0, v);
-    load_row32(a.QKV + (base + row) * ld + 256 + c0, rv, v);
-    store_split32(s2, s3, row, c0, v);
-    load_row32(a.QKV + (base + row) * ld + 128 + c0, rv, v);
-    store_split32(sKh, sKl, row, c0, v);
-    load_row32(a.QKV + (base + row) * ld + c0, rv, q32);
-    store_row32<false>(sQh, row, c0, q32);
+    // dPG (columns below m1; the row-sum adjoint, column m1, separately) and G
+    load_cols32(a.dPG + (base + row) * a.ldpg, a.m1, c0, rv, v);
+    const float dpg1 = rv ? a.dPG[(base + row) * a.ldpg + a.m1] : 0.f;
+    store_split32(T[0], T[1], row, c0, v);
+    load_cols32(a.G + (base + row) * a.m1, a.m1, c0, rv, v);
+    store_split32(T[2], T[3], row, c0, v);
+    load_row32(qk + AW + c0, rv, v);  // K, first half
+    store_split32(T[5], T[6], row, c0, v);
+    load_row32(qk + c0, rv, q32);  // Q, first half
+    store_row32<false>(T[4], row, c0, q32);
     if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     handoff();
-    // M1: dP = dO V^T -> [128, 256); S = Q_hi K^T -> [0, 128)
+    // dP = dPG G^T -> [128, 256); S = Q0_hi K0^T -> [0, 128)
     if (issuer) {
-      mma_block<false>(tm + 128, tOh, false, 128, t2, false, 128, 128, 8, false);
-      mma_block<false>(tm + 128, tOl, false, 128, t2, false, 128, 128, 8, true);
-      mma_block<false>(tm + 128, tOh, false, 128, t3, false, 128, 128, 8, true);
-      mma_block<false>(tm, tQh, false, 128, tKh, false, 128, 128, 8, false);
-      mma_block<false>(tm, tQh, false, 128, tKl, false, 128, 128, 8, true);
+      mma_block<false>(tm + 128, t[0], false, 128, t[2], false, 128, 128, kg, false);
+      mma_block<false>(tm + 128, t[1], false, 128, t[2], false, 128, 128, kg, true);
+      mma_block<false>(tm + 128, t[0], false, 128, t[3], false, 128, 128, kg, true);
+      mma_block<false>(tm, t[4], false, 128, t[5], false, 128, 128, 8, false);
+      mma_block<false>(tm, t[4], false, 128, t[6], false, 128, 128, 8, true);
     }
     commit_and_sync(sy, issuer);
-    // V is dead: Q lo -> tile 2, then S += Q_lo K_hi
-    store_row32<false, true>(s2, row, c0, q32);
-    handoff();
-    if (issuer) mma_block<false>(tm, t2, false, 128, tKh, false, 128, 128, 8, true);
-    commit_and_sync(sy, issuer);
-    // softmax adjoint over this thread's 32 keys (S and dP re-read from TMEM
-    // in pieces of 8): A recomputed with its row max and normaliser;
-    // tsum = sum_k A_jk dA_jk with dA = dP w_j w_k c_jk; then per key
-    // dLp = A (dA - tsum), dS = dLp w_j w_k scale -> TMEM over S, P -> tile 3,
-    // dE/d(w_j w_k) = dP A c + dLp (l + shift), dE/dc = dP A w_j w_k.  The
-    // row parts (this thread's row) and column parts (lanes 0-15: key c0 + h
-    // + lane) of dE/drhat and dE/dw stay in registers.
+    // G is dead: Q0 lo -> T2, S += Q0_lo K0_hi (NH = 2: with the second half's
+    // Q hi, K hi / lo, then its Q lo)
+    store_row32<false, true>(T[2], row, c0, q32);
+    int pti;  // the P / dS tile
+    if constexpr (NH == 1) {
+      handoff();
+      if (issuer) mma_block<false>(tm, t[2], false, 128, t[5], false, 128, 128, 8, true);
+      commit_and_sync(sy, issuer);
+      pti = 3;
+    } else {
+      load_row32(qk + 128 + c0, rv, q32);  // Q1
+      store_row32<false>(T[3], row, c0, q32);
+      load_row32(qk + AW + 128 + c0, rv, v);  // K1 (hi -> T4 over Q0 hi, lo -> T6 over K0 lo)
+      store_row32<false>(T[4], row, c0, v);
+      store_row32<false, true>(T[6], row, c0, v);
+      handoff();
+      if (issuer) {
+        mma_block<false>(tm, t[2], false, 128, t[5], false, 128, 128, 8, true);  // Q0_lo K0_hi
+        mma_block<false>(tm, t[3], false, 128, t[4], false, 128, 128, 8, true);  // Q1_hi K1_hi
+        mma_block<false>(tm, t[3], false, 128, t[6], false, 128, 128, 8, true);  // Q1_hi K1_lo
+      }
+      commit_and_sync(sy, issuer);
+      store_row32<false, true>(T[5], row, c0, q32);  // Q1 lo over K0 hi
+      handoff();
+      if (issuer) mma_block<false>(tm, t[5], false, 128, t[4], false, 128, 128, 8, true);  // Q1_lo K1_hi
+      commit_and_sync(sy, issuer);
+      pti = 2;
+    }
     float4 rpart, cpart[2];
-    {
-      const RowXchg xr(s3, row, part, lane, quad);  // V lo is dead; P goes to tile 3 after the exchanges
-      const uint32_t tS = tm + lane_off + c0, tP = tm + lane_off + 128 + c0;
-      const float4 kj = s_key[row];
-      const float wj = kj.w;
-      // the TMEM loads are warp-collective: their condition is uniform over
-      // the warp (c0), the row mask (rv) is applied per lane
-      const bool wlive = c0 < nn;
-      const bool live = wlive && rv;
-      float mx = -INFINITY;
-      if (wlive) {
-#pragma unroll
-        for (int e8 = 0; e8 < 32; e8 += 8) {
-          float t[8];
-          tmem_ld8(tS + e8, t);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = c0 + e8 + i;
-            if (k < nn && rv) mx = fmaxf(mx, (t[i] * a.scale + a.shift) * (wj * s_key[k].w));
-          }
-        }
-      }
-      mx = xr.max(mx);
-      const float mxs = mx == -INFINITY ? 0.f : mx;
-      float sum = 0.f, esum = 0.f;  // sum_k e_k and sum_k e_k dA_k
-      if (wlive) {
-#pragma unroll
-        for (int e8 = 0; e8 < 32; e8 += 8) {
-          float t[8], u[8];
-          tmem_ld8(tS + e8, t);
-          tmem_ld8(tP + e8, u);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = c0 + e8 + i;
-            if (k < nn && rv) {
-              const float4 kk = s_key[k];
-              const float ww = wj * kk.w;
-              const float e = exp_sfu((t[i] * a.scale + a.shift) * ww - mxs);
-              sum += e;
-              esum += e * u[i] * ww * (kj.x * kk.x + kj.y * kk.y + kj.z * kk.z);
-            }
-          }
-        }
-      }
-      const float2 ss = xr.sum2(make_float2(sum, esum));
-      const float inv = ss.x > 0.f ? 1.0f / ss.x : 0.f;
-      const float tsum = ss.y * inv;
-      float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-#pragma unroll 1
-      for (int h = 0; h < 32; h += 16) {
-        float4 cph = make_float4(0.f, 0.f, 0.f, 0.f);
-        float cw[16], dcv[16];
-#pragma unroll
-        for (int e8 = 0; e8 < 16; e8 += 8) {
-          float t[8], u[8], pv[8];
-          tmem_ld8(tS + h + e8, t);
-          tmem_ld8(tP + h + e8, u);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = c0 + h + e8 + i;
-            const float4 kk = s_key[k];
-            const float ww = wj * kk.w;
-            const float c = kj.x * kk.x + kj.y * kk.y + kj.z * kk.z;
-            const float lg = t[i] * a.scale + a.shift;
-            const float A = (live && k < nn) ? exp_sfu(lg * ww - mxs) * inv : 0.f;
-            const float dA = u[i] * ww * c;
-            const float dLp = A * (dA - tsum);
-            const float H = fmaf(dLp, lg, u[i] * A * c);  // dE/d(w_j w_k)
-            const float dc = u[i] * A * ww;               // dE/dc_jk
-            rw_ += H * kk.w;
-            rx += dc * kk.x; ry += dc * kk.y; rz += dc * kk.z;
-            cw[e8 + i] = H * wj;
-            dcv[e8 + i] = dc;
-            pv[i] = A * ww * c;
-            t[i] = dLp * ww * a.scale;  // dS
-          }
-          uint4 w4;
-          w4.x = pack_bf16(pv[0], pv[1]);
-          w4.y = pack_bf16(pv[2], pv[3]);
-          w4.z = pack_bf16(pv[4], pv[5]);
-          w4.w = pack_bf16(pv[6], pv[7]);
-          sw128_store8(s3, row, c0 + h + e8, 128, w4);
-          tmem_st8_async(tS + h + e8, t);
-        }
-        cph.w = warp_reduce_scatter16(cw);
-        float tmp[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.x;
-        cph.x = warp_reduce_scatter16(tmp);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.y;
-        cph.y = warp_reduce_scatter16(tmp);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tmp[i] = dcv[i] * kj.z;
-        cph.z = warp_reduce_scatter16(tmp);
-        cpart[h >> 4] = cph;
-      }
-      rpart = make_float4(rx, ry, rz, rw_);
-      tmem_wait_st();
-    }
+    softmax_adjoint(a, T[pti], s_key, tm + lane_off + c0, tm + lane_off + 128 + c0, row, part, lane, quad, nn, dpg1,
+                    rpart, cpart);
     handoff();
-    // M2: dV = P^T dO -> [256, 384)
+    // P^T dPG -> [256, 256 + npg) (P^T and dPG as MN-major operands)
     if (issuer) {
-      mma_block<false>(tm + 256, t3, true, 128, tOh, true, 128, 128, 8, false);
-      mma_block<false>(tm + 256, t3, true, 128, tOl, true, 128, 128, 8, true);
+      mma_block<false>(tm + 256, t[pti], true, 128, t[0], true, 128, a.npg, 8, false);
+      mma_block<false>(tm + 256, t[pti], true, 128, t[1], true, 128, a.npg, 8, true);
     }
     commit_and_sync(sy, issuer);
-    tmem_ld32(tm + lane_off + c0, v);  // dS
-    store_row32<false>(s3, row, c0, v);
-    handoff();
-    // M3: dQ = dS K -> [0, 128); dK = dS^T Q -> [384, 512)
-    if (issuer) {
-      mma_block<false>(tm, t3, false, 128, tKh, true, 128, 128, 8, false);
-      mma_block<false>(tm, t3, false, 128, tKl, true, 128, 128, 8, true);
-      mma_block<false>(tm + 384, t3, true, 128, tQh, true, 128, 128, 8, false);
-      mma_block<false>(tm + 384, t3, true, 128, t2, true, 128, 128, 8, true);
-    }
-    commit_and_sync(sy, issuer);
-    // dQ, dK, dV -> global; the row and column parts -> tile 0 (dO is dead):
-    // [quadrant][128 keys] column parts, then [quarter][128 rows] row parts
-    {
-      float* dst = a.dQKV + (base + row) * ld + c0;
-      tmem_ld32(tm + lane_off + c0, v);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      tmem_ld32(tm + lane_off + 384 + c0, v);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst + 128)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    // dE/dG (this row) += P^T dPG, columns below m1
+    if (c0 < a.m1) {  // warp-uniform
       tmem_ld32(tm + lane_off + 256 + c0, v);
+      if (rv) {
+        float4* dg = reinterpret_cast<float4*>(a.dG + (base + row) * a.m1);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst + 256)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + 4 * q;
+          if (c < a.m1) {
+            float4 x = dg[c >> 2];
+            x.x += v[4 * q]; x.y += v[4 * q + 1]; x.z += v[4 * q + 2]; x.w += v[4 * q + 3];
+            dg[c >> 2] = x;
+          }
+        }
+      }
     }
-    float4* parts = reinterpret_cast<float4*>(sOh);
+    // dS -> the P tile (P is dead)
+    tmem_ld32(tm + lane_off + c0, v);
+    store_row32<false>(T[pti], row, c0, v);
+    if constexpr (NH == 1) {
+      handoff();
+      // dQ = dS K -> [0, 128); dK = dS^T Q -> [384, 512)
+      if (issuer) {
+        mma_block<false>(tm, t[3], false, 128, t[5], true, 128, 128, 8, false);
+        mma_block<false>(tm, t[3], false, 128, t[6], true, 128, 128, 8, true);
+        mma_block<false>(tm + 384, t[3], true, 128, t[4], true, 128, 128, 8, false);
+        mma_block<false>(tm + 384, t[3], true, 128, t[2], true, 128, 128, 8, true);
+      }
+      commit_and_sync(sy, issuer);
+      tmem_to_row32(tm + lane_off + c0, a.dQK + (base + row) * ld + c0);
+      tmem_to_row32(tm + lane_off + 384 + c0, a.dQK + (base + row) * ld + AW + c0);
+    } else {
+      load_row32(qk + AW + c0, rv, v);  // K0 again -> T0 / T1
+      store_split32(T[0], T[1], row, c0, v);
+      handoff();
+      // dQ0 = dS K0 -> [0, 128), dQ1 = dS K1 -> [128, 256), dK1 = dS^T Q1 -> [384, 512)
+      if (issuer) {
+        mma_block<false>(tm, t[2], false, 128, t[0], true, 128, 128, 8, false);
+        mma_block<false>(tm, t[2], false, 128, t[1], true, 128, 128, 8, true);
+        mma_block<false>(tm + 128, t[2], false, 128, t[4], true, 128, 128, 8, false);
+        mma_block<false>(tm + 128, t[2], false, 128, t[6], true, 128, 128, 8, true);
+        mma_block<false>(tm + 384, t[2], true, 128, t[3], true, 128, 128, 8, false);
+        mma_block<false>(tm + 384, t[2], true, 128, t[5], true, 128, 128, 8, true);
+      }
+      commit_and_sync(sy, issuer);
+      load_row32(qk + c0, rv, v);  // Q0 again -> T0 / T1
+      store_split32(T[0], T[1], row, c0, v);
+      handoff();
+      // dK0 = dS^T Q0 -> [256, 384)
+      if (issuer) {
+        mma_block<false>(tm + 256, t[2], true, 128, t[0], true, 128, 128, 8, false);
+        mma_block<false>(tm + 256, t[2], true, 128, t[1], true, 128, 128, 8, true);
+      }
+      commit_and_sync(sy, issuer);
+      float* dst = a.dQK + (base + row) * ld;
+      tmem_to_row32(tm + lane_off + c0, dst + c0);
+      tmem_to_row32(tm + lane_off + 128 + c0, dst + 128 + c0);
+      tmem_to_row32(tm + lane_off + 256 + c0, dst + AW + c0);
+      tmem_to_row32(tm + lane_off + 384 + c0, dst + AW + 128 + c0);
+    }
+    // the row and column parts -> T0 (dead): [quadrant][128 keys] column
+    // parts, then [quarter][128 rows] row parts
+    float4* parts = reinterpret_cast<float4*>(T[0]);
     if (lane < 16) {
       parts[quad * 128 + c0 + lane] = cpart[0];
       parts[quad * 128 + c0 + 16 + lane] = cpart[1];
@@ -716,7 +836,7 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
 // ------------------------------------------------------------------ host
 
 bool bf16x_supported(const dp_model* m) {
-  if (m->nattn > 0 && (m->A != 128 || pg_ld(m->m1) > 128 || m->m1 % 4 != 0)) return false;
+  if (m->nattn > 0 && ((m->A != 128 && m->A != 256) || m->m1 > 128 || m->m1 % 4 != 0)) return false;
   int fan = m->fit_in;
   if (fan % 4) return false;
   for (int l = 0; l < m->nfit; ++l) {
@@ -738,7 +858,8 @@ XImage x_image_shape(int K, int N) {
   return s;
 }
 
-int x_image_build(dp_model* m, XImage& im, const float* B, cudaStream_t st, std::string& msg) {
+// B: [K][ldb] row-major, the image's N columns taken from the left.
+int x_image_build(dp_model* m, XImage& im, const float* B, int ldb, cudaStream_t st, std::string& msg) {
   if (!im.d) {
     void* d = nullptr;
     if (cudaMalloc(&d, im.bytes()) != cudaSuccess) {
@@ -749,7 +870,7 @@ int x_image_build(dp_model* m, XImage& im, const float* B, cudaStream_t st, std:
     im.d = d;
   }
   const long long total = (long long)im.nnb * im.nkb * im.bn_max * XBK;
-  k_x_image<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(B, im.K, im.N, im.nkb, im.bn_max,
+  k_x_image<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(B, ldb, im.K, im.N, im.nkb, im.bn_max,
                                                              reinterpret_cast<uint8_t*>(im.d));
   note_launch();
   return DP_OK;
@@ -760,8 +881,8 @@ int x_image_build(dp_model* m, XImage& im, const float* B, cudaStream_t st, std:
 int bf16x_init_weights(dp_model* m, std::string& msg) {
   XWeights& w = m->xw;
   if (!bf16x_supported(m)) {
-    msg = "the BF16-split path needs attention width 128, an embedding width <= 124 divisible by 4 and fitting "
-          "widths divisible by 4";
+    msg = "the BF16-split path needs attention width 128 or 256, an embedding width <= 128 divisible by 4 and "
+          "fitting widths divisible by 4";
     return DP_ERR_UNSUPPORTED;
   }
   if (!g_x_encode) {
@@ -779,15 +900,16 @@ int bf16x_init_weights(dp_model* m, std::string& msg) {
   for (int l = 0; l < m->nattn; ++l) {
     XWeights::Layer& L = w.layers[l];
     const AttnLayerW& aw = m->attn[l];
-    L.qkv = x_image_shape(m1, 3 * A);
+    // V only enters through [Wv Wo; bv Wo], so the projection stops at [Q K]
+    L.qk = x_image_shape(m1, 2 * A);    // the first 2A columns of Wqkv
     L.vo = x_image_shape(pg_ld(m1), m1);
-    L.woT = x_image_shape(m1, A);
-    L.qkvT = x_image_shape(3 * A, m1);
+    L.voT = x_image_shape(m1, pg_ld(m1));
+    L.qkT = x_image_shape(2 * A, m1);   // the first 2A rows of Wqkv^T: [Wq Wk]^T
     int rc;
-    if ((rc = x_image_build(m, L.qkv, aw.Wqkv, nullptr, msg)) != DP_OK) return rc;
-    if ((rc = x_image_build(m, L.vo, aw.Wvo, nullptr, msg)) != DP_OK) return rc;
-    if ((rc = x_image_build(m, L.woT, aw.WoT, nullptr, msg)) != DP_OK) return rc;
-    if ((rc = x_image_build(m, L.qkvT, aw.WqkvT, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.qk, aw.Wqkv, 3 * A, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.vo, aw.Wvo, m1, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.voT, aw.WvoT, pg_ld(m1), nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.qkT, aw.WqkvT, m1, nullptr, msg)) != DP_OK) return rc;
   }
   w.fit.assign(m->nfit, XImage{});
   w.fitT.assign(m->nfit, XImage{});
@@ -799,8 +921,10 @@ int bf16x_init_weights(dp_model* m, std::string& msg) {
   }
   bf16x_refresh(m, nullptr);
   cudaFuncSetAttribute(k_gemm_bf16x, cudaFuncAttributeMaxDynamicSharedMemorySize, x_smem(XBN));
-  cudaFuncSetAttribute(k_attn_core_fwd_bf16x, cudaFuncAttributeMaxDynamicSharedMemorySize, XF_SMEM);
-  cudaFuncSetAttribute(k_attn_core_bwd_bf16x, cudaFuncAttributeMaxDynamicSharedMemorySize, XB_SMEM);
+  cudaFuncSetAttribute(k_attn_core_fwd_bf16x<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, XF_SMEM);
+  cudaFuncSetAttribute(k_attn_core_fwd_bf16x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, XF_SMEM);
+  cudaFuncSetAttribute(k_attn_core_bwd_bf16x<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, XB_SMEM);
+  cudaFuncSetAttribute(k_attn_core_bwd_bf16x<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, XB_SMEM);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     msg = "building the BF16 weight images failed";
     return DP_ERR_CUDA;
@@ -814,8 +938,8 @@ void bf16x_refresh(dp_model* m, cudaStream_t st) {
   XWeights& w = m->xw;
   std::string msg;
   for (int l = 0; l < (int)w.fit.size(); ++l) {
-    x_image_build(m, w.fit[l], m->fitW[l], st, msg);
-    x_image_build(m, w.fitT[l], m->fitWT[l], st, msg);
+    x_image_build(m, w.fit[l], m->fitW[l], w.fit[l].N, st, msg);
+    x_image_build(m, w.fitT[l], m->fitWT[l], w.fitT[l].N, st, msg);
   }
 }
 
@@ -862,18 +986,20 @@ namespace {
 XCoreArgs core_args(dp_model* m, int n, int l) {
   Workspace& ws = m->ws;
   XCoreArgs a{};
-  a.QKV = ws.QKV[l];
+  a.QK = ws.QKV[l];  // [rows][2A]: Q | K
   a.G = ws.G[l];
   a.PG = ws.O[l];
-  a.dO = ws.dO;
-  a.dQKV = ws.dQKV;
+  a.dPG = ws.dO;  // dE/d[P G, rowsum P], [rows][ldpg]
+  a.dQK = ws.dQKV;
+  a.dG = ws.dG;
   a.dgeo = ws.dgeo;
   a.rw = ws.rw;
   a.nnei = ws.nnei;
   a.n = n;
   a.m1 = m->m1;
   a.ldpg = pg_ld(m->m1);
-  a.npg = (a.ldpg + 15) & ~15;
+  a.npg = (m->m1 + 15) & ~15;
+  a.ldq = 2 * m->A;
   a.scale = (float)(1.0 / std::sqrt((double)m->A));
   a.shift = (float)m->shift;
   a.err = m->d_err;
@@ -884,14 +1010,20 @@ XCoreArgs core_args(dp_model* m, int n, int l) {
 void attn_core_fwd_bf16x(dp_model* m, int n, int l, cudaStream_t st) {
   if (n == 0) return;
   const int grid = std::min(n, x_sm_count(m->device));
-  k_attn_core_fwd_bf16x<<<grid, XC_NT, XF_SMEM, st>>>(core_args(m, n, l));
+  if (m->A == 256)
+    k_attn_core_fwd_bf16x<2><<<grid, XC_NT, XF_SMEM, st>>>(core_args(m, n, l));
+  else
+    k_attn_core_fwd_bf16x<1><<<grid, XC_NT, XF_SMEM, st>>>(core_args(m, n, l));
   note_launch();
 }
 
 void attn_core_bwd_bf16x(dp_model* m, int n, int l, cudaStream_t st) {
   if (n == 0) return;
   const int grid = std::min(n, x_sm_count(m->device));
-  k_attn_core_bwd_bf16x<<<grid, XC_NT, XB_SMEM, st>>>(core_args(m, n, l));
+  if (m->A == 256)
+    k_attn_core_bwd_bf16x<2><<<grid, XC_NT, XB_SMEM, st>>>(core_args(m, n, l));
+  else
+    k_attn_core_bwd_bf16x<1><<<grid, XC_NT, XB_SMEM, st>>>(core_args(m, n, l));
   note_launch();
 }
 

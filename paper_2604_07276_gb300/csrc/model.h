@@ -29,8 +29,10 @@ struct Arena {
 struct AttnLayerW {
   float *Wqkv, *bqkv, *WqkvT, *Wo, *bo, *WoT, *ln_g, *ln_b;
   // FP32 path: [Wv Wo; bv Wo; 0...] ([pg_ld(m1)][m1]), formed in FP64, so that
-  // Y = O Wo + bo = [P G, rowsum(P)] Wvo + bo (see launch_attn_fwd_f32)
+  // Y = O Wo + bo = [P G, rowsum(P)] Wvo + bo (see launch_attn_fwd_f32); and
+  // its transpose [m1][pg_ld(m1)] (the bf16x adjoint)
   float* Wvo;
+  float* WvoT;
 };
 // Row stride of [P G, rowsum(P)]: M1 + 1 columns rounded up to 8.
 inline int pg_ld(int m1) { return (m1 + 1 + 7) & ~7; }
@@ -67,10 +69,10 @@ struct XWeights {
   bool ready = false;
   std::vector<void*> allocations;
   struct Layer {
-    XImage qkv;   // Wqkv [m1][3A]
+    XImage qk;    // [Wq Wk] [m1][2A]
     XImage vo;    // [Wv Wo; bv Wo; 0] [pg_ld(m1)][m1]
-    XImage woT;   // Wo^T [m1][A]
-    XImage qkvT;  // Wqkv^T [3A][m1]
+    XImage voT;   // [Wv Wo; bv Wo]^T [m1][pg_ld(m1)]
+    XImage qkT;   // [Wq Wk]^T [2A][m1]
   };
   std::vector<Layer> layers;
   std::vector<XImage> fit, fitT;  // fitting layers, forward and transposed

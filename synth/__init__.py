@@ -7,7 +7,7 @@ fixed seeds and serialises weights to the binary file format that
 benchmark import it; it imports neither of them.
 """
 
-from .model import (ModelConfig, make_weights, write_weights, STUDENT_CONFIG, DEFAULT_CONFIG,
+from .model import (ModelConfig, make_weights, write_weights, STUDENT_CONFIG, DEFAULT_CONFIG, PAPER_SIZE_CONFIG,
                     TEACHER_BASE_OUT_SCALE, teacher_base_weights, teacher_weights, perturbed)
 from .systems import (
     water_box,
@@ -26,6 +26,7 @@ __all__ = [
     "write_weights",
     "DEFAULT_CONFIG",
     "STUDENT_CONFIG",
+    "PAPER_SIZE_CONFIG",
     "TEACHER_BASE_OUT_SCALE",
     "teacher_base_weights",
     "teacher_weights",

@@ -76,6 +76,11 @@ class ModelConfig:
 # the absolute force tolerances (eV/A) a meaning for random weights.
 DEFAULT_CONFIG = ModelConfig(out_scale=16.873387265124986)
 STUDENT_CONFIG = ModelConfig(embed=(16, 32, 64), axis=8, attn_layers=0, fitting=(128, 128), out_scale=1.0)
+# The paper's own model size (Sec. IV-B: embedding net [32, 64, 128], three
+# gated attention layers of width 256, fitting net [256, 256, 256]); its output
+# scale is calibrated the same way (seed-0 weights).
+PAPER_SIZE_CONFIG = ModelConfig(embed=(32, 64, 128), attn_layers=3, attn_dim=256, fitting=(256, 256, 256),
+                                out_scale=8.82029019500646)
 
 
 def tensor_order(cfg: ModelConfig) -> List[Tuple[str, Tuple[int, ...]]]:

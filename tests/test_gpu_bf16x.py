@@ -5,8 +5,6 @@ the fitting net runs on tcgen05 with BF16 operands (both split in two
 terms) and FP32 accumulation.  The whole 15,668-atom box is compared in
 test_gpu_fullbox.py, the intermediates stage by stage in test_gpu_stages.py."""
 
-import dataclasses
-
 import numpy as np
 import pytest
 
@@ -109,12 +107,3 @@ def test_bf16x_without_attention(lib, water):
     assert frmse <= 1e-3
     m.close()
 
-
-def test_bf16x_refuses_paper_size(lib):
-    """Attention width 256 has no BF16-split core kernel: dp_init says so."""
-    cfg = dataclasses.replace(synth.DEFAULT_CONFIG, embed=(32, 64, 128), attn_layers=1, attn_dim=256,
-                              fitting=(256, 256, 256))
-    w = synth.make_weights(cfg, seed=0)
-    with pytest.raises(lib.DPError) as ei:
-        lib.DPA1(weight_file(cfg, w, "paper_l1"), precision="bf16x")
-    assert ei.value.code == -8
