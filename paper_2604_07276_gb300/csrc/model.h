@@ -53,8 +53,8 @@ struct TcWeights {
   };
   std::vector<Vectors> vectors;  // per attention layer, host copies passed as kernel parameters
   struct EmbVectors {
-    float W0[25] = {}, b0[25] = {}, b1[50] = {}, b2[100] = {};
-  } emb_vec;  // embedding net's 1 -> 25 layer and biases
+    float W0[32] = {}, b0[32] = {}, b1[64] = {}, b2[128] = {};
+  } emb_vec;  // the tensor-core embedding net's 1 -> E0 layer and biases
 };
 
 // BF16 two-term-split image of one GEMM operand B [K][N] (bf16x.cu).

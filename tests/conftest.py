@@ -50,6 +50,18 @@ def concat_model():
 
 
 @pytest.fixture(scope="session")
+def paper_size_model():
+    """The paper's model size (Sec. IV-B) with non-zero biases, perturbed
+    LayerNorm and davg/dstd."""
+    import synth
+    from oracle import OracleModel
+
+    cfg = synth.PAPER_SIZE_CONFIG
+    w = synth.make_weights(cfg, seed=17, bias_scale=0.05, ln_scale=0.1, stats=True)
+    return cfg, w, OracleModel.from_numpy(cfg, w)
+
+
+@pytest.fixture(scope="session")
 def water():
     import synth
 

@@ -76,6 +76,23 @@ def test_paper_size_bf16x(paper_model, paper_model_rich, water, ragged, weights)
         m.close()
 
 
+def test_paper_size_bf16x_concat(water):
+    """The concat type-embedding form (the embedding net reads [s, T_j, T_i])
+    at the paper's size, on the tensor-core embedding net."""
+    import dataclasses
+
+    import paper_2604_07276_gb300 as p
+
+    cfg = dataclasses.replace(PAPER_SIZE, tebd_input_mode="concat")
+    w = synth.make_weights(cfg, seed=19, bias_scale=0.05)
+    om = OracleModel.from_numpy(cfg, w)
+    m = p.DPA1(weight_file(cfg, w, "paper_size_concat"), precision="bf16x")
+    try:
+        _check(m, om, water, BF16_FORCE_RMSE, BF16_ATOM_ENERGY, 1e-3)
+    finally:
+        m.close()
+
+
 def test_paper_size_bf16x_deterministic(paper_model, ragged):
     import paper_2604_07276_gb300 as p
 
