@@ -244,9 +244,6 @@ int alloc_workspace(dp_model* m, int cap) {
   cap_dim = std::max(3, std::min(cap_dim, 1024));
   ws.cap_dim = cap_dim;
   ws.cell_cap = cap_dim * cap_dim * cap_dim;
-  int dev_sm = 0;
-  cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, m->device);
-  ws.attn_scratch_blocks = std::max(1, dev_sm);
   auto plan = [&](Arena& a) {
     ws.grid = a.take<CellGrid>(1);
     ws.cell_of = a.take<int>(cap);
@@ -272,8 +269,8 @@ int alloc_workspace(dp_model* m, int cap) {
     for (int l = 0; l <= L; ++l) ws.G[l] = a.take<float>(rows * m1);
     ws.QKV.assign(L, nullptr); ws.O.assign(L, nullptr); ws.Y.assign(L, nullptr); ws.stats.assign(L, nullptr);
     if (!fused_tc_precision(m->precision)) {
-      // bf16x keeps Q | K only (V enters through [Wv Wo; bv Wo])
-      const size_t nqkv = (m->precision == DP_PREC_BF16X ? 2 : 3) * (size_t)A;
+      // Q | K only (V enters through [Wv Wo; bv Wo])
+      const size_t nqkv = 2 * (size_t)A;
       for (int l = 0; l < L; ++l) {
         ws.QKV[l] = a.take<float>(rows * nqkv);
         ws.O[l] = a.take<float>(rows * pg_ld(m1));  // [P G, rowsum(P)]
@@ -281,11 +278,9 @@ int alloc_workspace(dp_model* m, int cap) {
         ws.stats[l] = a.take<float>(rows * 2);
       }
       ws.dY = a.take<float>(rows * m1);
-      // dO, or in bf16x dE/d[P G, rowsum P]
-      ws.dO = a.take<float>(rows * (L > 0 ? std::max(A, pg_ld(m1)) : 1));
+      // dE/d[P G, rowsum P]
+      ws.dO = a.take<float>(rows * (L > 0 ? pg_ld(m1) : 1));
       ws.dQKV = a.take<float>(rows * (L > 0 ? nqkv : 1));
-      if (m->precision == DP_PREC_FP32)  // dS^T, P^T, dP per block of the FP32 adjoint
-        ws.attn_scratch = a.take<float>((size_t)ws.attn_scratch_blocks * 3 * NP * NP);
     }
     ws.dG = a.take<float>(rows * m1);
     ws.T = a.take<float>((size_t)cap * 4 * m1);
@@ -484,10 +479,12 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   // a6: attention layers
   for (int l = 0; l < L; ++l) {
     const AttnLayerW& w = m->attn[l];
-    gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 3 * A, rows, 3 * A, m1, EPI_BIAS, st);
+    // [Q K] = G [Wq Wk] + [bq bk] (V only enters through [Wv Wo; bv Wo])
+    gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 2 * A, rows, 2 * A, m1, EPI_BIAS, st);
     prof_mark(m, "qkv_gemm", st);
     AttnArgs aa{};
-    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
+    aa.QK = ws.QKV[l]; aa.ldq = 2 * A; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A;
+    aa.shift = (float)m->shift;
     aa.G = ws.G[l]; aa.m1 = m1; aa.ldpg = pg_ld(m1); aa.PG = ws.O[l];
     launch_attn_fwd_f32(aa, st);
     prof_mark(m, "attn_fwd", st);
@@ -503,15 +500,17 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   for (int l = L - 1; l >= 0; --l) {
     const AttnLayerW& w = m->attn[l];
     launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
-    gemm_f32(ws.dY, m1, w.WoT, A, nullptr, nullptr, 0, ws.dO, A, rows, A, m1, EPI_BIAS, st);
+    // dE/d[P G, rowsum P] = dY [Wv Wo; bv Wo]^T
+    gemm_f32(ws.dY, m1, w.WvoT, pg_ld(m1), nullptr, nullptr, 0, ws.dO, pg_ld(m1), rows, pg_ld(m1), m1, EPI_BIAS, st);
     prof_mark(m, "ln_wo_bwd", st);
     AttnArgs aa{};
-    aa.QKV = ws.QKV[l]; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A; aa.shift = (float)m->shift;
-    aa.dO = ws.dO; aa.dQKV = ws.dQKV; aa.dgeo = ws.dgeo; aa.scratch = ws.attn_scratch;
-    aa.scratch_blocks = ws.attn_scratch_blocks;
-    launch_attn_bwd_f32(aa, st);
+    aa.QK = ws.QKV[l]; aa.ldq = 2 * A; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A;
+    aa.shift = (float)m->shift; aa.G = ws.G[l]; aa.m1 = m1; aa.ldpg = pg_ld(m1);
+    aa.dPG = ws.dO; aa.dQK = ws.dQKV; aa.dG = ws.dG; aa.dgeo = ws.dgeo;
+    launch_attn_bwd_f32(aa, st);  // dQ, dK; dE/dG += P^T dPG
     prof_mark(m, "attn_bwd", st);
-    gemm_f32(ws.dQKV, 3 * A, w.WqkvT, m1, nullptr, nullptr, 0, ws.dG, m1, rows, m1, 3 * A, EPI_ACCUM, st);
+    // dE/dG += [dQ dK] [Wq Wk]^T (the first 2A rows of Wqkv^T)
+    gemm_f32(ws.dQKV, 2 * A, w.WqkvT, m1, nullptr, nullptr, 0, ws.dG, m1, rows, m1, 2 * A, EPI_ACCUM, st);
     prof_mark(m, "qkv_bwd_gemm", st);
   }
   // a13: embedding backward -> dR[:,0]
@@ -864,8 +863,6 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
     if ((rc = dev_upload(m, &L.Wqkv, to_f(Wqkv))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.WqkvT, transpose_f(Wqkv, m1, 3 * A))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.bqkv, to_f(bqkv))) != DP_OK) return fail_free(rc);
-    if ((rc = dev_upload(m, &L.Wo, to_f(*w.get(p + "Wo")))) != DP_OK) return fail_free(rc);
-    if ((rc = dev_upload(m, &L.WoT, transpose_f(*w.get(p + "Wo"), A, m1))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.bo, to_f(*w.get(p + "bo")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_g, to_f(*w.get(p + "ln_g")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_b, to_f(*w.get(p + "ln_b")))) != DP_OK) return fail_free(rc);

@@ -130,20 +130,19 @@ void launch_ln_bwd(const float* dZ, const float* Y, const float* stats, const in
                    float* dY, int rows, int m1, cudaStream_t st);
 
 struct AttnArgs {
-  const float* QKV;  // [rows][3A]
+  const float* QK;   // [rows][ldq]: Q | K (A columns each)
   const float* rw;   // [rows][4]
   const double* w64; // [rows] switch weights in FP64
   const int* nnei;
-  int n, A;
+  int n, A, ldq;
   float shift;
-  const float* G;    // fwd: [rows][m1] layer input
-  int m1, ldpg;      // fwd: width of G, row stride of PG (pg_ld(m1))
+  const float* G;    // [rows][m1] layer input
+  int m1, ldpg;      // width of G, row stride of PG and dPG (pg_ld(m1))
   float* PG;         // fwd: [rows][ldpg] = [P G, rowsum(P), 0 ...]
-  const float* dO;   // bwd: [rows][A]
-  float* dQKV;       // bwd: [rows][3A]
+  const float* dPG;  // bwd: [rows][ldpg] dE/d[P G, rowsum P]
+  float* dQK;        // bwd: [rows][ldq] dQ | dK
+  float* dG;         // bwd: [rows][m1] += P^T dE/d(P G)
   float* dgeo;       // bwd: [rows][4] +=
-  float* scratch;    // bwd: per resident block 2 * NP * NP floats
-  int scratch_blocks;
 };
 void launch_attn_fwd_f32(const AttnArgs& a, cudaStream_t st);
 void launch_attn_bwd_f32(const AttnArgs& a, cudaStream_t st);

@@ -27,10 +27,10 @@ struct Arena {
 
 
 struct AttnLayerW {
-  float *Wqkv, *bqkv, *WqkvT, *Wo, *bo, *WoT, *ln_g, *ln_b;
-  // FP32 path: [Wv Wo; bv Wo; 0...] ([pg_ld(m1)][m1]), formed in FP64, so that
+  float *Wqkv, *bqkv, *WqkvT, *bo, *ln_g, *ln_b;
+  // [Wv Wo; bv Wo; 0...] ([pg_ld(m1)][m1]), formed in FP64, so that
   // Y = O Wo + bo = [P G, rowsum(P)] Wvo + bo (see launch_attn_fwd_f32); and
-  // its transpose [m1][pg_ld(m1)] (the bf16x adjoint)
+  // its transpose [m1][pg_ld(m1)] (the adjoints of the FP32 and bf16x paths)
   float* Wvo;
   float* WvoT;
 };
@@ -102,8 +102,6 @@ struct Workspace {
   float *T, *X, *dX, *e;
   std::vector<float*> H;
   float *dHa, *dHb, *dZ;
-  float* attn_scratch;
-  int attn_scratch_blocks;
   double* partials;
   // host-API staging
   double *coord, *box, *force, *virial, *energy, *atom_energy;

@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
   float4* rws = reinterpret_cast<float4*>(Y + 128 * TLD);  // [NP]
   float2* w2s = reinterpret_cast<float2*>(rws + NP);       // [NP] switch weights as float pairs
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int ld = 3 * A;
+  const int ld = a.ldq;  // Q | K
   for (int atom = blockIdx.x; atom < a.n; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
@@ -622,8 +622,8 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
         const int j = idx & (NP - 1), f = 4 * (idx >> 7);
         float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
         if (j < nn) {
-          qv = *reinterpret_cast<const float4*>(a.QKV + (base + j) * ld + c0 + f);
-          kv = *reinterpret_cast<const float4*>(a.QKV + (base + j) * ld + A + c0 + f);
+          qv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + c0 + f);
+          kv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + A + c0 + f);
         }
         X[(f + 0) * TLD + j] = qv.x; X[(f + 1) * TLD + j] = qv.y;
         X[(f + 2) * TLD + j] = qv.z; X[(f + 3) * TLD + j] = qv.w;
@@ -743,336 +743,317 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
   }
 }
 
-// Adjoint of one attention layer for one centre.  Pass 1 (a warp per RB rows
-// j) recomputes l, A and P, forms dP = dO_j . V_k (at width 256 in a pass 0
-// with V in shared memory, into the scratch slot), the softmax adjoint and
-// dQ_j, and the row / column parts of dE/dw and dE/drhat.  Pass 2 (a warp per
-// RB keys k) forms dK_k = sum_j dS_jk Q_j and dV_k = sum_j P_jk dO_j from dS
-// and P that pass 1 left (transposed) in this block's global scratch slot.
-// Every K, V, Q and dO element a warp loads serves its RB rows or keys; 16
-// warps per block (8 at width 256, for shared memory).
+// Adjoint of one attention layer for one centre, register-tiled like the
+// forward (256 threads as a 16 x 16 grid; thread (ty, tx) owns rows 8 ty ..
+// 8 ty + 7 and keys or columns 8 tx .. 8 tx + 7 of each 128 x 128 product),
+// in the form of the forward's output Y = [P G, rowsum P] [Wv Wo; bv Wo] +
+// bo: with dPG = dE/d[P G, rowsum P] (a GEMM of dY with [Wv Wo; bv Wo]^T),
+//   dP_jk = sum_c dPG_jc G_kc + dPG_j,m1        (the values V never appear)
+//   softmax adjoint: dS, and the row / column parts of dE/dw and dE/drhat
+//   dQ = dS K,  dK = dS^T Q,  dE/dG += P^T dPG (columns below m1).
+// S and dP stay in registers through the softmax adjoint; dS and P then go to
+// shared memory (row-major), where the three last products read them.  The
+// column parts are summed over the 16 row groups in a fixed order.
 template <int A>
-__host__ __device__ constexpr int bwd_warps() { return A > 128 ? 8 : 16; }
-
-template <int A>
-__global__ void __launch_bounds__(32 * bwd_warps<A>(), 1) k_attn_bwd_f32(AttnArgs a, float scale) {
-  constexpr bool VG = A > 128;  // V and dO from global memory, as in the forward
-  constexpr int AW = bwd_warps<A>(), RB = 2;
+__global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
   extern __shared__ float sm[];
-  constexpr int KS = A + 4;                         // row stride: 16-byte rows for 128-bit loads
-  float* Ks = sm;                                   // [NP][KS]   pass 0: V, pass 2: Q
-  float* Vs = Ks + NP * KS;                         // [NP][KS]   pass 2: dO (not with VG)
-  float4* rws = reinterpret_cast<float4*>(Vs + (VG ? 0 : NP * KS));  // [NP]
-  float4* rowg = rws + NP;                          // [NP] (d rhat_j, d w_j) row parts
-  float* qrow = reinterpret_cast<float*>(rowg + NP);  // [AW][RB][A]
-  float* dorow = qrow + AW * RB * A;                // [AW][RB][A]
-  float* prow = dorow + AW * RB * A;                // [AW][RB][NP]
-  float* colw = prow + AW * RB * NP;                // [AW][NP]
-  float* colr = colw + AW * NP;                     // [AW][NP][3]
-  float2* w2s = reinterpret_cast<float2*>(colr + 3 * AW * NP);  // [NP] switch weights as float pairs
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int FQ = A / 32;
-  const int ld = 3 * A;
-  float* dST = a.scratch + (size_t)blockIdx.x * 3 * NP * NP;  // [NP k][NP j]
-  float* PT = dST + NP * NP;
-  float* dPs = PT + NP * NP;  // VG: [NP j][NP k] dP = dO V^T from pass 0
+  float* B0 = sm;               // [128][TLD] operand chunks
+  float* B1 = B0 + 128 * TLD;   // [128][TLD] K / G chunk, then dS (row-major)
+  float* B2 = B1 + 128 * TLD;   // [128][TLD] P (row-major)
+  float4* rws = reinterpret_cast<float4*>(B2 + 128 * TLD);  // [NP]
+  float2* w2s = reinterpret_cast<float2*>(rws + NP);         // [NP] switch weights as float pairs
+  float4* rowg = reinterpret_cast<float4*>(w2s + NP);        // [NP] row parts of (d rhat, d w)
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int ld = a.ldq;  // Q | K, and dQ | dK
   for (int atom = blockIdx.x; atom < a.n; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
-    if (VG) {
-      // pass 0: V into Ks, dP_jk = dO_j . V_k for every live row
-      for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
-        const int r = idx / A, f = idx % A;
-        Ks[r * KS + f] = a.QKV[(base + r) * ld + 2 * A + f];
-      }
-      __syncthreads();
-      for (int j0 = warp * RB; j0 < nn; j0 += AW * RB) {
-        float* dq = dorow + warp * RB * A;
-        for (int t = lane; t < RB * A; t += 32) {
-          const int r = t / A, f = t % A;
-          dq[t] = j0 + r < nn ? a.dO[(base + j0 + r) * A + f] : 0.f;
-        }
-        __syncwarp();
-        float d[RB][4];
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-#pragma unroll
-          for (int m = 0; m < 4; ++m) d[r][m] = 0.f;
-        for (int f = 0; f < A; f += 4) {
-          float4 vf[4];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) vf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
-#pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            const float4 gf = *reinterpret_cast<const float4*>(dq + r * A + f);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              d[r][m] = fmaf(gf.x, vf[m].x, d[r][m]);
-              d[r][m] = fmaf(gf.y, vf[m].y, d[r][m]);
-              d[r][m] = fmaf(gf.z, vf[m].z, d[r][m]);
-              d[r][m] = fmaf(gf.w, vf[m].w, d[r][m]);
-            }
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-          if (j0 + r < nn)
-#pragma unroll
-            for (int m = 0; m < 4; ++m) dPs[(size_t)(j0 + r) * NP + lane + 32 * m] = d[r][m];
-        __syncwarp();
-      }
-      __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
-      const int r = idx / A, f = idx % A;
-      Ks[r * KS + f] = a.QKV[(base + r) * ld + A + f];
-      if (!VG) Vs[r * KS + f] = a.QKV[(base + r) * ld + 2 * A + f];
-    }
-    for (int r = threadIdx.x; r < NP; r += blockDim.x) {
+    __syncthreads();  // the previous atom is done with every shared array
+    for (int r = tid; r < NP; r += FT) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
       w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
-    for (int t = threadIdx.x; t < AW * NP; t += blockDim.x) {
-      colw[t] = 0.f;
-      colr[3 * t] = 0.f; colr[3 * t + 1] = 0.f; colr[3 * t + 2] = 0.f;
+    const bool live = 8 * ty < nn && 8 * tx < nn;
+    float s[8][8], dp[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) { s[i][jj] = 0.f; dp[i][jj] = 0.f; }
+    // S = Q K^T over feature chunks of 128 (feature-major in B0, B1)
+    for (int c0 = 0; c0 < A; c0 += 128) {
+      if (c0 > 0) __syncthreads();
+      for (int idx = tid; idx < NP * 32; idx += FT) {
+        const int j = idx & (NP - 1), f = 4 * (idx >> 7);
+        float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
+        if (j < nn) {
+          qv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + c0 + f);
+          kv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + A + c0 + f);
+        }
+        B0[(f + 0) * TLD + j] = qv.x; B0[(f + 1) * TLD + j] = qv.y;
+        B0[(f + 2) * TLD + j] = qv.z; B0[(f + 3) * TLD + j] = qv.w;
+        B1[(f + 0) * TLD + j] = kv.x; B1[(f + 1) * TLD + j] = kv.y;
+        B1[(f + 2) * TLD + j] = kv.z; B1[(f + 3) * TLD + j] = kv.w;
+      }
+      __syncthreads();
+      if (live) {
+        for (int f = 0; f < 128; ++f) {
+          const float4 a0 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty);
+          const float4 a1 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty + 4);
+          const float4 b0 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx);
+          const float4 b1 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx + 4);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) s[i][jj] = fmaf(av[i], bv[jj], s[i][jj]);
+        }
+      }
     }
     __syncthreads();
-    for (int j0 = warp * RB; j0 < nn; j0 += AW * RB) {
-      float* q = qrow + warp * RB * A;
-      float* dq = dorow + warp * RB * A;
-      for (int t = lane; t < RB * A; t += 32) {
-        const int r = t / A, f = t % A;
-        const bool live = j0 + r < nn;
-        q[t] = live ? a.QKV[(base + j0 + r) * ld + f] : 0.f;
-        if (!VG) dq[t] = live ? a.dO[(base + j0 + r) * A + f] : 0.f;
+    // dP = dPG G^T over the m1 columns (feature-major: dPG in B0, G in B1;
+    // m1 % 4 == 0)
+    for (int idx = tid; idx < NP * 32; idx += FT) {
+      const int j = idx & (NP - 1), f = 4 * (idx >> 7);
+      float4 dv = make_float4(0.f, 0.f, 0.f, 0.f), gv = dv;
+      if (j < nn && f < a.m1) {
+        dv = *reinterpret_cast<const float4*>(a.dPG + (base + j) * a.ldpg + f);
+        gv = *reinterpret_cast<const float4*>(a.G + (base + j) * a.m1 + f);
       }
-      __syncwarp();
-      float s[RB][4], dp[RB][4];
+      B0[(f + 0) * TLD + j] = dv.x; B0[(f + 1) * TLD + j] = dv.y;
+      B0[(f + 2) * TLD + j] = dv.z; B0[(f + 3) * TLD + j] = dv.w;
+      B1[(f + 0) * TLD + j] = gv.x; B1[(f + 1) * TLD + j] = gv.y;
+      B1[(f + 2) * TLD + j] = gv.z; B1[(f + 3) * TLD + j] = gv.w;
+    }
+    __syncthreads();
+    if (live) {
+      for (int f = 0; f < a.m1; ++f) {
+        const float4 a0 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty);
+        const float4 a1 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx);
+        const float4 b1 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx + 4);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int r = 0; r < RB; ++r)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) { s[r][m] = 0.f; dp[r][m] = 0.f; }
-      if (VG) {
-        for (int f = 0; f < A; f += 4) {
-          float4 kf[4];
+          for (int jj = 0; jj < 8; ++jj) dp[i][jj] = fmaf(av[i], bv[jj], dp[i][jj]);
+      }
+    }
+    __syncthreads();  // B0 and B1 are free: dS goes to B1, P to B2, column parts to B0
+    // softmax adjoint per row over the 16 threads of a half warp (every lane
+    // takes part in the shuffles; rows and keys past nnei come out zero)
+    float cw[8], cx[8], cy[8], cz[8];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) kf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
+    for (int jj = 0; jj < 8; ++jj) { cw[jj] = 0.f; cx[jj] = 0.f; cy[jj] = 0.f; cz[jj] = 0.f; }
 #pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            const float4 qf = *reinterpret_cast<const float4*>(q + r * A + f);
+    for (int i = 0; i < 8; ++i) {
+      const int j = 8 * ty + i;
+      const float4 rj = rws[j];
+      const float2 wj = w2s[j];
+      const float dpg1 = j < nn ? a.dPG[(base + j) * a.ldpg + a.m1] : 0.f;  // adjoint of rowsum P
+      float2 lp[8], mx = make_float2(-3.0e38f, 0.f);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              s[r][m] = fmaf(qf.x, kf[m].x, s[r][m]);
-              s[r][m] = fmaf(qf.y, kf[m].y, s[r][m]);
-              s[r][m] = fmaf(qf.z, kf[m].z, s[r][m]);
-              s[r][m] = fmaf(qf.w, kf[m].w, s[r][m]);
-            }
-          }
-        }
-        // dp from pass 0 (the scratch rows of this block, written by this
-        // block before the barrier)
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-          if (j0 + r < nn)
-#pragma unroll
-            for (int m = 0; m < 4; ++m) dp[r][m] = dPs[(size_t)(j0 + r) * NP + lane + 32 * m];
-      } else {
-        for (int f = 0; f < A; f += 4) {
-          float4 kf[4], vf[4];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            kf[m] = *reinterpret_cast<const float4*>(Ks + (lane + 32 * m) * KS + f);
-            vf[m] = *reinterpret_cast<const float4*>(Vs + (lane + 32 * m) * KS + f);
-          }
-#pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            const float4 qf = *reinterpret_cast<const float4*>(q + r * A + f);
-            const float4 gf = *reinterpret_cast<const float4*>(dq + r * A + f);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              s[r][m] = fmaf(qf.x, kf[m].x, s[r][m]);
-              s[r][m] = fmaf(qf.y, kf[m].y, s[r][m]);
-              s[r][m] = fmaf(qf.z, kf[m].z, s[r][m]);
-              s[r][m] = fmaf(qf.w, kf[m].w, s[r][m]);
-              dp[r][m] = fmaf(gf.x, vf[m].x, dp[r][m]);
-              dp[r][m] = fmaf(gf.y, vf[m].y, dp[r][m]);
-              dp[r][m] = fmaf(gf.z, vf[m].z, dp[r][m]);
-              dp[r][m] = fmaf(gf.w, vf[m].w, dp[r][m]);
-            }
-          }
+      for (int jj = 0; jj < 8; ++jj) {
+        const int k = 8 * tx + jj;
+        lp[jj] = make_float2(-3.0e38f, 0.f);
+        if (k < nn) {
+          lp[jj] = smooth_logit(s[i][jj] * scale, a.shift, wj, w2s[k]);  // as in the forward kernel
+          if (lp[jj].x > mx.x || (lp[jj].x == mx.x && lp[jj].y > mx.y)) mx = lp[jj];
         }
       }
-      float* pr = prow + warp * RB * NP;
 #pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int j = j0 + r;
-        if (j >= nn) {  // uniform over the warp
+      for (int o = 8; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, mx.x, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, mx.y, o);
+        if (oh > mx.x || (oh == mx.x && ol > mx.y)) mx = make_float2(oh, ol);
+      }
+      float e[8], sum = 0.f;
 #pragma unroll
-          for (int m = 0; m < 4; ++m) pr[r * NP + lane + 32 * m] = 0.f;
-          continue;
-        }
-        const float4 rj = rws[j];
-        const float2 wj = w2s[j];
-        float l[4], ww[4], c[4];
-        float2 lp[4], mx = make_float2(-3.0e38f, 0.f);
+      for (int jj = 0; jj < 8; ++jj) {
+        e[jj] = 8 * tx + jj < nn ? expf(pair_diff(lp[jj], mx)) : 0.f;
+        sum += e[jj];
+      }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = lane + 32 * m;
+      for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      const float inv = sum > 0.f ? 1.0f / sum : 0.f;
+      float At[8], dA[8], tsum = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int k = 8 * tx + jj;
+        const float4 rk = rws[k];
+        At[jj] = e[jj] * inv;
+        dA[jj] = k < nn ? (dp[i][jj] + dpg1) * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z) : 0.f;
+        tsum += At[jj] * dA[jj];
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+      float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f, ds[8], pv[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int k = 8 * tx + jj;
+        ds[jj] = 0.f;
+        pv[jj] = 0.f;
+        if (j < nn && k < nn) {
           const float4 rk = rws[k];
-          ww[m] = rj.w * rk.w;
-          c[m] = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
-          l[m] = s[r][m] * scale;
-          lp[m] = make_float2(-3.0e38f, 0.f);
-          if (k < nn) {
-            lp[m] = smooth_logit(l[m], a.shift, wj, w2s[k]);  // as in the forward kernel
-            if (lp[m].x > mx.x || (lp[m].x == mx.x && lp[m].y > mx.y)) mx = lp[m];
-          }
-        }
-        mx = warp_max_pair(mx);
-        float e[4], sum = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          e[m] = (lane + 32 * m) < nn ? expf(pair_diff(lp[m], mx)) : 0.f;
-          sum += e[m];
-        }
-        sum = warp_sum(sum);
-        const float inv = 1.0f / sum;
-        float At[4], dA[4], tsum = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          At[m] = e[m] * inv;
-          dA[m] = (lane + 32 * m) < nn ? dp[r][m] * ww[m] * c[m] : 0.f;
-          tsum += At[m] * dA[m];
-        }
-        tsum = warp_sum(tsum);
-        float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int k = lane + 32 * m;
-          float dS = 0.f;
-          if (k < nn) {
-            const float dLp = At[m] * (dA[m] - tsum);
-            dS = dLp * ww[m] * scale;
-            const float H = dp[r][m] * At[m] * c[m] + dLp * (l[m] + a.shift);
-            const float dc = dp[r][m] * At[m] * ww[m];
-            const float4 rk = rws[k];
-            rw_ += H * rk.w;
-            rx += dc * rk.x; ry += dc * rk.y; rz += dc * rk.z;
-            colw[warp * NP + k] += H * rj.w;
-            colr[(warp * NP + k) * 3 + 0] += dc * rj.x;
-            colr[(warp * NP + k) * 3 + 1] += dc * rj.y;
-            colr[(warp * NP + k) * 3 + 2] += dc * rj.z;
-            dST[(size_t)k * NP + j] = dS;
-            PT[(size_t)k * NP + j] = At[m] * ww[m] * c[m];
-          }
-          pr[r * NP + k] = dS;
-        }
-        rw_ = warp_sum(rw_); rx = warp_sum(rx); ry = warp_sum(ry); rz = warp_sum(rz);
-        if (lane == 0) rowg[j] = make_float4(rx, ry, rz, rw_);
-      }
-      __syncwarp();
-      float acc[RB][FQ];
-#pragma unroll
-      for (int r = 0; r < RB; ++r)
-#pragma unroll
-        for (int m = 0; m < FQ; ++m) acc[r][m] = 0.f;
-      for (int k = 0; k < nn; ++k) {
-        float kk[FQ];
-#pragma unroll
-        for (int m = 0; m < FQ; ++m) kk[m] = Ks[k * KS + lane + 32 * m];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          const float d = pr[r * NP + k];
-#pragma unroll
-          for (int m = 0; m < FQ; ++m) acc[r][m] = fmaf(d, kk[m], acc[r][m]);
+          const float ww = rj.w * rk.w;
+          const float c = rj.x * rk.x + rj.y * rk.y + rj.z * rk.z;
+          const float dpv = dp[i][jj] + dpg1;
+          const float dLp = At[jj] * (dA[jj] - tsum);
+          ds[jj] = dLp * ww * scale;
+          pv[jj] = At[jj] * ww * c;
+          const float H = dpv * At[jj] * c + dLp * (s[i][jj] * scale + a.shift);  // dE/d(w_j w_k)
+          const float dc = dpv * At[jj] * ww;                                      // dE/dc_jk
+          rw_ += H * rk.w;
+          rx += dc * rk.x; ry += dc * rk.y; rz += dc * rk.z;
+          cw[jj] += H * rj.w;
+          cx[jj] += dc * rj.x; cy[jj] += dc * rj.y; cz[jj] += dc * rj.z;
         }
       }
+      *reinterpret_cast<float4*>(B1 + j * TLD + 8 * tx) = make_float4(ds[0], ds[1], ds[2], ds[3]);
+      *reinterpret_cast<float4*>(B1 + j * TLD + 8 * tx + 4) = make_float4(ds[4], ds[5], ds[6], ds[7]);
+      *reinterpret_cast<float4*>(B2 + j * TLD + 8 * tx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      *reinterpret_cast<float4*>(B2 + j * TLD + 8 * tx + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
 #pragma unroll
-      for (int r = 0; r < RB; ++r)
-        if (j0 + r < nn)
-#pragma unroll
-          for (int m = 0; m < FQ; ++m) a.dQKV[(base + j0 + r) * ld + lane + 32 * m] = acc[r][m];
-      __syncwarp();
+      for (int o = 8; o > 0; o >>= 1) {
+        rw_ += __shfl_xor_sync(0xffffffffu, rw_, o);
+        rx += __shfl_xor_sync(0xffffffffu, rx, o);
+        ry += __shfl_xor_sync(0xffffffffu, ry, o);
+        rz += __shfl_xor_sync(0xffffffffu, rz, o);
+      }
+      if (tx == 0) rowg[j] = make_float4(rx, ry, rz, rw_);
     }
+    // column parts of this thread's 8 rows -> B0 as [ty][key]
+    float4* colp = reinterpret_cast<float4*>(B0);
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) colp[ty * NP + 8 * tx + jj] = make_float4(cx[jj], cy[jj], cz[jj], cw[jj]);
     __syncthreads();
-    // pass 2: Q into Ks, dO into Vs (dO from global memory with VG)
-    for (int idx = threadIdx.x; idx < nn * A; idx += blockDim.x) {
-      const int r = idx / A, f = idx % A;
-      Ks[r * KS + f] = a.QKV[(base + r) * ld + f];
-      if (!VG) Vs[r * KS + f] = a.dO[(base + r) * A + f];
-    }
-    __syncthreads();
-    for (int k0 = warp * RB; k0 < NP; k0 += AW * RB) {
-      if (k0 >= nn) {
-        for (int t = lane; t < RB * ld; t += 32) a.dQKV[(base + k0) * ld + t] = 0.f;
-        continue;
+    if (tid < nn) {
+      float4 acc = rowg[tid];
+      for (int q = 0; q < 16; ++q) {
+        const float4 c = colp[q * NP + tid];
+        acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
       }
-      float dK[RB][FQ], dV[RB][FQ];
+      float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
+      float4 cur = *dg;
+      cur.x += acc.x; cur.y += acc.y; cur.z += acc.z; cur.w += acc.w;
+      *dg = cur;
+    }
+    const int nn4 = (nn + 3) & ~3;
+    for (int c0 = 0; c0 < A; c0 += 128) {
+      // dQ = dS K: K key-major in B0
+      __syncthreads();
+      for (int idx = tid; idx < NP * 32; idx += FT) {
+        const int k = idx >> 5, f = 4 * (idx & 31);
+        *reinterpret_cast<float4*>(B0 + k * TLD + f) =
+            k < nn ? *reinterpret_cast<const float4*>(a.QK + (base + k) * ld + A + c0 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncthreads();
+      float acc[8][8];
 #pragma unroll
-      for (int r = 0; r < RB; ++r)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int m = 0; m < FQ; ++m) { dK[r][m] = 0.f; dV[r][m] = 0.f; }
-      for (int jb = 0; jb < nn; jb += 32) {
-        const int jj = jb + lane;
-        float dsv[RB], pv[RB];
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
+      if (8 * ty < nn) {
+        for (int k = 0; k < nn4; k += 4) {
+          float4 da[8];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          const bool live = jj < nn && k0 + r < nn;
-          dsv[r] = live ? dST[(size_t)(k0 + r) * NP + jj] : 0.f;
-          pv[r] = live ? PT[(size_t)(k0 + r) * NP + jj] : 0.f;
-        }
-        const int cnt = (nn - jb) < 32 ? (nn - jb) : 32;
-        for (int t = 0; t < cnt; ++t) {
-          const int j = jb + t;
-          const float* doj = VG ? a.dO + (base + j) * A : Vs + j * KS;
-          float qv[FQ], dv[FQ];
+          for (int i = 0; i < 8; ++i) da[i] = *reinterpret_cast<const float4*>(B1 + (8 * ty + i) * TLD + k);
 #pragma unroll
-          for (int m = 0; m < FQ; ++m) {
-            qv[m] = Ks[j * KS + lane + 32 * m];
-            dv[m] = doj[lane + 32 * m];
-          }
+          for (int u = 0; u < 4; ++u) {
+            const float4 v0 = *reinterpret_cast<const float4*>(B0 + (k + u) * TLD + 8 * tx);
+            const float4 v1 = *reinterpret_cast<const float4*>(B0 + (k + u) * TLD + 8 * tx + 4);
+            const float vb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            const float d = __shfl_sync(0xffffffffu, dsv[r], t);
-            const float p = __shfl_sync(0xffffffffu, pv[r], t);
+            for (int i = 0; i < 8; ++i) {
+              const float d = u == 0 ? da[i].x : u == 1 ? da[i].y : u == 2 ? da[i].z : da[i].w;
 #pragma unroll
-            for (int m = 0; m < FQ; ++m) {
-              dK[r][m] = fmaf(d, qv[m], dK[r][m]);
-              dV[r][m] = fmaf(p, dv[m], dV[r][m]);
+              for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(d, vb[jj], acc[i][jj]);
             }
           }
         }
       }
 #pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int k = k0 + r;
-        float* dqk = a.dQKV + (base + k) * ld;
-        if (k >= nn) {
-          for (int f = lane; f < ld; f += 32) dqk[f] = 0.f;
-          continue;
-        }
+      for (int i = 0; i < 8; ++i) {
+        float* o = a.dQK + (base + 8 * ty + i) * ld + c0 + 8 * tx;
+        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      }
+      // dK = dS^T Q: Q row-major in B0
+      __syncthreads();
+      for (int idx = tid; idx < NP * 32; idx += FT) {
+        const int j = idx >> 5, f = 4 * (idx & 31);
+        *reinterpret_cast<float4*>(B0 + j * TLD + f) =
+            j < nn ? *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + c0 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncthreads();
 #pragma unroll
-        for (int m = 0; m < FQ; ++m) {
-          dqk[A + lane + 32 * m] = dK[r][m];
-          dqk[2 * A + lane + 32 * m] = dV[r][m];
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
+      if (8 * ty < nn) {
+        for (int j = 0; j < nn; ++j) {
+          const float4 d0 = *reinterpret_cast<const float4*>(B1 + j * TLD + 8 * ty);
+          const float4 d1 = *reinterpret_cast<const float4*>(B1 + j * TLD + 8 * ty + 4);
+          const float4 q0 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx);
+          const float4 q1 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx + 4);
+          const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+          const float qv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(dv[i], qv[jj], acc[i][jj]);
         }
-        if (lane == 0) {
-          float cw = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-          for (int w = 0; w < AW; ++w) {
-            cw += colw[w * NP + k];
-            cx += colr[(w * NP + k) * 3 + 0];
-            cy += colr[(w * NP + k) * 3 + 1];
-            cz += colr[(w * NP + k) * 3 + 2];
-          }
-          const float4 rg = rowg[k];
-          float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + k;
-          float4 cur = *dg;
-          cur.x += rg.x + cx; cur.y += rg.y + cy; cur.z += rg.z + cz; cur.w += rg.w + cw;
-          *dg = cur;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float* o = a.dQK + (base + 8 * ty + i) * ld + A + c0 + 8 * tx;
+        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      }
+    }
+    // dE/dG += P^T dPG: dPG row-major in B0 (columns below m1; m1 <= 128)
+    __syncthreads();
+    for (int idx = tid; idx < NP * 32; idx += FT) {
+      const int j = idx >> 5, f = 4 * (idx & 31);
+      *reinterpret_cast<float4*>(B0 + j * TLD + f) = j < nn && f < a.m1
+                                                         ? *reinterpret_cast<const float4*>(a.dPG + (base + j) * a.ldpg + f)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (8 * ty < nn && 8 * tx < a.m1) {
+      float acc[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
+      for (int j = 0; j < nn; ++j) {
+        const float4 p0 = *reinterpret_cast<const float4*>(B2 + j * TLD + 8 * ty);
+        const float4 p1 = *reinterpret_cast<const float4*>(B2 + j * TLD + 8 * ty + 4);
+        const float4 g0 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx);
+        const float4 g1 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx + 4);
+        const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(pv[i], gv[jj], acc[i][jj]);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = 8 * ty + i;
+        if (k >= nn) continue;
+        float4* dg = reinterpret_cast<float4*>(a.dG + (base + k) * a.m1 + 8 * tx);
+        float4 x = dg[0];
+        x.x += acc[i][0]; x.y += acc[i][1]; x.z += acc[i][2]; x.w += acc[i][3];
+        dg[0] = x;
+        if (8 * tx + 4 < a.m1) {
+          x = dg[1];
+          x.x += acc[i][4]; x.y += acc[i][5]; x.z += acc[i][6]; x.w += acc[i][7];
+          dg[1] = x;
         }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -1089,22 +1070,16 @@ static int sm_count() {
 
 template <int A>
 static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
-  constexpr bool VG = A > 128;
   const float scale = (float)(1.0 / sqrt((double)A));
-  // the adjoint's blocks each own a slot of the dS / P scratch
-  const int cap = bwd ? a.scratch_blocks : sm_count();
-  const int grid = a.n < cap ? a.n : cap;
+  const int grid = a.n < sm_count() ? a.n : sm_count();
   if (!bwd) {
     const size_t smem = sizeof(float) * (2 * 128 * TLD + 4 * NP) + sizeof(float2) * NP;
     cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_attn_fwd_f32<A><<<grid, FT, smem, st>>>(a, scale);
   } else {
-    constexpr int RB = 2, AW = bwd_warps<A>();  // rows / keys per warp, warps of the adjoint
-    const size_t smem = sizeof(float) * (NP * (A + 4) * (VG ? 1 : 2) + 8 * NP + 2 * AW * RB * A + AW * RB * NP +
-                                         4 * AW * NP) +
-                        sizeof(double) * NP;
+    const size_t smem = sizeof(float) * (3 * 128 * TLD + 8 * NP) + sizeof(float2) * NP;
     cudaFuncSetAttribute(k_attn_bwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_attn_bwd_f32<A><<<grid, 32 * AW, smem, st>>>(a, scale);
+    k_attn_bwd_f32<A><<<grid, FT, smem, st>>>(a, scale);
   }
   note_launch();
 }
