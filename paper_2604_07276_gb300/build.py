@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libdpa1.so")
-SOURCES = ["api.cu", "nbr.cu", "env.cu", "simt.cu", "tc.cu", "fit.cu", "bf16x.cu", "md.cu", "train.cu"]
+SOURCES = ["api.cu", "nbr.cu", "env.cu", "simt.cu", "tc.cu", "tc_embed.cu", "fit.cu", "bf16x.cu", "md.cu", "train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -51,7 +51,7 @@ namespace {
 
 // ------------------------------------------------------------------- GEMM
 // C = epi(A B + bias (+ R)), A [M][K] FP32 row-major, B [K][N] from a
-// pre-split image.  Persistent: CTA (x, y) keeps N block y (<= 192 columns)
+// pre-split image.  Persistent: CTA (x, y) keeps N block y (<= 144 columns)
 // and walks the 128-row tiles x, x + gridDim.x, ...; the K loop runs in
 // stages of 64 through a two-stage ring that continues across tiles, and
 // the accumulator alternates between two TMEM buffers, so that the epilogue
@@ -63,10 +63,14 @@ namespace {
 //   warp 1      : issues the MMAs (one thread).
 //   warp 2      : allocates / frees TMEM.
 //   warps 8-11  : epilogue (TMEM lane quadrant w - 8 -> bias, tanh,
-//                 residual / accumulate -> global).
-constexpr int XBM = 128, XBK = 64, XBN = 192, XSTAGES = 2, XTHREADS = 384;
+//                 residual / accumulate -> global).  A warp takes its 32
+//                 rows 32 columns at a time through a shared staging block,
+//                 so that each global access covers 4 rows x 128 bytes.
+constexpr int XBM = 128, XBK = 64, XBN = 144, XSTAGES = 2, XTHREADS = 384;
 constexpr int XF32 = 2 * XBM * 32 * 4;  // FP32 staging of one stage: two TMA boxes (32 KB)
 constexpr int XAT = XBM * XBK * 2;      // one BF16 A tile (hi or lo): 16 KB
+constexpr int XSLD = 36;                // row stride (floats) of an epilogue warp's 32 x 32 staging block
+constexpr int XSTG = 32 * XSLD * 4;     // bytes of one staging block
 
 struct XGemmArgs {
   const uint8_t* bimg;  // [n block][k block][hi, lo] tiles of bn_max rows x 64 K (BF16, K-major, SW128)
@@ -115,7 +119,10 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
   uint64_t* tfull = bars + 3 * XSTAGES;  // [2] accumulator buffer complete
   uint64_t* tempty = tfull + 2;          // [2] accumulator buffer read out (4 warp arrivals)
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(tempty + 2);
-  float* s_bias = reinterpret_cast<float*>(bars + 16);  // [XBN] this N block's bias (0 without one)
+  // [XBN + 32] this N block's bias (0 without one, and past the block: the
+  // epilogue's last 32-column chunk may reach past it)
+  float* s_bias = reinterpret_cast<float*>(bars + 16);
+  float* s_stg = s_bias + XBN + 32;  // [4][32][XSLD] epilogue staging
   auto sF = [&](int s) { return sm + s * stage_bytes; };
   auto sAh = [&](int s) { return sm + s * stage_bytes + XF32; };
   auto sAl = [&](int s) { return sm + s * stage_bytes + XF32 + XAT; };
@@ -136,7 +143,7 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
     fence_mbar_init();
   }
   if (warp == 2) tmem_alloc(s_tmem, 512);
-  for (int c = threadIdx.x; c < XBN; c += blockDim.x) {
+  for (int c = threadIdx.x; c < XBN + 32; c += blockDim.x) {
     const int n = nb * XBN + c;
     s_bias[c] = (a.bias && c < bn && n < a.N) ? a.bias[n] : 0.f;
   }
@@ -220,39 +227,56 @@ k_gemm_bf16x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ XG
     }
   } else if (warp >= 8) {
     const int quad = warp - 8;
-    const int r = quad * 32 + lane;  // row in the tile = TMEM lane
+    float* stg = s_stg + quad * 32 * XSLD;
     for (int it = 0; it < ntile && ok; ++it) {
       const int b = it & 1;
       wait(tfull + b, (it >> 1) & 1);
       fence_after_sync();
-      const long long m = (long long)(blockIdx.x + it * gridDim.x) * XBM + r;
+      const long long m0 = (long long)(blockIdx.x + it * gridDim.x) * XBM + quad * 32;  // this warp's first row
       const uint32_t taddr = tm + (uint32_t)(b * 256) + ((uint32_t)(quad * 32) << 16);
-      for (int c0 = 0; c0 < bn; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + c0, v);
-        if (m >= a.M || !ok) continue;
+      for (int c0 = 0; c0 < bn; c0 += 32) {
+        float v[32];
+        tmem_ld32(taddr + c0, v);
+        // lane = row: bias and tanh, then the row into the staging block
 #pragma unroll
-        for (int q = 0; q < 16; q += 4) {
-          const int n = nb * XBN + c0 + q;
-          if (n >= a.N) break;  // N % 4 == 0
+        for (int q = 0; q < 32; q += 4) {
           const float4 bb = *reinterpret_cast<const float4*>(s_bias + c0 + q);
           float4 o = make_float4(v[q] + bb.x, v[q + 1] + bb.y, v[q + 2] + bb.z, v[q + 3] + bb.w);
-          float* op = &o.x;
           if (a.epi == EPI_TANH || a.epi == EPI_RES_TANH) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) op[t] = tanhf(op[t]);
+            o.x = tanhf(o.x); o.y = tanhf(o.y); o.z = tanhf(o.z); o.w = tanhf(o.w);
           }
-          if (a.epi == EPI_RES_TANH || a.epi == EPI_RES) {
-            const float4 rr = *reinterpret_cast<const float4*>(a.R + m * a.ldr + n);
-            o.x += rr.x; o.y += rr.y; o.z += rr.z; o.w += rr.w;
-          }
-          float4* cp = reinterpret_cast<float4*>(a.C + m * a.ldc + n);
-          if (a.epi == EPI_ACCUM) {
-            const float4 cc = *cp;
-            o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
-          }
-          *cp = o;
+          *reinterpret_cast<float4*>(stg + lane * XSLD + q) = o;
         }
+        __syncwarp();
+        // 8 lanes per row, 4 rows per access: residual / accumulate, store
+        const int q = 4 * (lane & 7);
+        const int nl = c0 + q;  // column within the N block
+        const int n = nb * XBN + nl;
+        if (ok && nl < bn && n < a.N) {  // N % 4 == 0
+          // four rows at a time: the residual / accumulator loads, then the stores
+          const bool res = a.epi == EPI_RES_TANH || a.epi == EPI_RES, acc = a.epi == EPI_ACCUM;
+#pragma unroll
+          for (int k0 = 0; k0 < 8; k0 += 4) {
+            float4 o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int rr = 4 * (k0 + k) + (lane >> 3);
+              const long long m = m0 + rr;
+              o[k] = *reinterpret_cast<const float4*>(stg + rr * XSLD + q);
+              if (m < a.M && (res || acc)) {
+                const float4 e = res ? *reinterpret_cast<const float4*>(a.R + m * a.ldr + n)
+                                     : *reinterpret_cast<const float4*>(a.C + m * a.ldc + n);
+                o[k].x += e.x; o[k].y += e.y; o[k].z += e.z; o[k].w += e.w;
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const long long m = m0 + 4 * (k0 + k) + (lane >> 3);
+              if (m < a.M) *reinterpret_cast<float4*>(a.C + m * a.ldc + n) = o[k];
+            }
+          }
+        }
+        __syncwarp();
       }
       // the buffer is read: the MMAs of tile it + 2 may overwrite it
       fence_before_sync();
@@ -292,8 +316,11 @@ __global__ void k_x_image(const float* __restrict__ B, int ldb, int K, int N, in
 
 PFN_cuTensorMapEncodeTiled_v12000 g_x_encode = nullptr;
 
-// the stages, 1024 bytes of alignment slack, the barriers (128 bytes) and the bias (XBN floats)
-int x_smem(int bn_max) { return XSTAGES * (XF32 + 2 * XAT + 2 * bn_max * 128) + 1024 + 128 + XBN * 4; }
+// the stages, 1024 bytes of alignment slack, the barriers (128 bytes), the
+// bias (XBN + 32 floats) and the epilogue staging (4 blocks)
+int x_smem(int bn_max) {
+  return XSTAGES * (XF32 + 2 * XAT + 2 * bn_max * 128) + 1024 + 128 + (XBN + 32) * 4 + 4 * XSTG;
+}
 
 int x_sm_count(int dev) {
   int c = 0;
@@ -324,36 +351,95 @@ struct XCoreArgs {
   int* err;
 };
 
-// 32 consecutive FP32 values of one row (zeros for rows past the last
-// neighbour), 16-byte loads.
-__device__ __forceinline__ void load_row32(const float* p, bool live, float* v) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (live) x = reinterpret_cast<const float4*>(p)[q];
-    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-  }
-}
-
 __device__ __forceinline__ void store_split32(uint8_t* hi, uint8_t* lo, int r, int c0, const float* v) {
   store_row32<false>(hi, r, c0, v);
   store_row32<false, true>(lo, r, c0, v);
 }
 
-constexpr int XF_SMEM = 6 * XT + 2048 + 64;
+// Coalesced block access of the cores: in access t (0..7) warp w (of 16)
+// takes row w + 16 t and lane l columns 4 l .. 4 l + 3 of a 128-column
+// block, so that each warp access is one row's 512 contiguous bytes.
+__device__ __forceinline__ int blk_row(int t) { return (int)(threadIdx.x >> 5) + 16 * t; }
 
-// Columns [c0, c0 + 32) of one row (p: the row's start): values for columns
-// below ncols, zeros past them and for rows past the last neighbour (ncols % 4
-// == 0, p 16-byte aligned).
-__device__ __forceinline__ void load_cols32(const float* p, int ncols, int c0, bool rv, float* v) {
+// v[4 t .. 4 t + 3] = src[r][c .. c + 3] (r = blk_row(t), c = 4 lane), zero
+// for rows at or past nrows and columns at or past ncols (ncols % 4 == 0).
+__device__ __forceinline__ void load_blk(const float* src, size_t ld, int nrows, int ncols, float* v) {
+  const int c = 4 * (threadIdx.x & 31);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = c0 + 4 * q;
+  for (int t = 0; t < 8; ++t) {
+    const int r = blk_row(t);
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (rv && c < ncols) x = *reinterpret_cast<const float4*>(p + c);
-    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    if (r < nrows && c < ncols) x = *reinterpret_cast<const float4*>(src + (size_t)r * ld + c);
+    v[4 * t] = x.x; v[4 * t + 1] = x.y; v[4 * t + 2] = x.z; v[4 * t + 3] = x.w;
   }
 }
+
+// The BF16 high parts (LO = false) or the BF16 roundings of the residues of a
+// block loaded by load_blk, into a 128 x 128 SW128 tile.
+template <bool LO>
+__device__ __forceinline__ void store_blk(uint8_t* tile, const float* v) {
+  const int c = 4 * (threadIdx.x & 31);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    float x[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = LO ? v[4 * t + i] - round16<false>(v[4 * t + i]) : v[4 * t + i];
+    *reinterpret_cast<uint2*>(tile + sw128_offset(blk_row(t), c, 128)) =
+        make_uint2(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]));
+  }
+}
+
+__device__ __forceinline__ void store_blk_split(uint8_t* hi, uint8_t* lo, const float* v) {
+  store_blk<false>(hi, v);
+  store_blk<true>(lo, v);
+}
+
+// FP32 staging of a 128 x 128 block in shared memory (64 KB): float4 q of
+// row r at r * 128 + 4 (q ^ (r % 8)), free of bank conflicts both for a warp
+// writing one float4 column of 32 rows and for a warp reading one row.
+__device__ __forceinline__ float4* stg4(float* s, int r, int q) {
+  return reinterpret_cast<float4*>(s + r * 128 + 4 * (q ^ (r & 7)));
+}
+
+// TMEM columns [taddr, taddr + 32) of this thread's lane (row) -> the staging
+// block, columns c0 .. c0 + 31.
+__device__ __forceinline__ void tmem_to_stg(uint32_t taddr, float* s, int row, int c0) {
+  float v[32];
+  tmem_ld32(taddr, v);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) *stg4(s, row, (c0 >> 2) + q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// Rows [0, nrows), columns [0, ncols) of a staged block -> dst (row stride
+// ld), one row per warp access; ACC: dst += (a thread's loads are issued four
+// rows at a time before their stores).  ncols % 4 == 0, ncols <= 128.
+template <bool ACC>
+__device__ __forceinline__ void stg_to_global(float* s, float* dst, size_t ld, int nrows, int ncols) {
+  const int q = threadIdx.x & 31;
+  if (4 * q >= ncols) return;
+#pragma unroll
+  for (int t0 = 0; t0 < 8; t0 += 4) {
+    float4 x[4], y[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int r = blk_row(t0 + t);
+      if (r < nrows) {
+        x[t] = *stg4(s, r, q);
+        if (ACC) y[t] = *reinterpret_cast<const float4*>(dst + (size_t)r * ld + 4 * q);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int r = blk_row(t0 + t);
+      if (r < nrows) {
+        if (ACC) { x[t].x += y[t].x; x[t].y += y[t].y; x[t].z += y[t].z; x[t].w += y[t].w; }
+        *reinterpret_cast<float4*>(dst + (size_t)r * ld + 4 * q) = x[t];
+      }
+    }
+  }
+}
+
+constexpr int XF_SMEM = 6 * XT + 2048 + 64;
 
 // NH feature halves of 128 (attention width 128 NH).  Tiles: Q hi / lo of
 // one half (then P hi / lo), K hi / lo of one half, G hi / lo.  S is summed
@@ -402,16 +488,16 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
       if (issuer) prefetch_l2(a.G + nb * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
     }
     float v[32];
-    load_cols32(a.G + (base + row) * a.m1, a.m1, c0, rv, v);
-    store_split32(sGh, sGl, row, c0, v);
+    load_blk(a.G + base * a.m1, a.m1, nn, a.m1, v);
+    store_blk_split(sGh, sGl, v);
     if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     // S = sum over the halves of Q_h K_h^T (three split products each) -> TMEM [0, 128)
 #pragma unroll 1
     for (int h = 0; h < NH; ++h) {
-      load_row32(a.QK + (base + row) * ld + h * 128 + c0, rv, v);
-      store_split32(sQh, sQl, row, c0, v);
-      load_row32(a.QK + (base + row) * ld + NH * 128 + h * 128 + c0, rv, v);
-      store_split32(sKh, sKl, row, c0, v);
+      load_blk(a.QK + base * ld + h * 128, ld, nn, 128, v);
+      store_blk_split(sQh, sQl, v);
+      load_blk(a.QK + base * ld + NH * 128 + h * 128, ld, nn, 128, v);
+      store_blk_split(sKh, sKl, v);
       handoff();
       if (issuer) {
         mma_block<false>(tm, tQh, false, 128, tKh, false, 128, 128, 8, h > 0);
@@ -475,18 +561,28 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
       mma_block<false>(tm + 128, tQh, false, 128, tGl, true, 128, a.npg, 8, true);
     }
     commit_and_sync(sy, issuer);
-    // [P G, rowsum P, 0 ...] -> row of PG (ldpg columns)
+    // [P G, rowsum P, 0 ...] (ldpg columns) -> staging over the dead Q tiles
+    // (the first 128 columns) -> PG, a row per warp access
+    float* stg = reinterpret_cast<float*>(sm);
     {
-      float4* out = reinterpret_cast<float4*>(a.PG + (base + row) * a.ldpg);
-      if (c0 < a.m1) {  // warp-uniform
-        tmem_ld32(tm + lane_off + 128 + c0, v);
+      if (c0 < a.m1) tmem_ld32(tm + lane_off + 128 + c0, v);  // warp-uniform
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (c0 + 4 * q < a.m1) out[(c0 >> 2) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      for (int q = 0; q < 8; ++q) {
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = c0 + 4 * q + i;
+          o[i] = c < a.m1 ? v[4 * q + i] : (c == a.m1 ? psum : 0.f);
+        }
+        *stg4(stg, row, (c0 >> 2) + q) = make_float4(o[0], o[1], o[2], o[3]);
       }
-      if (part == 0)
-        for (int c = a.m1; c < a.ldpg; c += 4) out[c >> 2] = make_float4(c == a.m1 ? psum : 0.f, 0.f, 0.f, 0.f);
+      if (part == 0) {  // columns past 128 (m1 = 128: the row sum and padding)
+        float4* out = reinterpret_cast<float4*>(a.PG + (base + row) * a.ldpg);
+        for (int c = 128; c < a.ldpg; c += 4) out[c >> 2] = make_float4(c == a.m1 ? psum : 0.f, 0.f, 0.f, 0.f);
+      }
     }
+    __syncthreads();
+    stg_to_global<false>(stg, a.PG + base * a.ldpg, a.ldpg, 128, a.ldpg < 128 ? a.ldpg : 128);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -610,14 +706,6 @@ __device__ __forceinline__ void softmax_adjoint(const XCoreArgs& a, uint8_t* pt,
   tmem_wait_st();
 }
 
-// TMEM columns [col, col + 32) of this warp's lanes -> 32 floats at dst.
-__device__ __forceinline__ void tmem_to_row32(uint32_t taddr, float* dst) {
-  float v[32];
-  tmem_ld32(taddr, v);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-}
-
 // Adjoint core, in the form of the forward (Y = [P G, rowsum P] [Wv Wo; bv Wo]
 // + bo): with dPG = dE/d[P G, rowsum P] (a GEMM of dY with [Wv Wo; bv Wo]^T),
 // dP_jk = (dPG G^T)_jk + dPG_j,m1 and dE/dG += P^T dPG (columns below m1), so
@@ -670,7 +758,7 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     const bool rv = row < nn;
-    const float* qk = a.QK + (base + row) * ld;
+    const float* qk0 = a.QK + base * ld;  // this atom's Q | K block
     // the next atom's Q and K rows, dPG and layer input into L2
     if (atom + (int)gridDim.x < a.n) {
       const size_t nb = (size_t)(atom + gridDim.x) * NP;
@@ -681,16 +769,17 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
       }
     }
     float v[32], q32[32];
-    // dPG (columns below m1; the row-sum adjoint, column m1, separately) and G
-    load_cols32(a.dPG + (base + row) * a.ldpg, a.m1, c0, rv, v);
+    // dPG (columns below m1; the row-sum adjoint, column m1, separately) and
+    // G, then K and Q of the first half, in coalesced block accesses
+    load_blk(a.dPG + base * a.ldpg, a.ldpg, nn, a.m1, v);
     const float dpg1 = rv ? a.dPG[(base + row) * a.ldpg + a.m1] : 0.f;
-    store_split32(T[0], T[1], row, c0, v);
-    load_cols32(a.G + (base + row) * a.m1, a.m1, c0, rv, v);
-    store_split32(T[2], T[3], row, c0, v);
-    load_row32(qk + AW + c0, rv, v);  // K, first half
-    store_split32(T[5], T[6], row, c0, v);
-    load_row32(qk + c0, rv, q32);  // Q, first half
-    store_row32<false>(T[4], row, c0, q32);
+    store_blk_split(T[0], T[1], v);
+    load_blk(a.G + base * a.m1, a.m1, nn, a.m1, v);
+    store_blk_split(T[2], T[3], v);
+    load_blk(qk0 + AW, ld, nn, 128, v);  // K, first half
+    store_blk_split(T[5], T[6], v);
+    load_blk(qk0, ld, nn, 128, q32);  // Q, first half
+    store_blk<false>(T[4], q32);
     if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     handoff();
     // dP = dPG G^T -> [128, 256); S = Q0_hi K0^T -> [0, 128)
@@ -704,7 +793,7 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
     commit_and_sync(sy, issuer);
     // G is dead: Q0 lo -> T2, S += Q0_lo K0_hi (NH = 2: with the second half's
     // Q hi, K hi / lo, then its Q lo)
-    store_row32<false, true>(T[2], row, c0, q32);
+    store_blk<true>(T[2], q32);
     int pti;  // the P / dS tile
     if constexpr (NH == 1) {
       handoff();
@@ -712,11 +801,11 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
       commit_and_sync(sy, issuer);
       pti = 3;
     } else {
-      load_row32(qk + 128 + c0, rv, q32);  // Q1
-      store_row32<false>(T[3], row, c0, q32);
-      load_row32(qk + AW + 128 + c0, rv, v);  // K1 (hi -> T4 over Q0 hi, lo -> T6 over K0 lo)
-      store_row32<false>(T[4], row, c0, v);
-      store_row32<false, true>(T[6], row, c0, v);
+      load_blk(qk0 + 128, ld, nn, 128, q32);  // Q1
+      store_blk<false>(T[3], q32);
+      load_blk(qk0 + AW + 128, ld, nn, 128, v);  // K1 (hi -> T4 over Q0 hi, lo -> T6 over K0 lo)
+      store_blk<false>(T[4], v);
+      store_blk<true>(T[6], v);
       handoff();
       if (issuer) {
         mma_block<false>(tm, t[2], false, 128, t[5], false, 128, 128, 8, true);  // Q0_lo K0_hi
@@ -724,7 +813,7 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
         mma_block<false>(tm, t[3], false, 128, t[6], false, 128, 128, 8, true);  // Q1_hi K1_lo
       }
       commit_and_sync(sy, issuer);
-      store_row32<false, true>(T[5], row, c0, q32);  // Q1 lo over K0 hi
+      store_blk<true>(T[5], q32);  // Q1 lo over K0 hi
       handoff();
       if (issuer) mma_block<false>(tm, t[5], false, 128, t[4], false, 128, 128, 8, true);  // Q1_lo K1_hi
       commit_and_sync(sy, issuer);
@@ -740,40 +829,34 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
       mma_block<false>(tm + 256, t[pti], true, 128, t[1], true, 128, a.npg, 8, true);
     }
     commit_and_sync(sy, issuer);
-    // dE/dG (this row) += P^T dPG, columns below m1
-    if (c0 < a.m1) {  // warp-uniform
-      tmem_ld32(tm + lane_off + 256 + c0, v);
-      if (rv) {
-        float4* dg = reinterpret_cast<float4*>(a.dG + (base + row) * a.m1);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + 4 * q;
-          if (c < a.m1) {
-            float4 x = dg[c >> 2];
-            x.x += v[4 * q]; x.y += v[4 * q + 1]; x.z += v[4 * q + 2]; x.w += v[4 * q + 3];
-            dg[c >> 2] = x;
-          }
-        }
-      }
-    }
-    // dS -> the P tile (P is dead)
+    // P^T dPG -> staging over T0 / T1 (dPG is dead), dS -> the P tile
+    float* stg01 = reinterpret_cast<float*>(T[0]);
+    if (c0 < a.m1) tmem_to_stg(tm + lane_off + 256 + c0, stg01, row, c0);  // warp-uniform
     tmem_ld32(tm + lane_off + c0, v);
     store_row32<false>(T[pti], row, c0, v);
+    float* dqk = a.dQK + base * ld;
     if constexpr (NH == 1) {
       handoff();
-      // dQ = dS K -> [0, 128); dK = dS^T Q -> [384, 512)
+      // dQ = dS K -> [0, 128); dK = dS^T Q -> [384, 512), while the threads
+      // add P^T dPG to dE/dG (this atom's rows, columns below m1)
       if (issuer) {
         mma_block<false>(tm, t[3], false, 128, t[5], true, 128, 128, 8, false);
         mma_block<false>(tm, t[3], false, 128, t[6], true, 128, 128, 8, true);
         mma_block<false>(tm + 384, t[3], true, 128, t[4], true, 128, 128, 8, false);
         mma_block<false>(tm + 384, t[3], true, 128, t[2], true, 128, 128, 8, true);
       }
+      stg_to_global<true>(stg01, a.dG + base * a.m1, a.m1, nn, a.m1);
       commit_and_sync(sy, issuer);
-      tmem_to_row32(tm + lane_off + c0, a.dQK + (base + row) * ld + c0);
-      tmem_to_row32(tm + lane_off + 384 + c0, a.dQK + (base + row) * ld + AW + c0);
+      // dQ -> staging over T0 / T1, dK over T2 / T3
+      float* stg23 = reinterpret_cast<float*>(T[2]);
+      tmem_to_stg(tm + lane_off + c0, stg01, row, c0);
+      tmem_to_stg(tm + lane_off + 384 + c0, stg23, row, c0);
     } else {
-      load_row32(qk + AW + c0, rv, v);  // K0 again -> T0 / T1
-      store_split32(T[0], T[1], row, c0, v);
+      handoff();
+      stg_to_global<true>(stg01, a.dG + base * a.m1, a.m1, nn, a.m1);
+      handoff();
+      load_blk(qk0 + AW, ld, nn, 128, v);  // K0 again -> T0 / T1
+      store_blk_split(T[0], T[1], v);
       handoff();
       // dQ0 = dS K0 -> [0, 128), dQ1 = dS K1 -> [128, 256), dK1 = dS^T Q1 -> [384, 512)
       if (issuer) {
@@ -785,8 +868,8 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
         mma_block<false>(tm + 384, t[2], true, 128, t[5], true, 128, 128, 8, true);
       }
       commit_and_sync(sy, issuer);
-      load_row32(qk + c0, rv, v);  // Q0 again -> T0 / T1
-      store_split32(T[0], T[1], row, c0, v);
+      load_blk(qk0, ld, nn, 128, v);  // Q0 again -> T0 / T1
+      store_blk_split(T[0], T[1], v);
       handoff();
       // dK0 = dS^T Q0 -> [256, 384)
       if (issuer) {
@@ -794,21 +877,34 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
         mma_block<false>(tm + 256, t[2], true, 128, t[1], true, 128, 128, 8, true);
       }
       commit_and_sync(sy, issuer);
-      float* dst = a.dQK + (base + row) * ld;
-      tmem_to_row32(tm + lane_off + c0, dst + c0);
-      tmem_to_row32(tm + lane_off + 128 + c0, dst + 128 + c0);
-      tmem_to_row32(tm + lane_off + 256 + c0, dst + AW + c0);
-      tmem_to_row32(tm + lane_off + 384 + c0, dst + AW + 128 + c0);
+      // dQ0, dQ1 -> staging over T0 - T3 -> dQ; then dK0, dK1 the same way
+      float* stg23 = reinterpret_cast<float*>(T[2]);
+      tmem_to_stg(tm + lane_off + c0, stg01, row, c0);
+      tmem_to_stg(tm + lane_off + 128 + c0, stg23, row, c0);
+      __syncthreads();
+      stg_to_global<false>(stg01, dqk, ld, 128, 128);
+      stg_to_global<false>(stg23, dqk + 128, ld, 128, 128);
+      __syncthreads();
+      tmem_to_stg(tm + lane_off + 256 + c0, stg01, row, c0);
+      tmem_to_stg(tm + lane_off + 384 + c0, stg23, row, c0);
     }
-    // the row and column parts -> T0 (dead): [quadrant][128 keys] column
-    // parts, then [quarter][128 rows] row parts
-    float4* parts = reinterpret_cast<float4*>(T[0]);
+    // the row and column parts of dE/drhat, dE/dw -> T4 (dead): [quadrant][128
+    // keys] column parts, then [quarter][128 rows] row parts
+    float4* parts = reinterpret_cast<float4*>(T[4]);
     if (lane < 16) {
       parts[quad * 128 + c0 + lane] = cpart[0];
       parts[quad * 128 + c0 + 16 + lane] = cpart[1];
     }
     parts[512 + part * 128 + row] = rpart;
     __syncthreads();
+    // dK (NH = 1: dQ | dK; NH = 2: dK0 | dK1) from the staging, and dgeo
+    if constexpr (NH == 1) {
+      stg_to_global<false>(stg01, dqk, ld, 128, 128);
+      stg_to_global<false>(reinterpret_cast<float*>(T[2]), dqk + AW, ld, 128, 128);
+    } else {
+      stg_to_global<false>(stg01, dqk + AW, ld, 128, 128);
+      stg_to_global<false>(reinterpret_cast<float*>(T[2]), dqk + AW + 128, ld, 128, 128);
+    }
     if (tid < nn) {
       float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll

@@ -188,11 +188,13 @@ void prof_mark(dp_model* m, const char* stage, cudaStream_t st);
 
 namespace dpa1 {
 using HostArrays = std::vector<std::pair<std::string, std::vector<double>>>;
-// tensor-core (BF16) path, tc.cu
+// fused 16-bit tensor-core path, tc.cu
 int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg);
+// tensor-core embedding net, tc_embed.cu
 int tc_init_embedding(dp_model* m, const HostArrays& arrays, std::string& msg);
 void tc_embed_bf16(dp_model* m, int n, const int* atype, bool bwd, float* G0, const float* dG0, float* dR,
                    float* H12, cudaStream_t st);
+void tc_embed_fused(dp_model* m, int n, const int* atype, bool bwd, cudaStream_t st);
 void tc_plan_buffers(dp_model* m, Arena& a, int cap);
 void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st);
 void tc_free_weights(dp_model* m);
