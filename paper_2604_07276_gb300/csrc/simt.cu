@@ -573,9 +573,9 @@ __device__ __forceinline__ float2 warp_max_pair(float2 v) {
 __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
 // Forward, register-tiled: 256 threads as a 16 x 16 grid.  Thread (ty, tx)
-// owns rows 8 ty .. 8 ty + 7 and keys 8 tx .. 8 tx + 7 of S (128 x 128), then
-// rows 8 ty .. and columns 8 tx .. of each 128-column part of PG.  Q and K
-// pass through shared memory feature-major, 128 features at a time; P stays
+// owns rows t_rc(ty, i) and keys t_rc(tx, jj), i, jj < 8, of S (128 x 128),
+// then the same rows and columns of each 128-column part of PG.  Q and K pass
+// through shared memory feature-major, 128 features at a time; P stays
 // row-major and [G 1] comes in 128-column parts, key-major.  S sums over the
 // features and PG over the keys in order, as a plain loop would.
 //
@@ -589,14 +589,79 @@ __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b
 // a few atoms.  Summing the exact layer input G instead leaves only the
 // rounding of the cancelling sum itself (a CPU emulation of both forms on the
 // 15,668-atom box: force RMSE 7.5e-6 -> 2.4e-6 eV/A).
-constexpr int FT = 256;        // threads of the forward
-constexpr int TLD = NP + 4;    // row stride of its shared tiles (16-byte rows)
+constexpr int FT = 256;        // threads of the forward and the adjoint
+constexpr int TLD = NP + 4;    // row stride of their shared tiles (16-byte rows)
+
+// Row (or column) i < 8 of thread coordinate t < 16: the quarter tiles
+// 4 t .. 4 t + 3 and 64 + 4 t .. 64 + 4 t + 3, so that the 16 threads of a
+// half warp read 16 consecutive float4 of a shared row (no bank conflicts).
+__device__ __forceinline__ int t_rc(int t, int i) { return i < 4 ? 4 * t + i : 60 + 4 * t + i; }
+
+// Feature-major staging of a 128-row chunk: element idx (0 .. 4095) of the
+// CTA's accesses takes row j and features f .. f + 3, 16 rows x 32 bytes per
+// warp access (full sectors), and its transposed stores (feature f + u, row
+// j) fall on distinct banks.
+__device__ __forceinline__ void fm_pos(int idx, int& j, int& f) {
+  const int w = idx >> 5, l = idx & 31;
+  j = 16 * (w & 7) + (l >> 1);
+  f = 4 * ((l & 1) + 2 * (w >> 3));
+}
+
+__device__ __forceinline__ void fm_store(float* T, int j, int f, float4 v) {
+  T[(f + 0) * TLD + j] = v.x; T[(f + 1) * TLD + j] = v.y;
+  T[(f + 2) * TLD + j] = v.z; T[(f + 3) * TLD + j] = v.w;
+}
+
+// The 8 x 8 outer-product step of a register tile: acc[i][jj] += a[i] b[jj],
+// with a = (A[r0 .. r0 + 3], A[r0 + 64 .. r0 + 67]) and the same for b.
+__device__ __forceinline__ void tile_fma(float (&acc)[8][8], const float* A, int ra, const float* B, int rb) {
+  const float4 a0 = *reinterpret_cast<const float4*>(A + ra);
+  const float4 a1 = *reinterpret_cast<const float4*>(A + ra + 64);
+  const float4 b0 = *reinterpret_cast<const float4*>(B + rb);
+  const float4 b1 = *reinterpret_cast<const float4*>(B + rb + 64);
+  const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(av[i], bv[jj], acc[i][jj]);
+}
+
+// acc[i][jj] += sum over k0 .. k0 + 3 of A[t_rc(ty, i)][k] B[k][t_rc(tx, jj)]
+// (A row-major, B key-major, both with row stride TLD).
+__device__ __forceinline__ void tile_fma4(float (&acc)[8][8], const float* A, const float* B, int k0, int ty,
+                                          int tx) {
+  float4 pa[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) pa[i] = *reinterpret_cast<const float4*>(A + t_rc(ty, i) * TLD + k0);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float4 v0 = *reinterpret_cast<const float4*>(B + (k0 + u) * TLD + 4 * tx);
+    const float4 v1 = *reinterpret_cast<const float4*>(B + (k0 + u) * TLD + 64 + 4 * tx);
+    const float vb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float p = u == 0 ? pa[i].x : u == 1 ? pa[i].y : u == 2 ? pa[i].z : pa[i].w;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(p, vb[jj], acc[i][jj]);
+    }
+  }
+}
+
+// Row t_rc(ty, i) of a register tile -> dst row (columns 4 tx .. and 64 + 4
+// tx .. from col0, each float4 only below ncols).
+__device__ __forceinline__ void tile_store_row(float* dst, const float* accrow, int col0, int tx, int ncols) {
+  if (col0 + 4 * tx < ncols)
+    *reinterpret_cast<float4*>(dst + col0 + 4 * tx) = make_float4(accrow[0], accrow[1], accrow[2], accrow[3]);
+  if (col0 + 64 + 4 * tx < ncols)
+    *reinterpret_cast<float4*>(dst + col0 + 64 + 4 * tx) = make_float4(accrow[4], accrow[5], accrow[6], accrow[7]);
+}
 
 template <int A>
 __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
   extern __shared__ float sm[];
   float* X = sm;                 // [128][TLD]: Q chunk (feature-major), then P (row-major)
-  float* Y = X + 128 * TLD;      // [128][TLD]: K chunk (feature-major), then a part of V (key-major)
+  float* Y = X + 128 * TLD;      // [128][TLD]: K chunk (feature-major), then a part of [G 1] (key-major)
   float4* rws = reinterpret_cast<float4*>(Y + 128 * TLD);  // [NP]
   float2* w2s = reinterpret_cast<float2*>(rws + NP);       // [NP] switch weights as float pairs
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -614,50 +679,36 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) s[i][jj] = 0.f;
-    const bool live = 8 * ty < nn && 8 * tx < nn;
+    const bool live = 4 * ty < nn && 4 * tx < nn;
     for (int c0 = 0; c0 < A; c0 += 128) {
       if (c0 > 0) __syncthreads();  // the previous chunk's products are done
-      // row j, features f .. f + 3 of Q and K -> X[f + u][j], Y[f + u][j]
       for (int idx = tid; idx < NP * 32; idx += FT) {
-        const int j = idx & (NP - 1), f = 4 * (idx >> 7);
+        int j, f;
+        fm_pos(idx, j, f);
         float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
         if (j < nn) {
           qv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + c0 + f);
           kv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + A + c0 + f);
         }
-        X[(f + 0) * TLD + j] = qv.x; X[(f + 1) * TLD + j] = qv.y;
-        X[(f + 2) * TLD + j] = qv.z; X[(f + 3) * TLD + j] = qv.w;
-        Y[(f + 0) * TLD + j] = kv.x; Y[(f + 1) * TLD + j] = kv.y;
-        Y[(f + 2) * TLD + j] = kv.z; Y[(f + 3) * TLD + j] = kv.w;
+        fm_store(X, j, f, qv);
+        fm_store(Y, j, f, kv);
       }
       __syncthreads();
-      if (live) {
-        for (int f = 0; f < 128; ++f) {
-          const float4 a0 = *reinterpret_cast<const float4*>(X + f * TLD + 8 * ty);
-          const float4 a1 = *reinterpret_cast<const float4*>(X + f * TLD + 8 * ty + 4);
-          const float4 b0 = *reinterpret_cast<const float4*>(Y + f * TLD + 8 * tx);
-          const float4 b1 = *reinterpret_cast<const float4*>(Y + f * TLD + 8 * tx + 4);
-          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) s[i][jj] = fmaf(av[i], bv[jj], s[i][jj]);
-        }
-      }
+      if (live)
+        for (int f = 0; f < 128; ++f) tile_fma(s, X, f * TLD + 4 * ty, Y, f * TLD + 4 * tx);
     }
     __syncthreads();  // X and Y are free: P goes to X
     // softmax per row over the 16 threads of a half warp (every lane takes
     // part in the shuffles; rows and keys past nnei come out zero)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int j = 8 * ty + i;
+      const int j = t_rc(ty, i);
       const float4 rj = rws[j];
       const float2 wj = w2s[j];
       float2 lp[8], mx = make_float2(-3.0e38f, 0.f);
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int k = 8 * tx + jj;
+        const int k = t_rc(tx, jj);
         lp[jj] = make_float2(-3.0e38f, 0.f);
         if (k < nn) {
           lp[jj] = smooth_logit(s[i][jj] * scale, a.shift, wj, w2s[k]);
@@ -673,7 +724,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
       float e[8], sum = 0.f;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        e[jj] = 8 * tx + jj < nn ? expf(pair_diff(lp[jj], mx)) : 0.f;
+        e[jj] = t_rc(tx, jj) < nn ? expf(pair_diff(lp[jj], mx)) : 0.f;
         sum += e[jj];
       }
 #pragma unroll
@@ -682,15 +733,14 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
       float pv[8];
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int k = 8 * tx + jj;
+        const int k = t_rc(tx, jj);
         pv[jj] = 0.f;
         if (j < nn && k < nn) {
           const float4 rk = rws[k];
           pv[jj] = e[jj] * inv * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z);
         }
       }
-      *reinterpret_cast<float4*>(X + j * TLD + 8 * tx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
-      *reinterpret_cast<float4*>(X + j * TLD + 8 * tx + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
+      tile_store_row(X + j * TLD, pv, 0, tx, 128);
     }
     // PG = P [G 1], 128 columns at a time (column m1 of [G 1] is 1, later
     // ones 0; m1 % 4 == 0)
@@ -706,46 +756,23 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
         }
         *reinterpret_cast<float4*>(Y + k * TLD + f - c0) = vv;
       }
-      __syncthreads();  // P (first part) and this part of V are in place
+      __syncthreads();  // P (first part) and this part of [G 1] are in place
       float acc[8][8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
-      if (8 * ty < nn) {
-        for (int k = 0; k < nn4; k += 4) {
-          float4 pa[8];
+      if (4 * ty < nn)
+        for (int k = 0; k < nn4; k += 4) tile_fma4(acc, X, Y, k, ty, tx);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) pa[i] = *reinterpret_cast<const float4*>(X + (8 * ty + i) * TLD + k);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 v0 = *reinterpret_cast<const float4*>(Y + (k + u) * TLD + 8 * tx);
-            const float4 v1 = *reinterpret_cast<const float4*>(Y + (k + u) * TLD + 8 * tx + 4);
-            const float vb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float pk = u == 0 ? pa[i].x : u == 1 ? pa[i].y : u == 2 ? pa[i].z : pa[i].w;
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(pk, vb[jj], acc[i][jj]);
-            }
-          }
-        }
-      }
-      if (c0 + 8 * tx < a.ldpg) {  // ldpg % 8 == 0
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float* o = a.PG + (base + 8 * ty + i) * a.ldpg + c0 + 8 * tx;
-          *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-          *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-        }
-      }
+      for (int i = 0; i < 8; ++i) tile_store_row(a.PG + (base + t_rc(ty, i)) * a.ldpg, acc[i], c0, tx, a.ldpg);
     }
   }
 }
 
 // Adjoint of one attention layer for one centre, register-tiled like the
-// forward (256 threads as a 16 x 16 grid; thread (ty, tx) owns rows 8 ty ..
-// 8 ty + 7 and keys or columns 8 tx .. 8 tx + 7 of each 128 x 128 product),
+// forward (256 threads as a 16 x 16 grid; thread (ty, tx) owns rows t_rc(ty,
+// i) and keys or columns t_rc(tx, jj) of each 128 x 128 product),
 // in the form of the forward's output Y = [P G, rowsum P] [Wv Wo; bv Wo] +
 // bo: with dPG = dE/d[P G, rowsum P] (a GEMM of dY with [Wv Wo; bv Wo]^T),
 //   dP_jk = sum_c dPG_jc G_kc + dPG_j,m1        (the values V never appear)
@@ -773,7 +800,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
       w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
-    const bool live = 8 * ty < nn && 8 * tx < nn;
+    const bool live = 4 * ty < nn && 4 * tx < nn;
     float s[8][8], dp[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -783,63 +810,37 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     for (int c0 = 0; c0 < A; c0 += 128) {
       if (c0 > 0) __syncthreads();
       for (int idx = tid; idx < NP * 32; idx += FT) {
-        const int j = idx & (NP - 1), f = 4 * (idx >> 7);
+        int j, f;
+        fm_pos(idx, j, f);
         float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
         if (j < nn) {
           qv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + c0 + f);
           kv = *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + A + c0 + f);
         }
-        B0[(f + 0) * TLD + j] = qv.x; B0[(f + 1) * TLD + j] = qv.y;
-        B0[(f + 2) * TLD + j] = qv.z; B0[(f + 3) * TLD + j] = qv.w;
-        B1[(f + 0) * TLD + j] = kv.x; B1[(f + 1) * TLD + j] = kv.y;
-        B1[(f + 2) * TLD + j] = kv.z; B1[(f + 3) * TLD + j] = kv.w;
+        fm_store(B0, j, f, qv);
+        fm_store(B1, j, f, kv);
       }
       __syncthreads();
-      if (live) {
-        for (int f = 0; f < 128; ++f) {
-          const float4 a0 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty);
-          const float4 a1 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty + 4);
-          const float4 b0 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx);
-          const float4 b1 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx + 4);
-          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) s[i][jj] = fmaf(av[i], bv[jj], s[i][jj]);
-        }
-      }
+      if (live)
+        for (int f = 0; f < 128; ++f) tile_fma(s, B0, f * TLD + 4 * ty, B1, f * TLD + 4 * tx);
     }
     __syncthreads();
     // dP = dPG G^T over the m1 columns (feature-major: dPG in B0, G in B1;
     // m1 % 4 == 0)
     for (int idx = tid; idx < NP * 32; idx += FT) {
-      const int j = idx & (NP - 1), f = 4 * (idx >> 7);
+      int j, f;
+      fm_pos(idx, j, f);
       float4 dv = make_float4(0.f, 0.f, 0.f, 0.f), gv = dv;
       if (j < nn && f < a.m1) {
         dv = *reinterpret_cast<const float4*>(a.dPG + (base + j) * a.ldpg + f);
         gv = *reinterpret_cast<const float4*>(a.G + (base + j) * a.m1 + f);
       }
-      B0[(f + 0) * TLD + j] = dv.x; B0[(f + 1) * TLD + j] = dv.y;
-      B0[(f + 2) * TLD + j] = dv.z; B0[(f + 3) * TLD + j] = dv.w;
-      B1[(f + 0) * TLD + j] = gv.x; B1[(f + 1) * TLD + j] = gv.y;
-      B1[(f + 2) * TLD + j] = gv.z; B1[(f + 3) * TLD + j] = gv.w;
+      fm_store(B0, j, f, dv);
+      fm_store(B1, j, f, gv);
     }
     __syncthreads();
-    if (live) {
-      for (int f = 0; f < a.m1; ++f) {
-        const float4 a0 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty);
-        const float4 a1 = *reinterpret_cast<const float4*>(B0 + f * TLD + 8 * ty + 4);
-        const float4 b0 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx);
-        const float4 b1 = *reinterpret_cast<const float4*>(B1 + f * TLD + 8 * tx + 4);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) dp[i][jj] = fmaf(av[i], bv[jj], dp[i][jj]);
-      }
-    }
+    if (live)
+      for (int f = 0; f < a.m1; ++f) tile_fma(dp, B0, f * TLD + 4 * ty, B1, f * TLD + 4 * tx);
     __syncthreads();  // B0 and B1 are free: dS goes to B1, P to B2, column parts to B0
     // softmax adjoint per row over the 16 threads of a half warp (every lane
     // takes part in the shuffles; rows and keys past nnei come out zero)
@@ -848,14 +849,14 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     for (int jj = 0; jj < 8; ++jj) { cw[jj] = 0.f; cx[jj] = 0.f; cy[jj] = 0.f; cz[jj] = 0.f; }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int j = 8 * ty + i;
+      const int j = t_rc(ty, i);
       const float4 rj = rws[j];
       const float2 wj = w2s[j];
       const float dpg1 = j < nn ? a.dPG[(base + j) * a.ldpg + a.m1] : 0.f;  // adjoint of rowsum P
       float2 lp[8], mx = make_float2(-3.0e38f, 0.f);
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int k = 8 * tx + jj;
+        const int k = t_rc(tx, jj);
         lp[jj] = make_float2(-3.0e38f, 0.f);
         if (k < nn) {
           lp[jj] = smooth_logit(s[i][jj] * scale, a.shift, wj, w2s[k]);  // as in the forward kernel
@@ -871,7 +872,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       float e[8], sum = 0.f;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        e[jj] = 8 * tx + jj < nn ? expf(pair_diff(lp[jj], mx)) : 0.f;
+        e[jj] = t_rc(tx, jj) < nn ? expf(pair_diff(lp[jj], mx)) : 0.f;
         sum += e[jj];
       }
 #pragma unroll
@@ -880,7 +881,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       float At[8], dA[8], tsum = 0.f;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int k = 8 * tx + jj;
+        const int k = t_rc(tx, jj);
         const float4 rk = rws[k];
         At[jj] = e[jj] * inv;
         dA[jj] = k < nn ? (dp[i][jj] + dpg1) * (rj.w * rk.w) * (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z) : 0.f;
@@ -891,7 +892,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       float rw_ = 0.f, rx = 0.f, ry = 0.f, rz = 0.f, ds[8], pv[8];
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int k = 8 * tx + jj;
+        const int k = t_rc(tx, jj);
         ds[jj] = 0.f;
         pv[jj] = 0.f;
         if (j < nn && k < nn) {
@@ -910,10 +911,8 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
           cx[jj] += dc * rj.x; cy[jj] += dc * rj.y; cz[jj] += dc * rj.z;
         }
       }
-      *reinterpret_cast<float4*>(B1 + j * TLD + 8 * tx) = make_float4(ds[0], ds[1], ds[2], ds[3]);
-      *reinterpret_cast<float4*>(B1 + j * TLD + 8 * tx + 4) = make_float4(ds[4], ds[5], ds[6], ds[7]);
-      *reinterpret_cast<float4*>(B2 + j * TLD + 8 * tx) = make_float4(pv[0], pv[1], pv[2], pv[3]);
-      *reinterpret_cast<float4*>(B2 + j * TLD + 8 * tx + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
+      tile_store_row(B1 + j * TLD, ds, 0, tx, 128);
+      tile_store_row(B2 + j * TLD, pv, 0, tx, 128);
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         rw_ += __shfl_xor_sync(0xffffffffu, rw_, o);
@@ -926,7 +925,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     // column parts of this thread's 8 rows -> B0 as [ty][key]
     float4* colp = reinterpret_cast<float4*>(B0);
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) colp[ty * NP + 8 * tx + jj] = make_float4(cx[jj], cy[jj], cz[jj], cw[jj]);
+    for (int jj = 0; jj < 8; ++jj) colp[ty * NP + t_rc(tx, jj)] = make_float4(cx[jj], cy[jj], cz[jj], cw[jj]);
     __syncthreads();
     if (tid < nn) {
       float4 acc = rowg[tid];
@@ -954,31 +953,10 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
-      if (8 * ty < nn) {
-        for (int k = 0; k < nn4; k += 4) {
-          float4 da[8];
+      if (4 * ty < nn)
+        for (int k = 0; k < nn4; k += 4) tile_fma4(acc, B1, B0, k, ty, tx);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) da[i] = *reinterpret_cast<const float4*>(B1 + (8 * ty + i) * TLD + k);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 v0 = *reinterpret_cast<const float4*>(B0 + (k + u) * TLD + 8 * tx);
-            const float4 v1 = *reinterpret_cast<const float4*>(B0 + (k + u) * TLD + 8 * tx + 4);
-            const float vb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float d = u == 0 ? da[i].x : u == 1 ? da[i].y : u == 2 ? da[i].z : da[i].w;
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(d, vb[jj], acc[i][jj]);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float* o = a.dQK + (base + 8 * ty + i) * ld + c0 + 8 * tx;
-        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-      }
+      for (int i = 0; i < 8; ++i) tile_store_row(a.dQK + (base + t_rc(ty, i)) * ld, acc[i], c0, tx, A);
       // dK = dS^T Q: Q row-major in B0
       __syncthreads();
       for (int idx = tid; idx < NP * 32; idx += FT) {
@@ -991,26 +969,10 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
-      if (8 * ty < nn) {
-        for (int j = 0; j < nn; ++j) {
-          const float4 d0 = *reinterpret_cast<const float4*>(B1 + j * TLD + 8 * ty);
-          const float4 d1 = *reinterpret_cast<const float4*>(B1 + j * TLD + 8 * ty + 4);
-          const float4 q0 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx);
-          const float4 q1 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx + 4);
-          const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-          const float qv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      if (4 * ty < nn)
+        for (int j = 0; j < nn; ++j) tile_fma(acc, B1, j * TLD + 4 * ty, B0, j * TLD + 4 * tx);
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(dv[i], qv[jj], acc[i][jj]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float* o = a.dQK + (base + 8 * ty + i) * ld + A + c0 + 8 * tx;
-        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-      }
+      for (int i = 0; i < 8; ++i) tile_store_row(a.dQK + (base + t_rc(ty, i)) * ld + A, acc[i], c0, tx, A);
     }
     // dE/dG += P^T dPG: dPG row-major in B0 (columns below m1; m1 <= 128)
     __syncthreads();
@@ -1021,36 +983,27 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    if (8 * ty < nn && 8 * tx < a.m1) {
+    if (4 * ty < nn && 4 * tx < a.m1) {
       float acc[8][8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
-      for (int j = 0; j < nn; ++j) {
-        const float4 p0 = *reinterpret_cast<const float4*>(B2 + j * TLD + 8 * ty);
-        const float4 p1 = *reinterpret_cast<const float4*>(B2 + j * TLD + 8 * ty + 4);
-        const float4 g0 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx);
-        const float4 g1 = *reinterpret_cast<const float4*>(B0 + j * TLD + 8 * tx + 4);
-        const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(pv[i], gv[jj], acc[i][jj]);
-      }
+      for (int j = 0; j < nn; ++j) tile_fma(acc, B2, j * TLD + 4 * ty, B0, j * TLD + 4 * tx);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int k = 8 * ty + i;
+        const int k = t_rc(ty, i);
         if (k >= nn) continue;
-        float4* dg = reinterpret_cast<float4*>(a.dG + (base + k) * a.m1 + 8 * tx);
-        float4 x = dg[0];
-        x.x += acc[i][0]; x.y += acc[i][1]; x.z += acc[i][2]; x.w += acc[i][3];
-        dg[0] = x;
-        if (8 * tx + 4 < a.m1) {
-          x = dg[1];
-          x.x += acc[i][4]; x.y += acc[i][5]; x.z += acc[i][6]; x.w += acc[i][7];
-          dg[1] = x;
+        float* dgrow = a.dG + (base + k) * a.m1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 64 * h + 4 * tx;
+          if (c < a.m1) {
+            float4* dg = reinterpret_cast<float4*>(dgrow + c);
+            float4 x = *dg;
+            x.x += acc[i][4 * h]; x.y += acc[i][4 * h + 1]; x.z += acc[i][4 * h + 2]; x.w += acc[i][4 * h + 3];
+            *dg = x;
+          }
         }
       }
     }
