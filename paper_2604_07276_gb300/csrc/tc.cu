@@ -6,11 +6,13 @@
 //
 // One persistent CTA per SM walks over centre atoms; an atom is one 128-row
 // tile (its neighbour slots).  Every product of a layer runs on the tensor
-// cores from 128x128 16-bit tiles in shared memory:
-//   forward : [Q K V] = G Wqkv, S = Q K^T, O = P V, Y = O Wo
-//   backward: [Q K V] = G Wqkv and S = Q K^T (recomputed), dO = dY Wo^T,
-//             dP = dO V^T, dV = P^T dO, dQ = dS K, dK = dS^T Q,
-//             dG = dQ Wq^T + dK Wk^T + dV Wv^T
+// cores from 128x128 16-bit tiles in shared memory.  With V = G Wv + bv,
+// O Wo = P V Wo = [P G, rowsum P] [Wv Wo; bv Wo], so the values V are never
+// formed:
+//   forward : [Q K] = G [Wq Wk], S = Q K^T, PG = P [G 1], Y = PG Wvo
+//   backward: [Q K] and S recomputed, dPG = dY Wvo^T, dP = dPG [G 1]^T,
+//             dQ = dS K, dK = dS^T Q,
+//             dG = dQ Wq^T + dK Wk^T + P^T dPG
 // The transposed operands are MN-major views of the same tiles, so no
 // transpose is ever materialised.  Softmax, LayerNorm and all element-wise
 // work run in FP32 on 512 threads (a thread owns a quarter of a row: 32
@@ -36,11 +38,12 @@ namespace {
 
 constexpr int NT = 512;           // threads per CTA of the layer kernels
 constexpr int TILE = 32768;       // 128 x 128 bf16 SW128 tile
-constexpr int WO_ROWS = 112;      // Wo tile: M1 = 100 output rows padded to 112
+constexpr int WO_ROWS = 112;      // Wvo tile: M1 = 100 output rows padded to 112
 constexpr int WO_TILE = 2 * WO_ROWS * 128;  // 28 KB
-// per-layer weight image (bytes): [Wq; Wk], Wv, Wo and the rounding residue
-// Wo - round16(Wo) (the low part of a two-term split of Wo)
-constexpr int WIMG = 3 * TILE + 2 * WO_TILE;
+// per-layer weight image (bytes): [Wq; Wk], then Wvo = [Wv Wo; bv Wo] and its
+// rounding residue Wvo - round16(Wvo) (the low part of a two-term split)
+constexpr int WV_OFF = 2 * TILE;
+constexpr int WIMG = WV_OFF + 2 * WO_TILE;
 constexpr int KS_M1 = 7;          // K-steps covering the M1 = 100 (<= 112) inputs
 
 struct LayerArgs {
@@ -86,20 +89,20 @@ __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool
 }
 
 // ------------------------------------------------------------------ forward
-// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K,224K), then the
-// per-key (rhat, w) table and the barriers.  Slot use per atom: G (hi, lo)
-// in A, B; Q, K in C, D while V is still accumulating; V (hi, lo) in A, B;
-// P (hi, lo) in C, D; then O in A and Wo, streamed per atom by a bulk
-// asynchronous copy, in D.  TMEM columns: [Q K V] accumulators
-// 0-383 (S and O reuse 0-127, Y 128-239) and the FP32 layer input kept at
-// 384-511 for the residual.  Thread layout: warp w owns TMEM lane quadrant
-// w % 4 (rows 32 (w % 4) .. +31) and column quarter w / 4 (32 columns).
+// Shared memory: slots A-D [0,128K), Wq, Wk [128K,192K), then the per-key
+// (rhat, w) table and the barriers.  Slot use per atom: G (hi, lo) in A, B
+// until P G is formed; Q, K in C, D; P (hi, lo) in C, D; then P G in A and
+// Wvo, streamed per atom by a bulk asynchronous copy, in D (its residue in
+// C).  TMEM columns: [Q K] accumulators 0-255 (S and P G reuse 0-127, Y
+// 128-239) and the FP32 layer input kept at 384-511 for the residual.
+// Thread layout: warp w owns TMEM lane quadrant w % 4 (rows 32 (w % 4) ..
+// +31) and column quarter w / 4 (32 columns).
 constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_SLOT_D = 3 * TILE, F_W = 4 * TILE;
-constexpr int F_SMALL = 7 * TILE;
+constexpr int F_SMALL = 6 * TILE;
 constexpr int F_SMEM = F_SMALL + 2048 + 64;
 
-// F16 = true: FP16 operands with two-term splits of G (in [Q K V] = G Wqkv),
-// of P and of V (in O = P V); F16 = false: plain BF16 operands.
+// F16 = true: FP16 operands with two-term splits of G (in [Q K] = G [Wq Wk]
+// and P G) and of P; F16 = false: plain BF16 operands.
 template <bool F16>
 __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ LayerArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -112,7 +115,6 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sC = sm + F_SLOT_C;
   uint8_t* sD = sm + F_SLOT_D;
   uint8_t* sWqk = sm + F_W;  // [Wq; Wk], 256 rows
-  uint8_t* sWv = sWqk + 2 * TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wo copy, Q K, Q K out, V, inputs
   uint64_t* bar_ld = bar + 1;
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   // last neighbour of most atoms, columns 96-127 past the embedding width)
   const bool issuer = tid == NT - 32;
 
-  copy_image(sWqk, a.wimg, 3 * TILE);
+  copy_image(sWqk, a.wimg, 2 * TILE);
   if (issuer) {
     for (int i = 0; i < 6; ++i) mbar_init(bar + i, i == 3 ? NT / 32 : 1);  // [3]: one arrival per warp
     fence_mbar_init();
@@ -139,11 +141,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   const uint32_t tm = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
-  const uint32_t tWqk = smem_u32(sWqk), tWv = smem_u32(sWv);
-  const uint4* wo_img = a.wimg + 3 * TILE / 16;
+  const uint32_t tWqk = smem_u32(sWqk);
+  const uint4* wo_img = a.wimg + WV_OFF / 16;
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
-  Sync sq{bar_q, 0u, a.err}, sv{bar_q + 2, 0u, a.err};
+  Sync sq{bar_q, 0u, a.err};
   Sync so{bar_q + 1, 0u, a.err};  // Q and K are out of TMEM: waited on by the issuer only
   Sync si{bar_in, 0u, a.err};
   const uint32_t g_bytes = (uint32_t)(NP * a.m1 * sizeof(float)), k_bytes = NP * sizeof(float4);
@@ -172,40 +174,29 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
     handoff();
-    // [Q K] = G [Wq Wk] (N = 256) and V = G Wv (+ the G_lo products), one
-    // commit group each, so that Q and K leave TMEM while V's products run
+    // [Q K] = G [Wq Wk] (N = 256, + the G_lo product)
     if (issuer) {
       mma_block<F16>(tm + 0, tA, false, 128, tWqk, false, 256, 256, KS_M1, false);
       if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWqk, false, 256, 256, KS_M1, true);
       mma_commit(bar_q);
-      mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
-      if (F16) mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
-      mma_commit(bar_q + 2);
     }
-    // Q -> C, K -> D (G in A, B is still being read)
+    // Q -> C, K -> D (G stays in A, B for P G)
     sq.wait();
     tmem_ld32(tm + lane_off + 0 + c0, v);
     store_row32<F16>(sC, row, c0, v);
     tmem_ld32(tm + lane_off + 128 + c0, v);
     store_row32<F16>(sD, row, c0, v);
-    // an arrival, not a CTA barrier: no warp waits while the issuer is still
-    // queueing V's products
+    // an arrival per warp, then S = Q K^T -> TMEM [0,128)
     warp_arrive(bar_q + 1);
-    // S = Q K^T -> TMEM [0,128) while V -> A (+ V_lo -> B); the tiles of V
-    // reach the tensor cores through the handoff after the softmax
     if (issuer) {
       if (so.wait()) mma_block<F16>(tm + 0, tC, false, 128, tD, false, 128, 128, 8, false);
       mma_commit(bar);
     }
-    sv.wait();
-    tmem_ld32(tm + lane_off + 256 + c0, v);
-    store_row32<F16>(sA, row, c0, v);
-    if (F16) store_row32<F16, true>(sB, row, c0, v);
     sy.wait();
     // smooth softmax and gate: P -> slot C (+ P_lo -> slot D); Q and K are dead.
     // Row j of P carries the factor w_j, which vanishes for neighbours near
     // rcut; the tiles hold P / w_j instead (no FP16 subnormals), and w_j is
-    // applied to Y = (P / w_j) V Wo in FP32 before the LayerNorm.
+    // applied to Y = (P / w_j) G Wvo in FP32 before the LayerNorm.
     tmem_ld32(tm + lane_off + 0 + c0, v);
     float w_row;
     {
@@ -255,18 +246,20 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       if (F16) store_row32<F16, true>(sD, row, c0, v);
     }
     handoff();
-    // O = P V (+ P_lo V + P V_lo)  (V as an MN-major operand)
+    // P G = P [G 1 1] (+ P_lo G + P G_lo) -> TMEM [0, 112) (G as an MN-major
+    // operand; its columns M1, M1 + 1 are 1, so those of P G are rowsum P)
     if (issuer) {
-      mma_block<F16>(tm + 0, tC, false, 128, tA, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tC, false, 128, tA, true, 128, WO_ROWS, 8, false);
       if (F16) {
-        mma_block<F16>(tm + 0, tD, false, 128, tA, true, 128, 128, 8, true);
-        mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, 128, 8, true);
+        mma_block<F16>(tm + 0, tD, false, 128, tA, true, 128, WO_ROWS, 8, true);
+        mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, WO_ROWS, 8, true);
       }
     }
     commit_and_sync(sy, issuer);
-    // Wo -> slot D (bulk copy, P_lo is dead) while O leaves TMEM -> A; with
-    // FP16 operands also Wo_lo -> slot C (P is dead): rounding Wo itself to
-    // FP16 would shift the atomic energies by up to ~1e-3 eV
+    // Wvo -> slot D (bulk copy, P_lo is dead) while P G leaves TMEM -> A; with
+    // FP16 operands also the residue of Wvo -> slot C (P is dead): rounding the
+    // weights themselves to FP16 would shift the atomic energies by up to
+    // ~1e-3 eV.  Columns past 112 of the P G tile are never read (K = 112).
     if (issuer) {
       mbar_expect_tx(bar_ld, F16 ? 2 * WO_TILE : WO_TILE);
       bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
@@ -275,17 +268,17 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     tmem_ld32(tm + lane_off + 0 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     handoff();
-    // Y = O Wo (+ O Wo_lo) -> TMEM [128, 240)
+    // Y = P G Wvo (+ P G Wvo_lo) -> TMEM [128, 240)
     if (issuer && sl.wait()) {
-      mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, 8, false);
-      if (F16) mma_block<F16>(tm + 128, tA, false, 128, tC, false, WO_ROWS, WO_ROWS, 8, true);
+      mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, KS_M1, false);
+      if (F16) mma_block<F16>(tm + 128, tA, false, 128, tC, false, WO_ROWS, WO_ROWS, KS_M1, true);
     }
     commit_and_sync(sy, issuer);
     // C, D and the key table are dead: the next atom's inputs start to arrive
     if (issuer && atom + (int)gridDim.x < a.n) fetch_inputs(atom + gridDim.x);
     // LayerNorm, residual
     {
-      const RowXchg xr(sB, row, part, lane, quad);  // V_lo is dead
+      const RowXchg xr(sB, row, part, lane, quad);  // G_lo is dead
       tmem_ld32(tm + lane_off + 128 + c0, v);
       float s1 = 0.f;
 #pragma unroll
@@ -350,9 +343,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 }
 
 // ----------------------------------------------------------------- backward
-// Shared memory: slots A-D [0,128K), Wq, Wk, Wv [128K, 224K), per-key table,
-// barriers.  Wo is streamed per atom into slot D.  Same thread layout as the
-// forward kernel.
+// Shared memory: slots A-D [0,128K), Wq, Wk [128K, 192K), slot E [192K,
+// 224K), per-key table, barriers.  Wvo is streamed per atom into slot D.
+// Same thread layout as the forward kernel.
 constexpr int B_SLOT_A = 0, B_SLOT_B = TILE, B_SLOT_C = 2 * TILE, B_SLOT_D = 3 * TILE, B_W = 4 * TILE;
 constexpr int B_SMALL = 4 * TILE + 3 * TILE;
 constexpr int B_SMEM = B_SMALL + 2048 + 64;
@@ -369,9 +362,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   uint8_t* sC = sm + B_SLOT_C;
   uint8_t* sD = sm + B_SLOT_D;
   uint8_t* sWqk = sm + B_W;  // [Wq; Wk], 256 rows
-  uint8_t* sWv = sWqk + 2 * TILE;
+  uint8_t* sE = sWqk + 2 * TILE;
   float4* s_key = reinterpret_cast<float4*>(sm + B_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  // [5]: general, Wo copy, Q K V, G ready, dY ready (the last two take one
+  // [5]: general, Wvo copy, Q K, G ready, dY ready (the last two take one
   // arrival per warp; each sees exactly one phase per atom)
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);
   uint64_t* bar_ld = bar + 1;
@@ -389,7 +382,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   // last neighbour of most atoms, columns 96-127 past the embedding width)
   const bool issuer = tid == NT - 32;
 
-  copy_image(sWqk, a.wimg, 3 * TILE);
+  copy_image(sWqk, a.wimg, 2 * TILE);
   if (issuer) {
     for (int i = 0; i < 3; ++i) mbar_init(bar + i, 1);
     mbar_init(bar_g, NT / 32);
@@ -401,14 +394,14 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
   const uint32_t tm = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const uint32_t tA = smem_u32(sA), tB = smem_u32(sB), tC = smem_u32(sC), tD = smem_u32(sD);
-  const uint32_t tWqk = smem_u32(sWqk), tWv = smem_u32(sWv);
+  const uint32_t tWqk = smem_u32(sWqk), tE = smem_u32(sE);
   const uint32_t tWk = tWqk + 128 * 128;  // rows 128-255 of the [Wq; Wk] tile
   Sync sy{bar, 0u, a.err};
   Sync sl{bar_ld, 0u, a.err};
   Sync sq{bar_q, 0u, a.err};
   Sync sg{bar_g, 0u, a.err}, sd{bar_dy, 0u, a.err};  // waited on by the issuer only
-  const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + 3 * TILE;
-  // An atom's Wo copy (slot D) and its layer-input rows (parked in TMEM
+  const uint8_t* wo_img = reinterpret_cast<const uint8_t*>(a.wimg) + WV_OFF;
+  // An atom's Wvo copy (slot D) and its layer-input rows (parked in TMEM
   // columns [0, 128)) arrive during the previous atom's last phase; the
   // first atom's here
   int nn_next = (int)blockIdx.x < a.n ? a.nnei[blockIdx.x] : 0;
@@ -464,15 +457,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     // The two handoffs to the issuer in P0 are arrivals on mbarriers, not CTA
     // barriers: no warp waits while the issuer is held up issuing M0a
     warp_arrive(bar_g);
-    // M0a: [Q K] = G [Wq Wk] (N = 256), V = G Wv (+ the G_lo products) -> [0, 384)
+    // M0a: [Q K] = G [Wq Wk] (N = 256, + the G_lo product) -> [0, 256)
     if (issuer) {
       if (sg.wait()) {
         mma_block<F16>(tm + 0, tA, false, 128, tWqk, false, 256, 256, KS_M1, false);
-        mma_block<F16>(tm + 256, tA, false, 128, tWv, false, 128, 128, KS_M1, false);
-        if (F16) {
-          mma_block<F16>(tm + 0, tB, false, 128, tWqk, false, 256, 256, KS_M1, true);
-          mma_block<F16>(tm + 256, tB, false, 128, tWv, false, 128, 128, KS_M1, true);
-        }
+        if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWqk, false, 256, 256, KS_M1, true);
       }
       mma_commit(bar_q);
     }
@@ -522,28 +511,27 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       store_row32<F16>(sC, row, c0, v);
     }
     warp_arrive(bar_dy);
-    // M0b: dO = dY Wo^T -> [384, 512) (Wo tile as MN-major)
+    // M0b: dPG = dY Wvo^T -> [256, 368) (Wvo tile as MN-major)
     if (issuer) {
-      if (sd.wait() && sl.wait()) mma_block<F16>(tm + 384, tC, false, 128, tD, true, WO_ROWS, 128, KS_M1, false);
+      if (sd.wait() && sl.wait()) mma_block<F16>(tm + 256, tC, false, 128, tD, true, WO_ROWS, WO_ROWS, KS_M1, false);
       mma_commit(bar);
     }
-    // P1: Q -> A, K -> B once M0a is done (G is dead); V -> C, dO -> D once
-    // M0b is done (dY and Wo are dead)
+    // P1: Q -> B, K -> E once M0a is done (G_lo is dead; G stays in A); dPG
+    // -> D once M0b is done (Wvo is dead; its columns past 112 are never read)
     sq.wait();
     tmem_ld32(tm + lane_off + 0 + c0, v);
-    store_row32<F16>(sA, row, c0, v);
-    tmem_ld32(tm + lane_off + 128 + c0, v);
     store_row32<F16>(sB, row, c0, v);
+    tmem_ld32(tm + lane_off + 128 + c0, v);
+    store_row32<F16>(sE, row, c0, v);
     sy.wait();
     tmem_ld32(tm + lane_off + 256 + c0, v);
-    store_row32<F16>(sC, row, c0, v);
-    tmem_ld32(tm + lane_off + 384 + c0, v);
     store_row32<F16>(sD, row, c0, v);
     handoff();
-    // M1: S = Q K^T -> [384,512) ; dP = dO V^T -> [0,128)
+    // M1: S = Q K^T -> [384,512) ; dP = dPG [G 1 1]^T -> [0,128) (the ones
+    // columns of G give the row-sum term dPG_j,M1 + dPG_j,M1+1 of every key)
     if (issuer) {
-      mma_block<F16>(tm + 384, tA, false, 128, tB, false, 128, 128, 8, false);
-      mma_block<F16>(tm + 0, tD, false, 128, tC, false, 128, 128, 8, false);
+      mma_block<F16>(tm + 384, tB, false, 128, tE, false, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tD, false, 128, tA, false, 128, 128, KS_M1, false);
     }
     commit_and_sync(sy, issuer);
     // P2: softmax adjoint over this thread's 32 keys, with the row max and
@@ -555,13 +543,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     // of dE/drhat and dE/dw stay in registers until slot C is free.
     float4 rpart, cpart[2];
     {
-      const RowXchg xr(sC, row, part, lane, quad);  // V is dead after dP
+      const RowXchg xr(sC, row, part, lane, quad);  // dY is dead after dPG
       const uint32_t tS = tm + lane_off + 384 + c0, tP = tm + lane_off + 0 + c0;
       const float4 kj = s_key[row];
       const float wj = kj.w;
       const float mx = sst.x, inv = sst.y;
       // A and the gate cosine c of this thread's keys, kept in the dead K and
-      // V accumulator columns for the main pass
+      // dPG accumulator columns for the main pass
       const uint32_t tAw = tm + lane_off + 128 + c0, tCs = tm + lane_off + 256 + c0;
       float wsum = 0.f;
       if (c0 < nn) {
@@ -649,27 +637,25 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       tmem_wait_st();
     }
     handoff();
-    // M2: dV = P^T dO -> [128,256)
-    if (issuer) mma_block<F16>(tm + 128, tC, true, 128, tD, true, 128, 128, 8, false);
+    // M2: P^T dPG -> [128, 240) (kept in TMEM until P5)
+    if (issuer) mma_block<F16>(tm + 128, tC, true, 128, tD, true, 128, WO_ROWS, 8, false);
     commit_and_sync(sy, issuer);
     tmem_ld32(tm + lane_off + 384 + c0, v);  // dS
     store_row32<F16>(sC, row, c0, v);
     handoff();
     // M3: dQ = dS K -> [0,128) ; dK = dS^T Q -> [256,384)
     if (issuer) {
-      mma_block<F16>(tm + 0, tC, false, 128, tB, true, 128, 128, 8, false);
-      mma_block<F16>(tm + 256, tC, true, 128, tA, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 0, tC, false, 128, tE, true, 128, 128, 8, false);
+      mma_block<F16>(tm + 256, tC, true, 128, tB, true, 128, 128, 8, false);
     }
     commit_and_sync(sy, issuer);
-    // P4: dQ -> B, dK -> A, dV -> D; the row and column parts -> slot C
+    // P4: dQ -> B, dK -> A (G is dead); the row and column parts -> slot C
     // (dS is dead): [quadrant][128 keys] column parts, then [quarter][128
     // rows] row parts, float4 (x, y, z, w) each
     tmem_ld32(tm + lane_off + 0 + c0, v);
     store_row32<F16>(sB, row, c0, v);
     tmem_ld32(tm + lane_off + 256 + c0, v);
     store_row32<F16>(sA, row, c0, v);
-    tmem_ld32(tm + lane_off + 128 + c0, v);
-    store_row32<F16>(sD, row, c0, v);
     float4* parts = reinterpret_cast<float4*>(sC);
     if (lane < 16) {
       parts[quad * 128 + c0 + lane] = cpart[0];
@@ -677,11 +663,10 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     }
     parts[512 + part * 128 + row] = rpart;
     handoff();
-    // M4: dG = dQ Wq^T + dK Wk^T + dV Wv^T -> [384, 496)
+    // M4: dQ Wq^T + dK Wk^T -> [384, 496)
     if (issuer) {
       mma_block<F16>(tm + 384, tB, false, 128, tWqk, true, 256, WO_ROWS, 8, false);
       mma_block<F16>(tm + 384, tA, false, 128, tWk, true, 256, WO_ROWS, 8, true);
-      mma_block<F16>(tm + 384, tD, false, 128, tWv, true, 128, WO_ROWS, 8, true);
       mma_commit(bar);
     }
     // while M4 runs: dZ for the residual, and dgeo of this atom (key `tid`:
@@ -714,21 +699,23 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       *dg = cur;
     }
     sy.wait();
-    // Slot D is free: the next atom's Wo copy
+    // Slot D is free: the next atom's Wvo copy
     if (issuer && next < a.n) {
       mbar_expect_tx(bar_ld, WO_TILE);
       bulk_g2s(sD, wo_img, WO_TILE, bar_ld);
     }
-    // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + dV Wv^T), in place, 16 columns at a time
+    // P5: dG_l = dZ + (dQ Wq^T + dK Wk^T + P^T dPG), in place, 16 columns at a time
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
+      float u[16];
       tmem_ld16(tm + lane_off + 384 + c0 + h, v);
+      tmem_ld16(tm + lane_off + 128 + c0 + h, u);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = c0 + h + 4 * q, i = 4 * q;
         float4& gq = g[(h >> 2) + q];
         if (c < a.m1) {
-          gq.x += v[i]; gq.y += v[i + 1]; gq.z += v[i + 2]; gq.w += v[i + 3];
+          gq.x += v[i] + u[i]; gq.y += v[i + 1] + u[i + 1]; gq.z += v[i + 2] + u[i + 2]; gq.w += v[i + 3] + u[i + 3];
           dg4[(c >> 2) * NP + row] = gq;
         }
       }
@@ -774,13 +761,15 @@ int sm_count_dev(int dev) {
   return c > 0 ? c : 1;
 }
 
-// Build the swizzled shared-memory image of one layer's weights:
-// [Wq; Wk] as a [256 out][128 in] K-major tile, Wv as a [128 out][128 in]
-// one (in = M1 padded with zeros), Wo as a [112 out][128 in] one and the
-// 16-bit rounding residue of Wo in the same layout.  Inputs M1 and M1 + 1 of Wq,
-// Wk, Wv hold the 16-bit high and low parts of the biases bq, bk, bv: the
-// kernels set the layer input's columns M1 and M1 + 1 to 1, so the products
-// carry the biases (to about 22 bits in FP16, 16 in BF16).
+// Build the swizzled shared-memory image of one layer's weights: [Wq; Wk]
+// as a [256 out][128 in] K-major tile (in = M1 padded with zeros), then
+// Wvo = [Wv Wo; (bv Wo)_hi; (bv Wo)_lo] (formed in FP64) as a [112 out][128
+// in] tile and the 16-bit rounding residue of Wvo in the same layout.  Inputs
+// M1 and M1 + 1 of Wq, Wk hold the 16-bit high and low parts of the biases
+// bq, bk: the kernels set the layer input's columns M1 and M1 + 1 to 1, so the
+// products carry the biases (to about 22 bits in FP16, 16 in BF16); the same
+// columns of P G are then the row sums of P, which rows M1 and M1 + 1 of Wvo
+// turn into rowsum(P) bv Wo.
 std::vector<uint8_t> layer_image(const std::vector<double>* Ws[3], const std::vector<double>* bs[3],
                                  const std::vector<double>& Wo, int m1, int A, bool f16) {
   std::vector<uint8_t> img(WIMG, 0);
@@ -796,24 +785,33 @@ std::vector<uint8_t> layer_image(const std::vector<double>* Ws[3], const std::ve
       memcpy(tile + sw128_offset(r, c, R), &h, 2);
     }
   };
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < 2; ++t) {
     // Wq and Wk form one 256-row tile (outputs 0-127: Q, 128-255: K), so that
-    // [Q K] is one N = 256 product; Wv is a 128-row tile after it
-    uint8_t* tile = img.data() + (t < 2 ? 0 : 2 * TILE);
-    const int R = t < 2 ? 256 : 128, r0 = t == 1 ? 128 : 0;
+    // [Q K] is one N = 256 product
+    const int r0 = t == 1 ? 128 : 0;
     for (int f = 0; f < A; ++f) {
-      for (int m = 0; m < m1; ++m) put(tile, r0 + f, m, R, (*Ws[t])[(size_t)m * A + f]);
+      for (int m = 0; m < m1; ++m) put(img.data(), r0 + f, m, 256, (*Ws[t])[(size_t)m * A + f]);
       const double b = (*bs[t])[f], hi = r16(b);
-      put(tile, r0 + f, m1, R, hi);
-      put(tile, r0 + f, m1 + 1, R, b - hi);
+      put(img.data(), r0 + f, m1, 256, hi);
+      put(img.data(), r0 + f, m1 + 1, 256, b - hi);
     }
   }
-  for (int m = 0; m < m1; ++m)
-    for (int f = 0; f < A; ++f) {
-      const double x = Wo[(size_t)f * m1 + m];
-      put(img.data() + 3 * TILE, m, f, WO_ROWS, x);
-      put(img.data() + 3 * TILE + WO_TILE, m, f, WO_ROWS, x - r16(x));
+  const std::vector<double>& Wv = *Ws[2];
+  const std::vector<double>& bv = *bs[2];
+  for (int c = 0; c < m1; ++c) {
+    for (int p = 0; p < m1; ++p) {
+      double x = 0.0;
+      for (int f = 0; f < A; ++f) x += Wv[(size_t)p * A + f] * Wo[(size_t)f * m1 + c];
+      put(img.data() + WV_OFF, c, p, WO_ROWS, x);
+      put(img.data() + WV_OFF + WO_TILE, c, p, WO_ROWS, x - r16(x));
     }
+    double b = 0.0;
+    for (int f = 0; f < A; ++f) b += bv[f] * Wo[(size_t)f * m1 + c];
+    const double bh = r16(b), bl = b - bh;
+    put(img.data() + WV_OFF, c, m1, WO_ROWS, bh);
+    put(img.data() + WV_OFF, c, m1 + 1, WO_ROWS, r16(bl));
+    put(img.data() + WV_OFF + WO_TILE, c, m1 + 1, WO_ROWS, bl - r16(bl));
+  }
   return img;
 }
 
