@@ -74,7 +74,8 @@ def _args():
     ap.add_argument("--natoms", type=int, default=NATOMS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=3072, help="oracle centres timed for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=12288,
+                    help="oracle centres timed for cpu_baseline (about 11 s on 16 cores)")
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
     ap.add_argument("--md-steps", type=int, default=1000, help="graph-captured velocity-Verlet steps to time (0: skip)")
     ap.add_argument("--no-student", action="store_true", help="skip the distilled-student line")
@@ -671,11 +672,13 @@ def run_ours(a):
         "config": {"workload": workload(n), "model": model_desc, "natoms": n, "global_batch": ws * n,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "per-step working set is several GB of intermediates, far above the 129 MB L2",
-                   "arithmetic": {"fp16x": "attention layers on tcgen05: FP16 operands, two-term splits of G, P, V; "
+                   "arithmetic": {"fp16x": "attention layers, embedding and fitting nets on tcgen05: FP16 operands, "
+                                           "two-term splits of G, P and the weights (Y = P [G 1] [Wv Wo; bv Wo]); "
                                            "FP32 accumulation; FP64 energy / virial sums",
-                                  "bf16x": "attention layers and fitting net on tcgen05: BF16 operands with two-term "
-                                           "splits of both operands, FP32 accumulation; FP64 energy / virial sums",
-                                  "bf16": "attention layers on tcgen05: BF16 operands, FP32 accumulation",
+                                  "bf16x": "attention layers, embedding and fitting nets on tcgen05: BF16 operands with "
+                                           "two-term splits of both operands, FP32 accumulation; FP64 energy / "
+                                           "virial sums",
+                                  "bf16": "attention layers on tcgen05: plain BF16 operands, FP32 accumulation",
                                   "fp32": "FP32 SIMT"}[head]},
         "clocks": r["clocks"],
         "e2e": {"value": job_rate(ws, n, e2e_steps, e2e_s), "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
