@@ -107,3 +107,26 @@ def test_bf16x_without_attention(lib, water):
     assert frmse <= 1e-3
     m.close()
 
+
+
+@pytest.mark.parametrize("shape", ["width256_m1_100", "width128_m1_128"])
+def test_bf16x_mixed_widths(lib, water, shape):
+    """The cores' two branches on the other embedding widths: attention width
+    256 over M1 = 100 (two feature halves; the row-sum column inside the MMA
+    width) and width 128 over M1 = 128 (one half; [P G, rowsum P] reaching
+    past 128 columns), each with biases and descriptor statistics."""
+    import dataclasses
+
+    if shape == "width256_m1_100":
+        cfg = dataclasses.replace(synth.DEFAULT_CONFIG, attn_layers=2, attn_dim=256)
+    else:
+        cfg = dataclasses.replace(synth.PAPER_SIZE_CONFIG, attn_layers=2, attn_dim=128)
+    w = synth.make_weights(cfg, seed=23, bias_scale=0.05, stats=True)
+    om = OracleModel.from_numpy(cfg, w)
+    m = lib.DPA1(weight_file(cfg, w, shape), precision="bf16x")
+    try:
+        _check(m, om, *water, tag=shape)
+        coord, atype, box = synth.lattice_system(400, seed=29)
+        _check(m, om, coord, atype, box, tag=shape + " lattice")
+    finally:
+        m.close()
