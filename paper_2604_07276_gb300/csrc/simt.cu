@@ -10,39 +10,55 @@ namespace dpa1 {
 static int sm_count();
 
 // ----------------------------------------------------------------- FP32 GEMM
-// 128x128 tile, K step 8, 256 threads with 8x8 outputs each (two 4x4
-// quadrants 64 apart), shared-memory double buffering.
-template <int EPI>
-__global__ void __launch_bounds__(256)
+// C = epi(A B + bias (+R)), A [M][K], B [K][N] row-major.  128x128 tile, K
+// step 16, 256 threads with 8x8 outputs each (two 4x4 quadrants 64 apart, so
+// that the 16 threads of a half warp read 16 consecutive float4 of a shared
+// row), shared-memory double buffering with the next tile held in registers.
+// VEC: 16-byte global loads and stores (every leading dimension, K and N
+// multiples of 4, the arrays 16-byte aligned); otherwise 4-byte ones.
+constexpr int GBK = 16, GLD = 128 + 4;
+
+template <int EPI, bool VEC>
+__global__ void __launch_bounds__(256, 2)
 k_sgemm128(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
            const float* __restrict__ bias, const float* __restrict__ R, int ldr, float* __restrict__ C, int ldc,
            int M, int N, int K) {
-  __shared__ __align__(16) float As[2][8][128 + 4];
-  __shared__ __align__(16) float Bs[2][8][128 + 4];
+  __shared__ __align__(16) float As[2][GBK][GLD];  // k-major: As[k][row]
+  __shared__ __align__(16) float Bs[2][GBK][GLD];  // Bs[k][column]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const long long m0 = (long long)blockIdx.x * 128;
   const int n0 = blockIdx.y * 128;
-  const int ar = tid >> 1, ak = (tid & 1) * 4;   // A: row, first k of 4
-  const int bk = tid >> 5, bc = (tid & 31) * 4;  // B: k, first column of 4
-  float ra[4], rb[4];
+  const int ar = tid >> 1, ak = (tid & 1) * 8;   // A: row, first of its 8 k
+  const int bk = tid >> 4, bc = (tid & 15) * 8;  // B: k, first of its 8 columns
+  float ra[8], rb[8];
   auto load = [&](int k0) {
     const long long gm = m0 + ar;
+    const int gka = k0 + ak, gkb = k0 + bk;
+    if (VEC) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gk = k0 + ak + q;
-      ra[q] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
-    }
-    const int gk = k0 + bk;
+      for (int h = 0; h < 2; ++h) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gm < M && gka + 4 * h < K) x = *reinterpret_cast<const float4*>(A + gm * lda + gka + 4 * h);
+        ra[4 * h] = x.x; ra[4 * h + 1] = x.y; ra[4 * h + 2] = x.z; ra[4 * h + 3] = x.w;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int gn = n0 + bc + 4 * h;
+        if (gkb < K && gn < N) y = *reinterpret_cast<const float4*>(B + (long long)gkb * ldb + gn);
+        rb[4 * h] = y.x; rb[4 * h + 1] = y.y; rb[4 * h + 2] = y.z; rb[4 * h + 3] = y.w;
+      }
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gn = n0 + bc + q;
-      rb[q] = (gk < K && gn < N) ? B[(long long)gk * ldb + gn] : 0.f;
+      for (int q = 0; q < 8; ++q) {
+        const int gk = gka + q, gn = n0 + bc + q;
+        ra[q] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
+        rb[q] = (gkb < K && gn < N) ? B[(long long)gkb * ldb + gn] : 0.f;
+      }
     }
   };
   auto store = [&](int buf) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) As[buf][ak + q][ar] = ra[q];
+    for (int q = 0; q < 8; ++q) As[buf][ak + q][ar] = ra[q];
     *reinterpret_cast<float4*>(&Bs[buf][bk][bc]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *reinterpret_cast<float4*>(&Bs[buf][bk][bc + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
   };
   float acc[8][8];
 #pragma unroll
@@ -53,11 +69,11 @@ k_sgemm128(const float* __restrict__ A, int lda, const float* __restrict__ B, in
   store(0);
   __syncthreads();
   int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += 8) {
-    const bool more = k0 + 8 < K;
-    if (more) load(k0 + 8);
+  for (int k0 = 0; k0 < K; k0 += GBK) {
+    const bool more = k0 + GBK < K;
+    if (more) load(k0 + GBK);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < GBK; ++k) {
       const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
       const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
@@ -80,30 +96,72 @@ k_sgemm128(const float* __restrict__ A, int lda, const float* __restrict__ B, in
     const long long m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-      if (n >= N) continue;
-      const float v = acc[i][j];
-      float* c = C + m * ldc + n;
-      if (EPI == EPI_BIAS) *c = v + (bias ? bias[n] : 0.f);
-      if (EPI == EPI_TANH) *c = tanhf(v + (bias ? bias[n] : 0.f));
-      if (EPI == EPI_RES_TANH) *c = R[m * ldr + n] + tanhf(v + (bias ? bias[n] : 0.f));
-      if (EPI == EPI_ACCUM) *c = *c + v;
-      if (EPI == EPI_RES) *c = R[m * ldr + n] + v;
+    for (int h = 0; h < 2; ++h) {
+      const int nq = n0 + h * 64 + tx * 4;  // first of this thread's 4 columns
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = nq + j;
+        float x = acc[i][4 * h + j];
+        if (n < N) {
+          if (EPI == EPI_BIAS || EPI == EPI_TANH || EPI == EPI_RES_TANH) x += bias ? bias[n] : 0.f;
+          if (EPI == EPI_TANH || EPI == EPI_RES_TANH) x = tanhf(x);
+        }
+        v[j] = x;
+      }
+      if (VEC) {
+        if (nq < N) {  // N % 4 == 0: the 4 columns are all in range
+          float4 o = make_float4(v[0], v[1], v[2], v[3]);
+          if (EPI == EPI_RES_TANH || EPI == EPI_RES) {
+            const float4 r = *reinterpret_cast<const float4*>(R + m * ldr + nq);
+            o.x += r.x; o.y += r.y; o.z += r.z; o.w += r.w;
+          }
+          float4* c = reinterpret_cast<float4*>(C + m * ldc + nq);
+          if (EPI == EPI_ACCUM) {
+            const float4 cc = *c;
+            o.x += cc.x; o.y += cc.y; o.z += cc.z; o.w += cc.w;
+          }
+          *c = o;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int n = nq + j;
+          if (n >= N) continue;
+          float* c = C + m * ldc + n;
+          if (EPI == EPI_RES_TANH || EPI == EPI_RES) *c = R[m * ldr + n] + v[j];
+          else if (EPI == EPI_ACCUM) *c = *c + v[j];
+          else *c = v[j];
+        }
+      }
     }
   }
+}
+
+template <int EPI>
+static void sgemm_launch(dim3 grid, bool vec, const float* A, int lda, const float* B, int ldb, const float* bias,
+                         const float* R, int ldr, float* C, int ldc, int M, int N, int K, cudaStream_t st) {
+  if (vec)
+    k_sgemm128<EPI, true><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K);
+  else
+    k_sgemm128<EPI, false><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K);
 }
 
 void gemm_f32(const float* A, int lda, const float* B, int ldb, const float* bias, const float* R, int ldr,
               float* C, int ldc, int M, int N, int K, int epi, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + 127) / 128));
+  const bool res = epi == EPI_RES || epi == EPI_RES_TANH;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
+                         reinterpret_cast<uintptr_t>(C) | (res ? reinterpret_cast<uintptr_t>(R) : 0);
+  const bool vec = (addr & 15) == 0 && lda % 4 == 0 && ldb % 4 == 0 && ldc % 4 == 0 && (!res || ldr % 4 == 0) &&
+                   N % 4 == 0 && K % 4 == 0;
   switch (epi) {
-    case EPI_BIAS: k_sgemm128<EPI_BIAS><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    case EPI_TANH: k_sgemm128<EPI_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    case EPI_RES_TANH: k_sgemm128<EPI_RES_TANH><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    case EPI_ACCUM: k_sgemm128<EPI_ACCUM><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
-    default: k_sgemm128<EPI_RES><<<grid, 256, 0, st>>>(A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K); break;
+    case EPI_BIAS: sgemm_launch<EPI_BIAS>(grid, vec, A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K, st); break;
+    case EPI_TANH: sgemm_launch<EPI_TANH>(grid, vec, A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K, st); break;
+    case EPI_RES_TANH: sgemm_launch<EPI_RES_TANH>(grid, vec, A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K, st); break;
+    case EPI_ACCUM: sgemm_launch<EPI_ACCUM>(grid, vec, A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K, st); break;
+    default: sgemm_launch<EPI_RES>(grid, vec, A, lda, B, ldb, bias, R, ldr, C, ldc, M, N, K, st); break;
   }
   note_launch();
 }
@@ -166,13 +224,23 @@ __device__ __forceinline__ void embed_forward(float* sm, int cnt, const float* b
     sm[S::H1 + r * (E0 + 1) + p] = r < cnt ? tanhf(fmaf(sm[S::X + r], sm[S::W0 + p], b)) : 0.f;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
-    const int r = idx / E1, b = idx % E1;
-    const float* h1 = sm + S::H1 + r * (E0 + 1);
-    float z = sm[S::B1 + b];
+  for (int idx = threadIdx.x; idx < (EROWS / 4) * E1; idx += ETHREADS) {  // four rows per thread
+    const int r0 = (idx / E1) * 4, b = idx % E1;
+    const float* h1 = sm + S::H1 + r0 * (E0 + 1);
+    float z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) z[u] = sm[S::B1 + b];
 #pragma unroll 5
-    for (int p = 0; p < E0; ++p) z = fmaf(h1[p], sm[S::W1 + p * E1 + b], z);
-    sm[S::H2 + r * (E1 + 1) + b] = r < cnt ? skip_in<E0, E1>(h1, b) + tanhf(z) : 0.f;
+    for (int p = 0; p < E0; ++p) {
+      const float w = sm[S::W1 + p * E1 + b];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) z[u] = fmaf(h1[u * (E0 + 1) + p], w, z[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + u;
+      sm[S::H2 + r * (E1 + 1) + b] = r < cnt ? skip_in<E0, E1>(h1 + u * (E0 + 1), b) + tanhf(z[u]) : 0.f;
+    }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < (EROWS / 4) * E2; idx += ETHREADS) {
@@ -246,23 +314,35 @@ __global__ void __launch_bounds__(ETHREADS) k_embed_bwd(EmbedArgs a) {
     sm[S::Z + r * (E2 + 1) + c] = dz;
   }
   __syncthreads();
-  // dH2[r][b] = skip^T(g)[b] + sum_c W2[b][c] dZ3[r][c]
-  for (int idx = threadIdx.x; idx < EROWS * E1; idx += ETHREADS) {
-    const int r = idx / E1, b = idx % E1;
-    float s = 0.f;
-    if (r < cnt) {
-      const float* dz = sm + S::Z + r * (E2 + 1);
+  // dH2[r][b] = skip^T(g)[b] + sum_c W2[b][c] dZ3[r][c], four rows per
+  // thread so that each weight load serves four products (dZ3 is zero on
+  // rows past cnt)
+  for (int idx = threadIdx.x; idx < (EROWS / 4) * E1; idx += ETHREADS) {
+    const int r0 = (idx / E1) * 4, b = idx % E1;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r0 < cnt) {
+      const float* dz = sm + S::Z + r0 * (E2 + 1);
       const float* w2 = sm + S::W2 + b * S::P2;
 #pragma unroll 4
-      for (int c = 0; c < E2; ++c) s = fmaf(w2[c], dz[c], s);
+      for (int c = 0; c < E2; ++c) {
+        const float w = w2[c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fmaf(w, dz[u * (E2 + 1) + c], s[u]);
+      }
       if (E2 == E1 || E2 == 2 * E1) {
-        const int tj = a.atype[a.nlist[base + r]];
-        const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
-        const float* dg = a.dG0 + (base + r) * a.m1;
-        for (int c = b; c < E2; c += E1) s += dg[c] * (1.f + gt[c]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u;
+          if (r >= cnt) break;
+          const int tj = a.atype[a.nlist[base + r]];
+          const float* gt = a.Gt + ((size_t)ti * a.ntypes + tj) * E2;
+          const float* dg = a.dG0 + (base + r) * a.m1;
+          for (int c = b; c < E2; c += E1) s[u] += dg[c] * (1.f + gt[c]);
+        }
       }
     }
-    sm[S::DH2 + r * (E1 + 1) + b] = s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sm[S::DH2 + (r0 + u) * (E1 + 1) + b] = r0 + u < cnt ? s[u] : 0.f;
   }
   __syncthreads();
   // dZ2 = dH2 (1 - t2^2) with t2 = H2 - skip(H1)
@@ -272,21 +352,31 @@ __global__ void __launch_bounds__(ETHREADS) k_embed_bwd(EmbedArgs a) {
     sm[S::DZ2 + r * (E1 + 1) + b] = sm[S::DH2 + r * (E1 + 1) + b] * (1.f - t * t);
   }
   __syncthreads();
-  // dH1[r][p] = skip^T(dH2)[p] + sum_b W1[p][b] dZ2[r][b]; term of dx: W0[p] dH1 (1 - H1^2)
-  for (int idx = threadIdx.x; idx < EROWS * E0; idx += ETHREADS) {
-    const int r = idx / E0, p = idx % E0;
-    float s = 0.f;
-    if (r < cnt) {
-      const float* dz2 = sm + S::DZ2 + r * (E1 + 1);
+  // dH1[r][p] = skip^T(dH2)[p] + sum_b W1[p][b] dZ2[r][b]; term of dx: W0[p]
+  // dH1 (1 - H1^2); four rows per thread as above (dZ2 is zero past cnt)
+  for (int idx = threadIdx.x; idx < (EROWS / 4) * E0; idx += ETHREADS) {
+    const int r0 = (idx / E0) * 4, p = idx % E0;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r0 < cnt) {
+      const float* dz2 = sm + S::DZ2 + r0 * (E1 + 1);
       const float* w1 = sm + S::W1 + p * E1;
 #pragma unroll 5
-      for (int b = 0; b < E1; ++b) s = fmaf(w1[b], dz2[b], s);
-      if (E1 == E0 || E1 == 2 * E0)
-        for (int b = p; b < E1; b += E0) s += sm[S::DH2 + r * (E1 + 1) + b];
-      const float h1 = sm[S::H1 + r * (E0 + 1) + p];
-      s = s * (1.f - h1 * h1) * sm[S::W0 + p];
+      for (int b = 0; b < E1; ++b) {
+        const float w = w1[b];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fmaf(w, dz2[u * (E1 + 1) + b], s[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        if (E1 == E0 || E1 == 2 * E0)
+          for (int b = p; b < E1; b += E0) s[u] += sm[S::DH2 + r * (E1 + 1) + b];
+        const float h1 = sm[S::H1 + r * (E0 + 1) + p];
+        s[u] = s[u] * (1.f - h1 * h1) * sm[S::W0 + p];
+      }
     }
-    sm[S::DH1 + r * (E0 + 1) + p] = s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sm[S::DH1 + (r0 + u) * (E0 + 1) + p] = r0 + u < cnt ? s[u] : 0.f;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < cnt; r += ETHREADS) {
