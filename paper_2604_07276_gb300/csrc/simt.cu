@@ -662,9 +662,9 @@ __device__ __forceinline__ float2 warp_max_pair(float2 v) {
 
 __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
-// Forward, register-tiled: 256 threads as a 16 x 16 grid.  Thread (ty, tx)
-// owns rows t_rc(ty, i) and keys t_rc(tx, jj), i, jj < 8, of S (128 x 128),
-// then the same rows and columns of each 128-column part of PG.  Q and K pass
+// Forward, register-tiled: 512 threads as a 32 x 16 grid.  Thread (ty, tx)
+// owns rows 4 ty + i (i < 4) and keys t_rc(tx, jj) (jj < 8) of S (128 x
+// 128), then the same rows and columns of each 128-column part of PG.  Q and K pass
 // through shared memory feature-major, 128 features at a time; P stays
 // row-major and [G 1] comes in 128-column parts, key-major.  S sums over the
 // features and PG over the keys in order, as a plain loop would.
@@ -679,7 +679,7 @@ __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b
 // a few atoms.  Summing the exact layer input G instead leaves only the
 // rounding of the cancelling sum itself (a CPU emulation of both forms on the
 // 15,668-atom box: force RMSE 7.5e-6 -> 2.4e-6 eV/A).
-constexpr int FT = 256;        // threads of the forward and the adjoint
+constexpr int FTF = 512;       // threads of the forward and the adjoint (4 x 8 tiles)
 constexpr int TLD = NP + 4;    // row stride of their shared tiles (16-byte rows)
 
 // Row (or column) i < 8 of thread coordinate t < 16: the quarter tiles
@@ -702,35 +702,47 @@ __device__ __forceinline__ void fm_store(float* T, int j, int f, float4 v) {
   T[(f + 2) * TLD + j] = v.z; T[(f + 3) * TLD + j] = v.w;
 }
 
-// The 8 x 8 outer-product step of a register tile: acc[i][jj] += a[i] b[jj],
-// with a = (A[r0 .. r0 + 3], A[r0 + 64 .. r0 + 67]) and the same for b.
-__device__ __forceinline__ void tile_fma(float (&acc)[8][8], const float* A, int ra, const float* B, int rb) {
+// Row i < TR of thread row coordinate ty: with TR = 8 (16 thread rows) the
+// quarter tiles of t_rc; with TR = 4 (32 thread rows) rows 4 ty .. 4 ty + 3.
+template <int TR>
+__device__ __forceinline__ int r_of(int ty, int i) { return TR == 8 ? t_rc(ty, i) : 4 * ty + i; }
+
+// The TR x 8 outer-product step of a register tile: acc[i][jj] += a[i] b[jj],
+// with a = (A[ra .. ra + 3] (, A[ra + 64 .. ra + 67] for TR = 8)) and b =
+// (B[rb .. rb + 3], B[rb + 64 .. rb + 67]).
+template <int TR>
+__device__ __forceinline__ void tile_fma(float (&acc)[TR][8], const float* A, int ra, const float* B, int rb) {
+  float av[TR];
   const float4 a0 = *reinterpret_cast<const float4*>(A + ra);
-  const float4 a1 = *reinterpret_cast<const float4*>(A + ra + 64);
+  av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+  if constexpr (TR == 8) {
+    const float4 a1 = *reinterpret_cast<const float4*>(A + ra + 64);
+    av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+  }
   const float4 b0 = *reinterpret_cast<const float4*>(B + rb);
   const float4 b1 = *reinterpret_cast<const float4*>(B + rb + 64);
-  const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
   const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(av[i], bv[jj], acc[i][jj]);
 }
 
-// acc[i][jj] += sum over k0 .. k0 + 3 of A[t_rc(ty, i)][k] B[k][t_rc(tx, jj)]
+// acc[i][jj] += sum over k0 .. k0 + 3 of A[r_of(ty, i)][k] B[k][t_rc(tx, jj)]
 // (A row-major, B key-major, both with row stride TLD).
-__device__ __forceinline__ void tile_fma4(float (&acc)[8][8], const float* A, const float* B, int k0, int ty,
+template <int TR>
+__device__ __forceinline__ void tile_fma4(float (&acc)[TR][8], const float* A, const float* B, int k0, int ty,
                                           int tx) {
-  float4 pa[8];
+  float4 pa[TR];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) pa[i] = *reinterpret_cast<const float4*>(A + t_rc(ty, i) * TLD + k0);
+  for (int i = 0; i < TR; ++i) pa[i] = *reinterpret_cast<const float4*>(A + r_of<TR>(ty, i) * TLD + k0);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const float4 v0 = *reinterpret_cast<const float4*>(B + (k0 + u) * TLD + 4 * tx);
     const float4 v1 = *reinterpret_cast<const float4*>(B + (k0 + u) * TLD + 64 + 4 * tx);
     const float vb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < TR; ++i) {
       const float p = u == 0 ? pa[i].x : u == 1 ? pa[i].y : u == 2 ? pa[i].z : pa[i].w;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(p, vb[jj], acc[i][jj]);
@@ -738,7 +750,7 @@ __device__ __forceinline__ void tile_fma4(float (&acc)[8][8], const float* A, co
   }
 }
 
-// Row t_rc(ty, i) of a register tile -> dst row (columns 4 tx .. and 64 + 4
+// One row of a register tile -> dst row (columns 4 tx .. and 64 + 4
 // tx .. from col0, each float4 only below ncols).
 __device__ __forceinline__ void tile_store_row(float* dst, const float* accrow, int col0, int tx, int ncols) {
   if (col0 + 4 * tx < ncols)
@@ -748,7 +760,7 @@ __device__ __forceinline__ void tile_store_row(float* dst, const float* accrow, 
 }
 
 template <int A>
-__global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
+__global__ void __launch_bounds__(FTF, 1) k_attn_fwd_f32(AttnArgs a, float scale) {
   extern __shared__ float sm[];
   float* X = sm;                 // [128][TLD]: Q chunk (feature-major), then P (row-major)
   float* Y = X + 128 * TLD;      // [128][TLD]: K chunk (feature-major), then a part of [G 1] (key-major)
@@ -760,19 +772,19 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     __syncthreads();  // the previous atom is done with every shared array
-    for (int r = tid; r < NP; r += FT) {
+    for (int r = tid; r < NP; r += FTF) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
       w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
-    float s[8][8];
+    float s[4][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) s[i][jj] = 0.f;
     const bool live = 4 * ty < nn && 4 * tx < nn;
     for (int c0 = 0; c0 < A; c0 += 128) {
       if (c0 > 0) __syncthreads();  // the previous chunk's products are done
-      for (int idx = tid; idx < NP * 32; idx += FT) {
+      for (int idx = tid; idx < NP * 32; idx += FTF) {
         int j, f;
         fm_pos(idx, j, f);
         float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
@@ -785,14 +797,14 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
       }
       __syncthreads();
       if (live)
-        for (int f = 0; f < 128; ++f) tile_fma(s, X, f * TLD + 4 * ty, Y, f * TLD + 4 * tx);
+        for (int f = 0; f < 128; ++f) tile_fma<4>(s, X, f * TLD + 4 * ty, Y, f * TLD + 4 * tx);
     }
     __syncthreads();  // X and Y are free: P goes to X
     // softmax per row over the 16 threads of a half warp (every lane takes
     // part in the shuffles; rows and keys past nnei come out zero)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int j = t_rc(ty, i);
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * ty + i;
       const float4 rj = rws[j];
       const float2 wj = w2s[j];
       float2 lp[8], mx = make_float2(-3.0e38f, 0.f);
@@ -837,7 +849,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
     const int nn4 = (nn + 3) & ~3;
     for (int c0 = 0; c0 < a.ldpg; c0 += 128) {
       if (c0 > 0) __syncthreads();  // the previous part's products are done
-      for (int idx = tid; idx < NP * 32; idx += FT) {
+      for (int idx = tid; idx < NP * 32; idx += FTF) {
         const int k = idx >> 5, f = c0 + 4 * (idx & 31);
         float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < nn) {
@@ -847,22 +859,22 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
         *reinterpret_cast<float4*>(Y + k * TLD + f - c0) = vv;
       }
       __syncthreads();  // P (first part) and this part of [G 1] are in place
-      float acc[8][8];
+      float acc[4][8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
       if (4 * ty < nn)
-        for (int k = 0; k < nn4; k += 4) tile_fma4(acc, X, Y, k, ty, tx);
+        for (int k = 0; k < nn4; k += 4) tile_fma4<4>(acc, X, Y, k, ty, tx);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tile_store_row(a.PG + (base + t_rc(ty, i)) * a.ldpg, acc[i], c0, tx, a.ldpg);
+      for (int i = 0; i < 4; ++i) tile_store_row(a.PG + (base + 4 * ty + i) * a.ldpg, acc[i], c0, tx, a.ldpg);
     }
   }
 }
 
 // Adjoint of one attention layer for one centre, register-tiled like the
-// forward (256 threads as a 16 x 16 grid; thread (ty, tx) owns rows t_rc(ty,
-// i) and keys or columns t_rc(tx, jj) of each 128 x 128 product),
+// forward (512 threads as a 32 x 16 grid; thread (ty, tx) owns rows 4 ty + i
+// (i < 4) and keys or columns t_rc(tx, jj) (jj < 8) of each 128 x 128 product),
 // in the form of the forward's output Y = [P G, rowsum P] [Wv Wo; bv Wo] +
 // bo: with dPG = dE/d[P G, rowsum P] (a GEMM of dY with [Wv Wo; bv Wo]^T),
 //   dP_jk = sum_c dPG_jc G_kc + dPG_j,m1        (the values V never appear)
@@ -872,7 +884,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_fwd_f32(AttnArgs a, float scale)
 // shared memory (row-major), where the three last products read them.  The
 // column parts are summed over the 16 row groups in a fixed order.
 template <int A>
-__global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
+__global__ void __launch_bounds__(FTF, 1) k_attn_bwd_f32(AttnArgs a, float scale) {
   extern __shared__ float sm[];
   float* B0 = sm;               // [128][TLD] operand chunks
   float* B1 = B0 + 128 * TLD;   // [128][TLD] K / G chunk, then dS (row-major)
@@ -886,20 +898,20 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
     __syncthreads();  // the previous atom is done with every shared array
-    for (int r = tid; r < NP; r += FT) {
+    for (int r = tid; r < NP; r += FTF) {
       rws[r] = r < nn ? reinterpret_cast<const float4*>(a.rw)[base + r] : make_float4(0.f, 0.f, 0.f, 0.f);
       w2s[r] = split_pair(r < nn ? a.w64[base + r] : 0.0);
     }
     const bool live = 4 * ty < nn && 4 * tx < nn;
-    float s[8][8], dp[8][8];
+    float s[4][8], dp[4][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) { s[i][jj] = 0.f; dp[i][jj] = 0.f; }
     // S = Q K^T over feature chunks of 128 (feature-major in B0, B1)
     for (int c0 = 0; c0 < A; c0 += 128) {
       if (c0 > 0) __syncthreads();
-      for (int idx = tid; idx < NP * 32; idx += FT) {
+      for (int idx = tid; idx < NP * 32; idx += FTF) {
         int j, f;
         fm_pos(idx, j, f);
         float4 qv = make_float4(0.f, 0.f, 0.f, 0.f), kv = qv;
@@ -912,12 +924,12 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       }
       __syncthreads();
       if (live)
-        for (int f = 0; f < 128; ++f) tile_fma(s, B0, f * TLD + 4 * ty, B1, f * TLD + 4 * tx);
+        for (int f = 0; f < 128; ++f) tile_fma<4>(s, B0, f * TLD + 4 * ty, B1, f * TLD + 4 * tx);
     }
     __syncthreads();
     // dP = dPG G^T over the m1 columns (feature-major: dPG in B0, G in B1;
     // m1 % 4 == 0)
-    for (int idx = tid; idx < NP * 32; idx += FT) {
+    for (int idx = tid; idx < NP * 32; idx += FTF) {
       int j, f;
       fm_pos(idx, j, f);
       float4 dv = make_float4(0.f, 0.f, 0.f, 0.f), gv = dv;
@@ -930,7 +942,7 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     }
     __syncthreads();
     if (live)
-      for (int f = 0; f < a.m1; ++f) tile_fma(dp, B0, f * TLD + 4 * ty, B1, f * TLD + 4 * tx);
+      for (int f = 0; f < a.m1; ++f) tile_fma<4>(dp, B0, f * TLD + 4 * ty, B1, f * TLD + 4 * tx);
     __syncthreads();  // B0 and B1 are free: dS goes to B1, P to B2, column parts to B0
     // softmax adjoint per row over the 16 threads of a half warp (every lane
     // takes part in the shuffles; rows and keys past nnei come out zero)
@@ -938,8 +950,8 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) { cw[jj] = 0.f; cx[jj] = 0.f; cy[jj] = 0.f; cz[jj] = 0.f; }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int j = t_rc(ty, i);
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * ty + i;
       const float4 rj = rws[j];
       const float2 wj = w2s[j];
       const float dpg1 = j < nn ? a.dPG[(base + j) * a.ldpg + a.m1] : 0.f;  // adjoint of rowsum P
@@ -1012,14 +1024,14 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
       }
       if (tx == 0) rowg[j] = make_float4(rx, ry, rz, rw_);
     }
-    // column parts of this thread's 8 rows -> B0 as [ty][key]
+    // column parts of this thread's 4 rows -> B0 as [ty][key] (32 x 128 float4)
     float4* colp = reinterpret_cast<float4*>(B0);
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) colp[ty * NP + t_rc(tx, jj)] = make_float4(cx[jj], cy[jj], cz[jj], cw[jj]);
     __syncthreads();
     if (tid < nn) {
       float4 acc = rowg[tid];
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < 32; ++q) {
         const float4 c = colp[q * NP + tid];
         acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
       }
@@ -1032,41 +1044,41 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     for (int c0 = 0; c0 < A; c0 += 128) {
       // dQ = dS K: K key-major in B0
       __syncthreads();
-      for (int idx = tid; idx < NP * 32; idx += FT) {
+      for (int idx = tid; idx < NP * 32; idx += FTF) {
         const int k = idx >> 5, f = 4 * (idx & 31);
         *reinterpret_cast<float4*>(B0 + k * TLD + f) =
             k < nn ? *reinterpret_cast<const float4*>(a.QK + (base + k) * ld + A + c0 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncthreads();
-      float acc[8][8];
+      float acc[4][8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
       if (4 * ty < nn)
-        for (int k = 0; k < nn4; k += 4) tile_fma4(acc, B1, B0, k, ty, tx);
+        for (int k = 0; k < nn4; k += 4) tile_fma4<4>(acc, B1, B0, k, ty, tx);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tile_store_row(a.dQK + (base + t_rc(ty, i)) * ld, acc[i], c0, tx, A);
+      for (int i = 0; i < 4; ++i) tile_store_row(a.dQK + (base + 4 * ty + i) * ld, acc[i], c0, tx, A);
       // dK = dS^T Q: Q row-major in B0
       __syncthreads();
-      for (int idx = tid; idx < NP * 32; idx += FT) {
+      for (int idx = tid; idx < NP * 32; idx += FTF) {
         const int j = idx >> 5, f = 4 * (idx & 31);
         *reinterpret_cast<float4*>(B0 + j * TLD + f) =
             j < nn ? *reinterpret_cast<const float4*>(a.QK + (base + j) * ld + c0 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncthreads();
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
       if (4 * ty < nn)
-        for (int j = 0; j < nn; ++j) tile_fma(acc, B1, j * TLD + 4 * ty, B0, j * TLD + 4 * tx);
+        for (int j = 0; j < nn; ++j) tile_fma<4>(acc, B1, j * TLD + 4 * ty, B0, j * TLD + 4 * tx);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tile_store_row(a.dQK + (base + t_rc(ty, i)) * ld + A, acc[i], c0, tx, A);
+      for (int i = 0; i < 4; ++i) tile_store_row(a.dQK + (base + 4 * ty + i) * ld + A, acc[i], c0, tx, A);
     }
     // dE/dG += P^T dPG: dPG row-major in B0 (columns below m1; m1 <= 128)
     __syncthreads();
-    for (int idx = tid; idx < NP * 32; idx += FT) {
+    for (int idx = tid; idx < NP * 32; idx += FTF) {
       const int j = idx >> 5, f = 4 * (idx & 31);
       *reinterpret_cast<float4*>(B0 + j * TLD + f) = j < nn && f < a.m1
                                                          ? *reinterpret_cast<const float4*>(a.dPG + (base + j) * a.ldpg + f)
@@ -1074,15 +1086,15 @@ __global__ void __launch_bounds__(FT, 1) k_attn_bwd_f32(AttnArgs a, float scale)
     }
     __syncthreads();
     if (4 * ty < nn && 4 * tx < a.m1) {
-      float acc[8][8];
+      float acc[4][8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.f;
-      for (int j = 0; j < nn; ++j) tile_fma(acc, B2, j * TLD + 4 * ty, B0, j * TLD + 4 * tx);
+      for (int j = 0; j < nn; ++j) tile_fma<4>(acc, B2, j * TLD + 4 * ty, B0, j * TLD + 4 * tx);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int k = t_rc(ty, i);
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * ty + i;
         if (k >= nn) continue;
         float* dgrow = a.dG + (base + k) * a.m1;
 #pragma unroll
@@ -1118,11 +1130,11 @@ static void attn_f32_launch(const AttnArgs& a, bool bwd, cudaStream_t st) {
   if (!bwd) {
     const size_t smem = sizeof(float) * (2 * 128 * TLD + 4 * NP) + sizeof(float2) * NP;
     cudaFuncSetAttribute(k_attn_fwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_attn_fwd_f32<A><<<grid, FT, smem, st>>>(a, scale);
+    k_attn_fwd_f32<A><<<grid, FTF, smem, st>>>(a, scale);
   } else {
     const size_t smem = sizeof(float) * (3 * 128 * TLD + 8 * NP) + sizeof(float2) * NP;
     cudaFuncSetAttribute(k_attn_bwd_f32<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_attn_bwd_f32<A><<<grid, FT, smem, st>>>(a, scale);
+    k_attn_bwd_f32<A><<<grid, FTF, smem, st>>>(a, scale);
   }
   note_launch();
 }
