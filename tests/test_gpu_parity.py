@@ -99,6 +99,20 @@ def test_fp32_water_rich_weights(fp32_rich, rich_model, water):
     _compare(fp32_rich, om, coord, atype, box, FP32_FORCE_RMSE, 1e-4, 1e-4)
 
 
+def test_fp32_fitting_widths_not_multiples_of_4(lib, water):
+    """Fitting widths of 30: the FP32 GEMM's 4-byte load and store path
+    (16-byte accesses need every width a multiple of 4)."""
+    cfg = dataclasses.replace(synth.DEFAULT_CONFIG, fitting=(30, 30))
+    w = synth.make_weights(cfg, seed=37, bias_scale=0.1, stats=True)
+    om = OracleModel.from_numpy(cfg, w)
+    m = lib.DPA1(weight_file(cfg, w, "fit30"), precision="fp32")
+    try:
+        coord, atype, box = water
+        _compare(m, om, coord, atype, box, FP32_FORCE_RMSE, 1e-4, 1e-4)
+    finally:
+        m.close()
+
+
 def test_fp32_lattice_ragged(fp32_model, default_model):
     cfg, w, om = default_model
     coord, atype, box = synth.lattice_system(1123, seed=31)
