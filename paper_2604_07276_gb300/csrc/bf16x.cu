@@ -488,15 +488,19 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
       if (issuer) prefetch_l2(a.G + nb * a.m1, (uint32_t)(NP * a.m1 * sizeof(float)));
     }
     float v[32];
+    // two blocks in flight: each block's loads are issued before the
+    // previous block is split into its tiles
+    float w[32];
     load_blk(a.G + base * a.m1, a.m1, nn, a.m1, v);
+    load_blk(a.QK + base * ld, ld, nn, 128, w);  // Q, first half
     store_blk_split(sGh, sGl, v);
     if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     // S = sum over the halves of Q_h K_h^T (three split products each) -> TMEM [0, 128)
 #pragma unroll 1
     for (int h = 0; h < NH; ++h) {
-      load_blk(a.QK + base * ld + h * 128, ld, nn, 128, v);
-      store_blk_split(sQh, sQl, v);
+      if (h > 0) load_blk(a.QK + base * ld + h * 128, ld, nn, 128, w);
       load_blk(a.QK + base * ld + NH * 128 + h * 128, ld, nn, 128, v);
+      store_blk_split(sQh, sQl, w);
       store_blk_split(sKh, sKl, v);
       handoff();
       if (issuer) {
@@ -771,14 +775,16 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
     float v[32], q32[32];
     // dPG (columns below m1; the row-sum adjoint, column m1, separately) and
     // G, then K and Q of the first half, in coalesced block accesses
+    // two blocks in flight: each block's loads are issued before the previous
+    // block is split into its tiles
     load_blk(a.dPG + base * a.ldpg, a.ldpg, nn, a.m1, v);
+    load_blk(a.G + base * a.m1, a.m1, nn, a.m1, q32);
     const float dpg1 = rv ? a.dPG[(base + row) * a.ldpg + a.m1] : 0.f;
     store_blk_split(T[0], T[1], v);
-    load_blk(a.G + base * a.m1, a.m1, nn, a.m1, v);
-    store_blk_split(T[2], T[3], v);
     load_blk(qk0 + AW, ld, nn, 128, v);  // K, first half
-    store_blk_split(T[5], T[6], v);
+    store_blk_split(T[2], T[3], q32);
     load_blk(qk0, ld, nn, 128, q32);  // Q, first half
+    store_blk_split(T[5], T[6], v);
     store_blk<false>(T[4], q32);
     if (tid < 128) s_key[tid] = tid < nn ? reinterpret_cast<const float4*>(a.rw)[base + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     handoff();
@@ -802,8 +808,8 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
       pti = 3;
     } else {
       load_blk(qk0 + 128, ld, nn, 128, q32);  // Q1
-      store_blk<false>(T[3], q32);
       load_blk(qk0 + AW + 128, ld, nn, 128, v);  // K1 (hi -> T4 over Q0 hi, lo -> T6 over K0 lo)
+      store_blk<false>(T[3], q32);
       store_blk<false>(T[4], v);
       store_blk<true>(T[6], v);
       handoff();
@@ -847,6 +853,9 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
       }
       stg_to_global<true>(stg01, a.dG + base * a.m1, a.m1, nn, a.m1);
       commit_and_sync(sy, issuer);
+      // every thread's reads of the staging (the dE/dG update) are done before
+      // it takes dQ: the MMA wait above is not a CTA barrier
+      __syncthreads();
       // dQ -> staging over T0 / T1, dK over T2 / T3
       float* stg23 = reinterpret_cast<float*>(T[2]);
       tmem_to_stg(tm + lane_off + c0, stg01, row, c0);
