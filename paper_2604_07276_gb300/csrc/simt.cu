@@ -1282,25 +1282,38 @@ __global__ void k_desc_bwd(DescArgs a) {
     }
     return;
   }
-  // dG rows (all NP rows; zero on padding)
-  for (long long idx = threadIdx.x; idx < (long long)NP * m1; idx += blockDim.x) {
-    const int s = (int)(idx / m1), p = (int)(idx % m1);
-    float v = 0.f;
+  // dG rows (all NP rows; zero on padding), a column quad per thread (m1 % 4 == 0)
+  const int q4 = m1 / 4;
+  float4* dG4 = reinterpret_cast<float4*>(a.dG + base * m1);
+  for (int idx = threadIdx.x; idx < NP * q4; idx += blockDim.x) {
+    const int s = idx / q4, q = idx % q4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (s < nn) {
       const float4 r = reinterpret_cast<const float4*>(a.R)[base + s];
-      v = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
+      float* vp = &v.x;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int p = 4 * q + k;
+        vp[k] = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
+      }
     }
-    a.dG[(base + s) * m1 + p] = v;
+    dG4[idx] = v;
   }
-  // dR rows: a warp per row
+  // dR rows: a warp per row, a column quad per lane
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float4* G4 = reinterpret_cast<const float4*>(a.G + base * m1);
   for (int s = warp; s < NP; s += nw) {
     float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
     if (s < nn) {
-      for (int p = lane; p < m1; p += 32) {
-        const float gv = a.G[(base + s) * m1 + p];
-        d0 = fmaf(gv, dTs[p], d0); d1 = fmaf(gv, dTs[m1 + p], d1);
-        d2 = fmaf(gv, dTs[2 * m1 + p], d2); d3 = fmaf(gv, dTs[3 * m1 + p], d3);
+      for (int q = lane; q < q4; q += 32) {
+        const float4 g = G4[(size_t)s * q4 + q];
+        const float gg[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int p = 4 * q + k;
+          d0 = fmaf(gg[k], dTs[p], d0); d1 = fmaf(gg[k], dTs[m1 + p], d1);
+          d2 = fmaf(gg[k], dTs[2 * m1 + p], d2); d3 = fmaf(gg[k], dTs[3 * m1 + p], d3);
+        }
       }
     }
     d0 = warp_sum(d0); d1 = warp_sum(d1); d2 = warp_sum(d2); d3 = warp_sum(d3);
