@@ -56,13 +56,14 @@ enum dp_status {
 
 enum dp_precision {
   DP_PREC_FP32 = 0,  /* every matrix product in FP32 SIMT arithmetic */
-  DP_PREC_BF16 = 1,  /* attention-layer products on tcgen05 tensor cores: BF16 operands, FP32 accumulation */
+  DP_PREC_BF16 = 1,  /* attention-layer products on tcgen05 tensor cores (fused per-atom layer kernels):
+                        BF16 operands, FP32 accumulation; attention width 128, embedding width <= 108 */
   DP_PREC_FP16X = 2, /* as DP_PREC_BF16 with FP16 operands and two-term (hi + lo) splits of the layer
-                        input, the attention weights, the values and the output projection; FP32
-                        accumulation */
-  DP_PREC_BF16X = 3  /* every product of the attention layers and of the fitting net on tcgen05 tensor
-                        cores with BF16 operands, both operands split in two terms (x = bf16(x) +
-                        bf16(x - bf16(x)), three products), FP32 accumulation; attention width 128 */
+                        input, the attention weights and [Wv Wo; bv Wo]; FP32 accumulation */
+  DP_PREC_BF16X = 3  /* every product of the attention layers, the embedding net (25-50-100 and
+                        32-64-128 nets) and the fitting net on tcgen05 tensor cores with BF16 operands,
+                        both operands split in two terms (x = bf16(x) + bf16(x - bf16(x)), three
+                        products), FP32 accumulation; attention width 128 or 256, embedding width <= 128 */
 };
 
 /* Load a model.

@@ -267,20 +267,20 @@ int alloc_workspace(dp_model* m, int cap) {
     ws.g = a.take<float>(rows * 4);
     ws.G.assign(L + 1, nullptr);
     for (int l = 0; l <= L; ++l) ws.G[l] = a.take<float>(rows * m1);
-    ws.QKV.assign(L, nullptr); ws.O.assign(L, nullptr); ws.Y.assign(L, nullptr); ws.stats.assign(L, nullptr);
+    ws.QK.assign(L, nullptr); ws.PG.assign(L, nullptr); ws.Y.assign(L, nullptr); ws.stats.assign(L, nullptr);
     if (!fused_tc_precision(m->precision)) {
       // Q | K only (V enters through [Wv Wo; bv Wo])
-      const size_t nqkv = 2 * (size_t)A;
+      const size_t nqk = 2 * (size_t)A;
       for (int l = 0; l < L; ++l) {
-        ws.QKV[l] = a.take<float>(rows * nqkv);
-        ws.O[l] = a.take<float>(rows * pg_ld(m1));  // [P G, rowsum(P)]
+        ws.QK[l] = a.take<float>(rows * nqk);
+        ws.PG[l] = a.take<float>(rows * pg_ld(m1));  // [P G, rowsum(P)]
         ws.Y[l] = a.take<float>(rows * m1);
         ws.stats[l] = a.take<float>(rows * 2);
       }
       ws.dY = a.take<float>(rows * m1);
       // dE/d[P G, rowsum P]
-      ws.dO = a.take<float>(rows * (L > 0 ? pg_ld(m1) : 1));
-      ws.dQKV = a.take<float>(rows * (L > 0 ? nqkv : 1));
+      ws.dPG = a.take<float>(rows * (L > 0 ? pg_ld(m1) : 1));
+      ws.dQK = a.take<float>(rows * (L > 0 ? nqk : 1));
     }
     ws.dG = a.take<float>(rows * m1);
     ws.T = a.take<float>((size_t)cap * 4 * m1);
@@ -480,16 +480,16 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
   for (int l = 0; l < L; ++l) {
     const AttnLayerW& w = m->attn[l];
     // [Q K] = G [Wq Wk] + [bq bk] (V only enters through [Wv Wo; bv Wo])
-    gemm_f32(ws.G[l], m1, w.Wqkv, 3 * A, w.bqkv, nullptr, 0, ws.QKV[l], 2 * A, rows, 2 * A, m1, EPI_BIAS, st);
+    gemm_f32(ws.G[l], m1, w.Wqk, 2 * A, w.bqk, nullptr, 0, ws.QK[l], 2 * A, rows, 2 * A, m1, EPI_BIAS, st);
     prof_mark(m, "qkv_gemm", st);
     AttnArgs aa{};
-    aa.QK = ws.QKV[l]; aa.ldq = 2 * A; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A;
+    aa.QK = ws.QK[l]; aa.ldq = 2 * A; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A;
     aa.shift = (float)m->shift;
-    aa.G = ws.G[l]; aa.m1 = m1; aa.ldpg = pg_ld(m1); aa.PG = ws.O[l];
+    aa.G = ws.G[l]; aa.m1 = m1; aa.ldpg = pg_ld(m1); aa.PG = ws.PG[l];
     launch_attn_fwd_f32(aa, st);
     prof_mark(m, "attn_fwd", st);
     // Y = O Wo + bo = [P G, rowsum(P)] [Wv Wo; bv Wo] + bo
-    gemm_f32(ws.O[l], pg_ld(m1), w.Wvo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, pg_ld(m1), EPI_BIAS, st);
+    gemm_f32(ws.PG[l], pg_ld(m1), w.Wvo, m1, w.bo, nullptr, 0, ws.Y[l], m1, rows, m1, pg_ld(m1), EPI_BIAS, st);
     launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
                       m1, st);
     prof_mark(m, "wo_gemm_ln", st);
@@ -501,16 +501,16 @@ void run_network_f32(dp_model* m, int n, const int* atype, cudaStream_t st) {
     const AttnLayerW& w = m->attn[l];
     launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
     // dE/d[P G, rowsum P] = dY [Wv Wo; bv Wo]^T
-    gemm_f32(ws.dY, m1, w.WvoT, pg_ld(m1), nullptr, nullptr, 0, ws.dO, pg_ld(m1), rows, pg_ld(m1), m1, EPI_BIAS, st);
+    gemm_f32(ws.dY, m1, w.WvoT, pg_ld(m1), nullptr, nullptr, 0, ws.dPG, pg_ld(m1), rows, pg_ld(m1), m1, EPI_BIAS, st);
     prof_mark(m, "ln_wo_bwd", st);
     AttnArgs aa{};
-    aa.QK = ws.QKV[l]; aa.ldq = 2 * A; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A;
+    aa.QK = ws.QK[l]; aa.ldq = 2 * A; aa.rw = ws.rw; aa.w64 = ws.w64; aa.nnei = ws.nnei; aa.n = n; aa.A = A;
     aa.shift = (float)m->shift; aa.G = ws.G[l]; aa.m1 = m1; aa.ldpg = pg_ld(m1);
-    aa.dPG = ws.dO; aa.dQK = ws.dQKV; aa.dG = ws.dG; aa.dgeo = ws.dgeo;
+    aa.dPG = ws.dPG; aa.dQK = ws.dQK; aa.dG = ws.dG; aa.dgeo = ws.dgeo;
     launch_attn_bwd_f32(aa, st);  // dQ, dK; dE/dG += P^T dPG
     prof_mark(m, "attn_bwd", st);
-    // dE/dG += [dQ dK] [Wq Wk]^T (the first 2A rows of Wqkv^T)
-    gemm_f32(ws.dQKV, 2 * A, w.WqkvT, m1, nullptr, nullptr, 0, ws.dG, m1, rows, m1, 2 * A, EPI_ACCUM, st);
+    // dE/dG += [dQ dK] [Wq Wk]^T
+    gemm_f32(ws.dQK, 2 * A, w.WqkT, m1, nullptr, nullptr, 0, ws.dG, m1, rows, m1, 2 * A, EPI_ACCUM, st);
     prof_mark(m, "qkv_bwd_gemm", st);
   }
   // a13: embedding backward -> dR[:,0]
@@ -542,11 +542,11 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
   for (int l = 0; l < L; ++l) {
     const AttnLayerW& w = m->attn[l];
     const XWeights::Layer& x = m->xw.layers[l];
-    gemm_bf16x(m, x.qk, ws.G[l], m1, w.bqkv, nullptr, 0, ws.QKV[l], 2 * A, rows, EPI_BIAS, st);
+    gemm_bf16x(m, x.qk, ws.G[l], m1, w.bqk, nullptr, 0, ws.QK[l], 2 * A, rows, EPI_BIAS, st);
     prof_mark(m, "qkv_gemm", st);
     attn_core_fwd_bf16x(m, n, l, st);
     prof_mark(m, "attn_fwd", st);
-    gemm_bf16x(m, x.vo, ws.O[l], pg_ld(m1), w.bo, nullptr, 0, ws.Y[l], m1, rows, EPI_BIAS, st);
+    gemm_bf16x(m, x.vo, ws.PG[l], pg_ld(m1), w.bo, nullptr, 0, ws.Y[l], m1, rows, EPI_BIAS, st);
     launch_ln_res_fwd(ws.Y[l], ws.G[l], ws.nlist, w.ln_g, w.ln_b, (float)m->ln_eps, ws.G[l + 1], ws.stats[l], rows,
                       m1, st);
     prof_mark(m, "wo_gemm_ln", st);
@@ -557,12 +557,12 @@ void run_network_bf16x(dp_model* m, int n, const int* atype, cudaStream_t st) {
     const AttnLayerW& w = m->attn[l];
     const XWeights::Layer& x = m->xw.layers[l];
     launch_ln_bwd(ws.dG, ws.Y[l], ws.stats[l], ws.nlist, w.ln_g, ws.dY, rows, m1, st);
-    // dE/d[P G, rowsum P] = dY [Wv Wo; bv Wo]^T (into the dO buffer)
-    gemm_bf16x(m, x.voT, ws.dY, m1, nullptr, nullptr, 0, ws.dO, pg_ld(m1), rows, EPI_BIAS, st);
+    // dE/d[P G, rowsum P] = dY [Wv Wo; bv Wo]^T
+    gemm_bf16x(m, x.voT, ws.dY, m1, nullptr, nullptr, 0, ws.dPG, pg_ld(m1), rows, EPI_BIAS, st);
     prof_mark(m, "ln_wo_bwd", st);
     attn_core_bwd_bf16x(m, n, l, st);  // dQ, dK; dE/dG += P^T dPG
     prof_mark(m, "attn_bwd", st);
-    gemm_bf16x(m, x.qkT, ws.dQKV, 2 * A, nullptr, nullptr, 0, ws.dG, m1, rows, EPI_ACCUM, st);
+    gemm_bf16x(m, x.qkT, ws.dQK, 2 * A, nullptr, nullptr, 0, ws.dG, m1, rows, EPI_ACCUM, st);
     prof_mark(m, "qkv_bwd_gemm", st);
   }
   ea.dG0 = ws.dG; ea.dR = ws.dR;
@@ -850,19 +850,19 @@ int dp_init(dp_model** out, const char* weights_path, const char* const* type_ma
   for (int l = 0; l < m->nattn; ++l) {
     std::string p = "at" + std::to_string(l) + "_";
     auto* Wq = w.get(p + "Wq"); auto* Wk = w.get(p + "Wk"); auto* Wv = w.get(p + "Wv");
-    std::vector<double> Wqkv((size_t)m1 * 3 * A);
+    // [Wq Wk] [m1][2A] and its transpose; V only enters through [Wv Wo; bv Wo]
+    std::vector<double> Wqk((size_t)m1 * 2 * A);
     for (int r = 0; r < m1; ++r)
       for (int c = 0; c < A; ++c) {
-        Wqkv[(size_t)r * 3 * A + c] = (*Wq)[(size_t)r * A + c];
-        Wqkv[(size_t)r * 3 * A + A + c] = (*Wk)[(size_t)r * A + c];
-        Wqkv[(size_t)r * 3 * A + 2 * A + c] = (*Wv)[(size_t)r * A + c];
+        Wqk[(size_t)r * 2 * A + c] = (*Wq)[(size_t)r * A + c];
+        Wqk[(size_t)r * 2 * A + A + c] = (*Wk)[(size_t)r * A + c];
       }
-    std::vector<double> bqkv;
-    for (auto nm : {"bq", "bk", "bv"}) bqkv.insert(bqkv.end(), w.get(p + nm)->begin(), w.get(p + nm)->end());
+    std::vector<double> bqk;
+    for (auto nm : {"bq", "bk"}) bqk.insert(bqk.end(), w.get(p + nm)->begin(), w.get(p + nm)->end());
     AttnLayerW& L = m->attn[l];
-    if ((rc = dev_upload(m, &L.Wqkv, to_f(Wqkv))) != DP_OK) return fail_free(rc);
-    if ((rc = dev_upload(m, &L.WqkvT, transpose_f(Wqkv, m1, 3 * A))) != DP_OK) return fail_free(rc);
-    if ((rc = dev_upload(m, &L.bqkv, to_f(bqkv))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.Wqk, to_f(Wqk))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.WqkT, transpose_f(Wqk, m1, 2 * A))) != DP_OK) return fail_free(rc);
+    if ((rc = dev_upload(m, &L.bqk, to_f(bqk))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.bo, to_f(*w.get(p + "bo")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_g, to_f(*w.get(p + "ln_g")))) != DP_OK) return fail_free(rc);
     if ((rc = dev_upload(m, &L.ln_b, to_f(*w.get(p + "ln_b")))) != DP_OK) return fail_free(rc);

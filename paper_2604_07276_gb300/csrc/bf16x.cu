@@ -1006,15 +1006,15 @@ int bf16x_init_weights(dp_model* m, std::string& msg) {
     XWeights::Layer& L = w.layers[l];
     const AttnLayerW& aw = m->attn[l];
     // V only enters through [Wv Wo; bv Wo], so the projection stops at [Q K]
-    L.qk = x_image_shape(m1, 2 * A);    // the first 2A columns of Wqkv
+    L.qk = x_image_shape(m1, 2 * A);    // [Wq Wk]
     L.vo = x_image_shape(pg_ld(m1), m1);
     L.voT = x_image_shape(m1, pg_ld(m1));
-    L.qkT = x_image_shape(2 * A, m1);   // the first 2A rows of Wqkv^T: [Wq Wk]^T
+    L.qkT = x_image_shape(2 * A, m1);   // [Wq Wk]^T
     int rc;
-    if ((rc = x_image_build(m, L.qk, aw.Wqkv, 3 * A, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.qk, aw.Wqk, 2 * A, nullptr, msg)) != DP_OK) return rc;
     if ((rc = x_image_build(m, L.vo, aw.Wvo, m1, nullptr, msg)) != DP_OK) return rc;
     if ((rc = x_image_build(m, L.voT, aw.WvoT, pg_ld(m1), nullptr, msg)) != DP_OK) return rc;
-    if ((rc = x_image_build(m, L.qkT, aw.WqkvT, m1, nullptr, msg)) != DP_OK) return rc;
+    if ((rc = x_image_build(m, L.qkT, aw.WqkT, m1, nullptr, msg)) != DP_OK) return rc;
   }
   w.fit.assign(m->nfit, XImage{});
   w.fitT.assign(m->nfit, XImage{});
@@ -1091,11 +1091,11 @@ namespace {
 XCoreArgs core_args(dp_model* m, int n, int l) {
   Workspace& ws = m->ws;
   XCoreArgs a{};
-  a.QK = ws.QKV[l];  // [rows][2A]: Q | K
+  a.QK = ws.QK[l];  // [rows][2A]: Q | K
   a.G = ws.G[l];
-  a.PG = ws.O[l];
-  a.dPG = ws.dO;  // dE/d[P G, rowsum P], [rows][ldpg]
-  a.dQK = ws.dQKV;
+  a.PG = ws.PG[l];
+  a.dPG = ws.dPG;  // dE/d[P G, rowsum P], [rows][ldpg]
+  a.dQK = ws.dQK;
   a.dG = ws.dG;
   a.dgeo = ws.dgeo;
   a.rw = ws.rw;

@@ -27,7 +27,7 @@ struct Arena {
 
 
 struct AttnLayerW {
-  float *Wqkv, *bqkv, *WqkvT, *bo, *ln_g, *ln_b;
+  float *Wqk, *bqk, *WqkT, *bo, *ln_g, *ln_b;  // [Wq Wk] [m1][2A], [bq bk], [Wq Wk]^T
   // [Wv Wo; bv Wo; 0...] ([pg_ld(m1)][m1]), formed in FP64, so that
   // Y = O Wo + bo = [P G, rowsum(P)] Wvo + bo (see launch_attn_fwd_f32); and
   // its transpose [m1][pg_ld(m1)] (the adjoints of the FP32 and bf16x paths)
@@ -40,9 +40,10 @@ inline int pg_ld(int m1) { return (m1 + 1 + 7) & ~7; }
 struct TcWeights {
   bool ready = false;
   std::vector<void*> allocations;
-  // per attention layer: BF16 weights in the [out][in] (K-major) layout of the
-  // tcgen05 B operand
-  std::vector<void*> Wqkv_t, Wo_t, WoT_t, WqkvT_t;
+  // per attention layer: the swizzled weight image of the fused layer kernels
+  // ([Wq; Wk], Wvo and its residue, K-major tcgen05 B operands), with BF16
+  // (plain bf16 mode) and with FP16 entries (fp16x)
+  std::vector<void*> layer_bf16_t, layer_f16_t;
   std::vector<void*> fitW_t, fitWT_t;
   void* emb_W1_t = nullptr;  // embedding net W1 / W2 hi + lo tiles, FP16 (fused 16-bit paths)
   void* emb_W2_t = nullptr;  // the same in BF16 (bf16x)
@@ -97,8 +98,10 @@ struct Workspace {
   float *R, *rw, *rv, *dR, *dgeo, *g;
   double* w64;
   // network
-  std::vector<float*> G, QKV, O, Y, stats;
-  float *dG, *dY, *dO, *dQKV;
+  // modular layer layout (FP32, bf16x): per layer Q | K, [P G, rowsum P], Y and
+  // the LayerNorm statistics; dE/d[P G, rowsum P] and dE/d[Q K] for the adjoint
+  std::vector<float*> G, QK, PG, Y, stats;
+  float *dG, *dY, *dPG, *dQK;
   float *T, *X, *dX, *e;
   std::vector<float*> H;
   float *dHa, *dHb, *dZ;
@@ -213,7 +216,7 @@ void attn_core_fwd_bf16x(dp_model* m, int n, int l, cudaStream_t st);
 void attn_core_bwd_bf16x(dp_model* m, int n, int l, cudaStream_t st);
 // the fused 16-bit layer kernels (tc.cu) serve DP_PREC_BF16 and DP_PREC_FP16X;
 // DP_PREC_FP32 and DP_PREC_BF16X share the modular layer layout (row-major G,
-// stored Q K V, LayerNorm kernels)
+// stored Q | K and [P G, rowsum P], LayerNorm kernels)
 inline bool fused_tc_precision(int p) { return p == DP_PREC_BF16 || p == DP_PREC_FP16X; }
 int fit_gemm_tc(dp_model* m, int layer, bool backward, const float* A, int lda, const float* bias, const float* R,
                 int ldr, float* C, int ldc, int M, int epi, cudaStream_t st);

@@ -842,7 +842,7 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg) {
         return DP_ERR_CUDA;
       }
       w.allocations.push_back(d);
-      (f16 ? w.Wo_t : w.Wqkv_t).push_back(d);  // images: [0] bf16 layers, [1] fp16 layers
+      (f16 ? w.layer_f16_t : w.layer_bf16_t).push_back(d);
     }
   if (int rc = tc_init_embedding(m, arrays, msg)) return rc;
   w.vectors.assign(m->nattn, TcWeights::Vectors{});
@@ -905,7 +905,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
     la.n = n;
     la.m1 = m->m1;
     la.yld = yhat_ld(m->m1);
-    la.wimg = reinterpret_cast<const uint4*>(f16 ? m->tcw.Wo_t[l] : m->tcw.Wqkv_t[l]);
+    la.wimg = reinterpret_cast<const uint4*>(f16 ? m->tcw.layer_f16_t[l] : m->tcw.layer_bf16_t[l]);
     const TcWeights::Vectors& vec = m->tcw.vectors[l];
     memcpy(la.bo, vec.bo, sizeof(la.bo));
     memcpy(la.gamma, vec.gamma, sizeof(la.gamma));
@@ -961,8 +961,8 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
 void tc_free_weights(dp_model* m) {
   for (void* p : m->tcw.allocations) cudaFree(p);
   m->tcw.allocations.clear();
-  m->tcw.Wqkv_t.clear();
-  m->tcw.Wo_t.clear();
+  m->tcw.layer_bf16_t.clear();
+  m->tcw.layer_f16_t.clear();
   m->tcw.fitW_t.clear();
   m->tcw.fitWT_t.clear();
   m->tcw.ready = false;
