@@ -1,8 +1,9 @@
 // Tensor-core (tcgen05, 16-bit operands, FP32 accumulation in TMEM) path of
 // the gated attention layers (stage a6) and their adjoint (stage a12).
 // Two operand modes: plain BF16, and FP16 with two-term (hi + lo) splits of
-// the layer input G, the attention weights P and the values V in the forward
-// products, whose rounding the LayerNorm of weakly attended rows amplifies.
+// the layer input G, the attention weights P and the output weights Wvo in the
+// forward products, whose rounding the LayerNorm of weakly attended rows
+// amplifies.
 //
 // One persistent CTA per SM walks over centre atoms; an atom is one 128-row
 // tile (its neighbour slots).  Every product of a layer runs on the tensor
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   uint8_t* sD = sm + F_SLOT_D;
   uint8_t* sWqk = sm + F_W;  // [Wq; Wk], 256 rows
   float4* s_key = reinterpret_cast<float4*>(sm + F_SMALL);  // [128] (rhat_x, rhat_y, rhat_z, w)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wo copy, Q K, Q K out, V, inputs
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_key + 128);  // [6]: general, Wvo copy, Q K, Q K out, (unused), inputs
   uint64_t* bar_ld = bar + 1;
   uint64_t* bar_q = bar + 2;
   uint64_t* bar_in = bar + 5;
