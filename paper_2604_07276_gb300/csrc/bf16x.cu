@@ -359,6 +359,7 @@ __device__ __forceinline__ void store_split32(uint8_t* hi, uint8_t* lo, int r, i
 // Coalesced block access of the cores: in access t (0..7) warp w (of 16)
 // takes row w + 16 t and lane l columns 4 l .. 4 l + 3 of a 128-column
 // block, so that each warp access is one row's 512 contiguous bytes.
+static_assert(XC_NT == 512, "block accesses: 16 warps x 8 accesses cover the 128 rows");
 __device__ __forceinline__ int blk_row(int t) { return (int)(threadIdx.x >> 5) + 16 * t; }
 
 // v[4 t .. 4 t + 3] = src[r][c .. c + 3] (r = blk_row(t), c = 4 lane), zero

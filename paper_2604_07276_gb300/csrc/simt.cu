@@ -680,6 +680,8 @@ __device__ __forceinline__ float pair_diff(float2 a, float2 b) { return (a.x - b
 // rounding of the cancelling sum itself (a CPU emulation of both forms on the
 // 15,668-atom box: force RMSE 7.5e-6 -> 2.4e-6 eV/A).
 constexpr int FTF = 512;       // threads of the forward and the adjoint (4 x 8 tiles)
+static_assert(4 * (FTF / 16) == NP, "32 thread rows of 4 rows each cover the 128 rows of an atom");
+static_assert((FTF / 16) * NP * 4 <= 128 * (NP + 4), "the adjoint's column parts fit one shared tile");
 constexpr int TLD = NP + 4;    // row stride of their shared tiles (16-byte rows)
 
 // Row (or column) i < 8 of thread coordinate t < 16: the quarter tiles
