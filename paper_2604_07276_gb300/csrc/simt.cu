@@ -1246,22 +1246,21 @@ __global__ void k_desc_bwd(DescArgs a) {
   }
   __syncthreads();
   if (a.cq) {
-    // dG in column quads (consecutive threads -> consecutive rows), zero on padding
+    // dG in column quads (consecutive threads -> consecutive rows), live rows
+    // only: the fused layer kernels and the embedding adjoint read no others
     float4* dG4 = reinterpret_cast<float4*>(a.dG + base * m1);
     const float4* R4 = reinterpret_cast<const float4*>(a.R) + base;
-    for (int idx = threadIdx.x; idx < NP * (m1 / 4); idx += blockDim.x) {
-      const int q = idx / NP, s = idx % NP;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (s < nn) {
-        const float4 r = R4[s];
-        float* vp = &v.x;
+    for (int idx = threadIdx.x; idx < nn * (m1 / 4); idx += blockDim.x) {
+      const int q = idx / nn, s = idx % nn;
+      const float4 r = R4[s];
+      float4 v;
+      float* vp = &v.x;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int p = 4 * q + k;
-          vp[k] = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
-        }
+      for (int k = 0; k < 4; ++k) {
+        const int p = 4 * q + k;
+        vp[k] = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
       }
-      dG4[idx] = v;
+      dG4[(size_t)q * NP + s] = v;
     }
     // dR rows: a thread per row
     const float4* G4 = reinterpret_cast<const float4*>(a.G + base * m1);

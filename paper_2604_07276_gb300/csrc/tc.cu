@@ -71,11 +71,18 @@ struct LayerArgs {
 // G_l, G_{l+1} and dE/dG are column-quad interleaved per atom (cq_off);
 // yhat likewise in groups of 8 bf16 columns: element (r, c) of an atom at
 // ((c / 8) * NP + r) * 8 + c % 8.  A warp's per-row 16-byte accesses are then
-// 512 contiguous bytes.
+// 512 contiguous bytes.  Only an atom's live rows (its first nnei) of these
+// blocks and of rstd and smax are read or written: the rows past them stay
+// as they were (the layer input's are treated as zeros), which leaves every
+// live row's result unchanged, since the attention weights of keys past the
+// last neighbour are exact zeros.
 __host__ __device__ constexpr int yhat_ld(int m1) { return (m1 + 7) & ~7; }
 
 // Bring the per-row inputs of centre atom `atom` (if it exists) into L2 ahead
-// of its turn: one thread, bulk prefetches.
+// of its turn: one thread, bulk prefetches of whole blocks.  (Prefetching the
+// live rows alone takes one prefetch per column quad, ~60 instead of 6 per
+// atom, and the issuing warp, which holds the MMA issuer, then stalls for
+// longer than the prefetches save.)
 __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool bwd) {
   if (atom >= a.n) return;
   const size_t base = (size_t)atom * NP;
@@ -152,7 +159,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   const uint32_t g_bytes = (uint32_t)(NP * a.m1 * sizeof(float)), k_bytes = NP * sizeof(float4);
   // An atom's layer input (its column-quad interleaved block, as stored) and
   // its per-key (rhat, w) rows (zero past nnei) arrive by bulk copies: into
-  // slots C..D and the key table, during the previous atom's LayerNorm.
+  // slots C..D and the key table, during the previous atom's LayerNorm.  One
+  // copy of the whole block: its rows past the last neighbour hold whatever
+  // was there and are replaced by zeros when read.
   auto fetch_inputs = [&](int at) {
     const size_t b = (size_t)at * NP;
     mbar_expect_tx(bar_in, g_bytes + k_bytes);
@@ -164,12 +173,14 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = a.nnei[atom];
     const size_t base = (size_t)atom * NP;
-    if (issuer) prefetch_atom(a, atom + gridDim.x, false);
+    const int next = atom + (int)gridDim.x;
+    const bool rv = row < nn;
+    if (issuer) prefetch_atom(a, next, false);
     si.wait();
     float v[32];
     // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B), and
-    // kept in TMEM for the residual
-    load_cq32(reinterpret_cast<const float*>(sC), a.m1, row, c0, v);
+    // kept in TMEM for the residual; rows past the last neighbour as zeros
+    load_cq32(reinterpret_cast<const float*>(sC), a.m1, row, c0, v, rv);
     tmem_st32(tm + lane_off + 384 + c0, v);
     set_bias_ones(v, c0, a.m1);
     store_row32<F16>(sA, row, c0, v);
@@ -202,7 +213,6 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     float w_row;
     {
       const RowXchg xr(sC, row, part, lane, quad);
-      const bool rv = row < nn;
       const float4 kj = s_key[row];
       const float wj = kj.w;
       w_row = wj;
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       }
       sum = xr.sum(sum);
       const float inv = sum > 0.f ? 1.0f / sum : 0.f;
-      if (part == 0) a.smax[base + row] = make_float2(mx, inv);
+      if (part == 0 && rv) a.smax[base + row] = make_float2(mx, inv);
       if (live) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     }
     commit_and_sync(sy, issuer);
     // C, D and the key table are dead: the next atom's inputs start to arrive
-    if (issuer && atom + (int)gridDim.x < a.n) fetch_inputs(atom + gridDim.x);
+    if (issuer && next < a.n) fetch_inputs(next);
     // LayerNorm, residual
     {
       const RowXchg xr(sB, row, part, lane, quad);  // G_lo is dead
@@ -298,7 +308,6 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       }
       const float var = xr.sum(s2) / (float)a.m1;
       const float rs = 1.0f / sqrtf(var + a.eps);
-      const bool rv = row < nn;
       float4* gout = reinterpret_cast<float4*>(a.Gout + base * a.m1);
       uint4* yh = reinterpret_cast<uint4*>(a.yhat + base * a.yld);
       float gin[32];
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
 #pragma unroll
       for (int i = 0; i < 32; i += 8) {
         const int c = c0 + i;
-        if (c < a.m1) {
+        if (c < a.m1 && rv) {
           float y[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) y[k] = c + k < a.m1 ? (v[i + k] - mean) * rs : 0.f;
@@ -315,12 +324,10 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
             const int cc = c + h;
             if (cc < a.m1) {
               float4 g = make_float4(gin[i + h], gin[i + h + 1], gin[i + h + 2], gin[i + h + 3]);
-              if (rv) {
-                g.x += y[h] * a.gamma[cc] + a.beta[cc];
-                g.y += y[h + 1] * a.gamma[cc + 1] + a.beta[cc + 1];
-                g.z += y[h + 2] * a.gamma[cc + 2] + a.beta[cc + 2];
-                g.w += y[h + 3] * a.gamma[cc + 3] + a.beta[cc + 3];
-              }
+              g.x += y[h] * a.gamma[cc] + a.beta[cc];
+              g.y += y[h + 1] * a.gamma[cc + 1] + a.beta[cc + 1];
+              g.z += y[h + 2] * a.gamma[cc + 2] + a.beta[cc + 2];
+              g.w += y[h + 3] * a.gamma[cc + 3] + a.beta[cc + 3];
               gout[(cc >> 2) * NP + row] = g;
             }
           }
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
           yh[(c >> 3) * NP + row] = u;
         }
       }
-      if (part == 0) a.rstd[base + row] = rs;
+      if (part == 0 && rv) a.rstd[base + row] = rs;
     }
     fence_before_sync();
     __syncthreads();
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       prefetch_atom(a, blockIdx.x, true);
     }
     float gn[32];
-    load_cq32(a.Gin + (size_t)blockIdx.x * NP * a.m1, a.m1, row, c0, gn);
+    load_cq32(a.Gin + (size_t)blockIdx.x * NP * a.m1, a.m1, row, c0, gn, row < nn_next);
     tmem_st32(tm + lane_off + 0 + c0, gn);
   }
 
@@ -423,14 +430,14 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     const bool rv = row < nn;
     const int next = atom + (int)gridDim.x;
     if (issuer) prefetch_atom(a, next, true);  // the next atom's inputs -> L2
-    // Every per-row input of the atom in one round trip (the NP-row blocks
-    // exist past nnei; what is read there is masked, never used)
+    // Every per-row input of the atom in one round trip (live rows only: the
+    // rows past the last neighbour are not kept)
     float v[32];
     tmem_ld32(tm + lane_off + 0 + c0, v);
-    const float rs_in = a.rstd[base + row];
-    const float2 sst_in = a.smax[base + row];
+    const float rs = rv ? a.rstd[base + row] : 0.f;
+    const float2 sst = rv ? a.smax[base + row] : make_float2(0.f, 0.f);
     float4 kr = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tid < 128) kr = reinterpret_cast<const float4*>(a.rw)[base + tid];
+    if (tid < nn) kr = reinterpret_cast<const float4*>(a.rw)[base + tid];
     if (next < a.n) nn_next = a.nnei[next];
     float4 dz[8];
     uint4 yy[4];
@@ -440,17 +447,15 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int c = c0 + 4 * q;
-        dz[q] = c < a.m1 ? dz4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dz[q] = c < a.m1 && rv ? dz4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = c0 + 8 * q;
-        yy[q] = c < a.m1 ? yh8[(c >> 3) * NP + row] : make_uint4(0u, 0u, 0u, 0u);
+        yy[q] = c < a.m1 && rv ? yh8[(c >> 3) * NP + row] : make_uint4(0u, 0u, 0u, 0u);
       }
     }
-    const float rs = rv ? rs_in : 0.f;
-    const float2 sst = rv ? sst_in : make_float2(0.f, 0.f);
-    if (tid < 128) s_key[tid] = tid < nn ? kr : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < 128) s_key[tid] = kr;
     // P0a: G_l -> A (+ G_lo -> B), the bias columns set to 1
     set_bias_ones(v, c0, a.m1);
     store_row32<F16>(sA, row, c0, v);
@@ -677,13 +682,13 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int c = c0 + 4 * q;
-      g[q] = c < a.m1 ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      g[q] = c < a.m1 && rv ? dg4[(c >> 2) * NP + row] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // the next atom's layer-input row, parked in TMEM [0, 128) (dQ is dead
     // since P4)
     if (next < a.n) {
       float gn[32];
-      load_cq32(a.Gin + (size_t)next * NP * a.m1, a.m1, row, c0, gn);
+      load_cq32(a.Gin + (size_t)next * NP * a.m1, a.m1, row, c0, gn, row < nn_next);
       tmem_st32(tm + lane_off + 0 + c0, gn);
     }
     if (tid < nn) {
@@ -715,7 +720,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
       for (int q = 0; q < 4; ++q) {
         const int c = c0 + h + 4 * q, i = 4 * q;
         float4& gq = g[(h >> 2) + q];
-        if (c < a.m1) {
+        if (c < a.m1 && rv) {
           gq.x += v[i] + u[i]; gq.y += v[i + 1] + u[i + 1]; gq.z += v[i + 2] + u[i + 2]; gq.w += v[i + 3] + u[i + 3];
           dg4[(c >> 2) * NP + row] = gq;
         }

@@ -85,6 +85,8 @@ struct EmbedTcArgs {
   const uint4* wimg;      // W1/W2 hi/lo tiles (FP16 or BF16, as the kernel's operands)
   int n, ntypes;
   int rm;                 // G0 and dG0 row-major (the modular layer layout) instead of interleaved
+  int live_only;          // G0's rows past the last neighbour are not written (their content is
+                          // undefined: the fused layer kernels never read them); else zeros
   int* err;
   float W0[32], b0[32], b1[64], b2[128];  // the net's first layer and biases (first E0 / E1 / E2 used)
 };
@@ -207,18 +209,18 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
 // Z3 = H2 W2; returns once Z3 is in TMEM columns [64, 64 + E2P).
 template <class S, bool F16, int H, class BeforeZ3>
 __device__ __forceinline__ void embed_bwd_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, Sync& sy, int row,
-                                                int atom, float* h1, float* h2, BeforeZ3 before_z3) {
+                                                bool rv, int atom, float* h1, float* h2, BeforeZ3 before_z3) {
   using O = EmbOwn<S, H>;
   uint8_t* sW2h = sm + 2 * S::T1;
   uint8_t* sW2l = sW2h + S::T2;
   uint8_t* sH2h = sm + S::WIMG + 2 * EMB_TA;
   uint8_t* sH2l = sH2h + EMB_TA;
   const bool issuer = threadIdx.x == 0;
-  const float* hs = a.H12 + (size_t)atom * (S::E0 + S::E1) * NP + row;
+  const float* hs = a.H12 + (size_t)atom * (S::E0 + S::E1) * NP + row;  // live rows only were stored
 #pragma unroll
-  for (int p = 0; p < S::E0; ++p) h1[p] = hs[p * NP];
+  for (int p = 0; p < S::E0; ++p) h1[p] = rv ? hs[p * NP] : 0.f;
 #pragma unroll
-  for (int i = 0; i < O::nb; ++i) h2[i] = hs[(S::E0 + O::b0 + i) * NP];
+  for (int i = 0; i < O::nb; ++i) h2[i] = rv ? hs[(S::E0 + O::b0 + i) * NP] : 0.f;
 #pragma unroll
   for (int g = O::g_lo; g < O::g_hi; ++g) {
     float v[8];
@@ -248,7 +250,7 @@ struct EmbRowIn {
   float x = 0.f;
   __device__ void count(const EmbedTcArgs& a, int atom) { nn = atom < a.n ? a.nnei[atom] : 0; }
   __device__ void rows(const EmbedTcArgs& a, int atom, int row) {
-    if (atom < a.n) {  // the NP-row blocks exist past nnei: read unmasked, used masked
+    if (atom < a.n) {  // R and nlist are written for all NP rows: read unmasked, used masked
       const size_t rg = (size_t)atom * NP + row;
       x = a.R[rg * 4];
       nl = a.nlist[rg];
@@ -327,7 +329,8 @@ __device__ __forceinline__ void embed_fwd_out(const EmbedTcArgs& a, uint32_t tad
       float2 o;
       o.x = rv ? (h2[c % S::E1 - O::b0] + tanhf(z[i] + a.b2[c])) * (1.f + g2.x) : 0.f;
       o.y = rv ? (h2[(c + 1) % S::E1 - O::b0] + tanhf(z[i + 1] + a.b2[c + 1])) * (1.f + g2.y) : 0.f;
-      *reinterpret_cast<float2*>(out_blk + (a.rm ? (size_t)row * S::E2 + c : cq_off(row, c))) = o;
+      if (rv || !a.live_only)
+        *reinterpret_cast<float2*>(out_blk + (a.rm ? (size_t)row * S::E2 + c : cq_off(row, c))) = o;
     }
   }
 }
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(EMB_THREADS, S::MIN_CTAS) k_embed_tc_fwd(const
       embed_tc_front<S, F16, 0>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
     else
       embed_tc_front<S, F16, 1>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
-    {  // layers 1 and 2 for the adjoint: this half's layer-1 units, its layer-2 units
+    if (rv) {  // layers 1 and 2 of a live row for the adjoint: this half's layer-1 units, its layer-2 units
       float* hs = a.H12 + (size_t)atom * (S::E0 + S::E1) * NP + row;
       if (half == 0) {
 #pragma unroll
@@ -548,7 +551,7 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
   float h1[S::E0], h2[O::nb];
   float4 d0[4];
-  embed_bwd_front<S, F16, H>(a, sm, tm, sy, row, (int)(rowg / NP), h1, h2, [&] {
+  embed_bwd_front<S, F16, H>(a, sm, tm, sy, row, rv, (int)(rowg / NP), h1, h2, [&] {
     embed_bwd_load16<S, H>(dg, a.rm, 0, row, rv, d0);
     embed_bwd_prefetch16<S, H>(dg, a.rm, 1, row, rv);
   });
@@ -779,7 +782,7 @@ void tc_embed_fused(dp_model* m, int n, const int* atype, bool bwd, cudaStream_t
   if (n == 0) return;
   Workspace& ws = m->ws;
   EmbedTcArgs et = embed_tc_args(m, n, atype);
-  et.G0 = ws.G[0]; et.dG0 = ws.dG; et.dR = ws.dR; et.rm = 0;
+  et.G0 = ws.G[0]; et.dG0 = ws.dG; et.dR = ws.dR; et.rm = 0; et.live_only = 1;
   et.H12 = reinterpret_cast<float*>(ws.tc.p[5]);
   et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W1_t);
   tc_embed_launch(m, et, bwd, false, st);

@@ -79,14 +79,15 @@ __device__ __forceinline__ void store_row32(uint8_t* tile, int r, int c0, const 
 }
 
 // Load row r, columns c0..c0+31 (zero past m1), of an atom's column-quad
-// interleaved FP32 block.
-__device__ __forceinline__ void load_cq32(const float* blk, int m1, int r, int c0, float* v) {
+// interleaved FP32 block; a row that is not live (past the last neighbour,
+// whose content is not kept) reads as zeros without a load.
+__device__ __forceinline__ void load_cq32(const float* blk, int m1, int r, int c0, float* v, bool live = true) {
   const float4* b4 = reinterpret_cast<const float4*>(blk);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int c = c0 + 4 * q;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < m1) x = b4[(c >> 2) * NP + r];  // m1 % 4 == 0
+    if (c < m1 && live) x = b4[(c >> 2) * NP + r];  // m1 % 4 == 0
     v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
   }
 }
