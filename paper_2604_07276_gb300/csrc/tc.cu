@@ -169,9 +169,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     bulk_g2s(s_key, a.rw + b * 4, k_bytes, bar_in);
   };
   if (issuer && (int)blockIdx.x < a.n) fetch_inputs(blockIdx.x);
+  // neighbour counts are read one atom ahead
+  int nn_next = (int)blockIdx.x < a.n ? a.nnei[blockIdx.x] : 0;
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
-    const int nn = a.nnei[atom];
+    const int nn = nn_next;
     const size_t base = (size_t)atom * NP;
     const int next = atom + (int)gridDim.x;
     const bool rv = row < nn;
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     commit_and_sync(sy, issuer);
     // C, D and the key table are dead: the next atom's inputs start to arrive
     if (issuer && next < a.n) fetch_inputs(next);
+    if (next < a.n) nn_next = a.nnei[next];
     // LayerNorm, residual
     {
       const RowXchg xr(sB, row, part, lane, quad);  // G_lo is dead
