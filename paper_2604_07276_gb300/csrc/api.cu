@@ -1522,6 +1522,16 @@ int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const dou
     CUDA_TRY(cudaMalloc(&p, sizeof(int)));
     m->d_md_counter = reinterpret_cast<int*>(p);
   }
+  const int nb_cap = verlet_kick_blocks(m->ws.cap);
+  if (!m->d_md_partial || m->md_partial_cap < nb_cap) {
+    if (m->d_md_partial) cudaFree(m->d_md_partial);
+    m->d_md_partial = nullptr;
+    m->md_partial_cap = 0;
+    void* p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, sizeof(double) * (size_t)(nb_cap > 0 ? nb_cap : 1)));
+    m->d_md_partial = reinterpret_cast<double*>(p);
+    m->md_partial_cap = nb_cap;
+  }
   CUDA_TRY(cudaMemsetAsync(m->d_md_counter, 0, sizeof(int), st));
   // forces at the starting coordinates
   int rc = run_device(m, natoms, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
@@ -1530,7 +1540,8 @@ int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const dou
   auto one_step = [&]() -> int {
     launch_verlet_drift(natoms, dt, d_mass, d_force, d_vel, d_coord, st);
     int r = run_device(m, natoms, natoms, d_coord, d_box, d_atype, d_energy, d_force, d_virial, nullptr, st);
-    launch_verlet_kick(natoms, dt, d_mass, d_force, d_vel, d_energy, m->d_md_counter, d_thermo, nsteps, st);
+    launch_verlet_kick(natoms, dt, d_mass, d_force, d_vel, m->d_md_partial, d_energy, m->d_md_counter, d_thermo,
+                       nsteps, st);
     return r;
   };
   if (!use_graph) {
@@ -1541,6 +1552,7 @@ int dp_md_run(dp_model* m, int natoms, double* d_coord, double* d_vel, const dou
     const void* key_dt = nullptr;
     memcpy(&key_dt, &dtv, sizeof(dtv) < sizeof(key_dt) ? sizeof(dtv) : sizeof(key_dt));
     std::vector<const void*> key = {d_coord, d_vel, d_mass, d_box, d_atype, d_force, d_energy, d_virial, d_thermo,
+                                    m->d_md_partial,
                                     reinterpret_cast<const void*>((intptr_t)natoms),
                                     reinterpret_cast<const void*>((intptr_t)nsteps),
                                     reinterpret_cast<const void*>((intptr_t)m->precision), key_dt};
@@ -1580,6 +1592,7 @@ void dp_free(dp_model* m) {
   if (m->md_exec) cudaGraphExecDestroy(m->md_exec);
   if (m->md_graph) cudaGraphDestroy(m->md_graph);
   if (m->d_md_counter) cudaFree(m->d_md_counter);
+  if (m->d_md_partial) cudaFree(m->d_md_partial);
   if (m->batch_buf) cudaFree(m->batch_buf);
   if (m->t_buf) cudaFree(m->t_buf);
   delete m;

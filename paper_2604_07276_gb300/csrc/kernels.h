@@ -234,7 +234,9 @@ void launch_add_rows(const float* rows, const float* vec, int nrows, int width, 
 
 // --- velocity-Verlet MD (md.cu)
 void launch_verlet_drift(int n, double dt, const double* mass, const double* f, double* v, double* x, cudaStream_t st);
-void launch_verlet_kick(int n, double dt, const double* mass, const double* f, double* v, const double* energy,
-                        int* counter, double* thermo, int nrec, cudaStream_t st);
+// Blocks of the second half kick for n atoms (one partial kinetic energy each).
+int verlet_kick_blocks(int n);
+void launch_verlet_kick(int n, double dt, const double* mass, const double* f, double* v, double* partial,
+                        const double* energy, int* counter, double* thermo, int nrec, cudaStream_t st);
 
 }  // namespace dpa1

@@ -21,19 +21,41 @@ __global__ void k_verlet_drift(int n, double dt, const double* __restrict__ mass
   x[i] += dt * vi;
 }
 
-// Second half kick with the new forces and the kinetic energy of the step,
-// reduced in FP64 in a fixed order (one block).
-__global__ void k_verlet_kick(int n, double dt, const double* __restrict__ mass, const double* __restrict__ f,
-                              double* __restrict__ v, const double* __restrict__ energy, int* __restrict__ counter,
-                              double* __restrict__ thermo, int nrec) {
-  __shared__ double red[32];
+constexpr int KICK_THREADS = 256;
+
+int verlet_kick_blocks(int n) { return (3 * n + KICK_THREADS - 1) / KICK_THREADS; }
+
+// Second half kick with the new forces: v += dt/2 F/m.  Each block's kinetic
+// energy (a fixed warp tree, then its warps in order) goes to partial[block].
+__global__ void __launch_bounds__(KICK_THREADS) k_verlet_kick(int n, double dt, const double* __restrict__ mass,
+                                                                const double* __restrict__ f, double* __restrict__ v,
+                                                                double* __restrict__ partial) {
+  __shared__ double red[KICK_THREADS / 32];
+  const int i = blockIdx.x * KICK_THREADS + threadIdx.x;
   double ke = 0.0;
-  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+  if (i < 3 * n) {
     const double m = mass[i / 3];
     const double vi = v[i] + 0.5 * dt * f[i] / m * ACC;
     v[i] = vi;
-    ke += 0.5 * m * vi * vi;
+    ke = 0.5 * m * vi * vi;
   }
+  ke = warp_sum_d(ke);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ke;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < KICK_THREADS / 32; ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+// The step's kinetic energy from the `nb` blocks' partial sums, reduced in
+// FP64 in a fixed order (one block), and its record (E, kinetic, total).
+__global__ void k_verlet_thermo(int nb, const double* __restrict__ partial, const double* __restrict__ energy,
+                                int* __restrict__ counter, double* __restrict__ thermo, int nrec) {
+  __shared__ double red[32];
+  double ke = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) ke += partial[b];
   ke = warp_sum_d(ke);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ke;
   __syncthreads();
@@ -57,9 +79,14 @@ void launch_verlet_drift(int n, double dt, const double* mass, const double* f, 
   note_launch();
 }
 
-void launch_verlet_kick(int n, double dt, const double* mass, const double* f, double* v, const double* energy,
-                        int* counter, double* thermo, int nrec, cudaStream_t st) {
-  k_verlet_kick<<<1, 1024, 0, st>>>(n, dt, mass, f, v, energy, counter, thermo, nrec);
+void launch_verlet_kick(int n, double dt, const double* mass, const double* f, double* v, double* partial,
+                        const double* energy, int* counter, double* thermo, int nrec, cudaStream_t st) {
+  const int nb = verlet_kick_blocks(n);
+  if (nb > 0) {
+    k_verlet_kick<<<nb, KICK_THREADS, 0, st>>>(n, dt, mass, f, v, partial);
+    note_launch();
+  }
+  k_verlet_thermo<<<1, 1024, 0, st>>>(nb, partial, energy, counter, thermo, nrec);
   note_launch();
 }
 

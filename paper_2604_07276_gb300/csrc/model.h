@@ -173,8 +173,11 @@ struct dp_model {
   cudaStream_t last_stream = nullptr;
   int last_natoms = 0;
   dpa1::Profiler prof;
-  // velocity-Verlet: step counter and the cached graph of one step
+  // velocity-Verlet: step counter, the kick's per-block kinetic energies and
+  // the cached graph of one step
   int* d_md_counter = nullptr;
+  double* d_md_partial = nullptr;
+  int md_partial_cap = 0;
   // dp_compute_batch: device copies of a batch's inputs and results, grown on demand
   void* batch_buf = nullptr;
   size_t batch_cap = 0;
