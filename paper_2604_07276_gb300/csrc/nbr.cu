@@ -142,7 +142,9 @@ __device__ __forceinline__ double mic_near(double d, double L) {
 // first sel.  FP64 is slow on this part, so it is kept to the ~11 % of
 // candidates that pass the screen.
 constexpr int NBR_WARPS = 4;
-__global__ void __launch_bounds__(32 * NBR_WARPS)
+// 10 blocks per SM (48 registers, no spills): the search is latency-bound and
+// gains from the extra resident warps
+__global__ void __launch_bounds__(32 * NBR_WARPS, 10)
 k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const CellGrid* __restrict__ cgp,
             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
             const int* __restrict__ cell_atoms, double rc2, int sel, int* __restrict__ nlist,

@@ -1157,7 +1157,9 @@ void launch_attn_bwd_f32(const AttnArgs& a, cudaStream_t st) {
 
 // ------------------------------------------------------------- descriptor
 // T = R^T G / sel (4 x m1); D = T^T T[:, :axis]; X = [D (row-major), Z[t_i]].
-__global__ void k_desc_fwd(DescArgs a) {
+// A block of 128 threads per atom, 10 blocks per SM (48 registers): the kernel
+// waits on its loads, and more resident warps hide more of them.
+__global__ void __launch_bounds__(128, 10) k_desc_fwd(DescArgs a) {
   extern __shared__ float sm[];
   float* Ts = sm;  // [4][m1]
   const int atom = blockIdx.x;
@@ -1229,54 +1231,55 @@ __global__ void k_desc_bwd(DescArgs a) {
   float* Ts = sm;              // [4][m1]
   float* dTs = Ts + 4 * m1;    // [4][m1]
   float* dD = dTs + 4 * m1;    // [m1][axis]
+  float* dDt = dD + m1 * ax;   // [axis][m1]: dD transposed, so that threads with consecutive p read consecutive words
   const int atom = blockIdx.x;
   const int nn = a.nnei[atom];
   const size_t base = (size_t)atom * NP;
   const float inv_sel = 1.0f / (float)a.sel;
   for (int t = threadIdx.x; t < 4 * m1; t += blockDim.x) Ts[t] = a.T[(size_t)atom * 4 * m1 + t];
-  for (int t = threadIdx.x; t < m1 * ax; t += blockDim.x) dD[t] = a.dX[(size_t)atom * a.fit_in + t];
+  for (int t = threadIdx.x; t < m1 * ax; t += blockDim.x) {
+    const float v = a.dX[(size_t)atom * a.fit_in + t];
+    dD[t] = v;
+    dDt[(t % ax) * m1 + t / ax] = v;
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < 4 * m1; t += blockDim.x) {
     const int c = t / m1, p = t % m1;
     float v = 0.f;
-    for (int b = 0; b < ax; ++b) v = fmaf(dD[p * ax + b], Ts[c * m1 + b], v);
+    for (int b = 0; b < ax; ++b) v = fmaf(dDt[b * m1 + p], Ts[c * m1 + b], v);
     if (p < ax)
       for (int q = 0; q < m1; ++q) v = fmaf(dD[q * ax + p], Ts[c * m1 + q], v);
     dTs[t] = v * inv_sel;
   }
   __syncthreads();
   if (a.cq) {
-    // dG in column quads (consecutive threads -> consecutive rows), live rows
-    // only: the fused layer kernels and the embedding adjoint read no others
+    // A thread per row: its dG row in column quads (consecutive threads ->
+    // consecutive rows; live rows only: the fused layer kernels and the
+    // embedding adjoint read no others) and its dR row, with the columns of
+    // dT read as float4 broadcasts (m1 % 4 == 0)
+    const int q4 = m1 / 4;
     float4* dG4 = reinterpret_cast<float4*>(a.dG + base * m1);
-    const float4* R4 = reinterpret_cast<const float4*>(a.R) + base;
-    for (int idx = threadIdx.x; idx < nn * (m1 / 4); idx += blockDim.x) {
-      const int q = idx / nn, s = idx % nn;
-      const float4 r = R4[s];
-      float4 v;
-      float* vp = &v.x;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int p = 4 * q + k;
-        vp[k] = r.x * dTs[p] + r.y * dTs[m1 + p] + r.z * dTs[2 * m1 + p] + r.w * dTs[3 * m1 + p];
-      }
-      dG4[(size_t)q * NP + s] = v;
-    }
-    // dR rows: a thread per row
     const float4* G4 = reinterpret_cast<const float4*>(a.G + base * m1);
+    const float4* dT4 = reinterpret_cast<const float4*>(dTs);
     for (int s = threadIdx.x; s < NP; s += blockDim.x) {
       float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
       if (s < nn) {
-#pragma unroll 5
-        for (int q = 0; q < m1 / 4; ++q) {
+        const float4 r = reinterpret_cast<const float4*>(a.R)[base + s];
+#pragma unroll 1  // at 48 registers 10 blocks fit per SM (unrolled: 66 and 7, 30 % slower)
+        for (int q = 0; q < q4; ++q) {
           const float4 g = G4[(size_t)q * NP + s];
+          const float4 t[4] = {dT4[q], dT4[q4 + q], dT4[2 * q4 + q], dT4[3 * q4 + q]};
           const float gg[4] = {g.x, g.y, g.z, g.w};
+          float4 v;
+          float* vp = &v.x;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const int p = 4 * q + k;
-            d0 = fmaf(gg[k], dTs[p], d0); d1 = fmaf(gg[k], dTs[m1 + p], d1);
-            d2 = fmaf(gg[k], dTs[2 * m1 + p], d2); d3 = fmaf(gg[k], dTs[3 * m1 + p], d3);
+            const float t0 = (&t[0].x)[k], t1 = (&t[1].x)[k], t2 = (&t[2].x)[k], t3 = (&t[3].x)[k];
+            vp[k] = r.x * t0 + r.y * t1 + r.z * t2 + r.w * t3;
+            d0 = fmaf(gg[k], t0, d0); d1 = fmaf(gg[k], t1, d1);
+            d2 = fmaf(gg[k], t2, d2); d3 = fmaf(gg[k], t3, d3);
           }
+          dG4[(size_t)q * NP + s] = v;
         }
       }
       reinterpret_cast<float4*>(a.dR)[base + s] = make_float4(d0, d1, d2, d3);
@@ -1329,7 +1332,7 @@ void launch_desc_fwd(const DescArgs& a, cudaStream_t st) {
 }
 void launch_desc_bwd(const DescArgs& a, cudaStream_t st) {
   if (a.n == 0) return;
-  size_t sm = sizeof(float) * (8 * a.m1 + a.m1 * a.axis);
+  size_t sm = sizeof(float) * (8 * a.m1 + 2 * a.m1 * a.axis);
   k_desc_bwd<<<a.n, 128, sm, st>>>(a);
   note_launch();
 }
