@@ -581,13 +581,17 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_fwd_bf16x(const __grid_c
         }
         *stg4(stg, row, (c0 >> 2) + q) = make_float4(o[0], o[1], o[2], o[3]);
       }
-      if (part == 0) {  // columns past 128 (m1 = 128: the row sum and padding)
+      if (part == 0 && row < nn) {  // columns past 128 (m1 = 128: the row sum and padding)
         float4* out = reinterpret_cast<float4*>(a.PG + (base + row) * a.ldpg);
         for (int c = 128; c < a.ldpg; c += 4) out[c >> 2] = make_float4(c == a.m1 ? psum : 0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
-    stg_to_global<false>(stg, a.PG + base * a.ldpg, a.ldpg, 128, a.ldpg < 128 ? a.ldpg : 128);
+    // live rows only: every later reader of P G works row by row, and the
+    // cores read no row past the last neighbour.  (The adjoint core's dE/dQ,
+    // dE/dK stores stay whole-block: restricted to the live rows they made
+    // the width-256 core 16 % slower.)
+    stg_to_global<false>(stg, a.PG + base * a.ldpg, a.ldpg, nn, a.ldpg < 128 ? a.ldpg : 128);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
