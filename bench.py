@@ -79,6 +79,9 @@ def _args():
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle centres per --impl reference step")
     ap.add_argument("--md-steps", type=int, default=1000, help="graph-captured velocity-Verlet steps to time (0: skip)")
     ap.add_argument("--no-student", action="store_true", help="skip the distilled-student line")
+    ap.add_argument("--student-frames", type=int, default=0,
+                    help="also run the student configuration at full size with this many teacher frames of the "
+                         "measured box (20000: about 15 minutes; 0: skip)")
     ap.add_argument("--model", default="dpa1", choices=sorted(MODELS), help="dpa1: the measured model")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-frame dp_compute_batch line")
     ap.add_argument("--scale-natoms", type=int, default=250000,
@@ -277,6 +280,76 @@ def _student_line(dev, coord, atype, box, full_rates, batch=16, md_steps=100):
     base.close()
     acc["frames"] = {"train": len(wf), "held_out": len(held), "system": "three 192-atom water boxes, 10 K"}
     out["distillation"] = acc
+    return out
+
+
+def _student_config_line(dev, coord, atype, box, nframes, batch=16, held_traj=25):
+    """The distilled-student configuration at full size: ``nframes`` teacher
+    frames of the measured box from full-model MD (fp16x; 2 fs trajectories at
+    10 K from fresh Maxwell-Boltzmann draws, dt 0.25 fs, a frame every 2
+    steps), all held in device memory; one epoch of training in batches of
+    ``batch`` frames with the fitting net's products as BF16 two-term splits
+    (bf16x); the held-out force error before and after against the family's
+    floor; and student MD on the box with the full-model check every 10 steps
+    at 0.05 eV/A, trained against untrained."""
+    import math
+
+    import torch
+
+    import synth
+    import paper_2604_07276_gb300 as dp
+    from paper_2604_07276_gb300 import md as dmd, student as stu
+
+    d = tempfile.mkdtemp(prefix="dpa1sc_")
+    tcfg, tw = synth.teacher_weights(ln_gain=3e-3)
+    scfg, bw = synth.teacher_base_weights(synth.TEACHER_BASE_OUT_SCALE)
+    sw = synth.perturbed(bw, 0.03, seed=21)
+    tpath, bpath, spath = (os.path.join(d, f) for f in ("teacher.bin", "base.bin", "student.bin"))
+    synth.write_weights(tpath, tcfg, tw)
+    synth.write_weights(bpath, scfg, bw)
+    synth.write_weights(spath, scfg, sw)
+    n = len(coord)
+    teacher = dp.DPA1(tpath, precision="fp16x", device=dev.index)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    t0 = time.perf_counter()
+    frames = stu.teacher_frames(teacher, [(coord, atype, box)], synth.MASSES, n_traj=math.ceil(nframes / 4), steps=8,
+                                every=2, dt=0.25, temperature=10.0, seed=1)[:nframes]
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    frames_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
+    held = stu.teacher_frames(teacher, [(coord, atype, box)], synth.MASSES, n_traj=held_traj, steps=8, every=4,
+                              dt=0.25, temperature=10.0, seed=2)
+    out = {"frames": len(frames), "box_atoms": n, "batch": batch, "held_out_frames": len(held),
+           "generate_s": gen_s, "generate_frames_per_s": len(frames) / gen_s,
+           "frames_device_bytes": frames_bytes}
+    base = dp.DPA1(bpath, precision="fp32", device=dev.index)
+    out["floor_force_rmse"] = stu.force_rmse(base, held)
+    base.close()
+    s = dp.DPA1(spath, precision="bf16x", device=dev.index)
+    s0 = dp.DPA1(spath, precision="bf16x", device=dev.index)
+    out["held_out_force_rmse_before"] = stu.force_rmse(s, held)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    hist = stu.train(s, frames, epochs=1, batch=batch, lr0=1e-5, lr_end=1e-6)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    out["train_s"] = train_s
+    out["train_frames_per_s"] = len(frames) / train_s
+    out["adam_steps"] = len(hist)
+    out["loss_first_last_batch"] = [float(hist[0][0]), float(hist[-1][0])]
+    out["held_out_force_rmse_after"] = stu.force_rmse(s, held)
+    del frames
+    vel = synth.maxwell_boltzmann(atype, 10.0, seed=33)
+    runs = {}
+    for name, mdl in (("trained", s), ("untrained", s0)):
+        st = dmd.MDState(coord, vel, synth.MASSES[atype], box, atype)
+        u_s, u_t, checks = stu.md_with_fallback(mdl, teacher, st, nsteps=40, dt=0.25, check_every=10,
+                                                threshold=0.05)
+        runs[name] = {"student_segments": u_s, "fallback_segments": u_t, "check_force_rmse": checks}
+    out["md_at_0.05"] = {"steps": 40, "dt_fs": 0.25, "check_every": 10, **runs}
+    s.close()
+    s0.close()
+    teacher.close()
     return out
 
 
@@ -596,6 +669,9 @@ def run_ours(a):
     if not a.no_student:
         student = _student_line(dev, coord, atype, box,
                                 {p: job_rate(1, n, a.steps, rr["ms"] / 1e3) for p, rr in results.items()})
+    if a.student_frames > 0:
+        student = dict(student or {})
+        student["configuration_run"] = _student_config_line(dev, coord, atype, box, a.student_frames)
 
     # parity of this run against the FP64 oracle over the whole box: every
     # atomic energy, every force, the total energy and the virial
