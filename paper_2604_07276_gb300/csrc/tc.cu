@@ -101,8 +101,9 @@ __device__ __forceinline__ void prefetch_atom(const LayerArgs& a, int atom, bool
 // (rhat, w) table and the barriers.  Slot use per atom: G (hi, lo) in A, B
 // until P G is formed; Q, K in C, D; P (hi, lo) in C, D; then P G in A and
 // Wvo, streamed per atom by a bulk asynchronous copy, in D (its residue in
-// C).  TMEM columns: [Q K] accumulators 0-255 (S and P G reuse 0-127, Y
-// 128-239) and the FP32 layer input kept at 384-511 for the residual.
+// C).  TMEM columns: [Q K] accumulators 0-255 (S and P G reuse 0-127) and Y
+// at 256-367, where it waits for its LayerNorm: an atom's LayerNorm runs
+// while the next atom's [Q K] product is on the tensor cores.
 // Thread layout: warp w owns TMEM lane quadrant w % 4 (rows 32 (w % 4) ..
 // +31) and column quarter w / 4 (32 columns).
 constexpr int F_SLOT_A = 0, F_SLOT_B = TILE, F_SLOT_C = 2 * TILE, F_SLOT_D = 3 * TILE, F_W = 4 * TILE;
@@ -171,6 +172,72 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
   if (issuer && (int)blockIdx.x < a.n) fetch_inputs(blockIdx.x);
   // neighbour counts are read one atom ahead
   int nn_next = (int)blockIdx.x < a.n ? a.nnei[blockIdx.x] : 0;
+  // LayerNorm and residual of an atom whose Y = P G Wvo is in TMEM [256,
+  // 368): G_l+1 = G_l + LN(w_j Y + bo) on its live rows (G_l read again, from
+  // L2), and the normalised input yhat and 1 / sigma for the adjoint.  The
+  // row exchanges park in slot C, which is free between the layer input's
+  // copy and Q (a row's line is only touched by that row's four threads, and
+  // each exchange ends with their barrier).
+  auto layer_norm_out = [&](size_t lbase, int lnn, float lw) {
+    const bool lrv = row < lnn;
+    const RowXchg xr(sC, row, part, lane, quad);
+    float v[32];
+    tmem_ld32(tm + lane_off + 256 + c0, v);
+    float s1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int c = c0 + i;
+      v[i] = c < a.m1 ? lw * v[i] + a.bo[c] : 0.f;
+      s1 += v[i];
+    }
+    const float mean = xr.sum(s1) / (float)a.m1;
+    float s2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int c = c0 + i;
+      const float d = c < a.m1 ? v[i] - mean : 0.f;
+      s2 += d * d;
+    }
+    const float var = xr.sum(s2) / (float)a.m1;
+    const float rs = 1.0f / sqrtf(var + a.eps);
+    float4* gout = reinterpret_cast<float4*>(a.Gout + lbase * a.m1);
+    uint4* yh = reinterpret_cast<uint4*>(a.yhat + lbase * a.yld);
+    float gin[32];
+    load_cq32(a.Gin + lbase * a.m1, a.m1, row, c0, gin, lrv);
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+      const int c = c0 + i;
+      if (c < a.m1 && lrv) {
+        float y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[k] = c + k < a.m1 ? (v[i + k] - mean) * rs : 0.f;
+#pragma unroll
+        for (int h = 0; h < 8; h += 4) {
+          const int cc = c + h;
+          if (cc < a.m1) {
+            float4 g = make_float4(gin[i + h], gin[i + h + 1], gin[i + h + 2], gin[i + h + 3]);
+            g.x += y[h] * a.gamma[cc] + a.beta[cc];
+            g.y += y[h + 1] * a.gamma[cc + 1] + a.beta[cc + 1];
+            g.z += y[h + 2] * a.gamma[cc + 2] + a.beta[cc + 2];
+            g.w += y[h + 3] * a.gamma[cc + 3] + a.beta[cc + 3];
+            gout[(cc >> 2) * NP + row] = g;
+          }
+        }
+        uint4 u;
+        u.x = pack_bf16(y[0], y[1]);
+        u.y = pack_bf16(y[2], y[3]);
+        u.z = pack_bf16(y[4], y[5]);
+        u.w = pack_bf16(y[6], y[7]);
+        yh[(c >> 3) * NP + row] = u;
+      }
+    }
+    if (part == 0 && lrv) a.rstd[lbase + row] = rs;
+  };
+  // the atom whose LayerNorm is pending
+  bool have_prev = false;
+  size_t prev_base = 0;
+  int prev_nn = 0;
+  float prev_w = 0.f;
 
   for (int atom = blockIdx.x; atom < a.n && sy.ok; atom += gridDim.x) {
     const int nn = nn_next;
@@ -180,10 +247,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     if (issuer) prefetch_atom(a, next, false);
     si.wait();
     float v[32];
-    // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B), and
-    // kept in TMEM for the residual; rows past the last neighbour as zeros
+    // G_l (FP32) -> 16-bit slot A (+ its rounding residue in slot B); rows
+    // past the last neighbour as zeros
     load_cq32(reinterpret_cast<const float*>(sC), a.m1, row, c0, v, rv);
-    tmem_st32(tm + lane_off + 384 + c0, v);
     set_bias_ones(v, c0, a.m1);
     store_row32<F16>(sA, row, c0, v);
     if (F16) store_row32<F16, true>(sB, row, c0, v);
@@ -194,6 +260,8 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       if (F16) mma_block<F16>(tm + 0, tB, false, 128, tWqk, false, 256, 256, KS_M1, true);
       mma_commit(bar_q);
     }
+    // meanwhile: the previous atom's LayerNorm
+    if (have_prev) layer_norm_out(prev_base, prev_nn, prev_w);
     // Q -> C, K -> D (G stays in A, B for P G)
     sq.wait();
     tmem_ld32(tm + lane_off + 0 + c0, v);
@@ -281,73 +349,23 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
     tmem_ld32(tm + lane_off + 0 + c0, v);
     store_row32<F16>(sA, row, c0, v);
     handoff();
-    // Y = P G Wvo (+ P G Wvo_lo) -> TMEM [128, 240)
+    // Y = P G Wvo (+ P G Wvo_lo) -> TMEM [256, 368)
     if (issuer && sl.wait()) {
-      mma_block<F16>(tm + 128, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, KS_M1, false);
-      if (F16) mma_block<F16>(tm + 128, tA, false, 128, tC, false, WO_ROWS, WO_ROWS, KS_M1, true);
+      mma_block<F16>(tm + 256, tA, false, 128, tD, false, WO_ROWS, WO_ROWS, KS_M1, false);
+      if (F16) mma_block<F16>(tm + 256, tA, false, 128, tC, false, WO_ROWS, WO_ROWS, KS_M1, true);
     }
     commit_and_sync(sy, issuer);
     // C, D and the key table are dead: the next atom's inputs start to arrive
+    // (no thread reads C, D or the key table again for this atom; its
+    // LayerNorm runs during the next atom's [Q K] product)
     if (issuer && next < a.n) fetch_inputs(next);
     if (next < a.n) nn_next = a.nnei[next];
-    // LayerNorm, residual
-    {
-      const RowXchg xr(sB, row, part, lane, quad);  // G_lo is dead
-      tmem_ld32(tm + lane_off + 128 + c0, v);
-      float s1 = 0.f;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int c = c0 + i;
-        v[i] = c < a.m1 ? w_row * v[i] + a.bo[c] : 0.f;
-        s1 += v[i];
-      }
-      const float mean = xr.sum(s1) / (float)a.m1;
-      float s2 = 0.f;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int c = c0 + i;
-        const float d = c < a.m1 ? v[i] - mean : 0.f;
-        s2 += d * d;
-      }
-      const float var = xr.sum(s2) / (float)a.m1;
-      const float rs = 1.0f / sqrtf(var + a.eps);
-      float4* gout = reinterpret_cast<float4*>(a.Gout + base * a.m1);
-      uint4* yh = reinterpret_cast<uint4*>(a.yhat + base * a.yld);
-      float gin[32];
-      tmem_ld32(tm + lane_off + 384 + c0, gin);
-#pragma unroll
-      for (int i = 0; i < 32; i += 8) {
-        const int c = c0 + i;
-        if (c < a.m1 && rv) {
-          float y[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) y[k] = c + k < a.m1 ? (v[i + k] - mean) * rs : 0.f;
-#pragma unroll
-          for (int h = 0; h < 8; h += 4) {
-            const int cc = c + h;
-            if (cc < a.m1) {
-              float4 g = make_float4(gin[i + h], gin[i + h + 1], gin[i + h + 2], gin[i + h + 3]);
-              g.x += y[h] * a.gamma[cc] + a.beta[cc];
-              g.y += y[h + 1] * a.gamma[cc + 1] + a.beta[cc + 1];
-              g.z += y[h + 2] * a.gamma[cc + 2] + a.beta[cc + 2];
-              g.w += y[h + 3] * a.gamma[cc + 3] + a.beta[cc + 3];
-              gout[(cc >> 2) * NP + row] = g;
-            }
-          }
-          uint4 u;
-          u.x = pack_bf16(y[0], y[1]);
-          u.y = pack_bf16(y[2], y[3]);
-          u.z = pack_bf16(y[4], y[5]);
-          u.w = pack_bf16(y[6], y[7]);
-          yh[(c >> 3) * NP + row] = u;
-        }
-      }
-      if (part == 0 && rv) a.rstd[base + row] = rs;
-    }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
+    have_prev = true;
+    prev_base = base;
+    prev_nn = nn;
+    prev_w = w_row;
   }
+  if (have_prev && sy.ok) layer_norm_out(prev_base, prev_nn, prev_w);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tm, 512);
