@@ -927,10 +927,8 @@ __global__ void __launch_bounds__(XC_NT, 1) k_attn_core_bwd_bf16x(const __grid_c
         const float4 c = parts[q * 128 + tid];
         s.x += r.x + c.x; s.y += r.y + c.y; s.z += r.z + c.z; s.w += r.w + c.w;
       }
-      float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
-      float4 cur = *dg;
-      cur.x += s.x; cur.y += s.y; cur.z += s.z; cur.w += s.w;
-      *dg = cur;
+      // one writer per row in a launch: a reduction without a return
+      atomicAdd(reinterpret_cast<float4*>(a.dgeo) + base + tid, s);
     }
     fence_before_sync();
     __syncthreads();

@@ -720,10 +720,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
         const float4 c = parts[q * 128 + tid];
         s.x += r.x + c.x; s.y += r.y + c.y; s.z += r.z + c.z; s.w += r.w + c.w;
       }
-      float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
-      float4 cur = *dg;
-      cur.x += s.x; cur.y += s.y; cur.z += s.z; cur.w += s.w;
-      *dg = cur;
+      // one writer per row in a launch: a reduction without a return (the
+      // same FP32 adds as a load, add and store, without the round trip)
+      atomicAdd(reinterpret_cast<float4*>(a.dgeo) + base + tid, s);
     }
     sy.wait();
     // Slot D is free: the next atom's Wvo copy
