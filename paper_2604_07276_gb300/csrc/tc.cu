@@ -452,9 +452,11 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
     const int next = atom + (int)gridDim.x;
     if (issuer) prefetch_atom(a, next, true);  // the next atom's inputs -> L2
     // Every per-row input of the atom in one round trip (live rows only: the
-    // rows past the last neighbour are not kept)
+    // rows past the last neighbour are not kept).  With FP16 operands the
+    // loads are issued before the TMEM read of the layer-input row, which the
+    // compiler does not move loads across (with BF16 that order spills)
     float v[32];
-    tmem_ld32(tm + lane_off + 0 + c0, v);
+    if constexpr (!F16) tmem_ld32(tm + lane_off + 0 + c0, v);
     const float rs = rv ? a.rstd[base + row] : 0.f;
     const float2 sst = rv ? a.smax[base + row] : make_float2(0.f, 0.f);
     float4 kr = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -476,6 +478,7 @@ __global__ void __launch_bounds__(NT, 1) k_layer_bwd_tc(const __grid_constant__ 
         yy[q] = c < a.m1 && rv ? yh8[(c >> 3) * NP + row] : make_uint4(0u, 0u, 0u, 0u);
       }
     }
+    if constexpr (F16) tmem_ld32(tm + lane_off + 0 + c0, v);
     if (tid < 128) s_key[tid] = kr;
     // P0a: G_l -> A (+ G_lo -> B), the bias columns set to 1
     set_bias_ones(v, c0, a.m1);
