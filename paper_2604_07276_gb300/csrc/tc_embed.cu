@@ -585,7 +585,9 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   // half 1 hands its part to half 0, which owns the row's dR update
   if (H == 1) xch[row] = dx;
   __syncthreads();
-  if (H == 0 && rv) a.dR[rowg * 4] += dx + xch[row];
+  // one writer per row in a launch: a reduction without a return (the same
+  // FP32 add as a load, add and store, without waiting for the load)
+  if (H == 0 && rv) atomicAdd(a.dR + rowg * 4, dx + xch[row]);
 }
 
 template <class S, bool F16>
