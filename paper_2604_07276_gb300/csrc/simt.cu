@@ -1037,10 +1037,8 @@ __global__ void __launch_bounds__(FTF, 1) k_attn_bwd_f32(AttnArgs a, float scale
         const float4 c = colp[q * NP + tid];
         acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
       }
-      float4* dg = reinterpret_cast<float4*>(a.dgeo) + base + tid;
-      float4 cur = *dg;
-      cur.x += acc.x; cur.y += acc.y; cur.z += acc.z; cur.w += acc.w;
-      *dg = cur;
+      // one writer per row in a launch: a reduction without a return
+      atomicAdd(reinterpret_cast<float4*>(a.dgeo) + base + tid, acc);
     }
     const int nn4 = (nn + 3) & ~3;
     for (int c0 = 0; c0 < A; c0 += 128) {
