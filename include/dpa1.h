@@ -227,6 +227,15 @@ DP_API int dp_inspect_weights(const char* weights_path, int* ints16, double* dbl
  * dp_status. */
 DP_API long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t bytes);
 
+/* Diagnostics: fill the model's whole workspace (every intermediate buffer of
+ * a call, not the weights) with 0xFF bytes, i.e. NaN in every floating-point
+ * array and -1 in every integer one, and wait for it.  A later call must give
+ * the same results bit for bit as before: no stage may depend on what an
+ * earlier call left behind, nor on memory it never writes (e.g. the rows past
+ * an atom's last neighbour, which the 16-bit paths neither read nor write).
+ * Errors: DP_ERR_ARG for a null model, DP_ERR_CUDA. */
+DP_API int dp_debug_poison(dp_model* m);
+
 /* Profiling: dp_set_profiling(m, 1) clears the record and makes every later
  * call record a CUDA event on its stream after each stage (the per-region
  * timing of the paper's profiling setup, Sec. V-D); 0 switches it off.

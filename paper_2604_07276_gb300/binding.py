@@ -22,7 +22,7 @@ STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_IO", -3: "DP_ERR_BOX", -4: "
 PRECISION = {"fp32": 0, "bf16": 1, "fp16x": 2, "bf16x": 3}
 
 EXPORTS = ("dp_init", "dp_compute", "dp_compute_device", "dp_compute_local", "dp_compute_device_local", "dp_compute_batch", "dp_reserve", "dp_set_precision",
-           "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy",
+           "dp_get_status", "dp_nlist_device", "dp_stats", "dp_inspect_weights", "dp_debug_copy", "dp_debug_poison",
            "dp_set_profiling", "dp_stage_times", "dp_kernel_launches", "dp_nlist_noalloc", "dp_md_run", "dp_param_count", "dp_get_params",
            "dp_set_params", "dp_get_grad", "dp_zero_grad", "dp_train_frame", "dp_adam_step", "dp_last_error",
            "dp_free")
@@ -62,6 +62,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dp_inspect_weights.argtypes = [ctypes.c_char_p, I, D]
     lib.dp_debug_copy.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t]
     lib.dp_debug_copy.restype = ctypes.c_longlong
+    lib.dp_debug_poison.argtypes = [P]
     lib.dp_set_profiling.argtypes = [P, ctypes.c_int]
     lib.dp_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     F = ctypes.POINTER(ctypes.c_float)
@@ -235,6 +236,10 @@ class DPA1:
         if r < 0:
             _check(int(r))
         return out
+
+    def debug_poison(self) -> None:
+        """Fill the model's workspace with NaN / -1 bit patterns (dp_debug_poison)."""
+        _check(self.lib.dp_debug_poison(self.h))
 
     # -- training (models without attention, FP32) ----------------------------
     def param_count(self) -> int:

@@ -1253,6 +1253,14 @@ int dp_stats(const dp_model* m, int* max_nnei, long long* n_truncated) {
   return DP_OK;
 }
 
+int dp_debug_poison(dp_model* m) {
+  if (check_model(m)) return DP_ERR_ARG;
+  CUDA_TRY(cudaSetDevice(m->device));
+  if (m->ws.mem) CUDA_TRY(cudaMemset(m->ws.mem, 0xFF, m->ws.bytes));
+  CUDA_TRY(cudaDeviceSynchronize());
+  return DP_OK;
+}
+
 long long dp_debug_copy(dp_model* m, const char* name, void* host_dst, size_t bytes) {
   if (check_model(m) || !name || !host_dst) return DP_ERR_ARG;
   Workspace& ws = m->ws;
