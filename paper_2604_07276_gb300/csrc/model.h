@@ -200,6 +200,7 @@ int tc_init_weights(dp_model* m, const HostArrays& arrays, std::string& msg);
 int tc_init_embedding(dp_model* m, const HostArrays& arrays, std::string& msg);
 void tc_embed_bf16(dp_model* m, int n, const int* atype, bool bwd, float* G0, const float* dG0, float* dR,
                    float* H12, cudaStream_t st);
+void tc_live_rows(dp_model* m, int n, cudaStream_t st);
 void tc_embed_fused(dp_model* m, int n, const int* atype, bool bwd, cudaStream_t st);
 void tc_plan_buffers(dp_model* m, Arena& a, int cap);
 void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st);

@@ -286,8 +286,9 @@ __global__ void __launch_bounds__(NT, 1) k_layer_fwd_tc(const __grid_constant__ 
       const float4 kj = s_key[row];
       const float wj = kj.w;
       w_row = wj;
-      // a column quarter past the last neighbour has nothing to compute
-      const bool live = c0 < nn;
+      // a column quarter past the last neighbour, or a lane quadrant whose
+      // rows are all past it, has nothing to compute
+      const bool live = c0 < nn && quad * 32 < nn;
       float mx = -INFINITY;
       if (live) {
 #pragma unroll
@@ -911,6 +912,9 @@ void tc_plan_buffers(dp_model* m, Arena& a, int cap) {
   ws.tc.p[3] = m->tcw.emb_W1_t ? nullptr : a.take<float>(rows * m->m1);
   // layers 1 and 2 of the tensor-core embedding net, for its adjoint
   ws.tc.p[5] = m->tcw.emb_W1_t ? a.take<float>(rows * (size_t)(m->emb[0] + m->emb[1])) : nullptr;
+  // the live neighbour rows the tensor-core embedding net runs over, and their number
+  ws.tc.p[6] = m->tcw.emb_W1_t ? a.take<int>(rows) : nullptr;
+  ws.tc.p[7] = m->tcw.emb_W1_t ? a.take<int>(64) : nullptr;
 }
 
 
@@ -952,6 +956,7 @@ void tc_run_network(dp_model* m, int n, const int* atype, cudaStream_t st) {
   ea.w = m->emb_packed; ea.Gt = m->Gt; ea.b0t = m->b0t; ea.G0 = rm_stage;
   const bool emb_tc = m->tcw.emb_W1_t != nullptr;
   if (emb_tc) {
+    tc_live_rows(m, n, st);
     tc_embed_fused(m, n, atype, false, st);
   } else {
     launch_embed_fwd(ea, m->emb, st);

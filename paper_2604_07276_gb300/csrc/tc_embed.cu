@@ -86,7 +86,10 @@ struct EmbedTcArgs {
   int n, ntypes;
   int rm;                 // G0 and dG0 row-major (the modular layer layout) instead of interleaved
   int live_only;          // G0's rows past the last neighbour are not written (their content is
-                          // undefined: the fused layer kernels never read them); else zeros
+                          // undefined: the fused layer kernels never read them); else zeros.
+                          // The live-row kernels need 1 (a row past the list's end stores nothing)
+  const int* rowmap;      // live-row kernels: the live rows (atom * NP + slot) in tile order
+  const int* nrows;       // live-row kernels: their number (device)
   int* err;
   float W0[32], b0[32], b1[64], b2[128];  // the net's first layer and biases (first E0 / E1 / E2 used)
 };
@@ -96,7 +99,8 @@ struct EmbedTcArgs {
 // the layer-2 units b in [0, SPLIT), half 1 those in [SPLIT, E1); a layer-3
 // output c belongs to the owner of c % E1 (the residual input it needs), so no
 // row data crosses between the halves except one partial sum at the end of
-// the adjoint.  Both halves evaluate the E0 layer-1 units.
+// the adjoint.  Layer 1 is split between the halves (units 0-15 and the
+// rest), which exchange their units through TMEM.
 template <bool F16>
 __device__ __forceinline__ void emb_store8(uint8_t* tile, int r, int c0, int R, const float* v, bool lo) {
   float x[8];
@@ -209,14 +213,15 @@ __device__ __forceinline__ void embed_tc_front(const EmbedTcArgs& a, uint8_t* sm
 // Z3 = H2 W2; returns once Z3 is in TMEM columns [64, 64 + E2P).
 template <class S, bool F16, int H, class BeforeZ3>
 __device__ __forceinline__ void embed_bwd_front(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, Sync& sy, int row,
-                                                bool rv, int atom, float* h1, float* h2, BeforeZ3 before_z3) {
+                                                bool rv, int atom, int slot, float* h1, float* h2,
+                                                BeforeZ3 before_z3) {
   using O = EmbOwn<S, H>;
   uint8_t* sW2h = sm + 2 * S::T1;
   uint8_t* sW2l = sW2h + S::T2;
   uint8_t* sH2h = sm + S::WIMG + 2 * EMB_TA;
   uint8_t* sH2l = sH2h + EMB_TA;
   const bool issuer = threadIdx.x == 0;
-  const float* hs = a.H12 + (size_t)atom * (S::E0 + S::E1) * NP + row;  // live rows only were stored
+  const float* hs = a.H12 + (size_t)atom * (S::E0 + S::E1) * NP + slot;  // live rows only were stored
 #pragma unroll
   for (int p = 0; p < S::E0; ++p) h1[p] = rv ? hs[p * NP] : 0.f;
 #pragma unroll
@@ -330,7 +335,7 @@ __device__ __forceinline__ void embed_fwd_out(const EmbedTcArgs& a, uint32_t tad
       o.x = rv ? (h2[c % S::E1 - O::b0] + tanhf(z[i] + a.b2[c])) * (1.f + g2.x) : 0.f;
       o.y = rv ? (h2[(c + 1) % S::E1 - O::b0] + tanhf(z[i + 1] + a.b2[c + 1])) * (1.f + g2.y) : 0.f;
       if (rv || !a.live_only)
-        *reinterpret_cast<float2*>(out_blk + (a.rm ? (size_t)row * S::E2 + c : cq_off(row, c))) = o;
+        __stcs(reinterpret_cast<float2*>(out_blk + (a.rm ? (size_t)row * S::E2 + c : cq_off(row, c))), o);
     }
   }
 }
@@ -449,14 +454,14 @@ __device__ __forceinline__ void embed_bwd_prefetch16(const float4* dg, bool rm, 
 // processed.
 template <class S, bool F16, int H>
 __device__ __forceinline__ void embed_bwd_dz3(const EmbedTcArgs& a, uint32_t taddr, const float* gt, const float4* dg,
-                                              bool rv, int row, uint8_t* sDZ3h, uint8_t* sDZ3l, float* dh2,
+                                              bool rv, int row, int slot, uint8_t* sDZ3h, uint8_t* sDZ3l, float* dh2,
                                               float4* dcur) {
   using O = EmbOwn<S, H>;
   using D = EmbDz3<S, H>;
 #pragma unroll
   for (int k = 0; k < S::NK3; ++k) {
-    if (k > 0 && D::any16(k)) embed_bwd_load16<S, H>(dg, a.rm, k, row, rv, dcur);
-    if (k + 2 < S::NK3 && D::any16(k + 2)) embed_bwd_prefetch16<S, H>(dg, a.rm, k + 2, row, rv);
+    if (k > 0 && D::any16(k)) embed_bwd_load16<S, H>(dg, a.rm, k, slot, rv, dcur);
+    if (k + 2 < S::NK3 && D::any16(k + 2)) embed_bwd_prefetch16<S, H>(dg, a.rm, k + 2, slot, rv);
     if (D::any16(k)) {
     float z[16];
     tmem_ld16(taddr + 64 + 16 * k, z);
@@ -533,10 +538,13 @@ __device__ __forceinline__ void embed_bwd_dz2(uint32_t taddr, const float* h1, c
   }
 }
 
-template <class S, bool F16, int H>
+// rowg = atom * NP + slot: the row's place in the atom blocks (row is its
+// place in the tile); pre() runs with the row's first loads, before the wait
+// for Z3.
+template <class S, bool F16, int H, class Pre>
 __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm, uint32_t tm, uint32_t lane_off,
                                                Sync& sy, int row, bool rv, size_t rowg, const float* gt,
-                                               const float4* dg, float* xch) {
+                                               const float4* dg, float* xch, Pre pre) {
   using O = EmbOwn<S, H>;
   const bool issuer = threadIdx.x == 0;
   uint8_t* sW1h = sm;
@@ -551,14 +559,16 @@ __device__ __forceinline__ void embed_bwd_tail(const EmbedTcArgs& a, uint8_t* sm
   uint8_t* sDZ2l = sDZ2h + EMB_TA;
   float h1[S::E0], h2[O::nb];
   float4 d0[4];
-  embed_bwd_front<S, F16, H>(a, sm, tm, sy, row, rv, (int)(rowg / NP), h1, h2, [&] {
-    embed_bwd_load16<S, H>(dg, a.rm, 0, row, rv, d0);
-    embed_bwd_prefetch16<S, H>(dg, a.rm, 1, row, rv);
+  const int atom = (int)(rowg / NP), slot = (int)(rowg - (size_t)atom * NP);
+  embed_bwd_front<S, F16, H>(a, sm, tm, sy, row, rv, atom, slot, h1, h2, [&] {
+    embed_bwd_load16<S, H>(dg, a.rm, 0, slot, rv, d0);
+    embed_bwd_prefetch16<S, H>(dg, a.rm, 1, slot, rv);
+    pre();
   });
   float dh2[O::nb];
 #pragma unroll
   for (int b = 0; b < O::nb; ++b) dh2[b] = 0.f;
-  embed_bwd_dz3<S, F16, H>(a, tm + lane_off, gt, dg, rv, row, sDZ3h, sDZ3l, dh2, d0);
+  embed_bwd_dz3<S, F16, H>(a, tm + lane_off, gt, dg, rv, row, slot, sDZ3h, sDZ3l, dh2, d0);
   handoff();
   // dH2 (product part) = dZ3 W2^T -> TMEM [0, 64)
   if (issuer)
@@ -627,10 +637,206 @@ __global__ void __launch_bounds__(EMB_THREADS, S::MIN_CTAS) k_embed_tc_bwd(const
     embed_tc_atom_start<S>(a, s_gt, nullptr, atom, true);  // visible after the front's barriers
     const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)atom * NP * S::E2);
     if (half == 0)
-      embed_bwd_tail<S, F16, 0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * S::E2, dg, xch);
+      embed_bwd_tail<S, F16, 0>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * S::E2, dg, xch, [] {});
     else
-      embed_bwd_tail<S, F16, 1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * S::E2, dg, xch);
+      embed_bwd_tail<S, F16, 1>(a, sm, tm, lane_off, sy, row, rv, rowg, s_gt + tj * S::E2, dg, xch, [] {});
     in.type(a, row);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+// ------------------------------------------------- live-row tiles
+// The net treats every neighbour row on its own, so its tiles need not
+// follow the atoms: the live-row kernels below take 128 live rows at a time
+// from one list of all atoms' live rows (atom * NP + slot), so that no lane
+// of a tile holds a row past its atom's last neighbour (with 72-103
+// neighbours per atom, per-atom tiles leave lane quadrant 3, and with it
+// one of the SM's four schedulers, idle).  A row's results do not depend on
+// where in the list it is or which rows share its tile: every product row
+// and every element-wise step is the row's own.
+
+constexpr int LR_THREADS = 256;
+
+// The list: each block takes LR_THREADS atoms, reserves room for their live
+// rows with one atomic add and writes them, an atom's slots in order.  The
+// blocks' order in the list is that of their reservations.
+__global__ void __launch_bounds__(LR_THREADS) k_live_rows(const int* __restrict__ nnei, int n, int* __restrict__ count,
+                                                          int* __restrict__ rows) {
+  __shared__ int s_warp[LR_THREADS / 32];
+  __shared__ int s_base;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int first = blockIdx.x * LR_THREADS;
+  const int nn = first + t < n ? nnei[first + t] : 0;
+  int x = nn;  // inclusive sum over the warp's atoms
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (t == 0) {
+    int tot = 0;
+    for (int k = 0; k < LR_THREADS / 32; ++k) {
+      const int c = s_warp[k];
+      s_warp[k] = tot;
+      tot += c;
+    }
+    s_base = tot > 0 ? atomicAdd(count, tot) : 0;
+  }
+  __syncthreads();
+  const int off = s_base + s_warp[w] + x - nn;  // this atom's first place in the list
+  for (int j = 0; j < 32; ++j) {                // the warp writes its atoms one at a time
+    const int nj = __shfl_sync(0xffffffffu, nn, j), oj = __shfl_sync(0xffffffffu, off, j);
+    const int aj = first + 32 * w + j;
+    for (int s = lane; s < nj; s += 32) rows[oj + s] = aj * NP + s;
+  }
+}
+
+// A row of a live-row tile: its place in the atom blocks (rg = atom * NP +
+// slot, -1 past the end of the list), s, and the centre and neighbour types.
+// map() reads the list for the next tile, rows() its s and neighbour index
+// once map's load is back, type() the types at the end of the current tile.
+struct LiveRowIn {
+  int rg = -1, nl = 0, atom = 0, slot = 0, ti = 0, tj = 0;
+  float x = 0.f;
+  __device__ void map(const EmbedTcArgs& a, int nrows, int tile, int row) {
+    const long long r = (long long)tile * 128 + row;
+    rg = r < nrows ? a.rowmap[r] : -1;
+  }
+  __device__ void rows(const EmbedTcArgs& a, bool need_x) {
+    if (rg >= 0) {
+      if (need_x) x = a.R[(size_t)rg * 4];
+      nl = a.nlist[rg];
+    }
+  }
+  __device__ void type(const EmbedTcArgs& a) {
+    const bool v = rg >= 0;
+    atom = v ? rg / NP : 0;
+    slot = v ? rg - atom * NP : 0;
+    ti = v ? a.atype[atom] : 0;
+    tj = v ? a.atype[nl] : 0;
+    x = v ? x : 0.f;
+  }
+  // the row's entry of the type-pair table (and of the first-layer bias
+  // table in concat mode): small tables, read through L1
+  __device__ const float* gt(const EmbedTcArgs& a, int e2) const {
+    return a.Gt + ((size_t)ti * a.ntypes + tj) * e2;
+  }
+};
+
+template <class S>
+__global__ void __launch_bounds__(EMB_THREADS, S::MIN_CTAS) k_embed_tc_fwd_live(const __grid_constant__ EmbedTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint64_t* bar;
+  uint32_t* s_tmem;
+  embed_tc_setup<S>(a, sm, bar, s_tmem, S::F_SMEM);
+  const uint32_t tm = *s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  Sync sy{bar, 0u, a.err};
+  const int nrows = *a.nrows;
+  const int ntiles = (nrows + 127) / 128;
+  float h1[S::E0], h2[S::E1 - S::SPLIT];
+  LiveRowIn in;
+  in.map(a, nrows, blockIdx.x, row);
+  in.rows(a, true);
+  in.type(a);
+  for (int tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
+    const LiveRowIn cur = in;
+    const bool rv = cur.rg >= 0;
+    in.map(a, nrows, tile + gridDim.x, row);
+    auto rows_next = [&] { in.rows(a, true); };
+    const float* b0row = a.b0t && rv ? a.b0t + ((size_t)cur.ti * a.ntypes + cur.tj) * S::E0 : nullptr;
+    if (half == 0)
+      embed_tc_front<S, true, 0>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
+    else
+      embed_tc_front<S, true, 1>(a, sm, tm, lane_off, sy, row, rv, cur.x, b0row, h1, h2, rows_next);
+    if (rv) {  // layers 1 and 2 of the row for the adjoint, as the per-atom kernel stores them
+      float* hs = a.H12 + (size_t)cur.atom * (S::E0 + S::E1) * NP + cur.slot;
+      if (half == 0) {
+#pragma unroll
+        for (int p = 0; p < 16; ++p) __stcs(hs + p * NP, h1[p]);
+#pragma unroll
+        for (int i = 0; i < S::SPLIT; ++i) __stcs(hs + (S::E0 + i) * NP, h2[i]);
+      } else {
+#pragma unroll
+        for (int p = 16; p < S::E0; ++p) __stcs(hs + p * NP, h1[p]);
+#pragma unroll
+        for (int i = 0; i < S::E1 - S::SPLIT; ++i) __stcs(hs + (S::E0 + S::SPLIT + i) * NP, h2[i]);
+      }
+    }
+    float* out = a.G0 + (size_t)cur.atom * NP * S::E2;
+    if (half == 0)
+      embed_fwd_out<S, 0>(a, tm + lane_off, cur.gt(a, S::E2), h2, rv, out, cur.slot);
+    else
+      embed_fwd_out<S, 1>(a, tm + lane_off, cur.gt(a, S::E2), h2, rv, out, cur.slot);
+    in.type(a);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+template <class S>
+__global__ void __launch_bounds__(EMB_THREADS, S::MIN_CTAS) k_embed_tc_bwd_live(const __grid_constant__ EmbedTcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  if ((smem_u32(sm) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_err(a.err, ERR_CAPACITY);
+    return;
+  }
+  uint64_t* bar;
+  uint32_t* s_tmem;
+  embed_tc_setup<S>(a, sm, bar, s_tmem, S::B_SMEM);
+  const uint32_t tm = *s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  float* xch = reinterpret_cast<float*>(sm + S::WIMG + 4 * EMB_TA) + EMB_MAXT * S::E2;  // [128] half 1's dE/dx
+  Sync sy{bar, 0u, a.err};
+  const int nrows = *a.nrows;
+  const int ntiles = (nrows + 127) / 128;
+  LiveRowIn in;
+  in.map(a, nrows, blockIdx.x, row);
+  in.rows(a, false);
+  in.type(a);
+  for (int tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
+    const LiveRowIn cur = in;
+    const bool rv = cur.rg >= 0;
+    in.map(a, nrows, tile + gridDim.x, row);
+    // with the row's first loads: the next tile's neighbour indices, and its
+    // atoms' dE/dG0 and layer blocks brought into L2 (by the thread of an
+    // atom's first row in that tile)
+    auto pre = [&] {
+      in.rows(a, false);
+      if (half == 0 && in.rg >= 0) {
+        const int at = in.rg / NP;
+        if (row == 0 || in.rg == at * NP) {
+          prefetch_l2(a.dG0 + (size_t)at * NP * S::E2, NP * S::E2 * sizeof(float));
+          prefetch_l2(a.H12 + (size_t)at * (S::E0 + S::E1) * NP, NP * (S::E0 + S::E1) * sizeof(float));
+        }
+      }
+    };
+    const size_t rowg = rv ? (size_t)cur.rg : 0;
+    const float4* dg = reinterpret_cast<const float4*>(a.dG0 + (size_t)cur.atom * NP * S::E2);
+    if (half == 0)
+      embed_bwd_tail<S, true, 0>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.gt(a, S::E2), dg, xch, pre);
+    else
+      embed_bwd_tail<S, true, 1>(a, sm, tm, lane_off, sy, row, rv, rowg, cur.gt(a, S::E2), dg, xch, pre);
+    in.type(a);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -675,10 +881,10 @@ std::vector<uint8_t> emb_image(const std::vector<double>& W1, const std::vector<
 
 template <class S>
 void emb_set_smem() {
-  cudaFuncSetAttribute(k_embed_tc_fwd<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::F_SMEM);
-  cudaFuncSetAttribute(k_embed_tc_bwd<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::B_SMEM);
   cudaFuncSetAttribute(k_embed_tc_fwd<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::F_SMEM);
   cudaFuncSetAttribute(k_embed_tc_bwd<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::B_SMEM);
+  cudaFuncSetAttribute(k_embed_tc_fwd_live<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::F_SMEM);
+  cudaFuncSetAttribute(k_embed_tc_bwd_live<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::B_SMEM);
 }
 
 template <class S>
@@ -731,23 +937,28 @@ int tc_init_embedding(dp_model* m, const HostArrays& arrays, std::string& msg) {
 }
 
 namespace {
-// One launch of the tensor-core embedding net: forward or adjoint, FP16
-// operand splits (the fused 16-bit paths) or BF16 ones (bf16x).
+// One launch of the tensor-core embedding net, forward or adjoint: live-row
+// tiles with FP16 operand splits (the fused 16-bit paths, given a row list),
+// or per-atom tiles with BF16 ones (bf16x).
 template <class S>
-void tc_embed_launch_s(int grid, const EmbedTcArgs& et, bool bwd, bool bf16, cudaStream_t st) {
-  if (!bwd && !bf16) k_embed_tc_fwd<S, true><<<grid, EMB_THREADS, S::F_SMEM, st>>>(et);
-  if (!bwd && bf16) k_embed_tc_fwd<S, false><<<grid, EMB_THREADS, S::F_SMEM, st>>>(et);
-  if (bwd && !bf16) k_embed_tc_bwd<S, true><<<grid, EMB_THREADS, S::B_SMEM, st>>>(et);
-  if (bwd && bf16) k_embed_tc_bwd<S, false><<<grid, EMB_THREADS, S::B_SMEM, st>>>(et);
+void tc_embed_launch_s(int grid, const EmbedTcArgs& et, bool bwd, cudaStream_t st) {
+  if (et.rowmap) {
+    if (!bwd) k_embed_tc_fwd_live<S><<<grid, EMB_THREADS, S::F_SMEM, st>>>(et);
+    if (bwd) k_embed_tc_bwd_live<S><<<grid, EMB_THREADS, S::B_SMEM, st>>>(et);
+  } else {
+    if (!bwd) k_embed_tc_fwd<S, false><<<grid, EMB_THREADS, S::F_SMEM, st>>>(et);
+    if (bwd) k_embed_tc_bwd<S, false><<<grid, EMB_THREADS, S::B_SMEM, st>>>(et);
+  }
 }
 
-void tc_embed_launch(dp_model* m, const EmbedTcArgs& et, bool bwd, bool bf16, cudaStream_t st) {
+void tc_embed_launch(dp_model* m, const EmbedTcArgs& et, bool bwd, cudaStream_t st) {
   const int per_sm = emb_is<EmbS100>(m) ? EmbS100::MIN_CTAS : EmbS128::MIN_CTAS;
+  // at most n tiles either way: n atoms, or n * NP live rows at most
   const int grid = std::min(et.n, per_sm * emb_sm_count(m->device));
   if (emb_is<EmbS100>(m))
-    tc_embed_launch_s<EmbS100>(grid, et, bwd, bf16, st);
+    tc_embed_launch_s<EmbS100>(grid, et, bwd, st);
   else
-    tc_embed_launch_s<EmbS128>(grid, et, bwd, bf16, st);
+    tc_embed_launch_s<EmbS128>(grid, et, bwd, st);
   note_launch();
 }
 
@@ -773,21 +984,37 @@ void tc_embed_bf16(dp_model* m, int n, const int* atype, bool bwd, float* G0, co
   EmbedTcArgs et = embed_tc_args(m, n, atype);
   et.G0 = G0; et.dG0 = dG0; et.dR = dR; et.H12 = H12; et.rm = 1;
   et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W2_t);
-  tc_embed_launch(m, et, bwd, true, st);
+  tc_embed_launch(m, et, bwd, st);
 }
 
 
+// The list of live neighbour rows the fused paths' embedding net runs over
+// (after the neighbour list, before the net's forward; its adjoint reads the
+// same list).
+void tc_live_rows(dp_model* m, int n, cudaStream_t st) {
+  if (n == 0) return;
+  Workspace& ws = m->ws;
+  int* count = reinterpret_cast<int*>(ws.tc.p[7]);
+  cudaMemsetAsync(count, 0, sizeof(int), st);
+  k_live_rows<<<(n + LR_THREADS - 1) / LR_THREADS, LR_THREADS, 0, st>>>(ws.nnei, n, count,
+                                                                          reinterpret_cast<int*>(ws.tc.p[6]));
+  note_launch();
+}
+
 // The embedding net of the fused 16-bit paths on the tensor cores (FP16 hi +
-// lo splits), G0 and dE/dG0 column-quad interleaved per atom: forward (G0 ->
-// G[0]), or adjoint (dE/dG0 from dG, dR[:, 0] +=).
+// lo splits) over the live-row tiles of tc_live_rows, G0 and dE/dG0
+// column-quad interleaved per atom: forward (G0 -> G[0]), or adjoint (dE/dG0
+// from dG, dR[:, 0] +=).
 void tc_embed_fused(dp_model* m, int n, const int* atype, bool bwd, cudaStream_t st) {
   if (n == 0) return;
   Workspace& ws = m->ws;
   EmbedTcArgs et = embed_tc_args(m, n, atype);
   et.G0 = ws.G[0]; et.dG0 = ws.dG; et.dR = ws.dR; et.rm = 0; et.live_only = 1;
+  et.rowmap = reinterpret_cast<const int*>(ws.tc.p[6]);
+  et.nrows = reinterpret_cast<const int*>(ws.tc.p[7]);
   et.H12 = reinterpret_cast<float*>(ws.tc.p[5]);
   et.wimg = reinterpret_cast<const uint4*>(m->tcw.emb_W1_t);
-  tc_embed_launch(m, et, bwd, false, st);
+  tc_embed_launch(m, et, bwd, st);
 }
 
 }  // namespace dpa1
