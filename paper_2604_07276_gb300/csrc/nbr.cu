@@ -184,13 +184,16 @@ k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const 
   // compacted into idx[] so that the FP64 decision below runs on full warps
   // (this part's FP64 rate is low, and a divergent FP64 branch costs the whole
   // warp)
+  // a neighbouring cell's index along an axis, wrapped without a division
+  // (offsets are -1, 0 or +1)
+  auto wrap = [](int x, int nc) { return x < 0 ? x + nc : (x >= nc ? x - nc : x); };
   int ns = 0;
   for (int dz = -oz; dz <= oz; ++dz)
     for (int dy = -oy; dy <= oy; ++dy)
       for (int dx = -ox; dx <= ox; ++dx) {
-        int nx = (cx + dx + g.nc[0]) % g.nc[0];
-        int ny = (cy + dy + g.nc[1]) % g.nc[1];
-        int nz = (cz + dz + g.nc[2]) % g.nc[2];
+        const int nx = wrap(cx + dx, g.nc[0]);
+        const int ny = wrap(cy + dy, g.nc[1]);
+        const int nz = wrap(cz + dz, g.nc[2]);
         int c = cbase + (nz * g.nc[1] + ny) * g.nc[0] + nx;
         int b = cell_start[c], e = cell_start[c + 1];
         for (int base = b; base < e; base += 32) {
@@ -255,19 +258,19 @@ k_neighbors(const double* __restrict__ coord, int n, int n_out, int base, const 
     idx[t] = 0x7fffffff;
   }
   __syncwarp();
+  // the bitonic network, a lane per compare-exchange pair (t, t + jj): pair
+  // q has t = q with a zero bit inserted at jj
   for (int k = 2; k <= P; k <<= 1)
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int t = lane; t < P; t += 32) {
-        int o = t ^ jj;
-        if (o > t) {
-          bool asc = (t & k) == 0;
-          const unsigned long long ka = key[t], kb = key[o];
-          int ia = idx[t], ib = idx[o];
-          bool sw = asc ? key_gt(ka, ia, kb, ib) : key_gt(kb, ib, ka, ia);
-          if (sw) {
-            key[t] = kb; key[o] = ka;
-            idx[t] = ib; idx[o] = ia;
-          }
+      for (int q = lane; q < (P >> 1); q += 32) {
+        const int t = ((q & ~(jj - 1)) << 1) | (q & (jj - 1)), o = t | jj;
+        const bool asc = (t & k) == 0;
+        const unsigned long long ka = key[t], kb = key[o];
+        const int ia = idx[t], ib = idx[o];
+        const bool sw = asc ? key_gt(ka, ia, kb, ib) : key_gt(kb, ib, ka, ia);
+        if (sw) {
+          key[t] = kb; key[o] = ka;
+          idx[t] = ib; idx[o] = ia;
         }
       }
       __syncwarp();
